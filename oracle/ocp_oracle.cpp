@@ -1,0 +1,748 @@
+/*
+ * CPU ORACLE for the trapezoidal direct transcription of an optimal control problem.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This is the plain, slow, obviously-correct FP64 statement of
+ * what the CUDA library computes.  Only the test-suite, the package smoke check and the
+ * CPU-baseline leg of the benchmark may load it.  It shares no code, header, table or
+ * helper with the CUDA library, and neither side includes or links the other.
+ *
+ * What it computes (paper sections in brackets):
+ *   - the NLP unknown vector  x = [X_0..X_N (nx each, node-major); U_0..U_N (nu each)]
+ *     (Sec. 3 unknown vector; Sec. 5: the state is an nx x (N+1) array, controls after it;
+ *      the trapezoid cost uses u at j = 0..N, so controls live on N+1 nodes);
+ *   - constraints, in declaration order: the initial boundary rows x(0) (the expression
+ *     X_{0,k}, bounds lcon = ucon = x0, Sec. 5), optional final rows X_{N,k}, then one
+ *     block of N trapezoidal defects per state component (Sec. 5 defect generator):
+ *         c_{k,j} = (X_{j+1,k} - X_{j,k}) - h (f_k(z_j) + f_k(z_{j+1})) / 2 ,  row nb + k N + j;
+ *   - objective: the trapezoidal Lagrange cost (Sec. 5, two objective generators summed),
+ *         F = sum_j w_j f0(z_j),  w_0 = w_N = h/2,  w_j = h otherwise,  h = T/N (uniform grid);
+ *   - gradient of F, the Jacobian of c, and the Lagrangian Hessian
+ *         H = sigma * Hess F + sum_r y_r Hess c_r   (lower triangle)
+ *     as COO with one entry per structural nonzero, sorted by (row, col);
+ *   - the products J v, J^T w, H v, defined as plain COO matrix-vector products;
+ *   - (dc/dp)^T w for the first model parameter (the Van der Pol mu).
+ *
+ * Derivatives of the model right-hand sides are derived by hand and written out in
+ * straight-line code (quotient rule for the cart-pole).  Everything is templated on the
+ * scalar type so that the same code runs in
+ *   - double                 (the oracle values),
+ *   - std::complex<double>   (complex-step derivatives used by the tests to pin the
+ *                             hand-derived derivatives against the residual itself),
+ *   - Sh                     (a running error bound: value v plus magnitude m such that the
+ *                             rounding error of v is about u*m; used for the tolerance gate
+ *                             of entries that suffer cancellation).
+ * The objective and the (dc/dp)^T w reduction use Neumaier compensated summation.
+ * Build: g++ -O2 -ffp-contract=off (no FMA contraction, host libm for sin/cos).
+ */
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdint>
+#include <cstring>
+#include <map>
+#include <utility>
+#include <vector>
+
+namespace orc {
+
+// ---------------------------------------------------------------------------------------
+// Scalar types
+// ---------------------------------------------------------------------------------------
+struct Sh {  // running error analysis: |computed - exact| <~ u * m
+  double v, m;
+  Sh(double value = 0.0, double mag = 0.0) : v(value), m(mag) {}
+};
+inline Sh operator+(Sh a, Sh b) { double v = a.v + b.v; return Sh(v, a.m + b.m + std::fabs(v)); }
+inline Sh operator-(Sh a, Sh b) { double v = a.v - b.v; return Sh(v, a.m + b.m + std::fabs(v)); }
+inline Sh operator-(Sh a) { return Sh(-a.v, a.m); }
+inline Sh operator*(Sh a, Sh b) {
+  double v = a.v * b.v;
+  return Sh(v, std::fabs(b.v) * a.m + std::fabs(a.v) * b.m + std::fabs(v));
+}
+inline Sh operator/(Sh a, Sh b) {
+  double v = a.v / b.v;
+  return Sh(v, (a.m + std::fabs(v) * b.m) / std::fabs(b.v) + std::fabs(v));
+}
+inline Sh& operator+=(Sh& a, Sh b) { a = a + b; return a; }
+inline Sh sin(Sh a) { return Sh(std::sin(a.v), std::fabs(std::cos(a.v)) * a.m + std::fabs(std::sin(a.v))); }
+inline Sh cos(Sh a) { return Sh(std::cos(a.v), std::fabs(std::sin(a.v)) * a.m + std::fabs(std::cos(a.v))); }
+
+typedef std::complex<double> Cx;
+
+inline double mag(double a) { return std::fabs(a); }
+inline double mag(const Cx& a) { return std::fabs(a.real()); }
+inline double mag(const Sh& a) { return std::fabs(a.v); }
+
+inline double val(double a) { return a; }
+inline double val(const Sh& a) { return a.v; }
+inline double shadow(const Sh& a) { return a.m; }
+
+// Neumaier (1974) compensated summation.
+template <class S>
+struct Neumaier {
+  S sum = S(0.0), comp = S(0.0);
+  void add(const S& t) {
+    S s = sum + t;
+    if (mag(sum) >= mag(t)) comp += (sum - s) + t;
+    else comp += (t - s) + sum;
+    sum = s;
+  }
+  S result() const { return sum + comp; }
+};
+
+// ---------------------------------------------------------------------------------------
+// Problem description (mirrored by a ctypes Structure in oracle.py)
+// ---------------------------------------------------------------------------------------
+enum { M_VDP = 1, M_CARTPOLE = 2, M_HEAT = 3, M_DINT = 4 };
+
+struct Prob {
+  int32_t model, nx, nu, has_final;
+  int64_t N;
+  double T;
+  double par[8];
+  int32_t npar, pad;
+  const double* q;     // running cost weights on the state (nx)
+  const double* r;     // running cost weights on the control (nu)
+  const double* xref;  // state reference (nx)
+  const double* uref;  // control reference (nu)
+};
+
+template <class S> struct JEnt { int k, v; S val; };      // d f_k / d z_v
+template <class S> struct HEnt { int k, a, b; S val; };   // d2 f_k / d z_a d z_b, a >= b
+
+// ---------------------------------------------------------------------------------------
+// Models.  z = (x_1..x_nx, u_1..u_nu) at one node; p = parameters.
+// Every structural entry is emitted whatever its value at z.
+// ---------------------------------------------------------------------------------------
+
+// Van der Pol: x1' = x2, x2' = mu (1 - x1^2) x2 - x1 + u ; p = (mu).
+template <class S> void vdp_f(const S* p, const S* z, S* f) {
+  const S mu = p[0], x1 = z[0], x2 = z[1], u = z[2];
+  f[0] = x2;
+  f[1] = mu * (S(1.0) - x1 * x1) * x2 - x1 + u;
+}
+template <class S> void vdp_jac(const S* p, const S* z, std::vector<JEnt<S>>& e) {
+  const S mu = p[0], x1 = z[0], x2 = z[1];
+  e.push_back({0, 1, S(1.0)});
+  e.push_back({1, 0, S(-2.0) * mu * x1 * x2 - S(1.0)});
+  e.push_back({1, 1, mu * (S(1.0) - x1 * x1)});
+  e.push_back({1, 2, S(1.0)});
+}
+template <class S> void vdp_hess(const S* p, const S* z, std::vector<HEnt<S>>& e) {
+  const S mu = p[0], x1 = z[0], x2 = z[1];
+  e.push_back({1, 0, 0, S(-2.0) * mu * x2});
+  e.push_back({1, 1, 0, S(-2.0) * mu * x1});
+}
+template <class S> void vdp_dpar(const S* p, const S* z, S* d) {
+  (void)p;
+  const S x1 = z[0], x2 = z[1];
+  d[0] = S(0.0);
+  d[1] = (S(1.0) - x1 * x1) * x2;
+}
+
+// Cart-pole with a point-mass pole of length l, theta measured from the downward vertical.
+// Euler-Lagrange equations of L = 1/2 (mc+mp) pd^2 + mp l pd w cos(th) + 1/2 mp l^2 w^2
+// + mp g l cos(th), with the force F on the cart, solved for the accelerations:
+//   D  = mc + mp sin^2(th)
+//   p'' = (F + mp sin(th) (l w^2 + g cos(th))) / D
+//   th''= (-F cos(th) - mp l w^2 cos(th) sin(th) - (mc+mp) g sin(th)) / (l D)
+// state z = (p, pd, th, w, F);  p = (mc, mp, l, g).
+template <class S> void cp_f(const S* p, const S* z, S* f) {
+  using std::cos; using std::sin;
+  const S mc = p[0], mp = p[1], l = p[2], g = p[3];
+  const S pd = z[1], th = z[2], w = z[3], F = z[4];
+  const S s = sin(th), c = cos(th);
+  const S D = mc + mp * s * s;
+  f[0] = pd;
+  f[1] = (F + mp * s * (l * w * w + g * c)) / D;
+  f[2] = w;
+  f[3] = (S(0.0) - F * c - mp * l * w * w * c * s - (mc + mp) * g * s) / (l * D);
+}
+
+// Quotient rule for q = A / D with D depending on th only (local variables th, w, F):
+//   q_a  = A_a / D - A D_a / D^2
+//   q_ab = A_ab / D - (A_a D_b + A_b D_a) / D^2 - A D_ab / D^2 + 2 A D_a D_b / D^3
+template <class S> void cp_parts(const S* p, const S* z,
+                                 S& A, S& A_t, S& A_w, S& A_F, S& A_tt, S& A_tw, S& A_ww, S& A_tF,
+                                 S& B, S& B_t, S& B_w, S& B_F, S& B_tt, S& B_tw, S& B_ww, S& B_tF,
+                                 S& D, S& D_t, S& D_tt, S& E, S& E_t, S& E_tt) {
+  using std::cos; using std::sin;
+  const S mc = p[0], mp = p[1], l = p[2], g = p[3];
+  const S th = z[2], w = z[3], F = z[4];
+  const S s = sin(th), c = cos(th);
+  // numerator of p'':  A = F + mp l w^2 s + mp g s c
+  A = F + mp * s * (l * w * w + g * c);
+  A_t = mp * l * w * w * c + mp * g * (c * c - s * s);
+  A_w = S(2.0) * mp * l * w * s;
+  A_F = S(1.0);
+  A_tt = S(0.0) - mp * l * w * w * s - S(4.0) * mp * g * s * c;
+  A_tw = S(2.0) * mp * l * w * c;
+  A_ww = S(2.0) * mp * l * s;
+  A_tF = S(0.0);
+  // numerator of th'':  B = -F c - mp l w^2 c s - (mc+mp) g s
+  B = S(0.0) - F * c - mp * l * w * w * c * s - (mc + mp) * g * s;
+  B_t = F * s - mp * l * w * w * (c * c - s * s) - (mc + mp) * g * c;
+  B_w = S(-2.0) * mp * l * w * c * s;
+  B_F = S(0.0) - c;
+  B_tt = F * c + S(4.0) * mp * l * w * w * s * c + (mc + mp) * g * s;
+  B_tw = S(-2.0) * mp * l * w * (c * c - s * s);
+  B_ww = S(-2.0) * mp * l * c * s;
+  B_tF = s;
+  // denominators
+  D = mc + mp * s * s;
+  D_t = S(2.0) * mp * s * c;
+  D_tt = S(2.0) * mp * (c * c - s * s);
+  E = l * D;
+  E_t = l * D_t;
+  E_tt = l * D_tt;
+}
+
+template <class S> void cp_jac(const S* p, const S* z, std::vector<JEnt<S>>& e) {
+  S A, A_t, A_w, A_F, A_tt, A_tw, A_ww, A_tF, B, B_t, B_w, B_F, B_tt, B_tw, B_ww, B_tF, D, D_t, D_tt, E, E_t, E_tt;
+  cp_parts(p, z, A, A_t, A_w, A_F, A_tt, A_tw, A_ww, A_tF, B, B_t, B_w, B_F, B_tt, B_tw, B_ww, B_tF,
+           D, D_t, D_tt, E, E_t, E_tt);
+  e.push_back({0, 1, S(1.0)});
+  e.push_back({1, 2, A_t / D - A * D_t / (D * D)});
+  e.push_back({1, 3, A_w / D});
+  e.push_back({1, 4, A_F / D});
+  e.push_back({2, 3, S(1.0)});
+  e.push_back({3, 2, B_t / E - B * E_t / (E * E)});
+  e.push_back({3, 3, B_w / E});
+  e.push_back({3, 4, B_F / E});
+}
+
+template <class S> void cp_hess(const S* p, const S* z, std::vector<HEnt<S>>& e) {
+  S A, A_t, A_w, A_F, A_tt, A_tw, A_ww, A_tF, B, B_t, B_w, B_F, B_tt, B_tw, B_ww, B_tF, D, D_t, D_tt, E, E_t, E_tt;
+  cp_parts(p, z, A, A_t, A_w, A_F, A_tt, A_tw, A_ww, A_tF, B, B_t, B_w, B_F, B_tt, B_tw, B_ww, B_tF,
+           D, D_t, D_tt, E, E_t, E_tt);
+  // local indices: th = 2, w = 3, F = 4; only D depends on th (D_w = D_F = 0)
+  const S D2 = D * D, D3 = D * D * D, E2 = E * E, E3 = E * E * E;
+  e.push_back({1, 2, 2, A_tt / D - (A_t * D_t + A_t * D_t) / D2 - A * D_tt / D2 + S(2.0) * A * D_t * D_t / D3});
+  e.push_back({1, 3, 2, A_tw / D - A_w * D_t / D2});
+  e.push_back({1, 3, 3, A_ww / D});
+  e.push_back({1, 4, 2, A_tF / D - A_F * D_t / D2});
+  e.push_back({3, 2, 2, B_tt / E - (B_t * E_t + B_t * E_t) / E2 - B * E_tt / E2 + S(2.0) * B * E_t * E_t / E3});
+  e.push_back({3, 3, 2, B_tw / E - B_w * E_t / E2});
+  e.push_back({3, 3, 3, B_ww / E});
+  e.push_back({3, 4, 2, B_tF / E - B_F * E_t / E2});
+}
+
+// Heat equation by the method of lines on n cells of width dx = 1/n:
+//   x_k' = (x_{k-1} - 2 x_k + x_{k+1}) / dx^2 - x_k^3,
+// left ghost x_0 = u (Dirichlet control), right ghost x_{n+1} = x_n (homogeneous Neumann).
+// Local indices: cell k (1-based) is z[k-1], the control is z[n].
+template <class S> void heat_f(int n, const S* z, S* f) {
+  const double dx = 1.0 / n;
+  for (int k = 0; k < n; ++k) {
+    const S left = (k == 0) ? z[n] : z[k - 1];
+    const S right = (k == n - 1) ? z[n - 1] : z[k + 1];
+    f[k] = (left - S(2.0) * z[k] + right) / S(dx * dx) - z[k] * z[k] * z[k];
+  }
+}
+template <class S> void heat_jac(int n, const S* z, std::vector<JEnt<S>>& e) {
+  const double dx = 1.0 / n;
+  const S inv = S(1.0) / S(dx * dx);
+  for (int k = 0; k < n; ++k) {
+    const int left = (k == 0) ? n : k - 1;
+    e.push_back({k, left, inv});
+    if (k < n - 1) {
+      e.push_back({k, k, S(-2.0) * inv - S(3.0) * z[k] * z[k]});
+      e.push_back({k, k + 1, inv});
+    } else {
+      e.push_back({k, k, S(-1.0) * inv - S(3.0) * z[k] * z[k]});
+    }
+  }
+}
+template <class S> void heat_hess(int n, const S* z, std::vector<HEnt<S>>& e) {
+  for (int k = 0; k < n; ++k) e.push_back({k, k, k, S(-6.0) * z[k]});
+}
+
+// Double integrator: x1' = x2, x2' = u.
+template <class S> void dint_f(const S* z, S* f) { f[0] = z[1]; f[1] = z[2]; }
+template <class S> void dint_jac(std::vector<JEnt<S>>& e) {
+  e.push_back({0, 1, S(1.0)});
+  e.push_back({1, 2, S(1.0)});
+}
+
+// Dispatch ------------------------------------------------------------------------------
+template <class S> void model_f(const Prob& P, const S* p, const S* z, S* f) {
+  switch (P.model) {
+    case M_VDP: vdp_f(p, z, f); break;
+    case M_CARTPOLE: cp_f(p, z, f); break;
+    case M_HEAT: heat_f(P.nx, z, f); break;
+    case M_DINT: dint_f(z, f); break;
+  }
+}
+template <class S> void model_jac(const Prob& P, const S* p, const S* z, std::vector<JEnt<S>>& e) {
+  switch (P.model) {
+    case M_VDP: vdp_jac(p, z, e); break;
+    case M_CARTPOLE: cp_jac(p, z, e); break;
+    case M_HEAT: heat_jac(P.nx, z, e); break;
+    case M_DINT: dint_jac(e); break;
+  }
+}
+template <class S> void model_hess(const Prob& P, const S* p, const S* z, std::vector<HEnt<S>>& e) {
+  switch (P.model) {
+    case M_VDP: vdp_hess(p, z, e); break;
+    case M_CARTPOLE: cp_hess(p, z, e); break;
+    case M_HEAT: heat_hess(P.nx, z, e); break;
+    case M_DINT: break;
+  }
+}
+
+// Running cost f0 = sum_k q_k (x_k - xref_k)^2 + sum_i r_i (u_i - uref_i)^2.
+template <class S> S cost_f0(const Prob& P, const S* z) {
+  S s = S(0.0);
+  for (int k = 0; k < P.nx; ++k) { S d = z[k] - S(P.xref[k]); s += S(P.q[k]) * d * d; }
+  for (int i = 0; i < P.nu; ++i) { S d = z[P.nx + i] - S(P.uref[i]); s += S(P.r[i]) * d * d; }
+  return s;
+}
+template <class S> void cost_grad(const Prob& P, const S* z, S* g) {
+  for (int k = 0; k < P.nx; ++k) g[k] = S(2.0) * S(P.q[k]) * (z[k] - S(P.xref[k]));
+  for (int i = 0; i < P.nu; ++i) g[P.nx + i] = S(2.0) * S(P.r[i]) * (z[P.nx + i] - S(P.uref[i]));
+}
+inline double cost_hess_diag(const Prob& P, int a) {  // d2 f0 / d z_a^2 (constant)
+  return a < P.nx ? 2.0 * P.q[a] : 2.0 * P.r[a - P.nx];
+}
+
+// ---------------------------------------------------------------------------------------
+// Transcription layout
+// ---------------------------------------------------------------------------------------
+struct Layout {
+  int nx, nu, nz;
+  int64_t N, n, m, nb;
+  explicit Layout(const Prob& P) {
+    nx = P.nx; nu = P.nu; nz = nx + nu; N = P.N;
+    n = (int64_t)nz * (N + 1);
+    nb = (int64_t)nx * (P.has_final ? 2 : 1);
+    m = nb + (int64_t)nx * N;
+  }
+  int64_t colX(int64_t j, int k) const { return k + (int64_t)nx * j; }
+  int64_t colU(int64_t j, int i) const { return (int64_t)nx * (N + 1) + i + (int64_t)nu * j; }
+  int64_t col(int64_t j, int v) const { return v < nx ? colX(j, v) : colU(j, v - nx); }
+  int64_t defect_row(int k, int64_t j) const { return nb + (int64_t)k * N + j; }
+};
+
+template <class S> void gather_node(const Layout& L, const S* x, int64_t j, S* z) {
+  for (int v = 0; v < L.nz; ++v) z[v] = x[L.col(j, v)];
+}
+
+inline double weight(const Prob& P, int64_t j) {
+  const double h = P.T / (double)P.N;
+  return (j == 0 || j == P.N) ? h / 2.0 : h;
+}
+
+template <class S> void params_of(const Prob& P, S* p) { for (int i = 0; i < 8; ++i) p[i] = S(P.par[i]); }
+
+// Objective F = sum_j w_j f0(z_j)   (trapezoidal Lagrange cost)
+template <class S> S objective(const Prob& P, const S* x) {
+  Layout L(P);
+  std::vector<S> z(L.nz);
+  Neumaier<S> acc;
+  for (int64_t j = 0; j <= L.N; ++j) {
+    gather_node(L, x, j, z.data());
+    acc.add(S(weight(P, j)) * cost_f0(P, z.data()));
+  }
+  return acc.result();
+}
+
+// Constraints: boundary rows, then trapezoidal defects, component-major.
+template <class S> void constraints(const Prob& P, const S* p, const S* x, S* c) {
+  Layout L(P);
+  const double h = P.T / (double)P.N;
+  for (int k = 0; k < L.nx; ++k) c[k] = x[L.colX(0, k)];
+  if (P.has_final) for (int k = 0; k < L.nx; ++k) c[L.nx + k] = x[L.colX(L.N, k)];
+  std::vector<S> f((size_t)L.nx * (L.N + 1)), z(L.nz);
+  for (int64_t j = 0; j <= L.N; ++j) {
+    gather_node(L, x, j, z.data());
+    model_f(P, p, z.data(), &f[(size_t)L.nx * j]);
+  }
+  for (int k = 0; k < L.nx; ++k)
+    for (int64_t j = 0; j < L.N; ++j) {
+      const S fj = f[(size_t)L.nx * j + k], fj1 = f[(size_t)L.nx * (j + 1) + k];
+      c[L.defect_row(k, j)] = (x[L.colX(j + 1, k)] - x[L.colX(j, k)]) - S(h) * (fj + fj1) / S(2.0);
+    }
+}
+
+// Gradient of F (node-local).
+template <class S> void gradient(const Prob& P, const S* x, S* g) {
+  Layout L(P);
+  std::vector<S> z(L.nz), gz(L.nz);
+  for (int64_t j = 0; j <= L.N; ++j) {
+    gather_node(L, x, j, z.data());
+    cost_grad(P, z.data(), gz.data());
+    for (int v = 0; v < L.nz; ++v) g[L.col(j, v)] = S(weight(P, j)) * gz[v];
+  }
+}
+
+// Jacobian in COO, one entry per structural nonzero, sorted by (row, col).
+template <class S> struct Coo { std::vector<int64_t> row, col; std::vector<S> val; };
+
+template <class S> void jacobian(const Prob& P, const S* p, const S* x, Coo<S>& J) {
+  Layout L(P);
+  const double h = P.T / (double)P.N;
+  // derivative entries of f at every node
+  std::vector<std::vector<JEnt<S>>> nodeJ((size_t)L.N + 1);
+  std::vector<S> z(L.nz);
+  for (int64_t j = 0; j <= L.N; ++j) {
+    gather_node(L, x, j, z.data());
+    model_jac(P, p, z.data(), nodeJ[j]);
+  }
+  auto emit = [&](int64_t r, int64_t c, S v) { J.row.push_back(r); J.col.push_back(c); J.val.push_back(v); };
+  for (int k = 0; k < L.nx; ++k) emit(k, L.colX(0, k), S(1.0));
+  if (P.has_final) for (int k = 0; k < L.nx; ++k) emit(L.nx + k, L.colX(L.N, k), S(1.0));
+  std::vector<std::pair<int64_t, S>> ent;
+  for (int k = 0; k < L.nx; ++k)
+    for (int64_t j = 0; j < L.N; ++j) {
+      ent.clear();
+      // d c_{k,j} / d z_j : -[v == x_k] - h (df_k/dz_v)(z_j) / 2
+      for (auto& e : nodeJ[j]) if (e.k == k) ent.push_back({L.col(j, e.v), S(0.0) - S(h) * e.val / S(2.0)});
+      ent.push_back({L.colX(j, k), S(-1.0)});
+      // d c_{k,j} / d z_{j+1} : +[v == x_k] - h (df_k/dz_v)(z_{j+1}) / 2
+      for (auto& e : nodeJ[j + 1]) if (e.k == k) ent.push_back({L.col(j + 1, e.v), S(0.0) - S(h) * e.val / S(2.0)});
+      ent.push_back({L.colX(j + 1, k), S(1.0)});
+      std::stable_sort(ent.begin(), ent.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+      const int64_t r = L.defect_row(k, j);
+      for (size_t i = 0; i < ent.size();) {
+        S v = ent[i].second;
+        size_t t = i + 1;
+        while (t < ent.size() && ent[t].first == ent[i].first) { v = v + ent[t].second; ++t; }
+        emit(r, ent[i].first, v);
+        i = t;
+      }
+    }
+}
+
+// Lagrangian Hessian sigma * Hess F + sum_r y_r Hess c_r, lower triangle, sorted by (row, col).
+// Boundary rows are linear.  The defect row (k, j) involves only z_j and z_{j+1}, so the
+// block of node j collects the rows (k, j-1) and (k, j), each through -h/2 Hess f_k(z_j).
+template <class S> void hessian(const Prob& P, const S* p, const S* x, const S* y, S sigma, Coo<S>& H) {
+  Layout L(P);
+  const double h = P.T / (double)P.N;
+  std::vector<S> z(L.nz);
+  std::vector<HEnt<S>> he;
+  struct Trip { int64_t r, c; S v; };
+  std::vector<Trip> all;
+  for (int64_t j = 0; j <= L.N; ++j) {
+    gather_node(L, x, j, z.data());
+    he.clear();
+    model_hess(P, p, z.data(), he);
+    std::map<std::pair<int, int>, S> blk;
+    for (int a = 0; a < L.nz; ++a)
+      if (cost_hess_diag(P, a) != 0.0) blk[{a, a}] = S(0.0);
+    for (auto& e : he) blk[{e.a, e.b}] = S(0.0);
+    // sigma * w_j * Hess f0
+    for (int a = 0; a < L.nz; ++a)
+      if (cost_hess_diag(P, a) != 0.0) blk[{a, a}] = blk[{a, a}] + sigma * S(weight(P, j)) * S(cost_hess_diag(P, a));
+    // sum over the defect rows that touch node j
+    for (auto& e : he) {
+      if (j >= 1) {
+        const S yr = y[L.defect_row(e.k, j - 1)];
+        blk[{e.a, e.b}] = blk[{e.a, e.b}] + yr * (S(0.0) - S(h) * e.val / S(2.0));
+      }
+      if (j <= L.N - 1) {
+        const S yr = y[L.defect_row(e.k, j)];
+        blk[{e.a, e.b}] = blk[{e.a, e.b}] + yr * (S(0.0) - S(h) * e.val / S(2.0));
+      }
+    }
+    for (auto& kv : blk) all.push_back({L.col(j, kv.first.first), L.col(j, kv.first.second), kv.second});
+  }
+  std::stable_sort(all.begin(), all.end(), [](const Trip& a, const Trip& b) {
+    return a.r != b.r ? a.r < b.r : a.c < b.c;
+  });
+  for (auto& t : all) { H.row.push_back(t.r); H.col.push_back(t.c); H.val.push_back(t.v); }
+}
+
+// Plain COO products.
+template <class S> void coo_mv(const Coo<S>& A, const S* v, S* out, int64_t nout) {
+  for (int64_t i = 0; i < nout; ++i) out[i] = S(0.0);
+  for (size_t e = 0; e < A.val.size(); ++e) out[A.row[e]] = out[A.row[e]] + A.val[e] * v[A.col[e]];
+}
+template <class S> void coo_mtv(const Coo<S>& A, const S* w, S* out, int64_t nout) {
+  for (int64_t i = 0; i < nout; ++i) out[i] = S(0.0);
+  for (size_t e = 0; e < A.val.size(); ++e) out[A.col[e]] = out[A.col[e]] + A.val[e] * w[A.row[e]];
+}
+template <class S> void coo_symv_lower(const Coo<S>& A, const S* v, S* out, int64_t nout) {
+  for (int64_t i = 0; i < nout; ++i) out[i] = S(0.0);
+  for (size_t e = 0; e < A.val.size(); ++e) {
+    out[A.row[e]] = out[A.row[e]] + A.val[e] * v[A.col[e]];
+    if (A.row[e] != A.col[e]) out[A.col[e]] = out[A.col[e]] + A.val[e] * v[A.row[e]];
+  }
+}
+
+// (dc/dp0)^T w = sum over defect rows of w_r * ( -h (df_k/dp0(z_j) + df_k/dp0(z_{j+1})) / 2 )
+template <class S> S dpar_vjp(const Prob& P, const S* p, const S* x, const S* w) {
+  Layout L(P);
+  const double h = P.T / (double)P.N;
+  std::vector<S> d((size_t)L.nx * (L.N + 1)), z(L.nz);
+  for (int64_t j = 0; j <= L.N; ++j) {
+    gather_node(L, x, j, z.data());
+    vdp_dpar(p, z.data(), &d[(size_t)L.nx * j]);
+  }
+  Neumaier<S> acc;
+  for (int k = 0; k < L.nx; ++k)
+    for (int64_t j = 0; j < L.N; ++j) {
+      const S dc = S(0.0) - S(h) * (d[(size_t)L.nx * j + k] + d[(size_t)L.nx * (j + 1) + k]) / S(2.0);
+      acc.add(w[L.defect_row(k, j)] * dc);
+    }
+  return acc.result();
+}
+
+// Gradient of the Lagrangian sigma F + y^T c, from the analytic gradient and Jacobian.
+template <class S> void lagrangian_grad(const Prob& P, const S* p, const S* x, const S* y, S sigma, S* out) {
+  Layout L(P);
+  std::vector<S> g(L.n), jty(L.n);
+  gradient(P, x, g.data());
+  Coo<S> J;
+  jacobian(P, p, x, J);
+  coo_mtv(J, y, jty.data(), L.n);
+  for (int64_t i = 0; i < L.n; ++i) out[i] = sigma * g[i] + jty[i];
+}
+
+int check(const Prob& P) {
+  if (P.N < 1 || !(P.T > 0.0)) return 2;
+  switch (P.model) {
+    case M_VDP: return (P.nx == 2 && P.nu == 1) ? 0 : 2;
+    case M_CARTPOLE: return (P.nx == 4 && P.nu == 1) ? 0 : 2;
+    case M_HEAT: return (P.nx >= 2 && P.nu == 1 && (int)P.par[0] == P.nx) ? 0 : 2;
+    case M_DINT: return (P.nx == 2 && P.nu == 1) ? 0 : 2;
+    default: return 6;
+  }
+}
+
+template <class S> std::vector<S> lift(const double* a, int64_t n) {
+  std::vector<S> v(n);
+  for (int64_t i = 0; i < n; ++i) v[i] = S(a[i]);
+  return v;
+}
+
+}  // namespace orc
+
+// =======================================================================================
+// C interface (ctypes).  Status: 0 ok, 2 bad dimensions, 6 unknown model.
+// =======================================================================================
+using namespace orc;
+
+extern "C" {
+
+int orc_dims(const Prob* P, int64_t* n, int64_t* m, int64_t* nnzj, int64_t* nnzh) {
+  int st = check(*P);
+  if (st) return st;
+  Layout L(*P);
+  *n = L.n; *m = L.m;
+  // count structure by building it at a tiny horizon is not needed: count directly
+  std::vector<double> z(L.nz, 0.5), p(8);
+  params_of(*P, p.data());
+  std::vector<JEnt<double>> je; model_jac(*P, p.data(), z.data(), je);
+  int64_t perrow = 0;
+  for (int k = 0; k < L.nx; ++k) {
+    // distinct columns of row k on one side: f-derivative columns plus x_k itself
+    std::vector<int> cols;
+    for (auto& e : je) if (e.k == k) cols.push_back(e.v);
+    cols.push_back(k);
+    std::sort(cols.begin(), cols.end());
+    perrow += 2 * (int64_t)(std::unique(cols.begin(), cols.end()) - cols.begin());
+  }
+  *nnzj = L.nb + perrow * L.N;
+  std::vector<HEnt<double>> he; model_hess(*P, p.data(), z.data(), he);
+  std::vector<std::pair<int, int>> keys;
+  for (int a = 0; a < L.nz; ++a) if (cost_hess_diag(*P, a) != 0.0) keys.push_back({a, a});
+  for (auto& e : he) keys.push_back({e.a, e.b});
+  std::sort(keys.begin(), keys.end());
+  *nnzh = (int64_t)(std::unique(keys.begin(), keys.end()) - keys.begin()) * (L.N + 1);
+  return 0;
+}
+
+int orc_jac_structure(const Prob* P, int32_t* rows, int32_t* cols) {
+  int st = check(*P);
+  if (st) return st;
+  Layout L(*P);
+  std::vector<double> x(L.n, 0.5), p(8);
+  params_of(*P, p.data());
+  Coo<double> J; jacobian(*P, p.data(), x.data(), J);
+  for (size_t e = 0; e < J.val.size(); ++e) { rows[e] = (int32_t)J.row[e]; cols[e] = (int32_t)J.col[e]; }
+  return 0;
+}
+
+int orc_hess_structure(const Prob* P, int32_t* rows, int32_t* cols) {
+  int st = check(*P);
+  if (st) return st;
+  Layout L(*P);
+  std::vector<double> x(L.n, 0.5), y(L.m, 1.0), p(8);
+  params_of(*P, p.data());
+  Coo<double> H; hessian(*P, p.data(), x.data(), y.data(), 1.0, H);
+  for (size_t e = 0; e < H.val.size(); ++e) { rows[e] = (int32_t)H.row[e]; cols[e] = (int32_t)H.col[e]; }
+  return 0;
+}
+
+// Values (double).  Any output pointer may be null.
+int orc_eval(const Prob* P, const double* x, const double* y, double sigma,
+             double* f, double* c, double* g, double* jv, double* hv) {
+  int st = check(*P);
+  if (st) return st;
+  Layout L(*P);
+  std::vector<double> p(8); params_of(*P, p.data());
+  if (f) *f = objective(*P, x);
+  if (c) constraints(*P, p.data(), x, c);
+  if (g) gradient(*P, x, g);
+  if (jv) { Coo<double> J; jacobian(*P, p.data(), x, J); std::copy(J.val.begin(), J.val.end(), jv); }
+  if (hv) { Coo<double> H; hessian(*P, p.data(), x, y, sigma, H); std::copy(H.val.begin(), H.val.end(), hv); }
+  return 0;
+}
+
+// Running-error magnitudes of the same outputs (the tolerance gate for cancellation).
+int orc_eval_shadow(const Prob* P, const double* x, const double* y, double sigma,
+                    double* f, double* c, double* g, double* jv, double* hv) {
+  int st = check(*P);
+  if (st) return st;
+  Layout L(*P);
+  std::vector<Sh> p(8); params_of(*P, p.data());
+  auto X = lift<Sh>(x, L.n);
+  auto Y = lift<Sh>(y, L.m);
+  if (f) *f = shadow(objective(*P, X.data()));
+  if (c) { std::vector<Sh> o(L.m); constraints(*P, p.data(), X.data(), o.data()); for (int64_t i = 0; i < L.m; ++i) c[i] = o[i].m; }
+  if (g) { std::vector<Sh> o(L.n); gradient(*P, X.data(), o.data()); for (int64_t i = 0; i < L.n; ++i) g[i] = o[i].m; }
+  if (jv) { Coo<Sh> J; jacobian(*P, p.data(), X.data(), J); for (size_t e = 0; e < J.val.size(); ++e) jv[e] = J.val[e].m; }
+  if (hv) { Coo<Sh> H; hessian(*P, p.data(), X.data(), Y.data(), Sh(sigma), H); for (size_t e = 0; e < H.val.size(); ++e) hv[e] = H.val[e].m; }
+  return 0;
+}
+
+// Products; `mag` (nullable) receives the running-error magnitudes.
+int orc_jprod(const Prob* P, const double* x, const double* v, double* out, double* mag) {
+  int st = check(*P);
+  if (st) return st;
+  Layout L(*P);
+  { std::vector<double> p(8); params_of(*P, p.data());
+    Coo<double> J; jacobian(*P, p.data(), x, J); coo_mv(J, v, out, L.m); }
+  if (mag) {
+    std::vector<Sh> p(8); params_of(*P, p.data());
+    auto X = lift<Sh>(x, L.n); auto V = lift<Sh>(v, L.n);
+    Coo<Sh> J; jacobian(*P, p.data(), X.data(), J);
+    std::vector<Sh> o(L.m); coo_mv(J, V.data(), o.data(), L.m);
+    for (int64_t i = 0; i < L.m; ++i) mag[i] = o[i].m;
+  }
+  return 0;
+}
+
+int orc_jtprod(const Prob* P, const double* x, const double* w, double* out, double* mag) {
+  int st = check(*P);
+  if (st) return st;
+  Layout L(*P);
+  { std::vector<double> p(8); params_of(*P, p.data());
+    Coo<double> J; jacobian(*P, p.data(), x, J); coo_mtv(J, w, out, L.n); }
+  if (mag) {
+    std::vector<Sh> p(8); params_of(*P, p.data());
+    auto X = lift<Sh>(x, L.n); auto W = lift<Sh>(w, L.m);
+    Coo<Sh> J; jacobian(*P, p.data(), X.data(), J);
+    std::vector<Sh> o(L.n); coo_mtv(J, W.data(), o.data(), L.n);
+    for (int64_t i = 0; i < L.n; ++i) mag[i] = o[i].m;
+  }
+  return 0;
+}
+
+int orc_hprod(const Prob* P, const double* x, const double* y, double sigma, const double* v,
+              double* out, double* mag) {
+  int st = check(*P);
+  if (st) return st;
+  Layout L(*P);
+  { std::vector<double> p(8); params_of(*P, p.data());
+    Coo<double> H; hessian(*P, p.data(), x, y, sigma, H); coo_symv_lower(H, v, out, L.n); }
+  if (mag) {
+    std::vector<Sh> p(8); params_of(*P, p.data());
+    auto X = lift<Sh>(x, L.n); auto Y = lift<Sh>(y, L.m); auto V = lift<Sh>(v, L.n);
+    Coo<Sh> H; hessian(*P, p.data(), X.data(), Y.data(), Sh(sigma), H);
+    std::vector<Sh> o(L.n); coo_symv_lower(H, V.data(), o.data(), L.n);
+    for (int64_t i = 0; i < L.n; ++i) mag[i] = o[i].m;
+  }
+  return 0;
+}
+
+// (dc/dmu)^T w for the Van der Pol model.
+int orc_dpar_vjp(const Prob* P, const double* x, const double* w, double* out, double* mag) {
+  int st = check(*P);
+  if (st) return st;
+  if (P->model != M_VDP) return 6;
+  Layout L(*P);
+  { std::vector<double> p(8); params_of(*P, p.data()); *out = dpar_vjp(*P, p.data(), x, w); }
+  if (mag) {
+    std::vector<Sh> p(8); params_of(*P, p.data());
+    auto X = lift<Sh>(x, L.n); auto W = lift<Sh>(w, L.m);
+    *mag = shadow(dpar_vjp(*P, p.data(), X.data(), W.data()));
+  }
+  return 0;
+}
+
+// Gradient of the Lagrangian (analytic), double.
+int orc_lagrangian_grad(const Prob* P, const double* x, const double* y, double sigma, double* out) {
+  int st = check(*P);
+  if (st) return st;
+  std::vector<double> p(8); params_of(*P, p.data());
+  lagrangian_grad(*P, p.data(), x, y, sigma, out);
+  return 0;
+}
+
+// ---- complex-step directional derivatives (Im f(x + i eps d) / eps), for the pins -------
+int orc_cs_cons(const Prob* P, const double* x, const double* dx, double dmu, double eps, double* out) {
+  int st = check(*P);
+  if (st) return st;
+  Layout L(*P);
+  std::vector<Cx> X(L.n), p(8), c(L.m);
+  for (int64_t i = 0; i < L.n; ++i) X[i] = Cx(x[i], eps * dx[i]);
+  params_of(*P, p.data());
+  p[0] = Cx(P->par[0], eps * dmu);
+  constraints(*P, p.data(), X.data(), c.data());
+  for (int64_t i = 0; i < L.m; ++i) out[i] = c[i].imag() / eps;
+  return 0;
+}
+
+int orc_cs_obj(const Prob* P, const double* x, const double* dx, double eps, double* out) {
+  int st = check(*P);
+  if (st) return st;
+  Layout L(*P);
+  std::vector<Cx> X(L.n);
+  for (int64_t i = 0; i < L.n; ++i) X[i] = Cx(x[i], eps * dx[i]);
+  *out = objective(*P, X.data()).imag() / eps;
+  return 0;
+}
+
+int orc_cs_lagrangian_grad(const Prob* P, const double* x, const double* dx, const double* y, double sigma,
+                           double eps, double* out) {
+  int st = check(*P);
+  if (st) return st;
+  Layout L(*P);
+  std::vector<Cx> X(L.n), Y(L.m), p(8), o(L.n);
+  for (int64_t i = 0; i < L.n; ++i) X[i] = Cx(x[i], eps * dx[i]);
+  for (int64_t i = 0; i < L.m; ++i) Y[i] = Cx(y[i], 0.0);
+  params_of(*P, p.data());
+  lagrangian_grad(*P, p.data(), X.data(), Y.data(), Cx(sigma, 0.0), o.data());
+  for (int64_t i = 0; i < L.n; ++i) out[i] = o[i].imag() / eps;
+  return 0;
+}
+
+// Complex-step of the analytic Jacobian's transpose product in the parameter direction:
+// d/dmu (J^T w), used to pin the mixed second derivative.
+int orc_cs_jtprod_dmu(const Prob* P, const double* x, const double* w, double eps, double* out) {
+  int st = check(*P);
+  if (st) return st;
+  Layout L(*P);
+  std::vector<Cx> X(L.n), W(L.m), p(8), o(L.n);
+  for (int64_t i = 0; i < L.n; ++i) X[i] = Cx(x[i], 0.0);
+  for (int64_t i = 0; i < L.m; ++i) W[i] = Cx(w[i], 0.0);
+  params_of(*P, p.data());
+  p[0] = Cx(P->par[0], eps);
+  Coo<Cx> J; jacobian(*P, p.data(), X.data(), J);
+  coo_mtv(J, W.data(), o.data(), L.n);
+  for (int64_t i = 0; i < L.n; ++i) out[i] = o[i].imag() / eps;
+  return 0;
+}
+
+// Model right-hand side at one node (for the physics pins).
+int orc_model_f(const Prob* P, const double* z, double* f) {
+  int st = check(*P);
+  if (st) return st;
+  std::vector<double> p(8); params_of(*P, p.data());
+  model_f(*P, p.data(), z, f);
+  return 0;
+}
+
+}  // extern "C"

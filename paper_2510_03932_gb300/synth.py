@@ -1,0 +1,130 @@
+"""Seeded synthetic inputs shared byte-for-byte by the CUDA path and the CPU oracle.
+
+This module holds no arithmetic of the transcription method: it only draws numbers.
+Generator: splitmix64 (Steele, Lea & Flood, "Fast splittable pseudorandom number
+generators", OOPSLA 2014).  Element i of a stream with seed s is
+mix(s + (i+1) * 0x9E3779B97F4A7C15); a uniform in [0,1) is the top 53 bits times 2^-53;
+a standard normal is Box-Muller on two consecutive uniforms (the cosine branch).
+
+Draw order for one problem instance, all from one stream: X (vector order), U, y, then
+the product directions vn (length n) and vm (length m).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+_GAMMA = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+
+class Stream:
+    """A splitmix64 stream; `take(k)` returns the next k raw 64-bit outputs."""
+
+    def __init__(self, seed: int):
+        self.seed = np.uint64(seed & 0xFFFFFFFFFFFFFFFF)
+        self.pos = 0
+
+    def take(self, k: int) -> np.ndarray:
+        idx = np.arange(self.pos + 1, self.pos + 1 + k, dtype=np.uint64)
+        self.pos += k
+        with np.errstate(over="ignore"):
+            z = self.seed + idx * _GAMMA
+            z = (z ^ (z >> np.uint64(30))) * _M1
+            z = (z ^ (z >> np.uint64(27))) * _M2
+            z = z ^ (z >> np.uint64(31))
+        return z
+
+    def uniform(self, k: int, lo: float = 0.0, hi: float = 1.0) -> np.ndarray:
+        u = (self.take(k) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+        return lo + (hi - lo) * u
+
+    def normal(self, k: int) -> np.ndarray:
+        u = self.uniform(2 * k)
+        u1, u2 = u[0::2], u[1::2]
+        return np.sqrt(-2.0 * np.log1p(-u1)) * np.cos(2.0 * np.pi * u2)
+
+    def integers(self, k: int, lo: int, hi: int) -> np.ndarray:
+        """Uniform integers in [lo, hi] (inclusive)."""
+        u = self.uniform(k)
+        return (lo + np.floor(u * (hi - lo + 1))).astype(np.int64)
+
+
+# Value distributions of the five workloads (uniform bounds for X and U).
+DIST = {
+    "vdp": dict(x=(-1.0, 1.0), u=(-1.0, 1.0)),
+    "cartpole": dict(x=(-1.0, 1.0), u=(-10.0, 10.0)),
+    "heat": dict(x=(0.0, 1.0), u=(-1.0, 1.0)),
+    "dint": dict(x=(-1.0, 1.0), u=(-1.0, 1.0)),
+}
+
+
+def draw_instance(seed: int, kind: str, nx: int, nu: int, N: int, m: int,
+                  stream: Stream | None = None) -> dict:
+    """x = [X (node-major, nx per node); U (nu per node)], y ~ N(0,1), vn ~ U(-1,1), vm ~ N(0,1)."""
+    s = stream if stream is not None else Stream(seed)
+    d = DIST[kind]
+    X = s.uniform(nx * (N + 1), *d["x"])
+    U = s.uniform(nu * (N + 1), *d["u"])
+    x = np.concatenate([X, U])
+    y = s.normal(m)
+    vn = s.uniform(x.size, -1.0, 1.0)
+    vm = s.normal(m)
+    return dict(x=x, y=y, vn=vn, vm=vm)
+
+
+def draw_batch_meta(seed: int, count: int, nmin: int, nmax: int):
+    """Horizons N_i ~ U{nmin..nmax}, initial states ~ U(-0.5,0.5)^4, R_i ~ U(0.01,1)."""
+    s = Stream(seed)
+    Ns = s.integers(count, nmin, nmax)
+    x0 = s.uniform(4 * count, -0.5, 0.5).reshape(count, 4)
+    R = s.uniform(count, 0.01, 1.0)
+    return Ns, x0, R
+
+
+# Workload definitions (data only).  Model names: vdp, cartpole, heat, dint.
+# Running cost f0 = sum_k q_k (x_k - xref_k)^2 + sum_i r_i (u_i - uref_i)^2.
+def workload(name: str) -> dict:
+    if name == "vdp_n1e3":         # Van der Pol, N=1000, T=10, x0=(1,0), cost x1^2+x2^2+u^2
+        return dict(name=name, model="vdp", nx=2, nu=1, N=1000, T=10.0, params=[1.0],
+                    q=[1.0, 1.0], r=[1.0], xref=[0.0, 0.0], uref=[0.0], x0=[1.0, 0.0], xf=None,
+                    seed=1000, sigma=1.0, dist="vdp")
+    if name == "cartpole_n1e5":    # cart-pole, mc=1, mp=0.1, l=0.5, g=9.81, N=1e5, T=5, Q=I4, R=0.1
+        return dict(name=name, model="cartpole", nx=4, nu=1, N=100000, T=5.0,
+                    params=[1.0, 0.1, 0.5, 9.81], q=[1.0] * 4, r=[0.1], xref=[0.0] * 4, uref=[0.0],
+                    x0=[0.0] * 4, xf=None, seed=1001, sigma=1.0, dist="cartpole")
+    if name == "heat_n2e4":        # heat, 64 cells, dx=1/64, N=2e4, T=1, cost ||x-0.5||^2 + 1e-2 u^2
+        return dict(name=name, model="heat", nx=64, nu=1, N=20000, T=1.0, params=[64.0],
+                    q=[1.0] * 64, r=[1e-2], xref=[0.5] * 64, uref=[0.0], x0=[0.0] * 64, xf=None,
+                    seed=1002, sigma=1.0, dist="heat")
+    if name == "vdp_mu_n1e6":      # Van der Pol with parameter mu, N=1e6, T=10
+        return dict(name=name, model="vdp", nx=2, nu=1, N=1_000_000, T=10.0, params=[1.0],
+                    q=[1.0, 1.0], r=[1.0], xref=[0.0, 0.0], uref=[0.0], x0=[1.0, 0.0], xf=None,
+                    seed=1003, sigma=1.0, dist="vdp")
+    if name == "cartpole_n1e6":    # the cart-pole at N=1e6
+        w = workload("cartpole_n1e5")
+        w.update(name=name, N=1_000_000, seed=1005)
+        return w
+    if name == "dint":             # double integrator, min 1/2 int u^2, x(0)=(-1,0), x(1)=(0,0)
+        return dict(name=name, model="dint", nx=2, nu=1, N=100, T=1.0, params=[],
+                    q=[0.0, 0.0], r=[0.5], xref=[0.0, 0.0], uref=[0.0], x0=[-1.0, 0.0],
+                    xf=[0.0, 0.0], seed=1006, sigma=1.0, dist="dint")
+    raise KeyError(name)
+
+
+def with_horizon(w: dict, N: int) -> dict:
+    """The same workload at another horizon (parity cases at oracle-friendly sizes)."""
+    w = dict(w)
+    w["N"] = int(N)
+    return w
+
+
+def dims(w: dict):
+    """(n, m) of the transcription: n = (nx+nu)(N+1); m = nx (+nx final rows) + nx N."""
+    nb = w["nx"] * (2 if w.get("xf") is not None else 1)
+    return (w["nx"] + w["nu"]) * (w["N"] + 1), nb + w["nx"] * w["N"]
+
+
+def draw(w: dict, seed: int | None = None) -> dict:
+    n, m = dims(w)
+    return draw_instance(w["seed"] if seed is None else seed, w["dist"], w["nx"], w["nu"], w["N"], m)

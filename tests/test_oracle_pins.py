@@ -1,0 +1,340 @@
+"""Pins of the CPU oracle against facts fixed outside it (no GPU needed).
+
+Each test checks the oracle against something other than itself: closed forms of the
+paper's double-integrator example (Sec. 5), published constants of the Van der Pol limit
+cycle, conservation laws of the cart-pole, discrete summation-by-parts of the heat
+Laplacian, complex-step derivatives of the residual itself, brute-force structure
+detection, and the adjoint identity.  A plausible slip anywhere in the oracle (a sign, a
+dropped term, a wrong index or weight) fails at least one of these.
+"""
+import numpy as np
+import pytest
+
+from conftest import read_golden
+from oracle import oracle as O
+from paper_2510_03932_gb300 import synth
+
+MODELS = ["vdp_n1e3", "cartpole_n1e5", "heat_n2e4", "dint"]
+
+
+def small(name, N):
+    return synth.with_horizon(synth.workload(name), N)
+
+
+def rand_point(w, rng):
+    n, m = synth.dims(w)
+    d = synth.DIST[w["dist"]]
+    nx1 = w["nx"] * (w["N"] + 1)
+    x = np.concatenate([rng.uniform(*d["x"], nx1), rng.uniform(*d["u"], n - nx1)])
+    return x, rng.standard_normal(m)
+
+
+# ---------------------------------------------------------------------------------------
+# Counts and structure
+# ---------------------------------------------------------------------------------------
+# per node: (J entries of one defect-row set, H entries of one node block)
+NODE_COUNTS = {"vdp": (10, 4), "cartpole": (22, 7), "heat": (382, 65), "dint": (8, 1)}
+
+
+@pytest.mark.parametrize("name", MODELS)
+@pytest.mark.parametrize("N", [1, 2, 7])
+def test_counts_closed_form(name, N):
+    w = small(name, N)
+    P = O.Problem(w)
+    nx, nu = w["nx"], w["nu"]
+    nb = nx * (2 if w["xf"] is not None else 1)
+    jn, hn = NODE_COUNTS[w["model"]]
+    assert P.n == (nx + nu) * (N + 1)
+    assert P.m == nb + nx * N
+    assert P.nnzj == nb + jn * N
+    assert P.nnzh == hn * (N + 1)
+
+
+@pytest.mark.parametrize("name", MODELS)
+def test_structure_sorted_unique(name):
+    P = O.Problem(small(name, 5))
+    for rows, cols, lower in [(*O.jac_structure(P), False), (*O.hess_structure(P), True)]:
+        key = rows.astype(np.int64) * (1 << 32) + cols
+        assert np.all(np.diff(key) > 0), "COO must be sorted by (row, col) without duplicates"
+        if lower:
+            assert np.all(rows >= cols)
+        assert rows.min() >= 0 and cols.min() >= 0
+
+
+def dense_jac_cs(P, x):
+    cols = []
+    for i in range(P.n):
+        e = np.zeros(P.n); e[i] = 1.0
+        cols.append(O.cs_cons(P, x, e))
+    return np.array(cols).T  # m x n
+
+
+def dense_hess_cs(P, x, y, sigma):
+    cols = []
+    for i in range(P.n):
+        e = np.zeros(P.n); e[i] = 1.0
+        cols.append(O.cs_lagrangian_grad(P, x, e, y, sigma))
+    return np.array(cols).T  # n x n
+
+
+@pytest.mark.parametrize("name", MODELS)
+def test_structure_matches_bruteforce_detection(name):
+    """An entry is structural iff it is nonzero at one of 8 random points (complex step)."""
+    w = small(name, 2 if name == "heat_n2e4" else 3)
+    P = O.Problem(w)
+    rng = np.random.default_rng(7)
+    jmask = np.zeros((P.m, P.n), bool)
+    hmask = np.zeros((P.n, P.n), bool)
+    for _ in range(8):
+        x, y = rand_point(w, rng)
+        jmask |= dense_jac_cs(P, x) != 0.0
+        hmask |= np.tril(dense_hess_cs(P, x, y, 1.0)) != 0.0
+    jr, jc = O.jac_structure(P)
+    hr, hc = O.hess_structure(P)
+    jm = np.zeros_like(jmask); jm[jr, jc] = True
+    hm = np.zeros_like(hmask); hm[hr, hc] = True
+    assert np.array_equal(jm, jmask)
+    assert np.array_equal(hm, hmask)
+
+
+# ---------------------------------------------------------------------------------------
+# Derivative values against complex step of the residual / objective / Lagrangian gradient
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("name", MODELS)
+def test_jacobian_gradient_hessian_vs_complex_step(name):
+    w = small(name, 2 if name == "heat_n2e4" else 4)
+    P = O.Problem(w)
+    rng = np.random.default_rng(11)
+    x, y = rand_point(w, rng)
+    sigma = 0.7
+    ev = O.evaluate(P, x, y, sigma)
+    Jcs = dense_jac_cs(P, x)
+    jr, jc = O.jac_structure(P)
+    np.testing.assert_allclose(ev["jac"], Jcs[jr, jc], rtol=1e-13, atol=1e-15)
+    gcs = np.array([O.cs_obj(P, x, np.eye(P.n)[i]) for i in range(P.n)])
+    np.testing.assert_allclose(ev["g"], gcs, rtol=1e-13, atol=1e-15)
+    Hcs = dense_hess_cs(P, x, y, sigma)
+    hr, hc = O.hess_structure(P)
+    np.testing.assert_allclose(ev["hess"], Hcs[hr, hc], rtol=1e-12, atol=1e-14)
+    # the complex-step Hessian of an exact gradient is symmetric
+    np.testing.assert_allclose(Hcs, Hcs.T, rtol=1e-12, atol=1e-12)
+    # loose central finite differences as an independent sanity check of the residual
+    hfd = 1e-6
+    e = np.zeros(P.n); e[1] = 1.0
+    cfd = (O.evaluate(P, x + hfd * e, y, sigma)["c"] - O.evaluate(P, x - hfd * e, y, sigma)["c"]) / (2 * hfd)
+    np.testing.assert_allclose(cfd, Jcs[:, 1], rtol=1e-5, atol=1e-6)
+
+
+@pytest.mark.parametrize("name", ["vdp_n1e3", "cartpole_n1e5", "heat_n2e4"])
+def test_hessian_special_cases(name):
+    """y = 0, sigma = 1: H is the weighted cost Hessian 2 w_j diag(q, r).
+    sigma = 0, y = e_r: H is the Hessian of the single defect r (supported on 2 nodes)."""
+    w = small(name, 3)
+    P = O.Problem(w)
+    rng = np.random.default_rng(3)
+    x, _ = rand_point(w, rng)
+    hr, hc = O.hess_structure(P)
+    h = w["T"] / w["N"]
+    ev = O.evaluate(P, x, np.zeros(P.m), 1.0)
+    nx, nu, N = w["nx"], w["nu"], w["N"]
+    diag = np.concatenate([np.tile(2.0 * np.array(w["q"]), N + 1), np.tile(2.0 * np.array(w["r"]), N + 1)])
+    wts = np.concatenate([np.repeat([h / 2] + [h] * (N - 1) + [h / 2], nx),
+                          np.repeat([h / 2] + [h] * (N - 1) + [h / 2], nu)])
+    expect = np.where(hr == hc, (diag * wts)[hr], 0.0)
+    np.testing.assert_allclose(ev["hess"], expect, rtol=1e-15, atol=0)
+    r = P.m - 1  # last defect of the last component: nodes N-1 and N
+    y = np.zeros(P.m); y[r] = 1.0
+    ev = O.evaluate(P, x, y, 0.0)
+    Hcs = dense_hess_cs(P, x, y, 0.0)
+    np.testing.assert_allclose(ev["hess"], Hcs[hr, hc], rtol=1e-12, atol=1e-14)
+    nz = ev["hess"] != 0
+    node_of = lambda v: np.where(v < nx * (N + 1), v // nx, (v - nx * (N + 1)) // nu)
+    assert set(np.unique(node_of(hr[nz]))) <= {N - 1, N}
+
+
+# ---------------------------------------------------------------------------------------
+# Closed form: the paper's double integrator (Sec. 5)
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("N", [10, 100, 1000])
+def test_dint_closed_form(N):
+    gd = read_golden("dint_double_integrator.txt")
+    w = small("dint", N)
+    P = O.Problem(w)
+    h = 1.0 / N
+    t = np.arange(N + 1) * h
+    x1 = gd["x1_coef0"] + gd["x1_coef2"] * t**2 + gd["x1_coef3"] * t**3
+    x2 = gd["x2_coef1"] * t + gd["x2_coef2"] * t**2
+    u = gd["u_coef0"] + gd["u_coef1"] * t
+    X = np.stack([x1, x2], 1).ravel()
+    x = np.concatenate([X, u])
+    y = np.random.default_rng(0).standard_normal(P.m)
+    ev = O.evaluate(P, x, y, 1.0)
+    c = ev["c"]
+    # boundary rows are the state values themselves (bit-exact)
+    assert c[0] == X[0] and c[1] == X[1] and c[2] == X[2 * N] and c[3] == X[2 * N + 1]
+    np.testing.assert_allclose(c[4:4 + N], gd["defect1_h3_coef"] * h**3, rtol=1e-6, atol=4e-16)
+    np.testing.assert_allclose(c[4 + N:], gd["defect2"], atol=4e-15)
+    assert abs(ev["f"] - (gd["optimal_cost"] + gd["cost_h2_coef"] * h**2)) < 1e-13
+    # the Jacobian is constant: +-1 and -h/2, bit-exact
+    jr, jc = O.jac_structure(P)
+    J = ev["jac"]
+    assert set(np.unique(J)) <= {1.0, -1.0, -h / 2}
+    Jd = np.zeros((P.m, P.n)); Jd[jr, jc] = J
+    for j in range(N):
+        r1, r2 = 4 + j, 4 + N + j
+        assert Jd[r1, 2 * j] == -1 and Jd[r1, 2 * j + 2] == 1
+        assert Jd[r1, 2 * j + 1] == -h / 2 and Jd[r1, 2 * j + 3] == -h / 2
+        assert Jd[r2, 2 * j + 1] == -1 and Jd[r2, 2 * j + 3] == 1
+        uj = 2 * (N + 1) + j
+        assert Jd[r2, uj] == -h / 2 and Jd[r2, uj + 1] == -h / 2
+    # H is diagonal on u with value sigma * w_j (d2 (u^2/2) = 1)
+    hr, hc = O.hess_structure(P)
+    assert np.all(hr == hc) and np.all(hr >= 2 * (N + 1))
+    wts = np.array([h / 2] + [h] * (N - 1) + [h / 2])
+    assert np.array_equal(ev["hess"], wts)
+
+
+# ---------------------------------------------------------------------------------------
+# Physics pins of the model right-hand sides
+# ---------------------------------------------------------------------------------------
+def test_vdp_limit_cycle_period_and_amplitude():
+    """Integrate u = 0 with the oracle's own trapezoidal defect (Newton on c_{.,0} = 0 at N=1)
+    and recover the published period and amplitude of the mu = 1 limit cycle."""
+    gd = read_golden("vdp_limit_cycle.txt")
+    hstep = 0.004
+    w = dict(synth.workload("vdp_n1e3"), N=1, T=hstep, params=[gd["mu"]])
+    P = O.Problem(w)
+    jr, jc = O.jac_structure(P)
+    X = np.array([2.0, 0.0])
+    traj = [X.copy()]
+    for _ in range(int(40.0 / hstep)):
+        Xn = X.copy()
+        for _ in range(8):
+            x = np.concatenate([X, Xn, [0.0, 0.0]])
+            ev = O.evaluate(P, x, np.zeros(P.m), 1.0)
+            Jd = np.zeros((P.m, P.n)); Jd[jr, jc] = ev["jac"]
+            res = ev["c"][2:4]
+            dX = np.linalg.solve(Jd[2:4, 2:4], -res)
+            Xn = Xn + dX
+            if np.max(np.abs(dX)) < 1e-15:
+                break
+        X = Xn
+        traj.append(X.copy())
+    traj = np.array(traj)
+    t = np.arange(len(traj)) * hstep
+    x1 = traj[:, 0]
+    up = np.where((x1[:-1] < 0) & (x1[1:] >= 0))[0]
+    tc = t[up] + hstep * (-x1[up]) / (x1[up + 1] - x1[up])
+    period = np.mean(np.diff(tc[-3:]))
+    amp = np.max(np.abs(x1[t > 20.0]))
+    assert abs(period - gd["period"]) < 2e-3 * gd["period"]
+    assert abs(amp - gd["amplitude"]) < 2e-3 * gd["amplitude"]
+
+
+def test_cartpole_conservation_laws():
+    """With F the horizontal force on the cart: d/dt of the horizontal momentum
+    (mc+mp) pd + mp l w cos(th) equals F, and d/dt of the energy
+    1/2 (mc+mp) pd^2 + mp l pd w cos(th) + 1/2 mp l^2 w^2 - mp g l cos(th) equals F pd.
+    The two identities fix both accelerations."""
+    w = synth.workload("cartpole_n1e5")
+    P = O.Problem(small("cartpole_n1e5", 1))
+    mc, mp, l, g = w["params"]
+    rng = np.random.default_rng(5)
+    for _ in range(50):
+        p, pd, th, om, F = rng.uniform(-3, 3, 5)
+        f = O.model_f(P, [p, pd, th, om, F])
+        assert f[0] == pd and f[2] == om
+        pdd, thdd = f[1], f[3]
+        dmom = (mc + mp) * pdd + mp * l * (thdd * np.cos(th) - om**2 * np.sin(th))
+        dE = ((mc + mp) * pd * pdd + mp * l * (pdd * om * np.cos(th) + pd * thdd * np.cos(th)
+                                               - pd * om**2 * np.sin(th))
+              + mp * l**2 * om * thdd + mp * g * l * np.sin(th) * om)
+        assert abs(dmom - F) < 1e-12 * (1 + abs(F) + abs(pdd) + abs(thdd))
+        assert abs(dE - F * pd) < 1e-12 * (1 + abs(F * pd) + abs(pdd) + abs(thdd)) * 10
+
+
+def test_heat_laplacian_boundary_conditions():
+    """Sum of the discrete Laplacian telescopes to (x_0 - x_1) + (x_{n+1} - x_n) over dx^2:
+    with the Dirichlet ghost x_0 = u and the Neumann ghost x_{n+1} = x_n this is
+    (u - x_1) / dx^2.  A constant profile equal to u has zero Laplacian everywhere, and a
+    linear profile has zero second difference away from the Neumann end."""
+    P = O.Problem(small("heat_n2e4", 1))
+    n = 64
+    dx = 1.0 / n
+    rng = np.random.default_rng(9)
+    for _ in range(10):
+        xc = rng.uniform(0, 1, n); u = rng.uniform(-1, 1)
+        f = O.model_f(P, np.concatenate([xc, [u]]))
+        lap = f + xc**3
+        assert abs(lap.sum() - (u - xc[0]) / dx**2) < 1e-9 * np.abs(lap).sum()
+    cval = 0.37
+    f = O.model_f(P, np.full(n + 1, cval))
+    np.testing.assert_allclose(f, -cval**3, rtol=1e-13)
+    a, b = 0.2, 0.01
+    xc = a + b * np.arange(1, n + 1)
+    f = O.model_f(P, np.concatenate([xc, [a]]))
+    np.testing.assert_allclose(f[:-1], -xc[:-1] ** 3, rtol=1e-9, atol=1e-9)
+    assert abs(f[-1] - (-b / dx**2 - xc[-1] ** 3)) < 1e-9
+
+
+# ---------------------------------------------------------------------------------------
+# Products and the parameter derivative
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("name", MODELS)
+def test_products_vs_complex_step_and_adjoint(name):
+    w = small(name, 3 if name == "heat_n2e4" else 9)
+    P = O.Problem(w)
+    rng = np.random.default_rng(13)
+    x, y = rand_point(w, rng)
+    v = rng.uniform(-1, 1, P.n)
+    wv = rng.standard_normal(P.m)
+    sigma = 1.3
+    Jv = O.jprod(P, x, v)
+    np.testing.assert_allclose(Jv, O.cs_cons(P, x, v), rtol=1e-13, atol=1e-14)
+    Jtw = O.jtprod(P, x, wv)
+    Jtw_cs = np.array([wv @ O.cs_cons(P, x, np.eye(P.n)[i]) for i in range(P.n)])
+    np.testing.assert_allclose(Jtw, Jtw_cs, rtol=1e-12, atol=1e-13)
+    assert abs(wv @ Jv - Jtw @ v) <= 1e-13 * (np.abs(wv) @ np.abs(Jv) + np.abs(Jtw) @ np.abs(v))
+    Hv = O.hprod(P, x, y, sigma, v)
+    np.testing.assert_allclose(Hv, O.cs_lagrangian_grad(P, x, v, y, sigma), rtol=1e-12, atol=1e-13)
+
+
+def test_dpar_vjp_vs_complex_step():
+    w = small("vdp_n1e3", 17)
+    P = O.Problem(w, mu=1.7)
+    rng = np.random.default_rng(17)
+    x, _ = rand_point(w, rng)
+    wv = rng.standard_normal(P.m)
+    got = O.dpar_vjp(P, x, wv)
+    ref = wv @ O.cs_cons(P, x, np.zeros(P.n), dmu=1.0)
+    assert abs(got - ref) <= 1e-13 * (1 + abs(ref))
+    # the mixed derivative d/dmu (J^T w) is the gradient of (dc/dmu)^T w in x
+    mixed = O.cs_jtprod_dmu(P, x, wv)
+    fd = np.array([(O.dpar_vjp(P, x + 1e-6 * e, wv) - O.dpar_vjp(P, x - 1e-6 * e, wv)) / 2e-6
+                   for e in np.eye(P.n)])
+    np.testing.assert_allclose(mixed, fd, rtol=1e-6, atol=1e-8)
+
+
+def test_shadow_bounds_value():
+    w = small("cartpole_n1e5", 6)
+    P = O.Problem(w)
+    rng = np.random.default_rng(19)
+    x, y = rand_point(w, rng)
+    ev = O.evaluate(P, x, y, 1.0, shadow=True)
+    for k in ["c", "g", "jac", "hess"]:
+        mag, v = ev[k + "_mag"], np.abs(ev[k])
+        # an output copied from an input is exact (bound 0); every computed one is bounded by
+        # at least its own magnitude (the rounding of its last operation)
+        assert np.all((mag == 0) | (mag >= v * (1 - 1e-15)))
+    assert np.all(ev["c_mag"][:4] == 0)
+    assert ev["f_mag"] >= abs(ev["f"])
+
+
+def test_full_size_oracle_runs():
+    """The oracle evaluates the N=1000 Van der Pol workload end to end on seeded inputs."""
+    w = synth.workload("vdp_n1e3")
+    P = O.Problem(w)
+    d = synth.draw(w)
+    ev = O.evaluate(P, d["x"], d["y"], w["sigma"])
+    assert np.isfinite(ev["f"]) and ev["jac"].size == P.nnzj and ev["hess"].size == P.nnzh
+    assert ev["c"][0] == d["x"][0] and ev["c"][1] == d["x"][1]
