@@ -1,0 +1,349 @@
+"""Benchmark: Jacobian + Hessian COO nonzeros per second (FP64) of the trapezoidal
+transcription evaluator on GB300, with the HBM roofline fraction of the dominant kernel.
+
+One step = one pass of the hot path on one problem: the fused evaluation (objective,
+constraints, gradient, Jacobian and Hessian values) followed by the three products Jv,
+J^T v and H v.  value = (nnz_J + nnz_H) * steps * ranks / (max over ranks of the summed
+step times).  Inputs are resident in HBM; between timed steps the L2 is flushed by
+writing a 512 MB buffer (outside the timed events).  `e2e` repeats the step through the
+same API with pinned host buffers and every host<->device copy inside the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank evaluates its own instance (weak scaling, no collective
+in the data path); rank 0 prints the JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2510_03932_gb300 import synth  # noqa: E402
+
+METRIC = "Jac+Hess COO nnz/s (FP64) and % HBM roofline; batched/adjoint vs plain, 1e-12"
+DEFAULT_WORKLOAD = "vdp_mu_n1e6"
+
+
+def algorithmic_bytes(w, kind):
+    """Bytes each kernel must move at least once: inputs read once, outputs written once."""
+    n, m = synth.dims(w)
+    P = _counts(w)
+    nnzj, nnzh = P
+    if kind == "eval_all":
+        return 8 * (n + m + 1 + m + n + nnzj + nnzh)
+    if kind == "jh":
+        return 8 * (n + m + nnzj + nnzh)
+    if kind == "jprod":
+        return 8 * (n + n + m)
+    if kind == "jtprod":
+        return 8 * (n + m + n)
+    if kind == "hprod":
+        return 8 * (n + m + n + n)
+    raise KeyError(kind)
+
+
+_COUNT_CACHE = {}
+
+
+def _counts(w):
+    key = (w["model"], w["nx"], w["N"], tuple(w["q"]), tuple(w["r"]), w.get("xf") is not None)
+    if key not in _COUNT_CACHE:
+        from paper_2510_03932_gb300 import ocp
+        H = ocp.OCP.from_workload(w)
+        _COUNT_CACHE[key] = (H.nnzj, H.nnzh)
+        H.close()
+    return _COUNT_CACHE[key]
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        import tempfile
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [s.strip() for s in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1])); mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_2510_03932_gb300 import ocp
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    w = synth.workload(args.workload)
+    d = synth.draw(w, seed=w["seed"] + rank)
+    H = ocp.OCP.from_workload(w)
+    n, m, nnzj, nnzh = H.n, H.m, H.nnzj, H.nnzh
+    sigma = w["sigma"]
+    x = torch.from_numpy(d["x"]).to(dev)
+    y = torch.from_numpy(d["y"]).to(dev)
+    vn = torch.from_numpy(d["vn"]).to(dev)
+    vm = torch.from_numpy(d["vm"]).to(dev)
+    f = torch.empty(1, dtype=torch.float64, device=dev)
+    c = torch.empty(m, dtype=torch.float64, device=dev)
+    g = torch.empty(n, dtype=torch.float64, device=dev)
+    jv = torch.empty(nnzj, dtype=torch.float64, device=dev)
+    hv = torch.empty(nnzh, dtype=torch.float64, device=dev)
+    Jv = torch.empty(m, dtype=torch.float64, device=dev)
+    Jtv = torch.empty(n, dtype=torch.float64, device=dev)
+    Hv = torch.empty(n, dtype=torch.float64, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    names = ["eval_all", "jprod", "jtprod", "hprod"]
+
+    def step(ev=None):
+        if ev: ev[0].record(stream)
+        H.eval_all(x, y, sigma, f, c, g, jv, hv, alloc=False)
+        if ev: ev[1].record(stream)
+        H.jprod(x, vn, Jv)
+        if ev: ev[2].record(stream)
+        H.jtprod(x, vm, Jtv)
+        if ev: ev[3].record(stream)
+        H.hprod(x, y, sigma, vn, Hv)
+        if ev: ev[4].record(stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize(dev)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    sampler = ClockSampler(dev.index if rank == 0 else -1) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()
+        step(evs[k])
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - t0
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop() if sampler else None
+    per = np.array([[evs[k][i].elapsed_time(evs[k][i + 1]) for i in range(4)] for k in range(args.steps)])
+    step_ms = per.sum(axis=1)
+    tot_ms = float(step_ms.sum())
+    if world > 1:
+        t = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        tot_ms = float(t.item())
+    kern_ms = per.mean(axis=0)
+    # --- J+H alone (the fused Jacobian+Hessian values launch), timed the same way
+    jh = []
+    for k in range(min(args.steps, 50)):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        H.eval_all(x, y, sigma, None, None, None, jv, hv, alloc=False)
+        e1.record(stream)
+        jh.append((e0, e1))
+    torch.cuda.synchronize(dev)
+    jh_ms = float(np.mean([a.elapsed_time(b) for a, b in jh]))
+    # --- end to end: pinned host buffers, copies inside the timed region
+    hx = torch.from_numpy(d["x"]).pin_memory(); hy = torch.from_numpy(d["y"]).pin_memory()
+    hvn = torch.from_numpy(d["vn"]).pin_memory(); hvm = torch.from_numpy(d["vm"]).pin_memory()
+    outs = [f, c, g, jv, hv, Jv, Jtv, Hv]
+    houts = [torch.empty(t.numel(), dtype=torch.float64).pin_memory() for t in outs]
+    e2e_steps = max(3, min(args.steps, 20))
+    e2e_ms = []
+    for k in range(e2e_steps + 2):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        x.copy_(hx, non_blocking=True); y.copy_(hy, non_blocking=True)
+        vn.copy_(hvn, non_blocking=True); vm.copy_(hvm, non_blocking=True)
+        step()
+        for ho, t in zip(houts, outs):
+            ho.copy_(t, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        if k >= 2:
+            e2e_ms.append(e0.elapsed_time(e1))
+    nnz = nnzj + nnzh
+    e2e_val = nnz * world / (float(np.mean(e2e_ms)) * 1e-3)
+    hbm, peak_kind = peaks()
+    ab = algorithmic_bytes(w, "eval_all")
+    achieved = ab / (kern_ms[0] * 1e-3) / 1e9
+    res = dict(
+        metric=METRIC, value=nnz * args.steps * world / (tot_ms * 1e-3), unit="nnz/s", n_gpus=world,
+        steps=args.steps, warmup=args.warmup, ms_per_step=tot_ms / args.steps, higher_is_better=True,
+        scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+        config=dict(workload=args.workload, model=w["model"], N=w["N"], n=n, m=m, nnz_jac=nnzj, nnz_hess=nnzh,
+                    step="eval_all(F,c,grad,J,H)+jprod+jtprod+hprod", l2="flushed between steps (512 MB write)",
+                    parallelism="replicas" if world > 1 else "single"),
+        roofline=dict(bound="hbm", achieved=achieved, peak=hbm, unit="GB/s", frac=achieved / hbm, traffic=None,
+                      kernel="k_node_eval (fused eval_all)", peak_source=peak_kind,
+                      algorithmic_bytes=ab),
+        kernels={nm: dict(ms=float(kern_ms[i]), GBps=algorithmic_bytes(w, nm) / (kern_ms[i] * 1e-3) / 1e9)
+                 for i, nm in enumerate(names)},
+        jac_hess_only=dict(ms=jh_ms, nnz_per_s=nnz / (jh_ms * 1e-3),
+                           GBps=algorithmic_bytes(w, "jh") / (jh_ms * 1e-3) / 1e9,
+                           frac=algorithmic_bytes(w, "jh") / (jh_ms * 1e-3) / 1e9 / hbm),
+        e2e=dict(value=e2e_val, unit="nnz/s", h2d_bytes_per_step=8 * (n + m + n + m),
+                 d2h_bytes_per_step=8 * sum(t.numel() for t in outs), ms=float(np.mean(e2e_ms))),
+        gpu_launches=4 * args.steps, clocks=clocks, wall_s=wall,
+    )
+    return res
+
+
+def run_profile(args):
+    """Few launches of one call, for ncu captures (no timing output of value)."""
+    import torch
+    from paper_2510_03932_gb300 import ocp
+
+    w = synth.workload(args.workload)
+    d = synth.draw(w)
+    H = ocp.OCP.from_workload(w)
+    x, y = torch.from_numpy(d["x"]).cuda(), torch.from_numpy(d["y"]).cuda()
+    vn, vm = torch.from_numpy(d["vn"]).cuda(), torch.from_numpy(d["vm"]).cuda()
+    f, c, g, jv, hv = H.eval_all(x, y, 1.0)
+    Jv, Jtv, Hv = H.jprod(x, vn), H.jtprod(x, vm), H.hprod(x, y, 1.0, vn)
+    calls = {
+        "eval_all": lambda: H.eval_all(x, y, 1.0, f, c, g, jv, hv, alloc=False),
+        "jh": lambda: H.eval_all(x, y, 1.0, None, None, None, jv, hv, alloc=False),
+        "jprod": lambda: H.jprod(x, vn, Jv),
+        "jtprod": lambda: H.jtprod(x, vm, Jtv),
+        "hprod": lambda: H.hprod(x, y, 1.0, vn, Hv),
+    }
+    fns = list(calls.values()) if args.profile_kernel == "all" else [calls[args.profile_kernel]]
+    for _ in range(args.warmup + args.steps):
+        for fn in fns:
+            fn()
+    torch.cuda.synchronize()
+    print(json.dumps(dict(profile_kernel=args.profile_kernel, workload=args.workload, launches=args.warmup + args.steps)))
+
+
+def oracle_step_time(w, budget_s):
+    """Time the oracle on a bounded sample of the workload: the same problem at a shorter
+    horizon, evaluated in full (values, products) as many times as fit in budget_s."""
+    from oracle import oracle as O
+    Ns = min(w["N"], 100000)
+    ws = synth.with_horizon(w, Ns)
+    d = synth.draw(ws)
+    P = O.Problem(ws)
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        O.evaluate(P, d["x"], d["y"], ws["sigma"])
+        O.jprod(P, d["x"], d["vn"])
+        O.jtprod(P, d["x"], d["vm"])
+        O.hprod(P, d["x"], d["y"], ws["sigma"], d["vn"])
+        reps += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    dt = (time.perf_counter() - t0) / reps
+    return (P.nnzj + P.nnzh) / dt, dict(value=(P.nnzj + P.nnzh) / dt, unit="nnz/s", cores=1, kind="oracle",
+                                        sample="%s at N=%d (full step: eval + 3 products), %d reps, %.1f s"
+                                               % (w["name"], Ns, reps, reps * dt))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-budget", type=float, default=10.0)
+    ap.add_argument("--profile-kernel", default=None,
+                    choices=["eval_all", "jh", "jprod", "jtprod", "hprod", "all"],
+                    help="only launch this call warmup+steps times (for ncu captures)")
+    args = ap.parse_args()
+    if args.profile_kernel:
+        run_profile(args)
+        return
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        w = synth.workload(args.workload)
+        for _ in range(max(0, min(args.warmup, 1))):
+            oracle_step_time(w, 0.0)
+        vals = [oracle_step_time(w, max(1.0, args.cpu_budget / max(1, args.steps)))[0] for _ in range(args.steps)]
+        v = float(np.mean(vals))
+        cb = oracle_step_time(w, 0.0)[1]
+        cb["value"] = v
+        print(json.dumps(dict(metric=METRIC, value=v, unit="nnz/s", n_gpus=1, steps=args.steps, warmup=args.warmup,
+                              higher_is_better=True, impl="reference", dtype="f64", data="synthetic",
+                              config=dict(workload=args.workload, model=w["model"], N=w["N"]),
+                              cpu_baseline=cb, e2e=dict(value=v, unit="nnz/s", h2d_bytes_per_step=0,
+                                                        d2h_bytes_per_step=0))))
+        return
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    res = run_ours(args, rank, world)
+    if rank == 0:
+        _, cb = oracle_step_time(synth.workload(args.workload), args.cpu_budget)
+        res["cpu_baseline"] = cb
+        print(json.dumps(res))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,165 @@
+/*
+ * ocp.h — C-ABI of the GB300 (sm_103a) FP64 evaluator for trapezoidal direct transcriptions
+ * of optimal control problems.
+ *
+ * The problem (paper, Sec. 3 and Sec. 5):  minimise  int_0^T f0(x(t), u(t)) dt  subject to
+ * x' = f(x, u), x(0) = x0 (and optionally x(T) = xf), transcribed on the uniform grid
+ * t_j = j h, h = T/N, j = 0..N, with the trapezoidal rule for both the dynamics and the cost.
+ *
+ * Unknown vector (length n = (nx+nu)(N+1); Sec. 3 unknowns, Sec. 5 variable layout):
+ *     x = [ X_0, X_1, ..., X_N, U_0, U_1, ..., U_N ],   X_j in R^nx, U_j in R^nu,
+ *   i.e. X_{j,k} at index k + nx*j and U_{j,i} at index nx*(N+1) + i + nu*j (0-based).
+ * Constraints (length m = nb + nx*N, declaration order of Sec. 5):
+ *     rows 0..nx-1         : X_{0,k}                (the expression; bounds are x0)
+ *     rows nx..2nx-1       : X_{N,k}                (only when a final state was set)
+ *     row  nb + k*N + j    : (X_{j+1,k} - X_{j,k}) - h/2 (f_k(z_j) + f_k(z_{j+1})),  z_j = (X_j, U_j)
+ * Objective (Sec. 5 trapezoidal cost): F = sum_j w_j f0(z_j), w_0 = w_N = h/2, else w_j = h.
+ * Lagrangian Hessian: H = sigma * Hess F + sum_r y_r Hess c_r (lower triangle stored).
+ * Sparse matrices are COO, 0-based, one entry per structural nonzero (a derivative that is
+ * not identically zero, whatever its value at x, y, sigma), sorted by (row, col).
+ *
+ * Conventions for every call below:
+ *   - Array arguments of the evaluation calls are caller-owned, contiguous FP64 (or int32)
+ *     DEVICE pointers; the handle owns only its pattern tables and a small scratch area.
+ *   - Calls are asynchronous on the given stream (a cudaStream_t passed as void*; NULL is
+ *     the legacy default stream).  The status reports argument and launch errors only.
+ *   - Calls on one handle must not overlap on the GPU (they share the handle's scratch);
+ *     use one handle per concurrent stream.
+ *   - No call aborts the process.  On failure the status is non-zero and
+ *     ocp_last_error(handle) (or ocp_last_error(NULL) for ocp_create / ocp_batch_create)
+ *     returns a message.
+ */
+#ifndef OCP_GB300_H
+#define OCP_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ocp ocp_t;             /* opaque; created by ocp_create, owned by the library */
+typedef struct ocp_batch ocp_batch_t; /* opaque; many problems evaluated in one launch */
+
+typedef enum {
+  OCP_OK = 0,
+  OCP_EINVAL = 1,   /* null or malformed argument, unaligned pointer */
+  OCP_EDIM = 2,     /* dimensions disagree with the model, or a size does not fit int32 */
+  OCP_ENOMEM = 3,   /* device or host allocation failed */
+  OCP_ECUDA = 4,    /* a CUDA runtime call or kernel launch failed */
+  OCP_EMODEL = 5,   /* unknown model, cost kind, or operation not provided for this model */
+  OCP_ETIMEOUT = 6  /* a bounded device wait ran out (reserved; no current kernel waits) */
+} ocp_status;
+
+/* Models.  Parameters (params[], nparams):
+ *   VDP      (nx=2, nu=1): mu.         x1' = x2,  x2' = mu (1 - x1^2) x2 - x1 + u
+ *   CARTPOLE (nx=4, nu=1): mc, mp, l, g.  state (p, p', th, th'), th from the downward
+ *            vertical, point-mass pole:  D = mc + mp sin^2 th,
+ *            p''  = (u + mp sin th (l th'^2 + g cos th)) / D,
+ *            th'' = (-u cos th - mp l th'^2 cos th sin th - (mc+mp) g sin th) / (l D)
+ *   HEAT1D   (nx=ncell, nu=1): ncell.  x_k' = (x_{k-1} - 2 x_k + x_{k+1}) / dx^2 - x_k^3,
+ *            dx = 1/ncell, ghost x_0 = u (Dirichlet control), x_{ncell+1} = x_ncell (Neumann)
+ *   DINT     (nx=2, nu=1): none.       x1' = x2,  x2' = u   (the paper's Sec. 5 example) */
+enum { OCP_MODEL_VDP = 1, OCP_MODEL_CARTPOLE = 2, OCP_MODEL_HEAT1D = 3, OCP_MODEL_DINT = 4 };
+
+/* Running cost kinds.  DIAG_QUADRATIC: f0 = sum_k q_k (x_k - xref_k)^2 + sum_i r_i (u_i - uref_i)^2.
+ * q, r are required; xref, uref may be NULL (zero). */
+enum { OCP_COST_DIAG_QUADRATIC = 0 };
+
+typedef struct { int model; const double* params; int nparams; } ocp_dynamics;
+typedef struct { int kind; const double* q; const double* r; const double* xref; const double* uref; } ocp_cost;
+
+/* Build a problem (Sec. 5, the generated model constructor: scheme = trapezoid, grid size N,
+ * uniform grid).  Host pointers in `dyn` and `cost` are copied.  Runs the host pattern
+ * compiler and uploads the pattern once.  Errors: OCP_EMODEL (unknown model or cost kind),
+ * OCP_EDIM (nx/nu/nparams disagree with the model, N < 1, T <= 0, or n, m, nnz >= 2^31),
+ * OCP_ENOMEM, OCP_ECUDA.  Binds to the current CUDA device. */
+ocp_status ocp_create(const ocp_dynamics* dyn, const ocp_cost* cost, int nx, int nu, int64_t N,
+                      double T, ocp_t** out);
+void ocp_destroy(ocp_t* h);
+
+/* Boundary values (Sec. 5 boundary generator: lcon = ucon = x0).  Host pointers of length nx.
+ * xf == NULL leaves the problem without final rows; a non-NULL xf adds the nx rows X_{N,k}
+ * (this changes m and nnz_J; call it before asking for dimensions or structure).
+ * x0 == NULL keeps zeros. */
+ocp_status ocp_set_boundary(ocp_t* h, const double* x0, const double* xf);
+
+/* Sizes: n variables, m constraints, Jacobian and (lower) Hessian nonzeros.  Host outputs. */
+ocp_status ocp_dims(const ocp_t* h, int64_t* n, int64_t* m, int64_t* nnzj, int64_t* nnzh);
+
+/* Bounds (HOST arrays): lvar/uvar = -inf/+inf (the models carry no variable bounds),
+ * lcon = ucon = [x0; xf; 0 for every defect].  Any pointer may be NULL. */
+ocp_status ocp_bounds(const ocp_t* h, double* lvar, double* uvar, double* lcon, double* ucon);
+
+/* Objective F(x) (Sec. 5 trapezoidal cost) written to the device scalar f. */
+ocp_status eval_obj(ocp_t* h, const double* x, double* f, void* stream);
+/* Constraint vector c(x), length m (Sec. 5 boundary rows and trapezoidal defects). */
+ocp_status eval_cons(ocp_t* h, const double* x, double* c, void* stream);
+/* Gradient of F, length n. */
+ocp_status eval_grad(ocp_t* h, const double* x, double* g, void* stream);
+
+/* Jacobian of c: structure (int32 device arrays of length nnzj) and values (FP64, same order).
+ * Row (k,j) holds, by increasing column, the entries on X_j, X_{j+1}, U_j, U_{j+1}. */
+ocp_status jac_coo_structure(const ocp_t* h, int32_t* rows, int32_t* cols, void* stream);
+ocp_status jac_coo_values(ocp_t* h, const double* x, double* vals, void* stream);
+
+/* Lagrangian Hessian, lower triangle (row >= col): structure (length nnzh) and values for
+ * multipliers y (length m, boundary rows first) and objective weight sigma.  H is block-
+ * diagonal by node; the X rows of all nodes come first, then the U rows. */
+ocp_status hess_coo_structure(const ocp_t* h, int32_t* rows, int32_t* cols, void* stream);
+ocp_status hess_coo_values(ocp_t* h, const double* x, const double* y, double sigma, double* vals,
+                           void* stream);
+
+/* Matrix-free products at x:  Jv (v: n -> m),  J^T v (v: m -> n),  H v (v: n -> n, full
+ * symmetric H for multipliers y and weight sigma).  Output arrays must not alias inputs. */
+ocp_status jprod(ocp_t* h, const double* x, const double* v, double* Jv, void* stream);
+ocp_status jtprod(ocp_t* h, const double* x, const double* v, double* Jtv, void* stream);
+ocp_status hprod(ocp_t* h, const double* x, const double* y, double sigma, const double* v,
+                 double* Hv, void* stream);
+
+/* Everything one interior-point iteration needs, in one fused launch: f (device scalar), c,
+ * g, Jacobian values and Hessian values.  Any output pointer may be NULL (not computed). */
+ocp_status ocp_eval_all(ocp_t* h, const double* x, const double* y, double sigma, double* f,
+                        double* c, double* g, double* jvals, double* hvals, void* stream);
+
+/* Parameter derivative for the Van der Pol model (mu = params[0]):
+ *   dmu = (dc/dmu)^T w   (device scalar),  optionally together with J^T w into Jtw (may be NULL).
+ * Other models: OCP_EMODEL. */
+ocp_status ocp_vjp_param(ocp_t* h, const double* x, const double* w, double* Jtw, double* dmu,
+                         void* stream);
+
+/* Set the value of params[0] (e.g. Van der Pol mu) without rebuilding the pattern. */
+ocp_status ocp_set_param0(ocp_t* h, double value);
+
+/* Evaluate only the nodes [node_begin, node_end) (and the defect rows j in that range) of
+ * eval_all, writing into the full-size output arrays.  Used to split one problem into
+ * contiguous node shards (each shard reads a one-node halo of x and y).  f receives this
+ * shard's partial objective.  Boundary rows are written by the shards that own node 0 / N. */
+ocp_status ocp_eval_all_range(ocp_t* h, int64_t node_begin, int64_t node_end, const double* x,
+                              const double* y, double sigma, double* f, double* c, double* g,
+                              double* jvals, double* hvals, void* stream);
+
+/* Message of the last failure on this handle (NULL: of the last failed create). */
+const char* ocp_last_error(const ocp_t* h);
+
+/* Batched form: `count` problems of the same model, possibly different N, cost weights and
+ * boundary values, evaluated by one persistent launch over the concatenated node space.
+ * The handles must stay alive while the batch is used.  Variables, constraints and nonzeros
+ * of instance i start at the offsets returned by ocp_batch_offsets (prefix sums), each
+ * instance laid out exactly as its own handle.  Errors: OCP_EMODEL for mixed models or a
+ * model the batched kernel does not provide. */
+ocp_status ocp_batch_create(ocp_t* const* items, int count, ocp_batch_t** out);
+void ocp_batch_destroy(ocp_batch_t* b);
+/* Host arrays of length count+1: offsets into x, y/c, g, jac values, hess values. */
+ocp_status ocp_batch_offsets(const ocp_batch_t* b, int64_t* xoff, int64_t* coff, int64_t* joff,
+                             int64_t* hoff);
+/* Launch configuration: nodes handled per thread (1 or 2) and threads per CTA (128..1024). */
+ocp_status ocp_batch_set_config(ocp_batch_t* b, int nodes_per_thread, int threads);
+/* Per-instance objective values go to f[count]. */
+ocp_status ocp_batch_eval_all(ocp_batch_t* b, const double* x, const double* y, double sigma,
+                              double* f, double* g, double* jvals, double* hvals, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OCP_GB300_H */

@@ -1,0 +1,361 @@
+// C-ABI of the evaluator (declarations and contracts in include/ocp.h).
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <limits>
+#include <mutex>
+#include <new>
+#include <unordered_map>
+
+#include "ocp_internal.h"
+
+using namespace ocpg;
+
+static thread_local std::string g_create_err;
+
+namespace ocpg {
+
+ocp_status set_err(ocp* h, ocp_status st, const std::string& msg) {
+  if (h) h->err = msg;
+  else g_create_err = msg;
+  return st;
+}
+
+ocp_status cuda_err(ocp* h, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return OCP_OK;
+  return set_err(h, OCP_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// One CTA per tile: the hardware block scheduler balances the tail.  (Results do not depend
+// on the grid: reductions are per tile and summed in tile order.)
+int occupancy_grid(ocp* h, const void* kernel, int threads, size_t smem, int64_t work_tiles) {
+  (void)h; (void)kernel; (void)threads; (void)smem;
+  if (work_tiles < 1) return 1;
+  if (work_tiles > 0x7fffffff) return 0x7fffffff;
+  return (int)work_tiles;
+}
+
+}  // namespace ocpg
+
+// ---------------------------------------------------------------------------------------
+static bool aligned8(const void* p) { return ((uintptr_t)p & 7u) == 0; }
+
+static ocp_status upload_tables(ocp* h) {
+  cudaFree(h->d_rowtmpl); cudaFree(h->d_jbase); cudaFree(h->d_hent);
+  h->d_rowtmpl = nullptr; h->d_jbase = nullptr; h->d_hent = nullptr;
+  const Pattern& P = h->pat;
+  std::vector<int32_t> rt((size_t)8 * P.nx, -1);
+  for (int k = 0; k < P.nx; ++k) {
+    rt[8 * k + 0] = P.rows[k].rx;
+    rt[8 * k + 1] = P.rows[k].ru;
+    for (int e = 0; e < 4; ++e) rt[8 * k + 2 + e] = P.rows[k].xv[e];
+    for (int e = 0; e < 2; ++e) rt[8 * k + 6 + e] = P.rows[k].uv[e];
+  }
+  std::vector<int32_t> he;
+  for (auto& e : P.hent) { he.push_back(e.first); he.push_back(e.second); }
+  if (he.empty()) he.push_back(0);
+  cudaError_t e;
+  if ((e = cudaMalloc(&h->d_rowtmpl, rt.size() * sizeof(int32_t))) != cudaSuccess) return cuda_err(h, e, "cudaMalloc");
+  if ((e = cudaMalloc(&h->d_jbase, P.jbase.size() * sizeof(int64_t))) != cudaSuccess) return cuda_err(h, e, "cudaMalloc");
+  if ((e = cudaMalloc(&h->d_hent, he.size() * sizeof(int32_t))) != cudaSuccess) return cuda_err(h, e, "cudaMalloc");
+  if ((e = cudaMemcpy(h->d_rowtmpl, rt.data(), rt.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
+    return cuda_err(h, e, "cudaMemcpy");
+  if ((e = cudaMemcpy(h->d_jbase, P.jbase.data(), P.jbase.size() * 8, cudaMemcpyHostToDevice)) != cudaSuccess)
+    return cuda_err(h, e, "cudaMemcpy");
+  if ((e = cudaMemcpy(h->d_hent, he.data(), he.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
+    return cuda_err(h, e, "cudaMemcpy");
+  return OCP_OK;
+}
+
+static int model_nparams(int model) {
+  switch (model) {
+    case OCP_MODEL_VDP: return 1;
+    case OCP_MODEL_CARTPOLE: return 4;
+    case OCP_MODEL_HEAT1D: return 1;
+    case OCP_MODEL_DINT: return 0;
+  }
+  return -1;
+}
+
+static void free_handle(ocp* h) {
+  if (!h) return;
+  cudaFree(h->d_rowtmpl); cudaFree(h->d_jbase); cudaFree(h->d_hent);
+  cudaFree(h->d_partials); cudaFree(h->d_counter);
+  delete h;
+}
+
+extern "C" {
+
+ocp_status ocp_create(const ocp_dynamics* dyn, const ocp_cost* cost, int nx, int nu, int64_t N, double T,
+                      ocp_t** out) {
+  if (!out) return set_err(nullptr, OCP_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!dyn || !cost) return set_err(nullptr, OCP_EINVAL, "dynamics or cost is NULL");
+  const int np = model_nparams(dyn->model);
+  if (np < 0) return set_err(nullptr, OCP_EMODEL, "unknown model id");
+  if (cost->kind != OCP_COST_DIAG_QUADRATIC) return set_err(nullptr, OCP_EMODEL, "unknown cost kind");
+  if (dyn->nparams != np || (np > 0 && !dyn->params))
+    return set_err(nullptr, OCP_EDIM, "wrong number of model parameters");
+  int enx = 0, enu = 1;
+  switch (dyn->model) {
+    case OCP_MODEL_VDP: enx = 2; break;
+    case OCP_MODEL_CARTPOLE: enx = 4; break;
+    case OCP_MODEL_DINT: enx = 2; break;
+    case OCP_MODEL_HEAT1D: {
+      const double c = dyn->params[0];
+      if (!(c >= 2.0 && c <= 128.0) || c != std::floor(c))
+        return set_err(nullptr, OCP_EDIM, "heat model: ncell must be an integer in [2, 128]");
+      enx = (int)c;
+      break;
+    }
+  }
+  if (nx != enx || nu != enu) return set_err(nullptr, OCP_EDIM, "wrong bound dimension: nx/nu disagree with the model");
+  if (N < 1) return set_err(nullptr, OCP_EDIM, "N must be >= 1");
+  if (!(T > 0.0) || !std::isfinite(T)) return set_err(nullptr, OCP_EINVAL, "T must be positive and finite");
+  if (!cost->q || !cost->r) return set_err(nullptr, OCP_EINVAL, "cost weights q and r are required");
+  ocp* h = new (std::nothrow) ocp();
+  if (!h) return set_err(nullptr, OCP_ENOMEM, "host allocation failed");
+  h->model = dyn->model; h->nx = nx; h->nu = nu; h->N = N; h->T = T;
+  h->h = T / (double)N;
+  h->hh = h->h / 2.0;
+  h->params.assign(8, 0.0);
+  for (int i = 0; i < np; ++i) h->params[i] = dyn->params[i];
+  h->q.assign(cost->q, cost->q + nx);
+  h->r.assign(cost->r, cost->r + nu);
+  h->xref.assign(nx, 0.0);
+  h->uref.assign(nu, 0.0);
+  if (cost->xref) h->xref.assign(cost->xref, cost->xref + nx);
+  if (cost->uref) h->uref.assign(cost->uref, cost->uref + nu);
+  for (double v : h->xref) if (v != 0.0) h->has_ref = true;
+  for (double v : h->uref) if (v != 0.0) h->has_ref = true;
+  h->x0.assign(nx, 0.0);
+  std::string why;
+  if (!build_pattern(h, why)) { free_handle(h); return set_err(nullptr, OCP_EDIM, why); }
+  cudaError_t e;
+  if ((e = cudaGetDevice(&h->device)) != cudaSuccess) { free_handle(h); return cuda_err(nullptr, e, "cudaGetDevice"); }
+  if ((e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device)) != cudaSuccess) {
+    free_handle(h);
+    return cuda_err(nullptr, e, "cudaDeviceGetAttribute");
+  }
+  // one partial per tile of the smallest tile (31 owned nodes), plus slack
+  h->max_partials = (int)((N + 1) / 31 + 2);
+  if ((e = cudaMalloc(&h->d_partials, sizeof(double) * h->max_partials)) != cudaSuccess ||
+      (e = cudaMalloc(&h->d_counter, sizeof(unsigned))) != cudaSuccess ||
+      (e = cudaMemset(h->d_counter, 0, sizeof(unsigned))) != cudaSuccess) {
+    free_handle(h);
+    return set_err(nullptr, OCP_ENOMEM, std::string("device allocation failed: ") + cudaGetErrorString(e));
+  }
+  ocp_status st = upload_tables(h);
+  if (st != OCP_OK) { std::string m = h->err; free_handle(h); return set_err(nullptr, st, m); }
+  *out = h;
+  return OCP_OK;
+}
+
+void ocp_destroy(ocp_t* h) { free_handle(h); }
+
+ocp_status ocp_set_boundary(ocp_t* h, const double* x0, const double* xf) {
+  if (!h) return OCP_EINVAL;
+  h->x0.assign(h->nx, 0.0);
+  if (x0) h->x0.assign(x0, x0 + h->nx);
+  const bool fin = xf != nullptr;
+  if (fin) h->xf.assign(xf, xf + h->nx);
+  else h->xf.clear();
+  if (fin != h->has_final) {
+    h->has_final = fin;
+    std::string why;
+    if (!build_pattern(h, why)) return set_err(h, OCP_EDIM, why);
+    return upload_tables(h);
+  }
+  return OCP_OK;
+}
+
+ocp_status ocp_dims(const ocp_t* h, int64_t* n, int64_t* m, int64_t* nnzj, int64_t* nnzh) {
+  if (!h) return OCP_EINVAL;
+  if (n) *n = h->pat.n;
+  if (m) *m = h->pat.m;
+  if (nnzj) *nnzj = h->pat.nnzj;
+  if (nnzh) *nnzh = h->pat.nnzh;
+  return OCP_OK;
+}
+
+ocp_status ocp_bounds(const ocp_t* h, double* lvar, double* uvar, double* lcon, double* ucon) {
+  if (!h) return OCP_EINVAL;
+  const double inf = std::numeric_limits<double>::infinity();
+  for (int64_t i = 0; i < h->pat.n; ++i) {
+    if (lvar) lvar[i] = -inf;
+    if (uvar) uvar[i] = inf;
+  }
+  for (int64_t i = 0; i < h->pat.m; ++i) {
+    double v = 0.0;
+    if (i < h->nx) v = h->x0[i];
+    else if (h->has_final && i < 2 * h->nx) v = h->xf[i - h->nx];
+    if (lcon) lcon[i] = v;
+    if (ucon) ucon[i] = v;
+  }
+  return OCP_OK;
+}
+
+}  // extern "C"
+
+static ocp_status dispatch_eval(ocp* h, unsigned out, const EvalCall& c, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  switch (h->model) {
+    case OCP_MODEL_VDP: return node_eval_vdp(h, out, c, s);
+    case OCP_MODEL_CARTPOLE: return node_eval_cartpole(h, out, c, s);
+    case OCP_MODEL_DINT: return node_eval_dint(h, out, c, s);
+    case OCP_MODEL_HEAT1D: return heat_eval(h, out, c, s);
+  }
+  return set_err(h, OCP_EMODEL, "unknown model");
+}
+
+static ocp_status dispatch_prod(ocp* h, const ProdCall& c, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  switch (h->model) {
+    case OCP_MODEL_VDP: return node_prod_vdp(h, c, s);
+    case OCP_MODEL_CARTPOLE: return node_prod_cartpole(h, c, s);
+    case OCP_MODEL_DINT: return node_prod_dint(h, c, s);
+    case OCP_MODEL_HEAT1D: return heat_prod(h, c, s);
+  }
+  return set_err(h, OCP_EMODEL, "unknown model");
+}
+
+static ocp_status need(ocp* h, const void* p, const char* name) {
+  if (!p) return set_err(h, OCP_EINVAL, std::string(name) + " is NULL");
+  if (!aligned8(p)) return set_err(h, OCP_EINVAL, std::string(name) + " is not 8-byte aligned");
+  return OCP_OK;
+}
+
+#define NEED(p) do { ocp_status _s = need(h, (p), #p); if (_s != OCP_OK) return _s; } while (0)
+#define OPT(p) do { if ((p) && !aligned8(p)) return set_err(h, OCP_EINVAL, #p " is not 8-byte aligned"); } while (0)
+
+static EvalCall full_call(const ocp* h) {
+  EvalCall c;
+  c.B = 0;
+  c.E = h->N + 1;
+  return c;
+}
+
+extern "C" {
+
+ocp_status eval_obj(ocp_t* h, const double* x, double* f, void* stream) {
+  if (!h) return OCP_EINVAL;
+  NEED(x); NEED(f);
+  EvalCall c = full_call(h);
+  c.x = x; c.f = f;
+  return dispatch_eval(h, O_F, c, stream);
+}
+
+ocp_status eval_cons(ocp_t* h, const double* x, double* cv, void* stream) {
+  if (!h) return OCP_EINVAL;
+  NEED(x); NEED(cv);
+  EvalCall c = full_call(h);
+  c.x = x; c.c = cv;
+  return dispatch_eval(h, O_C, c, stream);
+}
+
+ocp_status eval_grad(ocp_t* h, const double* x, double* g, void* stream) {
+  if (!h) return OCP_EINVAL;
+  NEED(x); NEED(g);
+  EvalCall c = full_call(h);
+  c.x = x; c.g = g;
+  return dispatch_eval(h, O_G, c, stream);
+}
+
+ocp_status jac_coo_structure(const ocp_t* h, int32_t* rows, int32_t* cols, void* stream) {
+  if (!h || !rows || !cols) return OCP_EINVAL;
+  return launch_jac_structure(h, rows, cols, (cudaStream_t)stream);
+}
+
+ocp_status jac_coo_values(ocp_t* h, const double* x, double* vals, void* stream) {
+  if (!h) return OCP_EINVAL;
+  NEED(x); NEED(vals);
+  EvalCall c = full_call(h);
+  c.x = x; c.jv = vals;
+  return dispatch_eval(h, O_J, c, stream);
+}
+
+ocp_status hess_coo_structure(const ocp_t* h, int32_t* rows, int32_t* cols, void* stream) {
+  if (!h || !rows || !cols) return OCP_EINVAL;
+  return launch_hess_structure(h, rows, cols, (cudaStream_t)stream);
+}
+
+ocp_status hess_coo_values(ocp_t* h, const double* x, const double* y, double sigma, double* vals, void* stream) {
+  if (!h) return OCP_EINVAL;
+  NEED(x); NEED(y); NEED(vals);
+  EvalCall c = full_call(h);
+  c.x = x; c.y = y; c.sigma = sigma; c.hv = vals;
+  return dispatch_eval(h, O_H, c, stream);
+}
+
+ocp_status jprod(ocp_t* h, const double* x, const double* v, double* Jv, void* stream) {
+  if (!h) return OCP_EINVAL;
+  NEED(x); NEED(v); NEED(Jv);
+  ProdCall c;
+  c.kind = P_JPROD; c.x = x; c.v = v; c.out = Jv;
+  return dispatch_prod(h, c, stream);
+}
+
+ocp_status jtprod(ocp_t* h, const double* x, const double* v, double* Jtv, void* stream) {
+  if (!h) return OCP_EINVAL;
+  NEED(x); NEED(v); NEED(Jtv);
+  ProdCall c;
+  c.kind = P_JTPROD; c.x = x; c.v = v; c.out = Jtv;
+  return dispatch_prod(h, c, stream);
+}
+
+ocp_status hprod(ocp_t* h, const double* x, const double* y, double sigma, const double* v, double* Hv,
+                 void* stream) {
+  if (!h) return OCP_EINVAL;
+  NEED(x); NEED(y); NEED(v); NEED(Hv);
+  ProdCall c;
+  c.kind = P_HPROD; c.x = x; c.y = y; c.sigma = sigma; c.v = v; c.out = Hv;
+  return dispatch_prod(h, c, stream);
+}
+
+ocp_status ocp_eval_all(ocp_t* h, const double* x, const double* y, double sigma, double* f, double* cv, double* g,
+                        double* jvals, double* hvals, void* stream) {
+  if (!h) return OCP_EINVAL;
+  NEED(x);
+  OPT(f); OPT(cv); OPT(g); OPT(jvals); OPT(hvals);
+  if (hvals) NEED(y);
+  unsigned out = (f ? O_F : 0u) | (cv ? O_C : 0u) | (g ? O_G : 0u) | (jvals ? O_J : 0u) | (hvals ? O_H : 0u);
+  if (!out) return OCP_OK;
+  EvalCall c = full_call(h);
+  c.x = x; c.y = y; c.sigma = sigma; c.f = f; c.c = cv; c.g = g; c.jv = jvals; c.hv = hvals;
+  // subsets without a dedicated kernel run the full kernel, which skips the NULL outputs
+  return dispatch_eval(h, out, c, stream);
+}
+
+ocp_status ocp_eval_all_range(ocp_t* h, int64_t node_begin, int64_t node_end, const double* x, const double* y,
+                              double sigma, double* f, double* cv, double* g, double* jvals, double* hvals,
+                              void* stream) {
+  if (!h) return OCP_EINVAL;
+  if (node_begin < 0 || node_end > h->N + 1 || node_begin >= node_end)
+    return set_err(h, OCP_EDIM, "node range outside [0, N+1) or empty");
+  NEED(x); NEED(y); NEED(f); NEED(cv); NEED(g); NEED(jvals); NEED(hvals);
+  EvalCall c;
+  c.B = node_begin; c.E = node_end; c.range = true;
+  c.x = x; c.y = y; c.sigma = sigma; c.f = f; c.c = cv; c.g = g; c.jv = jvals; c.hv = hvals;
+  return dispatch_eval(h, O_ALL, c, stream);
+}
+
+ocp_status ocp_vjp_param(ocp_t* h, const double* x, const double* w, double* Jtw, double* dmu, void* stream) {
+  if (!h) return OCP_EINVAL;
+  if (h->model != OCP_MODEL_VDP) return set_err(h, OCP_EMODEL, "parameter derivative is provided for the Van der Pol model");
+  NEED(x); NEED(w); NEED(dmu); NEED(Jtw);
+  ProdCall c;
+  c.kind = P_JTPROD; c.x = x; c.v = w; c.out = Jtw; c.dmu = dmu;
+  return dispatch_prod(h, c, stream);
+}
+
+ocp_status ocp_set_param0(ocp_t* h, double value) {
+  if (!h) return OCP_EINVAL;
+  if (model_nparams(h->model) < 1) return set_err(h, OCP_EMODEL, "model has no parameters");
+  if (h->model == OCP_MODEL_HEAT1D) return set_err(h, OCP_EMODEL, "the heat cell count is structural");
+  h->params[0] = value;
+  return OCP_OK;
+}
+
+const char* ocp_last_error(const ocp_t* h) { return h ? h->err.c_str() : g_create_err.c_str(); }
+
+}  // extern "C"

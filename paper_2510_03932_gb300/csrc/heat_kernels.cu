@@ -1,0 +1,433 @@
+// FP64 kernels for the heat-equation model (method of lines, n cells, one control):
+//   f_k = (x_{k-1} - 2 x_k + x_{k+1}) / dx^2 - x_k^3,  ghost x_{-1} = u (Dirichlet control),
+//   ghost x_n = x_{n-1} (homogeneous Neumann);  0-based cells k = 0..n-1.
+// Per-cell derivatives (all other entries are the constant 1/dx^2 of the Laplacian):
+//   df_k/dx_k = -2/dx^2 - 3 x_k^2   (k < n-1),   -1/dx^2 - 3 x_k^2   (k = n-1)
+//   d2 f_k/dx_k^2 = -6 x_k.
+// Row template of component k (the defect of cell k): X cells {k-1, k, k+1} within 0..n-1 on
+// each side, plus the control for k = 0, so 6 entries per row except the last cell's 4.
+//
+// Work decomposition: a CTA covers 32 consecutive nodes (one per lane); its 8 warps take the
+// cells in groups of 8.  Row-coupled outputs (defects, Jacobian rows) use tiles that overlap
+// by one node (the CTA owns 31 of its 32 nodes); node-local products use disjoint tiles.
+// The states of the tile's nodes are staged in shared memory with a padded row (n+1 doubles)
+// so that lanes reading different nodes hit different banks; node-major outputs (Hessian
+// diagonal, gradient, J^T w, H v) are staged the same way and stored with consecutive
+// threads on consecutive addresses.  Component-major outputs (defects, Jacobian rows, Jv)
+// are consecutive across lanes and are stored directly or through a per-warp row buffer.
+#include <cstring>
+
+#include "node_kernels.cuh"
+#include "ocp_internal.h"
+
+namespace ocpg {
+
+constexpr int HEAT_MAXC = 128;
+constexpr int HT_LANES = 32;
+constexpr int HT_WARPS = 8;
+constexpr int HT_THREADS = HT_LANES * HT_WARPS;
+
+struct HeatArgs {
+  const double* __restrict__ x;
+  const double* __restrict__ y;
+  const double* __restrict__ v;
+  double *f, *c, *g, *jv, *hv, *out;
+  double* partials;
+  unsigned* counter;
+  int64_t N, nb, B, E, ntiles, uoff;
+  int n, has_final, has_ref, hu;
+  double hh, mhh, mhidx2;   // hh, -hh, -hh/dx^2
+  double d_in, d_last;      // hh * 2/dx^2, hh * 1/dx^2  (diagonal constant of -hh df_k/dx_k)
+  double h3, h6, hidx2;     // 3 hh, 6 hh, hh/dx^2
+  double cq_in[HEAT_MAXC + 1], cq_end[HEAT_MAXC + 1];
+  double gq_in[HEAT_MAXC + 1], gq_end[HEAT_MAXC + 1];
+  double ref[HEAT_MAXC + 1];
+};
+
+__device__ __forceinline__ int64_t heat_jbase(const HeatArgs& a, int k) { return a.nb + (int64_t)6 * k * a.N; }
+
+// Stage the states (and controls) of nodes [r0, r0+nn) into sX[t*(n+1) + k], sX[t*(n+1) + n] = u.
+__device__ __forceinline__ void heat_stage(const HeatArgs& a, const double* __restrict__ src, int64_t r0, int nn,
+                                           double* sX) {
+  const int n = a.n, ld = n + 1;
+  const int total = nn * n;
+  const double* base = src + (int64_t)n * r0;
+  for (int i = threadIdx.x; i < total; i += HT_THREADS) {
+    const int t = i / n, k = i - t * n;
+    sX[t * ld + k] = __ldg(base + i);
+  }
+  for (int t = threadIdx.x; t < nn; t += HT_THREADS) sX[t * ld + n] = __ldg(src + a.uoff + r0 + t);
+}
+
+// ======================================================================================
+// Fused evaluation
+// ======================================================================================
+template <unsigned OUT>
+__global__ void __launch_bounds__(HT_THREADS) k_heat_eval(const __grid_constant__ HeatArgs a) {
+  constexpr bool CF = OUT & O_F, CC = OUT & O_C, CG = OUT & O_G, CJ = OUT & O_J, CH = OUT & O_H;
+  // the full kernel also serves output subsets: NULL outputs are skipped
+  const bool WF = CF && a.f, WC = CC && a.c, WG = CG && a.g, WJ = CJ && a.jv, WH = CH && a.hv;
+  extern __shared__ __align__(16) double sm[];
+  const int n = a.n, ld = n + 1;
+  double* sX = sm;                                   // 32 * ld
+  double* sN = sX + HT_LANES * ld;                   // node-major Hessian staging, 31 * ld
+  double* sG = sN + (HT_LANES - 1) * ld;             // node-major gradient staging, 31 * ld
+  double* sJ = sG + (HT_LANES - 1) * ld;             // per-warp row buffer 8 * 31 * 6
+  double* red = sJ + HT_WARPS * (HT_LANES - 1) * 6;  // reduction
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double objacc = 0.0;
+
+  for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+    const int64_t r0 = a.B + tile * (HT_LANES - 1);
+    const int64_t own_end = min(r0 + HT_LANES - 1, a.E);
+    const int64_t row_end = min(own_end, a.N);
+    const int64_t eval_end = row_end + 1;
+    const int nn = (int)(eval_end - r0);
+    const int nown = (int)(own_end - r0);
+    const int nrows = (int)max(row_end - r0, (int64_t)0);
+    const int t = lane;
+    const int64_t j = r0 + t;
+    const bool act = t < nn;
+    const bool own = t < nown;
+    const bool endp = (j == 0) || (j == a.N);
+    heat_stage(a, a.x, r0, nn, sX);
+    __syncthreads();
+
+    // ---- control entries (warp 0): gradient, objective, Hessian (u,u)
+    if (warp == 0 && own) {
+      const double u = sX[t * ld + n];
+      if (WG || WF) {
+        const double d = a.has_ref ? u - a.ref[n] : u;
+        const double gu = (endp ? a.gq_end[n] : a.gq_in[n]) * d;
+        if (WG) a.g[a.uoff + j] = gu;
+        if (WF) objacc = fma(gu, d, objacc);
+      }
+      if (WH && a.hu) a.hv[(int64_t)n * (a.N + 1) + j] = endp ? a.cq_end[n] : a.cq_in[n];
+    }
+
+    const int ngroups = (n + 7) / 8;
+    double* sJw = sJ + warp * (HT_LANES - 1) * 6;
+    for (int gi = warp; gi < ngroups; gi += HT_WARPS) {
+      const int k0 = gi * 8, k1 = min(k0 + 8, n);
+      for (int k = k0; k < k1; ++k) {
+        double xk = 0.0, xl = 0.0, xr = 0.0;
+        if (act) {
+          xk = sX[t * ld + k];
+          xl = (k == 0) ? sX[t * ld + n] : sX[t * ld + k - 1];
+          xr = (k == n - 1) ? xk : sX[t * ld + k + 1];
+        }
+        const double x2 = xk * xk;
+        // -hh df_k/dx_k = hh (2/dx^2 + 3 x^2)  (or 1/dx^2 at the Neumann end)
+        const bool last = (k == n - 1);
+        if (WJ) {
+          const double dk = fma(a.h3, x2, last ? a.d_last : a.d_in);
+          const int cnt = last ? 4 : 6;
+          const int rx = (k == 0 || last) ? 2 : 3;
+          const int ru = (k == 0) ? 1 : 0;
+          const int kd = (k == 0) ? 0 : 1;  // position of cell k among the row's X cells
+          if (act && t < nrows) {
+            double* rp = sJw + t * cnt;
+            for (int e = 0; e < rx; ++e) rp[e] = (e == kd) ? dk - 1.0 : a.mhidx2;
+            if (ru) rp[2 * rx] = a.mhidx2;
+          }
+          if (act && t >= 1 && t - 1 < nrows) {
+            double* rp = sJw + (t - 1) * cnt;
+            for (int e = 0; e < rx; ++e) rp[rx + e] = (e == kd) ? dk + 1.0 : a.mhidx2;
+            if (ru) rp[2 * rx + 1] = a.mhidx2;
+          }
+          __syncwarp();
+          double* dst = a.jv + heat_jbase(a, k) + r0 * cnt;
+          const int total = nrows * cnt;
+          for (int i = lane; i < total; i += 32) dst[i] = sJw[i];
+          __syncwarp();
+        }
+        if (WJ && own) {  // boundary rows X_{0,k} (and X_{N,k}): one constant entry each
+          if (j == 0) a.jv[k] = 1.0;
+          if (a.has_final && j == a.N) a.jv[n + k] = 1.0;
+        }
+        if (WC) {
+          // hh f_k = hh (lap / dx^2 - x^3)
+          // pa = x + hh f, pb = x - hh f, with hh f = hh/dx^2 lap - hh x^3
+          const double lap = last ? (xl - xk) : fma(-2.0, xk, xl + xr);
+          const double x3 = x2 * xk;
+          const double pa = fma(a.hidx2, lap, fma(a.mhh, x3, xk));
+          const double pb = fma(-a.hidx2, lap, fma(a.hh, x3, xk));
+          const double nb = __shfl_down_sync(0xffffffffu, pb, 1);
+          if (t < nrows) a.c[a.nb + (int64_t)k * a.N + j] = nb - pa;
+          if (own && j == 0) a.c[k] = xk;
+          if (own && a.has_final && j == a.N) a.c[n + k] = xk;
+        }
+        if (own) {
+          if (WH) {
+            const double yl = (j >= 1) ? __ldg(a.y + a.nb + (int64_t)k * a.N + j - 1) : 0.0;
+            const double yr = (j < a.N) ? __ldg(a.y + a.nb + (int64_t)k * a.N + j) : 0.0;
+            const double ty = a.h6 * (yl + yr);
+            sN[t * ld + k] = fma(ty, xk, endp ? a.cq_end[k] : a.cq_in[k]);
+          }
+          if (WG || WF) {
+            const double d = a.has_ref ? xk - a.ref[k] : xk;
+            const double gk = (endp ? a.gq_end[k] : a.gq_in[k]) * d;
+            if (WF) objacc = fma(gk, d, objacc);
+            if (WG) sG[t * ld + k] = gk;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    if (WH) {
+      const int total = nown * n;
+      double* dst = a.hv + (int64_t)n * r0;
+      for (int i = threadIdx.x; i < total; i += HT_THREADS) {
+        const int tt = i / n, k = i - tt * n;
+        dst[i] = sN[tt * ld + k];
+      }
+    }
+    if (WG) {
+      const int total = nown * n;
+      double* dst = a.g + (int64_t)n * r0;
+      for (int i = threadIdx.x; i < total; i += HT_THREADS) {
+        const int tt = i / n, k = i - tt * n;
+        dst[i] = sG[tt * ld + k];
+      }
+    }
+    if (WF) {
+      const double ts = cta_sum<HT_THREADS>(objacc, red);
+      if (threadIdx.x == 0) a.partials[tile] = ts;
+      objacc = 0.0;
+    }
+    __syncthreads();
+  }
+  if (WF) finish_tiles<HT_THREADS>(a.partials, a.ntiles, a.counter, a.f, 0.5, red);
+}
+
+// ======================================================================================
+// Jv:  p_k(j) = -hh grad f_k(z_j) . v_{z_j};  row (k,j) = (p_k(j) - v_{X_j,k}) + (p_k(j+1) + v_{X_{j+1},k})
+// ======================================================================================
+__global__ void __launch_bounds__(HT_THREADS) k_heat_jprod(const __grid_constant__ HeatArgs a) {
+  extern __shared__ __align__(16) double sm[];
+  const int n = a.n, ld = n + 1;
+  double* sX = sm;
+  double* sV = sX + HT_LANES * ld;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+    const int64_t r0 = tile * (HT_LANES - 1);
+    const int64_t own_end = min(r0 + HT_LANES - 1, a.N + 1);
+    const int64_t row_end = min(own_end, a.N);
+    const int nn = (int)(row_end + 1 - r0);
+    const int nrows = (int)max(row_end - r0, (int64_t)0);
+    const int t = lane;
+    const int64_t j = r0 + t;
+    const bool act = t < nn;
+    heat_stage(a, a.x, r0, nn, sX);
+    heat_stage(a, a.v, r0, nn, sV);
+    __syncthreads();
+    const int ngroups = (n + 7) / 8;
+    for (int gi = warp; gi < ngroups; gi += HT_WARPS) {
+      const int k0 = gi * 8, k1 = min(k0 + 8, n);
+      for (int k = k0; k < k1; ++k) {
+        double p = 0.0, vk = 0.0;
+        if (act) {
+          const double xk = sX[t * ld + k];
+          const bool last = (k == n - 1);
+          vk = sV[t * ld + k];
+          const double vl = (k == 0) ? sV[t * ld + n] : sV[t * ld + k - 1];
+          const double dk = fma(a.h3, xk * xk, last ? a.d_last : a.d_in);
+          const double nsum = last ? vl : vl + sV[t * ld + k + 1];
+          p = fma(a.mhidx2, nsum, dk * vk);
+        }
+        const double right = __shfl_down_sync(0xffffffffu, p + vk, 1);
+        if (t < nrows) a.out[a.nb + (int64_t)k * a.N + j] = (p - vk) + right;
+        if (act && j == 0) a.out[k] = vk;
+        if (act && a.has_final && j == a.N && t < (int)(own_end - r0)) a.out[n + k] = vk;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ======================================================================================
+// J^T w (node-local):  out_a = (w_{a,j-1} - w_{a,j}) + wbar_a dd_a - hh/dx^2 (wbar_{a-1} + wbar_{a+1})
+//                      out_u = -hh/dx^2 wbar_0       (dd_a = -hh df_a/dx_a)
+// H v (node-local):    out_a = (2 sigma w q_a + 6 hh ybar_a x_a) v_a,  out_u = 2 sigma w r v_u
+// ======================================================================================
+template <bool JT>
+__global__ void __launch_bounds__(HT_THREADS) k_heat_local(const __grid_constant__ HeatArgs a) {
+  extern __shared__ __align__(16) double sm[];
+  const int n = a.n, ld = n + 1;
+  double* sX = sm;
+  double* sV = sX + HT_LANES * ld;  // H v: the direction; J^T w: the output staging
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+    const int64_t r0 = tile * HT_LANES;
+    const int nn = (int)min((int64_t)HT_LANES, a.N + 1 - r0);
+    const int t = lane;
+    const int64_t j = r0 + t;
+    const bool act = t < nn;
+    const bool endp = (j == 0) || (j == a.N);
+    heat_stage(a, a.x, r0, nn, sX);
+    if (!JT) heat_stage(a, a.v, r0, nn, sV);
+    __syncthreads();
+    const int ngroups = (n + 7) / 8;
+    for (int gi = warp; gi < ngroups; gi += HT_WARPS) {
+      const int k0 = gi * 8, k1 = min(k0 + 8, n);
+      if (JT) {
+        // wbar of cells k0-1 .. k1 (clamped), rolling window
+        auto wbar = [&](int k, double& wl, double& wr) {
+          const double* row = a.v + a.nb + (int64_t)k * a.N;
+          wl = (j >= 1) ? __ldg(row + j - 1) : 0.0;
+          wr = (j < a.N) ? __ldg(row + j) : 0.0;
+        };
+        double wl, wr, wbm = 0.0, wbc, wbp = 0.0, wlc, wrc;
+        if (act) {
+          if (k0 > 0) { double l2, r2; wbar(k0 - 1, l2, r2); wbm = l2 + r2; }
+          wbar(k0, wlc, wrc);
+          wbc = wlc + wrc;
+        }
+        for (int k = k0; k < k1; ++k) {
+          if (act) {
+            double wlp = 0.0, wrp = 0.0;
+            if (k + 1 < n) { wbar(k + 1, wlp, wrp); wbp = wlp + wrp; } else wbp = 0.0;
+            const double xk = sX[t * ld + k];
+            const bool last = (k == n - 1);
+            const double dk = fma(a.h3, xk * xk, last ? a.d_last : a.d_in);
+            double s = fma(wbc, dk, wlc - wrc);
+            s = fma(a.mhidx2, wbm + wbp, s);
+            if (j == 0) s += __ldg(a.v + k);
+            if (a.has_final && j == a.N) s += __ldg(a.v + n + k);
+            sV[t * ld + k] = s;
+            if (k == 0) sV[t * ld + n] = a.mhidx2 * wbc;
+            wbm = wbc; wbc = wbp; wlc = wlp; wrc = wrp;
+          }
+        }
+      } else {
+        for (int k = k0; k < k1; ++k) {
+          if (act) {
+            const double xk = sX[t * ld + k];
+            const double yl = (j >= 1) ? __ldg(a.y + a.nb + (int64_t)k * a.N + j - 1) : 0.0;
+            const double yr = (j < a.N) ? __ldg(a.y + a.nb + (int64_t)k * a.N + j) : 0.0;
+            const double hk = fma(a.h6 * (yl + yr), xk, endp ? a.cq_end[k] : a.cq_in[k]);
+            sX[t * ld + k] = hk * sV[t * ld + k];  // in place: x no longer needed for cell k
+          }
+        }
+      }
+    }
+    if (!JT && warp == 0 && act) {
+      const double cu = a.hu ? (endp ? a.cq_end[n] : a.cq_in[n]) : 0.0;
+      sX[t * ld + n] = cu * sV[t * ld + n];
+    }
+    __syncthreads();
+    const double* res = JT ? sV : sX;
+    {
+      const int total = nn * n;
+      double* dst = a.out + (int64_t)n * r0;
+      for (int i = threadIdx.x; i < total; i += HT_THREADS) {
+        const int tt = i / n, k = i - tt * n;
+        dst[i] = res[tt * ld + k];
+      }
+      for (int tt = threadIdx.x; tt < nn; tt += HT_THREADS) a.out[a.uoff + r0 + tt] = res[tt * ld + n];
+    }
+    __syncthreads();
+  }
+}
+
+// ======================================================================================
+// Host side
+// ======================================================================================
+static void heat_fill(const ocp* h, double sigma, HeatArgs& a) {
+  memset(&a, 0, sizeof(a));
+  const int n = h->nx;
+  const double idx2 = (double)n * (double)n;  // 1/dx^2 with dx = 1/n
+  a.N = h->N;
+  a.nb = h->pat.nb;
+  a.uoff = (int64_t)n * (h->N + 1);
+  a.n = n;
+  a.has_final = h->has_final;
+  a.has_ref = h->has_ref;
+  a.hu = h->pat.hu;
+  a.hh = h->hh;
+  a.mhh = -h->hh;
+  a.mhidx2 = -h->hh * idx2;
+  a.hidx2 = h->hh * idx2;
+  a.d_in = h->hh * (2.0 * idx2);
+  a.d_last = h->hh * idx2;
+  a.h3 = 3.0 * h->hh;
+  a.h6 = 6.0 * h->hh;
+  for (int v = 0; v <= n; ++v) {
+    const double w = v < n ? h->q[v] : h->r[0];
+    a.gq_in[v] = 2.0 * h->h * w;
+    a.gq_end[v] = h->h * w;
+    a.cq_in[v] = sigma * (2.0 * h->h * w);
+    a.cq_end[v] = sigma * (h->h * w);
+    a.ref[v] = v < n ? h->xref[v] : h->uref[0];
+  }
+  a.partials = h->d_partials;
+  a.counter = h->d_counter;
+}
+
+template <unsigned OUT>
+static ocp_status heat_eval_t(ocp* h, const EvalCall& c, cudaStream_t s) {
+  HeatArgs a;
+  heat_fill(h, c.sigma, a);
+  a.x = c.x; a.y = c.y; a.f = c.f; a.c = c.c; a.g = c.g; a.jv = c.jv; a.hv = c.hv;
+  a.B = c.B; a.E = c.E;
+  const int64_t nodes = c.E - c.B;
+  a.ntiles = (nodes + (HT_LANES - 2)) / (HT_LANES - 1);
+  if (a.ntiles < 1) a.ntiles = 1;
+  const int ld = h->nx + 1;
+  const size_t smem = sizeof(double) * ((size_t)HT_LANES * ld + 2 * (HT_LANES - 1) * ld +
+                                        HT_WARPS * (HT_LANES - 1) * 6 + HT_WARPS + 1);
+  auto kern = k_heat_eval<OUT>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_err(h, e, "cudaFuncSetAttribute(heat)");
+  const int grid = occupancy_grid(h, (const void*)kern, HT_THREADS, smem, a.ntiles);
+  if (grid <= 0) return set_err(h, OCP_ECUDA, "occupancy query failed");
+  kern<<<grid, HT_THREADS, smem, s>>>(a);
+  return cuda_err(h, cudaGetLastError(), "k_heat_eval launch");
+}
+
+ocp_status heat_eval(ocp* h, unsigned out, const EvalCall& c, cudaStream_t s) {
+  switch (out) {
+    case O_F: return heat_eval_t<O_F>(h, c, s);
+    case O_C: return heat_eval_t<O_C>(h, c, s);
+    case O_G: return heat_eval_t<O_G>(h, c, s);
+    case O_J: return heat_eval_t<O_J>(h, c, s);
+    case O_H: return heat_eval_t<O_H>(h, c, s);
+    case O_J | O_H: return heat_eval_t<O_J | O_H>(h, c, s);
+    default: return heat_eval_t<O_ALL>(h, c, s);
+  }
+}
+
+ocp_status heat_prod(ocp* h, const ProdCall& c, cudaStream_t s) {
+  HeatArgs a;
+  heat_fill(h, c.sigma, a);
+  a.x = c.x; a.y = c.y; a.v = c.v; a.out = c.out;
+  const int ld = h->nx + 1;
+  const size_t smem = sizeof(double) * (size_t)HT_LANES * ld * 2;
+  cudaError_t e;
+  if (c.kind == P_JPROD) {
+    a.ntiles = (h->N + 1 + (HT_LANES - 2)) / (HT_LANES - 1);
+    auto k = k_heat_jprod;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_err(h, e, "cudaFuncSetAttribute(heat jprod)");
+    const int grid = occupancy_grid(h, (const void*)k, HT_THREADS, smem, a.ntiles);
+    k<<<grid, HT_THREADS, smem, s>>>(a);
+  } else {
+    a.ntiles = (h->N + 1 + HT_LANES - 1) / HT_LANES;
+    if (c.kind == P_JTPROD) {
+      auto k = k_heat_local<true>;
+      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return cuda_err(h, e, "cudaFuncSetAttribute(heat jtprod)");
+      const int grid = occupancy_grid(h, (const void*)k, HT_THREADS, smem, a.ntiles);
+      k<<<grid, HT_THREADS, smem, s>>>(a);
+    } else {
+      auto k = k_heat_local<false>;
+      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return cuda_err(h, e, "cudaFuncSetAttribute(heat hprod)");
+      const int grid = occupancy_grid(h, (const void*)k, HT_THREADS, smem, a.ntiles);
+      k<<<grid, HT_THREADS, smem, s>>>(a);
+    }
+  }
+  return cuda_err(h, cudaGetLastError(), "heat product launch");
+}
+
+}  // namespace ocpg

@@ -1,0 +1,683 @@
+// Fused FP64 evaluation kernels for models with a few states per node (one thread per node).
+//
+// Work decomposition.  A CTA of TILE threads evaluates TILE consecutive nodes r0..r0+TILE-1
+// and OWNS the first TILE-1 of them: it writes their Hessian blocks, gradient entries and
+// objective terms, and it writes the complete defect rows (k, j) for j = r0..r0+TILE-2
+// (row (k, j) couples nodes j and j+1, paper Sec. 5 defect generator).  Consecutive tiles
+// overlap by one node, so every slot is written exactly once by one thread, without atomics,
+// at the cost of evaluating 1/TILE of the nodes twice.  CTAs are persistent and walk the
+// tiles in a fixed round-robin order.
+//
+// Data movement.  Each thread loads its node z_j = (X_j, U_j) and, for the Hessian, the
+// multiplier sums ybar_{j,k} = y_{k,j-1} + y_{k,j} (component-major, coalesced).  The
+// tile's Jacobian rows, Hessian blocks and gradient entries are staged in shared memory in
+// their final COO order and written out with consecutive threads on consecutive addresses;
+// defect rows are already consecutive in j and are stored directly.
+//
+// Objective.  Each thread accumulates 2 w_j f0(z_j) = sum_a g_a d_a (g the gradient entry,
+// d = z - ref) over its nodes; a fixed-shape tree reduces it per CTA, and the last CTA to
+// finish (completion ticket) sums the per-CTA partials in index order.  The result is
+// therefore deterministic for a given grid.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "models.cuh"
+#include "ocp_internal.h"
+
+namespace ocpg {
+
+// Max-template of the node Hessian block: every dynamics pair plus every diagonal entry
+// (the cost f0 is a diagonal quadratic), in canonical (a, b) order.  The host decides
+// which diagonal entries are structural (cost weight != 0) and passes their positions.
+template <class M>
+struct HTmpl {
+  static constexpr int CAP = M::NZ * (M::NZ + 1) / 2;
+  int n = 0, nxblk = 0;
+  int a[CAP] = {}, b[CAP] = {}, dyn[CAP] = {};
+  bool diag[CAP] = {};
+  constexpr HTmpl() {
+    for (int aa = 0; aa < M::NZ; ++aa)
+      for (int bb = 0; bb <= aa; ++bb) {
+        int d = -1;
+        for (int e = 0; e < M::NHD; ++e)
+          if (M::HA(e) == aa && M::HB(e) == bb) d = e;
+        if (d >= 0 || aa == bb) {
+          a[n] = aa; b[n] = bb; dyn[n] = d; diag[n] = (aa == bb);
+          if (aa < M::NX) ++nxblk;
+          ++n;
+        }
+      }
+  }
+};
+
+template <class M>
+struct NodeArgs {
+  const double* __restrict__ x;
+  const double* __restrict__ y;
+  const double* __restrict__ v;   // products: direction
+  double* f;
+  double* c;
+  double* g;
+  double* jv;
+  double* hv;
+  double* out;                    // products: result
+  double* partials;
+  unsigned* counter;
+  double* dmu;                    // jtprod with the parameter derivative
+  const double* pdir_dev;         // jprod: parameter direction (device scalar) or null
+  const double* mixw;             // hprod: multipliers of the mixed parameter term or null
+  const double* mixs;             // hprod: scale of the mixed term (device scalar)
+  double pdir;                    // jprod: parameter direction (host scalar)
+  const double* p0_dev;           // model parameter 0 read from the device (or null: K as given)
+  int64_t N, nb, B, E, ntiles, uoff;  // uoff = nx (N+1): first U entry of x
+  int has_final, has_ref, range;
+  ModelConst K;
+  double cq_in[M::NZ], cq_end[M::NZ];  // 2 sigma w q on the diagonal (interior / end node)
+  double gq_in[M::NZ], gq_end[M::NZ];  // 2 w q  (gradient)
+  double ref[M::NZ];
+  int64_t jbase[M::NX];
+  int64_t hbase_u;
+  int hx, hu;
+  int8_t hpos[HTmpl<M>::CAP];
+};
+
+template <class M>
+__host__ __device__ constexpr int row_count(int k) { return 2 * (M::RX(k) + M::RU(k)); }
+template <class M>
+__host__ __device__ constexpr int jrow_total() {
+  int s = 0;
+  for (int k = 0; k < M::NX; ++k) s += row_count<M>(k);
+  return s;
+}
+template <class M>
+__host__ __device__ constexpr int jrow_off(int k) {
+  int s = 0;
+  for (int q = 0; q < k; ++q) s += row_count<M>(q);
+  return s;
+}
+
+template <class M, int TILE, unsigned OUT>
+struct EvalSmem {
+  static constexpr int R = TILE - 1;
+  static constexpr int J = (OUT & O_J) ? jrow_total<M>() * R : 0;
+  static constexpr int oJ = 0, oRED = oJ + J;
+  static constexpr int total = oRED + TILE / 32 + 1;
+  static constexpr size_t bytes = sizeof(double) * total;
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Fixed-order CTA sum; result valid in thread 0.  `red` holds TILE/32 doubles.
+template <int TILE>
+__device__ __forceinline__ double cta_sum(double v, double* red) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int i = 0; i < TILE / 32; ++i) s += red[i];
+  }
+  return s;
+}
+
+// Completion of a reduction over tiles: every tile t stored its fixed-order CTA sum in
+// partials[t]; the last CTA to finish (completion ticket) adds partials[0..ntiles) in a
+// fixed order (strided per thread, then a fixed tree) and writes scale * sum to *dst.
+// The result depends only on the tile size, not on the grid or the kernel variant.
+template <int TILE>
+__device__ __forceinline__ void finish_tiles(const double* partials, int64_t ntiles, unsigned* counter, double* dst,
+                                             double scale, double* red) {
+  __shared__ int s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned ticket = atomicAdd(counter, 1u);
+    s_last = (ticket == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < ntiles; i += TILE) s += __ldcg(partials + i);
+  s = cta_sum<TILE>(s, red);
+  if (threadIdx.x == 0) {
+    *dst = scale * s;
+    *counter = 0u;
+  }
+}
+
+template <class M>
+__device__ __forceinline__ void load_node(const NodeArgs<M>& a, int64_t j, double (&z)[M::NZ]) {
+#pragma unroll
+  for (int k = 0; k < M::NX; ++k) z[k] = __ldg(a.x + M::NX * j + k);
+#pragma unroll
+  for (int i = 0; i < M::NU; ++i) z[M::NX + i] = __ldg(a.x + a.uoff + M::NU * j + i);
+}
+
+// ybar_k = w_{k,j-1} + w_{k,j} over the defect rows of component k (zero outside 0..N-1)
+template <class M>
+__device__ __forceinline__ void load_bar(const NodeArgs<M>& a, const double* w, int64_t j, double (&wb)[M::NX],
+                                         double (&wl)[M::NX], double (&wr)[M::NX]) {
+#pragma unroll
+  for (int k = 0; k < M::NX; ++k) {
+    const double* row = w + a.nb + (int64_t)k * a.N;
+    wl[k] = (j >= 1) ? __ldg(row + j - 1) : 0.0;
+    wr[k] = (j < a.N) ? __ldg(row + j) : 0.0;
+    wb[k] = wl[k] + wr[k];
+  }
+}
+
+// ======================================================================================
+// Fused evaluation: objective, constraints, gradient, Jacobian values, Hessian values.
+// ======================================================================================
+template <class M>
+__device__ __forceinline__ void node_cq(const NodeArgs<M>& a, bool endp, double (&cqd)[M::NZ]) {
+#pragma unroll
+  for (int v = 0; v < M::NZ; ++v) cqd[v] = endp ? a.cq_end[v] : a.cq_in[v];
+}
+
+template <class M>
+__device__ __forceinline__ void load_ybar(const NodeArgs<M>& a, const double* w, int64_t j, double (&wb)[M::NX]) {
+#pragma unroll
+  for (int k = 0; k < M::NX; ++k) {
+    if (M::HK(k)) {
+      const double* row = w + a.nb + (int64_t)k * a.N;
+      const double wl = (j >= 1) ? __ldg(row + j - 1) : 0.0;
+      const double wr = (j < a.N) ? __ldg(row + j) : 0.0;
+      wb[k] = wl + wr;
+    } else {
+      wb[k] = 0.0;
+    }
+  }
+}
+
+// gradient entries g_v = 2 w_j q_v (z_v - ref_v); returns 2 w_j f0(z_j) = sum_v g_v (z_v - ref_v)
+template <class M, bool REF, bool WG>
+__device__ __forceinline__ double node_grad(const NodeArgs<M>& a, const double (&z)[M::NZ], bool endp, int64_t j) {
+  double s = 0.0;
+#pragma unroll
+  for (int v = 0; v < M::NZ; ++v) {
+    const double d = REF ? z[v] - a.ref[v] : z[v];
+    const double gv = (endp ? a.gq_end[v] : a.gq_in[v]) * d;
+    if (WG) {
+      if (v < M::NX) a.g[(int64_t)M::NX * j + v] = gv;
+      else a.g[a.uoff + (int64_t)M::NU * j + (v - M::NX)] = gv;
+    }
+    s = (v == 0) ? gv * d : fma(gv, d, s);
+  }
+  return s;
+}
+
+template <class M, int TILE, unsigned OUT>
+__global__ void __launch_bounds__(TILE) k_node_eval(const __grid_constant__ NodeArgs<M> a) {
+  constexpr int NX = M::NX, NZ = M::NZ;
+  constexpr bool WF = OUT & O_F, WC = OUT & O_C, WG = OUT & O_G, WJ = OUT & O_J, WH = OUT & O_H;
+  // the full kernel also serves output subsets: NULL outputs are computed but not stored
+  const bool sF = WF && a.f, sC = WC && a.c, sG = WG && a.g, sJ = WJ && a.jv, sH = WH && a.hv;
+  using S = EvalSmem<M, TILE, OUT>;
+  constexpr HTmpl<M> HT{};
+  constexpr int NHD = (M::NHD > 0) ? M::NHD : 1;
+  extern __shared__ __align__(16) double sm[];
+  __shared__ double sEdge[(TILE / 32 + 1) * NX];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  ModelConst K = a.K;
+  if (a.p0_dev) M::device_param(K, __ldg(a.p0_dev));
+
+  for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+    const int64_t r0 = a.B + tile * (TILE - 1);
+    const int64_t own_end = min(r0 + TILE - 1, a.E);
+    const int64_t row_end = min(own_end, a.N);
+    const int64_t eval_end = row_end + 1;
+    const int nown = (int)(own_end - r0);
+    const int nrows = (int)max(row_end - r0, (int64_t)0);
+    const int64_t j = r0 + t;
+    const bool act = j < eval_end;
+    const bool own = t < nown;
+    const bool endp = (j == 0) || (j == a.N);
+    double objterm = 0.0;
+
+    double z[NZ], yb[NX], cqd[NZ], pa[NX], pb[NX], mjx[NX][M::MAXRX], mju[NX][M::MAXRU], hd[NHD];
+#pragma unroll
+    for (int k = 0; k < NX; ++k) { pa[k] = 0.0; pb[k] = 0.0; }
+    if (act) {
+      load_node<M>(a, j, z);
+      if (WH) {
+        load_ybar<M>(a, a.y, j, yb);
+        node_cq<M>(a, endp, cqd);
+      }
+      M::template eval<WC, WJ, WH>(K, z, yb, cqd, pa, pb, mjx, mju, hd);
+    }
+    if (own) {
+      // ---- Hessian block of node j (stored directly; X block then U block)
+      if (sH) {
+#pragma unroll
+        for (int e = 0; e < HT.n; ++e) {
+          const int p = a.hpos[e];
+          if (p >= 0) {
+            const double val = (HT.dyn[e] >= 0) ? hd[HT.dyn[e] >= 0 ? HT.dyn[e] : 0] : cqd[HT.a[e]];
+            if (HT.a[e] < NX) a.hv[j * a.hx + p] = val;
+            else a.hv[a.hbase_u + j * a.hu + p] = val;
+          }
+        }
+      }
+      // ---- gradient and objective term
+      if (sG || sF) {
+        double s2;
+        if (a.has_ref) s2 = sG ? node_grad<M, true, true>(a, z, endp, j) : node_grad<M, true, false>(a, z, endp, j);
+        else s2 = sG ? node_grad<M, false, true>(a, z, endp, j) : node_grad<M, false, false>(a, z, endp, j);
+        objterm = s2;
+      }
+      // ---- boundary rows X_{0,k} (and X_{N,k}): constraint value and the constant Jacobian entry
+      if (j == 0) {
+#pragma unroll
+        for (int k = 0; k < NX; ++k) {
+          if (sC) a.c[k] = z[k];
+          if (sJ) a.jv[k] = 1.0;
+        }
+      }
+      if (a.has_final && j == a.N) {
+#pragma unroll
+        for (int k = 0; k < NX; ++k) {
+          if (sC) a.c[NX + k] = z[k];
+          if (sJ) a.jv[NX + k] = 1.0;
+        }
+      }
+    }
+    // ---- Jacobian rows staged in shared memory: left part of row t, right part of row t-1
+    if (WJ && act) {
+#pragma unroll
+      for (int k = 0; k < NX; ++k) {
+        const int cnt = row_count<M>(k);
+        double* sj = sm + S::oJ + jrow_off<M>(k) * S::R;
+        if (t < nrows) {
+          double* rp = sj + t * cnt;
+#pragma unroll
+          for (int e = 0; e < M::RX(k); ++e) rp[e] = (M::XV(k, e) == k) ? (mjx[k][e] - 1.0) : mjx[k][e];
+#pragma unroll
+          for (int e = 0; e < M::RU(k); ++e) rp[2 * M::RX(k) + e] = mju[k][e];
+        }
+        if (t >= 1 && t - 1 < nrows) {
+          double* rp = sj + (t - 1) * cnt;
+#pragma unroll
+          for (int e = 0; e < M::RX(k); ++e) rp[M::RX(k) + e] = (M::XV(k, e) == k) ? (mjx[k][e] + 1.0) : mjx[k][e];
+#pragma unroll
+          for (int e = 0; e < M::RU(k); ++e) rp[2 * M::RX(k) + M::RU(k) + e] = mju[k][e];
+        }
+      }
+    }
+    // ---- defects: the right node's x - hh f comes from lane+1 (or the next warp's lane 0)
+    double nbv[NX];
+    if (WC) {
+#pragma unroll
+      for (int k = 0; k < NX; ++k) {
+        nbv[k] = __shfl_down_sync(0xffffffffu, pb[k], 1);
+        if (lane == 0) sEdge[warp * NX + k] = pb[k];
+      }
+    }
+    if (WC || WJ) __syncthreads();
+    if (sC && t < nrows) {
+#pragma unroll
+      for (int k = 0; k < NX; ++k) {
+        const double right = (lane == 31) ? sEdge[(warp + 1) * NX + k] : nbv[k];
+        a.c[a.nb + (int64_t)k * a.N + j] = right - pa[k];
+      }
+    }
+    // ---- coalesced copy-out of the staged Jacobian rows
+    if (sJ) {
+#pragma unroll
+      for (int k = 0; k < NX; ++k) {
+        const int cnt = row_count<M>(k);
+        const double* src = sm + S::oJ + jrow_off<M>(k) * S::R;
+        double* dst = a.jv + a.jbase[k] + r0 * cnt;
+        const int total = nrows * cnt;
+        for (int i = t; i < total; i += TILE) dst[i] = src[i];
+      }
+    }
+    if (sF) {
+      const double ts = cta_sum<TILE>(objterm, sm + S::oRED);
+      if (t == 0) a.partials[tile] = ts;
+    }
+    if (WC || WJ || WF) __syncthreads();
+  }
+  if (sF) finish_tiles<TILE>(a.partials, a.ntiles, a.counter, a.f, 0.5, sm + S::oRED);
+}
+
+// ======================================================================================
+// Jv.  Row (k,j) = (p_k(j) - v_{X_j,k}) + (p_k(j+1) + v_{X_{j+1},k}),
+// p_k(j) = -hh grad f_k(z_j) . v_{z_j}  (+ -hh df_k/dmu(z_j) * pdir for the parameter).
+// Same overlapping tiles as the evaluation; the right-node term comes from lane+1.
+// ======================================================================================
+template <class M, int TILE, bool PDIR>
+__global__ void __launch_bounds__(TILE) k_node_jprod(const __grid_constant__ NodeArgs<M> a) {
+  constexpr int NX = M::NX, NZ = M::NZ;
+  constexpr int NHD = (M::NHD > 0) ? M::NHD : 1;
+  __shared__ double sEdge[(TILE / 32 + 1) * NX];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  ModelConst K = a.K;
+  if (a.p0_dev) M::device_param(K, __ldg(a.p0_dev));
+  double pd = 0.0;
+  if (PDIR) pd = a.pdir_dev ? __ldg(a.pdir_dev) : a.pdir;
+  for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+    const int64_t r0 = tile * (TILE - 1);
+    const int64_t own_end = min(r0 + TILE - 1, a.N + 1);
+    const int64_t row_end = min(own_end, a.N);
+    const int nrows = (int)max(row_end - r0, (int64_t)0);
+    const int64_t j = r0 + t;
+    const bool act = j <= row_end;
+    double p[NX], vx[NX], A[NX];
+#pragma unroll
+    for (int k = 0; k < NX; ++k) { p[k] = 0.0; vx[k] = 0.0; A[k] = 0.0; }
+    if (act) {
+      double z[NZ], vz[NZ], yb[NX], cqd[NZ], pa[NX], pb[NX], mjx[NX][M::MAXRX], mju[NX][M::MAXRU], hd[NHD];
+      load_node<M>(a, j, z);
+#pragma unroll
+      for (int k = 0; k < NX; ++k) { vz[k] = __ldg(a.v + NX * j + k); vx[k] = vz[k]; }
+#pragma unroll
+      for (int i = 0; i < M::NU; ++i) vz[NX + i] = __ldg(a.v + a.uoff + M::NU * j + i);
+      M::template eval<false, true, false>(K, z, yb, cqd, pa, pb, mjx, mju, hd);
+      double mdp[NX];
+      if (PDIR) M::dparam(K, z, mdp);
+#pragma unroll
+      for (int k = 0; k < NX; ++k) {
+        double s = 0.0;
+        bool first = true;
+#pragma unroll
+        for (int e = 0; e < M::RX(k); ++e) {
+          if (!M::JZ(k, e)) {
+            s = first ? mjx[k][e] * vz[M::XV(k, e)] : fma(mjx[k][e], vz[M::XV(k, e)], s);
+            first = false;
+          }
+        }
+#pragma unroll
+        for (int e = 0; e < M::RU(k); ++e) {
+          s = first ? mju[k][e] * vz[NX + M::UV(k, e)] : fma(mju[k][e], vz[NX + M::UV(k, e)], s);
+          first = false;
+        }
+        if (PDIR) s = fma(mdp[k], pd, s);
+        p[k] = s;
+        A[k] = s + vx[k];
+      }
+      if (j == 0) {
+#pragma unroll
+        for (int k = 0; k < NX; ++k) a.out[k] = vx[k];
+      }
+      if (a.has_final && j == a.N && t < (int)(own_end - r0)) {
+#pragma unroll
+        for (int k = 0; k < NX; ++k) a.out[NX + k] = vx[k];
+      }
+    }
+    double nbv[NX];
+#pragma unroll
+    for (int k = 0; k < NX; ++k) {
+      nbv[k] = __shfl_down_sync(0xffffffffu, A[k], 1);
+      if (lane == 0) sEdge[warp * NX + k] = A[k];
+    }
+    __syncthreads();
+    if (t < nrows) {
+#pragma unroll
+      for (int k = 0; k < NX; ++k) {
+        const double right = (lane == 31) ? sEdge[(warp + 1) * NX + k] : nbv[k];
+        a.out[a.nb + (int64_t)k * a.N + j] = (p[k] - vx[k]) + right;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ======================================================================================
+// J^T w, node-local:  (J^T w)_{X_j,a} = (w_{a,j-1} - w_{a,j}) + sum_k wbar_k mjx_k,a(z_j)
+//                     (+ w of the boundary rows at j = 0 / N);  (J^T w)_{U_j,i} likewise.
+// With DPAR, also (dc/dmu)^T w = sum_j sum_k wbar_k mdp_k(z_j) (deterministic reduction).
+// ======================================================================================
+template <class M, int TILE, bool DPAR>
+__global__ void __launch_bounds__(TILE) k_node_jtprod(const __grid_constant__ NodeArgs<M> a) {
+  constexpr int NX = M::NX, NZ = M::NZ;
+  constexpr int NHD = (M::NHD > 0) ? M::NHD : 1;
+  __shared__ double red[TILE / 32 + 1];
+  ModelConst K = a.K;
+  if (a.p0_dev) M::device_param(K, __ldg(a.p0_dev));
+  const int64_t nchunks = (a.N + TILE) / TILE;
+  for (int64_t chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
+    const int64_t j = chunk * TILE + threadIdx.x;
+    double acc_mu = 0.0;
+    if (j <= a.N) {
+      double z[NZ], yb[NX], cqd[NZ], pa[NX], pb[NX], mjx[NX][M::MAXRX], mju[NX][M::MAXRU], hd[NHD];
+      double wb[NX], wl[NX], wr[NX];
+      load_node<M>(a, j, z);
+      load_bar<M>(a, a.v, j, wb, wl, wr);
+      M::template eval<false, true, false>(K, z, yb, cqd, pa, pb, mjx, mju, hd);
+#pragma unroll
+      for (int v = 0; v < NX; ++v) {
+        double s = wl[v] - wr[v];
+#pragma unroll
+        for (int k = 0; k < NX; ++k)
+#pragma unroll
+          for (int e = 0; e < M::RX(k); ++e)
+            if (M::XV(k, e) == v && !M::JZ(k, e)) s = fma(wb[k], mjx[k][e], s);
+        if (j == 0) s += __ldg(a.v + v);
+        if (a.has_final && j == a.N) s += __ldg(a.v + NX + v);
+        a.out[NX * j + v] = s;
+      }
+#pragma unroll
+      for (int i = 0; i < M::NU; ++i) {
+        double s = 0.0;
+        bool first = true;
+#pragma unroll
+        for (int k = 0; k < NX; ++k)
+#pragma unroll
+          for (int e = 0; e < M::RU(k); ++e)
+            if (M::UV(k, e) == i) { s = first ? wb[k] * mju[k][e] : fma(wb[k], mju[k][e], s); first = false; }
+        a.out[a.uoff + M::NU * j + i] = s;
+      }
+      if (DPAR) {
+        double mdp[NX];
+        M::dparam(K, z, mdp);
+#pragma unroll
+        for (int k = 0; k < NX; ++k)
+          if (M::HAS_DPARAM) acc_mu = fma(wb[k], mdp[k], acc_mu);
+      }
+    }
+    if (DPAR) {
+      const double ts = cta_sum<TILE>(acc_mu, red);
+      if (threadIdx.x == 0) a.partials[chunk] = ts;
+    }
+  }
+  if (DPAR) finish_tiles<TILE>(a.partials, nchunks, a.counter, a.dmu, 1.0, red);
+}
+
+// ======================================================================================
+// H v, node-local: the full symmetric block of node j times v_{z_j}.
+// With MIX (autograd double backward), also adds mixs * m_j, m_j = sum_k mixwbar_k
+// (-hh d2 f_k / dmu dz)(z_j), and reduces sum_j m_j . v_{z_j} into *dmu.
+// ======================================================================================
+template <class M, int TILE, bool MIX>
+__global__ void __launch_bounds__(TILE) k_node_hprod(const __grid_constant__ NodeArgs<M> a) {
+  constexpr int NX = M::NX, NZ = M::NZ;
+  constexpr int NHD = (M::NHD > 0) ? M::NHD : 1;
+  constexpr HTmpl<M> HT{};
+  __shared__ double red[TILE / 32 + 1];
+  ModelConst K = a.K;
+  if (a.p0_dev) M::device_param(K, __ldg(a.p0_dev));
+  double ms = 0.0;
+  if (MIX) ms = a.mixs ? __ldg(a.mixs) : 0.0;
+  const int64_t nchunks = (a.N + TILE) / TILE;
+  for (int64_t chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
+    const int64_t j = chunk * TILE + threadIdx.x;
+    double acc_mu = 0.0;
+    if (j <= a.N) {
+      double z[NZ], vz[NZ], yb[NX], cqd[NZ], pa[NX], pb[NX], mjx[NX][M::MAXRX], mju[NX][M::MAXRU], hd[NHD];
+      load_node<M>(a, j, z);
+      load_ybar<M>(a, a.y, j, yb);
+      const bool endp = (j == 0) || (j == a.N);
+      node_cq<M>(a, endp, cqd);
+#pragma unroll
+      for (int k = 0; k < NX; ++k) vz[k] = __ldg(a.v + NX * j + k);
+#pragma unroll
+      for (int i = 0; i < M::NU; ++i) vz[NX + i] = __ldg(a.v + a.uoff + M::NU * j + i);
+      M::template eval<false, false, true>(K, z, yb, cqd, pa, pb, mjx, mju, hd);
+      double o[NZ];
+      bool first[NZ];
+#pragma unroll
+      for (int v = 0; v < NZ; ++v) { o[v] = 0.0; first[v] = true; }
+#pragma unroll
+      for (int e = 0; e < HT.n; ++e) {
+        if (a.hpos[e] >= 0) {
+          const int aa = HT.a[e], bb = HT.b[e];
+          const double val = (HT.dyn[e] >= 0) ? hd[HT.dyn[e] >= 0 ? HT.dyn[e] : 0] : cqd[aa];
+          o[aa] = first[aa] ? val * vz[bb] : fma(val, vz[bb], o[aa]);
+          first[aa] = false;
+          if (aa != bb) {
+            o[bb] = first[bb] ? val * vz[aa] : fma(val, vz[aa], o[bb]);
+            first[bb] = false;
+          }
+        }
+      }
+      if (MIX) {
+        double mb[NX], mg[NZ], wl[NX], wr[NX];
+        load_bar<M>(a, a.mixw, j, mb, wl, wr);
+        M::dparam_grad(K, z, mb, mg);
+#pragma unroll
+        for (int v = 0; v < NZ; ++v) {
+          o[v] = fma(mg[v], ms, o[v]);
+          acc_mu = fma(mg[v], vz[v], acc_mu);
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < NX; ++v) a.out[NX * j + v] = o[v];
+#pragma unroll
+      for (int i = 0; i < M::NU; ++i) a.out[a.uoff + M::NU * j + i] = o[NX + i];
+    }
+    if (MIX && a.dmu) {
+      const double ts = cta_sum<TILE>(acc_mu, red);
+      if (threadIdx.x == 0) a.partials[chunk] = ts;
+    }
+  }
+  if (MIX && a.dmu) finish_tiles<TILE>(a.partials, nchunks, a.counter, a.dmu, 1.0, red);
+}
+
+// ======================================================================================
+// Host side
+// ======================================================================================
+template <class M>
+void fill_args(const ocp* h, double sigma, NodeArgs<M>& a) {
+  memset(&a, 0, sizeof(a));
+  const Pattern& P = h->pat;
+  a.N = h->N;
+  a.nb = P.nb;
+  a.uoff = (int64_t)M::NX * (h->N + 1);
+  a.has_final = h->has_final ? 1 : 0;
+  a.has_ref = h->has_ref ? 1 : 0;
+  M::host_consts(h->params.data(), h->hh, a.K);
+  for (int v = 0; v < M::NZ; ++v) {
+    const double w = v < M::NX ? h->q[v] : h->r[v - M::NX];
+    a.gq_in[v] = 2.0 * h->h * w;
+    a.gq_end[v] = h->h * w;
+    a.cq_in[v] = sigma * (2.0 * h->h * w);
+    a.cq_end[v] = sigma * (h->h * w);
+    a.ref[v] = v < M::NX ? h->xref[v] : h->uref[v - M::NX];
+  }
+  for (int k = 0; k < M::NX; ++k) a.jbase[k] = P.jbase[k];
+  a.hbase_u = P.hbase_u;
+  a.hx = P.hx;
+  a.hu = P.hu;
+  for (int e = 0; e < HTmpl<M>::CAP; ++e) a.hpos[e] = e < (int)P.hpos.size() ? P.hpos[e] : (int8_t)-1;
+  a.partials = h->d_partials;
+  a.counter = h->d_counter;
+  a.p0_dev = h->p0_dev;
+}
+
+template <class M, int TILE, unsigned OUT>
+ocp_status launch_eval_t(ocp* h, const EvalCall& c, cudaStream_t s) {
+  NodeArgs<M> a;
+  fill_args<M>(h, c.sigma, a);
+  a.x = c.x; a.y = c.y; a.f = c.f; a.c = c.c; a.g = c.g; a.jv = c.jv; a.hv = c.hv;
+  a.B = c.B; a.E = c.E;
+  a.range = c.range ? 1 : 0;
+  const int64_t nodes = c.E - c.B;
+  a.ntiles = (nodes + (TILE - 2)) / (TILE - 1);
+  if (a.ntiles < 1) a.ntiles = 1;
+  using S = EvalSmem<M, TILE, OUT>;
+  auto kern = k_node_eval<M, TILE, OUT>;
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
+    if (e != cudaSuccess) return cuda_err(h, e, "cudaFuncSetAttribute(eval)");
+    attr_done = true;
+  }
+  const int grid = occupancy_grid(h, (const void*)kern, TILE, S::bytes, a.ntiles);
+  if (grid <= 0) return set_err(h, OCP_ECUDA, "occupancy query failed");
+  kern<<<grid, TILE, S::bytes, s>>>(a);
+  return cuda_err(h, cudaGetLastError(), "k_node_eval launch");
+}
+
+template <class M, int TILE>
+ocp_status node_eval_dispatch(ocp* h, unsigned out, const EvalCall& c, cudaStream_t s) {
+  switch (out) {
+    case O_F: return launch_eval_t<M, TILE, O_F>(h, c, s);
+    case O_C: return launch_eval_t<M, TILE, O_C>(h, c, s);
+    case O_G: return launch_eval_t<M, TILE, O_G>(h, c, s);
+    case O_J: return launch_eval_t<M, TILE, O_J>(h, c, s);
+    case O_H: return launch_eval_t<M, TILE, O_H>(h, c, s);
+    case O_J | O_H: return launch_eval_t<M, TILE, O_J | O_H>(h, c, s);
+    default: return launch_eval_t<M, TILE, O_ALL>(h, c, s);
+  }
+}
+
+template <class M, int TILE>
+ocp_status node_prod_dispatch(ocp* h, const ProdCall& c, cudaStream_t s) {
+  NodeArgs<M> a;
+  fill_args<M>(h, c.sigma, a);
+  a.x = c.x; a.y = c.y; a.v = c.v; a.out = c.out; a.dmu = c.dmu;
+  a.pdir = c.pdir; a.pdir_dev = c.pdir_dev; a.mixw = c.mixw; a.mixs = c.mixs;
+  a.B = 0; a.E = h->N + 1;
+  cudaError_t e;
+  if (c.kind == P_JPROD) {
+    a.ntiles = (h->N + 1 + (TILE - 2)) / (TILE - 1);
+    const bool pd = (c.pdir != 0.0) || (c.pdir_dev != nullptr);
+    if (pd) {
+      auto k = k_node_jprod<M, TILE, true>;
+      int grid = occupancy_grid(h, (const void*)k, TILE, 0, a.ntiles);
+      k<<<grid, TILE, 0, s>>>(a);
+    } else {
+      auto k = k_node_jprod<M, TILE, false>;
+      int grid = occupancy_grid(h, (const void*)k, TILE, 0, a.ntiles);
+      k<<<grid, TILE, 0, s>>>(a);
+    }
+    e = cudaGetLastError();
+  } else if (c.kind == P_JTPROD) {
+    const int64_t blocks = (h->N + TILE) / TILE;
+    if (c.dmu) {
+      auto k = k_node_jtprod<M, TILE, true>;
+      int grid = occupancy_grid(h, (const void*)k, TILE, 0, blocks);
+      k<<<grid, TILE, 0, s>>>(a);
+    } else {
+      auto k = k_node_jtprod<M, TILE, false>;
+      int grid = occupancy_grid(h, (const void*)k, TILE, 0, blocks);
+      k<<<grid, TILE, 0, s>>>(a);
+    }
+    e = cudaGetLastError();
+  } else {
+    const int64_t blocks = (h->N + 1 + TILE - 1) / TILE;
+    if (c.mixw) {
+      auto k = k_node_hprod<M, TILE, true>;
+      int grid = occupancy_grid(h, (const void*)k, TILE, 0, blocks);
+      k<<<grid, TILE, 0, s>>>(a);
+    } else {
+      auto k = k_node_hprod<M, TILE, false>;
+      int grid = occupancy_grid(h, (const void*)k, TILE, 0, blocks);
+      k<<<grid, TILE, 0, s>>>(a);
+    }
+    e = cudaGetLastError();
+  }
+  return cuda_err(h, e, "node product launch");
+}
+
+}  // namespace ocpg

@@ -1,0 +1,9 @@
+// Instantiation of the node-model kernels for the VdP model.
+#include "node_kernels.cuh"
+
+namespace ocpg {
+ocp_status node_eval_vdp(ocp* h, unsigned out, const EvalCall& c, cudaStream_t s) {
+  return node_eval_dispatch<VdP, 256>(h, out, c, s);
+}
+ocp_status node_prod_vdp(ocp* h, const ProdCall& c, cudaStream_t s) { return node_prod_dispatch<VdP, 256>(h, c, s); }
+}  // namespace ocpg

@@ -1,0 +1,133 @@
+// Internal declarations shared by the C-ABI, the host pattern compiler and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "ocp.h"
+
+namespace ocpg {
+
+// Output selection bits of the fused evaluation kernels.
+enum : unsigned { O_F = 1u, O_C = 2u, O_G = 4u, O_J = 8u, O_H = 16u, O_ALL = 31u };
+
+// Per-component Jacobian row template (local variable indices), as read from the model.
+struct RowTemplate {
+  int rx = 0, ru = 0;
+  int xv[4] = {-1, -1, -1, -1};
+  int uv[2] = {-1, -1};
+  int count() const { return 2 * (rx + ru); }
+};
+
+// Host pattern: sizes, slot offsets and the node templates (paper Sec. 5: the generators
+// make one row per state component per interval; the pattern compiler lays out the COO
+// slots of every (component, interval) row and of every node's Hessian block).
+struct Pattern {
+  int nx = 0, nu = 0, nz = 0;
+  int64_t N = 0, n = 0, m = 0, nb = 0, nnzj = 0, nnzh = 0;
+  std::vector<RowTemplate> rows;         // per component k
+  std::vector<int64_t> jbase;            // slot of row (k, 0); size nx + 1 (last = nnzj)
+  std::vector<std::pair<int, int>> hent; // node Hessian entries (a, b), canonical order
+  int hx = 0, hu = 0;                    // entries per node in the X block / U block
+  int64_t hbase_u = 0;                   // first slot of the U block = (N+1) * hx
+  std::vector<int8_t> hpos;              // per max-template entry: position in its block or -1
+};
+
+}  // namespace ocpg
+
+struct ocp {
+  int model = 0, nx = 0, nu = 0;
+  int64_t N = 0;
+  double T = 0, h = 0, hh = 0;
+  std::vector<double> params, q, r, xref, uref, x0, xf;
+  bool has_final = false, has_ref = false;
+  const double* p0_dev = nullptr;  // device scalar overriding params[0] (or null)
+  ocpg::Pattern pat;
+  int device = 0, num_sms = 0;
+  // device-resident pattern tables for the structure kernels
+  int32_t* d_rowtmpl = nullptr;  // nx * 8 ints: rx, ru, xv[4], uv[2]
+  int64_t* d_jbase = nullptr;    // nx + 1
+  int32_t* d_hent = nullptr;     // 2 * (hx + hu)
+  // scratch: per-CTA partial sums and the completion ticket of the last-block reduction
+  double* d_partials = nullptr;
+  unsigned* d_counter = nullptr;
+  int max_partials = 0;
+  std::string err;
+};
+
+struct ocp_batch {
+  std::vector<ocp*> items;
+  int model = 0, count = 0;
+  std::vector<int64_t> xoff, coff, joff, hoff, tileoff;
+  int64_t ntiles = 0, total_nodes = 0;
+  int nodes_per_thread = 1, threads = 256;
+  // device tables
+  void* d_inst = nullptr;       // per-instance descriptors
+  int64_t* d_tileoff = nullptr; // count + 1 prefix sums of tiles per instance
+  double* d_partials = nullptr;
+  int max_partials = 0;
+  int tile_nodes = 0;
+  std::string err;
+};
+
+namespace ocpg {
+
+ocp_status set_err(ocp* h, ocp_status st, const std::string& msg);
+ocp_status cuda_err(ocp* h, cudaError_t e, const char* what);
+int occupancy_grid(ocp* h, const void* kernel, int threads, size_t smem, int64_t work_tiles);
+
+// Host pattern compiler.
+bool build_pattern(ocp* h, std::string& why);
+
+struct EvalCall {
+  const double* x = nullptr;
+  const double* y = nullptr;
+  double sigma = 1.0;
+  double *f = nullptr, *c = nullptr, *g = nullptr, *jv = nullptr, *hv = nullptr;
+  int64_t B = 0, E = 0;  // owned node range [B, E)
+  bool range = false;    // f receives the partial sum of this range
+};
+
+enum ProdKind { P_JPROD = 0, P_JTPROD = 1, P_HPROD = 2 };
+struct ProdCall {
+  int kind = 0;
+  const double* x = nullptr;
+  const double* y = nullptr;
+  double sigma = 1.0;
+  const double* v = nullptr;
+  double* out = nullptr;
+  double* dmu = nullptr;  // jtprod: (dc/dp0)^T v (device scalar), may be null
+  // autograd extensions (Van der Pol): parameter-direction terms
+  double pdir = 0.0;            // jprod: adds (dc/dp0) * pdir  (host scalar)
+  const double* pdir_dev = nullptr;  // jprod: same with a device scalar
+  const double* mixw = nullptr; // hprod: adds (d2 c / dp0 dx)^T mixw * mixs
+  const double* mixs = nullptr; // device scalar
+};
+
+// Per-model dispatchers (node models: VDP, CARTPOLE, DINT; HEAT1D separate).
+ocp_status node_eval_vdp(ocp* h, unsigned out, const EvalCall& c, cudaStream_t s);
+ocp_status node_eval_cartpole(ocp* h, unsigned out, const EvalCall& c, cudaStream_t s);
+ocp_status node_eval_dint(ocp* h, unsigned out, const EvalCall& c, cudaStream_t s);
+ocp_status node_prod_vdp(ocp* h, const ProdCall& c, cudaStream_t s);
+ocp_status node_prod_cartpole(ocp* h, const ProdCall& c, cudaStream_t s);
+ocp_status node_prod_dint(ocp* h, const ProdCall& c, cudaStream_t s);
+ocp_status heat_eval(ocp* h, unsigned out, const EvalCall& c, cudaStream_t s);
+ocp_status heat_prod(ocp* h, const ProdCall& c, cudaStream_t s);
+
+ocp_status launch_jac_structure(const ocp* h, int32_t* rows, int32_t* cols, cudaStream_t s);
+ocp_status launch_hess_structure(const ocp* h, int32_t* rows, int32_t* cols, cudaStream_t s);
+
+// Max-template of the node Hessian for node models (see node_kernels.cuh) and the
+// per-model Jacobian row templates, for the pattern compiler.
+void model_row_templates(int model, int nx, std::vector<RowTemplate>& rows);
+void model_hess_max_template(int model, int nx, std::vector<std::pair<int, int>>& ent,
+                             std::vector<int>& is_dyn);
+
+ocp_status batch_eval(ocp_batch* b, const double* x, const double* y, double sigma, double* f,
+                      double* g, double* jv, double* hv, cudaStream_t s);
+bool batch_prepare(ocp_batch* b, std::string& why);
+
+}  // namespace ocpg

@@ -1,0 +1,210 @@
+// Host pattern compiler and the COO structure kernels.
+//
+// The transcription (paper Sec. 5) makes, for every state component k, one defect row per
+// interval j; row (k, j) touches only z_j and z_{j+1}.  The pattern compiler turns the
+// model's per-node templates into the slot layout of the COO arrays:
+//   Jacobian:  [nb boundary rows, 1 entry each] then, component by component, N rows of
+//              count_k entries; row (k, j) starts at jbase[k] + j*count_k and lists, by
+//              increasing column, its entries on X_j, X_{j+1}, U_j, U_{j+1}.
+//   Hessian:   block-diagonal by node (the defects are sums of one-node terms and the cost is
+//              a sum over nodes): the hx X-row entries of every node in node order, then the
+//              hu U-row entries of every node; within a node, by (row, col).
+// Sorting by (row, col) globally gives exactly this order because X columns precede U columns.
+#include <algorithm>
+#include <cstring>
+
+#include "models.cuh"
+#include "node_kernels.cuh"
+#include "ocp_internal.h"
+
+namespace ocpg {
+
+template <class M>
+static void rows_from(std::vector<RowTemplate>& rows) {
+  rows.assign(M::NX, RowTemplate());
+  for (int k = 0; k < M::NX; ++k) {
+    rows[k].rx = M::RX(k);
+    rows[k].ru = M::RU(k);
+    for (int e = 0; e < M::RX(k); ++e) rows[k].xv[e] = M::XV(k, e);
+    for (int e = 0; e < M::RU(k); ++e) rows[k].uv[e] = M::UV(k, e);
+  }
+}
+
+void model_row_templates(int model, int nx, std::vector<RowTemplate>& rows) {
+  switch (model) {
+    case OCP_MODEL_VDP: rows_from<VdP>(rows); break;
+    case OCP_MODEL_CARTPOLE: rows_from<CartPole>(rows); break;
+    case OCP_MODEL_DINT: rows_from<Dint>(rows); break;
+    case OCP_MODEL_HEAT1D:
+      rows.assign(nx, RowTemplate());
+      for (int k = 0; k < nx; ++k) {
+        RowTemplate& r = rows[k];
+        r.rx = 0;
+        if (k > 0) r.xv[r.rx++] = k - 1;
+        r.xv[r.rx++] = k;
+        if (k < nx - 1) r.xv[r.rx++] = k + 1;
+        r.ru = (k == 0) ? 1 : 0;
+        r.uv[0] = (k == 0) ? 0 : -1;
+      }
+      break;
+    default: rows.clear();
+  }
+}
+
+template <class M>
+static void hmax_from(std::vector<std::pair<int, int>>& ent, std::vector<int>& is_dyn) {
+  constexpr HTmpl<M> HT{};
+  ent.clear();
+  is_dyn.clear();
+  for (int e = 0; e < HT.n; ++e) {
+    ent.push_back({HT.a[e], HT.b[e]});
+    is_dyn.push_back(HT.dyn[e] >= 0 ? 1 : 0);
+  }
+}
+
+void model_hess_max_template(int model, int nx, std::vector<std::pair<int, int>>& ent, std::vector<int>& is_dyn) {
+  switch (model) {
+    case OCP_MODEL_VDP: hmax_from<VdP>(ent, is_dyn); break;
+    case OCP_MODEL_CARTPOLE: hmax_from<CartPole>(ent, is_dyn); break;
+    case OCP_MODEL_DINT: hmax_from<Dint>(ent, is_dyn); break;
+    case OCP_MODEL_HEAT1D:
+      ent.clear();
+      is_dyn.clear();
+      for (int k = 0; k < nx; ++k) { ent.push_back({k, k}); is_dyn.push_back(1); }
+      ent.push_back({nx, nx});
+      is_dyn.push_back(0);
+      break;
+    default: ent.clear(); is_dyn.clear();
+  }
+}
+
+bool build_pattern(ocp* h, std::string& why) {
+  Pattern& P = h->pat;
+  P = Pattern();
+  P.nx = h->nx; P.nu = h->nu; P.nz = h->nx + h->nu; P.N = h->N;
+  P.n = (int64_t)P.nz * (P.N + 1);
+  P.nb = (int64_t)P.nx * (h->has_final ? 2 : 1);
+  P.m = P.nb + (int64_t)P.nx * P.N;
+  model_row_templates(h->model, h->nx, P.rows);
+  if ((int)P.rows.size() != P.nx) { why = "no row template for this model"; return false; }
+  P.jbase.assign(P.nx + 1, 0);
+  P.jbase[0] = P.nb;
+  for (int k = 0; k < P.nx; ++k) P.jbase[k + 1] = P.jbase[k] + (int64_t)P.rows[k].count() * P.N;
+  P.nnzj = P.jbase[P.nx];
+  std::vector<std::pair<int, int>> ent;
+  std::vector<int> dyn;
+  model_hess_max_template(h->model, h->nx, ent, dyn);
+  P.hpos.assign(ent.size(), (int8_t)-1);
+  int px = 0, pu = 0;
+  std::vector<std::pair<int, int>> ex, eu;
+  for (size_t e = 0; e < ent.size(); ++e) {
+    const int a = ent[e].first, b = ent[e].second;
+    const double coef = a < P.nx ? h->q[a] : h->r[a - P.nx];
+    const bool present = dyn[e] || (a == b && coef != 0.0);
+    if (!present) continue;
+    if (a < P.nx) { P.hpos[e] = (int8_t)(px < 127 ? px : 127); ++px; ex.push_back(ent[e]); }
+    else { P.hpos[e] = (int8_t)pu; ++pu; eu.push_back(ent[e]); }
+  }
+  P.hx = px;
+  P.hu = pu;
+  P.hent = ex;
+  P.hent.insert(P.hent.end(), eu.begin(), eu.end());
+  P.hbase_u = (int64_t)P.hx * (P.N + 1);
+  P.nnzh = (int64_t)(P.hx + P.hu) * (P.N + 1);
+  const int64_t lim = (int64_t)1 << 31;
+  if (P.n >= lim || P.m >= lim || P.nnzj >= lim || P.nnzh >= lim) {
+    why = "problem too large for the int32 COO interface (n, m or nnz >= 2^31)";
+    return false;
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------------------
+// Structure kernels: one thread per slot, decoding (row, col) from the templates.
+// ---------------------------------------------------------------------------------------
+struct JacStructArgs {
+  int32_t* rows;
+  int32_t* cols;
+  const int32_t* tmpl;   // per component: rx, ru, xv[4], uv[2]
+  const int64_t* jbase;  // nx + 1
+  int64_t N, nb, nnzj, uoff;
+  int nx, nu, has_final;
+};
+
+__global__ void k_jac_structure(const __grid_constant__ JacStructArgs a) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < a.nnzj; s += stride) {
+    int64_t row, col;
+    if (s < a.nb) {
+      row = s;
+      col = (s < a.nx) ? s : (int64_t)a.nx * a.N + (s - a.nx);
+    } else {
+      int lo = 0, hi = a.nx - 1;  // last component with jbase <= s
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.jbase[mid] <= s) lo = mid; else hi = mid - 1;
+      }
+      const int k = lo;
+      const int32_t* t = a.tmpl + 8 * k;
+      const int rx = t[0], ru = t[1];
+      const int cnt = 2 * (rx + ru);
+      const int64_t rel = s - a.jbase[k];
+      const int64_t j = rel / cnt;
+      const int e = (int)(rel - j * cnt);
+      row = a.nb + (int64_t)k * a.N + j;
+      if (e < rx) col = (int64_t)a.nx * j + t[2 + e];
+      else if (e < 2 * rx) col = (int64_t)a.nx * (j + 1) + t[2 + (e - rx)];
+      else if (e < 2 * rx + ru) col = a.uoff + (int64_t)a.nu * j + t[6 + (e - 2 * rx)];
+      else col = a.uoff + (int64_t)a.nu * (j + 1) + t[6 + (e - 2 * rx - ru)];
+    }
+    a.rows[s] = (int32_t)row;
+    a.cols[s] = (int32_t)col;
+  }
+}
+
+struct HessStructArgs {
+  int32_t* rows;
+  int32_t* cols;
+  const int32_t* hent;  // (a, b) pairs: hx X-block entries then hu U-block entries
+  int64_t N, hbase_u, nnzh, uoff;
+  int nx, nu, hx, hu;
+};
+
+__device__ __forceinline__ int64_t local_col(int64_t j, int v, int nx, int nu, int64_t uoff) {
+  return v < nx ? (int64_t)nx * j + v : uoff + (int64_t)nu * j + (v - nx);
+}
+
+__global__ void k_hess_structure(const __grid_constant__ HessStructArgs a) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < a.nnzh; s += stride) {
+    int64_t j;
+    int e;
+    if (s < a.hbase_u) { j = s / a.hx; e = (int)(s - j * a.hx); }
+    else { const int64_t r = s - a.hbase_u; j = r / a.hu; e = a.hx + (int)(r - j * a.hu); }
+    const int va = a.hent[2 * e], vb = a.hent[2 * e + 1];
+    a.rows[s] = (int32_t)local_col(j, va, a.nx, a.nu, a.uoff);
+    a.cols[s] = (int32_t)local_col(j, vb, a.nx, a.nu, a.uoff);
+  }
+}
+
+ocp_status launch_jac_structure(const ocp* h, int32_t* rows, int32_t* cols, cudaStream_t s) {
+  JacStructArgs a;
+  a.rows = rows; a.cols = cols; a.tmpl = h->d_rowtmpl; a.jbase = h->d_jbase;
+  a.N = h->N; a.nb = h->pat.nb; a.nnzj = h->pat.nnzj; a.uoff = (int64_t)h->nx * (h->N + 1);
+  a.nx = h->nx; a.nu = h->nu; a.has_final = h->has_final;
+  const int64_t blocks = std::min<int64_t>((a.nnzj + 255) / 256, (int64_t)h->num_sms * 16);
+  k_jac_structure<<<(int)std::max<int64_t>(blocks, 1), 256, 0, s>>>(a);
+  return cudaGetLastError() == cudaSuccess ? OCP_OK : OCP_ECUDA;
+}
+
+ocp_status launch_hess_structure(const ocp* h, int32_t* rows, int32_t* cols, cudaStream_t s) {
+  HessStructArgs a;
+  a.rows = rows; a.cols = cols; a.hent = h->d_hent;
+  a.N = h->N; a.hbase_u = h->pat.hbase_u; a.nnzh = h->pat.nnzh; a.uoff = (int64_t)h->nx * (h->N + 1);
+  a.nx = h->nx; a.nu = h->nu; a.hx = h->pat.hx; a.hu = h->pat.hu;
+  const int64_t blocks = std::min<int64_t>((a.nnzh + 255) / 256, (int64_t)h->num_sms * 16);
+  k_hess_structure<<<(int)std::max<int64_t>(blocks, 1), 256, 0, s>>>(a);
+  return cudaGetLastError() == cudaSuccess ? OCP_OK : OCP_ECUDA;
+}
+
+}  // namespace ocpg

@@ -1,0 +1,312 @@
+"""Python binding of the C-ABI (include/ocp.h): argument marshalling only.
+
+Every computation runs in the CUDA library libocp_gb300.so; this module checks tensor
+arguments (FP64, contiguous, on the handle's CUDA device), passes raw pointers and the
+current torch stream, and turns non-zero statuses into exceptions.  There is no CPU
+fallback: without the compiled library (or without a GPU) every evaluation raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+from . import build as _build
+
+MODEL_IDS = {"vdp": 1, "cartpole": 2, "heat": 3, "dint": 4}
+STATUS = {0: "OCP_OK", 1: "OCP_EINVAL", 2: "OCP_EDIM", 3: "OCP_ENOMEM", 4: "OCP_ECUDA", 5: "OCP_EMODEL",
+          6: "OCP_ETIMEOUT"}
+
+_lib = None
+
+
+class OcpError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+class _Dyn(C.Structure):
+    _fields_ = [("model", C.c_int), ("params", C.c_void_p), ("nparams", C.c_int)]
+
+
+class _Cost(C.Structure):
+    _fields_ = [("kind", C.c_int), ("q", C.c_void_p), ("r", C.c_void_p), ("xref", C.c_void_p),
+                ("uref", C.c_void_p)]
+
+
+_P = C.c_void_p
+_D = C.c_double
+_I64 = C.c_int64
+_SIGS = {
+    "ocp_create": [C.POINTER(_Dyn), C.POINTER(_Cost), C.c_int, C.c_int, _I64, _D, C.POINTER(_P)],
+    "ocp_destroy": [_P],
+    "ocp_set_boundary": [_P, _P, _P],
+    "ocp_dims": [_P, C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_I64)],
+    "ocp_bounds": [_P, _P, _P, _P, _P],
+    "eval_obj": [_P, _P, _P, _P],
+    "eval_cons": [_P, _P, _P, _P],
+    "eval_grad": [_P, _P, _P, _P],
+    "jac_coo_structure": [_P, _P, _P, _P],
+    "jac_coo_values": [_P, _P, _P, _P],
+    "hess_coo_structure": [_P, _P, _P, _P],
+    "hess_coo_values": [_P, _P, _P, _D, _P, _P],
+    "jprod": [_P, _P, _P, _P, _P],
+    "jtprod": [_P, _P, _P, _P, _P],
+    "hprod": [_P, _P, _P, _D, _P, _P, _P],
+    "ocp_eval_all": [_P, _P, _P, _D, _P, _P, _P, _P, _P, _P],
+    "ocp_eval_all_range": [_P, _I64, _I64, _P, _P, _D, _P, _P, _P, _P, _P, _P],
+    "ocp_vjp_param": [_P, _P, _P, _P, _P, _P],
+    "ocp_set_param0": [_P, _D],
+    "ocp_last_error": [_P],
+}
+
+
+def lib():
+    """Load (building first if needed) the CUDA library.  Raises if it cannot be built."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not _build.up_to_date():
+            path = _build.build()
+        L = C.CDLL(path)
+        for name, argt in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = argt
+            fn.restype = C.c_int
+        L.ocp_destroy.restype = None
+        L.ocp_last_error.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _check(st, h=None):
+    if st != 0:
+        msg = lib().ocp_last_error(h)
+        raise OcpError(st, msg.decode() if msg else "")
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+class OCP:
+    """A transcribed optimal control problem (an `ocp_t` handle)."""
+
+    def __init__(self, model: str, nx: int, nu: int, N: int, T: float, params, q, r, xref=None, uref=None,
+                 x0=None, xf=None):
+        L = lib()
+        self._keep = []
+
+        def arr(v):
+            if v is None:
+                return None
+            a = (C.c_double * len(v))(*[float(e) for e in v])
+            self._keep.append(a)
+            return C.cast(a, C.c_void_p)
+
+        dyn = _Dyn(MODEL_IDS[model], arr(params) if len(params) else None, len(params))
+        cost = _Cost(0, arr(q), arr(r), arr(xref), arr(uref))
+        h = C.c_void_p()
+        _check(L.ocp_create(C.byref(dyn), C.byref(cost), nx, nu, int(N), float(T), C.byref(h)))
+        self.h = h
+        self.model, self.nx, self.nu, self.N, self.T = model, nx, nu, int(N), float(T)
+        if x0 is not None or xf is not None:
+            _check(L.ocp_set_boundary(h, arr(x0), arr(xf)), h)
+        n, m, nj, nh = _I64(), _I64(), _I64(), _I64()
+        _check(L.ocp_dims(h, C.byref(n), C.byref(m), C.byref(nj), C.byref(nh)), h)
+        self.n, self.m, self.nnzj, self.nnzh = n.value, m.value, nj.value, nh.value
+        self.device = torch.device("cuda", torch.cuda.current_device())
+
+    @classmethod
+    def from_workload(cls, w: dict) -> "OCP":
+        return cls(w["model"], w["nx"], w["nu"], w["N"], w["T"], w["params"], w["q"], w["r"], w.get("xref"),
+                   w.get("uref"), w.get("x0"), w.get("xf"))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ocp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- argument checks --------------------------------------------------------------
+    def _vec(self, t, size, name):
+        if t is None:
+            raise ValueError("%s is required" % name)
+        if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
+            raise TypeError("%s must be a contiguous float64 CUDA tensor" % name)
+        if t.numel() != size:
+            raise ValueError("%s has %d elements, expected %d" % (name, t.numel(), size))
+        return t
+
+    def _out(self, t, size, name):
+        if t is None:
+            return torch.empty(size, dtype=torch.float64, device=self.device)
+        return self._vec(t, size, name)
+
+    # ---- C-ABI calls ------------------------------------------------------------------
+    def bounds(self):
+        import numpy as np
+        lv, uv, lc, uc = (np.empty(self.n), np.empty(self.n), np.empty(self.m), np.empty(self.m))
+        _check(lib().ocp_bounds(self.h, lv.ctypes.data_as(_P), uv.ctypes.data_as(_P), lc.ctypes.data_as(_P),
+                                uc.ctypes.data_as(_P)), self.h)
+        return lv, uv, lc, uc
+
+    def eval_obj(self, x, out=None, stream=None):
+        x = self._vec(x, self.n, "x")
+        out = self._out(out, 1, "f")
+        _check(lib().eval_obj(self.h, _ptr(x), _ptr(out), _stream(stream)), self.h)
+        return out
+
+    def eval_cons(self, x, out=None, stream=None):
+        x = self._vec(x, self.n, "x")
+        out = self._out(out, self.m, "c")
+        _check(lib().eval_cons(self.h, _ptr(x), _ptr(out), _stream(stream)), self.h)
+        return out
+
+    def eval_grad(self, x, out=None, stream=None):
+        x = self._vec(x, self.n, "x")
+        out = self._out(out, self.n, "g")
+        _check(lib().eval_grad(self.h, _ptr(x), _ptr(out), _stream(stream)), self.h)
+        return out
+
+    def jac_coo_structure(self, stream=None):
+        rows = torch.empty(self.nnzj, dtype=torch.int32, device=self.device)
+        cols = torch.empty(self.nnzj, dtype=torch.int32, device=self.device)
+        _check(lib().jac_coo_structure(self.h, _ptr(rows), _ptr(cols), _stream(stream)), self.h)
+        return rows, cols
+
+    def hess_coo_structure(self, stream=None):
+        rows = torch.empty(self.nnzh, dtype=torch.int32, device=self.device)
+        cols = torch.empty(self.nnzh, dtype=torch.int32, device=self.device)
+        _check(lib().hess_coo_structure(self.h, _ptr(rows), _ptr(cols), _stream(stream)), self.h)
+        return rows, cols
+
+    def jac_coo_values(self, x, out=None, stream=None):
+        x = self._vec(x, self.n, "x")
+        out = self._out(out, self.nnzj, "vals")
+        _check(lib().jac_coo_values(self.h, _ptr(x), _ptr(out), _stream(stream)), self.h)
+        return out
+
+    def hess_coo_values(self, x, y, sigma, out=None, stream=None):
+        x = self._vec(x, self.n, "x")
+        y = self._vec(y, self.m, "y")
+        out = self._out(out, self.nnzh, "vals")
+        _check(lib().hess_coo_values(self.h, _ptr(x), _ptr(y), float(sigma), _ptr(out), _stream(stream)), self.h)
+        return out
+
+    def jprod(self, x, v, out=None, stream=None):
+        x = self._vec(x, self.n, "x")
+        v = self._vec(v, self.n, "v")
+        out = self._out(out, self.m, "Jv")
+        _check(lib().jprod(self.h, _ptr(x), _ptr(v), _ptr(out), _stream(stream)), self.h)
+        return out
+
+    def jtprod(self, x, v, out=None, stream=None):
+        x = self._vec(x, self.n, "x")
+        v = self._vec(v, self.m, "v")
+        out = self._out(out, self.n, "Jtv")
+        _check(lib().jtprod(self.h, _ptr(x), _ptr(v), _ptr(out), _stream(stream)), self.h)
+        return out
+
+    def hprod(self, x, y, sigma, v, out=None, stream=None):
+        x = self._vec(x, self.n, "x")
+        y = self._vec(y, self.m, "y")
+        v = self._vec(v, self.n, "v")
+        out = self._out(out, self.n, "Hv")
+        _check(lib().hprod(self.h, _ptr(x), _ptr(y), float(sigma), _ptr(v), _ptr(out), _stream(stream)), self.h)
+        return out
+
+    def eval_all(self, x, y, sigma, f=None, c=None, g=None, jvals=None, hvals=None, stream=None, alloc=True):
+        """Fused evaluation; with alloc=True missing outputs are allocated (all five computed)."""
+        x = self._vec(x, self.n, "x")
+        if y is not None:
+            y = self._vec(y, self.m, "y")
+        if alloc:
+            f = self._out(f, 1, "f"); c = self._out(c, self.m, "c"); g = self._out(g, self.n, "g")
+            jvals = self._out(jvals, self.nnzj, "jvals"); hvals = self._out(hvals, self.nnzh, "hvals")
+        _check(lib().ocp_eval_all(self.h, _ptr(x), _ptr(y), float(sigma), _ptr(f), _ptr(c), _ptr(g), _ptr(jvals),
+                                  _ptr(hvals), _stream(stream)), self.h)
+        return f, c, g, jvals, hvals
+
+    def eval_all_range(self, node_begin, node_end, x, y, sigma, f, c, g, jvals, hvals, stream=None):
+        _check(lib().ocp_eval_all_range(self.h, int(node_begin), int(node_end), _ptr(x), _ptr(y), float(sigma),
+                                        _ptr(f), _ptr(c), _ptr(g), _ptr(jvals), _ptr(hvals), _stream(stream)),
+               self.h)
+
+    def vjp_param(self, x, w, Jtw=None, dmu=None, stream=None):
+        x = self._vec(x, self.n, "x")
+        w = self._vec(w, self.m, "w")
+        Jtw = self._out(Jtw, self.n, "Jtw")
+        dmu = self._out(dmu, 1, "dmu")
+        _check(lib().ocp_vjp_param(self.h, _ptr(x), _ptr(w), _ptr(Jtw), _ptr(dmu), _stream(stream)), self.h)
+        return Jtw, dmu
+
+    def set_param0(self, value: float):
+        _check(lib().ocp_set_param0(self.h, float(value)), self.h)
+
+
+def ocp_create(w: dict) -> OCP:
+    """Create a problem from a workload description (see synth.workload)."""
+    return OCP.from_workload(w)
+
+
+# C-ABI names as module-level functions (handle first, then the arguments of include/ocp.h)
+def eval_obj(h: OCP, x, f=None, stream=None):
+    return h.eval_obj(x, f, stream)
+
+
+def eval_cons(h: OCP, x, c=None, stream=None):
+    return h.eval_cons(x, c, stream)
+
+
+def eval_grad(h: OCP, x, g=None, stream=None):
+    return h.eval_grad(x, g, stream)
+
+
+def jac_coo_structure(h: OCP, stream=None):
+    return h.jac_coo_structure(stream)
+
+
+def jac_coo_values(h: OCP, x, vals=None, stream=None):
+    return h.jac_coo_values(x, vals, stream)
+
+
+def hess_coo_structure(h: OCP, stream=None):
+    return h.hess_coo_structure(stream)
+
+
+def hess_coo_values(h: OCP, x, y, sigma, vals=None, stream=None):
+    return h.hess_coo_values(x, y, sigma, vals, stream)
+
+
+def jprod(h: OCP, x, v, Jv=None, stream=None):
+    return h.jprod(x, v, Jv, stream)
+
+
+def jtprod(h: OCP, x, v, Jtv=None, stream=None):
+    return h.jtprod(x, v, Jtv, stream)
+
+
+def hprod(h: OCP, x, y, sigma, v, Hv=None, stream=None):
+    return h.hprod(x, y, sigma, v, Hv, stream)
+
+
+def ocp_eval_all(h: OCP, x, y, sigma, f=None, c=None, g=None, jvals=None, hvals=None, stream=None):
+    return h.eval_all(x, y, sigma, f, c, g, jvals, hvals, stream)
+
+
+def library_path() -> str:
+    return os.path.abspath(_build.LIB)

@@ -1,0 +1,82 @@
+"""The C-ABI library loads and exports every entry point of include/ocp.h; host-side
+argument validation works without a GPU (these calls fail before touching CUDA)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_2510_03932_gb300 import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s+\**([a-z_][a-z0-9_]*)\s*\(", text, re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return C.CDLL(build.build())
+
+
+def test_header_declares_the_calls():
+    names = declared_functions()
+    for n in ["ocp_create", "eval_obj", "eval_cons", "eval_grad", "jac_coo_structure", "jac_coo_values",
+              "hess_coo_structure", "hess_coo_values", "jprod", "jtprod", "hprod", "ocp_eval_all"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+class Dyn(C.Structure):
+    _fields_ = [("model", C.c_int), ("params", C.c_void_p), ("nparams", C.c_int)]
+
+
+class Cost(C.Structure):
+    _fields_ = [("kind", C.c_int), ("q", C.c_void_p), ("r", C.c_void_p), ("xref", C.c_void_p), ("uref", C.c_void_p)]
+
+
+def create(lib, model, params, nx, nu, N=10, T=1.0, kind=0):
+    p = (C.c_double * max(1, len(params)))(*params)
+    q = (C.c_double * 64)(*([1.0] * 64))
+    r = (C.c_double * 1)(0.1)
+    d = Dyn(model, C.cast(p, C.c_void_p), len(params))
+    c = Cost(kind, C.cast(q, C.c_void_p), C.cast(r, C.c_void_p), None, None)
+    h = C.c_void_p()
+    lib.ocp_create.restype = C.c_int
+    lib.ocp_create.argtypes = [C.POINTER(Dyn), C.POINTER(Cost), C.c_int, C.c_int, C.c_int64, C.c_double,
+                               C.POINTER(C.c_void_p)]
+    st = lib.ocp_create(C.byref(d), C.byref(c), nx, nu, N, T, C.byref(h))
+    lib.ocp_last_error.restype = C.c_char_p
+    lib.ocp_last_error.argtypes = [C.c_void_p]
+    return st, lib.ocp_last_error(None).decode()
+
+
+def test_create_rejects_bad_arguments_on_the_host(lib):
+    assert create(lib, 99, [1.0], 2, 1)[0] == 5                 # OCP_EMODEL: unknown model
+    assert create(lib, 1, [1.0], 3, 1)[0] == 2                  # OCP_EDIM: wrong nx (Sec. 5 dimension check)
+    st, msg = create(lib, 1, [1.0], 2, 2)
+    assert st == 2 and "dimension" in msg
+    assert create(lib, 1, [], 2, 1)[0] == 2                     # wrong number of parameters
+    assert create(lib, 2, [1, 0.1, 0.5, 9.81], 4, 1, N=0)[0] == 2  # N < 1
+    assert create(lib, 1, [1.0], 2, 1, T=-1.0)[0] == 1          # OCP_EINVAL
+    assert create(lib, 1, [1.0], 2, 1, kind=7)[0] == 5          # unknown cost kind
+    assert create(lib, 3, [200.0], 200, 1)[0] == 2              # heat: ncell out of range
+    assert create(lib, 1, [1.0], 2, 1, N=2**31)[0] == 2         # n >= 2^31 does not fit int32 COO
+
+
+def test_null_handle_is_rejected(lib):
+    lib.eval_obj.restype = C.c_int
+    lib.eval_obj.argtypes = [C.c_void_p] * 4
+    assert lib.eval_obj(None, None, None, None) == 1

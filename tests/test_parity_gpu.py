@@ -1,0 +1,184 @@
+"""Parity of the CUDA path (through the C-ABI) with the CPU oracle, on seeded inputs.
+
+Sparsity patterns must match bit-exact; values must pass the per-entry gate of
+tests/parity.py (1e-12 relative + 1e-14 absolute, or 1e-12 of the oracle's running-error
+magnitude for entries with cancellation).  Small horizons span several tiles and a ragged
+tail; the full-size workloads are compared entry by entry as well.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2510_03932_gb300 import synth
+from parity import gate
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ocp():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2510_03932_gb300 import ocp as M
+    M.lib()
+    return M
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def full_check(ocp, w, report=None, products=True):
+    """Everything the C-ABI computes for workload w versus the oracle."""
+    d = synth.draw(w)
+    P = O.Problem(w)
+    H = ocp.OCP.from_workload(w)
+    assert (H.n, H.m, H.nnzj, H.nnzh) == (P.n, P.m, P.nnzj, P.nnzh)
+    x, y, vn, vm = dev(d["x"]), dev(d["y"]), dev(d["vn"]), dev(d["vm"])
+    sigma = w["sigma"]
+    # structure: bit-exact
+    jr, jc = H.jac_coo_structure()
+    hr, hc = H.hess_coo_structure()
+    ojr, ojc = O.jac_structure(P)
+    ohr, ohc = O.hess_structure(P)
+    torch.cuda.synchronize()
+    assert np.array_equal(host(jr), ojr) and np.array_equal(host(jc), ojc)
+    assert np.array_equal(host(hr), ohr) and np.array_equal(host(hc), ohc)
+    # values
+    ref = O.evaluate(P, d["x"], d["y"], sigma, shadow=True)
+    f, c, g, jv, hv = H.eval_all(x, y, sigma)
+    torch.cuda.synchronize()
+    rep = {} if report is None else report
+    gate("f", host(f), np.array([ref["f"]]), np.array([ref["f_mag"]]), rep)
+    gate("c", host(c), ref["c"], ref["c_mag"], rep)
+    gate("g", host(g), ref["g"], ref["g_mag"], rep)
+    gate("jac", host(jv), ref["jac"], ref["jac_mag"], rep)
+    gate("hess", host(hv), ref["hess"], ref["hess_mag"], rep)
+    # the single-output calls give bit-identical values to the fused call
+    assert np.array_equal(host(H.eval_obj(x)), host(f))
+    assert np.array_equal(host(H.eval_cons(x)), host(c))
+    assert np.array_equal(host(H.eval_grad(x)), host(g))
+    assert np.array_equal(host(H.jac_coo_values(x)), host(jv))
+    assert np.array_equal(host(H.hess_coo_values(x, y, sigma)), host(hv))
+    if products:
+        o, m = O.jprod(P, d["x"], d["vn"], shadow=True)
+        gate("jprod", host(H.jprod(x, vn)), o, m, rep)
+        o, m = O.jtprod(P, d["x"], d["vm"], shadow=True)
+        gate("jtprod", host(H.jtprod(x, vm)), o, m, rep)
+        o, m = O.hprod(P, d["x"], d["y"], 0.75, d["vn"], shadow=True)
+        gate("hprod", host(H.hprod(x, y, 0.75, vn)), o, m, rep)
+    H.close()
+    return rep
+
+
+SMALL = [("vdp_n1e3", N) for N in (1, 2, 3, 254, 255, 256, 510, 1000, 1777)] + \
+        [("cartpole_n1e5", N) for N in (1, 2, 126, 127, 128, 1000, 1303)] + \
+        [("heat_n2e4", N) for N in (1, 2, 30, 31, 32, 100, 333)] + \
+        [("dint", N) for N in (1, 2, 100, 997)]
+
+
+@pytest.mark.parametrize("name,N", SMALL)
+def test_parity_small_horizons(ocp, name, N):
+    full_check(ocp, synth.with_horizon(synth.workload(name), N))
+
+
+def test_parity_vdp_mu_variants(ocp):
+    w = dict(synth.with_horizon(synth.workload("vdp_n1e3"), 300), params=[2.5])
+    full_check(ocp, w)
+
+
+def test_parity_reference_offsets(ocp):
+    """Non-zero tracking references (cart-pole with xref/uref) and sigma != 1."""
+    w = dict(synth.with_horizon(synth.workload("cartpole_n1e5"), 400), xref=[0.1, -0.2, 0.3, 0.0], uref=[1.5],
+             sigma=0.3, r=[0.25])
+    full_check(ocp, w)
+
+
+def test_parity_cost_structure_follows_weights(ocp):
+    """A zero cost weight drops a diagonal Hessian entry that the dynamics do not need."""
+    w = dict(synth.with_horizon(synth.workload("vdp_n1e3"), 50), q=[1.0, 0.0])
+    full_check(ocp, w)
+
+
+@pytest.mark.parametrize("name", ["vdp_n1e3", "cartpole_n1e5", "heat_n2e4", "vdp_mu_n1e6"])
+def test_parity_full_size_workloads(ocp, name):
+    rep = full_check(ocp, synth.workload(name), products=(name != "vdp_mu_n1e6"))
+    print(name, rep)
+
+
+def test_every_slot_written_once_and_nothing_beyond(ocp):
+    """NaN-prefilled outputs with guard words after the end: every slot gets a finite value
+    and no guard word changes."""
+    w = synth.with_horizon(synth.workload("cartpole_n1e5"), 1000)
+    d = synth.draw(w)
+    H = ocp.OCP.from_workload(w)
+    G = 64
+    bufs = {k: torch.full((sz + G,), float("nan"), dtype=torch.float64, device="cuda")
+            for k, sz in dict(f=1, c=H.m, g=H.n, j=H.nnzj, h=H.nnzh).items()}
+    for b in bufs.values():
+        b[-G:] = 12345.5
+    x, y = dev(d["x"]), dev(d["y"])
+    H.eval_all(x, y, 1.0, bufs["f"][:1], bufs["c"][:H.m], bufs["g"][:H.n], bufs["j"][:H.nnzj],
+               bufs["h"][:H.nnzh], alloc=False)
+    torch.cuda.synchronize()
+    for k, b in bufs.items():
+        assert torch.isfinite(b[:-G]).all(), k
+        assert (b[-G:] == 12345.5).all(), k
+
+
+def test_deterministic_run_to_run(ocp):
+    w = synth.with_horizon(synth.workload("vdp_n1e3"), 100000)
+    d = synth.draw(w)
+    H = ocp.OCP.from_workload(w)
+    x, y = dev(d["x"]), dev(d["y"])
+    a = [host(t) for t in H.eval_all(x, y, 1.0)]
+    b = [host(t) for t in H.eval_all(x, y, 1.0)]
+    for u, v in zip(a, b):
+        assert np.array_equal(u, v)
+
+
+@pytest.mark.parametrize("name,N,S", [("vdp_n1e3", 5000, 3), ("cartpole_n1e5", 2000, 4), ("heat_n2e4", 500, 3),
+                                      ("dint", 300, 2)])
+def test_virtual_shards_match_unsharded(ocp, name, N, S):
+    """S contiguous node shards, each reading a one-node halo, reproduce the unsharded
+    evaluation slot for slot; the objective is the sum of the shard partials."""
+    w = synth.with_horizon(synth.workload(name), N)
+    d = synth.draw(w)
+    H = ocp.OCP.from_workload(w)
+    x, y = dev(d["x"]), dev(d["y"])
+    f0, c0, g0, j0, h0 = H.eval_all(x, y, 1.0)
+    c = torch.full_like(c0, float("nan")); g = torch.full_like(g0, float("nan"))
+    j = torch.full_like(j0, float("nan")); h = torch.full_like(h0, float("nan"))
+    cuts = np.linspace(0, N + 1, S + 1).astype(int)
+    parts = []
+    for s in range(S):
+        f = torch.zeros(1, dtype=torch.float64, device="cuda")
+        H.eval_all_range(cuts[s], cuts[s + 1], x, y, 1.0, f, c, g, j, h)
+        parts.append(f)
+    torch.cuda.synchronize()
+    for u, v in [(c, c0), (g, g0), (j, j0), (h, h0)]:
+        assert torch.equal(u, v)
+    total = sum(float(p) for p in parts)
+    assert abs(total - float(f0)) <= 1e-12 * abs(float(f0))
+
+
+def test_dimension_and_argument_errors(ocp):
+    w = synth.with_horizon(synth.workload("vdp_n1e3"), 10)
+    H = ocp.OCP.from_workload(w)
+    with pytest.raises(ValueError):
+        H.eval_cons(torch.zeros(5, dtype=torch.float64, device="cuda"))
+    with pytest.raises(TypeError):
+        H.eval_cons(torch.zeros(H.n, dtype=torch.float32, device="cuda"))
+    import ctypes as C
+    x = torch.zeros(H.n + 1, dtype=torch.float64, device="cuda")
+    c = torch.zeros(H.m, dtype=torch.float64, device="cuda")
+    st = ocp.lib().eval_cons(H.h, C.c_void_p(x.data_ptr() + 4), C.c_void_p(c.data_ptr()), None)
+    assert st == 1  # OCP_EINVAL: misaligned pointer
+    st = ocp.lib().ocp_eval_all_range(H.h, 5, 3, C.c_void_p(x.data_ptr()), None, 1.0, None, None, None, None,
+                                      None, None)
+    assert st == 2  # OCP_EDIM: empty range
