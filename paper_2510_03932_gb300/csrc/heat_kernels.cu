@@ -69,11 +69,12 @@ __global__ void __launch_bounds__(HT_THREADS) k_heat_eval(const __grid_constant_
   const bool WF = CF && a.f, WC = CC && a.c, WG = CG && a.g, WJ = CJ && a.jv, WH = CH && a.hv;
   extern __shared__ __align__(16) double sm[];
   const int n = a.n, ld = n + 1;
-  double* sX = sm;                                   // 32 * ld
-  double* sN = sX + HT_LANES * ld;                   // node-major Hessian staging, 31 * ld
-  double* sG = sN + (HT_LANES - 1) * ld;             // node-major gradient staging, 31 * ld
-  double* sJ = sG + (HT_LANES - 1) * ld;             // per-warp row buffer 8 * 31 * 6
-  double* red = sJ + HT_WARPS * (HT_LANES - 1) * 6;  // reduction
+  // shared memory: states, then only the staging buffers this variant needs
+  double* sX = sm;                                             // 32 * ld
+  double* sN = sX + HT_LANES * ld;                             // Hessian diagonal, 31 * ld
+  double* sG = sN + (CH ? (HT_LANES - 1) * ld : 0);            // gradient, 31 * ld
+  double* sJ = sG + (CG ? (HT_LANES - 1) * ld : 0);            // per-warp row buffer 8 * 31 * 6
+  double* red = sJ + (CJ ? HT_WARPS * (HT_LANES - 1) * 6 : 0); // reduction, 256
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double objacc = 0.0;
 
@@ -191,7 +192,7 @@ __global__ void __launch_bounds__(HT_THREADS) k_heat_eval(const __grid_constant_
       }
     }
     if (WF) {
-      const double ts = cta_sum<HT_THREADS>(objacc, red);
+      const double ts = tile_sum<HT_THREADS>(objacc, red);
       if (threadIdx.x == 0) a.partials[tile] = ts;
       objacc = 0.0;
     }
@@ -260,6 +261,7 @@ __global__ void __launch_bounds__(HT_THREADS) k_heat_local(const __grid_constant
   for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
     const int64_t r0 = tile * HT_LANES;
     const int nn = (int)min((int64_t)HT_LANES, a.N + 1 - r0);
+    const bool bnd = (tile == 0) || (r0 + HT_LANES > a.N);
     const int t = lane;
     const int64_t j = r0 + t;
     const bool act = t < nn;
@@ -277,11 +279,12 @@ __global__ void __launch_bounds__(HT_THREADS) k_heat_local(const __grid_constant
           wl = (j >= 1) ? __ldg(row + j - 1) : 0.0;
           wr = (j < a.N) ? __ldg(row + j) : 0.0;
         };
-        double wl, wr, wbm = 0.0, wbc, wbp = 0.0, wlc, wrc;
+        double wbm = 0.0, wbc = 0.0, wbp = 0.0, wlc = 0.0, wrc = 0.0;
         if (act) {
           if (k0 > 0) { double l2, r2; wbar(k0 - 1, l2, r2); wbm = l2 + r2; }
           wbar(k0, wlc, wrc);
           wbc = wlc + wrc;
+          if (k0 == 0) sV[t * ld + n] = a.mhidx2 * wbc;  // control column: -hh/dx^2 wbar_0
         }
         for (int k = k0; k < k1; ++k) {
           if (act) {
@@ -292,10 +295,11 @@ __global__ void __launch_bounds__(HT_THREADS) k_heat_local(const __grid_constant
             const double dk = fma(a.h3, xk * xk, last ? a.d_last : a.d_in);
             double s = fma(wbc, dk, wlc - wrc);
             s = fma(a.mhidx2, wbm + wbp, s);
-            if (j == 0) s += __ldg(a.v + k);
-            if (a.has_final && j == a.N) s += __ldg(a.v + n + k);
+            if (bnd) {  // only the CTAs holding node 0 or node N (uniform branch)
+              if (j == 0) s += __ldg(a.v + k);
+              if (a.has_final && j == a.N) s += __ldg(a.v + n + k);
+            }
             sV[t * ld + k] = s;
-            if (k == 0) sV[t * ld + n] = a.mhidx2 * wbc;
             wbm = wbc; wbc = wbp; wlc = wlp; wrc = wrp;
           }
         }
@@ -374,8 +378,9 @@ static ocp_status heat_eval_t(ocp* h, const EvalCall& c, cudaStream_t s) {
   a.ntiles = (nodes + (HT_LANES - 2)) / (HT_LANES - 1);
   if (a.ntiles < 1) a.ntiles = 1;
   const int ld = h->nx + 1;
-  const size_t smem = sizeof(double) * ((size_t)HT_LANES * ld + 2 * (HT_LANES - 1) * ld +
-                                        HT_WARPS * (HT_LANES - 1) * 6 + HT_WARPS + 1);
+  const size_t smem = sizeof(double) * ((size_t)HT_LANES * ld + ((OUT & O_H) ? (HT_LANES - 1) * ld : 0) +
+                                        ((OUT & O_G) ? (HT_LANES - 1) * ld : 0) +
+                                        ((OUT & O_J) ? HT_WARPS * (HT_LANES - 1) * 6 : 0) + HT_THREADS);
   auto kern = k_heat_eval<OUT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_err(h, e, "cudaFuncSetAttribute(heat)");
@@ -402,7 +407,7 @@ ocp_status heat_prod(ocp* h, const ProdCall& c, cudaStream_t s) {
   heat_fill(h, c.sigma, a);
   a.x = c.x; a.y = c.y; a.v = c.v; a.out = c.out;
   const int ld = h->nx + 1;
-  const size_t smem = sizeof(double) * (size_t)HT_LANES * ld * 2;
+  const size_t smem = sizeof(double) * (size_t)HT_LANES * ld * 2;  // states and direction/result
   cudaError_t e;
   if (c.kind == P_JPROD) {
     a.ntiles = (h->N + 1 + (HT_LANES - 2)) / (HT_LANES - 1);

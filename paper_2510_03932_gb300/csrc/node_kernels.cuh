@@ -102,7 +102,7 @@ struct EvalSmem {
   static constexpr int R = TILE - 1;
   static constexpr int J = (OUT & O_J) ? jrow_total<M>() * R : 0;
   static constexpr int oJ = 0, oRED = oJ + J;
-  static constexpr int total = oRED + TILE / 32 + 1;
+  static constexpr int total = oRED + TILE;
   static constexpr size_t bytes = sizeof(double) * total;
 };
 
@@ -124,6 +124,23 @@ __device__ __forceinline__ double cta_sum(double v, double* red) {
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int i = 0; i < TILE / 32; ++i) s += red[i];
+  }
+  return s;
+}
+
+// Fixed-order sum of one value per thread over the CTA through shared memory: warp 0 adds
+// the TILE/32 values of each lane position, then a warp tree.  Result valid in thread 0.
+// (Cheaper on the FP64 pipe than a tree in every warp.)  `red` holds TILE doubles.
+template <int TILE>
+__device__ __forceinline__ double tile_sum(double v, double* red) {
+  red[threadIdx.x] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < 32) {
+    s = red[threadIdx.x];
+#pragma unroll
+    for (int i = 1; i < TILE / 32; ++i) s += red[threadIdx.x + 32 * i];
+    s = warp_sum(s);
   }
   return s;
 }
@@ -342,7 +359,7 @@ __global__ void __launch_bounds__(TILE) k_node_eval(const __grid_constant__ Node
       }
     }
     if (sF) {
-      const double ts = cta_sum<TILE>(objterm, sm + S::oRED);
+      const double ts = tile_sum<TILE>(objterm, sm + S::oRED);
       if (t == 0) a.partials[tile] = ts;
     }
     if (WC || WJ || WF) __syncthreads();
@@ -351,7 +368,7 @@ __global__ void __launch_bounds__(TILE) k_node_eval(const __grid_constant__ Node
 }
 
 // ======================================================================================
-// Jv.  Row (k,j) = (p_k(j) - v_{X_j,k}) + (p_k(j+1) + v_{X_{j+1},k}),
+// Jv.  Row (k,j) = (p_k(j) - v_{X_j,k}) + (p_k(j+1) + v_{X_{j+1},k}),  (B(j) + A(j+1)),
 // p_k(j) = -hh grad f_k(z_j) . v_{z_j}  (+ -hh df_k/dmu(z_j) * pdir for the parameter).
 // Same overlapping tiles as the evaluation; the right-node term comes from lane+1.
 // ======================================================================================
@@ -387,23 +404,29 @@ __global__ void __launch_bounds__(TILE) k_node_jprod(const __grid_constant__ Nod
       if (PDIR) M::dparam(K, z, mdp);
 #pragma unroll
       for (int k = 0; k < NX; ++k) {
+        // terms c_i * v_i of p_k in template order; the last one is fused into both
+        // A = p + v_{X_j,k} and B = p - v_{X_j,k}
+        double cf[M::MAXRX + M::MAXRU + 1], vv[M::MAXRX + M::MAXRU + 1];
+        int nt = 0;
+#pragma unroll
+        for (int e = 0; e < M::RX(k); ++e)
+          if (!M::JZ(k, e)) { cf[nt] = mjx[k][e]; vv[nt] = vz[M::XV(k, e)]; ++nt; }
+#pragma unroll
+        for (int e = 0; e < M::RU(k); ++e) { cf[nt] = mju[k][e]; vv[nt] = vz[NX + M::UV(k, e)]; ++nt; }
+        if (PDIR) { cf[nt] = mdp[k]; vv[nt] = pd; ++nt; }
         double s = 0.0;
-        bool first = true;
 #pragma unroll
-        for (int e = 0; e < M::RX(k); ++e) {
-          if (!M::JZ(k, e)) {
-            s = first ? mjx[k][e] * vz[M::XV(k, e)] : fma(mjx[k][e], vz[M::XV(k, e)], s);
-            first = false;
-          }
+        for (int i = 0; i + 1 < nt; ++i) s = (i == 0) ? cf[i] * vv[i] : fma(cf[i], vv[i], s);
+        if (nt == 0) {
+          A[k] = vx[k];
+          p[k] = -vx[k];
+        } else if (nt == 1) {
+          A[k] = fma(cf[0], vv[0], vx[k]);
+          p[k] = fma(cf[0], vv[0], -vx[k]);
+        } else {
+          A[k] = fma(cf[nt - 1], vv[nt - 1], s + vx[k]);
+          p[k] = fma(cf[nt - 1], vv[nt - 1], s - vx[k]);
         }
-#pragma unroll
-        for (int e = 0; e < M::RU(k); ++e) {
-          s = first ? mju[k][e] * vz[NX + M::UV(k, e)] : fma(mju[k][e], vz[NX + M::UV(k, e)], s);
-          first = false;
-        }
-        if (PDIR) s = fma(mdp[k], pd, s);
-        p[k] = s;
-        A[k] = s + vx[k];
       }
       if (j == 0) {
 #pragma unroll
@@ -425,7 +448,7 @@ __global__ void __launch_bounds__(TILE) k_node_jprod(const __grid_constant__ Nod
 #pragma unroll
       for (int k = 0; k < NX; ++k) {
         const double right = (lane == 31) ? sEdge[(warp + 1) * NX + k] : nbv[k];
-        a.out[a.nb + (int64_t)k * a.N + j] = (p[k] - vx[k]) + right;
+        a.out[a.nb + (int64_t)k * a.N + j] = p[k] + right;
       }
     }
     __syncthreads();
@@ -441,12 +464,13 @@ template <class M, int TILE, bool DPAR>
 __global__ void __launch_bounds__(TILE) k_node_jtprod(const __grid_constant__ NodeArgs<M> a) {
   constexpr int NX = M::NX, NZ = M::NZ;
   constexpr int NHD = (M::NHD > 0) ? M::NHD : 1;
-  __shared__ double red[TILE / 32 + 1];
+  __shared__ double red[TILE];
   ModelConst K = a.K;
   if (a.p0_dev) M::device_param(K, __ldg(a.p0_dev));
   const int64_t nchunks = (a.N + TILE) / TILE;
   for (int64_t chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
     const int64_t j = chunk * TILE + threadIdx.x;
+    const bool bnd = (chunk == 0) || (chunk == nchunks - 1);
     double acc_mu = 0.0;
     if (j <= a.N) {
       double z[NZ], yb[NX], cqd[NZ], pa[NX], pb[NX], mjx[NX][M::MAXRX], mju[NX][M::MAXRU], hd[NHD];
@@ -462,8 +486,10 @@ __global__ void __launch_bounds__(TILE) k_node_jtprod(const __grid_constant__ No
 #pragma unroll
           for (int e = 0; e < M::RX(k); ++e)
             if (M::XV(k, e) == v && !M::JZ(k, e)) s = fma(wb[k], mjx[k][e], s);
-        if (j == 0) s += __ldg(a.v + v);
-        if (a.has_final && j == a.N) s += __ldg(a.v + NX + v);
+        if (bnd) {  // only the CTAs holding node 0 or node N (uniform branch)
+          if (j == 0) s += __ldg(a.v + v);
+          if (a.has_final && j == a.N) s += __ldg(a.v + NX + v);
+        }
         a.out[NX * j + v] = s;
       }
 #pragma unroll
@@ -486,8 +512,9 @@ __global__ void __launch_bounds__(TILE) k_node_jtprod(const __grid_constant__ No
       }
     }
     if (DPAR) {
-      const double ts = cta_sum<TILE>(acc_mu, red);
+      const double ts = tile_sum<TILE>(acc_mu, red);
       if (threadIdx.x == 0) a.partials[chunk] = ts;
+      __syncthreads();
     }
   }
   if (DPAR) finish_tiles<TILE>(a.partials, nchunks, a.counter, a.dmu, 1.0, red);
@@ -503,7 +530,7 @@ __global__ void __launch_bounds__(TILE) k_node_hprod(const __grid_constant__ Nod
   constexpr int NX = M::NX, NZ = M::NZ;
   constexpr int NHD = (M::NHD > 0) ? M::NHD : 1;
   constexpr HTmpl<M> HT{};
-  __shared__ double red[TILE / 32 + 1];
+  __shared__ double red[TILE];
   ModelConst K = a.K;
   if (a.p0_dev) M::device_param(K, __ldg(a.p0_dev));
   double ms = 0.0;
@@ -556,8 +583,9 @@ __global__ void __launch_bounds__(TILE) k_node_hprod(const __grid_constant__ Nod
       for (int i = 0; i < M::NU; ++i) a.out[a.uoff + M::NU * j + i] = o[NX + i];
     }
     if (MIX && a.dmu) {
-      const double ts = cta_sum<TILE>(acc_mu, red);
+      const double ts = tile_sum<TILE>(acc_mu, red);
       if (threadIdx.x == 0) a.partials[chunk] = ts;
+      __syncthreads();
     }
   }
   if (MIX && a.dmu) finish_tiles<TILE>(a.partials, nchunks, a.counter, a.dmu, 1.0, red);
