@@ -139,6 +139,24 @@ ocp_status ocp_eval_all_range(ocp_t* h, int64_t node_begin, int64_t node_end, co
                               const double* y, double sigma, double* f, double* c, double* g,
                               double* jvals, double* hvals, void* stream);
 
+/* Objective F(x) without any device allocation, for callers that cannot call cudaMalloc at
+ * evaluation time: a real-time control loop that must not allocate after start-up (cudaMalloc
+ * can synchronize the device and its latency is unbounded), or a framework whose allocator
+ * owns all device memory.  The paper has no counterpart: its evaluator owns its buffers.
+ * Arguments: the problem description of ocp_create (host pointers, copied) instead of a handle;
+ * x (length (nx+nu)(N+1)) and f (one double) are device pointers, as in eval_obj; the call is
+ * asynchronous on `stream`.  The reduction scratch is a file-scope device array of 65536
+ * tiles (about 512 KB on every device that loads the library, held until the process exits);
+ * a horizon needing more tiles (N+1 above 65536 x 255 nodes for Van der Pol and the double
+ * integrator, x 127 for the cart-pole, x 31 for the heat model) returns OCP_EDIM without
+ * launching.  The first call on a device looks up the array's device address with that device
+ * current; make that first call before any stream capture.  Every call on a device shares the
+ * array and the last call's contents stay in it: calls that overlap on the GPU race.  Errors
+ * as ocp_create and eval_obj, reported by ocp_last_error(NULL).  Calls neither cudaMalloc nor
+ * cudaFree. */
+ocp_status ocp_eval_obj_noalloc(const ocp_dynamics* dyn, const ocp_cost* cost, int nx, int nu, int64_t N,
+                                double T, const double* x, double* f, void* stream);
+
 /* Message of the last failure on this handle (NULL: of the last failed create). */
 const char* ocp_last_error(const ocp_t* h);
 

@@ -35,6 +35,18 @@ int occupancy_grid(ocp* h, const void* kernel, int threads, size_t smem, int64_t
   return (int)work_tiles;
 }
 
+int64_t objective_tiles(int model, int64_t nodes) {
+  int owned = 0;
+  switch (model) {
+    case OCP_MODEL_VDP: owned = TILE_VDP - 1; break;
+    case OCP_MODEL_CARTPOLE: owned = TILE_CARTPOLE - 1; break;
+    case OCP_MODEL_DINT: owned = TILE_DINT - 1; break;
+    case OCP_MODEL_HEAT1D: owned = HEAT_TILE_NODES - 1; break;
+    default: return -1;
+  }
+  return (nodes + owned - 1) / owned;
+}
+
 }  // namespace ocpg
 
 // ---------------------------------------------------------------------------------------
@@ -84,12 +96,10 @@ static void free_handle(ocp* h) {
   delete h;
 }
 
-extern "C" {
+namespace ocpg {
 
-ocp_status ocp_create(const ocp_dynamics* dyn, const ocp_cost* cost, int nx, int nu, int64_t N, double T,
-                      ocp_t** out) {
-  if (!out) return set_err(nullptr, OCP_EINVAL, "out is NULL");
-  *out = nullptr;
+// Host part of ocp_create: validation, parameters and the pattern; no device work.
+ocp_status init_host(ocp* h, const ocp_dynamics* dyn, const ocp_cost* cost, int nx, int nu, int64_t N, double T) {
   if (!dyn || !cost) return set_err(nullptr, OCP_EINVAL, "dynamics or cost is NULL");
   const int np = model_nparams(dyn->model);
   if (np < 0) return set_err(nullptr, OCP_EMODEL, "unknown model id");
@@ -113,8 +123,6 @@ ocp_status ocp_create(const ocp_dynamics* dyn, const ocp_cost* cost, int nx, int
   if (N < 1) return set_err(nullptr, OCP_EDIM, "N must be >= 1");
   if (!(T > 0.0) || !std::isfinite(T)) return set_err(nullptr, OCP_EINVAL, "T must be positive and finite");
   if (!cost->q || !cost->r) return set_err(nullptr, OCP_EINVAL, "cost weights q and r are required");
-  ocp* h = new (std::nothrow) ocp();
-  if (!h) return set_err(nullptr, OCP_ENOMEM, "host allocation failed");
   h->model = dyn->model; h->nx = nx; h->nu = nu; h->N = N; h->T = T;
   h->h = T / (double)N;
   h->hh = h->h / 2.0;
@@ -130,7 +138,24 @@ ocp_status ocp_create(const ocp_dynamics* dyn, const ocp_cost* cost, int nx, int
   for (double v : h->uref) if (v != 0.0) h->has_ref = true;
   h->x0.assign(nx, 0.0);
   std::string why;
-  if (!build_pattern(h, why)) { free_handle(h); return set_err(nullptr, OCP_EDIM, why); }
+  if (!build_pattern(h, why)) return set_err(nullptr, OCP_EDIM, why);
+  return OCP_OK;
+}
+
+}  // namespace ocpg
+
+extern "C" {
+
+ocp_status ocp_create(const ocp_dynamics* dyn, const ocp_cost* cost, int nx, int nu, int64_t N, double T,
+                      ocp_t** out) {
+  if (!out) return set_err(nullptr, OCP_EINVAL, "out is NULL");
+  *out = nullptr;
+  ocp* h = new (std::nothrow) ocp();
+  if (!h) return set_err(nullptr, OCP_ENOMEM, "host allocation failed");
+  {
+    ocp_status st = init_host(h, dyn, cost, nx, nu, N, T);
+    if (st != OCP_OK) { delete h; return st; }
+  }
   cudaError_t e;
   if ((e = cudaGetDevice(&h->device)) != cudaSuccess) { free_handle(h); return cuda_err(nullptr, e, "cudaGetDevice"); }
   if ((e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device)) != cudaSuccess) {
@@ -197,7 +222,7 @@ ocp_status ocp_bounds(const ocp_t* h, double* lvar, double* uvar, double* lcon, 
 
 }  // extern "C"
 
-static ocp_status dispatch_eval(ocp* h, unsigned out, const EvalCall& c, void* stream) {
+ocp_status ocpg::dispatch_eval(ocp* h, unsigned out, const EvalCall& c, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   switch (h->model) {
     case OCP_MODEL_VDP: return node_eval_vdp(h, out, c, s);

@@ -23,7 +23,7 @@
 namespace ocpg {
 
 constexpr int HEAT_MAXC = 128;
-constexpr int HT_LANES = 32;
+constexpr int HT_LANES = HEAT_TILE_NODES;
 constexpr int HT_WARPS = 8;
 constexpr int HT_THREADS = HT_LANES * HT_WARPS;
 

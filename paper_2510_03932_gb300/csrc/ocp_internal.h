@@ -11,6 +11,11 @@
 
 namespace ocpg {
 
+// Threads (= nodes) per CTA of the node-model kernels; a tile owns TILE-1 nodes.
+constexpr int TILE_VDP = 256, TILE_CARTPOLE = 128, TILE_DINT = 256;
+// Nodes per CTA of the heat-equation kernels (one per lane); a tile owns 31 nodes.
+constexpr int HEAT_TILE_NODES = 32;
+
 // Output selection bits of the fused evaluation kernels.
 enum : unsigned { O_F = 1u, O_C = 2u, O_G = 4u, O_J = 8u, O_H = 16u, O_ALL = 31u };
 
@@ -81,6 +86,8 @@ int occupancy_grid(ocp* h, const void* kernel, int threads, size_t smem, int64_t
 
 // Host pattern compiler.
 bool build_pattern(ocp* h, std::string& why);
+// Host part of ocp_create (validation, parameters, pattern); no device allocation.
+ocp_status init_host(ocp* h, const ocp_dynamics* dyn, const ocp_cost* cost, int nx, int nu, int64_t N, double T);
 
 struct EvalCall {
   const double* x = nullptr;
@@ -116,6 +123,11 @@ ocp_status node_prod_cartpole(ocp* h, const ProdCall& c, cudaStream_t s);
 ocp_status node_prod_dint(ocp* h, const ProdCall& c, cudaStream_t s);
 ocp_status heat_eval(ocp* h, unsigned out, const EvalCall& c, cudaStream_t s);
 ocp_status heat_prod(ocp* h, const ProdCall& c, cudaStream_t s);
+
+struct EvalCall;
+ocp_status dispatch_eval(ocp* h, unsigned out, const EvalCall& c, void* stream);
+// Tiles of the objective reduction for a problem of this model and horizon.
+int64_t objective_tiles(int model, int64_t nodes);
 
 ocp_status launch_jac_structure(const ocp* h, int32_t* rows, int32_t* cols, cudaStream_t s);
 ocp_status launch_hess_structure(const ocp* h, int32_t* rows, int32_t* cols, cudaStream_t s);
