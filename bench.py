@@ -64,6 +64,18 @@ def _counts(w):
     return _COUNT_CACHE[key]
 
 
+# FP64 instructions (DFMA, DADD, DMUL per thread) each kernel executes per node, counted from
+# the kernel source and equal to ncu's sm__sass_thread_inst_executed_op_{dfma,dadd,dmul}
+# counts divided by N+1 (Van der Pol: the objective's tile reduction adds 1.5 per node).
+FP64_OPS_PER_NODE = {("vdp", "eval_all"): 26.5, ("vdp", "jh"): 10.0, ("vdp", "jprod"): 14.0,
+                     ("vdp", "jtprod"): 12.0, ("vdp", "hprod"): 11.0}
+# DRAM bytes (read + write) of one launch, from an ncu capture of the same kernel (see
+# profiles/); None until captured for the current kernel version.
+TRAFFIC = {}
+FP64_INST_PER_CLK_PER_SM = 2.0   # measured: DFMA throughput of one SM (DADD/DMUL are ~15% slower)
+NUM_SMS = 152
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -227,6 +239,10 @@ def run_ours(args, rank, world):
     hbm, peak_kind = peaks()
     ab = algorithmic_bytes(w, "eval_all")
     achieved = ab / (kern_ms[0] * 1e-3) / 1e9
+    clk = (clocks or {}).get("sm_mhz") or 2070.0
+    fp64_peak = FP64_INST_PER_CLK_PER_SM * NUM_SMS * clk * 1e6 / 1e9   # G FP64 inst/s
+    ops = FP64_OPS_PER_NODE.get((w["model"], "eval_all"))
+    fp64_ach = ops * (w["N"] + 1) / (kern_ms[0] * 1e-3) / 1e9 if ops else None
     res = dict(
         metric=METRIC, value=nnz * args.steps * world / (tot_ms * 1e-3), unit="nnz/s", n_gpus=world,
         steps=args.steps, warmup=args.warmup, ms_per_step=tot_ms / args.steps, higher_is_better=True,
@@ -234,10 +250,18 @@ def run_ours(args, rank, world):
         config=dict(workload=args.workload, model=w["model"], N=w["N"], n=n, m=m, nnz_jac=nnzj, nnz_hess=nnzh,
                     step="eval_all(F,c,grad,J,H)+jprod+jtprod+hprod", l2="flushed between steps (512 MB write)",
                     parallelism="replicas" if world > 1 else "single"),
-        roofline=dict(bound="hbm", achieved=achieved, peak=hbm, unit="GB/s", frac=achieved / hbm, traffic=None,
-                      kernel="k_node_eval (fused eval_all)", peak_source=peak_kind,
-                      algorithmic_bytes=ab),
-        kernels={nm: dict(ms=float(kern_ms[i]), GBps=algorithmic_bytes(w, nm) / (kern_ms[i] * 1e-3) / 1e9)
+        roofline=dict(bound="alu", achieved=fp64_ach, peak=fp64_peak, unit="G FP64 inst/s",
+                      frac=(fp64_ach / fp64_peak) if fp64_ach else None, traffic=TRAFFIC.get((w["model"], "eval_all")),
+                      kernel="k_node_eval (fused eval_all)", fp64_inst_per_node=ops,
+                      peak_basis="%.0f FP64 inst/clk/SM x %d SMs x %.0f MHz (median SM clock under load)"
+                                 % (FP64_INST_PER_CLK_PER_SM, NUM_SMS, clk)),
+        roofline_hbm=dict(bound="hbm", achieved=achieved, peak=hbm, unit="GB/s", frac=achieved / hbm,
+                          peak_source=peak_kind, algorithmic_bytes=ab,
+                          traffic=TRAFFIC.get((w["model"], "eval_all"))),
+        kernels={nm: dict(ms=float(kern_ms[i]), GBps=algorithmic_bytes(w, nm) / (kern_ms[i] * 1e-3) / 1e9,
+                          hbm_frac=algorithmic_bytes(w, nm) / (kern_ms[i] * 1e-3) / 1e9 / hbm,
+                          fp64_frac=(FP64_OPS_PER_NODE[(w["model"], nm)] * (w["N"] + 1) / (kern_ms[i] * 1e-3) / 1e9
+                                     / fp64_peak) if (w["model"], nm) in FP64_OPS_PER_NODE else None)
                  for i, nm in enumerate(names)},
         jac_hess_only=dict(ms=jh_ms, nnz_per_s=nnz / (jh_ms * 1e-3),
                            GBps=algorithmic_bytes(w, "jh") / (jh_ms * 1e-3) / 1e9,
@@ -247,6 +271,99 @@ def run_ours(args, rank, world):
         gpu_launches=4 * args.steps, clocks=clocks, wall_s=wall,
     )
     return res
+
+
+def run_forms(args, hbm):
+    """The batched and differentiation forms, each against the plain evaluator on this GPU."""
+    import torch
+    from paper_2510_03932_gb300 import autograd as A
+    from paper_2510_03932_gb300 import ocp
+
+    out = {}
+    # ---- batched: 256 cart-pole instances, N ~ U{500..50000}, one persistent launch in a graph
+    ws = synth.batch_workloads()
+    probs = [ocp.OCP.from_workload(w) for w in ws]
+    B = ocp.OCPBatch(probs)
+    draws = [synth.draw(w) for w in ws]
+    x = torch.from_numpy(np.concatenate([d["x"] for d in draws])).cuda()
+    y = torch.from_numpy(np.concatenate([d["y"] for d in draws])).cuda()
+    del draws
+    f, c, g, jv, hv = B.outputs()
+    best = B.autotune(x, y, 1.0, f, None, g, jv, hv)
+    cfg = B.get_config()
+    s = torch.cuda.Stream()
+    B.graph_capture(x, y, 1.0, f, None, g, jv, hv, stream=s)
+    reps = 20
+    for _ in range(3):
+        B.graph_launch(stream=s)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(reps):
+        B.graph_launch(stream=s)
+    e1.record(s)
+    s.synchronize()
+    t_batch = e0.elapsed_time(e1) / reps
+    # the same work as 256 separate plain calls (f, g, J, H per instance)
+    xs = [x[B.xoff[i]:B.xoff[i + 1]] for i in range(B.count)]
+    ys = [y[B.coff[i]:B.coff[i + 1]] for i in range(B.count)]
+    views = [(f[i:i + 1], g[B.xoff[i]:B.xoff[i + 1]], jv[B.joff[i]:B.joff[i + 1]], hv[B.hoff[i]:B.hoff[i + 1]])
+             for i in range(B.count)]
+
+    def plain_all():
+        for P, xi, yi, (fi, gi, ji, hi) in zip(probs, xs, ys, views):
+            P.eval_all(xi, yi, 1.0, fi, None, gi, ji, hi, alloc=False)
+    plain_all()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(5):
+        plain_all()
+    e1.record()
+    torch.cuda.synchronize()
+    t_plain = e0.elapsed_time(e1) / 5
+    nnz = B.nnzj + B.nnzh
+    byts = 8 * (B.n + B.m + B.count + B.n + B.nnzj + B.nnzh)
+    out["batched"] = dict(workload="256 cart-pole, N~U{500..50000}, seed 1004", total_nodes=int(B.n // 5),
+                          nnz=nnz, config=cfg, autotune_best_ms=best, ms=t_batch,
+                          nnz_per_s=nnz / (t_batch * 1e-3), GBps=byts / (t_batch * 1e-3) / 1e9,
+                          hbm_frac=byts / (t_batch * 1e-3) / 1e9 / hbm,
+                          plain_256_calls_ms=t_plain, speedup_vs_plain=t_plain / t_batch,
+                          outputs="f, grad, J, H per instance (graph replay of one persistent launch)")
+    del B, probs, x, y, f, c, g, jv, hv, xs, ys, views
+    torch.cuda.empty_cache()
+    # ---- differentiation: c(x; mu) forward + J^T w, (dc/dmu)^T w backward at N = 1e6
+    w = synth.workload("vdp_mu_n1e6")
+    d = synth.draw(w)
+    H = ocp.OCP.from_workload(w)
+    xg = torch.from_numpy(d["x"]).cuda().requires_grad_(True)
+    mu = torch.tensor([1.0], dtype=torch.float64, device="cuda", requires_grad=True)
+    wv = torch.from_numpy(d["vm"]).cuda()
+
+    def ad_step():
+        cc = A.constraints(H, xg, mu)
+        return torch.autograd.grad(cc, (xg, mu), grad_outputs=wv)
+
+    def plain_step():
+        H.eval_cons(xg.detach())
+        H.vjp_param(xg.detach(), wv)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    res = {}
+    for nm, fn in (("autograd", ad_step), ("plain", plain_step)):
+        for _ in range(3):
+            fn()
+        ts = []
+        for _ in range(20):
+            flush.zero_()
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record()
+            fn()
+            a1.record()
+            ts.append((a0, a1))
+        torch.cuda.synchronize()
+        res[nm] = float(np.median([a.elapsed_time(b) for a, b in ts]))
+    out["adjoint"] = dict(workload="vdp_mu_n1e6", step="c(x;mu) forward + (J^T w, dc/dmu^T w) backward",
+                          autograd_ms=res["autograd"], plain_ms=res["plain"],
+                          overhead=res["autograd"] / res["plain"])
+    return out
 
 
 def run_profile(args):
@@ -307,6 +424,7 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=10.0)
+    ap.add_argument("--no-forms", action="store_true", help="skip the batched and differentiation forms")
     ap.add_argument("--profile-kernel", default=None,
                     choices=["eval_all", "jh", "jprod", "jtprod", "hprod", "all"],
                     help="only launch this call warmup+steps times (for ncu captures)")
@@ -336,6 +454,8 @@ def main():
         import torch
         torch.distributed.init_process_group("nccl")
     res = run_ours(args, rank, world)
+    if rank == 0 and not args.no_forms:
+        res["forms"] = run_forms(args, res["roofline_hbm"]["peak"])
     if rank == 0:
         _, cb = oracle_step_time(synth.workload(args.workload), args.cpu_budget)
         res["cpu_baseline"] = cb

@@ -131,6 +131,24 @@ ocp_status ocp_vjp_param(ocp_t* h, const double* x, const double* w, double* Jtw
 /* Set the value of params[0] (e.g. Van der Pol mu) without rebuilding the pattern. */
 ocp_status ocp_set_param0(ocp_t* h, double value);
 
+/* Differentiation support (the autograd form; Van der Pol parameter mu = params[0]).
+ * ocp_bind_param0: later calls on this handle read mu from the device scalar p0_dev (NULL
+ *   unbinds and returns to the host value); the pointer must stay valid while bound.
+ * ocp_jprod_param: Jv = J v + (dc/dmu) s, with s a device scalar (NULL: plain jprod).
+ * ocp_hprod_param: Hv = (sigma Hess F + sum_r y_r Hess c_r) v + s sum_r y_r d2 c_r/dmu dx, and
+ *   dmu = (sum_r y_r d2 c_r / dx dmu) . v (device scalar, NULL: not computed; needs s).
+ *   s == NULL: plain hprod.  These are the second-order terms of the constraint adjoint.
+ * ocp_eval_grad_scaled: g = s grad F(x), s a device scalar (the upstream gradient).
+ * ocp_obj_hvp: Hv = s Hess F(x) v, and dot = grad F(x) . v (device scalar, may be NULL).
+ * Models without a parameter derivative return OCP_EMODEL when s or p0_dev is given. */
+ocp_status ocp_bind_param0(ocp_t* h, const double* p0_dev);
+ocp_status ocp_jprod_param(ocp_t* h, const double* x, const double* v, const double* s, double* Jv, void* stream);
+ocp_status ocp_hprod_param(ocp_t* h, const double* x, const double* y, double sigma, const double* v,
+                           const double* s, double* Hv, double* dmu, void* stream);
+ocp_status ocp_eval_grad_scaled(ocp_t* h, const double* x, const double* s, double* g, void* stream);
+ocp_status ocp_obj_hvp(ocp_t* h, const double* x, const double* s, const double* v, double* Hv, double* dot,
+                       void* stream);
+
 /* Evaluate only the nodes [node_begin, node_end) (and the defect rows j in that range) of
  * eval_all, writing into the full-size output arrays.  Used to split one problem into
  * contiguous node shards (each shard reads a one-node halo of x and y).  f receives this
@@ -160,22 +178,37 @@ ocp_status ocp_eval_obj_noalloc(const ocp_dynamics* dyn, const ocp_cost* cost, i
 /* Message of the last failure on this handle (NULL: of the last failed create). */
 const char* ocp_last_error(const ocp_t* h);
 
-/* Batched form: `count` problems of the same model, possibly different N, cost weights and
- * boundary values, evaluated by one persistent launch over the concatenated node space.
- * The handles must stay alive while the batch is used.  Variables, constraints and nonzeros
- * of instance i start at the offsets returned by ocp_batch_offsets (prefix sums), each
- * instance laid out exactly as its own handle.  Errors: OCP_EMODEL for mixed models or a
- * model the batched kernel does not provide. */
+/* Batched form (many problems of one model, possibly different N, cost weights and boundary
+ * values, in ONE persistent launch).  Provided for the cart-pole and Van der Pol models;
+ * others return OCP_EMODEL.  The handles must stay alive while the batch is used.
+ * Variables, constraints, Jacobian and Hessian values of instance i start at the prefix
+ * offsets given by ocp_batch_offsets (host arrays of length count+1 for x/g, y/c, jac values,
+ * hess values), each instance laid out exactly as for its own handle: its slices are
+ * bit-identical to the plain evaluator's; its objective goes to f[i] (device, length count).
+ * Any output may be NULL (not stored); y is required with Hessian values.
+ * Launch configuration: threads per CTA (64, 128, 256), nodes per thread (1 or 2: 32 or 64
+ * nodes per warp), CTAs per SM of the persistent grid (0: as many as fit).
+ * ocp_batch_autotune times every configuration on the caller's data (synchronizes the
+ * stream) and keeps the fastest; best_ms (host, may be NULL) receives its time.
+ * ocp_batch_graph_capture records one ocp_batch_eval_all launch with these arguments in a
+ * CUDA graph (stream must be a created stream, not the legacy default one);
+ * ocp_batch_graph_launch replays it.  Changing the configuration drops the graph. */
 ocp_status ocp_batch_create(ocp_t* const* items, int count, ocp_batch_t** out);
 void ocp_batch_destroy(ocp_batch_t* b);
-/* Host arrays of length count+1: offsets into x, y/c, g, jac values, hess values. */
 ocp_status ocp_batch_offsets(const ocp_batch_t* b, int64_t* xoff, int64_t* coff, int64_t* joff,
                              int64_t* hoff);
-/* Launch configuration: nodes handled per thread (1 or 2) and threads per CTA (128..1024). */
-ocp_status ocp_batch_set_config(ocp_batch_t* b, int nodes_per_thread, int threads);
-/* Per-instance objective values go to f[count]. */
+ocp_status ocp_batch_set_config(ocp_batch_t* b, int nodes_per_thread, int threads, int ctas_per_sm);
+ocp_status ocp_batch_get_config(const ocp_batch_t* b, int* nodes_per_thread, int* threads, int* ctas_per_sm);
 ocp_status ocp_batch_eval_all(ocp_batch_t* b, const double* x, const double* y, double sigma,
-                              double* f, double* g, double* jvals, double* hvals, void* stream);
+                              double* f, double* c, double* g, double* jvals, double* hvals, void* stream);
+ocp_status ocp_batch_autotune(ocp_batch_t* b, const double* x, const double* y, double sigma,
+                              double* f, double* c, double* g, double* jvals, double* hvals,
+                              void* stream, double* best_ms);
+ocp_status ocp_batch_graph_capture(ocp_batch_t* b, const double* x, const double* y, double sigma,
+                                   double* f, double* c, double* g, double* jvals, double* hvals,
+                                   void* stream);
+ocp_status ocp_batch_graph_launch(ocp_batch_t* b, void* stream);
+const char* ocp_batch_last_error(const ocp_batch_t* b);
 
 #ifdef __cplusplus
 }

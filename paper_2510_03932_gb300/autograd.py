@@ -1,0 +1,112 @@
+"""Differentiation form: torch.autograd.Functions over the transcription evaluator.
+
+  c = constraints(H, x, mu)    c(x; mu), the constraint vector (Van der Pol: mu = params[0])
+  F = objective(H, x)          the trapezoidal objective
+
+Every forward and backward step is one launch of the CUDA library; node states are
+recomputed from x in each kernel, never stored.  Derivatives:
+  constraints   backward:  (J^T w, (dc/dmu)^T w)                 ocp_vjp_param / jtprod
+                double backward, for cotangents (gx, gmu) of that pair:
+                  w-bar  = J gx + (dc/dmu) gmu                    ocp_jprod_param
+                  x-bar  = (sum_r w_r Hess c_r) gx + gmu m(x, w)   ocp_hprod_param (sigma = 0)
+                  mu-bar = m(x, w) . gx                            (same launch)
+                where m(x, w) = sum_r w_r d2 c_r / dx dmu  (c is linear in mu: d2c/dmu2 = 0)
+  objective     backward:  s grad F(x)                             ocp_eval_grad_scaled
+                double backward:  x-bar = s Hess F gx,  s-bar = grad F . gx   ocp_obj_hvp
+mu and the upstream scalars stay on the device: the kernels read them through pointers.
+"""
+from __future__ import annotations
+
+import torch
+
+from .ocp import OCP
+
+
+def _zero_scalar(like):
+    return torch.zeros(1, dtype=torch.float64, device=like.device)
+
+
+class _ConsVJP(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, H: OCP, x, mu, w):
+        ctx.H = H
+        ctx.save_for_backward(x, mu, w)
+        w = w.contiguous()
+        if H.model == "vdp":
+            with H.param0(mu.reshape(1)):
+                gx, gmu = H.vjp_param(x, w)
+            return gx, gmu.reshape(mu.shape)
+        return H.jtprod(x, w), torch.zeros_like(mu)
+
+    @staticmethod
+    def backward(ctx, ggx, ggmu):
+        H = ctx.H
+        x, mu, w = ctx.saved_tensors
+        ggx = torch.zeros_like(x) if ggx is None else ggx.contiguous()
+        if H.model == "vdp":
+            s = _zero_scalar(x) if ggmu is None else ggmu.reshape(1).contiguous()
+            dmu = torch.empty(1, dtype=torch.float64, device=x.device)
+            with H.param0(mu.reshape(1)):
+                dw = H.jprod_param(x, ggx, s)
+                dx = H.hprod_param(x, w.contiguous(), 0.0, ggx, s, dmu=dmu)
+            return None, dx, dmu.reshape(mu.shape), dw
+        dw = H.jprod(x, ggx)
+        dx = H.hprod(x, w.contiguous(), 0.0, ggx)
+        return None, dx, torch.zeros_like(mu), dw
+
+
+class _Constraints(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, H: OCP, x, mu):
+        ctx.H = H
+        ctx.save_for_backward(x, mu)
+        if H.model == "vdp":
+            with H.param0(mu.reshape(1)):
+                return H.eval_cons(x)
+        return H.eval_cons(x)
+
+    @staticmethod
+    def backward(ctx, gc):
+        x, mu = ctx.saved_tensors
+        gx, gmu = _ConsVJP.apply(ctx.H, x, mu, gc.contiguous())
+        return None, gx, gmu
+
+
+class _ObjGrad(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, H: OCP, x, s):
+        ctx.H = H
+        ctx.save_for_backward(x, s)
+        return H.eval_grad_scaled(x, s.reshape(1).contiguous())
+
+    @staticmethod
+    def backward(ctx, gg):
+        x, s = ctx.saved_tensors
+        dot = torch.empty(1, dtype=torch.float64, device=x.device)
+        dx = ctx.H.obj_hvp(x, s.reshape(1).contiguous(), gg.contiguous(), dot=dot)
+        return None, dx, dot.reshape(s.shape)
+
+
+class _Objective(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, H: OCP, x):
+        ctx.H = H
+        ctx.save_for_backward(x)
+        return H.eval_obj(x).reshape(())
+
+    @staticmethod
+    def backward(ctx, gF):
+        (x,) = ctx.saved_tensors
+        return None, _ObjGrad.apply(ctx.H, x, gF.reshape(1))
+
+
+def constraints(H: OCP, x: torch.Tensor, mu: torch.Tensor) -> torch.Tensor:
+    """c(x; mu) with backward J^T w (and (dc/dmu)^T w) and a double backward."""
+    if H.model == "vdp" and mu.numel() != 1:
+        raise ValueError("mu must be a one-element tensor")
+    return _Constraints.apply(H, x, mu)
+
+
+def objective(H: OCP, x: torch.Tensor) -> torch.Tensor:
+    """F(x) with backward grad F and double backward Hess F v."""
+    return _Objective.apply(H, x)

@@ -1,27 +1,405 @@
-// Batched evaluation of many problems of one model in one persistent launch.
+// Batched evaluation: many problems of one model (different horizons, cost weights and
+// boundary values) evaluated by ONE persistent launch over the concatenation of their tiles.
+//
+// Layout: instance i's variables, constraints, gradient, Jacobian and Hessian values start at
+// the prefix offsets xoff[i], coff[i], xoff[i], joff[i], hoff[i] of the concatenated arrays
+// and are laid out exactly as for its own handle, so every instance slice is bit-identical to
+// the plain evaluator's output (same per-node arithmetic; only the objective's summation
+// tiles may differ when the tile size differs).
+//
+// Work decomposition: instance i is cut into tiles of NPT*TILE nodes (owning NPT*TILE-1); the
+// tiles of all instances form one index space.  A persistent grid of (CTAs per SM) x (SMs)
+// CTAs walks it in a fixed round-robin order; a CTA maps its tile to the instance by binary
+// search over the tile prefix sums, copies that instance's argument block into shared
+// memory, and runs the same tile body as the plain kernel.  The last CTA to finish sums the
+// per-tile objective terms of each instance in tile order.  No spin waits, no value atomics.
+//
+// Tuning: threads per CTA (64, 128, 256), nodes per thread (1, 2: nodes per warp 32 or 64) and
+// CTAs per SM are chosen by ocp_batch_autotune, which times every candidate on the caller's
+// data.  ocp_batch_graph_capture records one launch in a CUDA graph for cheap replay.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "node_kernels.cuh"
 #include "ocp_internal.h"
 
 using namespace ocpg;
 
+namespace ocpg {
+
+template <class M>
+struct BatchArgs {
+  const NodeArgs<M>* inst;
+  const int64_t* tileoff;  // count + 1
+  const int64_t* xoff;
+  const int64_t* coff;
+  const int64_t* joff;
+  const int64_t* hoff;
+  const double* x;
+  const double* y;
+  double *f, *c, *g, *jv, *hv;
+  double* partials;
+  unsigned* counter;
+  double sigma;
+  int64_t ntiles;
+  int count;
+};
+
+template <class M, int TILE, int NPT>
+__global__ void __launch_bounds__(TILE) k_batch_eval(const __grid_constant__ BatchArgs<M> b) {
+  extern __shared__ __align__(16) double sm[];
+  __shared__ double sEdge[(TILE / 32 + 1) * M::NX];
+  __shared__ NodeArgs<M> sa;
+  __shared__ int s_inst;
+  static_assert(sizeof(NodeArgs<M>) % 8 == 0, "argument block is copied in 8-byte words");
+  for (int64_t gt = blockIdx.x; gt < b.ntiles; gt += gridDim.x) {
+    if (threadIdx.x == 0) {
+      int lo = 0, hi = b.count - 1;  // last instance whose first tile is <= gt
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(b.tileoff + mid) <= gt) lo = mid; else hi = mid - 1;
+      }
+      s_inst = lo;
+    }
+    __syncthreads();
+    const int i = s_inst;
+    {
+      const unsigned long long* src = reinterpret_cast<const unsigned long long*>(b.inst + i);
+      unsigned long long* dst = reinterpret_cast<unsigned long long*>(&sa);
+      for (int w = threadIdx.x; w < (int)(sizeof(NodeArgs<M>) / 8); w += TILE) dst[w] = __ldg(src + w);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      sa.x = b.x + __ldg(b.xoff + i);
+      sa.y = b.y ? b.y + __ldg(b.coff + i) : nullptr;
+      sa.f = b.f;
+      sa.c = b.c ? b.c + __ldg(b.coff + i) : nullptr;
+      sa.g = b.g ? b.g + __ldg(b.xoff + i) : nullptr;
+      sa.jv = b.jv ? b.jv + __ldg(b.joff + i) : nullptr;
+      sa.hv = b.hv ? b.hv + __ldg(b.hoff + i) : nullptr;
+      for (int v = 0; v < M::NZ; ++v) {  // the argument blocks hold sigma = 1 coefficients
+        sa.cq_in[v] *= b.sigma;
+        sa.cq_end[v] *= b.sigma;
+      }
+    }
+    __syncthreads();
+    const ModelConst K = sa.K;
+    node_eval_tile<M, TILE, NPT, O_ALL>(sa, K, gt - __ldg(b.tileoff + i), sm, sEdge, b.partials + gt);
+  }
+  if (b.f) {
+    __shared__ int s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      const unsigned ticket = atomicAdd(b.counter, 1u);
+      s_last = (ticket == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    for (int i = threadIdx.x; i < b.count; i += TILE) {
+      double s = 0.0;
+      const int64_t t1 = __ldg(b.tileoff + i + 1);
+      for (int64_t t = __ldg(b.tileoff + i); t < t1; ++t) s += __ldcg(b.partials + t);
+      b.f[i] = 0.5 * s;
+    }
+    if (threadIdx.x == 0) *b.counter = 0u;
+  }
+}
+
+struct BatchConfig {
+  int threads, npt;
+};
+static const BatchConfig kConfigs[] = {{64, 1}, {128, 1}, {256, 1}, {64, 2}, {128, 2}, {256, 2}};
+
+template <class M, int TILE, int NPT>
+static const void* batch_kernel() {
+  return (const void*)k_batch_eval<M, TILE, NPT>;
+}
+
+template <class M>
+static const void* kernel_for(int threads, int npt) {
+  if (npt == 1) {
+    if (threads == 64) return batch_kernel<M, 64, 1>();
+    if (threads == 128) return batch_kernel<M, 128, 1>();
+    if (threads == 256) return batch_kernel<M, 256, 1>();
+  } else {
+    if (threads == 64) return batch_kernel<M, 64, 2>();
+    if (threads == 128) return batch_kernel<M, 128, 2>();
+    if (threads == 256) return batch_kernel<M, 256, 2>();
+  }
+  return nullptr;
+}
+
+template <class M>
+static size_t smem_bytes(int threads, int npt) {
+  return sizeof(double) * ((size_t)jrow_total<M>() * (npt * threads - 1) + threads);
+}
+
+}  // namespace ocpg
+
+struct ocp_batch_impl {
+  int model = 0, count = 0, device = 0, num_sms = 0;
+  std::vector<ocp*> items;
+  std::vector<int64_t> xoff, coff, joff, hoff, tileoff;
+  int threads = 128, npt = 1, ctas_per_sm = 0;
+  int64_t ntiles = 0;
+  void* d_inst = nullptr;
+  int64_t *d_tileoff = nullptr, *d_xoff = nullptr, *d_coff = nullptr, *d_joff = nullptr, *d_hoff = nullptr;
+  double* d_partials = nullptr;
+  int64_t partials_cap = 0;
+  unsigned* d_counter = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  std::string err;
+};
+
+struct ocp_batch : ocp_batch_impl {};
+
+static ocp_status berr(ocp_batch* b, ocp_status st, const std::string& m) {
+  if (b) b->err = m;
+  return set_err(nullptr, st, m);
+}
+
+template <class M>
+static ocp_status batch_upload_inst(ocp_batch* b) {
+  std::vector<NodeArgs<M>> inst(b->count);
+  for (int i = 0; i < b->count; ++i) {
+    fill_args<M>(b->items[i], 1.0, inst[i]);
+    inst[i].B = 0;
+    inst[i].E = b->items[i]->N + 1;
+    inst[i].p0_dev = nullptr;
+  }
+  cudaError_t e = cudaMalloc(&b->d_inst, sizeof(NodeArgs<M>) * b->count);
+  if (e != cudaSuccess) return berr(b, OCP_ENOMEM, "cudaMalloc(batch instances)");
+  e = cudaMemcpy(b->d_inst, inst.data(), sizeof(NodeArgs<M>) * b->count, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return berr(b, OCP_ECUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(e));
+  // allow the largest shared-memory request of every configuration once
+  for (const auto& cf : kConfigs) {
+    e = cudaFuncSetAttribute(kernel_for<M>(cf.threads, cf.npt), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_bytes<M>(cf.threads, cf.npt));
+    if (e != cudaSuccess) return berr(b, OCP_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
+  }
+  return OCP_OK;
+}
+
+static ocp_status batch_tiles(ocp_batch* b) {
+  const int64_t owned = (int64_t)b->npt * b->threads - 1;
+  b->tileoff.assign(b->count + 1, 0);
+  for (int i = 0; i < b->count; ++i) b->tileoff[i + 1] = b->tileoff[i] + (b->items[i]->N + 1 + owned - 1) / owned;
+  b->ntiles = b->tileoff[b->count];
+  if (b->ntiles > b->partials_cap) return berr(b, OCP_EDIM, "tile count exceeds the partial-sum buffer");
+  cudaError_t e = cudaMemcpy(b->d_tileoff, b->tileoff.data(), sizeof(int64_t) * (b->count + 1), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return berr(b, OCP_ECUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(e));
+  return OCP_OK;
+}
+
+template <class M>
+static int max_ctas_per_sm(const ocp_batch* b) {
+  int per = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel_for<M>(b->threads, b->npt), b->threads,
+                                                    smem_bytes<M>(b->threads, b->npt)) != cudaSuccess || per < 1)
+    per = 1;
+  return per;
+}
+
+template <class M>
+static ocp_status batch_launch(ocp_batch* b, const double* x, const double* y, double sigma, double* f, double* c,
+                               double* g, double* jv, double* hv, cudaStream_t s) {
+  BatchArgs<M> a;
+  memset(&a, 0, sizeof(a));
+  a.inst = (const NodeArgs<M>*)b->d_inst;
+  a.tileoff = b->d_tileoff; a.xoff = b->d_xoff; a.coff = b->d_coff; a.joff = b->d_joff; a.hoff = b->d_hoff;
+  a.x = x; a.y = y; a.f = f; a.c = c; a.g = g; a.jv = jv; a.hv = hv;
+  a.partials = b->d_partials; a.counter = b->d_counter;
+  a.sigma = sigma;
+  a.ntiles = b->ntiles;
+  a.count = b->count;
+  const int per = b->ctas_per_sm > 0 ? std::min(b->ctas_per_sm, max_ctas_per_sm<M>(b)) : max_ctas_per_sm<M>(b);
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(b->ntiles, (int64_t)per * b->num_sms));
+  const size_t sm = smem_bytes<M>(b->threads, b->npt);
+  const int T = b->threads;
+#define OCP_BATCH_LAUNCH(TT, PP) k_batch_eval<M, TT, PP><<<grid, TT, sm, s>>>(a)
+  if (b->npt == 1) {
+    if (T == 64) OCP_BATCH_LAUNCH(64, 1); else if (T == 128) OCP_BATCH_LAUNCH(128, 1); else OCP_BATCH_LAUNCH(256, 1);
+  } else {
+    if (T == 64) OCP_BATCH_LAUNCH(64, 2); else if (T == 128) OCP_BATCH_LAUNCH(128, 2); else OCP_BATCH_LAUNCH(256, 2);
+  }
+#undef OCP_BATCH_LAUNCH
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return berr(b, OCP_ECUDA, std::string("batch launch: ") + cudaGetErrorString(e));
+  return OCP_OK;
+}
+
+static ocp_status dispatch_batch(ocp_batch* b, const double* x, const double* y, double sigma, double* f, double* c,
+                                 double* g, double* jv, double* hv, cudaStream_t s) {
+  if (b->model == OCP_MODEL_CARTPOLE) return batch_launch<CartPole>(b, x, y, sigma, f, c, g, jv, hv, s);
+  return batch_launch<VdP>(b, x, y, sigma, f, c, g, jv, hv, s);
+}
+
+static void batch_free(ocp_batch* b) {
+  if (!b) return;
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  cudaFree(b->d_inst); cudaFree(b->d_tileoff); cudaFree(b->d_xoff); cudaFree(b->d_coff); cudaFree(b->d_joff);
+  cudaFree(b->d_hoff); cudaFree(b->d_partials); cudaFree(b->d_counter);
+  delete b;
+}
+
 extern "C" {
 
 ocp_status ocp_batch_create(ocp_t* const* items, int count, ocp_batch_t** out) {
-  (void)items; (void)count;
-  if (out) *out = nullptr;
-  return set_err(nullptr, OCP_EMODEL, "batched evaluation is not available in this build");
+  if (!out) return set_err(nullptr, OCP_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!items || count < 1) return set_err(nullptr, OCP_EINVAL, "need at least one problem");
+  const int model = items[0] ? items[0]->model : 0;
+  if (model != OCP_MODEL_CARTPOLE && model != OCP_MODEL_VDP)
+    return set_err(nullptr, OCP_EMODEL, "batched evaluation is provided for the cart-pole and Van der Pol models");
+  for (int i = 0; i < count; ++i) {
+    if (!items[i]) return set_err(nullptr, OCP_EINVAL, "NULL problem in the batch");
+    if (items[i]->model != model) return set_err(nullptr, OCP_EMODEL, "all problems of a batch must share the model");
+    if (items[i]->device != items[0]->device) return set_err(nullptr, OCP_EINVAL, "problems on different devices");
+  }
+  ocp_batch* b = new (std::nothrow) ocp_batch();
+  if (!b) return set_err(nullptr, OCP_ENOMEM, "host allocation failed");
+  b->model = model; b->count = count; b->device = items[0]->device; b->num_sms = items[0]->num_sms;
+  b->items.assign(items, items + count);
+  b->xoff.assign(count + 1, 0); b->coff.assign(count + 1, 0); b->joff.assign(count + 1, 0); b->hoff.assign(count + 1, 0);
+  int64_t cap = 0;
+  for (int i = 0; i < count; ++i) {
+    const Pattern& P = items[i]->pat;
+    b->xoff[i + 1] = b->xoff[i] + P.n;
+    b->coff[i + 1] = b->coff[i] + P.m;
+    b->joff[i + 1] = b->joff[i] + P.nnzj;
+    b->hoff[i + 1] = b->hoff[i] + P.nnzh;
+    cap += (items[i]->N + 1 + 62) / 63;  // tiles of the smallest configuration (64 threads, 1 node)
+  }
+  b->partials_cap = cap;
+  cudaError_t e;
+  auto up = [&](int64_t** d, const std::vector<int64_t>& h) -> bool {
+    if (cudaMalloc(d, sizeof(int64_t) * h.size()) != cudaSuccess) return false;
+    return cudaMemcpy(*d, h.data(), sizeof(int64_t) * h.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+  };
+  if (!up(&b->d_xoff, b->xoff) || !up(&b->d_coff, b->coff) || !up(&b->d_joff, b->joff) || !up(&b->d_hoff, b->hoff) ||
+      cudaMalloc(&b->d_tileoff, sizeof(int64_t) * (count + 1)) != cudaSuccess ||
+      cudaMalloc(&b->d_partials, sizeof(double) * cap) != cudaSuccess ||
+      cudaMalloc(&b->d_counter, sizeof(unsigned)) != cudaSuccess ||
+      (e = cudaMemset(b->d_counter, 0, sizeof(unsigned))) != cudaSuccess) {
+    batch_free(b);
+    return set_err(nullptr, OCP_ENOMEM, "device allocation failed for the batch");
+  }
+  ocp_status st = (model == OCP_MODEL_CARTPOLE) ? batch_upload_inst<CartPole>(b) : batch_upload_inst<VdP>(b);
+  if (st == OCP_OK) st = batch_tiles(b);
+  if (st != OCP_OK) { batch_free(b); return st; }
+  *out = b;
+  return OCP_OK;
 }
 
-void ocp_batch_destroy(ocp_batch_t* b) { delete b; }
+void ocp_batch_destroy(ocp_batch_t* b) { batch_free(b); }
 
-ocp_status ocp_batch_offsets(const ocp_batch_t* b, int64_t*, int64_t*, int64_t*, int64_t*) {
-  return b ? OCP_EMODEL : OCP_EINVAL;
+ocp_status ocp_batch_offsets(const ocp_batch_t* b, int64_t* xoff, int64_t* coff, int64_t* joff, int64_t* hoff) {
+  if (!b) return OCP_EINVAL;
+  for (int i = 0; i <= b->count; ++i) {
+    if (xoff) xoff[i] = b->xoff[i];
+    if (coff) coff[i] = b->coff[i];
+    if (joff) joff[i] = b->joff[i];
+    if (hoff) hoff[i] = b->hoff[i];
+  }
+  return OCP_OK;
 }
 
-ocp_status ocp_batch_set_config(ocp_batch_t* b, int, int) { return b ? OCP_EMODEL : OCP_EINVAL; }
-
-ocp_status ocp_batch_eval_all(ocp_batch_t* b, const double*, const double*, double, double*, double*, double*,
-                              double*, void*) {
-  return b ? OCP_EMODEL : OCP_EINVAL;
+ocp_status ocp_batch_set_config(ocp_batch_t* b, int nodes_per_thread, int threads, int ctas_per_sm) {
+  if (!b) return OCP_EINVAL;
+  if ((nodes_per_thread != 1 && nodes_per_thread != 2) || (threads != 64 && threads != 128 && threads != 256) ||
+      ctas_per_sm < 0)
+    return berr(b, OCP_EINVAL, "config: nodes_per_thread in {1,2}, threads in {64,128,256}, ctas_per_sm >= 0");
+  b->npt = nodes_per_thread;
+  b->threads = threads;
+  b->ctas_per_sm = ctas_per_sm;
+  if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+  return batch_tiles(b);
 }
+
+ocp_status ocp_batch_get_config(const ocp_batch_t* b, int* nodes_per_thread, int* threads, int* ctas_per_sm) {
+  if (!b) return OCP_EINVAL;
+  if (nodes_per_thread) *nodes_per_thread = b->npt;
+  if (threads) *threads = b->threads;
+  if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm;
+  return OCP_OK;
+}
+
+ocp_status ocp_batch_eval_all(ocp_batch_t* b, const double* x, const double* y, double sigma, double* f, double* c,
+                              double* g, double* jvals, double* hvals, void* stream) {
+  if (!b) return OCP_EINVAL;
+  if (!x) return berr(b, OCP_EINVAL, "x is NULL");
+  if (hvals && !y) return berr(b, OCP_EINVAL, "y is required for Hessian values");
+  return dispatch_batch(b, x, y, sigma, f, c, g, jvals, hvals, (cudaStream_t)stream);
+}
+
+ocp_status ocp_batch_autotune(ocp_batch_t* b, const double* x, const double* y, double sigma, double* f, double* c,
+                              double* g, double* jvals, double* hvals, void* stream, double* best_ms) {
+  if (!b) return OCP_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return berr(b, OCP_ECUDA, "cudaEventCreate");
+  float best = 1e30f;
+  int bt = 128, bn = 1, bc = 0;
+  ocp_status st = OCP_OK;
+  for (const auto& cf : kConfigs) {
+    b->threads = cf.threads; b->npt = cf.npt; b->ctas_per_sm = 0;
+    if ((st = batch_tiles(b)) != OCP_OK) break;
+    const int maxc = (b->model == OCP_MODEL_CARTPOLE) ? max_ctas_per_sm<CartPole>(b) : max_ctas_per_sm<VdP>(b);
+    for (int cps = maxc; cps >= 1; cps = (cps > 2 ? cps / 2 : cps - 1)) {
+      b->ctas_per_sm = cps;
+      if ((st = dispatch_batch(b, x, y, sigma, f, c, g, jvals, hvals, s)) != OCP_OK) break;  // warm-up
+      float tms[3];
+      for (int r = 0; r < 3 && st == OCP_OK; ++r) {
+        cudaEventRecord(e0, s);
+        st = dispatch_batch(b, x, y, sigma, f, c, g, jvals, hvals, s);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&tms[r], e0, e1);
+      }
+      if (st != OCP_OK) break;
+      std::sort(tms, tms + 3);
+      if (tms[1] < best) { best = tms[1]; bt = cf.threads; bn = cf.npt; bc = cps; }
+    }
+    if (st != OCP_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != OCP_OK) return st;
+  if (best_ms) *best_ms = best;
+  return ocp_batch_set_config(b, bn, bt, bc);
+}
+
+ocp_status ocp_batch_graph_capture(ocp_batch_t* b, const double* x, const double* y, double sigma, double* f, double* c,
+                                   double* g, double* jvals, double* hvals, void* stream) {
+  if (!b) return OCP_EINVAL;
+  if (!stream) return berr(b, OCP_EINVAL, "graph capture needs a created (non-default) stream");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
+  cudaGraph_t gr = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return berr(b, OCP_ECUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e));
+  ocp_status st = dispatch_batch(b, x, y, sigma, f, c, g, jvals, hvals, s);
+  e = cudaStreamEndCapture(s, &gr);
+  if (st != OCP_OK) { if (gr) cudaGraphDestroy(gr); return st; }
+  if (e != cudaSuccess) return berr(b, OCP_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&b->graph, gr, 0);
+  cudaGraphDestroy(gr);
+  if (e != cudaSuccess) { b->graph = nullptr; return berr(b, OCP_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e)); }
+  return OCP_OK;
+}
+
+ocp_status ocp_batch_graph_launch(ocp_batch_t* b, void* stream) {
+  if (!b) return OCP_EINVAL;
+  if (!b->graph) return berr(b, OCP_EINVAL, "no captured graph");
+  cudaError_t e = cudaGraphLaunch(b->graph, (cudaStream_t)stream);
+  if (e != cudaSuccess) return berr(b, OCP_ECUDA, std::string("cudaGraphLaunch: ") + cudaGetErrorString(e));
+  return OCP_OK;
+}
+
+const char* ocp_batch_last_error(const ocp_batch_t* b) { return b ? b->err.c_str() : ""; }
 
 }  // extern "C"

@@ -373,6 +373,50 @@ ocp_status ocp_vjp_param(ocp_t* h, const double* x, const double* w, double* Jtw
   return dispatch_prod(h, c, stream);
 }
 
+ocp_status ocp_bind_param0(ocp_t* h, const double* p0_dev) {
+  if (!h) return OCP_EINVAL;
+  if (p0_dev && h->model != OCP_MODEL_VDP)
+    return set_err(h, OCP_EMODEL, "a device parameter is provided for the Van der Pol model");
+  OPT(p0_dev);
+  h->p0_dev = p0_dev;
+  return OCP_OK;
+}
+
+ocp_status ocp_jprod_param(ocp_t* h, const double* x, const double* v, const double* s, double* Jv, void* stream) {
+  if (!h) return OCP_EINVAL;
+  NEED(x); NEED(v); NEED(Jv); OPT(s);
+  if (s && h->model != OCP_MODEL_VDP) return set_err(h, OCP_EMODEL, "parameter direction: Van der Pol model only");
+  ProdCall c;
+  c.kind = P_JPROD; c.x = x; c.v = v; c.out = Jv; c.pdir_dev = s;
+  return dispatch_prod(h, c, stream);
+}
+
+ocp_status ocp_hprod_param(ocp_t* h, const double* x, const double* y, double sigma, const double* v, const double* s,
+                           double* Hv, double* dmu, void* stream) {
+  if (!h) return OCP_EINVAL;
+  NEED(x); NEED(y); NEED(v); NEED(Hv); OPT(s); OPT(dmu);
+  if ((s || dmu) && h->model != OCP_MODEL_VDP)
+    return set_err(h, OCP_EMODEL, "mixed parameter term: Van der Pol model only");
+  if (dmu && !s) return set_err(h, OCP_EINVAL, "dmu needs the scale s (pass a device zero for none)");
+  ProdCall c;
+  c.kind = P_HPROD; c.x = x; c.y = y; c.sigma = sigma; c.v = v; c.out = Hv;
+  if (s) { c.mixw = y; c.mixs = s; c.dmu = dmu; }
+  return dispatch_prod(h, c, stream);
+}
+
+ocp_status ocp_eval_grad_scaled(ocp_t* h, const double* x, const double* s, double* g, void* stream) {
+  if (!h) return OCP_EINVAL;
+  NEED(x); NEED(s); NEED(g);
+  return obj_launch(h, false, x, s, nullptr, g, nullptr, (cudaStream_t)stream);
+}
+
+ocp_status ocp_obj_hvp(ocp_t* h, const double* x, const double* s, const double* v, double* Hv, double* dot,
+                       void* stream) {
+  if (!h) return OCP_EINVAL;
+  NEED(x); NEED(s); NEED(v); NEED(Hv); OPT(dot);
+  return obj_launch(h, true, x, s, v, Hv, dot, (cudaStream_t)stream);
+}
+
 ocp_status ocp_set_param0(ocp_t* h, double value) {
   if (!h) return OCP_EINVAL;
   if (model_nparams(h->model) < 1) return set_err(h, OCP_EMODEL, "model has no parameters");

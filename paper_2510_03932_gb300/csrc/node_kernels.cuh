@@ -97,12 +97,11 @@ __host__ __device__ constexpr int jrow_off(int k) {
   return s;
 }
 
-template <class M, int TILE, unsigned OUT>
+template <class M, int TILE, int NPT, unsigned OUT>
 struct EvalSmem {
-  static constexpr int R = TILE - 1;
+  static constexpr int R = NPT * TILE - 1;
   static constexpr int J = (OUT & O_J) ? jrow_total<M>() * R : 0;
-  static constexpr int oJ = 0, oRED = oJ + J;
-  static constexpr int total = oRED + TILE;
+  static constexpr int total = J + TILE;
   static constexpr size_t bytes = sizeof(double) * total;
 };
 
@@ -233,44 +232,51 @@ __device__ __forceinline__ double node_grad(const NodeArgs<M>& a, const double (
   return s;
 }
 
-template <class M, int TILE, unsigned OUT>
-__global__ void __launch_bounds__(TILE) k_node_eval(const __grid_constant__ NodeArgs<M> a) {
+// One tile of the fused evaluation.  The CTA's TILE threads cover NPT*TILE consecutive
+// nodes r0.. (thread t takes nodes r0 + NPT t + q, q < NPT: consecutive pairs give each thread
+// independent FP64 dependency chains) and own the first NPT*TILE - 1 of them.  `a` may live in
+// parameter or shared memory.  The tile's objective term (2 w_j f0 summed in a fixed order)
+// goes to *partial.
+template <class M, int TILE, int NPT, unsigned OUT>
+__device__ __forceinline__ void node_eval_tile(const NodeArgs<M>& a, const ModelConst& K, int64_t tile, double* sm,
+                                               double* sEdge, double* partial) {
   constexpr int NX = M::NX, NZ = M::NZ;
+  constexpr int NT = NPT * TILE;  // nodes per tile
   constexpr bool WF = OUT & O_F, WC = OUT & O_C, WG = OUT & O_G, WJ = OUT & O_J, WH = OUT & O_H;
   // the full kernel also serves output subsets: NULL outputs are computed but not stored
   const bool sF = WF && a.f, sC = WC && a.c, sG = WG && a.g, sJ = WJ && a.jv, sH = WH && a.hv;
-  using S = EvalSmem<M, TILE, OUT>;
   constexpr HTmpl<M> HT{};
   constexpr int NHD = (M::NHD > 0) ? M::NHD : 1;
-  extern __shared__ __align__(16) double sm[];
-  __shared__ double sEdge[(TILE / 32 + 1) * NX];
+  constexpr int R = NT - 1;            // owned rows / nodes per tile
+  constexpr int oRED = (OUT & O_J) ? jrow_total<M>() * R : 0;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  ModelConst K = a.K;
-  if (a.p0_dev) M::device_param(K, __ldg(a.p0_dev));
 
-  for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
-    const int64_t r0 = a.B + tile * (TILE - 1);
-    const int64_t own_end = min(r0 + TILE - 1, a.E);
-    const int64_t row_end = min(own_end, a.N);
-    const int64_t eval_end = row_end + 1;
-    const int nown = (int)(own_end - r0);
-    const int nrows = (int)max(row_end - r0, (int64_t)0);
-    const int64_t j = r0 + t;
-    const bool act = j < eval_end;
-    const bool own = t < nown;
-    const bool endp = (j == 0) || (j == a.N);
-    double objterm = 0.0;
+  const int64_t r0 = a.B + tile * R;
+  const int64_t own_end = min(r0 + R, a.E);
+  const int64_t row_end = min(own_end, a.N);
+  const int64_t eval_end = row_end + 1;
+  const int nown = (int)(own_end - r0);
+  const int nrows = (int)max(row_end - r0, (int64_t)0);
+  double objterm = 0.0;
+  double pa[NPT][NX], pb[NPT][NX];
 
-    double z[NZ], yb[NX], cqd[NZ], pa[NX], pb[NX], mjx[NX][M::MAXRX], mju[NX][M::MAXRU], hd[NHD];
 #pragma unroll
-    for (int k = 0; k < NX; ++k) { pa[k] = 0.0; pb[k] = 0.0; }
+  for (int q = 0; q < NPT; ++q) {
+    const int lt = NPT * t + q;       // node index within the tile
+    const int64_t j = r0 + lt;
+    const bool act = j < eval_end;
+    const bool own = lt < nown;
+    const bool endp = (j == 0) || (j == a.N);
+    double z[NZ], yb[NX], cqd[NZ], mjx[NX][M::MAXRX], mju[NX][M::MAXRU], hd[NHD];
+#pragma unroll
+    for (int k = 0; k < NX; ++k) { pa[q][k] = 0.0; pb[q][k] = 0.0; }
     if (act) {
       load_node<M>(a, j, z);
       if (WH) {
         load_ybar<M>(a, a.y, j, yb);
         node_cq<M>(a, endp, cqd);
       }
-      M::template eval<WC, WJ, WH>(K, z, yb, cqd, pa, pb, mjx, mju, hd);
+      M::template eval<WC, WJ, WH>(K, z, yb, cqd, pa[q], pb[q], mjx, mju, hd);
     }
     if (own) {
       // ---- Hessian block of node j (stored directly; X block then U block)
@@ -290,7 +296,7 @@ __global__ void __launch_bounds__(TILE) k_node_eval(const __grid_constant__ Node
         double s2;
         if (a.has_ref) s2 = sG ? node_grad<M, true, true>(a, z, endp, j) : node_grad<M, true, false>(a, z, endp, j);
         else s2 = sG ? node_grad<M, false, true>(a, z, endp, j) : node_grad<M, false, false>(a, z, endp, j);
-        objterm = s2;
+        objterm = (q == 0) ? s2 : objterm + s2;
       }
       // ---- boundary rows X_{0,k} (and X_{N,k}): constraint value and the constant Jacobian entry
       if (j == 0) {
@@ -308,21 +314,21 @@ __global__ void __launch_bounds__(TILE) k_node_eval(const __grid_constant__ Node
         }
       }
     }
-    // ---- Jacobian rows staged in shared memory: left part of row t, right part of row t-1
+    // ---- Jacobian rows staged in shared memory: left part of row lt, right part of row lt-1
     if (WJ && act) {
 #pragma unroll
       for (int k = 0; k < NX; ++k) {
         const int cnt = row_count<M>(k);
-        double* sj = sm + S::oJ + jrow_off<M>(k) * S::R;
-        if (t < nrows) {
-          double* rp = sj + t * cnt;
+        double* sj = sm + jrow_off<M>(k) * R;
+        if (lt < nrows) {
+          double* rp = sj + lt * cnt;
 #pragma unroll
           for (int e = 0; e < M::RX(k); ++e) rp[e] = (M::XV(k, e) == k) ? (mjx[k][e] - 1.0) : mjx[k][e];
 #pragma unroll
           for (int e = 0; e < M::RU(k); ++e) rp[2 * M::RX(k) + e] = mju[k][e];
         }
-        if (t >= 1 && t - 1 < nrows) {
-          double* rp = sj + (t - 1) * cnt;
+        if (lt >= 1 && lt - 1 < nrows) {
+          double* rp = sj + (lt - 1) * cnt;
 #pragma unroll
           for (int e = 0; e < M::RX(k); ++e) rp[M::RX(k) + e] = (M::XV(k, e) == k) ? (mjx[k][e] + 1.0) : mjx[k][e];
 #pragma unroll
@@ -330,41 +336,60 @@ __global__ void __launch_bounds__(TILE) k_node_eval(const __grid_constant__ Node
         }
       }
     }
-    // ---- defects: the right node's x - hh f comes from lane+1 (or the next warp's lane 0)
-    double nbv[NX];
-    if (WC) {
-#pragma unroll
-      for (int k = 0; k < NX; ++k) {
-        nbv[k] = __shfl_down_sync(0xffffffffu, pb[k], 1);
-        if (lane == 0) sEdge[warp * NX + k] = pb[k];
-      }
-    }
-    if (WC || WJ) __syncthreads();
-    if (sC && t < nrows) {
-#pragma unroll
-      for (int k = 0; k < NX; ++k) {
-        const double right = (lane == 31) ? sEdge[(warp + 1) * NX + k] : nbv[k];
-        a.c[a.nb + (int64_t)k * a.N + j] = right - pa[k];
-      }
-    }
-    // ---- coalesced copy-out of the staged Jacobian rows
-    if (sJ) {
-#pragma unroll
-      for (int k = 0; k < NX; ++k) {
-        const int cnt = row_count<M>(k);
-        const double* src = sm + S::oJ + jrow_off<M>(k) * S::R;
-        double* dst = a.jv + a.jbase[k] + r0 * cnt;
-        const int total = nrows * cnt;
-        for (int i = t; i < total; i += TILE) dst[i] = src[i];
-      }
-    }
-    if (sF) {
-      const double ts = tile_sum<TILE>(objterm, sm + S::oRED);
-      if (t == 0) a.partials[tile] = ts;
-    }
-    if (WC || WJ || WF) __syncthreads();
   }
-  if (sF) finish_tiles<TILE>(a.partials, a.ntiles, a.counter, a.f, 0.5, sm + S::oRED);
+  // ---- defects: the right node's x - hh f is this thread's next node, or lane+1's first
+  double nbv[NX];
+  if (WC) {
+#pragma unroll
+    for (int k = 0; k < NX; ++k) {
+      nbv[k] = __shfl_down_sync(0xffffffffu, pb[0][k], 1);
+      if (lane == 0) sEdge[warp * NX + k] = pb[0][k];
+    }
+  }
+  if (WC || WJ) __syncthreads();
+  if (sC) {
+#pragma unroll
+    for (int q = 0; q < NPT; ++q) {
+      const int lt = NPT * t + q;
+      if (lt < nrows) {
+#pragma unroll
+        for (int k = 0; k < NX; ++k) {
+          double right;
+          if (q + 1 < NPT) right = pb[q + 1 < NPT ? q + 1 : 0][k];
+          else right = (lane == 31) ? sEdge[(warp + 1) * NX + k] : nbv[k];
+          a.c[a.nb + (int64_t)k * a.N + r0 + lt] = right - pa[q][k];
+        }
+      }
+    }
+  }
+  // ---- coalesced copy-out of the staged Jacobian rows
+  if (sJ) {
+#pragma unroll
+    for (int k = 0; k < NX; ++k) {
+      const int cnt = row_count<M>(k);
+      const double* src = sm + jrow_off<M>(k) * R;
+      double* dst = a.jv + a.jbase[k] + r0 * cnt;
+      const int total = nrows * cnt;
+      for (int i = t; i < total; i += TILE) dst[i] = src[i];
+    }
+  }
+  if (sF) {
+    const double ts = tile_sum<TILE>(objterm, sm + oRED);
+    if (t == 0) *partial = ts;
+  }
+  if (WC || WJ || WF) __syncthreads();
+}
+
+template <class M, int TILE, int NPT, unsigned OUT>
+__global__ void __launch_bounds__(TILE) k_node_eval(const __grid_constant__ NodeArgs<M> a) {
+  constexpr bool WF = OUT & O_F;
+  extern __shared__ __align__(16) double sm[];
+  __shared__ double sEdge[(TILE / 32 + 1) * M::NX];
+  ModelConst K = a.K;
+  if (a.p0_dev) M::device_param(K, __ldg(a.p0_dev));
+  for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x)
+    node_eval_tile<M, TILE, NPT, OUT>(a, K, tile, sm, sEdge, a.partials + tile);
+  if (WF && a.f) finish_tiles<TILE>(a.partials, a.ntiles, a.counter, a.f, 0.5, sm);
 }
 
 // ======================================================================================
@@ -622,7 +647,7 @@ void fill_args(const ocp* h, double sigma, NodeArgs<M>& a) {
   a.p0_dev = h->p0_dev;
 }
 
-template <class M, int TILE, unsigned OUT>
+template <class M, int TILE, int NPT, unsigned OUT>
 ocp_status launch_eval_t(ocp* h, const EvalCall& c, cudaStream_t s) {
   NodeArgs<M> a;
   fill_args<M>(h, c.sigma, a);
@@ -630,18 +655,19 @@ ocp_status launch_eval_t(ocp* h, const EvalCall& c, cudaStream_t s) {
   a.B = c.B; a.E = c.E;
   a.range = c.range ? 1 : 0;
   const int64_t nodes = c.E - c.B;
-  a.ntiles = (nodes + (TILE - 2)) / (TILE - 1);
+  constexpr int R = NPT * TILE - 1;
+  a.ntiles = (nodes + R - 1) / R;
   if (a.ntiles < 1) a.ntiles = 1;
-  using S = EvalSmem<M, TILE, OUT>;
-  auto kern = k_node_eval<M, TILE, OUT>;
-  static bool attr_done = false;
-  if (!attr_done) {
+  if (a.ntiles > h->max_partials) return set_err(h, OCP_EDIM, "too many tiles for the reduction scratch");
+  using S = EvalSmem<M, TILE, NPT, OUT>;
+  auto kern = k_node_eval<M, TILE, NPT, OUT>;
+  static unsigned attr_done = 0;
+  if (!(attr_done & (1u << (h->device & 31)))) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
     if (e != cudaSuccess) return cuda_err(h, e, "cudaFuncSetAttribute(eval)");
-    attr_done = true;
+    attr_done |= 1u << (h->device & 31);
   }
   const int grid = occupancy_grid(h, (const void*)kern, TILE, S::bytes, a.ntiles);
-  if (grid <= 0) return set_err(h, OCP_ECUDA, "occupancy query failed");
   kern<<<grid, TILE, S::bytes, s>>>(a);
   return cuda_err(h, cudaGetLastError(), "k_node_eval launch");
 }
@@ -649,13 +675,13 @@ ocp_status launch_eval_t(ocp* h, const EvalCall& c, cudaStream_t s) {
 template <class M, int TILE>
 ocp_status node_eval_dispatch(ocp* h, unsigned out, const EvalCall& c, cudaStream_t s) {
   switch (out) {
-    case O_F: return launch_eval_t<M, TILE, O_F>(h, c, s);
-    case O_C: return launch_eval_t<M, TILE, O_C>(h, c, s);
-    case O_G: return launch_eval_t<M, TILE, O_G>(h, c, s);
-    case O_J: return launch_eval_t<M, TILE, O_J>(h, c, s);
-    case O_H: return launch_eval_t<M, TILE, O_H>(h, c, s);
-    case O_J | O_H: return launch_eval_t<M, TILE, O_J | O_H>(h, c, s);
-    default: return launch_eval_t<M, TILE, O_ALL>(h, c, s);
+    case O_F: return launch_eval_t<M, TILE, 1, O_F>(h, c, s);
+    case O_C: return launch_eval_t<M, TILE, 1, O_C>(h, c, s);
+    case O_G: return launch_eval_t<M, TILE, 1, O_G>(h, c, s);
+    case O_J: return launch_eval_t<M, TILE, 1, O_J>(h, c, s);
+    case O_H: return launch_eval_t<M, TILE, 1, O_H>(h, c, s);
+    case O_J | O_H: return launch_eval_t<M, TILE, 1, O_J | O_H>(h, c, s);
+    default: return launch_eval_t<M, TILE, 1, O_ALL>(h, c, s);
   }
 }
 
@@ -694,7 +720,7 @@ ocp_status node_prod_dispatch(ocp* h, const ProdCall& c, cudaStream_t s) {
     e = cudaGetLastError();
   } else {
     const int64_t blocks = (h->N + 1 + TILE - 1) / TILE;
-    if (c.mixw) {
+    if (c.mixw && c.mixs) {
       auto k = k_node_hprod<M, TILE, true>;
       int grid = occupancy_grid(h, (const void*)k, TILE, 0, blocks);
       k<<<grid, TILE, 0, s>>>(a);

@@ -63,20 +63,6 @@ struct ocp {
   std::string err;
 };
 
-struct ocp_batch {
-  std::vector<ocp*> items;
-  int model = 0, count = 0;
-  std::vector<int64_t> xoff, coff, joff, hoff, tileoff;
-  int64_t ntiles = 0, total_nodes = 0;
-  int nodes_per_thread = 1, threads = 256;
-  // device tables
-  void* d_inst = nullptr;       // per-instance descriptors
-  int64_t* d_tileoff = nullptr; // count + 1 prefix sums of tiles per instance
-  double* d_partials = nullptr;
-  int max_partials = 0;
-  int tile_nodes = 0;
-  std::string err;
-};
 
 namespace ocpg {
 
@@ -138,8 +124,8 @@ void model_row_templates(int model, int nx, std::vector<RowTemplate>& rows);
 void model_hess_max_template(int model, int nx, std::vector<std::pair<int, int>>& ent,
                              std::vector<int>& is_dyn);
 
-ocp_status batch_eval(ocp_batch* b, const double* x, const double* y, double sigma, double* f,
-                      double* g, double* jv, double* hv, cudaStream_t s);
-bool batch_prepare(ocp_batch* b, std::string& why);
+ocp_status obj_launch(ocp* h, bool hvp, const double* x, const double* s, const double* v, double* out,
+                      double* dot, cudaStream_t st);
+
 
 }  // namespace ocpg

@@ -59,6 +59,12 @@ _SIGS = {
     "ocp_eval_all_range": [_P, _I64, _I64, _P, _P, _D, _P, _P, _P, _P, _P, _P],
     "ocp_vjp_param": [_P, _P, _P, _P, _P, _P],
     "ocp_set_param0": [_P, _D],
+    "ocp_bind_param0": [_P, _P],
+    "ocp_jprod_param": [_P, _P, _P, _P, _P, _P],
+    "ocp_hprod_param": [_P, _P, _P, _D, _P, _P, _P, _P, _P],
+    "ocp_eval_grad_scaled": [_P, _P, _P, _P, _P],
+    "ocp_obj_hvp": [_P, _P, _P, _P, _P, _P, _P],
+    "ocp_eval_obj_noalloc": [C.POINTER(_Dyn), C.POINTER(_Cost), C.c_int, C.c_int, _I64, _D, _P, _P, _P],
     "ocp_last_error": [_P],
 }
 
@@ -257,6 +263,62 @@ class OCP:
     def set_param0(self, value: float):
         _check(lib().ocp_set_param0(self.h, float(value)), self.h)
 
+    def _scalar(self, t, name):
+        if t is None:
+            return None
+        if t.dtype != torch.float64 or not t.is_cuda or t.numel() != 1 or not t.is_contiguous():
+            raise TypeError("%s must be a one-element contiguous float64 CUDA tensor" % name)
+        return t
+
+    def bind_param0(self, p0):
+        """Read params[0] (Van der Pol mu) from the one-element CUDA tensor p0 (None unbinds).
+        Launches capture the pointer, so unbinding right after them is safe."""
+        p0 = self._scalar(p0, "p0")
+        _check(lib().ocp_bind_param0(self.h, _ptr(p0)), self.h)
+
+    class _Bound:
+        def __init__(self, H, p0):
+            self.H, self.p0 = H, p0
+
+        def __enter__(self):
+            self.H.bind_param0(self.p0)
+            return self.H
+
+        def __exit__(self, *exc):
+            self.H.bind_param0(None)
+            return False
+
+    def param0(self, p0):
+        """Context manager: calls inside it read params[0] from the CUDA scalar p0."""
+        return OCP._Bound(self, p0)
+
+    def jprod_param(self, x, v, s=None, out=None, stream=None):
+        x = self._vec(x, self.n, "x"); v = self._vec(v, self.n, "v"); s = self._scalar(s, "s")
+        out = self._out(out, self.m, "Jv")
+        _check(lib().ocp_jprod_param(self.h, _ptr(x), _ptr(v), _ptr(s), _ptr(out), _stream(stream)), self.h)
+        return out
+
+    def hprod_param(self, x, y, sigma, v, s=None, out=None, dmu=None, stream=None):
+        x = self._vec(x, self.n, "x"); y = self._vec(y, self.m, "y"); v = self._vec(v, self.n, "v")
+        s = self._scalar(s, "s"); dmu = self._scalar(dmu, "dmu")
+        out = self._out(out, self.n, "Hv")
+        _check(lib().ocp_hprod_param(self.h, _ptr(x), _ptr(y), float(sigma), _ptr(v), _ptr(s), _ptr(out), _ptr(dmu),
+                                     _stream(stream)), self.h)
+        return out
+
+    def eval_grad_scaled(self, x, s, out=None, stream=None):
+        x = self._vec(x, self.n, "x"); s = self._scalar(s, "s")
+        out = self._out(out, self.n, "g")
+        _check(lib().ocp_eval_grad_scaled(self.h, _ptr(x), _ptr(s), _ptr(out), _stream(stream)), self.h)
+        return out
+
+    def obj_hvp(self, x, s, v, out=None, dot=None, stream=None):
+        x = self._vec(x, self.n, "x"); s = self._scalar(s, "s"); v = self._vec(v, self.n, "v")
+        dot = self._scalar(dot, "dot")
+        out = self._out(out, self.n, "Hv")
+        _check(lib().ocp_obj_hvp(self.h, _ptr(x), _ptr(s), _ptr(v), _ptr(out), _ptr(dot), _stream(stream)), self.h)
+        return out
+
 
 def ocp_create(w: dict) -> OCP:
     """Create a problem from a workload description (see synth.workload)."""
@@ -310,3 +372,95 @@ def ocp_eval_all(h: OCP, x, y, sigma, f=None, c=None, g=None, jvals=None, hvals=
 
 def library_path() -> str:
     return os.path.abspath(_build.LIB)
+
+
+_BATCH_SIGS = {
+    "ocp_batch_create": [C.POINTER(_P), C.c_int, C.POINTER(_P)],
+    "ocp_batch_destroy": [_P],
+    "ocp_batch_offsets": [_P, _P, _P, _P, _P],
+    "ocp_batch_set_config": [_P, C.c_int, C.c_int, C.c_int],
+    "ocp_batch_get_config": [_P, _P, _P, _P],
+    "ocp_batch_eval_all": [_P, _P, _P, _D, _P, _P, _P, _P, _P, _P],
+    "ocp_batch_autotune": [_P, _P, _P, _D, _P, _P, _P, _P, _P, _P, _P],
+    "ocp_batch_graph_capture": [_P, _P, _P, _D, _P, _P, _P, _P, _P, _P],
+    "ocp_batch_graph_launch": [_P, _P],
+    "ocp_batch_last_error": [_P],
+}
+
+
+def _blib():
+    L = lib()
+    if not getattr(L, "_batch_ready", False):
+        for name, argt in _BATCH_SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = argt
+            fn.restype = C.c_int
+        L.ocp_batch_destroy.restype = None
+        L.ocp_batch_last_error.restype = C.c_char_p
+        L._batch_ready = True
+    return L
+
+
+class OCPBatch:
+    """Many problems of one model evaluated by one persistent launch (`ocp_batch_t`)."""
+
+    def __init__(self, problems):
+        import numpy as np
+        L = _blib()
+        self.problems = list(problems)  # keeps the handles alive
+        arr = (_P * len(self.problems))(*[p.h for p in self.problems])
+        b = C.c_void_p()
+        _check(L.ocp_batch_create(arr, len(self.problems), C.byref(b)))
+        self.b = b
+        cnt = len(self.problems) + 1
+        self.xoff, self.coff, self.joff, self.hoff = (np.zeros(cnt, np.int64) for _ in range(4))
+        self._bcheck(L.ocp_batch_offsets(b, self.xoff.ctypes.data_as(_P), self.coff.ctypes.data_as(_P),
+                                         self.joff.ctypes.data_as(_P), self.hoff.ctypes.data_as(_P)))
+        self.n, self.m = int(self.xoff[-1]), int(self.coff[-1])
+        self.nnzj, self.nnzh = int(self.joff[-1]), int(self.hoff[-1])
+        self.count = len(self.problems)
+        self.device = self.problems[0].device
+
+    def _bcheck(self, st):
+        if st != 0:
+            raise OcpError(st, (_blib().ocp_batch_last_error(self.b) or b"").decode())
+
+    def close(self):
+        if getattr(self, "b", None):
+            _blib().ocp_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def outputs(self):
+        e = lambda k: torch.empty(k, dtype=torch.float64, device=self.device)
+        return e(self.count), e(self.m), e(self.n), e(self.nnzj), e(self.nnzh)
+
+    def set_config(self, nodes_per_thread=1, threads=128, ctas_per_sm=0):
+        self._bcheck(_blib().ocp_batch_set_config(self.b, nodes_per_thread, threads, ctas_per_sm))
+
+    def get_config(self):
+        a, b_, c = C.c_int(), C.c_int(), C.c_int()
+        self._bcheck(_blib().ocp_batch_get_config(self.b, C.byref(a), C.byref(b_), C.byref(c)))
+        return dict(nodes_per_thread=a.value, threads=b_.value, ctas_per_sm=c.value)
+
+    def eval_all(self, x, y, sigma, f=None, c=None, g=None, jvals=None, hvals=None, stream=None):
+        self._bcheck(_blib().ocp_batch_eval_all(self.b, _ptr(x), _ptr(y), float(sigma), _ptr(f), _ptr(c), _ptr(g),
+                                                _ptr(jvals), _ptr(hvals), _stream(stream)))
+
+    def autotune(self, x, y, sigma, f=None, c=None, g=None, jvals=None, hvals=None, stream=None):
+        best = C.c_double()
+        self._bcheck(_blib().ocp_batch_autotune(self.b, _ptr(x), _ptr(y), float(sigma), _ptr(f), _ptr(c), _ptr(g),
+                                                _ptr(jvals), _ptr(hvals), _stream(stream), C.byref(best)))
+        return best.value
+
+    def graph_capture(self, x, y, sigma, f=None, c=None, g=None, jvals=None, hvals=None, stream=None):
+        self._bcheck(_blib().ocp_batch_graph_capture(self.b, _ptr(x), _ptr(y), float(sigma), _ptr(f), _ptr(c),
+                                                     _ptr(g), _ptr(jvals), _ptr(hvals), _stream(stream)))
+
+    def graph_launch(self, stream=None):
+        self._bcheck(_blib().ocp_batch_graph_launch(self.b, _stream(stream)))

@@ -128,3 +128,16 @@ def dims(w: dict):
 def draw(w: dict, seed: int | None = None) -> dict:
     n, m = dims(w)
     return draw_instance(w["seed"] if seed is None else seed, w["dist"], w["nx"], w["nu"], w["N"], m)
+
+
+def batch_workloads(count=256, nmin=500, nmax=50000, seed=1004):
+    """The batched cart-pole workload: `count` instances, N_i ~ U{nmin..nmax},
+    x0_i ~ U(-0.5, 0.5)^4, R_i ~ U(0.01, 1); instance i draws its inputs with seed + 1 + i."""
+    Ns, x0, R = draw_batch_meta(seed, count, nmin, nmax)
+    base = workload("cartpole_n1e5")
+    out = []
+    for i in range(count):
+        w = dict(base, name="cartpole_batch_%d" % i, N=int(Ns[i]), r=[float(R[i])], x0=[float(v) for v in x0[i]],
+                 seed=seed + 1 + i)
+        out.append(w)
+    return out
