@@ -40,6 +40,8 @@ def algorithmic_bytes(w, kind):
     nnzj, nnzh = P
     if kind == "eval_all":
         return 8 * (n + m + 1 + m + n + nnzj + nnzh)
+    if kind == "step":  # reads x, y, vn, vm; writes f, c, g, J, H, Jv, J^T w, Hv
+        return 8 * (n + m + n + m + 1 + m + n + nnzj + nnzh + m + n + n)
     if kind == "jh":
         return 8 * (n + m + nnzj + nnzh)
     if kind == "jprod":
@@ -68,7 +70,7 @@ def _counts(w):
 # the kernel source and equal to ncu's sm__sass_thread_inst_executed_op_{dfma,dadd,dmul}
 # counts divided by N+1 (Van der Pol: the objective's tile reduction adds 1.5 per node).
 FP64_OPS_PER_NODE = {("vdp", "eval_all"): 26.5, ("vdp", "jh"): 10.0, ("vdp", "jprod"): 14.0,
-                     ("vdp", "jtprod"): 12.0, ("vdp", "hprod"): 11.0}
+                     ("vdp", "jtprod"): 12.0, ("vdp", "hprod"): 11.0, ("vdp", "step"): 51.6}
 # DRAM bytes (read + write) of one launch, from an ncu capture of the same kernel (see
 # profiles/); None until captured for the current kernel version.
 TRAFFIC = {}
@@ -163,23 +165,28 @@ def run_ours(args, rank, world):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
     names = ["eval_all", "jprod", "jtprod", "hprod"]
+    outs = (f, c, g, jv, hv, Jv, Jtv, Hv)
 
-    def step(ev=None):
-        if ev: ev[0].record(stream)
+    def step():
+        # one pass of the hot path: F, c, grad, J, H and Jv, J^T w, Hv at the same x
+        H.eval_step(x, y, sigma, vn, vm, outs)
+
+    def separate(ev):
+        ev[0].record(stream)
         H.eval_all(x, y, sigma, f, c, g, jv, hv, alloc=False)
-        if ev: ev[1].record(stream)
+        ev[1].record(stream)
         H.jprod(x, vn, Jv)
-        if ev: ev[2].record(stream)
+        ev[2].record(stream)
         H.jtprod(x, vm, Jtv)
-        if ev: ev[3].record(stream)
+        ev[3].record(stream)
         H.hprod(x, y, sigma, vn, Hv)
-        if ev: ev[4].record(stream)
+        ev[4].record(stream)
 
     for _ in range(args.warmup):
         flush.zero_()
         step()
     torch.cuda.synchronize(dev)
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
     sampler = ClockSampler(dev.index if rank == 0 else -1) if rank == 0 else None
     if sampler:
         sampler.start()
@@ -189,19 +196,27 @@ def run_ours(args, rank, world):
     t0 = time.perf_counter()
     for k in range(args.steps):
         flush.zero_()
-        step(evs[k])
+        evs[k][0].record(stream)
+        step()
+        evs[k][1].record(stream)
     torch.cuda.synchronize(dev)
     wall = time.perf_counter() - t0
     if world > 1:
         torch.distributed.barrier()
     clocks = sampler.stop() if sampler else None
-    per = np.array([[evs[k][i].elapsed_time(evs[k][i + 1]) for i in range(4)] for k in range(args.steps)])
-    step_ms = per.sum(axis=1)
+    step_ms = np.array([evs[k][0].elapsed_time(evs[k][1]) for k in range(args.steps)])
     tot_ms = float(step_ms.sum())
     if world > 1:
         t = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         tot_ms = float(t.item())
+    # --- the same work as four separate calls (per-kernel breakdown)
+    sev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(min(args.steps, 50))]
+    for ev in sev:
+        flush.zero_()
+        separate(ev)
+    torch.cuda.synchronize(dev)
+    per = np.array([[ev[i].elapsed_time(ev[i + 1]) for i in range(4)] for ev in sev])
     kern_ms = per.mean(axis=0)
     # --- J+H alone (the fused Jacobian+Hessian values launch), timed the same way
     jh = []
@@ -237,27 +252,31 @@ def run_ours(args, rank, world):
     nnz = nnzj + nnzh
     e2e_val = nnz * world / (float(np.mean(e2e_ms)) * 1e-3)
     hbm, peak_kind = peaks()
-    ab = algorithmic_bytes(w, "eval_all")
-    achieved = ab / (kern_ms[0] * 1e-3) / 1e9
+    step_mean = tot_ms / args.steps
+    ab = algorithmic_bytes(w, "step")
+    achieved = ab / (step_mean * 1e-3) / 1e9
     clk = (clocks or {}).get("sm_mhz") or 2070.0
     fp64_peak = FP64_INST_PER_CLK_PER_SM * NUM_SMS * clk * 1e6 / 1e9   # G FP64 inst/s
-    ops = FP64_OPS_PER_NODE.get((w["model"], "eval_all"))
-    fp64_ach = ops * (w["N"] + 1) / (kern_ms[0] * 1e-3) / 1e9 if ops else None
+    ops = FP64_OPS_PER_NODE.get((w["model"], "step"))
+    fp64_ach = ops * (w["N"] + 1) / (step_mean * 1e-3) / 1e9 if ops else None
     res = dict(
         metric=METRIC, value=nnz * args.steps * world / (tot_ms * 1e-3), unit="nnz/s", n_gpus=world,
         steps=args.steps, warmup=args.warmup, ms_per_step=tot_ms / args.steps, higher_is_better=True,
         scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
         config=dict(workload=args.workload, model=w["model"], N=w["N"], n=n, m=m, nnz_jac=nnzj, nnz_hess=nnzh,
-                    step="eval_all(F,c,grad,J,H)+jprod+jtprod+hprod", l2="flushed between steps (512 MB write)",
+                    step="ocp_eval_step: F, c, grad, J, H, Jv, J^T w, Hv in one pass",
+                    l2="flushed between steps (512 MB write)",
                     parallelism="replicas" if world > 1 else "single"),
         roofline=dict(bound="alu", achieved=fp64_ach, peak=fp64_peak, unit="G FP64 inst/s",
-                      frac=(fp64_ach / fp64_peak) if fp64_ach else None, traffic=TRAFFIC.get((w["model"], "eval_all")),
-                      kernel="k_node_eval (fused eval_all)", fp64_inst_per_node=ops,
+                      frac=(fp64_ach / fp64_peak) if fp64_ach else None, traffic=TRAFFIC.get((w["model"], "step")),
+                      kernel="k_node_eval<step> (fused step: F, c, grad, J, H, Jv, J^T w, Hv)",
+                      fp64_inst_per_node=ops,
                       peak_basis="%.0f FP64 inst/clk/SM x %d SMs x %.0f MHz (median SM clock under load)"
                                  % (FP64_INST_PER_CLK_PER_SM, NUM_SMS, clk)),
         roofline_hbm=dict(bound="hbm", achieved=achieved, peak=hbm, unit="GB/s", frac=achieved / hbm,
                           peak_source=peak_kind, algorithmic_bytes=ab,
-                          traffic=TRAFFIC.get((w["model"], "eval_all"))),
+                          traffic=TRAFFIC.get((w["model"], "step"))),
+        separate_calls_ms=float(kern_ms.sum()),
         kernels={nm: dict(ms=float(kern_ms[i]), GBps=algorithmic_bytes(w, nm) / (kern_ms[i] * 1e-3) / 1e9,
                           hbm_frac=algorithmic_bytes(w, nm) / (kern_ms[i] * 1e-3) / 1e9 / hbm,
                           fp64_frac=(FP64_OPS_PER_NODE[(w["model"], nm)] * (w["N"] + 1) / (kern_ms[i] * 1e-3) / 1e9
@@ -268,7 +287,7 @@ def run_ours(args, rank, world):
                            frac=algorithmic_bytes(w, "jh") / (jh_ms * 1e-3) / 1e9 / hbm),
         e2e=dict(value=e2e_val, unit="nnz/s", h2d_bytes_per_step=8 * (n + m + n + m),
                  d2h_bytes_per_step=8 * sum(t.numel() for t in outs), ms=float(np.mean(e2e_ms))),
-        gpu_launches=4 * args.steps, clocks=clocks, wall_s=wall,
+        gpu_launches=args.steps, clocks=clocks, wall_s=wall,
     )
     return res
 
@@ -384,6 +403,7 @@ def run_profile(args):
         "jprod": lambda: H.jprod(x, vn, Jv),
         "jtprod": lambda: H.jtprod(x, vm, Jtv),
         "hprod": lambda: H.hprod(x, y, 1.0, vn, Hv),
+        "step": lambda: H.eval_step(x, y, 1.0, vn, vm, (f, c, g, jv, hv, Jv, Jtv, Hv)),
     }
     fns = list(calls.values()) if args.profile_kernel == "all" else [calls[args.profile_kernel]]
     for _ in range(args.warmup + args.steps):
@@ -426,7 +446,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-forms", action="store_true", help="skip the batched and differentiation forms")
     ap.add_argument("--profile-kernel", default=None,
-                    choices=["eval_all", "jh", "jprod", "jtprod", "hprod", "all"],
+                    choices=["eval_all", "jh", "jprod", "jtprod", "hprod", "step", "all"],
                     help="only launch this call warmup+steps times (for ncu captures)")
     args = ap.parse_args()
     if args.profile_kernel:

@@ -122,6 +122,15 @@ ocp_status hprod(ocp_t* h, const double* x, const double* y, double sigma, const
 ocp_status ocp_eval_all(ocp_t* h, const double* x, const double* y, double sigma, double* f,
                         double* c, double* g, double* jvals, double* hvals, void* stream);
 
+/* The whole per-iteration evaluation in one pass over the nodes: everything of ocp_eval_all
+ * plus the products Jv = J vn, Jtv = J^T vm and Hv = H(y, sigma) vn at the same x, sharing the
+ * per-node derivative work and the loads of x and y (one launch for the node models; the heat
+ * model runs its four kernels in sequence).  vn has length n, vm length m.  All arguments are
+ * required.  Values are bit-identical to the separate calls. */
+ocp_status ocp_eval_step(ocp_t* h, const double* x, const double* y, double sigma, const double* vn,
+                         const double* vm, double* f, double* c, double* g, double* jvals,
+                         double* hvals, double* Jv, double* Jtv, double* Hv, void* stream);
+
 /* Parameter derivative for the Van der Pol model (mu = params[0]):
  *   dmu = (dc/dmu)^T w   (device scalar),  optionally together with J^T w into Jtw (may be NULL).
  * Other models: OCP_EMODEL. */

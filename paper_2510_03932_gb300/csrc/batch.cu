@@ -9,10 +9,12 @@
 //
 // Work decomposition: instance i is cut into tiles of NPT*TILE nodes (owning NPT*TILE-1); the
 // tiles of all instances form one index space.  A persistent grid of (CTAs per SM) x (SMs)
-// CTAs walks it in a fixed round-robin order; a CTA maps its tile to the instance by binary
-// search over the tile prefix sums, copies that instance's argument block into shared
-// memory, and runs the same tile body as the plain kernel.  The last CTA to finish sums the
-// per-tile objective terms of each instance in tile order.  No spin waits, no value atomics.
+// CTAs takes tiles from an atomic work counter (dynamic balance; no CTA ever waits for
+// another); a CTA maps its tile to the instance by binary search over the tile prefix sums,
+// copies that instance's argument block into shared memory, and runs the same tile body as
+// the plain kernel.  Each tile's objective term goes to its own slot; the CTA completing an
+// instance's last tile (per-instance completion counter) sums that instance's slots in tile
+// order, so the objective does not depend on the scheduling.  Counters are reset in-kernel.
 //
 // Tuning: threads per CTA (64, 128, 256), nodes per thread (1, 2: nodes per warp 32 or 64) and
 // CTAs per SM are chosen by ocp_batch_autotune, which times every candidate on the caller's
@@ -40,7 +42,9 @@ struct BatchArgs {
   const double* y;
   double *f, *c, *g, *jv, *hv;
   double* partials;
-  unsigned* counter;
+  unsigned* counter;             // CTAs that finished (reset by the last one)
+  unsigned long long* work;      // next tile to take (reset by the last CTA)
+  unsigned* icount;              // per instance: tiles completed (reset by the finishing CTA)
   double sigma;
   int64_t ntiles;
   int count;
@@ -49,11 +53,17 @@ struct BatchArgs {
 template <class M, int TILE, int NPT>
 __global__ void __launch_bounds__(TILE) k_batch_eval(const __grid_constant__ BatchArgs<M> b) {
   extern __shared__ __align__(16) double sm[];
-  __shared__ double sEdge[(TILE / 32 + 1) * M::NX];
+  __shared__ double sEdge[2 * (TILE / 32 + 1) * M::NX];
   __shared__ NodeArgs<M> sa;
-  __shared__ int s_inst;
+  __shared__ long long s_tile;
+  __shared__ int s_inst, s_fin;
   static_assert(sizeof(NodeArgs<M>) % 8 == 0, "argument block is copied in 8-byte words");
-  for (int64_t gt = blockIdx.x; gt < b.ntiles; gt += gridDim.x) {
+  for (;;) {
+    // dynamic tile scheduling: results do not depend on which CTA takes which tile
+    if (threadIdx.x == 0) s_tile = (long long)atomicAdd(b.work, 1ull);
+    __syncthreads();
+    const int64_t gt = s_tile;
+    if (gt >= b.ntiles) break;
     if (threadIdx.x == 0) {
       int lo = 0, hi = b.count - 1;  // last instance whose first tile is <= gt
       while (lo < hi) {
@@ -85,26 +95,38 @@ __global__ void __launch_bounds__(TILE) k_batch_eval(const __grid_constant__ Bat
     }
     __syncthreads();
     const ModelConst K = sa.K;
-    node_eval_tile<M, TILE, NPT, O_ALL>(sa, K, gt - __ldg(b.tileoff + i), sm, sEdge, b.partials + gt);
+    const int64_t t0 = __ldg(b.tileoff + i), t1 = __ldg(b.tileoff + i + 1);
+    node_eval_tile<M, TILE, NPT, O_ALL>(sa, K, gt - t0, sm, sEdge, b.partials + gt);
+    if (b.f) {
+      // the CTA that completes an instance's last tile sums its tile terms in tile order
+      if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned done = atomicAdd(b.icount + i, 1u);
+        s_fin = (done == (unsigned)(t1 - t0 - 1));
+      }
+      __syncthreads();
+      if (s_fin) {
+        __threadfence();
+        double s = 0.0;
+        for (int64_t t = t0 + threadIdx.x; t < t1; t += TILE) s += __ldcg(b.partials + t);
+        s = cta_sum<TILE>(s, sm);
+        if (threadIdx.x == 0) {
+          b.f[i] = 0.5 * s;
+          b.icount[i] = 0u;
+        }
+      }
+      __syncthreads();
+    }
   }
-  if (b.f) {
-    __shared__ int s_last;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      __threadfence();
-      const unsigned ticket = atomicAdd(b.counter, 1u);
-      s_last = (ticket == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!s_last) return;
+  // the last CTA to leave resets the work counter for the next launch
+  if (threadIdx.x == 0) {
     __threadfence();
-    for (int i = threadIdx.x; i < b.count; i += TILE) {
-      double s = 0.0;
-      const int64_t t1 = __ldg(b.tileoff + i + 1);
-      for (int64_t t = __ldg(b.tileoff + i); t < t1; ++t) s += __ldcg(b.partials + t);
-      b.f[i] = 0.5 * s;
+    const unsigned left = atomicAdd(b.counter, 1u);
+    if (left == gridDim.x - 1) {
+      *b.work = 0ull;
+      *b.counter = 0u;
+      __threadfence();
     }
-    if (threadIdx.x == 0) *b.counter = 0u;
   }
 }
 
@@ -212,6 +234,8 @@ static ocp_status batch_launch(ocp_batch* b, const double* x, const double* y, d
   a.tileoff = b->d_tileoff; a.xoff = b->d_xoff; a.coff = b->d_coff; a.joff = b->d_joff; a.hoff = b->d_hoff;
   a.x = x; a.y = y; a.f = f; a.c = c; a.g = g; a.jv = jv; a.hv = hv;
   a.partials = b->d_partials; a.counter = b->d_counter;
+  a.work = (unsigned long long*)(b->d_counter + 2);
+  a.icount = b->d_counter + 4;
   a.sigma = sigma;
   a.ntiles = b->ntiles;
   a.count = b->count;
@@ -282,8 +306,8 @@ ocp_status ocp_batch_create(ocp_t* const* items, int count, ocp_batch_t** out) {
   if (!up(&b->d_xoff, b->xoff) || !up(&b->d_coff, b->coff) || !up(&b->d_joff, b->joff) || !up(&b->d_hoff, b->hoff) ||
       cudaMalloc(&b->d_tileoff, sizeof(int64_t) * (count + 1)) != cudaSuccess ||
       cudaMalloc(&b->d_partials, sizeof(double) * cap) != cudaSuccess ||
-      cudaMalloc(&b->d_counter, sizeof(unsigned)) != cudaSuccess ||
-      (e = cudaMemset(b->d_counter, 0, sizeof(unsigned))) != cudaSuccess) {
+      cudaMalloc(&b->d_counter, sizeof(unsigned) * (4 + count)) != cudaSuccess ||
+      (e = cudaMemset(b->d_counter, 0, sizeof(unsigned) * (4 + count))) != cudaSuccess) {
     batch_free(b);
     return set_err(nullptr, OCP_ENOMEM, "device allocation failed for the batch");
   }

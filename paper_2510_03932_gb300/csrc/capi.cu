@@ -351,6 +351,25 @@ ocp_status ocp_eval_all(ocp_t* h, const double* x, const double* y, double sigma
   return dispatch_eval(h, out, c, stream);
 }
 
+ocp_status ocp_eval_step(ocp_t* h, const double* x, const double* y, double sigma, const double* vn, const double* vm,
+                         double* f, double* cv, double* g, double* jvals, double* hvals, double* Jv, double* Jtv,
+                         double* Hv, void* stream) {
+  if (!h) return OCP_EINVAL;
+  NEED(x); NEED(y); NEED(vn); NEED(vm); NEED(f); NEED(cv); NEED(g); NEED(jvals); NEED(hvals);
+  NEED(Jv); NEED(Jtv); NEED(Hv);
+  if (h->model == OCP_MODEL_HEAT1D) {  // the heat model runs its four kernels in sequence
+    ocp_status st = ocp_eval_all(h, x, y, sigma, f, cv, g, jvals, hvals, stream);
+    if (st == OCP_OK) st = jprod(h, x, vn, Jv, stream);
+    if (st == OCP_OK) st = jtprod(h, x, vm, Jtv, stream);
+    if (st == OCP_OK) st = hprod(h, x, y, sigma, vn, Hv, stream);
+    return st;
+  }
+  EvalCall c = full_call(h);
+  c.x = x; c.y = y; c.sigma = sigma; c.f = f; c.c = cv; c.g = g; c.jv = jvals; c.hv = hvals;
+  c.vn = vn; c.vm = vm; c.ojv = Jv; c.ojtv = Jtv; c.ohv = Hv;
+  return dispatch_eval(h, O_STEP, c, stream);
+}
+
 ocp_status ocp_eval_all_range(ocp_t* h, int64_t node_begin, int64_t node_end, const double* x, const double* y,
                               double sigma, double* f, double* cv, double* g, double* jvals, double* hvals,
                               void* stream) {

@@ -62,6 +62,10 @@ struct NodeArgs {
   double* jv;
   double* hv;
   double* out;                    // products: result
+  const double* __restrict__ wv;  // fused step: direction of J^T w (length m)
+  double* ojv;                    // fused step: J v   (length m)
+  double* ojtv;                   // fused step: J^T w (length n)
+  double* ohv;                    // fused step: H v   (length n)
   double* partials;
   unsigned* counter;
   double* dmu;                    // jtprod with the parameter derivative
@@ -232,6 +236,116 @@ __device__ __forceinline__ double node_grad(const NodeArgs<M>& a, const double (
   return s;
 }
 
+// ---- per-node product terms, shared by the product kernels and the fused step -----------
+// Jv: with p_k = -hh grad f_k(z_j) . v_{z_j} (+ -hh df_k/dmu * pdir), A_k = p_k + v_{X_j,k} is the
+// node's share of row (k, j-1) and B_k = p_k - v_{X_j,k} its share of row (k, j); the last term
+// of p_k is fused into both.
+template <class M, bool PDIR>
+__device__ __forceinline__ void jv_node(const double (&mjx)[M::NX][M::MAXRX], const double (&mju)[M::NX][M::MAXRU],
+                                        const double (&mdp)[M::NX], double pd, const double (&vz)[M::NZ],
+                                        double (&A)[M::NX], double (&Bm)[M::NX]) {
+  constexpr int NX = M::NX;
+#pragma unroll
+  for (int k = 0; k < NX; ++k) {
+    double cf[M::MAXRX + M::MAXRU + 1], vv[M::MAXRX + M::MAXRU + 1];
+    int nt = 0;
+#pragma unroll
+    for (int e = 0; e < M::RX(k); ++e)
+      if (!M::JZ(k, e)) { cf[nt] = mjx[k][e]; vv[nt] = vz[M::XV(k, e)]; ++nt; }
+#pragma unroll
+    for (int e = 0; e < M::RU(k); ++e) { cf[nt] = mju[k][e]; vv[nt] = vz[NX + M::UV(k, e)]; ++nt; }
+    if (PDIR) { cf[nt] = mdp[k]; vv[nt] = pd; ++nt; }
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i + 1 < nt; ++i) s = (i == 0) ? cf[i] * vv[i] : fma(cf[i], vv[i], s);
+    const double vk = vz[k];
+    if (nt == 0) {
+      A[k] = vk;
+      Bm[k] = -vk;
+    } else if (nt == 1) {
+      A[k] = fma(cf[0], vv[0], vk);
+      Bm[k] = fma(cf[0], vv[0], -vk);
+    } else {
+      A[k] = fma(cf[nt - 1], vv[nt - 1], s + vk);
+      Bm[k] = fma(cf[nt - 1], vv[nt - 1], s - vk);
+    }
+  }
+}
+
+// J^T w at node j: (w_{a,j-1} - w_{a,j}) + sum_k wbar_k mjx_{k,a}, the control entries
+// sum_k wbar_k mju_{k,i}, plus the boundary rows' w at j = 0 / N (bnd: this CTA may hold them).
+template <class M>
+__device__ __forceinline__ void jtv_node(const NodeArgs<M>& a, const double* w, int64_t j, bool bnd,
+                                         const double (&mjx)[M::NX][M::MAXRX], const double (&mju)[M::NX][M::MAXRU],
+                                         const double (&wl)[M::NX], const double (&wr)[M::NX],
+                                         const double (&wb)[M::NX], double (&o)[M::NZ]) {
+  constexpr int NX = M::NX;
+#pragma unroll
+  for (int v = 0; v < NX; ++v) {
+    double s = wl[v] - wr[v];
+#pragma unroll
+    for (int k = 0; k < NX; ++k)
+#pragma unroll
+      for (int e = 0; e < M::RX(k); ++e)
+        if (M::XV(k, e) == v && !M::JZ(k, e)) s = fma(wb[k], mjx[k][e], s);
+    if (bnd) {  // only CTAs holding node 0 or node N (uniform branch)
+      if (j == 0) s += __ldg(w + v);
+      if (a.has_final && j == a.N) s += __ldg(w + NX + v);
+    }
+    o[v] = s;
+  }
+#pragma unroll
+  for (int i = 0; i < M::NU; ++i) {
+    double s = 0.0;
+    bool first = true;
+#pragma unroll
+    for (int k = 0; k < NX; ++k)
+#pragma unroll
+      for (int e = 0; e < M::RU(k); ++e)
+        if (M::UV(k, e) == i) { s = first ? wb[k] * mju[k][e] : fma(wb[k], mju[k][e], s); first = false; }
+    o[NX + i] = s;
+  }
+}
+
+// H v at node j: the full symmetric block (structural entries only) times v_{z_j}.
+template <class M>
+__device__ __forceinline__ void hv_node(const NodeArgs<M>& a, const double* hd, const double (&cqd)[M::NZ],
+                                        const double (&vz)[M::NZ], double (&o)[M::NZ]) {
+  constexpr HTmpl<M> HT{};
+  bool first[M::NZ];
+#pragma unroll
+  for (int v = 0; v < M::NZ; ++v) { o[v] = 0.0; first[v] = true; }
+#pragma unroll
+  for (int e = 0; e < HT.n; ++e) {
+    if (a.hpos[e] >= 0) {
+      const int aa = HT.a[e], bb = HT.b[e];
+      const double val = (HT.dyn[e] >= 0) ? hd[HT.dyn[e] >= 0 ? HT.dyn[e] : 0] : cqd[aa];
+      o[aa] = first[aa] ? val * vz[bb] : fma(val, vz[bb], o[aa]);
+      first[aa] = false;
+      if (aa != bb) {
+        o[bb] = first[bb] ? val * vz[aa] : fma(val, vz[aa], o[bb]);
+        first[bb] = false;
+      }
+    }
+  }
+}
+
+template <class M>
+__device__ __forceinline__ void load_vz(const NodeArgs<M>& a, const double* v, int64_t j, double (&vz)[M::NZ]) {
+#pragma unroll
+  for (int k = 0; k < M::NX; ++k) vz[k] = __ldg(v + M::NX * j + k);
+#pragma unroll
+  for (int i = 0; i < M::NU; ++i) vz[M::NX + i] = __ldg(v + a.uoff + M::NU * j + i);
+}
+
+template <class M>
+__device__ __forceinline__ void store_nz(const NodeArgs<M>& a, double* out, int64_t j, const double (&o)[M::NZ]) {
+#pragma unroll
+  for (int v = 0; v < M::NX; ++v) out[M::NX * j + v] = o[v];
+#pragma unroll
+  for (int i = 0; i < M::NU; ++i) out[a.uoff + M::NU * j + i] = o[M::NX + i];
+}
+
 // One tile of the fused evaluation.  The CTA's TILE threads cover NPT*TILE consecutive
 // nodes r0.. (thread t takes nodes r0 + NPT t + q, q < NPT: consecutive pairs give each thread
 // independent FP64 dependency chains) and own the first NPT*TILE - 1 of them.  `a` may live in
@@ -243,6 +357,8 @@ __device__ __forceinline__ void node_eval_tile(const NodeArgs<M>& a, const Model
   constexpr int NX = M::NX, NZ = M::NZ;
   constexpr int NT = NPT * TILE;  // nodes per tile
   constexpr bool WF = OUT & O_F, WC = OUT & O_C, WG = OUT & O_G, WJ = OUT & O_J, WH = OUT & O_H;
+  constexpr bool WJV = OUT & O_JV, WJTV = OUT & O_JTV, WHV = OUT & O_HV;  // fused step products
+  constexpr bool NEEDJ = WJ || WJV || WJTV, NEEDH = WH || WHV;
   // the full kernel also serves output subsets: NULL outputs are computed but not stored
   const bool sF = WF && a.f, sC = WC && a.c, sG = WG && a.g, sJ = WJ && a.jv, sH = WH && a.hv;
   constexpr HTmpl<M> HT{};
@@ -259,6 +375,8 @@ __device__ __forceinline__ void node_eval_tile(const NodeArgs<M>& a, const Model
   const int nrows = (int)max(row_end - r0, (int64_t)0);
   double objterm = 0.0;
   double pa[NPT][NX], pb[NPT][NX];
+  double jA[NPT][NX], jB[NPT][NX];     // fused step: node shares of the Jv rows
+  const bool bnd = (r0 == 0) || (r0 + R > a.N);  // tile may hold node 0 or node N (uniform)
 
 #pragma unroll
   for (int q = 0; q < NPT; ++q) {
@@ -269,14 +387,43 @@ __device__ __forceinline__ void node_eval_tile(const NodeArgs<M>& a, const Model
     const bool endp = (j == 0) || (j == a.N);
     double z[NZ], yb[NX], cqd[NZ], mjx[NX][M::MAXRX], mju[NX][M::MAXRU], hd[NHD];
 #pragma unroll
-    for (int k = 0; k < NX; ++k) { pa[q][k] = 0.0; pb[q][k] = 0.0; }
+    for (int k = 0; k < NX; ++k) { pa[q][k] = 0.0; pb[q][k] = 0.0; jA[q][k] = 0.0; jB[q][k] = 0.0; }
+    double vz[NZ];
     if (act) {
       load_node<M>(a, j, z);
-      if (WH) {
+      if (NEEDH) {
         load_ybar<M>(a, a.y, j, yb);
         node_cq<M>(a, endp, cqd);
       }
-      M::template eval<WC, WJ, WH>(K, z, yb, cqd, pa[q], pb[q], mjx, mju, hd);
+      M::template eval<WC, NEEDJ, NEEDH>(K, z, yb, cqd, pa[q], pb[q], mjx, mju, hd);
+      if (WJV || WHV) load_vz<M>(a, a.v, j, vz);
+      if (WJV) {
+        double mdp[NX];
+        jv_node<M, false>(mjx, mju, mdp, 0.0, vz, jA[q], jB[q]);
+      }
+    }
+    if (own) {
+      if (WHV) {
+        double o[NZ];
+        hv_node<M>(a, hd, cqd, vz, o);
+        store_nz<M>(a, a.ohv, j, o);
+      }
+      if (WJTV) {
+        double wb[NX], wl[NX], wr[NX], o[NZ];
+        load_bar<M>(a, a.wv, j, wb, wl, wr);
+        jtv_node<M>(a, a.wv, j, bnd, mjx, mju, wl, wr, wb, o);
+        store_nz<M>(a, a.ojtv, j, o);
+      }
+      if (WJV && bnd) {
+        if (j == 0) {
+#pragma unroll
+          for (int k = 0; k < NX; ++k) a.ojv[k] = vz[k];
+        }
+        if (a.has_final && j == a.N) {
+#pragma unroll
+          for (int k = 0; k < NX; ++k) a.ojv[NX + k] = vz[k];
+        }
+      }
     }
     if (own) {
       // ---- Hessian block of node j (stored directly; X block then U block)
@@ -337,8 +484,8 @@ __device__ __forceinline__ void node_eval_tile(const NodeArgs<M>& a, const Model
       }
     }
   }
-  // ---- defects: the right node's x - hh f is this thread's next node, or lane+1's first
-  double nbv[NX];
+  // ---- defects (and Jv rows): the right node's share is this thread's next node, or lane+1's first
+  double nbv[NX], nbA[NX];
   if (WC) {
 #pragma unroll
     for (int k = 0; k < NX; ++k) {
@@ -346,7 +493,31 @@ __device__ __forceinline__ void node_eval_tile(const NodeArgs<M>& a, const Model
       if (lane == 0) sEdge[warp * NX + k] = pb[0][k];
     }
   }
-  if (WC || WJ) __syncthreads();
+  if (WJV) {
+    constexpr int EO = (TILE / 32 + 1) * NX;
+#pragma unroll
+    for (int k = 0; k < NX; ++k) {
+      nbA[k] = __shfl_down_sync(0xffffffffu, jA[0][k], 1);
+      if (lane == 0) sEdge[EO + warp * NX + k] = jA[0][k];
+    }
+  }
+  if (WC || WJ || WJV) __syncthreads();
+  if (WJV) {
+    constexpr int EO = (TILE / 32 + 1) * NX;
+#pragma unroll
+    for (int q = 0; q < NPT; ++q) {
+      const int lt = NPT * t + q;
+      if (lt < nrows) {
+#pragma unroll
+        for (int k = 0; k < NX; ++k) {
+          double right;
+          if (q + 1 < NPT) right = jA[q + 1 < NPT ? q + 1 : 0][k];
+          else right = (lane == 31) ? sEdge[EO + (warp + 1) * NX + k] : nbA[k];
+          a.ojv[a.nb + (int64_t)k * a.N + r0 + lt] = jB[q][k] + right;
+        }
+      }
+    }
+  }
   if (sC) {
 #pragma unroll
     for (int q = 0; q < NPT; ++q) {
@@ -377,14 +548,14 @@ __device__ __forceinline__ void node_eval_tile(const NodeArgs<M>& a, const Model
     const double ts = tile_sum<TILE>(objterm, sm + oRED);
     if (t == 0) *partial = ts;
   }
-  if (WC || WJ || WF) __syncthreads();
+  if (WC || WJ || WF || WJV) __syncthreads();
 }
 
 template <class M, int TILE, int NPT, unsigned OUT>
 __global__ void __launch_bounds__(TILE) k_node_eval(const __grid_constant__ NodeArgs<M> a) {
   constexpr bool WF = OUT & O_F;
   extern __shared__ __align__(16) double sm[];
-  __shared__ double sEdge[(TILE / 32 + 1) * M::NX];
+  __shared__ double sEdge[2 * (TILE / 32 + 1) * M::NX];
   ModelConst K = a.K;
   if (a.p0_dev) M::device_param(K, __ldg(a.p0_dev));
   for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x)
@@ -420,39 +591,13 @@ __global__ void __launch_bounds__(TILE) k_node_jprod(const __grid_constant__ Nod
     if (act) {
       double z[NZ], vz[NZ], yb[NX], cqd[NZ], pa[NX], pb[NX], mjx[NX][M::MAXRX], mju[NX][M::MAXRU], hd[NHD];
       load_node<M>(a, j, z);
+      load_vz<M>(a, a.v, j, vz);
 #pragma unroll
-      for (int k = 0; k < NX; ++k) { vz[k] = __ldg(a.v + NX * j + k); vx[k] = vz[k]; }
-#pragma unroll
-      for (int i = 0; i < M::NU; ++i) vz[NX + i] = __ldg(a.v + a.uoff + M::NU * j + i);
+      for (int k = 0; k < NX; ++k) vx[k] = vz[k];
       M::template eval<false, true, false>(K, z, yb, cqd, pa, pb, mjx, mju, hd);
       double mdp[NX];
       if (PDIR) M::dparam(K, z, mdp);
-#pragma unroll
-      for (int k = 0; k < NX; ++k) {
-        // terms c_i * v_i of p_k in template order; the last one is fused into both
-        // A = p + v_{X_j,k} and B = p - v_{X_j,k}
-        double cf[M::MAXRX + M::MAXRU + 1], vv[M::MAXRX + M::MAXRU + 1];
-        int nt = 0;
-#pragma unroll
-        for (int e = 0; e < M::RX(k); ++e)
-          if (!M::JZ(k, e)) { cf[nt] = mjx[k][e]; vv[nt] = vz[M::XV(k, e)]; ++nt; }
-#pragma unroll
-        for (int e = 0; e < M::RU(k); ++e) { cf[nt] = mju[k][e]; vv[nt] = vz[NX + M::UV(k, e)]; ++nt; }
-        if (PDIR) { cf[nt] = mdp[k]; vv[nt] = pd; ++nt; }
-        double s = 0.0;
-#pragma unroll
-        for (int i = 0; i + 1 < nt; ++i) s = (i == 0) ? cf[i] * vv[i] : fma(cf[i], vv[i], s);
-        if (nt == 0) {
-          A[k] = vx[k];
-          p[k] = -vx[k];
-        } else if (nt == 1) {
-          A[k] = fma(cf[0], vv[0], vx[k]);
-          p[k] = fma(cf[0], vv[0], -vx[k]);
-        } else {
-          A[k] = fma(cf[nt - 1], vv[nt - 1], s + vx[k]);
-          p[k] = fma(cf[nt - 1], vv[nt - 1], s - vx[k]);
-        }
-      }
+      jv_node<M, PDIR>(mjx, mju, mdp, pd, vz, A, p);
       if (j == 0) {
 #pragma unroll
         for (int k = 0; k < NX; ++k) a.out[k] = vx[k];
@@ -503,31 +648,9 @@ __global__ void __launch_bounds__(TILE) k_node_jtprod(const __grid_constant__ No
       load_node<M>(a, j, z);
       load_bar<M>(a, a.v, j, wb, wl, wr);
       M::template eval<false, true, false>(K, z, yb, cqd, pa, pb, mjx, mju, hd);
-#pragma unroll
-      for (int v = 0; v < NX; ++v) {
-        double s = wl[v] - wr[v];
-#pragma unroll
-        for (int k = 0; k < NX; ++k)
-#pragma unroll
-          for (int e = 0; e < M::RX(k); ++e)
-            if (M::XV(k, e) == v && !M::JZ(k, e)) s = fma(wb[k], mjx[k][e], s);
-        if (bnd) {  // only the CTAs holding node 0 or node N (uniform branch)
-          if (j == 0) s += __ldg(a.v + v);
-          if (a.has_final && j == a.N) s += __ldg(a.v + NX + v);
-        }
-        a.out[NX * j + v] = s;
-      }
-#pragma unroll
-      for (int i = 0; i < M::NU; ++i) {
-        double s = 0.0;
-        bool first = true;
-#pragma unroll
-        for (int k = 0; k < NX; ++k)
-#pragma unroll
-          for (int e = 0; e < M::RU(k); ++e)
-            if (M::UV(k, e) == i) { s = first ? wb[k] * mju[k][e] : fma(wb[k], mju[k][e], s); first = false; }
-        a.out[a.uoff + M::NU * j + i] = s;
-      }
+      double o[NZ];
+      jtv_node<M>(a, a.v, j, bnd, mjx, mju, wl, wr, wb, o);
+      store_nz<M>(a, a.out, j, o);
       if (DPAR) {
         double mdp[NX];
         M::dparam(K, z, mdp);
@@ -576,22 +699,7 @@ __global__ void __launch_bounds__(TILE) k_node_hprod(const __grid_constant__ Nod
       for (int i = 0; i < M::NU; ++i) vz[NX + i] = __ldg(a.v + a.uoff + M::NU * j + i);
       M::template eval<false, false, true>(K, z, yb, cqd, pa, pb, mjx, mju, hd);
       double o[NZ];
-      bool first[NZ];
-#pragma unroll
-      for (int v = 0; v < NZ; ++v) { o[v] = 0.0; first[v] = true; }
-#pragma unroll
-      for (int e = 0; e < HT.n; ++e) {
-        if (a.hpos[e] >= 0) {
-          const int aa = HT.a[e], bb = HT.b[e];
-          const double val = (HT.dyn[e] >= 0) ? hd[HT.dyn[e] >= 0 ? HT.dyn[e] : 0] : cqd[aa];
-          o[aa] = first[aa] ? val * vz[bb] : fma(val, vz[bb], o[aa]);
-          first[aa] = false;
-          if (aa != bb) {
-            o[bb] = first[bb] ? val * vz[aa] : fma(val, vz[aa], o[bb]);
-            first[bb] = false;
-          }
-        }
-      }
+      hv_node<M>(a, hd, cqd, vz, o);
       if (MIX) {
         double mb[NX], mg[NZ], wl[NX], wr[NX];
         load_bar<M>(a, a.mixw, j, mb, wl, wr);
@@ -602,10 +710,7 @@ __global__ void __launch_bounds__(TILE) k_node_hprod(const __grid_constant__ Nod
           acc_mu = fma(mg[v], vz[v], acc_mu);
         }
       }
-#pragma unroll
-      for (int v = 0; v < NX; ++v) a.out[NX * j + v] = o[v];
-#pragma unroll
-      for (int i = 0; i < M::NU; ++i) a.out[a.uoff + M::NU * j + i] = o[NX + i];
+      store_nz<M>(a, a.out, j, o);
     }
     if (MIX && a.dmu) {
       const double ts = tile_sum<TILE>(acc_mu, red);
@@ -652,6 +757,7 @@ ocp_status launch_eval_t(ocp* h, const EvalCall& c, cudaStream_t s) {
   NodeArgs<M> a;
   fill_args<M>(h, c.sigma, a);
   a.x = c.x; a.y = c.y; a.f = c.f; a.c = c.c; a.g = c.g; a.jv = c.jv; a.hv = c.hv;
+  a.v = c.vn; a.wv = c.vm; a.ojv = c.ojv; a.ojtv = c.ojtv; a.ohv = c.ohv;
   a.B = c.B; a.E = c.E;
   a.range = c.range ? 1 : 0;
   const int64_t nodes = c.E - c.B;
@@ -681,6 +787,7 @@ ocp_status node_eval_dispatch(ocp* h, unsigned out, const EvalCall& c, cudaStrea
     case O_J: return launch_eval_t<M, TILE, 1, O_J>(h, c, s);
     case O_H: return launch_eval_t<M, TILE, 1, O_H>(h, c, s);
     case O_J | O_H: return launch_eval_t<M, TILE, 1, O_J | O_H>(h, c, s);
+    case O_STEP: return launch_eval_t<M, TILE, 1, O_STEP>(h, c, s);
     default: return launch_eval_t<M, TILE, 1, O_ALL>(h, c, s);
   }
 }

@@ -17,7 +17,9 @@ constexpr int TILE_VDP = 256, TILE_CARTPOLE = 128, TILE_DINT = 256;
 constexpr int HEAT_TILE_NODES = 32;
 
 // Output selection bits of the fused evaluation kernels.
-enum : unsigned { O_F = 1u, O_C = 2u, O_G = 4u, O_J = 8u, O_H = 16u, O_ALL = 31u };
+enum : unsigned { O_F = 1u, O_C = 2u, O_G = 4u, O_J = 8u, O_H = 16u, O_ALL = 31u,
+                  // products evaluated in the same pass (the fused step)
+                  O_JV = 32u, O_JTV = 64u, O_HV = 128u, O_STEP = 255u };
 
 // Per-component Jacobian row template (local variable indices), as read from the model.
 struct RowTemplate {
@@ -80,6 +82,10 @@ struct EvalCall {
   const double* y = nullptr;
   double sigma = 1.0;
   double *f = nullptr, *c = nullptr, *g = nullptr, *jv = nullptr, *hv = nullptr;
+  // fused step only: directions and product outputs
+  const double* vn = nullptr;  // length n: for J vn and H vn
+  const double* vm = nullptr;  // length m: for J^T vm
+  double *ojv = nullptr, *ojtv = nullptr, *ohv = nullptr;
   int64_t B = 0, E = 0;  // owned node range [B, E)
   bool range = false;    // f receives the partial sum of this range
 };

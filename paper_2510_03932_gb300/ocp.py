@@ -56,6 +56,7 @@ _SIGS = {
     "jtprod": [_P, _P, _P, _P, _P],
     "hprod": [_P, _P, _P, _D, _P, _P, _P],
     "ocp_eval_all": [_P, _P, _P, _D, _P, _P, _P, _P, _P, _P],
+    "ocp_eval_step": [_P, _P, _P, _D, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P],
     "ocp_eval_all_range": [_P, _I64, _I64, _P, _P, _D, _P, _P, _P, _P, _P, _P],
     "ocp_vjp_param": [_P, _P, _P, _P, _P, _P],
     "ocp_set_param0": [_P, _D],
@@ -246,6 +247,18 @@ class OCP:
         _check(lib().ocp_eval_all(self.h, _ptr(x), _ptr(y), float(sigma), _ptr(f), _ptr(c), _ptr(g), _ptr(jvals),
                                   _ptr(hvals), _stream(stream)), self.h)
         return f, c, g, jvals, hvals
+
+    def eval_step(self, x, y, sigma, vn, vm, outs=None, stream=None):
+        """Fused step: (f, c, g, jvals, hvals, Jv, Jtv, Hv) in one pass; `outs` reuses buffers."""
+        x = self._vec(x, self.n, "x"); y = self._vec(y, self.m, "y")
+        vn = self._vec(vn, self.n, "vn"); vm = self._vec(vm, self.m, "vm")
+        if outs is None:
+            outs = (self._out(None, 1, "f"), self._out(None, self.m, "c"), self._out(None, self.n, "g"),
+                    self._out(None, self.nnzj, "jvals"), self._out(None, self.nnzh, "hvals"),
+                    self._out(None, self.m, "Jv"), self._out(None, self.n, "Jtv"), self._out(None, self.n, "Hv"))
+        _check(lib().ocp_eval_step(self.h, _ptr(x), _ptr(y), float(sigma), _ptr(vn), _ptr(vm),
+                                   *[_ptr(t) for t in outs], _stream(stream)), self.h)
+        return outs
 
     def eval_all_range(self, node_begin, node_end, x, y, sigma, f, c, g, jvals, hvals, stream=None):
         _check(lib().ocp_eval_all_range(self.h, int(node_begin), int(node_end), _ptr(x), _ptr(y), float(sigma),

@@ -182,3 +182,18 @@ def test_dimension_and_argument_errors(ocp):
     st = ocp.lib().ocp_eval_all_range(H.h, 5, 3, C.c_void_p(x.data_ptr()), None, 1.0, None, None, None, None,
                                       None, None)
     assert st == 2  # OCP_EDIM: empty range
+
+
+@pytest.mark.parametrize("name,N", [("vdp_n1e3", 1000), ("vdp_n1e3", 254), ("cartpole_n1e5", 1303),
+                                    ("dint", 97), ("heat_n2e4", 77)])
+def test_fused_step_equals_separate_calls(ocp, name, N):
+    """ocp_eval_step (one pass: eval + Jv + J^T w + Hv) is bit-identical to the separate calls."""
+    w = synth.with_horizon(synth.workload(name), N)
+    d = synth.draw(w)
+    H = ocp.OCP.from_workload(w)
+    x, y, vn, vm = dev(d["x"]), dev(d["y"]), dev(d["vn"]), dev(d["vm"])
+    outs = H.eval_step(x, y, 0.9, vn, vm)
+    sep = list(H.eval_all(x, y, 0.9)) + [H.jprod(x, vn), H.jtprod(x, vm), H.hprod(x, y, 0.9, vn)]
+    torch.cuda.synchronize()
+    for a, b in zip(outs, sep):
+        assert torch.equal(a, b)
