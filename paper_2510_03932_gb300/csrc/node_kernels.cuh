@@ -109,16 +109,17 @@ struct EvalSmem {
   static constexpr size_t bytes = sizeof(double) * total;
 };
 
-__device__ __forceinline__ double warp_sum(double v) {
+// Sums use fma(a, one, b) with one = 1.0 read at run time (see fadd in models.cuh).
+__device__ __forceinline__ double warp_sum(double v, double one) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  for (int o = 16; o > 0; o >>= 1) v = fma(__shfl_xor_sync(0xffffffffu, v, o), one, v);
   return v;
 }
 
 // Fixed-order CTA sum; result valid in thread 0.  `red` holds TILE/32 doubles.
 template <int TILE>
-__device__ __forceinline__ double cta_sum(double v, double* red) {
-  v = warp_sum(v);
+__device__ __forceinline__ double cta_sum(double v, double* red, double one = 1.0) {
+  v = warp_sum(v, one);
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
   __syncthreads();
   if (l == 0) red[w] = v;
@@ -126,7 +127,7 @@ __device__ __forceinline__ double cta_sum(double v, double* red) {
   double s = 0.0;
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int i = 0; i < TILE / 32; ++i) s += red[i];
+    for (int i = 0; i < TILE / 32; ++i) s = fma(red[i], one, s);
   }
   return s;
 }
@@ -135,15 +136,15 @@ __device__ __forceinline__ double cta_sum(double v, double* red) {
 // the TILE/32 values of each lane position, then a warp tree.  Result valid in thread 0.
 // (Cheaper on the FP64 pipe than a tree in every warp.)  `red` holds TILE doubles.
 template <int TILE>
-__device__ __forceinline__ double tile_sum(double v, double* red) {
+__device__ __forceinline__ double tile_sum(double v, double* red, double one) {
   red[threadIdx.x] = v;
   __syncthreads();
   double s = 0.0;
   if (threadIdx.x < 32) {
     s = red[threadIdx.x];
 #pragma unroll
-    for (int i = 1; i < TILE / 32; ++i) s += red[threadIdx.x + 32 * i];
-    s = warp_sum(s);
+    for (int i = 1; i < TILE / 32; ++i) s = fma(red[threadIdx.x + 32 * i], one, s);
+    s = warp_sum(s, one);
   }
   return s;
 }
@@ -166,7 +167,7 @@ __device__ __forceinline__ void finish_tiles(const double* partials, int64_t nti
   if (!s_last) return;
   __threadfence();
   double s = 0.0;
-  for (int64_t i = threadIdx.x; i < ntiles; i += TILE) s += __ldcg(partials + i);
+  for (int64_t i = threadIdx.x; i < ntiles; i += TILE) s = s + __ldcg(partials + i);
   s = cta_sum<TILE>(s, red);
   if (threadIdx.x == 0) {
     *dst = scale * s;
@@ -191,7 +192,7 @@ __device__ __forceinline__ void load_bar(const NodeArgs<M>& a, const double* w, 
     const double* row = w + a.nb + (int64_t)k * a.N;
     wl[k] = (j >= 1) ? __ldg(row + j - 1) : 0.0;
     wr[k] = (j < a.N) ? __ldg(row + j) : 0.0;
-    wb[k] = wl[k] + wr[k];
+    wb[k] = fadd(a.K, wl[k], wr[k]);
   }
 }
 
@@ -212,7 +213,7 @@ __device__ __forceinline__ void load_ybar(const NodeArgs<M>& a, const double* w,
       const double* row = w + a.nb + (int64_t)k * a.N;
       const double wl = (j >= 1) ? __ldg(row + j - 1) : 0.0;
       const double wr = (j < a.N) ? __ldg(row + j) : 0.0;
-      wb[k] = wl + wr;
+      wb[k] = fadd(a.K, wl, wr);
     } else {
       wb[k] = 0.0;
     }
@@ -225,13 +226,13 @@ __device__ __forceinline__ double node_grad(const NodeArgs<M>& a, const double (
   double s = 0.0;
 #pragma unroll
   for (int v = 0; v < M::NZ; ++v) {
-    const double d = REF ? z[v] - a.ref[v] : z[v];
-    const double gv = (endp ? a.gq_end[v] : a.gq_in[v]) * d;
+    const double d = REF ? fsub(a.K, z[v], a.ref[v]) : z[v];
+    const double gv = fmul(a.K, endp ? a.gq_end[v] : a.gq_in[v], d);
     if (WG) {
       if (v < M::NX) a.g[(int64_t)M::NX * j + v] = gv;
       else a.g[a.uoff + (int64_t)M::NU * j + (v - M::NX)] = gv;
     }
-    s = (v == 0) ? gv * d : fma(gv, d, s);
+    s = (v == 0) ? fmul(a.K, gv, d) : fma(gv, d, s);
   }
   return s;
 }
@@ -241,7 +242,8 @@ __device__ __forceinline__ double node_grad(const NodeArgs<M>& a, const double (
 // node's share of row (k, j-1) and B_k = p_k - v_{X_j,k} its share of row (k, j); the last term
 // of p_k is fused into both.
 template <class M, bool PDIR>
-__device__ __forceinline__ void jv_node(const double (&mjx)[M::NX][M::MAXRX], const double (&mju)[M::NX][M::MAXRU],
+__device__ __forceinline__ void jv_node(const ModelConst& K, const double (&mjx)[M::NX][M::MAXRX],
+                                        const double (&mju)[M::NX][M::MAXRU],
                                         const double (&mdp)[M::NX], double pd, const double (&vz)[M::NZ],
                                         double (&A)[M::NX], double (&Bm)[M::NX]) {
   constexpr int NX = M::NX;
@@ -257,7 +259,7 @@ __device__ __forceinline__ void jv_node(const double (&mjx)[M::NX][M::MAXRX], co
     if (PDIR) { cf[nt] = mdp[k]; vv[nt] = pd; ++nt; }
     double s = 0.0;
 #pragma unroll
-    for (int i = 0; i + 1 < nt; ++i) s = (i == 0) ? cf[i] * vv[i] : fma(cf[i], vv[i], s);
+    for (int i = 0; i + 1 < nt; ++i) s = (i == 0) ? fmul(K, cf[i], vv[i]) : fma(cf[i], vv[i], s);
     const double vk = vz[k];
     if (nt == 0) {
       A[k] = vk;
@@ -266,8 +268,10 @@ __device__ __forceinline__ void jv_node(const double (&mjx)[M::NX][M::MAXRX], co
       A[k] = fma(cf[0], vv[0], vk);
       Bm[k] = fma(cf[0], vv[0], -vk);
     } else {
-      A[k] = fma(cf[nt - 1], vv[nt - 1], s + vk);
-      Bm[k] = fma(cf[nt - 1], vv[nt - 1], s - vk);
+      // p = sum of all terms, then p + v and p - v (one operation fewer than fusing the last term twice)
+      const double pk = fma(cf[nt - 1], vv[nt - 1], s);
+      A[k] = fadd(K, pk, vk);
+      Bm[k] = fsub(K, pk, vk);
     }
   }
 }
@@ -282,15 +286,15 @@ __device__ __forceinline__ void jtv_node(const NodeArgs<M>& a, const double* w, 
   constexpr int NX = M::NX;
 #pragma unroll
   for (int v = 0; v < NX; ++v) {
-    double s = wl[v] - wr[v];
+    double s = fsub(a.K, wl[v], wr[v]);
 #pragma unroll
     for (int k = 0; k < NX; ++k)
 #pragma unroll
       for (int e = 0; e < M::RX(k); ++e)
         if (M::XV(k, e) == v && !M::JZ(k, e)) s = fma(wb[k], mjx[k][e], s);
     if (bnd) {  // only CTAs holding node 0 or node N (uniform branch)
-      if (j == 0) s += __ldg(w + v);
-      if (a.has_final && j == a.N) s += __ldg(w + NX + v);
+      if (j == 0) s = fadd(a.K, s, __ldg(w + v));
+      if (a.has_final && j == a.N) s = fadd(a.K, s, __ldg(w + NX + v));
     }
     o[v] = s;
   }
@@ -302,7 +306,7 @@ __device__ __forceinline__ void jtv_node(const NodeArgs<M>& a, const double* w, 
     for (int k = 0; k < NX; ++k)
 #pragma unroll
       for (int e = 0; e < M::RU(k); ++e)
-        if (M::UV(k, e) == i) { s = first ? wb[k] * mju[k][e] : fma(wb[k], mju[k][e], s); first = false; }
+        if (M::UV(k, e) == i) { s = first ? fmul(a.K, wb[k], mju[k][e]) : fma(wb[k], mju[k][e], s); first = false; }
     o[NX + i] = s;
   }
 }
@@ -320,10 +324,10 @@ __device__ __forceinline__ void hv_node(const NodeArgs<M>& a, const double* hd, 
     if (a.hpos[e] >= 0) {
       const int aa = HT.a[e], bb = HT.b[e];
       const double val = (HT.dyn[e] >= 0) ? hd[HT.dyn[e] >= 0 ? HT.dyn[e] : 0] : cqd[aa];
-      o[aa] = first[aa] ? val * vz[bb] : fma(val, vz[bb], o[aa]);
+      o[aa] = first[aa] ? fmul(a.K, val, vz[bb]) : fma(val, vz[bb], o[aa]);
       first[aa] = false;
       if (aa != bb) {
-        o[bb] = first[bb] ? val * vz[aa] : fma(val, vz[aa], o[bb]);
+        o[bb] = first[bb] ? fmul(a.K, val, vz[aa]) : fma(val, vz[aa], o[bb]);
         first[bb] = false;
       }
     }
@@ -399,7 +403,7 @@ __device__ __forceinline__ void node_eval_tile(const NodeArgs<M>& a, const Model
       if (WJV || WHV) load_vz<M>(a, a.v, j, vz);
       if (WJV) {
         double mdp[NX];
-        jv_node<M, false>(mjx, mju, mdp, 0.0, vz, jA[q], jB[q]);
+        jv_node<M, false>(K, mjx, mju, mdp, 0.0, vz, jA[q], jB[q]);
       }
     }
     if (own) {
@@ -443,7 +447,7 @@ __device__ __forceinline__ void node_eval_tile(const NodeArgs<M>& a, const Model
         double s2;
         if (a.has_ref) s2 = sG ? node_grad<M, true, true>(a, z, endp, j) : node_grad<M, true, false>(a, z, endp, j);
         else s2 = sG ? node_grad<M, false, true>(a, z, endp, j) : node_grad<M, false, false>(a, z, endp, j);
-        objterm = (q == 0) ? s2 : objterm + s2;
+        objterm = (q == 0) ? s2 : fadd(K, objterm, s2);
       }
       // ---- boundary rows X_{0,k} (and X_{N,k}): constraint value and the constant Jacobian entry
       if (j == 0) {
@@ -470,14 +474,14 @@ __device__ __forceinline__ void node_eval_tile(const NodeArgs<M>& a, const Model
         if (lt < nrows) {
           double* rp = sj + lt * cnt;
 #pragma unroll
-          for (int e = 0; e < M::RX(k); ++e) rp[e] = (M::XV(k, e) == k) ? (mjx[k][e] - 1.0) : mjx[k][e];
+          for (int e = 0; e < M::RX(k); ++e) rp[e] = (M::XV(k, e) == k) ? fma(mjx[k][e], K.one, -1.0) : mjx[k][e];
 #pragma unroll
           for (int e = 0; e < M::RU(k); ++e) rp[2 * M::RX(k) + e] = mju[k][e];
         }
         if (lt >= 1 && lt - 1 < nrows) {
           double* rp = sj + (lt - 1) * cnt;
 #pragma unroll
-          for (int e = 0; e < M::RX(k); ++e) rp[M::RX(k) + e] = (M::XV(k, e) == k) ? (mjx[k][e] + 1.0) : mjx[k][e];
+          for (int e = 0; e < M::RX(k); ++e) rp[M::RX(k) + e] = (M::XV(k, e) == k) ? fma(mjx[k][e], K.one, 1.0) : mjx[k][e];
 #pragma unroll
           for (int e = 0; e < M::RU(k); ++e) rp[2 * M::RX(k) + M::RU(k) + e] = mju[k][e];
         }
@@ -513,7 +517,7 @@ __device__ __forceinline__ void node_eval_tile(const NodeArgs<M>& a, const Model
           double right;
           if (q + 1 < NPT) right = jA[q + 1 < NPT ? q + 1 : 0][k];
           else right = (lane == 31) ? sEdge[EO + (warp + 1) * NX + k] : nbA[k];
-          a.ojv[a.nb + (int64_t)k * a.N + r0 + lt] = jB[q][k] + right;
+          a.ojv[a.nb + (int64_t)k * a.N + r0 + lt] = fadd(K, jB[q][k], right);
         }
       }
     }
@@ -528,7 +532,7 @@ __device__ __forceinline__ void node_eval_tile(const NodeArgs<M>& a, const Model
           double right;
           if (q + 1 < NPT) right = pb[q + 1 < NPT ? q + 1 : 0][k];
           else right = (lane == 31) ? sEdge[(warp + 1) * NX + k] : nbv[k];
-          a.c[a.nb + (int64_t)k * a.N + r0 + lt] = right - pa[q][k];
+          a.c[a.nb + (int64_t)k * a.N + r0 + lt] = fsub(K, right, pa[q][k]);
         }
       }
     }
@@ -545,14 +549,22 @@ __device__ __forceinline__ void node_eval_tile(const NodeArgs<M>& a, const Model
     }
   }
   if (sF) {
-    const double ts = tile_sum<TILE>(objterm, sm + oRED);
+    const double ts = tile_sum<TILE>(objterm, sm + oRED, K.one);
     if (t == 0) *partial = ts;
   }
   if (WC || WJ || WF || WJV) __syncthreads();
 }
 
+// Optional minimum of resident CTAs per SM asked of the register allocator (tuning macro;
+// by default the allocator's own heuristic applies).
+#ifdef OCP_EVAL_MINB
+#define OCP_EVAL_MINB_ARG , OCP_EVAL_MINB
+#else
+#define OCP_EVAL_MINB_ARG
+#endif
+
 template <class M, int TILE, int NPT, unsigned OUT>
-__global__ void __launch_bounds__(TILE) k_node_eval(const __grid_constant__ NodeArgs<M> a) {
+__global__ void __launch_bounds__(TILE OCP_EVAL_MINB_ARG) k_node_eval(const __grid_constant__ NodeArgs<M> a) {
   constexpr bool WF = OUT & O_F;
   extern __shared__ __align__(16) double sm[];
   __shared__ double sEdge[2 * (TILE / 32 + 1) * M::NX];
@@ -597,7 +609,7 @@ __global__ void __launch_bounds__(TILE) k_node_jprod(const __grid_constant__ Nod
       M::template eval<false, true, false>(K, z, yb, cqd, pa, pb, mjx, mju, hd);
       double mdp[NX];
       if (PDIR) M::dparam(K, z, mdp);
-      jv_node<M, PDIR>(mjx, mju, mdp, pd, vz, A, p);
+      jv_node<M, PDIR>(K, mjx, mju, mdp, pd, vz, A, p);
       if (j == 0) {
 #pragma unroll
         for (int k = 0; k < NX; ++k) a.out[k] = vx[k];
@@ -618,7 +630,7 @@ __global__ void __launch_bounds__(TILE) k_node_jprod(const __grid_constant__ Nod
 #pragma unroll
       for (int k = 0; k < NX; ++k) {
         const double right = (lane == 31) ? sEdge[(warp + 1) * NX + k] : nbv[k];
-        a.out[a.nb + (int64_t)k * a.N + j] = p[k] + right;
+        a.out[a.nb + (int64_t)k * a.N + j] = fadd(K, p[k], right);
       }
     }
     __syncthreads();
@@ -660,7 +672,7 @@ __global__ void __launch_bounds__(TILE) k_node_jtprod(const __grid_constant__ No
       }
     }
     if (DPAR) {
-      const double ts = tile_sum<TILE>(acc_mu, red);
+      const double ts = tile_sum<TILE>(acc_mu, red, K.one);
       if (threadIdx.x == 0) a.partials[chunk] = ts;
       __syncthreads();
     }
@@ -713,7 +725,7 @@ __global__ void __launch_bounds__(TILE) k_node_hprod(const __grid_constant__ Nod
       store_nz<M>(a, a.out, j, o);
     }
     if (MIX && a.dmu) {
-      const double ts = tile_sum<TILE>(acc_mu, red);
+      const double ts = tile_sum<TILE>(acc_mu, red, K.one);
       if (threadIdx.x == 0) a.partials[chunk] = ts;
       __syncthreads();
     }

@@ -25,6 +25,7 @@ struct ObjArgs {
   unsigned* counter;
   int64_t N, uoff;
   int nx, nu, has_ref;
+  double one, mz;   // 1.0 and -0.0 at run time: sums and products are issued as FMAs
   double gq_in[OBJ_MAXV], gq_end[OBJ_MAXV], ref[OBJ_MAXV];
 };
 
@@ -48,18 +49,19 @@ __global__ void __launch_bounds__(OBJ_THREADS) k_obj(const __grid_constant__ Obj
         const int64_t idx = var_index(a, j, v);
         const double gq = endp ? a.gq_end[v] : a.gq_in[v];   // 2 w_j q_v
         const double z = __ldg(a.x + idx);
-        const double d = a.has_ref ? z - a.ref[v] : z;
+        const double d = a.has_ref ? fma(-a.ref[v], a.one, z) : z;
+        const double sg = fma(s, gq, a.mz);
         if (HVP) {
           const double vv = __ldg(a.v + idx);
-          a.out[idx] = (s * gq) * vv;
-          acc = fma(gq * d, vv, acc);
+          a.out[idx] = fma(sg, vv, a.mz);
+          acc = fma(fma(gq, d, a.mz), vv, acc);
         } else {
-          a.out[idx] = (s * gq) * d;
+          a.out[idx] = fma(sg, d, a.mz);
         }
       }
     }
     if (HVP && a.dot) {
-      const double ts = tile_sum<OBJ_THREADS>(acc, red);
+      const double ts = tile_sum<OBJ_THREADS>(acc, red, a.one);
       if (threadIdx.x == 0) a.partials[chunk] = ts;
       __syncthreads();
     }
@@ -77,6 +79,8 @@ ocp_status obj_launch(ocp* h, bool hvp, const double* x, const double* s, const 
   a.partials = h->d_partials; a.counter = h->d_counter;
   a.N = h->N; a.uoff = (int64_t)h->nx * (h->N + 1);
   a.nx = h->nx; a.nu = h->nu; a.has_ref = h->has_ref ? 1 : 0;
+  a.one = 1.0;
+  a.mz = -0.0;
   for (int v2 = 0; v2 < nz; ++v2) {
     const double w = v2 < h->nx ? h->q[v2] : h->r[v2 - h->nx];
     a.gq_in[v2] = 2.0 * h->h * w;

@@ -74,9 +74,11 @@ def lib():
     """Load (building first if needed) the CUDA library.  Raises if it cannot be built."""
     global _lib
     if _lib is None:
-        path = _build.LIB
-        if not _build.up_to_date():
-            path = _build.build()
+        path = os.environ.get("OCP_GB300_LIB")  # an alternative build of the same library
+        if not path:
+            path = _build.LIB
+            if not _build.up_to_date():
+                path = _build.build()
         L = C.CDLL(path)
         for name, argt in _SIGS.items():
             fn = getattr(L, name)
