@@ -22,6 +22,12 @@
  *   - the products J v, J^T w, H v, defined as plain COO matrix-vector products;
  *   - (dc/dp)^T w for the first model parameter (the Van der Pol mu).
  *
+ * Models: Van der Pol, cart-pole, the heat equation by the method of lines, the Sec. 5
+ * double integrator and the quadrotor of the paper's appendix.  The running cost is a
+ * diagonal quadratic around a reference; the state reference may vary in time as
+ * xref_k + xslope_k t + xamp_k sin(xfreq_k t) (the quadrotor's tracking terms), evaluated at
+ * the node times t_j = j h.
+ *
  * Derivatives of the model right-hand sides are derived by hand and written out in
  * straight-line code (quotient rule for the cart-pole).  Everything is templated on the
  * scalar type so that the same code runs in
@@ -66,6 +72,10 @@ inline Sh operator/(Sh a, Sh b) {
 inline Sh& operator+=(Sh& a, Sh b) { a = a + b; return a; }
 inline Sh sin(Sh a) { return Sh(std::sin(a.v), std::fabs(std::cos(a.v)) * a.m + std::fabs(std::sin(a.v))); }
 inline Sh cos(Sh a) { return Sh(std::cos(a.v), std::fabs(std::sin(a.v)) * a.m + std::fabs(std::cos(a.v))); }
+inline Sh tan(Sh a) {
+  const double t = std::tan(a.v);
+  return Sh(t, (1.0 + t * t) * a.m + std::fabs(t));
+}
 
 typedef std::complex<double> Cx;
 
@@ -93,7 +103,7 @@ struct Neumaier {
 // ---------------------------------------------------------------------------------------
 // Problem description (mirrored by a ctypes Structure in oracle.py)
 // ---------------------------------------------------------------------------------------
-enum { M_VDP = 1, M_CARTPOLE = 2, M_HEAT = 3, M_DINT = 4 };
+enum { M_VDP = 1, M_CARTPOLE = 2, M_HEAT = 3, M_DINT = 4, M_QUAD = 5 };
 
 struct Prob {
   int32_t model, nx, nu, has_final;
@@ -105,6 +115,11 @@ struct Prob {
   const double* r;     // running cost weights on the control (nu)
   const double* xref;  // state reference (nx)
   const double* uref;  // control reference (nu)
+  // time-varying state reference (each nullable, nx):
+  //   xref_k(t) = xref_k + xslope_k t + xamp_k sin(xfreq_k t)
+  const double* xslope;
+  const double* xamp;
+  const double* xfreq;
 };
 
 template <class S> struct JEnt { int k, v; S val; };      // d f_k / d z_v
@@ -264,6 +279,136 @@ template <class S> void dint_jac(std::vector<JEnt<S>>& e) {
   e.push_back({1, 2, S(1.0)});
 }
 
+// Quadrotor (paper appendix, the second benchmark problem).  States x1..x9: positions
+// x1, x3, x5 with velocities x2, x4, x6 and the attitude angles x7, x8, x9; controls u1 (the
+// thrust per unit mass) and u2, u3, u4 (angular rate inputs); p = (g).
+//   x2' = u1 P,  x4' = u1 Q,  x6' = u1 R - g   with the thrust direction
+//     P = cos x7 sin x8 cos x9 + sin x7 sin x9,  Q = cos x7 sin x8 sin x9 - sin x7 cos x9,
+//     R = cos x7 cos x8;
+//   x7' = (u2 cos x7 + u3 sin x7) / cos x8,  x8' = -u2 sin x7 + u3 cos x7,
+//   x9' = (u2 cos x7 + u3 sin x7) tan x8 + u4.
+// Local indices: x1..x9 -> 0..8, u1..u4 -> 9..12.
+template <class S> void quad_f(const S* p, const S* z, S* f) {
+  using std::cos; using std::sin; using std::tan;
+  const S g = p[0];
+  const S x7 = z[6], x8 = z[7], x9 = z[8], u1 = z[9], u2 = z[10], u3 = z[11], u4 = z[12];
+  f[0] = z[1];
+  f[1] = u1 * (cos(x7) * sin(x8) * cos(x9) + sin(x7) * sin(x9));
+  f[2] = z[3];
+  f[3] = u1 * (cos(x7) * sin(x8) * sin(x9) - sin(x7) * cos(x9));
+  f[4] = z[5];
+  f[5] = u1 * cos(x7) * cos(x8) - g;
+  f[6] = (u2 * cos(x7) + u3 * sin(x7)) / cos(x8);
+  f[7] = u3 * cos(x7) - u2 * sin(x7);
+  f[8] = (u2 * cos(x7) + u3 * sin(x7)) * tan(x8) + u4;
+}
+
+// Trigonometric parts shared by the derivatives:  a = u2 c7 + u3 s7 (so x7' = a / c8),
+// b = da/dx7 = u3 c7 - u2 s7 (= x8'), e = 1 / c8, t = tan x8 (de/dx8 = e t, dt/dx8 = e^2).
+template <class S> struct QuadParts {
+  S s7, c7, s8, c8, s9, c9, e, t, a, b, P, P7, P8, P9, Q, Q7, Q8, Q9;
+  QuadParts(const S* z) {
+    using std::cos; using std::sin; using std::tan;
+    s7 = sin(z[6]); c7 = cos(z[6]); s8 = sin(z[7]); c8 = cos(z[7]); s9 = sin(z[8]); c9 = cos(z[8]);
+    e = S(1.0) / c8;
+    t = tan(z[7]);
+    a = z[10] * c7 + z[11] * s7;
+    b = z[11] * c7 - z[10] * s7;
+    P = c7 * s8 * c9 + s7 * s9;
+    P7 = c7 * s9 - s7 * s8 * c9;
+    P8 = c7 * c8 * c9;
+    P9 = s7 * c9 - c7 * s8 * s9;
+    Q = c7 * s8 * s9 - s7 * c9;
+    Q7 = S(0.0) - s7 * s8 * s9 - c7 * c9;
+    Q8 = c7 * c8 * s9;
+    Q9 = c7 * s8 * c9 + s7 * s9;
+  }
+};
+
+template <class S> void quad_jac(const S* z, std::vector<JEnt<S>>& e) {
+  const QuadParts<S> q(z);
+  const S u1 = z[9];
+  e.push_back({0, 1, S(1.0)});
+  e.push_back({1, 6, u1 * q.P7});
+  e.push_back({1, 7, u1 * q.P8});
+  e.push_back({1, 8, u1 * q.P9});
+  e.push_back({1, 9, q.P});
+  e.push_back({2, 3, S(1.0)});
+  e.push_back({3, 6, u1 * q.Q7});
+  e.push_back({3, 7, u1 * q.Q8});
+  e.push_back({3, 8, u1 * q.Q9});
+  e.push_back({3, 9, q.Q});
+  e.push_back({4, 5, S(1.0)});
+  e.push_back({5, 6, S(0.0) - u1 * q.s7 * q.c8});
+  e.push_back({5, 7, S(0.0) - u1 * q.c7 * q.s8});
+  e.push_back({5, 9, q.c7 * q.c8});
+  e.push_back({6, 6, q.b * q.e});
+  e.push_back({6, 7, q.a * q.e * q.t});
+  e.push_back({6, 10, q.c7 * q.e});
+  e.push_back({6, 11, q.s7 * q.e});
+  e.push_back({7, 6, S(0.0) - q.a});
+  e.push_back({7, 10, S(0.0) - q.s7});
+  e.push_back({7, 11, q.c7});
+  e.push_back({8, 6, q.b * q.t});
+  e.push_back({8, 7, q.a * q.e * q.e});
+  e.push_back({8, 10, q.c7 * q.t});
+  e.push_back({8, 11, q.s7 * q.t});
+  e.push_back({8, 12, S(1.0)});
+}
+
+template <class S> void quad_hess(const S* z, std::vector<HEnt<S>>& e) {
+  const QuadParts<S> q(z);
+  const S u1 = z[9];
+  // x2' = u1 P:  P_77 = P_99 = -P,  P_78 = -s7 c8 c9,  P_79 = s7 s8 s9 + c7 c9,
+  //              P_88 = -c7 s8 c9,  P_89 = -c7 c8 s9
+  e.push_back({1, 6, 6, S(0.0) - u1 * q.P});
+  e.push_back({1, 7, 6, S(0.0) - u1 * q.s7 * q.c8 * q.c9});
+  e.push_back({1, 7, 7, S(0.0) - u1 * q.c7 * q.s8 * q.c9});
+  e.push_back({1, 8, 6, u1 * (q.s7 * q.s8 * q.s9 + q.c7 * q.c9)});
+  e.push_back({1, 8, 7, S(0.0) - u1 * q.c7 * q.c8 * q.s9});
+  e.push_back({1, 8, 8, S(0.0) - u1 * q.P});
+  e.push_back({1, 9, 6, q.P7});
+  e.push_back({1, 9, 7, q.P8});
+  e.push_back({1, 9, 8, q.P9});
+  // x4' = u1 Q:  Q_77 = Q_99 = -Q,  Q_78 = -s7 c8 s9,  Q_79 = c7 s9 - s7 s8 c9,
+  //              Q_88 = -c7 s8 s9,  Q_89 = c7 c8 c9
+  e.push_back({3, 6, 6, S(0.0) - u1 * q.Q});
+  e.push_back({3, 7, 6, S(0.0) - u1 * q.s7 * q.c8 * q.s9});
+  e.push_back({3, 7, 7, S(0.0) - u1 * q.c7 * q.s8 * q.s9});
+  e.push_back({3, 8, 6, u1 * (q.c7 * q.s9 - q.s7 * q.s8 * q.c9)});
+  e.push_back({3, 8, 7, u1 * q.c7 * q.c8 * q.c9});
+  e.push_back({3, 8, 8, S(0.0) - u1 * q.Q});
+  e.push_back({3, 9, 6, q.Q7});
+  e.push_back({3, 9, 7, q.Q8});
+  e.push_back({3, 9, 8, q.Q9});
+  // x6' = u1 c7 c8 - g
+  e.push_back({5, 6, 6, S(0.0) - u1 * q.c7 * q.c8});
+  e.push_back({5, 7, 6, u1 * q.s7 * q.s8});
+  e.push_back({5, 7, 7, S(0.0) - u1 * q.c7 * q.c8});
+  e.push_back({5, 9, 6, S(0.0) - q.s7 * q.c8});
+  e.push_back({5, 9, 7, S(0.0) - q.c7 * q.s8});
+  // x7' = a e
+  e.push_back({6, 6, 6, S(0.0) - q.a * q.e});
+  e.push_back({6, 7, 6, q.b * q.e * q.t});
+  e.push_back({6, 7, 7, q.a * q.e * (q.t * q.t + q.e * q.e)});
+  e.push_back({6, 10, 6, S(0.0) - q.s7 * q.e});
+  e.push_back({6, 10, 7, q.c7 * q.e * q.t});
+  e.push_back({6, 11, 6, q.c7 * q.e});
+  e.push_back({6, 11, 7, q.s7 * q.e * q.t});
+  // x8' = b
+  e.push_back({7, 6, 6, S(0.0) - q.b});
+  e.push_back({7, 10, 6, S(0.0) - q.c7});
+  e.push_back({7, 11, 6, S(0.0) - q.s7});
+  // x9' = a t + u4
+  e.push_back({8, 6, 6, S(0.0) - q.a * q.t});
+  e.push_back({8, 7, 6, q.b * q.e * q.e});
+  e.push_back({8, 7, 7, S(2.0) * q.a * q.e * q.e * q.t});
+  e.push_back({8, 10, 6, S(0.0) - q.s7 * q.t});
+  e.push_back({8, 10, 7, q.c7 * q.e * q.e});
+  e.push_back({8, 11, 6, q.c7 * q.t});
+  e.push_back({8, 11, 7, q.s7 * q.e * q.e});
+}
+
 // Dispatch ------------------------------------------------------------------------------
 template <class S> void model_f(const Prob& P, const S* p, const S* z, S* f) {
   switch (P.model) {
@@ -271,6 +416,7 @@ template <class S> void model_f(const Prob& P, const S* p, const S* z, S* f) {
     case M_CARTPOLE: cp_f(p, z, f); break;
     case M_HEAT: heat_f(P.nx, z, f); break;
     case M_DINT: dint_f(z, f); break;
+    case M_QUAD: quad_f(p, z, f); break;
   }
 }
 template <class S> void model_jac(const Prob& P, const S* p, const S* z, std::vector<JEnt<S>>& e) {
@@ -279,6 +425,7 @@ template <class S> void model_jac(const Prob& P, const S* p, const S* z, std::ve
     case M_CARTPOLE: cp_jac(p, z, e); break;
     case M_HEAT: heat_jac(P.nx, z, e); break;
     case M_DINT: dint_jac(e); break;
+    case M_QUAD: quad_jac(z, e); break;
   }
 }
 template <class S> void model_hess(const Prob& P, const S* p, const S* z, std::vector<HEnt<S>>& e) {
@@ -287,18 +434,27 @@ template <class S> void model_hess(const Prob& P, const S* p, const S* z, std::v
     case M_CARTPOLE: cp_hess(p, z, e); break;
     case M_HEAT: heat_hess(P.nx, z, e); break;
     case M_DINT: break;
+    case M_QUAD: quad_hess(z, e); break;
   }
 }
 
-// Running cost f0 = sum_k q_k (x_k - xref_k)^2 + sum_i r_i (u_i - uref_i)^2.
-template <class S> S cost_f0(const Prob& P, const S* z) {
+// Running cost f0 = sum_k q_k (x_k - xref_k(t))^2 + sum_i r_i (u_i - uref_i)^2 at node time t,
+// with the state reference xref_k(t) = xref_k + xslope_k t + xamp_k sin(xfreq_k t) (a constant
+// reference when the three arrays are absent).
+inline double xref_at(const Prob& P, int k, double t) {
+  double r = P.xref[k];
+  if (P.xslope) r = r + P.xslope[k] * t;
+  if (P.xamp && P.xfreq) r = r + P.xamp[k] * std::sin(P.xfreq[k] * t);
+  return r;
+}
+template <class S> S cost_f0(const Prob& P, const S* z, double t) {
   S s = S(0.0);
-  for (int k = 0; k < P.nx; ++k) { S d = z[k] - S(P.xref[k]); s += S(P.q[k]) * d * d; }
+  for (int k = 0; k < P.nx; ++k) { S d = z[k] - S(xref_at(P, k, t)); s += S(P.q[k]) * d * d; }
   for (int i = 0; i < P.nu; ++i) { S d = z[P.nx + i] - S(P.uref[i]); s += S(P.r[i]) * d * d; }
   return s;
 }
-template <class S> void cost_grad(const Prob& P, const S* z, S* g) {
-  for (int k = 0; k < P.nx; ++k) g[k] = S(2.0) * S(P.q[k]) * (z[k] - S(P.xref[k]));
+template <class S> void cost_grad(const Prob& P, const S* z, double t, S* g) {
+  for (int k = 0; k < P.nx; ++k) g[k] = S(2.0) * S(P.q[k]) * (z[k] - S(xref_at(P, k, t)));
   for (int i = 0; i < P.nu; ++i) g[P.nx + i] = S(2.0) * S(P.r[i]) * (z[P.nx + i] - S(P.uref[i]));
 }
 inline double cost_hess_diag(const Prob& P, int a) {  // d2 f0 / d z_a^2 (constant)
@@ -327,6 +483,9 @@ template <class S> void gather_node(const Layout& L, const S* x, int64_t j, S* z
   for (int v = 0; v < L.nz; ++v) z[v] = x[L.col(j, v)];
 }
 
+// node time t_j = j h on the uniform grid
+inline double node_time(const Prob& P, int64_t j) { return (double)j * (P.T / (double)P.N); }
+
 inline double weight(const Prob& P, int64_t j) {
   const double h = P.T / (double)P.N;
   return (j == 0 || j == P.N) ? h / 2.0 : h;
@@ -341,7 +500,7 @@ template <class S> S objective(const Prob& P, const S* x) {
   Neumaier<S> acc;
   for (int64_t j = 0; j <= L.N; ++j) {
     gather_node(L, x, j, z.data());
-    acc.add(S(weight(P, j)) * cost_f0(P, z.data()));
+    acc.add(S(weight(P, j)) * cost_f0(P, z.data(), node_time(P, j)));
   }
   return acc.result();
 }
@@ -370,7 +529,7 @@ template <class S> void gradient(const Prob& P, const S* x, S* g) {
   std::vector<S> z(L.nz), gz(L.nz);
   for (int64_t j = 0; j <= L.N; ++j) {
     gather_node(L, x, j, z.data());
-    cost_grad(P, z.data(), gz.data());
+    cost_grad(P, z.data(), node_time(P, j), gz.data());
     for (int v = 0; v < L.nz; ++v) g[L.col(j, v)] = S(weight(P, j)) * gz[v];
   }
 }
@@ -506,6 +665,7 @@ int check(const Prob& P) {
     case M_CARTPOLE: return (P.nx == 4 && P.nu == 1) ? 0 : 2;
     case M_HEAT: return (P.nx >= 2 && P.nu == 1 && (int)P.par[0] == P.nx) ? 0 : 2;
     case M_DINT: return (P.nx == 2 && P.nu == 1) ? 0 : 2;
+    case M_QUAD: return (P.nx == 9 && P.nu == 4) ? 0 : 2;
     default: return 6;
   }
 }

@@ -12,14 +12,14 @@ import numpy as np
 
 from . import build as _build
 
-_MODEL_ID = {"vdp": 1, "cartpole": 2, "heat": 3, "dint": 4}
+_MODEL_ID = {"vdp": 1, "cartpole": 2, "heat": 3, "dint": 4, "quadrotor": 5}
 
 
 class _Prob(C.Structure):
     _fields_ = [("model", C.c_int32), ("nx", C.c_int32), ("nu", C.c_int32), ("has_final", C.c_int32),
                 ("N", C.c_int64), ("T", C.c_double), ("par", C.c_double * 8), ("npar", C.c_int32),
                 ("pad", C.c_int32), ("q", C.c_void_p), ("r", C.c_void_p), ("xref", C.c_void_p),
-                ("uref", C.c_void_p)]
+                ("uref", C.c_void_p), ("xslope", C.c_void_p), ("xamp", C.c_void_p), ("xfreq", C.c_void_p)]
 
 
 _lib = None
@@ -45,6 +45,9 @@ class Problem:
         self._r = np.ascontiguousarray(w["r"], dtype=np.float64)
         self._xref = np.ascontiguousarray(w["xref"], dtype=np.float64)
         self._uref = np.ascontiguousarray(w["uref"], dtype=np.float64)
+        # optional time-varying state reference xref_k + xslope_k t + xamp_k sin(xfreq_k t)
+        self._trk = [None if w.get(k) is None else np.ascontiguousarray(w[k], dtype=np.float64)
+                     for k in ("xslope", "xamp", "xfreq")]
         p = _Prob()
         p.model = _MODEL_ID[w["model"]]
         p.nx, p.nu = w["nx"], w["nu"]
@@ -58,6 +61,7 @@ class Problem:
         p.npar = len(pars)
         p.q, p.r = _ptr(self._q), _ptr(self._r)
         p.xref, p.uref = _ptr(self._xref), _ptr(self._uref)
+        p.xslope, p.xamp, p.xfreq = (_ptr(a) for a in self._trk)
         self.s = p
         n, m, nj, nh = (C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64())
         st = lib().orc_dims(C.byref(p), C.byref(n), C.byref(m), C.byref(nj), C.byref(nh))

@@ -56,6 +56,7 @@ DIST = {
     "cartpole": dict(x=(-1.0, 1.0), u=(-10.0, 10.0)),
     "heat": dict(x=(0.0, 1.0), u=(-1.0, 1.0)),
     "dint": dict(x=(-1.0, 1.0), u=(-1.0, 1.0)),
+    "quadrotor": dict(x=(-1.0, 1.0), u=(-10.0, 10.0)),
 }
 
 
@@ -82,8 +83,10 @@ def draw_batch_meta(seed: int, count: int, nmin: int, nmax: int):
     return Ns, x0, R
 
 
-# Workload definitions (data only).  Model names: vdp, cartpole, heat, dint.
-# Running cost f0 = sum_k q_k (x_k - xref_k)^2 + sum_i r_i (u_i - uref_i)^2.
+# Workload definitions (data only).  Model names: vdp, cartpole, heat, dint, quadrotor.
+# Running cost f0 = sum_k q_k (x_k - xref_k(t))^2 + sum_i r_i (u_i - uref_i)^2, where the
+# optional keys xslope, xamp, xfreq make the state reference time-varying:
+# xref_k(t) = xref_k + xslope_k t + xamp_k sin(xfreq_k t).
 def workload(name: str) -> dict:
     if name == "vdp_n1e3":         # Van der Pol, N=1000, T=10, x0=(1,0), cost x1^2+x2^2+u^2
         return dict(name=name, model="vdp", nx=2, nu=1, N=1000, T=10.0, params=[1.0],
@@ -109,6 +112,19 @@ def workload(name: str) -> dict:
         return dict(name=name, model="dint", nx=2, nu=1, N=100, T=1.0, params=[],
                     q=[0.0, 0.0], r=[0.5], xref=[0.0, 0.0], uref=[0.0], x0=[-1.0, 0.0],
                     xf=[0.0, 0.0], seed=1006, sigma=1.0, dist="dint")
+    if name.startswith("quadrotor_n"):  # the paper's quadrotor (appendix): T=1, g=9.8, r=0.1
+        N = {"quadrotor_n1e3": 1000, "quadrotor_n1e5": 100_000, "quadrotor_n1e6": 1_000_000}[name]
+        T = 1.0
+        # 1/2 [ (x1 - sin(2 pi t/T))^2 + (x3 - 2 sin(4 pi t/T))^2 + (x5 - 2 t/T)^2
+        #       + x7^2 + x8^2 + x9^2 + r |u|^2 ]
+        return dict(name=name, model="quadrotor", nx=9, nu=4, N=N, T=T, params=[9.8],
+                    q=[0.5, 0.0, 0.5, 0.0, 0.5, 0.0, 0.5, 0.5, 0.5], r=[0.05] * 4,
+                    xref=[0.0] * 9, uref=[0.0] * 4,
+                    xslope=[0.0, 0.0, 0.0, 0.0, 2.0 / T, 0.0, 0.0, 0.0, 0.0],
+                    xamp=[1.0, 0.0, 2.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0],
+                    xfreq=[2.0 * np.pi / T, 0.0, 4.0 * np.pi / T, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0],
+                    x0=[0.0] * 9, xf=None, seed={1000: 1007, 100_000: 1008, 1_000_000: 1009}[N],
+                    sigma=1.0, dist="quadrotor")
     raise KeyError(name)
 
 

@@ -14,7 +14,7 @@ from conftest import read_golden
 from oracle import oracle as O
 from paper_2510_03932_gb300 import synth
 
-MODELS = ["vdp_n1e3", "cartpole_n1e5", "heat_n2e4", "dint"]
+MODELS = ["vdp_n1e3", "cartpole_n1e5", "heat_n2e4", "dint", "quadrotor_n1e3"]
 
 
 def small(name, N):
@@ -33,7 +33,7 @@ def rand_point(w, rng):
 # Counts and structure
 # ---------------------------------------------------------------------------------------
 # per node: (J entries of one defect-row set, H entries of one node block)
-NODE_COUNTS = {"vdp": (10, 4), "cartpole": (22, 7), "heat": (382, 65), "dint": (8, 1)}
+NODE_COUNTS = {"vdp": (10, 4), "cartpole": (22, 7), "heat": (382, 65), "dint": (8, 1), "quadrotor": (68, 20)}
 
 
 @pytest.mark.parametrize("name", MODELS)
@@ -125,7 +125,7 @@ def test_jacobian_gradient_hessian_vs_complex_step(name):
     np.testing.assert_allclose(cfd, Jcs[:, 1], rtol=1e-5, atol=1e-6)
 
 
-@pytest.mark.parametrize("name", ["vdp_n1e3", "cartpole_n1e5", "heat_n2e4"])
+@pytest.mark.parametrize("name", ["vdp_n1e3", "cartpole_n1e5", "heat_n2e4", "quadrotor_n1e3"])
 def test_hessian_special_cases(name):
     """y = 0, sigma = 1: H is the weighted cost Hessian 2 w_j diag(q, r).
     sigma = 0, y = e_r: H is the Hessian of the single defect r (supported on 2 nodes)."""
@@ -275,6 +275,86 @@ def test_heat_laplacian_boundary_conditions():
     f = O.model_f(P, np.concatenate([xc, [a]]))
     np.testing.assert_allclose(f[:-1], -xc[:-1] ** 3, rtol=1e-9, atol=1e-9)
     assert abs(f[-1] - (-b / dx**2 - xc[-1] ** 3)) < 1e-9
+
+
+def test_quadrotor_hover_and_small_angle_linearisation():
+    """Hover (level attitude, thrust u1 = g, no rates) is an equilibrium: every defect is
+    exactly zero.  At level attitude (x7 = x8 = x9 = 0) the Jacobian is the small-angle model
+    of the rigid body, written out by hand below: the thrust tilts into x2' and x4', and the
+    angle rates are the inputs u2, u3, u4 with first-order couplings through x7 and x8."""
+    w = small("quadrotor_n1e3", 1)
+    P = O.Problem(w)
+    g = w["params"][0]
+    N, nx, nu = 1, 9, 4
+    X = np.zeros(nx * (N + 1))
+    U = np.tile([g, 0.0, 0.0, 0.0], N + 1)
+    ev = O.evaluate(P, np.concatenate([X, U]), np.zeros(P.m), 1.0)
+    assert np.all(ev["c"][nx:] == 0.0)
+    # linearisation at x7 = x8 = x9 = 0 with arbitrary controls (exact values at zero angles)
+    rng = np.random.default_rng(21)
+    u1, u2, u3, u4 = rng.uniform(-5, 5, 4)
+    z = np.zeros(13)
+    z[:6] = rng.uniform(-1, 1, 6)
+    z[9:] = [u1, u2, u3, u4]
+    x = np.concatenate([z[:9], z[:9], z[9:], z[9:]])
+    ev = O.evaluate(P, x, np.zeros(P.m), 1.0)
+    jr, jc = O.jac_structure(P)
+    Jd = np.zeros((P.m, P.n)); Jd[jr, jc] = ev["jac"]
+    h = w["T"] / N
+    # d f_k / d z_v at level attitude (rows: f1..f9, columns: x1..x9, u1..u4)
+    A = np.zeros((9, 13))
+    A[0, 1] = A[2, 3] = A[4, 5] = 1.0                  # position derivatives are velocities
+    A[1, 7] = u1                                       # x2' = u1 sin(x8) ~ u1 x8
+    A[3, 6] = -u1                                      # x4' = -u1 sin(x7) ~ -u1 x7
+    A[5, 9] = 1.0                                      # x6' = u1 - g
+    A[6, 6], A[6, 10] = u3, 1.0                        # x7' = u2 + u3 x7
+    A[7, 6], A[7, 11] = -u2, 1.0                       # x8' = u3 - u2 x7
+    A[8, 7], A[8, 12] = u2, 1.0                        # x9' = u2 x8 + u4
+    cols0 = [k for k in range(9)] + [9 * (N + 1) + i for i in range(4)]
+    cols1 = [9 + k for k in range(9)] + [9 * (N + 1) + 4 + i for i in range(4)]
+    rows = nx + np.arange(9) * N
+    expect0 = -h / 2 * A - np.hstack([np.eye(9), np.zeros((9, 4))])
+    expect1 = -h / 2 * A + np.hstack([np.eye(9), np.zeros((9, 4))])
+    np.testing.assert_allclose(Jd[np.ix_(rows, cols0)], expect0, rtol=1e-14, atol=1e-15)
+    np.testing.assert_allclose(Jd[np.ix_(rows, cols1)], expect1, rtol=1e-14, atol=1e-15)
+
+
+def test_quadrotor_rotation_invariants():
+    """The thrust acts along the body axis: (x2', x4', x6' + g) = u1 R e3 with R a rotation,
+    so its norm is |u1| for every attitude.  The angle rates rotate (u2, u3) by x7:
+    (x7' cos x8)^2 + x8'^2 = u2^2 + u3^2, and x9' - u4 = x7' sin x8."""
+    w = small("quadrotor_n1e3", 1)
+    P = O.Problem(w)
+    g = w["params"][0]
+    rng = np.random.default_rng(23)
+    for _ in range(50):
+        z = rng.uniform(-1.2, 1.2, 13)
+        z[9:] = rng.uniform(-8, 8, 4)
+        f = O.model_f(P, z)
+        assert f[0] == z[1] and f[2] == z[3] and f[4] == z[5]
+        thrust = np.sqrt(f[1] ** 2 + f[3] ** 2 + (f[5] + g) ** 2)
+        assert abs(thrust - abs(z[9])) < 1e-13 * (1 + abs(z[9]))
+        assert abs((f[6] * np.cos(z[7])) ** 2 + f[7] ** 2 - (z[10] ** 2 + z[11] ** 2)) < 1e-12 * (1 + z[10] ** 2 + z[11] ** 2)
+        assert abs((f[8] - z[12]) - f[6] * np.sin(z[7])) < 1e-12 * (1 + abs(f[6]))
+
+
+@pytest.mark.parametrize("N", [5, 16, 1000])
+def test_quadrotor_tracking_cost_closed_form(N):
+    """With every state and control at zero the running cost is the reference alone:
+    1/2 [sin^2(2 pi t) + 4 sin^2(4 pi t) + 4 t^2] on [0, 1].  The trapezoidal rule integrates
+    cos(2 pi k t) exactly to zero over a period when N does not divide k, and has the error
+    h^2/12 (f'(1) - f'(0)) on t^2, so F = 1/2 (1/2 + 2 + 4/3 + 2 h^2/3) = 23/12 + h^2/3."""
+    w = small("quadrotor_n1e3", N)
+    P = O.Problem(w)
+    h = 1.0 / N
+    ev = O.evaluate(P, np.zeros(P.n), np.zeros(P.m), 1.0)
+    assert abs(ev["f"] - (23.0 / 12.0 + h * h / 3.0)) < 1e-14 * 2
+    # on the reference the tracked gradient entries vanish (up to the rounding of sin)
+    t = np.arange(N + 1) * h
+    X = np.zeros((N + 1, 9))
+    X[:, 0], X[:, 2], X[:, 4] = np.sin(2 * np.pi * t), 2 * np.sin(4 * np.pi * t), 2 * t
+    ev = O.evaluate(P, np.concatenate([X.ravel(), np.zeros(4 * (N + 1))]), np.zeros(P.m), 1.0)
+    assert np.max(np.abs(ev["g"])) < 1e-15 and abs(ev["f"]) < 1e-30
 
 
 # ---------------------------------------------------------------------------------------
