@@ -59,11 +59,25 @@ typedef enum {
  *            th'' = (-u cos th - mp l th'^2 cos th sin th - (mc+mp) g sin th) / (l D)
  *   HEAT1D   (nx=ncell, nu=1): ncell.  x_k' = (x_{k-1} - 2 x_k + x_{k+1}) / dx^2 - x_k^3,
  *            dx = 1/ncell, ghost x_0 = u (Dirichlet control), x_{ncell+1} = x_ncell (Neumann)
- *   DINT     (nx=2, nu=1): none.       x1' = x2,  x2' = u   (the paper's Sec. 5 example) */
-enum { OCP_MODEL_VDP = 1, OCP_MODEL_CARTPOLE = 2, OCP_MODEL_HEAT1D = 3, OCP_MODEL_DINT = 4 };
+ *   DINT     (nx=2, nu=1): none.       x1' = x2,  x2' = u   (the paper's Sec. 5 example)
+ *   QUADROTOR (nx=9, nu=4): g.  The quadrotor of the paper's appendix: positions x1, x3, x5 with
+ *            velocities x2, x4, x6, attitude angles x7, x8, x9, thrust u1, angle-rate inputs
+ *            u2..u4 (ck = cos xk, sk = sin xk):
+ *            x1' = x2, x3' = x4, x5' = x6,
+ *            x2' = u1 (c7 s8 c9 + s7 s9),  x4' = u1 (c7 s8 s9 - s7 c9),  x6' = u1 c7 c8 - g,
+ *            x7' = (u2 c7 + u3 s7) / c8,  x8' = u3 c7 - u2 s7,  x9' = (u2 c7 + u3 s7) tan x8 + u4.
+ *            Values are finite for |x8| < pi/2; the kernels do not check the singularity. */
+enum {
+  OCP_MODEL_VDP = 1,
+  OCP_MODEL_CARTPOLE = 2,
+  OCP_MODEL_HEAT1D = 3,
+  OCP_MODEL_DINT = 4,
+  OCP_MODEL_QUADROTOR = 5
+};
 
 /* Running cost kinds.  DIAG_QUADRATIC: f0 = sum_k q_k (x_k - xref_k)^2 + sum_i r_i (u_i - uref_i)^2.
- * q, r are required; xref, uref may be NULL (zero). */
+ * q, r are required; xref, uref may be NULL (zero).  ocp_set_tracking makes the state reference
+ * time-varying. */
 enum { OCP_COST_DIAG_QUADRATIC = 0 };
 
 typedef struct { int model; const double* params; int nparams; } ocp_dynamics;
@@ -83,6 +97,19 @@ void ocp_destroy(ocp_t* h);
  * (this changes m and nnz_J; call it before asking for dimensions or structure).
  * x0 == NULL keeps zeros. */
 ocp_status ocp_set_boundary(ocp_t* h, const double* x0, const double* xf);
+
+/* Time-varying state reference (the quadrotor's tracking terms, paper appendix): the running
+ * cost uses, at node time t_j = j h,
+ *     xref_k(t_j) = xref_k + xslope_k t_j + xamp_k sin(xfreq_k t_j)
+ * instead of the constant xref_k.  Host arrays of length nx; NULL means zeros; all three NULL
+ * (or all coefficients zero) returns to the constant reference.  The values are tabulated once
+ * on the device, (N+1) doubles per tracked component (a component is tracked when its slope is
+ * non-zero, or its amplitude and frequency both are); the call synchronizes the device.  Only
+ * F, its gradient and the objective kernels of the differentiation form depend on it (the
+ * Hessian of the cost does not).  A batch created earlier from this handle keeps using the
+ * table it saw: re-create the batch after changing the reference.  Errors: OCP_EMODEL for
+ * HEAT1D, OCP_EINVAL for non-finite coefficients, OCP_ENOMEM / OCP_ECUDA. */
+ocp_status ocp_set_tracking(ocp_t* h, const double* xslope, const double* xamp, const double* xfreq);
 
 /* Sizes: n variables, m constraints, Jacobian and (lower) Hessian nonzeros.  Host outputs. */
 ocp_status ocp_dims(const ocp_t* h, int64_t* n, int64_t* m, int64_t* nnzj, int64_t* nnzh);
@@ -175,7 +202,8 @@ ocp_status ocp_eval_all_range(ocp_t* h, int64_t node_begin, int64_t node_end, co
  * asynchronous on `stream`.  The reduction scratch is a file-scope device array of 65536
  * tiles (about 512 KB on every device that loads the library, held until the process exits);
  * a horizon needing more tiles (N+1 above 65536 x 255 nodes for Van der Pol and the double
- * integrator, x 127 for the cart-pole, x 31 for the heat model) returns OCP_EDIM without
+ * integrator, x 127 for the cart-pole, x 63 for the quadrotor, x 31 for the heat model; the
+ * constant reference only) returns OCP_EDIM without
  * launching.  The first call on a device looks up the array's device address with that device
  * current; make that first call before any stream capture.  Every call on a device shares the
  * array and the last call's contents stay in it: calls that overlap on the GPU race.  Errors

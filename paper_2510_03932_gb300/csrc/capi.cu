@@ -1,4 +1,5 @@
 // C-ABI of the evaluator (declarations and contracts in include/ocp.h).
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -41,10 +42,50 @@ int64_t objective_tiles(int model, int64_t nodes) {
     case OCP_MODEL_VDP: owned = TILE_VDP - 1; break;
     case OCP_MODEL_CARTPOLE: owned = TILE_CARTPOLE - 1; break;
     case OCP_MODEL_DINT: owned = TILE_DINT - 1; break;
+    case OCP_MODEL_QUADROTOR: owned = TILE_QUAD - 1; break;
     case OCP_MODEL_HEAT1D: owned = HEAT_TILE_NODES - 1; break;
     default: return -1;
   }
   return (nodes + owned - 1) / owned;
+}
+
+// Time-varying state reference, tabulated once per node: for the tracked components i,
+//   out[ntrk j + i] = (xref + xslope t_j) + xamp sin(xfreq t_j),  t_j = j h
+// (plain operations in this order, no FMA).  One thread per table entry.
+struct TrackArgs {
+  double* out;
+  int64_t N;
+  double h;
+  int ntrk;
+  double ref[kMaxTrack], slope[kMaxTrack], amp[kMaxTrack], freq[kMaxTrack];
+};
+
+__global__ void k_fill_tracking(const __grid_constant__ TrackArgs a) {
+  const int64_t total = (a.N + 1) * a.ntrk;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += stride) {
+    const int64_t j = idx / a.ntrk;
+    const int i = (int)(idx - j * a.ntrk);
+    const double t = (double)j * a.h;
+    const double lin = a.ref[i] + a.slope[i] * t;
+    a.out[idx] = lin + a.amp[i] * sin(a.freq[i] * t);
+  }
+}
+
+ocp_status fill_tracking(ocp* h) {
+  TrackArgs a;
+  memset(&a, 0, sizeof(a));
+  a.out = h->d_xtrack; a.N = h->N; a.h = h->h; a.ntrk = h->ntrk;
+  for (int i = 0; i < h->ntrk; ++i) {
+    const int k = h->trk_comp[i];
+    a.ref[i] = h->xref[k]; a.slope[i] = h->xslope[k]; a.amp[i] = h->xamp[k]; a.freq[i] = h->xfreq[k];
+  }
+  const int64_t total = (h->N + 1) * h->ntrk;
+  const int64_t blocks = std::min<int64_t>((total + 255) / 256, (int64_t)h->num_sms * 8);
+  k_fill_tracking<<<(int)std::max<int64_t>(blocks, 1), 256>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  return cuda_err(h, e, "tracking table");
 }
 
 }  // namespace ocpg
@@ -56,12 +97,13 @@ static ocp_status upload_tables(ocp* h) {
   cudaFree(h->d_rowtmpl); cudaFree(h->d_jbase); cudaFree(h->d_hent);
   h->d_rowtmpl = nullptr; h->d_jbase = nullptr; h->d_hent = nullptr;
   const Pattern& P = h->pat;
-  std::vector<int32_t> rt((size_t)8 * P.nx, -1);
+  std::vector<int32_t> rt((size_t)RT_STRIDE * P.nx, -1);
   for (int k = 0; k < P.nx; ++k) {
-    rt[8 * k + 0] = P.rows[k].rx;
-    rt[8 * k + 1] = P.rows[k].ru;
-    for (int e = 0; e < 4; ++e) rt[8 * k + 2 + e] = P.rows[k].xv[e];
-    for (int e = 0; e < 2; ++e) rt[8 * k + 6 + e] = P.rows[k].uv[e];
+    int32_t* t = rt.data() + (size_t)RT_STRIDE * k;
+    t[0] = P.rows[k].rx;
+    t[1] = P.rows[k].ru;
+    for (int e = 0; e < RT_XV; ++e) t[2 + e] = P.rows[k].xv[e];
+    for (int e = 0; e < RT_UV; ++e) t[2 + RT_XV + e] = P.rows[k].uv[e];
   }
   std::vector<int32_t> he;
   for (auto& e : P.hent) { he.push_back(e.first); he.push_back(e.second); }
@@ -85,6 +127,7 @@ static int model_nparams(int model) {
     case OCP_MODEL_CARTPOLE: return 4;
     case OCP_MODEL_HEAT1D: return 1;
     case OCP_MODEL_DINT: return 0;
+    case OCP_MODEL_QUADROTOR: return 1;
   }
   return -1;
 }
@@ -92,7 +135,7 @@ static int model_nparams(int model) {
 static void free_handle(ocp* h) {
   if (!h) return;
   cudaFree(h->d_rowtmpl); cudaFree(h->d_jbase); cudaFree(h->d_hent);
-  cudaFree(h->d_partials); cudaFree(h->d_counter);
+  cudaFree(h->d_partials); cudaFree(h->d_counter); cudaFree(h->d_xtrack);
   delete h;
 }
 
@@ -111,6 +154,7 @@ ocp_status init_host(ocp* h, const ocp_dynamics* dyn, const ocp_cost* cost, int 
     case OCP_MODEL_VDP: enx = 2; break;
     case OCP_MODEL_CARTPOLE: enx = 4; break;
     case OCP_MODEL_DINT: enx = 2; break;
+    case OCP_MODEL_QUADROTOR: enx = 9; enu = 4; break;
     case OCP_MODEL_HEAT1D: {
       const double c = dyn->params[0];
       if (!(c >= 2.0 && c <= 128.0) || c != std::floor(c))
@@ -228,6 +272,7 @@ ocp_status ocpg::dispatch_eval(ocp* h, unsigned out, const EvalCall& c, void* st
     case OCP_MODEL_VDP: return node_eval_vdp(h, out, c, s);
     case OCP_MODEL_CARTPOLE: return node_eval_cartpole(h, out, c, s);
     case OCP_MODEL_DINT: return node_eval_dint(h, out, c, s);
+    case OCP_MODEL_QUADROTOR: return node_eval_quad(h, out, c, s);
     case OCP_MODEL_HEAT1D: return heat_eval(h, out, c, s);
   }
   return set_err(h, OCP_EMODEL, "unknown model");
@@ -239,6 +284,7 @@ static ocp_status dispatch_prod(ocp* h, const ProdCall& c, void* stream) {
     case OCP_MODEL_VDP: return node_prod_vdp(h, c, s);
     case OCP_MODEL_CARTPOLE: return node_prod_cartpole(h, c, s);
     case OCP_MODEL_DINT: return node_prod_dint(h, c, s);
+    case OCP_MODEL_QUADROTOR: return node_prod_quad(h, c, s);
     case OCP_MODEL_HEAT1D: return heat_prod(h, c, s);
   }
   return set_err(h, OCP_EMODEL, "unknown model");
@@ -442,6 +488,37 @@ ocp_status ocp_set_param0(ocp_t* h, double value) {
   if (h->model == OCP_MODEL_HEAT1D) return set_err(h, OCP_EMODEL, "the heat cell count is structural");
   h->params[0] = value;
   return OCP_OK;
+}
+
+ocp_status ocp_set_tracking(ocp_t* h, const double* xslope, const double* xamp, const double* xfreq) {
+  if (!h) return OCP_EINVAL;
+  if (h->model == OCP_MODEL_HEAT1D)
+    return set_err(h, OCP_EMODEL, "a time-varying reference is provided for the node models (not HEAT1D)");
+  const int nx = h->nx;
+  h->xslope.assign(nx, 0.0); h->xamp.assign(nx, 0.0); h->xfreq.assign(nx, 0.0);
+  if (xslope) h->xslope.assign(xslope, xslope + nx);
+  if (xamp) h->xamp.assign(xamp, xamp + nx);
+  if (xfreq) h->xfreq.assign(xfreq, xfreq + nx);
+  for (int k = 0; k < nx; ++k)
+    if (!std::isfinite(h->xslope[k]) || !std::isfinite(h->xamp[k]) || !std::isfinite(h->xfreq[k]))
+      return set_err(h, OCP_EINVAL, "tracking coefficients must be finite");
+  h->trk_comp.clear();
+  for (int k = 0; k < nx; ++k)
+    if (h->xslope[k] != 0.0 || (h->xamp[k] != 0.0 && h->xfreq[k] != 0.0)) h->trk_comp.push_back(k);
+  cudaFree(h->d_xtrack);
+  h->d_xtrack = nullptr;
+  h->ntrk = 0;
+  h->has_ref = false;
+  for (double v : h->xref) if (v != 0.0) h->has_ref = true;
+  for (double v : h->uref) if (v != 0.0) h->has_ref = true;
+  if (h->trk_comp.empty()) return OCP_OK;
+  if ((int)h->trk_comp.size() > kMaxTrack) return set_err(h, OCP_EDIM, "too many tracked components");
+  const size_t bytes = sizeof(double) * (size_t)(h->N + 1) * h->trk_comp.size();
+  cudaError_t e = cudaMalloc(&h->d_xtrack, bytes);
+  if (e != cudaSuccess) { h->d_xtrack = nullptr; h->trk_comp.clear(); return cuda_err(h, e, "cudaMalloc(tracking table)"); }
+  h->ntrk = (int)h->trk_comp.size();
+  h->has_ref = true;
+  return fill_tracking(h);
 }
 
 const char* ocp_last_error(const ocp_t* h) { return h ? h->err.c_str() : g_create_err.c_str(); }

@@ -76,6 +76,9 @@ struct NodeArgs {
   const double* p0_dev;           // model parameter 0 read from the device (or null: K as given)
   int64_t N, nb, B, E, ntiles, uoff;  // uoff = nx (N+1): first U entry of x
   int has_final, has_ref, range;
+  const double* xtrack;            // time-varying state reference, (N+1) x ntrk node-major, or null
+  int ntrk;
+  int8_t trk[M::NX];               // column of state k in xtrack, or -1 (constant reference)
   ModelConst K;
   double cq_in[M::NZ], cq_end[M::NZ];  // 2 sigma w q on the diagonal (interior / end node)
   double gq_in[M::NZ], gq_end[M::NZ];  // 2 w q  (gradient)
@@ -221,12 +224,16 @@ __device__ __forceinline__ void load_ybar(const NodeArgs<M>& a, const double* w,
 }
 
 // gradient entries g_v = 2 w_j q_v (z_v - ref_v); returns 2 w_j f0(z_j) = sum_v g_v (z_v - ref_v)
+// (ref_v of a tracked state component is read from the per-node table xtrack)
 template <class M, bool REF, bool WG>
 __device__ __forceinline__ double node_grad(const NodeArgs<M>& a, const double (&z)[M::NZ], bool endp, int64_t j) {
   double s = 0.0;
 #pragma unroll
   for (int v = 0; v < M::NZ; ++v) {
-    const double d = REF ? fsub(a.K, z[v], a.ref[v]) : z[v];
+    double rv = a.ref[v];
+    if (REF && v < M::NX && a.xtrack && a.trk[v < M::NX ? v : 0] >= 0)
+      rv = __ldg(a.xtrack + (int64_t)a.ntrk * j + a.trk[v < M::NX ? v : 0]);
+    const double d = REF ? fsub(a.K, z[v], rv) : z[v];
     const double gv = fmul(a.K, endp ? a.gq_end[v] : a.gq_in[v], d);
     if (WG) {
       if (v < M::NX) a.g[(int64_t)M::NX * j + v] = gv;
@@ -252,10 +259,11 @@ __device__ __forceinline__ void jv_node(const ModelConst& K, const double (&mjx)
     double cf[M::MAXRX + M::MAXRU + 1], vv[M::MAXRX + M::MAXRU + 1];
     int nt = 0;
 #pragma unroll
-    for (int e = 0; e < M::RX(k); ++e)
-      if (!M::JZ(k, e)) { cf[nt] = mjx[k][e]; vv[nt] = vz[M::XV(k, e)]; ++nt; }
+    for (int e = 0; e < M::MAXRX; ++e)
+      if (e < M::RX(k) && !M::JZ(k, e)) { cf[nt] = mjx[k][e]; vv[nt] = vz[M::XV(k, e)]; ++nt; }
 #pragma unroll
-    for (int e = 0; e < M::RU(k); ++e) { cf[nt] = mju[k][e]; vv[nt] = vz[NX + M::UV(k, e)]; ++nt; }
+    for (int e = 0; e < M::MAXRU; ++e)
+      if (e < M::RU(k)) { cf[nt] = mju[k][e]; vv[nt] = vz[NX + M::UV(k, e)]; ++nt; }
     if (PDIR) { cf[nt] = mdp[k]; vv[nt] = pd; ++nt; }
     double s = 0.0;
 #pragma unroll
@@ -284,19 +292,20 @@ __device__ __forceinline__ void jtv_node(const NodeArgs<M>& a, const double* w, 
                                          const double (&wl)[M::NX], const double (&wr)[M::NX],
                                          const double (&wb)[M::NX], double (&o)[M::NZ]) {
   constexpr int NX = M::NX;
+  // every state entry accumulates its terms in increasing k (one pass over the row templates)
 #pragma unroll
-  for (int v = 0; v < NX; ++v) {
-    double s = fsub(a.K, wl[v], wr[v]);
+  for (int v = 0; v < NX; ++v) o[v] = fsub(a.K, wl[v], wr[v]);
 #pragma unroll
-    for (int k = 0; k < NX; ++k)
+  for (int k = 0; k < NX; ++k)
 #pragma unroll
-      for (int e = 0; e < M::RX(k); ++e)
-        if (M::XV(k, e) == v && !M::JZ(k, e)) s = fma(wb[k], mjx[k][e], s);
-    if (bnd) {  // only CTAs holding node 0 or node N (uniform branch)
-      if (j == 0) s = fadd(a.K, s, __ldg(w + v));
-      if (a.has_final && j == a.N) s = fadd(a.K, s, __ldg(w + NX + v));
+    for (int e = 0; e < M::MAXRX; ++e)
+      if (e < M::RX(k) && !M::JZ(k, e)) o[M::XV(k, e)] = fma(wb[k], mjx[k][e], o[M::XV(k, e)]);
+  if (bnd) {  // only CTAs holding node 0 or node N (uniform branch)
+#pragma unroll
+    for (int v = 0; v < NX; ++v) {
+      if (j == 0) o[v] = fadd(a.K, o[v], __ldg(w + v));
+      if (a.has_final && j == a.N) o[v] = fadd(a.K, o[v], __ldg(w + NX + v));
     }
-    o[v] = s;
   }
 #pragma unroll
   for (int i = 0; i < M::NU; ++i) {
@@ -305,8 +314,8 @@ __device__ __forceinline__ void jtv_node(const NodeArgs<M>& a, const double* w, 
 #pragma unroll
     for (int k = 0; k < NX; ++k)
 #pragma unroll
-      for (int e = 0; e < M::RU(k); ++e)
-        if (M::UV(k, e) == i) { s = first ? fmul(a.K, wb[k], mju[k][e]) : fma(wb[k], mju[k][e], s); first = false; }
+      for (int e = 0; e < M::MAXRU; ++e)
+        if (e < M::RU(k) && M::UV(k, e) == i) { s = first ? fmul(a.K, wb[k], mju[k][e]) : fma(wb[k], mju[k][e], s); first = false; }
     o[NX + i] = s;
   }
 }
@@ -474,16 +483,20 @@ __device__ __forceinline__ void node_eval_tile(const NodeArgs<M>& a, const Model
         if (lt < nrows) {
           double* rp = sj + lt * cnt;
 #pragma unroll
-          for (int e = 0; e < M::RX(k); ++e) rp[e] = (M::XV(k, e) == k) ? fma(mjx[k][e], K.one, -1.0) : mjx[k][e];
+          for (int e = 0; e < M::MAXRX; ++e)
+            if (e < M::RX(k)) rp[e] = (M::XV(k, e) == k) ? fma(mjx[k][e], K.one, -1.0) : mjx[k][e];
 #pragma unroll
-          for (int e = 0; e < M::RU(k); ++e) rp[2 * M::RX(k) + e] = mju[k][e];
+          for (int e = 0; e < M::MAXRU; ++e)
+            if (e < M::RU(k)) rp[2 * M::RX(k) + e] = mju[k][e];
         }
         if (lt >= 1 && lt - 1 < nrows) {
           double* rp = sj + (lt - 1) * cnt;
 #pragma unroll
-          for (int e = 0; e < M::RX(k); ++e) rp[M::RX(k) + e] = (M::XV(k, e) == k) ? fma(mjx[k][e], K.one, 1.0) : mjx[k][e];
+          for (int e = 0; e < M::MAXRX; ++e)
+            if (e < M::RX(k)) rp[M::RX(k) + e] = (M::XV(k, e) == k) ? fma(mjx[k][e], K.one, 1.0) : mjx[k][e];
 #pragma unroll
-          for (int e = 0; e < M::RU(k); ++e) rp[2 * M::RX(k) + M::RU(k) + e] = mju[k][e];
+          for (int e = 0; e < M::MAXRU; ++e)
+            if (e < M::RU(k)) rp[2 * M::RX(k) + M::RU(k) + e] = mju[k][e];
         }
       }
     }
@@ -762,6 +775,10 @@ void fill_args(const ocp* h, double sigma, NodeArgs<M>& a) {
   a.partials = h->d_partials;
   a.counter = h->d_counter;
   a.p0_dev = h->p0_dev;
+  a.xtrack = h->d_xtrack;
+  a.ntrk = h->ntrk;
+  for (int k = 0; k < M::NX; ++k) a.trk[k] = -1;
+  for (int i = 0; i < h->ntrk; ++i) a.trk[h->trk_comp[i]] = (int8_t)i;
 }
 
 template <class M, int TILE, int NPT, unsigned OUT>

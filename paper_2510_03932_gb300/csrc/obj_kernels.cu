@@ -1,5 +1,6 @@
 // Objective-only kernels for the differentiation form (any model: the running cost is the
-// diagonal quadratic f0 = sum_v q_v (z_v - ref_v)^2, so only the cost coefficients matter):
+// diagonal quadratic f0 = sum_v q_v (z_v - ref_v)^2, so only the cost coefficients and the
+// reference matter; a tracked state's ref_v(t_j) comes from the per-node table):
 //   g  = s * grad F(x)                       (s a device scalar: the upstream gradient)
 //   Hv = s * Hess F(x) v,  dot = grad F(x) . v   (double backward of the objective)
 // with  grad F_{j,v} = 2 w_j q_v (z_v - ref_v)  and  Hess F = diag(2 w_j q_v)  (paper Sec. 5
@@ -26,7 +27,10 @@ struct ObjArgs {
   int64_t N, uoff;
   int nx, nu, has_ref;
   double one, mz;   // 1.0 and -0.0 at run time: sums and products are issued as FMAs
+  const double* xtrack;  // time-varying state reference, (N+1) x ntrk node-major, or null
+  int ntrk;
   double gq_in[OBJ_MAXV], gq_end[OBJ_MAXV], ref[OBJ_MAXV];
+  int trk[OBJ_MAXV];     // column of state v in xtrack, or -1
 };
 
 __device__ __forceinline__ int64_t var_index(const ObjArgs& a, int64_t j, int v) {
@@ -49,7 +53,9 @@ __global__ void __launch_bounds__(OBJ_THREADS) k_obj(const __grid_constant__ Obj
         const int64_t idx = var_index(a, j, v);
         const double gq = endp ? a.gq_end[v] : a.gq_in[v];   // 2 w_j q_v
         const double z = __ldg(a.x + idx);
-        const double d = a.has_ref ? fma(-a.ref[v], a.one, z) : z;
+        double rv = a.ref[v];
+        if (v < a.nx && a.xtrack && a.trk[v] >= 0) rv = __ldg(a.xtrack + (int64_t)a.ntrk * j + a.trk[v]);
+        const double d = a.has_ref ? fma(-rv, a.one, z) : z;
         const double sg = fma(s, gq, a.mz);
         if (HVP) {
           const double vv = __ldg(a.v + idx);
@@ -81,6 +87,10 @@ ocp_status obj_launch(ocp* h, bool hvp, const double* x, const double* s, const 
   a.nx = h->nx; a.nu = h->nu; a.has_ref = h->has_ref ? 1 : 0;
   a.one = 1.0;
   a.mz = -0.0;
+  a.xtrack = h->d_xtrack;
+  a.ntrk = h->ntrk;
+  for (int v2 = 0; v2 < OBJ_MAXV; ++v2) a.trk[v2] = -1;
+  for (int i = 0; i < h->ntrk; ++i) a.trk[h->trk_comp[i]] = i;
   for (int v2 = 0; v2 < nz; ++v2) {
     const double w = v2 < h->nx ? h->q[v2] : h->r[v2 - h->nx];
     a.gq_in[v2] = 2.0 * h->h * w;

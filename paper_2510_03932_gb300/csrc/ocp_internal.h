@@ -12,7 +12,9 @@
 namespace ocpg {
 
 // Threads (= nodes) per CTA of the node-model kernels; a tile owns TILE-1 nodes.
-constexpr int TILE_VDP = 256, TILE_CARTPOLE = 128, TILE_DINT = 256;
+constexpr int TILE_VDP = 256, TILE_CARTPOLE = 128, TILE_DINT = 256, TILE_QUAD = 64;
+// Most state components with a time-varying reference (node models have at most 9 states).
+constexpr int kMaxTrack = 16;
 // Nodes per CTA of the heat-equation kernels (one per lane); a tile owns 31 nodes.
 constexpr int HEAT_TILE_NODES = 32;
 
@@ -22,10 +24,12 @@ enum : unsigned { O_F = 1u, O_C = 2u, O_G = 4u, O_J = 8u, O_H = 16u, O_ALL = 31u
                   O_JV = 32u, O_JTV = 64u, O_HV = 128u, O_STEP = 255u };
 
 // Per-component Jacobian row template (local variable indices), as read from the model.
+constexpr int RT_XV = 6, RT_UV = 4;
+constexpr int RT_STRIDE = 2 + RT_XV + RT_UV;  // ints per row in the device table: rx, ru, xv[], uv[]
 struct RowTemplate {
   int rx = 0, ru = 0;
-  int xv[4] = {-1, -1, -1, -1};
-  int uv[2] = {-1, -1};
+  int xv[RT_XV] = {-1, -1, -1, -1, -1, -1};
+  int uv[RT_UV] = {-1, -1, -1, -1};
   int count() const { return 2 * (rx + ru); }
 };
 
@@ -52,10 +56,16 @@ struct ocp {
   std::vector<double> params, q, r, xref, uref, x0, xf;
   bool has_final = false, has_ref = false;
   const double* p0_dev = nullptr;  // device scalar overriding params[0] (or null)
+  // time-varying state reference: xref_k + xslope_k t_j + xamp_k sin(xfreq_k t_j) for the
+  // components trk_comp (ntrk of them), tabulated once per node in d_xtrack[(N+1) x ntrk]
+  std::vector<double> xslope, xamp, xfreq;
+  std::vector<int> trk_comp;
+  int ntrk = 0;
+  double* d_xtrack = nullptr;
   ocpg::Pattern pat;
   int device = 0, num_sms = 0;
   // device-resident pattern tables for the structure kernels
-  int32_t* d_rowtmpl = nullptr;  // nx * 8 ints: rx, ru, xv[4], uv[2]
+  int32_t* d_rowtmpl = nullptr;  // nx * RT_STRIDE ints: rx, ru, xv[RT_XV], uv[RT_UV]
   int64_t* d_jbase = nullptr;    // nx + 1
   int32_t* d_hent = nullptr;     // 2 * (hx + hu)
   // scratch: per-CTA partial sums and the completion ticket of the last-block reduction
@@ -106,13 +116,17 @@ struct ProdCall {
   const double* mixs = nullptr; // device scalar
 };
 
-// Per-model dispatchers (node models: VDP, CARTPOLE, DINT; HEAT1D separate).
+// Per-model dispatchers (node models: VDP, CARTPOLE, DINT, QUADROTOR; HEAT1D separate).
 ocp_status node_eval_vdp(ocp* h, unsigned out, const EvalCall& c, cudaStream_t s);
 ocp_status node_eval_cartpole(ocp* h, unsigned out, const EvalCall& c, cudaStream_t s);
 ocp_status node_eval_dint(ocp* h, unsigned out, const EvalCall& c, cudaStream_t s);
+ocp_status node_eval_quad(ocp* h, unsigned out, const EvalCall& c, cudaStream_t s);
 ocp_status node_prod_vdp(ocp* h, const ProdCall& c, cudaStream_t s);
 ocp_status node_prod_cartpole(ocp* h, const ProdCall& c, cudaStream_t s);
 ocp_status node_prod_dint(ocp* h, const ProdCall& c, cudaStream_t s);
+ocp_status node_prod_quad(ocp* h, const ProdCall& c, cudaStream_t s);
+// Tabulate the time-varying state reference of the handle into h->d_xtrack.
+ocp_status fill_tracking(ocp* h);
 ocp_status heat_eval(ocp* h, unsigned out, const EvalCall& c, cudaStream_t s);
 ocp_status heat_prod(ocp* h, const ProdCall& c, cudaStream_t s);
 

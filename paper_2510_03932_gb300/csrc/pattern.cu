@@ -21,6 +21,7 @@ namespace ocpg {
 
 template <class M>
 static void rows_from(std::vector<RowTemplate>& rows) {
+  static_assert(M::MAXRX <= RT_XV && M::MAXRU <= RT_UV, "row template wider than the device table");
   rows.assign(M::NX, RowTemplate());
   for (int k = 0; k < M::NX; ++k) {
     rows[k].rx = M::RX(k);
@@ -35,6 +36,7 @@ void model_row_templates(int model, int nx, std::vector<RowTemplate>& rows) {
     case OCP_MODEL_VDP: rows_from<VdP>(rows); break;
     case OCP_MODEL_CARTPOLE: rows_from<CartPole>(rows); break;
     case OCP_MODEL_DINT: rows_from<Dint>(rows); break;
+    case OCP_MODEL_QUADROTOR: rows_from<Quadrotor>(rows); break;
     case OCP_MODEL_HEAT1D:
       rows.assign(nx, RowTemplate());
       for (int k = 0; k < nx; ++k) {
@@ -67,6 +69,7 @@ void model_hess_max_template(int model, int nx, std::vector<std::pair<int, int>>
     case OCP_MODEL_VDP: hmax_from<VdP>(ent, is_dyn); break;
     case OCP_MODEL_CARTPOLE: hmax_from<CartPole>(ent, is_dyn); break;
     case OCP_MODEL_DINT: hmax_from<Dint>(ent, is_dyn); break;
+    case OCP_MODEL_QUADROTOR: hmax_from<Quadrotor>(ent, is_dyn); break;
     case OCP_MODEL_HEAT1D:
       ent.clear();
       is_dyn.clear();
@@ -125,7 +128,7 @@ bool build_pattern(ocp* h, std::string& why) {
 struct JacStructArgs {
   int32_t* rows;
   int32_t* cols;
-  const int32_t* tmpl;   // per component: rx, ru, xv[4], uv[2]
+  const int32_t* tmpl;   // per component (RT_STRIDE ints): rx, ru, xv[RT_XV], uv[RT_UV]
   const int64_t* jbase;  // nx + 1
   int64_t N, nb, nnzj, uoff;
   int nx, nu, has_final;
@@ -145,7 +148,7 @@ __global__ void k_jac_structure(const __grid_constant__ JacStructArgs a) {
         if (a.jbase[mid] <= s) lo = mid; else hi = mid - 1;
       }
       const int k = lo;
-      const int32_t* t = a.tmpl + 8 * k;
+      const int32_t* t = a.tmpl + RT_STRIDE * k;
       const int rx = t[0], ru = t[1];
       const int cnt = 2 * (rx + ru);
       const int64_t rel = s - a.jbase[k];
@@ -154,8 +157,8 @@ __global__ void k_jac_structure(const __grid_constant__ JacStructArgs a) {
       row = a.nb + (int64_t)k * a.N + j;
       if (e < rx) col = (int64_t)a.nx * j + t[2 + e];
       else if (e < 2 * rx) col = (int64_t)a.nx * (j + 1) + t[2 + (e - rx)];
-      else if (e < 2 * rx + ru) col = a.uoff + (int64_t)a.nu * j + t[6 + (e - 2 * rx)];
-      else col = a.uoff + (int64_t)a.nu * (j + 1) + t[6 + (e - 2 * rx - ru)];
+      else if (e < 2 * rx + ru) col = a.uoff + (int64_t)a.nu * j + t[2 + RT_XV + (e - 2 * rx)];
+      else col = a.uoff + (int64_t)a.nu * (j + 1) + t[2 + RT_XV + (e - 2 * rx - ru)];
     }
     a.rows[s] = (int32_t)row;
     a.cols[s] = (int32_t)col;

@@ -14,7 +14,7 @@ import torch
 
 from . import build as _build
 
-MODEL_IDS = {"vdp": 1, "cartpole": 2, "heat": 3, "dint": 4}
+MODEL_IDS = {"vdp": 1, "cartpole": 2, "heat": 3, "dint": 4, "quadrotor": 5}
 STATUS = {0: "OCP_OK", 1: "OCP_EINVAL", 2: "OCP_EDIM", 3: "OCP_ENOMEM", 4: "OCP_ECUDA", 5: "OCP_EMODEL",
           6: "OCP_ETIMEOUT"}
 
@@ -43,6 +43,7 @@ _SIGS = {
     "ocp_create": [C.POINTER(_Dyn), C.POINTER(_Cost), C.c_int, C.c_int, _I64, _D, C.POINTER(_P)],
     "ocp_destroy": [_P],
     "ocp_set_boundary": [_P, _P, _P],
+    "ocp_set_tracking": [_P, _P, _P, _P],
     "ocp_dims": [_P, C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_I64)],
     "ocp_bounds": [_P, _P, _P, _P, _P],
     "eval_obj": [_P, _P, _P, _P],
@@ -110,7 +111,7 @@ class OCP:
     """A transcribed optimal control problem (an `ocp_t` handle)."""
 
     def __init__(self, model: str, nx: int, nu: int, N: int, T: float, params, q, r, xref=None, uref=None,
-                 x0=None, xf=None):
+                 x0=None, xf=None, xslope=None, xamp=None, xfreq=None):
         L = lib()
         self._keep = []
 
@@ -129,6 +130,9 @@ class OCP:
         self.model, self.nx, self.nu, self.N, self.T = model, nx, nu, int(N), float(T)
         if x0 is not None or xf is not None:
             _check(L.ocp_set_boundary(h, arr(x0), arr(xf)), h)
+        if xslope is not None or xamp is not None or xfreq is not None:
+            # time-varying state reference xref_k + xslope_k t + xamp_k sin(xfreq_k t)
+            _check(L.ocp_set_tracking(h, arr(xslope), arr(xamp), arr(xfreq)), h)
         n, m, nj, nh = _I64(), _I64(), _I64(), _I64()
         _check(L.ocp_dims(h, C.byref(n), C.byref(m), C.byref(nj), C.byref(nh)), h)
         self.n, self.m, self.nnzj, self.nnzh = n.value, m.value, nj.value, nh.value
@@ -137,7 +141,7 @@ class OCP:
     @classmethod
     def from_workload(cls, w: dict) -> "OCP":
         return cls(w["model"], w["nx"], w["nu"], w["N"], w["T"], w["params"], w["q"], w["r"], w.get("xref"),
-                   w.get("uref"), w.get("x0"), w.get("xf"))
+                   w.get("uref"), w.get("x0"), w.get("xf"), w.get("xslope"), w.get("xamp"), w.get("xfreq"))
 
     def close(self):
         if getattr(self, "h", None):

@@ -52,7 +52,7 @@ def test_constraints_gradcheck_cartpole(mods):
     assert torch.autograd.gradgradcheck(f, (x,), eps=1e-6, atol=1e-5, rtol=1e-4)
 
 
-@pytest.mark.parametrize("name,N", [("vdp_n1e3", 12), ("heat_n2e4", 3)])
+@pytest.mark.parametrize("name,N", [("vdp_n1e3", 12), ("heat_n2e4", 3), ("quadrotor_n1e3", 4)])
 def test_objective_gradcheck(mods, name, N):
     ocp, A = mods
     w, d = small(name, N)

@@ -79,7 +79,8 @@ def full_check(ocp, w, report=None, products=True):
 SMALL = [("vdp_n1e3", N) for N in (1, 2, 3, 254, 255, 256, 510, 1000, 1777)] + \
         [("cartpole_n1e5", N) for N in (1, 2, 126, 127, 128, 1000, 1303)] + \
         [("heat_n2e4", N) for N in (1, 2, 30, 31, 32, 100, 333)] + \
-        [("dint", N) for N in (1, 2, 100, 997)]
+        [("dint", N) for N in (1, 2, 100, 997)] + \
+        [("quadrotor_n1e3", N) for N in (1, 2, 62, 63, 64, 126, 1000, 1777)]
 
 
 @pytest.mark.parametrize("name,N", SMALL)
@@ -99,13 +100,37 @@ def test_parity_reference_offsets(ocp):
     full_check(ocp, w)
 
 
+@pytest.mark.parametrize("name,N", [("vdp_n1e3", 600), ("cartpole_n1e5", 300), ("dint", 50)])
+def test_parity_time_varying_reference(ocp, name, N):
+    """The tracking reference xref + xslope t + xamp sin(xfreq t) on the other node models."""
+    w = synth.with_horizon(synth.workload(name), N)
+    nx = w["nx"]
+    w = dict(w, xslope=[0.3 * (k + 1) for k in range(nx)], xamp=[0.0] + [1.5] * (nx - 1),
+             xfreq=[2.0] * nx, q=[0.5] * nx)
+    full_check(ocp, w)
+
+
+def test_tracking_reset_returns_to_constant_reference(ocp):
+    """Zero coefficients drop the table: the objective equals that of the plain problem."""
+    w = synth.with_horizon(synth.workload("quadrotor_n1e3"), 200)
+    d = synth.draw(w)
+    x = dev(d["x"])
+    plain = {k: v for k, v in w.items() if k not in ("xslope", "xamp", "xfreq")}
+    H0 = ocp.OCP.from_workload(plain)
+    H1 = ocp.OCP.from_workload(dict(w, xslope=[0.0] * 9, xamp=[0.0] * 9, xfreq=[0.0] * 9))
+    H2 = ocp.OCP.from_workload(w)
+    f0, f1, f2 = H0.eval_obj(x), H1.eval_obj(x), H2.eval_obj(x)
+    torch.cuda.synchronize()
+    assert torch.equal(f0, f1) and not torch.equal(f0, f2)
+
+
 def test_parity_cost_structure_follows_weights(ocp):
     """A zero cost weight drops a diagonal Hessian entry that the dynamics do not need."""
     w = dict(synth.with_horizon(synth.workload("vdp_n1e3"), 50), q=[1.0, 0.0])
     full_check(ocp, w)
 
 
-@pytest.mark.parametrize("name", ["vdp_n1e3", "cartpole_n1e5", "heat_n2e4", "vdp_mu_n1e6"])
+@pytest.mark.parametrize("name", ["vdp_n1e3", "cartpole_n1e5", "heat_n2e4", "vdp_mu_n1e6", "quadrotor_n1e5"])
 def test_parity_full_size_workloads(ocp, name):
     rep = full_check(ocp, synth.workload(name), products=(name != "vdp_mu_n1e6"))
     print(name, rep)
@@ -143,7 +168,7 @@ def test_deterministic_run_to_run(ocp):
 
 
 @pytest.mark.parametrize("name,N,S", [("vdp_n1e3", 5000, 3), ("cartpole_n1e5", 2000, 4), ("heat_n2e4", 500, 3),
-                                      ("dint", 300, 2)])
+                                      ("dint", 300, 2), ("quadrotor_n1e3", 700, 3)])
 def test_virtual_shards_match_unsharded(ocp, name, N, S):
     """S contiguous node shards, each reading a one-node halo, reproduce the unsharded
     evaluation slot for slot; the objective is the sum of the shard partials."""
@@ -185,7 +210,7 @@ def test_dimension_and_argument_errors(ocp):
 
 
 @pytest.mark.parametrize("name,N", [("vdp_n1e3", 1000), ("vdp_n1e3", 254), ("cartpole_n1e5", 1303),
-                                    ("dint", 97), ("heat_n2e4", 77)])
+                                    ("dint", 97), ("heat_n2e4", 77), ("quadrotor_n1e3", 1000)])
 def test_fused_step_equals_separate_calls(ocp, name, N):
     """ocp_eval_step (one pass: eval + Jv + J^T w + Hv) is bit-identical to the separate calls."""
     w = synth.with_horizon(synth.workload(name), N)
