@@ -33,15 +33,22 @@ METRIC = "Jac+Hess COO nnz/s (FP64) and % HBM roofline; batched/adjoint vs plain
 DEFAULT_WORKLOAD = "vdp_mu_n1e6"
 
 
+def tracked_components(w):
+    """State components with a time-varying reference (their per-node table is read too)."""
+    sl, am, fr = (w.get(k) or [0.0] * w["nx"] for k in ("xslope", "xamp", "xfreq"))
+    return sum(1 for k in range(w["nx"]) if sl[k] != 0.0 or (am[k] != 0.0 and fr[k] != 0.0))
+
+
 def algorithmic_bytes(w, kind):
     """Bytes each kernel must move at least once: inputs read once, outputs written once."""
     n, m = synth.dims(w)
     P = _counts(w)
     nnzj, nnzh = P
+    trk = tracked_components(w) * (w["N"] + 1)   # reference table, read by F and grad
     if kind == "eval_all":
-        return 8 * (n + m + 1 + m + n + nnzj + nnzh)
+        return 8 * (n + m + 1 + m + n + nnzj + nnzh + trk)
     if kind == "step":  # reads x, y, vn, vm; writes f, c, g, J, H, Jv, J^T w, Hv
-        return 8 * (n + m + n + m + 1 + m + n + nnzj + nnzh + m + n + n)
+        return 8 * (n + m + n + m + 1 + m + n + nnzj + nnzh + m + n + n + trk)
     if kind == "jh":
         return 8 * (n + m + nnzj + nnzh)
     if kind == "jprod":
@@ -66,14 +73,23 @@ def _counts(w):
     return _COUNT_CACHE[key]
 
 
-# FP64 instructions (DFMA, DADD, DMUL per thread) each kernel executes per node, counted from
-# the kernel source and equal to ncu's sm__sass_thread_inst_executed_op_{dfma,dadd,dmul}
-# counts divided by N+1 (Van der Pol: the objective's tile reduction adds 1.5 per node).
+# FP64 instructions (DFMA, DADD, DMUL per thread) each kernel executes per node.  Van der Pol:
+# counted from the kernel source and equal to ncu's sm__sass_thread_inst_executed_op_{dfma,dadd,
+# dmul} counts divided by N+1 (the objective's tile reduction adds 1.5 per node).  Quadrotor:
+# ncu's sm__inst_executed_pipe_fp64 x 32 / (N+1) at N = 1e5, which includes the FP64 work of
+# the three sincos calls and the 1/cos division (about 130 per node).
 FP64_OPS_PER_NODE = {("vdp", "eval_all"): 26.5, ("vdp", "jh"): 10.0, ("vdp", "jprod"): 14.0,
-                     ("vdp", "jtprod"): 12.0, ("vdp", "hprod"): 11.0, ("vdp", "step"): 51.6}
-# DRAM bytes (read + write) of one launch, from an ncu capture of the same kernel (see
-# profiles/); None until captured for the current kernel version.
-TRAFFIC = {}
+                     ("vdp", "jtprod"): 12.0, ("vdp", "hprod"): 11.0, ("vdp", "step"): 51.6,
+                     ("quadrotor", "eval_all"): 275.4, ("quadrotor", "jh"): 199.1, ("quadrotor", "jprod"): 180.9,
+                     ("quadrotor", "jtprod"): 172.1, ("quadrotor", "hprod"): 214.1, ("quadrotor", "step"): 432.9}
+# Rows of the paper's workloads beyond the headline problem, measured the same way (fused
+# step with an L2 flush between steps) and reported under "widened".
+WIDENED = ["quadrotor_n1e6"]
+# DRAM bytes (read + write) of one launch of the fused step at the bench workload, from an ncu
+# capture of the same kernel version (dram__bytes_read.sum + dram__bytes_write.sum; writes
+# still dirty in L2 when the kernel ends are not counted).  Remove an entry when its kernel
+# changes.
+TRAFFIC = {("vdp_mu_n1e6", "step"): 228.05e6}
 FP64_INST_PER_CLK_PER_SM = 2.0   # measured: DFMA throughput of one SM (DADD/DMUL are ~15% slower)
 NUM_SMS = 152
 
@@ -268,14 +284,14 @@ def run_ours(args, rank, world):
                     l2="flushed between steps (512 MB write)",
                     parallelism="replicas" if world > 1 else "single"),
         roofline=dict(bound="alu", achieved=fp64_ach, peak=fp64_peak, unit="G FP64 inst/s",
-                      frac=(fp64_ach / fp64_peak) if fp64_ach else None, traffic=TRAFFIC.get((w["model"], "step")),
+                      frac=(fp64_ach / fp64_peak) if fp64_ach else None, traffic=TRAFFIC.get((w["name"], "step")),
                       kernel="k_node_eval<step> (fused step: F, c, grad, J, H, Jv, J^T w, Hv)",
                       fp64_inst_per_node=ops,
                       peak_basis="%.0f FP64 inst/clk/SM x %d SMs x %.0f MHz (median SM clock under load)"
                                  % (FP64_INST_PER_CLK_PER_SM, NUM_SMS, clk)),
         roofline_hbm=dict(bound="hbm", achieved=achieved, peak=hbm, unit="GB/s", frac=achieved / hbm,
                           peak_source=peak_kind, algorithmic_bytes=ab,
-                          traffic=TRAFFIC.get((w["model"], "step"))),
+                          traffic=TRAFFIC.get((w["name"], "step"))),
         separate_calls_ms=float(kern_ms.sum()),
         kernels={nm: dict(ms=float(kern_ms[i]), GBps=algorithmic_bytes(w, nm) / (kern_ms[i] * 1e-3) / 1e9,
                           hbm_frac=algorithmic_bytes(w, nm) / (kern_ms[i] * 1e-3) / 1e9 / hbm,
@@ -290,6 +306,63 @@ def run_ours(args, rank, world):
         gpu_launches=args.steps, clocks=clocks, wall_s=wall,
     )
     return res
+
+
+def run_widened(name, steps, warmup):
+    """Fused step, separate calls and J+H alone for one more workload (no e2e, no clocks)."""
+    import torch
+    from paper_2510_03932_gb300 import ocp
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    w = synth.workload(name)
+    d = synth.draw(w)
+    H = ocp.OCP.from_workload(w)
+    x, y, vn, vm = (torch.from_numpy(d[k]).to(dev) for k in ("x", "y", "vn", "vm"))
+    sigma = w["sigma"]
+    f, c, g, jv, hv, Jv, Jtv, Hv = H.eval_step(x, y, sigma, vn, vm)
+    outs = (f, c, g, jv, hv, Jv, Jtv, Hv)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    calls = {
+        "step": lambda: H.eval_step(x, y, sigma, vn, vm, outs),
+        "eval_all": lambda: H.eval_all(x, y, sigma, f, c, g, jv, hv, alloc=False),
+        "jh": lambda: H.eval_all(x, y, sigma, None, None, None, jv, hv, alloc=False),
+        "jprod": lambda: H.jprod(x, vn, Jv),
+        "jtprod": lambda: H.jtprod(x, vm, Jtv),
+        "hprod": lambda: H.hprod(x, y, sigma, vn, Hv),
+    }
+    ms = {}
+    for nm, fn in calls.items():
+        for _ in range(warmup):
+            fn()
+        evs = []
+        for _ in range(steps if nm == "step" else max(3, steps // 4)):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize(dev)
+        ms[nm] = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+    hbm, _ = peaks()
+    clk = 2070.0
+    fp64_peak = FP64_INST_PER_CLK_PER_SM * NUM_SMS * clk * 1e6 / 1e9
+    nnz = H.nnzj + H.nnzh
+    out = dict(workload=name, model=w["model"], N=w["N"], n=H.n, m=H.m, nnz_jac=H.nnzj, nnz_hess=H.nnzh,
+               step_ms=ms["step"], nnz_per_s=nnz / (ms["step"] * 1e-3),
+               separate_calls_ms=ms["eval_all"] + ms["jprod"] + ms["jtprod"] + ms["hprod"],
+               jac_hess_only=dict(ms=ms["jh"], nnz_per_s=nnz / (ms["jh"] * 1e-3)), kernels={})
+    for nm in ("step", "eval_all", "jh", "jprod", "jtprod", "hprod"):
+        ab = algorithmic_bytes(w, nm)
+        ops = FP64_OPS_PER_NODE.get((w["model"], nm))
+        out["kernels"][nm] = dict(
+            ms=ms[nm], hbm_frac=ab / (ms[nm] * 1e-3) / 1e9 / hbm,
+            fp64_frac=(ops * (w["N"] + 1) / (ms[nm] * 1e-3) / 1e9 / fp64_peak) if ops else None)
+    out["bound"] = "alu" if (out["kernels"]["step"]["fp64_frac"] or 0) > out["kernels"]["step"]["hbm_frac"] else "hbm"
+    out["fp64_peak_basis"] = "2 FP64 inst/clk/SM x 152 SMs x 2070 MHz"
+    H.close()
+    return out
 
 
 def run_forms(args, hbm):
@@ -445,6 +518,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-forms", action="store_true", help="skip the batched and differentiation forms")
+    ap.add_argument("--no-widened", action="store_true", help="skip the further workloads (quadrotor)")
     ap.add_argument("--profile-kernel", default=None,
                     choices=["eval_all", "jh", "jprod", "jtprod", "hprod", "step", "all"],
                     help="only launch this call warmup+steps times (for ncu captures)")
@@ -476,6 +550,9 @@ def main():
     res = run_ours(args, rank, world)
     if rank == 0 and not args.no_forms:
         res["forms"] = run_forms(args, res["roofline_hbm"]["peak"])
+    if rank == 0 and not args.no_widened:
+        res["widened"] = {nm: run_widened(nm, min(args.steps, 200), max(args.warmup, 3)) for nm in WIDENED
+                          if nm != args.workload}
     if rank == 0:
         _, cb = oracle_step_time(synth.workload(args.workload), args.cpu_budget)
         res["cpu_baseline"] = cb
