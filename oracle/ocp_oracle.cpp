@@ -72,6 +72,10 @@ inline Sh operator/(Sh a, Sh b) {
 inline Sh& operator+=(Sh& a, Sh b) { a = a + b; return a; }
 inline Sh sin(Sh a) { return Sh(std::sin(a.v), std::fabs(std::cos(a.v)) * a.m + std::fabs(std::sin(a.v))); }
 inline Sh cos(Sh a) { return Sh(std::cos(a.v), std::fabs(std::sin(a.v)) * a.m + std::fabs(std::cos(a.v))); }
+inline Sh exp(Sh a) {
+  const double e = std::exp(a.v);
+  return Sh(e, e * a.m + e);
+}
 inline Sh tan(Sh a) {
   const double t = std::tan(a.v);
   return Sh(t, (1.0 + t * t) * a.m + std::fabs(t));
@@ -103,7 +107,7 @@ struct Neumaier {
 // ---------------------------------------------------------------------------------------
 // Problem description (mirrored by a ctypes Structure in oracle.py)
 // ---------------------------------------------------------------------------------------
-enum { M_VDP = 1, M_CARTPOLE = 2, M_HEAT = 3, M_DINT = 4, M_QUAD = 5 };
+enum { M_VDP = 1, M_CARTPOLE = 2, M_HEAT = 3, M_DINT = 4, M_QUAD = 5, M_GODDARD = 6 };
 
 struct Prob {
   int32_t model, nx, nu, has_final;
@@ -120,6 +124,14 @@ struct Prob {
   const double* xslope;
   const double* xamp;
   const double* xfreq;
+  // free final time: the horizon tf is an unknown appended to x (h = tf / N); T is unused
+  int32_t free_tf;
+  // final rows X_{N,k} for the nfin components fin_comp[] (ascending); when has_final is set
+  // and fin_comp is null, every component has a final row
+  int32_t nfin;
+  const int32_t* fin_comp;
+  // linear terminal (Mayer) cost sum_k mayer_k X_{N,k} added to the objective (nullable, nx)
+  const double* mayer;
 };
 
 template <class S> struct JEnt { int k, v; S val; };      // d f_k / d z_v
@@ -279,6 +291,50 @@ template <class S> void dint_jac(std::vector<JEnt<S>>& e) {
   e.push_back({1, 2, S(1.0)});
 }
 
+// Goddard rocket (paper appendix, the first benchmark problem): state (r, v, m) = altitude,
+// speed and mass, control u = normalised thrust; p = (Cd, beta, Tmax, b):
+//   r' = v,
+//   v' = -Cd v^2 exp(-beta (r - 1)) / m - 1 / r^2 + u Tmax / m,
+//   m' = -b Tmax u.
+// With E = exp(-beta (r - 1)) and D = Cd v^2 E / m (the drag term), dD/dr = -beta D,
+// dD/dv = 2 Cd v E / m, dD/dm = -D / m; so dv'/dm = D / m - u Tmax / m^2 and
+// d2v'/dm2 = 2 (u Tmax / m - D) / m^2.
+template <class S> void god_f(const S* p, const S* z, S* f) {
+  using std::exp;
+  const S Cd = p[0], beta = p[1], Tmax = p[2], b = p[3];
+  const S r = z[0], v = z[1], m = z[2], u = z[3];
+  f[0] = v;
+  f[1] = S(0.0) - Cd * v * v * exp(S(0.0) - beta * (r - S(1.0))) / m - S(1.0) / (r * r) + u * Tmax / m;
+  f[2] = S(0.0) - b * Tmax * u;
+}
+template <class S> void god_jac(const S* p, const S* z, std::vector<JEnt<S>>& e) {
+  using std::exp;
+  const S Cd = p[0], beta = p[1], Tmax = p[2], b = p[3];
+  const S r = z[0], v = z[1], m = z[2], u = z[3];
+  const S E = exp(S(0.0) - beta * (r - S(1.0)));
+  const S D = Cd * v * v * E / m;
+  e.push_back({0, 1, S(1.0)});
+  e.push_back({1, 0, beta * D + S(2.0) / (r * r * r)});
+  e.push_back({1, 1, S(0.0) - S(2.0) * Cd * v * E / m});
+  e.push_back({1, 2, (D - u * Tmax / m) / m});
+  e.push_back({1, 3, Tmax / m});
+  e.push_back({2, 3, S(0.0) - b * Tmax});
+}
+template <class S> void god_hess(const S* p, const S* z, std::vector<HEnt<S>>& e) {
+  using std::exp;
+  const S Cd = p[0], beta = p[1], Tmax = p[2];
+  const S r = z[0], v = z[1], m = z[2], u = z[3];
+  const S E = exp(S(0.0) - beta * (r - S(1.0)));
+  const S D = Cd * v * v * E / m;
+  e.push_back({1, 0, 0, S(0.0) - beta * beta * D - S(6.0) / (r * r * r * r)});
+  e.push_back({1, 1, 0, S(2.0) * beta * Cd * v * E / m});
+  e.push_back({1, 1, 1, S(0.0) - S(2.0) * Cd * E / m});
+  e.push_back({1, 2, 0, S(0.0) - beta * D / m});
+  e.push_back({1, 2, 1, S(2.0) * Cd * v * E / (m * m)});
+  e.push_back({1, 2, 2, S(2.0) * (u * Tmax / m - D) / (m * m)});
+  e.push_back({1, 3, 2, S(0.0) - Tmax / (m * m)});
+}
+
 // Quadrotor (paper appendix, the second benchmark problem).  States x1..x9: positions
 // x1, x3, x5 with velocities x2, x4, x6 and the attitude angles x7, x8, x9; controls u1 (the
 // thrust per unit mass) and u2, u3, u4 (angular rate inputs); p = (g).
@@ -417,6 +473,7 @@ template <class S> void model_f(const Prob& P, const S* p, const S* z, S* f) {
     case M_HEAT: heat_f(P.nx, z, f); break;
     case M_DINT: dint_f(z, f); break;
     case M_QUAD: quad_f(p, z, f); break;
+    case M_GODDARD: god_f(p, z, f); break;
   }
 }
 template <class S> void model_jac(const Prob& P, const S* p, const S* z, std::vector<JEnt<S>>& e) {
@@ -426,6 +483,7 @@ template <class S> void model_jac(const Prob& P, const S* p, const S* z, std::ve
     case M_HEAT: heat_jac(P.nx, z, e); break;
     case M_DINT: dint_jac(e); break;
     case M_QUAD: quad_jac(z, e); break;
+    case M_GODDARD: god_jac(p, z, e); break;
   }
 }
 template <class S> void model_hess(const Prob& P, const S* p, const S* z, std::vector<HEnt<S>>& e) {
@@ -435,6 +493,7 @@ template <class S> void model_hess(const Prob& P, const S* p, const S* z, std::v
     case M_HEAT: heat_hess(P.nx, z, e); break;
     case M_DINT: break;
     case M_QUAD: quad_hess(z, e); break;
+    case M_GODDARD: god_hess(p, z, e); break;
   }
 }
 
@@ -466,11 +525,17 @@ inline double cost_hess_diag(const Prob& P, int a) {  // d2 f0 / d z_a^2 (consta
 // ---------------------------------------------------------------------------------------
 struct Layout {
   int nx, nu, nz;
-  int64_t N, n, m, nb;
+  int64_t N, n, m, nb, tau;   // tau: column of the free final time, or -1
+  std::vector<int> fin;       // components with a final row, ascending
   explicit Layout(const Prob& P) {
     nx = P.nx; nu = P.nu; nz = nx + nu; N = P.N;
-    n = (int64_t)nz * (N + 1);
-    nb = (int64_t)nx * (P.has_final ? 2 : 1);
+    if (P.has_final) {
+      if (P.fin_comp) fin.assign(P.fin_comp, P.fin_comp + P.nfin);
+      else for (int k = 0; k < nx; ++k) fin.push_back(k);
+    }
+    n = (int64_t)nz * (N + 1) + (P.free_tf ? 1 : 0);
+    tau = P.free_tf ? n - 1 : -1;
+    nb = (int64_t)nx + (int64_t)fin.size();
     m = nb + (int64_t)nx * N;
   }
   int64_t colX(int64_t j, int k) const { return k + (int64_t)nx * j; }
@@ -483,34 +548,46 @@ template <class S> void gather_node(const Layout& L, const S* x, int64_t j, S* z
   for (int v = 0; v < L.nz; ++v) z[v] = x[L.col(j, v)];
 }
 
-// node time t_j = j h on the uniform grid
+// step h = T / N, or tf / N with the free final time tf = x[tau]
+template <class S> S step_h(const Prob& P, const Layout& L, const S* x) {
+  if (L.tau >= 0) return x[L.tau] / S((double)P.N);
+  return S(P.T / (double)P.N);
+}
+
+// node time t_j = j h on the uniform grid (fixed horizon; the tracking reference needs it)
 inline double node_time(const Prob& P, int64_t j) { return (double)j * (P.T / (double)P.N); }
 
-inline double weight(const Prob& P, int64_t j) {
-  const double h = P.T / (double)P.N;
-  return (j == 0 || j == P.N) ? h / 2.0 : h;
+// trapezoidal weight w_j = h (interior) or h / 2 (end nodes), and omega_j = w_j / tf
+template <class S> S weight(const Prob& P, S h, int64_t j) {
+  return (j == 0 || j == P.N) ? h / S(2.0) : h;
+}
+inline double omega(const Prob& P, int64_t j) {
+  return (j == 0 || j == P.N) ? 1.0 / (2.0 * (double)P.N) : 1.0 / (double)P.N;
 }
 
 template <class S> void params_of(const Prob& P, S* p) { for (int i = 0; i < 8; ++i) p[i] = S(P.par[i]); }
 
-// Objective F = sum_j w_j f0(z_j)   (trapezoidal Lagrange cost)
+// Objective F = sum_j w_j f0(z_j) (trapezoidal Lagrange cost) + sum_k mayer_k X_{N,k}
 template <class S> S objective(const Prob& P, const S* x) {
   Layout L(P);
+  const S h = step_h(P, L, x);
   std::vector<S> z(L.nz);
   Neumaier<S> acc;
   for (int64_t j = 0; j <= L.N; ++j) {
     gather_node(L, x, j, z.data());
-    acc.add(S(weight(P, j)) * cost_f0(P, z.data(), node_time(P, j)));
+    acc.add(weight(P, h, j) * cost_f0(P, z.data(), node_time(P, j)));
   }
+  if (P.mayer)
+    for (int k = 0; k < L.nx; ++k) acc.add(S(P.mayer[k]) * x[L.colX(L.N, k)]);
   return acc.result();
 }
 
-// Constraints: boundary rows, then trapezoidal defects, component-major.
+// Constraints: initial rows, final rows, then trapezoidal defects, component-major.
 template <class S> void constraints(const Prob& P, const S* p, const S* x, S* c) {
   Layout L(P);
-  const double h = P.T / (double)P.N;
+  const S h = step_h(P, L, x);
   for (int k = 0; k < L.nx; ++k) c[k] = x[L.colX(0, k)];
-  if (P.has_final) for (int k = 0; k < L.nx; ++k) c[L.nx + k] = x[L.colX(L.N, k)];
+  for (size_t i = 0; i < L.fin.size(); ++i) c[L.nx + i] = x[L.colX(L.N, L.fin[i])];
   std::vector<S> f((size_t)L.nx * (L.N + 1)), z(L.nz);
   for (int64_t j = 0; j <= L.N; ++j) {
     gather_node(L, x, j, z.data());
@@ -519,19 +596,26 @@ template <class S> void constraints(const Prob& P, const S* p, const S* x, S* c)
   for (int k = 0; k < L.nx; ++k)
     for (int64_t j = 0; j < L.N; ++j) {
       const S fj = f[(size_t)L.nx * j + k], fj1 = f[(size_t)L.nx * (j + 1) + k];
-      c[L.defect_row(k, j)] = (x[L.colX(j + 1, k)] - x[L.colX(j, k)]) - S(h) * (fj + fj1) / S(2.0);
+      c[L.defect_row(k, j)] = (x[L.colX(j + 1, k)] - x[L.colX(j, k)]) - h * (fj + fj1) / S(2.0);
     }
 }
 
-// Gradient of F (node-local).
+// Gradient of F: node-local w_j grad f0, the Mayer weights at X_N, and with a free final time
+// dF/dtf = sum_j omega_j f0(z_j) (the Lagrange cost is linear in tf through w_j = tf omega_j).
 template <class S> void gradient(const Prob& P, const S* x, S* g) {
   Layout L(P);
+  const S h = step_h(P, L, x);
   std::vector<S> z(L.nz), gz(L.nz);
+  Neumaier<S> gt;
   for (int64_t j = 0; j <= L.N; ++j) {
     gather_node(L, x, j, z.data());
     cost_grad(P, z.data(), node_time(P, j), gz.data());
-    for (int v = 0; v < L.nz; ++v) g[L.col(j, v)] = S(weight(P, j)) * gz[v];
+    for (int v = 0; v < L.nz; ++v) g[L.col(j, v)] = weight(P, h, j) * gz[v];
+    if (L.tau >= 0) gt.add(S(omega(P, j)) * cost_f0(P, z.data(), node_time(P, j)));
   }
+  if (P.mayer)
+    for (int k = 0; k < L.nx; ++k) g[L.colX(L.N, k)] = g[L.colX(L.N, k)] + S(P.mayer[k]);
+  if (L.tau >= 0) g[L.tau] = gt.result();
 }
 
 // Jacobian in COO, one entry per structural nonzero, sorted by (row, col).
@@ -539,27 +623,31 @@ template <class S> struct Coo { std::vector<int64_t> row, col; std::vector<S> va
 
 template <class S> void jacobian(const Prob& P, const S* p, const S* x, Coo<S>& J) {
   Layout L(P);
-  const double h = P.T / (double)P.N;
-  // derivative entries of f at every node
+  const S h = step_h(P, L, x);
+  // derivative entries and values of f at every node
   std::vector<std::vector<JEnt<S>>> nodeJ((size_t)L.N + 1);
-  std::vector<S> z(L.nz);
+  std::vector<S> f((size_t)L.nx * (L.N + 1)), z(L.nz);
   for (int64_t j = 0; j <= L.N; ++j) {
     gather_node(L, x, j, z.data());
     model_jac(P, p, z.data(), nodeJ[j]);
+    model_f(P, p, z.data(), &f[(size_t)L.nx * j]);
   }
   auto emit = [&](int64_t r, int64_t c, S v) { J.row.push_back(r); J.col.push_back(c); J.val.push_back(v); };
   for (int k = 0; k < L.nx; ++k) emit(k, L.colX(0, k), S(1.0));
-  if (P.has_final) for (int k = 0; k < L.nx; ++k) emit(L.nx + k, L.colX(L.N, k), S(1.0));
+  for (size_t i = 0; i < L.fin.size(); ++i) emit(L.nx + (int64_t)i, L.colX(L.N, L.fin[i]), S(1.0));
   std::vector<std::pair<int64_t, S>> ent;
   for (int k = 0; k < L.nx; ++k)
     for (int64_t j = 0; j < L.N; ++j) {
       ent.clear();
       // d c_{k,j} / d z_j : -[v == x_k] - h (df_k/dz_v)(z_j) / 2
-      for (auto& e : nodeJ[j]) if (e.k == k) ent.push_back({L.col(j, e.v), S(0.0) - S(h) * e.val / S(2.0)});
+      for (auto& e : nodeJ[j]) if (e.k == k) ent.push_back({L.col(j, e.v), S(0.0) - h * e.val / S(2.0)});
       ent.push_back({L.colX(j, k), S(-1.0)});
       // d c_{k,j} / d z_{j+1} : +[v == x_k] - h (df_k/dz_v)(z_{j+1}) / 2
-      for (auto& e : nodeJ[j + 1]) if (e.k == k) ent.push_back({L.col(j + 1, e.v), S(0.0) - S(h) * e.val / S(2.0)});
+      for (auto& e : nodeJ[j + 1]) if (e.k == k) ent.push_back({L.col(j + 1, e.v), S(0.0) - h * e.val / S(2.0)});
       ent.push_back({L.colX(j + 1, k), S(1.0)});
+      // d c_{k,j} / d tf = -(f_k(z_j) + f_k(z_{j+1})) / (2N)
+      if (L.tau >= 0)
+        ent.push_back({L.tau, S(0.0) - (f[(size_t)L.nx * j + k] + f[(size_t)L.nx * (j + 1) + k]) / S(2.0 * (double)L.N)});
       std::stable_sort(ent.begin(), ent.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
       const int64_t r = L.defect_row(k, j);
       for (size_t i = 0; i < ent.size();) {
@@ -575,11 +663,16 @@ template <class S> void jacobian(const Prob& P, const S* p, const S* x, Coo<S>& 
 // Lagrangian Hessian sigma * Hess F + sum_r y_r Hess c_r, lower triangle, sorted by (row, col).
 // Boundary rows are linear.  The defect row (k, j) involves only z_j and z_{j+1}, so the
 // block of node j collects the rows (k, j-1) and (k, j), each through -h/2 Hess f_k(z_j).
+// With a free final time tf the last row couples tf to every node: d2 L / dtf dz_{j,v} =
+// sigma omega_j df0/dz_v - 1/(2N) sum_k ybar_{j,k} df_k/dz_v (c and F are linear in tf, so
+// there is no (tf, tf) entry); its structural columns are those of the model's Jacobian
+// entries and of the non-zero cost weights.
 template <class S> void hessian(const Prob& P, const S* p, const S* x, const S* y, S sigma, Coo<S>& H) {
   Layout L(P);
-  const double h = P.T / (double)P.N;
-  std::vector<S> z(L.nz);
+  const S h = step_h(P, L, x);
+  std::vector<S> z(L.nz), gz(L.nz);
   std::vector<HEnt<S>> he;
+  std::vector<JEnt<S>> je;
   struct Trip { int64_t r, c; S v; };
   std::vector<Trip> all;
   for (int64_t j = 0; j <= L.N; ++j) {
@@ -592,19 +685,35 @@ template <class S> void hessian(const Prob& P, const S* p, const S* x, const S* 
     for (auto& e : he) blk[{e.a, e.b}] = S(0.0);
     // sigma * w_j * Hess f0
     for (int a = 0; a < L.nz; ++a)
-      if (cost_hess_diag(P, a) != 0.0) blk[{a, a}] = blk[{a, a}] + sigma * S(weight(P, j)) * S(cost_hess_diag(P, a));
+      if (cost_hess_diag(P, a) != 0.0) blk[{a, a}] = blk[{a, a}] + sigma * weight(P, h, j) * S(cost_hess_diag(P, a));
     // sum over the defect rows that touch node j
     for (auto& e : he) {
       if (j >= 1) {
         const S yr = y[L.defect_row(e.k, j - 1)];
-        blk[{e.a, e.b}] = blk[{e.a, e.b}] + yr * (S(0.0) - S(h) * e.val / S(2.0));
+        blk[{e.a, e.b}] = blk[{e.a, e.b}] + yr * (S(0.0) - h * e.val / S(2.0));
       }
       if (j <= L.N - 1) {
         const S yr = y[L.defect_row(e.k, j)];
-        blk[{e.a, e.b}] = blk[{e.a, e.b}] + yr * (S(0.0) - S(h) * e.val / S(2.0));
+        blk[{e.a, e.b}] = blk[{e.a, e.b}] + yr * (S(0.0) - h * e.val / S(2.0));
       }
     }
     for (auto& kv : blk) all.push_back({L.col(j, kv.first.first), L.col(j, kv.first.second), kv.second});
+    if (L.tau >= 0) {
+      std::map<int, S> trow;
+      cost_grad(P, z.data(), node_time(P, j), gz.data());
+      for (int v = 0; v < L.nz; ++v)
+        if (cost_hess_diag(P, v) != 0.0) trow[v] = sigma * S(omega(P, j)) * gz[v];
+      je.clear();
+      model_jac(P, p, z.data(), je);
+      for (auto& e : je) {
+        S yb = S(0.0);
+        if (j >= 1) yb = yb + y[L.defect_row(e.k, j - 1)];
+        if (j <= L.N - 1) yb = yb + y[L.defect_row(e.k, j)];
+        if (!trow.count(e.v)) trow[e.v] = S(0.0);
+        trow[e.v] = trow[e.v] + yb * (S(0.0) - e.val / S(2.0 * (double)L.N));
+      }
+      for (auto& kv : trow) all.push_back({L.tau, L.col(j, kv.first), kv.second});
+    }
   }
   std::stable_sort(all.begin(), all.end(), [](const Trip& a, const Trip& b) {
     return a.r != b.r ? a.r < b.r : a.c < b.c;
@@ -632,7 +741,7 @@ template <class S> void coo_symv_lower(const Coo<S>& A, const S* v, S* out, int6
 // (dc/dp0)^T w = sum over defect rows of w_r * ( -h (df_k/dp0(z_j) + df_k/dp0(z_{j+1})) / 2 )
 template <class S> S dpar_vjp(const Prob& P, const S* p, const S* x, const S* w) {
   Layout L(P);
-  const double h = P.T / (double)P.N;
+  const S h = step_h(P, L, x);
   std::vector<S> d((size_t)L.nx * (L.N + 1)), z(L.nz);
   for (int64_t j = 0; j <= L.N; ++j) {
     gather_node(L, x, j, z.data());
@@ -641,7 +750,7 @@ template <class S> S dpar_vjp(const Prob& P, const S* p, const S* x, const S* w)
   Neumaier<S> acc;
   for (int k = 0; k < L.nx; ++k)
     for (int64_t j = 0; j < L.N; ++j) {
-      const S dc = S(0.0) - S(h) * (d[(size_t)L.nx * j + k] + d[(size_t)L.nx * (j + 1) + k]) / S(2.0);
+      const S dc = S(0.0) - h * (d[(size_t)L.nx * j + k] + d[(size_t)L.nx * (j + 1) + k]) / S(2.0);
       acc.add(w[L.defect_row(k, j)] * dc);
     }
   return acc.result();
@@ -660,12 +769,20 @@ template <class S> void lagrangian_grad(const Prob& P, const S* p, const S* x, c
 
 int check(const Prob& P) {
   if (P.N < 1 || !(P.T > 0.0)) return 2;
+  // the tracking reference is tabulated at t_j = j T / N: not with a free final time
+  if (P.free_tf && (P.xslope || P.xamp)) return 2;
+  if (P.has_final && P.fin_comp) {
+    if (P.nfin < 1 || P.nfin > P.nx) return 2;
+    for (int i = 0; i < P.nfin; ++i)
+      if (P.fin_comp[i] < 0 || P.fin_comp[i] >= P.nx || (i > 0 && P.fin_comp[i] <= P.fin_comp[i - 1])) return 2;
+  }
   switch (P.model) {
     case M_VDP: return (P.nx == 2 && P.nu == 1) ? 0 : 2;
     case M_CARTPOLE: return (P.nx == 4 && P.nu == 1) ? 0 : 2;
     case M_HEAT: return (P.nx >= 2 && P.nu == 1 && (int)P.par[0] == P.nx) ? 0 : 2;
     case M_DINT: return (P.nx == 2 && P.nu == 1) ? 0 : 2;
     case M_QUAD: return (P.nx == 9 && P.nu == 4) ? 0 : 2;
+    case M_GODDARD: return (P.nx == 3 && P.nu == 1) ? 0 : 2;
     default: return 6;
   }
 }
@@ -703,13 +820,21 @@ int orc_dims(const Prob* P, int64_t* n, int64_t* m, int64_t* nnzj, int64_t* nnzh
     std::sort(cols.begin(), cols.end());
     perrow += 2 * (int64_t)(std::unique(cols.begin(), cols.end()) - cols.begin());
   }
-  *nnzj = L.nb + perrow * L.N;
+  // a free final time adds one entry (the tf column) to every defect row
+  *nnzj = L.nb + perrow * L.N + (L.tau >= 0 ? (int64_t)L.nx * L.N : 0);
   std::vector<HEnt<double>> he; model_hess(*P, p.data(), z.data(), he);
   std::vector<std::pair<int, int>> keys;
   for (int a = 0; a < L.nz; ++a) if (cost_hess_diag(*P, a) != 0.0) keys.push_back({a, a});
   for (auto& e : he) keys.push_back({e.a, e.b});
   std::sort(keys.begin(), keys.end());
   *nnzh = (int64_t)(std::unique(keys.begin(), keys.end()) - keys.begin()) * (L.N + 1);
+  if (L.tau >= 0) {  // the tf row: model Jacobian columns and cost columns of every node
+    std::vector<int> tc;
+    for (auto& e : je) tc.push_back(e.v);
+    for (int a = 0; a < L.nz; ++a) if (cost_hess_diag(*P, a) != 0.0) tc.push_back(a);
+    std::sort(tc.begin(), tc.end());
+    *nnzh += (int64_t)(std::unique(tc.begin(), tc.end()) - tc.begin()) * (L.N + 1);
+  }
   return 0;
 }
 

@@ -12,14 +12,15 @@ import numpy as np
 
 from . import build as _build
 
-_MODEL_ID = {"vdp": 1, "cartpole": 2, "heat": 3, "dint": 4, "quadrotor": 5}
+_MODEL_ID = {"vdp": 1, "cartpole": 2, "heat": 3, "dint": 4, "quadrotor": 5, "goddard": 6}
 
 
 class _Prob(C.Structure):
     _fields_ = [("model", C.c_int32), ("nx", C.c_int32), ("nu", C.c_int32), ("has_final", C.c_int32),
                 ("N", C.c_int64), ("T", C.c_double), ("par", C.c_double * 8), ("npar", C.c_int32),
                 ("pad", C.c_int32), ("q", C.c_void_p), ("r", C.c_void_p), ("xref", C.c_void_p),
-                ("uref", C.c_void_p), ("xslope", C.c_void_p), ("xamp", C.c_void_p), ("xfreq", C.c_void_p)]
+                ("uref", C.c_void_p), ("xslope", C.c_void_p), ("xamp", C.c_void_p), ("xfreq", C.c_void_p),
+                ("free_tf", C.c_int32), ("nfin", C.c_int32), ("fin_comp", C.c_void_p), ("mayer", C.c_void_p)]
 
 
 _lib = None
@@ -62,6 +63,15 @@ class Problem:
         p.q, p.r = _ptr(self._q), _ptr(self._r)
         p.xref, p.uref = _ptr(self._xref), _ptr(self._uref)
         p.xslope, p.xamp, p.xfreq = (_ptr(a) for a in self._trk)
+        # free final time, final rows on a subset of the components, linear terminal cost
+        p.free_tf = 1 if w.get("free_tf") else 0
+        self._fin = None
+        if w.get("xf_comp") is not None:
+            self._fin = np.ascontiguousarray(w["xf_comp"], dtype=np.int32)
+            p.has_final, p.nfin = 1, len(self._fin)
+            p.fin_comp = _ptr(self._fin)
+        self._mayer = None if w.get("mayer") is None else np.ascontiguousarray(w["mayer"], dtype=np.float64)
+        p.mayer = _ptr(self._mayer)
         self.s = p
         n, m, nj, nh = (C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64())
         st = lib().orc_dims(C.byref(p), C.byref(n), C.byref(m), C.byref(nj), C.byref(nh))

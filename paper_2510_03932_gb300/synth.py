@@ -57,17 +57,30 @@ DIST = {
     "heat": dict(x=(0.0, 1.0), u=(-1.0, 1.0)),
     "dint": dict(x=(-1.0, 1.0), u=(-1.0, 1.0)),
     "quadrotor": dict(x=(-1.0, 1.0), u=(-10.0, 10.0)),
+    # Goddard: per-component ranges around the flight envelope (altitude r >= 1 with the drag
+    # factor exp(-500 (r - 1)) finite, speed in [0, vmax], mass between the final and initial
+    # mass), normalised thrust in [0, 1], free final time near the known optimum (~0.2)
+    "goddard": dict(xc=[(1.0, 1.02), (0.0, 0.1), (0.6, 1.0)], u=(0.0, 1.0), tf=(0.15, 0.25)),
 }
 
 
 def draw_instance(seed: int, kind: str, nx: int, nu: int, N: int, m: int,
-                  stream: Stream | None = None) -> dict:
-    """x = [X (node-major, nx per node); U (nu per node)], y ~ N(0,1), vn ~ U(-1,1), vm ~ N(0,1)."""
+                  stream: Stream | None = None, free_tf: bool = False) -> dict:
+    """x = [X (node-major, nx per node); U (nu per node) (; tf)], y ~ N(0,1), vn ~ U(-1,1),
+    vm ~ N(0,1).  X is uniform on one range, or on a range per state component ("xc")."""
     s = stream if stream is not None else Stream(seed)
     d = DIST[kind]
-    X = s.uniform(nx * (N + 1), *d["x"])
+    if "xc" in d:
+        lo = np.array([r[0] for r in d["xc"]])
+        hi = np.array([r[1] for r in d["xc"]])
+        X = (lo + (hi - lo) * s.uniform(nx * (N + 1)).reshape(N + 1, nx)).ravel()
+    else:
+        X = s.uniform(nx * (N + 1), *d["x"])
     U = s.uniform(nu * (N + 1), *d["u"])
-    x = np.concatenate([X, U])
+    parts = [X, U]
+    if free_tf:
+        parts.append(s.uniform(1, *d["tf"]))
+    x = np.concatenate(parts)
     y = s.normal(m)
     vn = s.uniform(x.size, -1.0, 1.0)
     vm = s.normal(m)
@@ -125,6 +138,17 @@ def workload(name: str) -> dict:
                     xfreq=[2.0 * np.pi / T, 0.0, 4.0 * np.pi / T, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0],
                     x0=[0.0] * 9, xf=None, seed={1000: 1007, 100_000: 1008, 1_000_000: 1009}[N],
                     sigma=1.0, dist="quadrotor")
+    if name.startswith("goddard_n"):  # the paper's Goddard rocket (appendix), free final time
+        N = {"goddard_n1e3": 1000, "goddard_n1e5": 100_000, "goddard_n1e6": 1_000_000}[name]
+        inf = float("inf")
+        # max r(tf)  s.t.  x(0) = (r0, v0, m0) = (1, 0, 1),  m(tf) = mf = 0.6,  0 <= u <= 1,
+        # r >= r0,  0 <= v <= vmax = 0.1;  Cd = 310, beta = 500, Tmax = 3.5, b = 2
+        return dict(name=name, model="goddard", nx=3, nu=1, N=N, T=1.0, params=[310.0, 500.0, 3.5, 2.0],
+                    q=[0.0] * 3, r=[0.0], xref=[0.0] * 3, uref=[0.0], x0=[1.0, 0.0, 1.0],
+                    xf=[0.6], xf_comp=[2], mayer=[-1.0, 0.0, 0.0], free_tf=True,
+                    bounds=dict(xlo=[1.0, 0.0, -inf], xhi=[inf, 0.1, inf], ulo=[0.0], uhi=[1.0],
+                                tflo=0.0, tfhi=inf),
+                    seed={1000: 1010, 100_000: 1011, 1_000_000: 1012}[N], sigma=1.0, dist="goddard")
     raise KeyError(name)
 
 
@@ -135,15 +159,24 @@ def with_horizon(w: dict, N: int) -> dict:
     return w
 
 
+def final_rows(w: dict) -> int:
+    """Number of final rows X_{N,k}: the listed components, or all when xf is given alone."""
+    if w.get("xf_comp") is not None:
+        return len(w["xf_comp"])
+    return w["nx"] if w.get("xf") is not None else 0
+
+
 def dims(w: dict):
-    """(n, m) of the transcription: n = (nx+nu)(N+1); m = nx (+nx final rows) + nx N."""
-    nb = w["nx"] * (2 if w.get("xf") is not None else 1)
-    return (w["nx"] + w["nu"]) * (w["N"] + 1), nb + w["nx"] * w["N"]
+    """(n, m) of the transcription: n = (nx+nu)(N+1) (+1 for a free final time);
+    m = nx + final rows + nx N."""
+    n = (w["nx"] + w["nu"]) * (w["N"] + 1) + (1 if w.get("free_tf") else 0)
+    return n, w["nx"] + final_rows(w) + w["nx"] * w["N"]
 
 
 def draw(w: dict, seed: int | None = None) -> dict:
     n, m = dims(w)
-    return draw_instance(w["seed"] if seed is None else seed, w["dist"], w["nx"], w["nu"], w["N"], m)
+    return draw_instance(w["seed"] if seed is None else seed, w["dist"], w["nx"], w["nu"], w["N"], m,
+                         free_tf=bool(w.get("free_tf")))
 
 
 def batch_workloads(count=256, nmin=500, nmax=50000, seed=1004):

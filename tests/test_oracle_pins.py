@@ -14,7 +14,7 @@ from conftest import read_golden
 from oracle import oracle as O
 from paper_2510_03932_gb300 import synth
 
-MODELS = ["vdp_n1e3", "cartpole_n1e5", "heat_n2e4", "dint", "quadrotor_n1e3"]
+MODELS = ["vdp_n1e3", "cartpole_n1e5", "heat_n2e4", "dint", "quadrotor_n1e3", "goddard_n1e3"]
 
 
 def small(name, N):
@@ -24,16 +24,25 @@ def small(name, N):
 def rand_point(w, rng):
     n, m = synth.dims(w)
     d = synth.DIST[w["dist"]]
-    nx1 = w["nx"] * (w["N"] + 1)
-    x = np.concatenate([rng.uniform(*d["x"], nx1), rng.uniform(*d["u"], n - nx1)])
-    return x, rng.standard_normal(m)
+    N1 = w["N"] + 1
+    if "xc" in d:
+        X = np.concatenate([rng.uniform(lo, hi, N1)[:, None] for lo, hi in d["xc"]], axis=1).ravel()
+    else:
+        X = rng.uniform(*d["x"], w["nx"] * N1)
+    parts = [X, rng.uniform(*d["u"], w["nu"] * N1)]
+    if w.get("free_tf"):
+        parts.append(rng.uniform(*d["tf"], 1))
+    return np.concatenate(parts), rng.standard_normal(m)
 
 
 # ---------------------------------------------------------------------------------------
 # Counts and structure
 # ---------------------------------------------------------------------------------------
 # per node: (J entries of one defect-row set, H entries of one node block)
-NODE_COUNTS = {"vdp": (10, 4), "cartpole": (22, 7), "heat": (382, 65), "dint": (8, 1), "quadrotor": (68, 20)}
+NODE_COUNTS = {"vdp": (10, 4), "cartpole": (22, 7), "heat": (382, 65), "dint": (8, 1), "quadrotor": (68, 20),
+               # Goddard: rows r {r, v | r, v | tf}, v {r, v, m | r, v, m | u | u | tf}, m {m | m | u | u | tf};
+               # Hessian block (r,r) (v,r) (v,v) (m,r) (m,v) (m,m) (u,m) plus the tf row on r, v, m, u
+               "goddard": (19, 11)}
 
 
 @pytest.mark.parametrize("name", MODELS)
@@ -42,9 +51,9 @@ def test_counts_closed_form(name, N):
     w = small(name, N)
     P = O.Problem(w)
     nx, nu = w["nx"], w["nu"]
-    nb = nx * (2 if w["xf"] is not None else 1)
+    nb = nx + synth.final_rows(w)
     jn, hn = NODE_COUNTS[w["model"]]
-    assert P.n == (nx + nu) * (N + 1)
+    assert P.n == (nx + nu) * (N + 1) + (1 if w.get("free_tf") else 0)
     assert P.m == nb + nx * N
     assert P.nnzj == nb + jn * N
     assert P.nnzh == hn * (N + 1)
@@ -355,6 +364,69 @@ def test_quadrotor_tracking_cost_closed_form(N):
     X[:, 0], X[:, 2], X[:, 4] = np.sin(2 * np.pi * t), 2 * np.sin(4 * np.pi * t), 2 * t
     ev = O.evaluate(P, np.concatenate([X.ravel(), np.zeros(4 * (N + 1))]), np.zeros(P.m), 1.0)
     assert np.max(np.abs(ev["g"])) < 1e-15 and abs(ev["f"]) < 1e-30
+
+
+def test_goddard_gravity_and_energy_balance():
+    """Without speed the only acceleration is the inverse-square gravity -1/r^2 (normalised
+    units) plus thrust; along any state the specific energy e = v^2/2 - 1/r changes at the
+    rate of thrust power minus drag power per unit mass: de/dt = v (u Tmax - Cd v^2 exp(-beta
+    (r - 1))) / m.  The mass flow is -b Tmax u.  Together these fix every term of v'."""
+    w = small("goddard_n1e3", 1)
+    P = O.Problem(w)
+    Cd, beta, Tmax, b = w["params"]
+    rng = np.random.default_rng(29)
+    for _ in range(50):
+        r, v, m, u = rng.uniform(1.0, 1.03), rng.uniform(-0.2, 0.2), rng.uniform(0.5, 1.0), rng.uniform(0, 1)
+        f = O.model_f(P, [r, 0.0, m, u])
+        assert abs(f[1] - (u * Tmax / m - 1.0 / r**2)) < 1e-15 * 8
+        f = O.model_f(P, [r, v, m, u])
+        assert f[0] == v and f[2] == -b * Tmax * u
+        de = v * f[1] + f[0] / r**2
+        expect = v * (u * Tmax - Cd * v * v * np.exp(-beta * (r - 1.0))) / m
+        assert abs(de - expect) < 1e-13 * (1 + abs(v) * (u * Tmax + Cd * v * v) / m)
+
+
+def test_free_final_time_reduces_to_fixed_horizon():
+    """With tf appended to x and set to T, the residual, the Jacobian entries on X and U, the
+    node Hessian blocks and the objective equal those of the fixed-horizon transcription (which
+    the other pins fix); the Lagrange cost is linear in tf, so dF/dtf tf = F."""
+    wf = dict(small("vdp_n1e3", 7), T=2.5)
+    wt = dict(wf, free_tf=True, T=1.0)
+    Pf, Pt = O.Problem(wf), O.Problem(wt)
+    assert Pt.n == Pf.n + 1 and Pt.m == Pf.m
+    rng = np.random.default_rng(31)
+    x, y = rand_point(wf, rng)
+    xt = np.concatenate([x, [2.5]])
+    ef, et = O.evaluate(Pf, x, y, 0.8), O.evaluate(Pt, xt, y, 0.8)
+    np.testing.assert_allclose(et["c"], ef["c"], rtol=1e-15, atol=1e-16)
+    assert abs(et["f"] - ef["f"]) <= 1e-15 * abs(ef["f"])
+    np.testing.assert_allclose(et["g"][:-1], ef["g"], rtol=1e-15, atol=1e-16)
+    assert abs(et["g"][-1] * 2.5 - ef["f"]) <= 1e-13 * abs(ef["f"])
+    jr, jc = O.jac_structure(Pt)
+    keep = jc != Pt.n - 1
+    np.testing.assert_allclose(et["jac"][keep], ef["jac"], rtol=1e-15, atol=1e-16)
+    hr, hc = O.hess_structure(Pt)
+    keep = hr != Pt.n - 1
+    np.testing.assert_allclose(et["hess"][keep], ef["hess"], rtol=1e-15, atol=1e-16)
+
+
+def test_goddard_mayer_objective_and_final_row():
+    """max r(tf) is the linear terminal cost F = -r_N: gradient -1 on r_N and nothing else
+    (no running cost, so dF/dtf = 0 and the Hessian has no cost entries); the single final row
+    is m_N with a unit Jacobian entry."""
+    w = small("goddard_n1e3", 6)
+    P = O.Problem(w)
+    rng = np.random.default_rng(37)
+    x, y = rand_point(w, rng)
+    ev = O.evaluate(P, x, np.zeros(P.m), 1.0)
+    rN = 3 * 6
+    assert ev["f"] == -x[rN]
+    g = np.zeros(P.n); g[rN] = -1.0
+    assert np.array_equal(ev["g"], g)
+    assert np.all(ev["hess"] == 0.0)
+    assert ev["c"][3] == x[3 * 6 + 2]
+    jr, jc = O.jac_structure(P)
+    assert jr[3] == 3 and jc[3] == 3 * 6 + 2 and ev["jac"][3] == 1.0
 
 
 # ---------------------------------------------------------------------------------------
