@@ -77,14 +77,17 @@ def _counts(w):
 # counted from the kernel source and equal to ncu's sm__sass_thread_inst_executed_op_{dfma,dadd,
 # dmul} counts divided by N+1 (the objective's tile reduction adds 1.5 per node).  Quadrotor:
 # ncu's sm__inst_executed_pipe_fp64 x 32 / (N+1) at N = 1e5, which includes the FP64 work of
-# the three sincos calls and the 1/cos division (about 130 per node).
+# the three sincos calls and the 1/cos division (about 130 per node).  Goddard: the same
+# measurement (exp and the divisions 1/m, 1/r included), free final time.
 FP64_OPS_PER_NODE = {("vdp", "eval_all"): 26.5, ("vdp", "jh"): 10.0, ("vdp", "jprod"): 14.0,
                      ("vdp", "jtprod"): 12.0, ("vdp", "hprod"): 11.0, ("vdp", "step"): 51.6,
                      ("quadrotor", "eval_all"): 275.4, ("quadrotor", "jh"): 199.1, ("quadrotor", "jprod"): 180.9,
-                     ("quadrotor", "jtprod"): 172.1, ("quadrotor", "hprod"): 214.1, ("quadrotor", "step"): 432.9}
+                     ("quadrotor", "jtprod"): 172.1, ("quadrotor", "hprod"): 214.1, ("quadrotor", "step"): 432.9,
+                     ("goddard", "eval_all"): 114.5, ("goddard", "jh"): 101.4, ("goddard", "jprod"): 78.3,
+                     ("goddard", "jtprod"): 81.4, ("goddard", "hprod"): 107.5, ("goddard", "step"): 171.8}
 # Rows of the paper's workloads beyond the headline problem, measured the same way (fused
 # step with an L2 flush between steps) and reported under "widened".
-WIDENED = ["quadrotor_n1e6"]
+WIDENED = ["quadrotor_n1e6", "goddard_n1e6"]
 # DRAM bytes (read + write) of one launch of the fused step at the bench workload, from an ncu
 # capture of the same kernel version (dram__bytes_read.sum + dram__bytes_write.sum; writes
 # still dirty in L2 when the kernel ends are not counted).  Remove an entry when its kernel
@@ -518,7 +521,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-forms", action="store_true", help="skip the batched and differentiation forms")
-    ap.add_argument("--no-widened", action="store_true", help="skip the further workloads (quadrotor)")
+    ap.add_argument("--no-widened", action="store_true", help="skip the further workloads (quadrotor, Goddard)")
     ap.add_argument("--profile-kernel", default=None,
                     choices=["eval_all", "jh", "jprod", "jtprod", "hprod", "step", "all"],
                     help="only launch this call warmup+steps times (for ncu captures)")

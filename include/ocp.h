@@ -8,10 +8,12 @@
  *
  * Unknown vector (length n = (nx+nu)(N+1); Sec. 3 unknowns, Sec. 5 variable layout):
  *     x = [ X_0, X_1, ..., X_N, U_0, U_1, ..., U_N ],   X_j in R^nx, U_j in R^nu,
- *   i.e. X_{j,k} at index k + nx*j and U_{j,i} at index nx*(N+1) + i + nu*j (0-based).
+ *   i.e. X_{j,k} at index k + nx*j and U_{j,i} at index nx*(N+1) + i + nu*j (0-based);
+ *   with a free final time tf is appended (n grows by one, h = tf / N).
  * Constraints (length m = nb + nx*N, declaration order of Sec. 5):
  *     rows 0..nx-1         : X_{0,k}                (the expression; bounds are x0)
- *     rows nx..2nx-1       : X_{N,k}                (only when a final state was set)
+ *     rows nx..nb-1        : X_{N,k}                (final rows: every component, or those set
+ *                                                   by ocp_set_final_components; nb = nx + count)
  *     row  nb + k*N + j    : (X_{j+1,k} - X_{j,k}) - h/2 (f_k(z_j) + f_k(z_{j+1})),  z_j = (X_j, U_j)
  * Objective (Sec. 5 trapezoidal cost): F = sum_j w_j f0(z_j), w_0 = w_N = h/2, else w_j = h.
  * Lagrangian Hessian: H = sigma * Hess F + sum_r y_r Hess c_r (lower triangle stored).
@@ -66,13 +68,22 @@ typedef enum {
  *            x1' = x2, x3' = x4, x5' = x6,
  *            x2' = u1 (c7 s8 c9 + s7 s9),  x4' = u1 (c7 s8 s9 - s7 c9),  x6' = u1 c7 c8 - g,
  *            x7' = (u2 c7 + u3 s7) / c8,  x8' = u3 c7 - u2 s7,  x9' = (u2 c7 + u3 s7) tan x8 + u4.
- *            Values are finite for |x8| < pi/2; the kernels do not check the singularity. */
+ *            Values are finite for |x8| < pi/2; the kernels do not check the singularity.
+ *   GODDARD  (nx=3, nu=1): Cd, beta, Tmax, b.  The Goddard rocket of the paper's appendix:
+ *            state (r, v, m) = altitude, speed, mass; u = normalised thrust:
+ *            r' = v,  v' = -Cd v^2 exp(-beta (r - 1)) / m - 1/r^2 + u Tmax / m,  m' = -b Tmax u.
+ *            The objective is a terminal cost (ocp_set_terminal_cost; q and r must be zero);
+ *            the final time may be free (ocp_set_free_final_time) and the final condition may
+ *            cover part of the state (ocp_set_final_components).  Its kernels are dedicated
+ *            (tf couples every node); node ranges, the batched form, the differentiation
+ *            form and ocp_eval_obj_noalloc are not provided for it (OCP_EMODEL). */
 enum {
   OCP_MODEL_VDP = 1,
   OCP_MODEL_CARTPOLE = 2,
   OCP_MODEL_HEAT1D = 3,
   OCP_MODEL_DINT = 4,
-  OCP_MODEL_QUADROTOR = 5
+  OCP_MODEL_QUADROTOR = 5,
+  OCP_MODEL_GODDARD = 6
 };
 
 /* Running cost kinds.  DIAG_QUADRATIC: f0 = sum_k q_k (x_k - xref_k)^2 + sum_i r_i (u_i - uref_i)^2.
@@ -111,11 +122,38 @@ ocp_status ocp_set_boundary(ocp_t* h, const double* x0, const double* xf);
  * HEAT1D, OCP_EINVAL for non-finite coefficients, OCP_ENOMEM / OCP_ECUDA. */
 ocp_status ocp_set_tracking(ocp_t* h, const double* xslope, const double* xamp, const double* xfreq);
 
+/* Free final time (Goddard; paper appendix "tf in R, variable"): enable != 0 appends tf to the
+ * unknowns (n grows by one, tf = x[n-1]) and the grid becomes t_j = j tf / N; T of ocp_create
+ * is then unused.  Every defect row gains its tf entry -(f_k(z_j) + f_k(z_{j+1})) / (2N) as its
+ * last (largest-column) entry; the Hessian gains the tf row (row n-1, after every other row)
+ * with the entries -(1/(2N)) sum_k ybar_{j,k} df_k/dz_{j,v} on the state columns of every
+ * node (node-major), then on the control columns (no (tf, tf) entry: c and F are linear in
+ * tf).  J^T w and H v get their tf component as a deterministic sum over the nodes.
+ * Rebuilds the pattern (n, nnz_J, nnz_H change).  Other models: OCP_EMODEL. */
+ocp_status ocp_set_free_final_time(ocp_t* h, int enable);
+
+/* Final rows on part of the state (Goddard: m(tf) = mf): rows nx..nx+count-1 are X_{N,comps[i]}
+ * with bounds values[i]; comps ascending state indices (host arrays).  count == 0 removes the
+ * final rows; count == nx is ocp_set_boundary's full final state.  Rebuilds the pattern.
+ * Errors: OCP_EINVAL (bad indices), OCP_EMODEL (models other than Goddard: use
+ * ocp_set_boundary). */
+ocp_status ocp_set_final_components(ocp_t* h, int count, const int32_t* comps, const double* values);
+
+/* Terminal (Mayer) cost added to the objective: F += sum_k mayer_k X_{N,k} (host array of nx;
+ * NULL removes it).  Goddard "r(tf) -> max" is mayer = (-1, 0, 0).  Other models: OCP_EMODEL. */
+ocp_status ocp_set_terminal_cost(ocp_t* h, const double* mayer);
+
+/* Variable bounds reported by ocp_bounds (host arrays of nx / nu, NULL = unbounded; tflo/tfhi
+ * bound the free final time).  They do not enter any evaluation. */
+ocp_status ocp_set_variable_bounds(ocp_t* h, const double* xlo, const double* xhi, const double* ulo,
+                                   const double* uhi, double tflo, double tfhi);
+
 /* Sizes: n variables, m constraints, Jacobian and (lower) Hessian nonzeros.  Host outputs. */
 ocp_status ocp_dims(const ocp_t* h, int64_t* n, int64_t* m, int64_t* nnzj, int64_t* nnzh);
 
-/* Bounds (HOST arrays): lvar/uvar = -inf/+inf (the models carry no variable bounds),
- * lcon = ucon = [x0; xf; 0 for every defect].  Any pointer may be NULL. */
+/* Bounds (HOST arrays): lvar/uvar = the variable bounds of ocp_set_variable_bounds (default
+ * -inf/+inf; the free final time last), lcon = ucon = [x0; final values; 0 for every defect].
+ * Any pointer may be NULL. */
 ocp_status ocp_bounds(const ocp_t* h, double* lvar, double* uvar, double* lcon, double* ucon);
 
 /* Objective F(x) (Sec. 5 trapezoidal cost) written to the device scalar f. */

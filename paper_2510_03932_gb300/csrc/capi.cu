@@ -94,8 +94,8 @@ ocp_status fill_tracking(ocp* h) {
 static bool aligned8(const void* p) { return ((uintptr_t)p & 7u) == 0; }
 
 static ocp_status upload_tables(ocp* h) {
-  cudaFree(h->d_rowtmpl); cudaFree(h->d_jbase); cudaFree(h->d_hent);
-  h->d_rowtmpl = nullptr; h->d_jbase = nullptr; h->d_hent = nullptr;
+  cudaFree(h->d_rowtmpl); cudaFree(h->d_jbase); cudaFree(h->d_hent); cudaFree(h->d_fin); cudaFree(h->d_tcol);
+  h->d_rowtmpl = nullptr; h->d_jbase = nullptr; h->d_hent = nullptr; h->d_fin = nullptr; h->d_tcol = nullptr;
   const Pattern& P = h->pat;
   std::vector<int32_t> rt((size_t)RT_STRIDE * P.nx, -1);
   for (int k = 0; k < P.nx; ++k) {
@@ -118,6 +118,15 @@ static ocp_status upload_tables(ocp* h) {
     return cuda_err(h, e, "cudaMemcpy");
   if ((e = cudaMemcpy(h->d_hent, he.data(), he.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
     return cuda_err(h, e, "cudaMemcpy");
+  std::vector<int32_t> fin(P.fin.begin(), P.fin.end()), tcol(P.tcol.begin(), P.tcol.end());
+  if (fin.empty()) fin.push_back(0);
+  if (tcol.empty()) tcol.push_back(0);
+  if ((e = cudaMalloc(&h->d_fin, fin.size() * sizeof(int32_t))) != cudaSuccess) return cuda_err(h, e, "cudaMalloc");
+  if ((e = cudaMalloc(&h->d_tcol, tcol.size() * sizeof(int32_t))) != cudaSuccess) return cuda_err(h, e, "cudaMalloc");
+  if ((e = cudaMemcpy(h->d_fin, fin.data(), fin.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
+    return cuda_err(h, e, "cudaMemcpy");
+  if ((e = cudaMemcpy(h->d_tcol, tcol.data(), tcol.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
+    return cuda_err(h, e, "cudaMemcpy");
   return OCP_OK;
 }
 
@@ -128,13 +137,14 @@ static int model_nparams(int model) {
     case OCP_MODEL_HEAT1D: return 1;
     case OCP_MODEL_DINT: return 0;
     case OCP_MODEL_QUADROTOR: return 1;
+    case OCP_MODEL_GODDARD: return 4;
   }
   return -1;
 }
 
 static void free_handle(ocp* h) {
   if (!h) return;
-  cudaFree(h->d_rowtmpl); cudaFree(h->d_jbase); cudaFree(h->d_hent);
+  cudaFree(h->d_rowtmpl); cudaFree(h->d_jbase); cudaFree(h->d_hent); cudaFree(h->d_fin); cudaFree(h->d_tcol);
   cudaFree(h->d_partials); cudaFree(h->d_counter); cudaFree(h->d_xtrack);
   delete h;
 }
@@ -155,6 +165,7 @@ ocp_status init_host(ocp* h, const ocp_dynamics* dyn, const ocp_cost* cost, int 
     case OCP_MODEL_CARTPOLE: enx = 4; break;
     case OCP_MODEL_DINT: enx = 2; break;
     case OCP_MODEL_QUADROTOR: enx = 9; enu = 4; break;
+    case OCP_MODEL_GODDARD: enx = 3; break;
     case OCP_MODEL_HEAT1D: {
       const double c = dyn->params[0];
       if (!(c >= 2.0 && c <= 128.0) || c != std::floor(c))
@@ -167,6 +178,16 @@ ocp_status init_host(ocp* h, const ocp_dynamics* dyn, const ocp_cost* cost, int 
   if (N < 1) return set_err(nullptr, OCP_EDIM, "N must be >= 1");
   if (!(T > 0.0) || !std::isfinite(T)) return set_err(nullptr, OCP_EINVAL, "T must be positive and finite");
   if (!cost->q || !cost->r) return set_err(nullptr, OCP_EINVAL, "cost weights q and r are required");
+  if (dyn->model == OCP_MODEL_GODDARD) {
+    for (int k = 0; k < nx; ++k)
+      if (cost->q[k] != 0.0) return set_err(nullptr, OCP_EMODEL, "Goddard: the objective is a terminal cost (q and r must be zero)");
+    for (int i = 0; i < nu; ++i)
+      if (cost->r[i] != 0.0) return set_err(nullptr, OCP_EMODEL, "Goddard: the objective is a terminal cost (q and r must be zero)");
+    for (int k = 0; k < nx && cost->xref; ++k)
+      if (cost->xref[k] != 0.0) return set_err(nullptr, OCP_EMODEL, "Goddard: no running-cost reference");
+    for (int i = 0; i < nu && cost->uref; ++i)
+      if (cost->uref[i] != 0.0) return set_err(nullptr, OCP_EMODEL, "Goddard: no running-cost reference");
+  }
   h->model = dyn->model; h->nx = nx; h->nu = nu; h->N = N; h->T = T;
   h->h = T / (double)N;
   h->hh = h->h / 2.0;
@@ -181,6 +202,11 @@ ocp_status init_host(ocp* h, const ocp_dynamics* dyn, const ocp_cost* cost, int 
   for (double v : h->xref) if (v != 0.0) h->has_ref = true;
   for (double v : h->uref) if (v != 0.0) h->has_ref = true;
   h->x0.assign(nx, 0.0);
+  {
+    const double inf = std::numeric_limits<double>::infinity();
+    h->xlo.assign(nx, -inf); h->xhi.assign(nx, inf); h->ulo.assign(nu, -inf); h->uhi.assign(nu, inf);
+    h->tflo = -inf; h->tfhi = inf;
+  }
   std::string why;
   if (!build_pattern(h, why)) return set_err(nullptr, OCP_EDIM, why);
   return OCP_OK;
@@ -229,8 +255,9 @@ ocp_status ocp_set_boundary(ocp_t* h, const double* x0, const double* xf) {
   const bool fin = xf != nullptr;
   if (fin) h->xf.assign(xf, xf + h->nx);
   else h->xf.clear();
-  if (fin != h->has_final) {
+  if (fin != h->has_final || !h->fin_comp.empty()) {
     h->has_final = fin;
+    h->fin_comp.clear();
     std::string why;
     if (!build_pattern(h, why)) return set_err(h, OCP_EDIM, why);
     return upload_tables(h);
@@ -249,15 +276,20 @@ ocp_status ocp_dims(const ocp_t* h, int64_t* n, int64_t* m, int64_t* nnzj, int64
 
 ocp_status ocp_bounds(const ocp_t* h, double* lvar, double* uvar, double* lcon, double* ucon) {
   if (!h) return OCP_EINVAL;
-  const double inf = std::numeric_limits<double>::infinity();
+  const int64_t nxN = (int64_t)h->nx * (h->N + 1), nX = nxN + (int64_t)h->nu * (h->N + 1);
   for (int64_t i = 0; i < h->pat.n; ++i) {
-    if (lvar) lvar[i] = -inf;
-    if (uvar) uvar[i] = inf;
+    double lo, hi;
+    if (i < nxN) { lo = h->xlo[i % h->nx]; hi = h->xhi[i % h->nx]; }
+    else if (i < nX) { lo = h->ulo[(i - nxN) % h->nu]; hi = h->uhi[(i - nxN) % h->nu]; }
+    else { lo = h->tflo; hi = h->tfhi; }  // the free final time
+    if (lvar) lvar[i] = lo;
+    if (uvar) uvar[i] = hi;
   }
+  const int64_t nfin = h->pat.nb - h->nx;
   for (int64_t i = 0; i < h->pat.m; ++i) {
     double v = 0.0;
     if (i < h->nx) v = h->x0[i];
-    else if (h->has_final && i < 2 * h->nx) v = h->xf[i - h->nx];
+    else if (i < h->nx + nfin) v = h->xf[i - h->nx];
     if (lcon) lcon[i] = v;
     if (ucon) ucon[i] = v;
   }
@@ -273,6 +305,7 @@ ocp_status ocpg::dispatch_eval(ocp* h, unsigned out, const EvalCall& c, void* st
     case OCP_MODEL_CARTPOLE: return node_eval_cartpole(h, out, c, s);
     case OCP_MODEL_DINT: return node_eval_dint(h, out, c, s);
     case OCP_MODEL_QUADROTOR: return node_eval_quad(h, out, c, s);
+    case OCP_MODEL_GODDARD: return goddard_eval(h, out, c, s);
     case OCP_MODEL_HEAT1D: return heat_eval(h, out, c, s);
   }
   return set_err(h, OCP_EMODEL, "unknown model");
@@ -285,6 +318,7 @@ static ocp_status dispatch_prod(ocp* h, const ProdCall& c, void* stream) {
     case OCP_MODEL_CARTPOLE: return node_prod_cartpole(h, c, s);
     case OCP_MODEL_DINT: return node_prod_dint(h, c, s);
     case OCP_MODEL_QUADROTOR: return node_prod_quad(h, c, s);
+    case OCP_MODEL_GODDARD: return goddard_prod(h, c, s);
     case OCP_MODEL_HEAT1D: return heat_prod(h, c, s);
   }
   return set_err(h, OCP_EMODEL, "unknown model");
@@ -422,6 +456,8 @@ ocp_status ocp_eval_all_range(ocp_t* h, int64_t node_begin, int64_t node_end, co
   if (!h) return OCP_EINVAL;
   if (node_begin < 0 || node_end > h->N + 1 || node_begin >= node_end)
     return set_err(h, OCP_EDIM, "node range outside [0, N+1) or empty");
+  if (h->model == OCP_MODEL_GODDARD)
+    return set_err(h, OCP_EMODEL, "node ranges are not provided for the Goddard model (tf couples every node)");
   NEED(x); NEED(y); NEED(f); NEED(cv); NEED(g); NEED(jvals); NEED(hvals);
   EvalCall c;
   c.B = node_begin; c.E = node_end; c.range = true;
@@ -490,10 +526,64 @@ ocp_status ocp_set_param0(ocp_t* h, double value) {
   return OCP_OK;
 }
 
+static ocp_status rebuild(ocp* h) {
+  std::string why;
+  if (!build_pattern(h, why)) return set_err(h, OCP_EDIM, why);
+  return upload_tables(h);
+}
+
+ocp_status ocp_set_free_final_time(ocp_t* h, int enable) {
+  if (!h) return OCP_EINVAL;
+  if (h->model != OCP_MODEL_GODDARD)
+    return set_err(h, OCP_EMODEL, "a free final time is provided for the Goddard model");
+  h->free_tf = enable != 0;
+  return rebuild(h);
+}
+
+ocp_status ocp_set_final_components(ocp_t* h, int count, const int32_t* comps, const double* values) {
+  if (!h) return OCP_EINVAL;
+  if (h->model != OCP_MODEL_GODDARD)
+    return set_err(h, OCP_EMODEL, "final rows on a subset of the state are provided for the Goddard model "
+                                  "(ocp_set_boundary sets them on every component)");
+  if (count < 0 || count > h->nx || (count > 0 && (!comps || !values)))
+    return set_err(h, OCP_EINVAL, "final components: bad count or NULL arrays");
+  for (int i = 0; i < count; ++i)
+    if (comps[i] < 0 || comps[i] >= h->nx || (i > 0 && comps[i] <= comps[i - 1]))
+      return set_err(h, OCP_EINVAL, "final components must be ascending state indices");
+  h->fin_comp.assign(comps, comps + count);
+  h->xf.assign(values, values + count);
+  h->has_final = count > 0;
+  if (count == h->nx) h->fin_comp.clear();  // every component: the plain final rows
+  return rebuild(h);
+}
+
+ocp_status ocp_set_terminal_cost(ocp_t* h, const double* mayer) {
+  if (!h) return OCP_EINVAL;
+  if (h->model != OCP_MODEL_GODDARD)
+    return set_err(h, OCP_EMODEL, "a terminal cost is provided for the Goddard model");
+  if (mayer) h->mayer.assign(mayer, mayer + h->nx);
+  else h->mayer.clear();
+  return OCP_OK;
+}
+
+ocp_status ocp_set_variable_bounds(ocp_t* h, const double* xlo, const double* xhi, const double* ulo,
+                                   const double* uhi, double tflo, double tfhi) {
+  if (!h) return OCP_EINVAL;
+  const double inf = std::numeric_limits<double>::infinity();
+  h->xlo.assign(h->nx, -inf); h->xhi.assign(h->nx, inf); h->ulo.assign(h->nu, -inf); h->uhi.assign(h->nu, inf);
+  if (xlo) h->xlo.assign(xlo, xlo + h->nx);
+  if (xhi) h->xhi.assign(xhi, xhi + h->nx);
+  if (ulo) h->ulo.assign(ulo, ulo + h->nu);
+  if (uhi) h->uhi.assign(uhi, uhi + h->nu);
+  h->tflo = tflo;
+  h->tfhi = tfhi;
+  return OCP_OK;
+}
+
 ocp_status ocp_set_tracking(ocp_t* h, const double* xslope, const double* xamp, const double* xfreq) {
   if (!h) return OCP_EINVAL;
-  if (h->model == OCP_MODEL_HEAT1D)
-    return set_err(h, OCP_EMODEL, "a time-varying reference is provided for the node models (not HEAT1D)");
+  if (h->model == OCP_MODEL_HEAT1D || h->model == OCP_MODEL_GODDARD)
+    return set_err(h, OCP_EMODEL, "a time-varying reference is provided for the node models with a running cost");
   const int nx = h->nx;
   h->xslope.assign(nx, 0.0); h->xamp.assign(nx, 0.0); h->xfreq.assign(nx, 0.0);
   if (xslope) h->xslope.assign(xslope, xslope + nx);

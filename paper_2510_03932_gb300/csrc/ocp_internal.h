@@ -30,6 +30,7 @@ struct RowTemplate {
   int rx = 0, ru = 0;
   int xv[RT_XV] = {-1, -1, -1, -1, -1, -1};
   int uv[RT_UV] = {-1, -1, -1, -1};
+  bool jz[RT_XV] = {};  // entry xv[e] is the identity term alone (df_k/dx_v identically zero)
   int count() const { return 2 * (rx + ru); }
 };
 
@@ -45,6 +46,15 @@ struct Pattern {
   int hx = 0, hu = 0;                    // entries per node in the X block / U block
   int64_t hbase_u = 0;                   // first slot of the U block = (N+1) * hx
   std::vector<int8_t> hpos;              // per max-template entry: position in its block or -1
+  // free final time tf (the last unknown, index n - 1): one more entry closing every defect
+  // row (its tf column) and a Hessian row of tf against the node variables tcol (local
+  // indices: tx state columns, then tu control columns) of every node
+  int free_tf = 0;
+  int tx = 0, tu = 0;
+  std::vector<int> tcol;
+  int64_t hbase_t = 0;                   // first slot of the tf row = (N+1) * (hx + hu)
+  std::vector<int> fin;                  // components with a final row X_{N,k}, ascending
+  int row_count(int k) const { return rows[k].count() + free_tf; }
 };
 
 }  // namespace ocpg
@@ -55,6 +65,14 @@ struct ocp {
   double T = 0, h = 0, hh = 0;
   std::vector<double> params, q, r, xref, uref, x0, xf;
   bool has_final = false, has_ref = false;
+  // final rows on a subset of the components (fin_comp, ascending; empty: all of them when
+  // has_final), a free final time and a linear terminal cost sum_k mayer_k X_{N,k}
+  std::vector<int> fin_comp;
+  bool free_tf = false;
+  std::vector<double> mayer;
+  // variable bounds reported by ocp_bounds (default -inf / +inf)
+  std::vector<double> xlo, xhi, ulo, uhi;
+  double tflo = 0, tfhi = 0;
   const double* p0_dev = nullptr;  // device scalar overriding params[0] (or null)
   // time-varying state reference: xref_k + xslope_k t_j + xamp_k sin(xfreq_k t_j) for the
   // components trk_comp (ntrk of them), tabulated once per node in d_xtrack[(N+1) x ntrk]
@@ -68,6 +86,8 @@ struct ocp {
   int32_t* d_rowtmpl = nullptr;  // nx * RT_STRIDE ints: rx, ru, xv[RT_XV], uv[RT_UV]
   int64_t* d_jbase = nullptr;    // nx + 1
   int32_t* d_hent = nullptr;     // 2 * (hx + hu)
+  int32_t* d_fin = nullptr;      // components of the final rows (nb - nx)
+  int32_t* d_tcol = nullptr;     // tf-row columns (tx + tu local indices)
   // scratch: per-CTA partial sums and the completion ticket of the last-block reduction
   double* d_partials = nullptr;
   unsigned* d_counter = nullptr;
@@ -127,6 +147,8 @@ ocp_status node_prod_dint(ocp* h, const ProdCall& c, cudaStream_t s);
 ocp_status node_prod_quad(ocp* h, const ProdCall& c, cudaStream_t s);
 // Tabulate the time-varying state reference of the handle into h->d_xtrack.
 ocp_status fill_tracking(ocp* h);
+ocp_status goddard_eval(ocp* h, unsigned out, const EvalCall& c, cudaStream_t s);
+ocp_status goddard_prod(ocp* h, const ProdCall& c, cudaStream_t s);
 ocp_status heat_eval(ocp* h, unsigned out, const EvalCall& c, cudaStream_t s);
 ocp_status heat_prod(ocp* h, const ProdCall& c, cudaStream_t s);
 

@@ -9,6 +9,10 @@
 //   Hessian:   block-diagonal by node (the defects are sums of one-node terms and the cost is
 //              a sum over nodes): the hx X-row entries of every node in node order, then the
 //              hu U-row entries of every node; within a node, by (row, col).
+//   Free final time tf (the last unknown): every defect row ends with its tf entry, and the
+//              Hessian ends with the tf row (tf against the state columns of every node, then
+//              the control columns; no (tf, tf) entry: c and F are linear in tf).
+//   Final rows may cover a subset of the components (nb = nx + their count).
 // Sorting by (row, col) globally gives exactly this order because X columns precede U columns.
 #include <algorithm>
 #include <cstring>
@@ -26,7 +30,7 @@ static void rows_from(std::vector<RowTemplate>& rows) {
   for (int k = 0; k < M::NX; ++k) {
     rows[k].rx = M::RX(k);
     rows[k].ru = M::RU(k);
-    for (int e = 0; e < M::RX(k); ++e) rows[k].xv[e] = M::XV(k, e);
+    for (int e = 0; e < M::RX(k); ++e) { rows[k].xv[e] = M::XV(k, e); rows[k].jz[e] = M::JZ(k, e); }
     for (int e = 0; e < M::RU(k); ++e) rows[k].uv[e] = M::UV(k, e);
   }
 }
@@ -37,6 +41,7 @@ void model_row_templates(int model, int nx, std::vector<RowTemplate>& rows) {
     case OCP_MODEL_CARTPOLE: rows_from<CartPole>(rows); break;
     case OCP_MODEL_DINT: rows_from<Dint>(rows); break;
     case OCP_MODEL_QUADROTOR: rows_from<Quadrotor>(rows); break;
+    case OCP_MODEL_GODDARD: rows_from<Goddard>(rows); break;
     case OCP_MODEL_HEAT1D:
       rows.assign(nx, RowTemplate());
       for (int k = 0; k < nx; ++k) {
@@ -70,6 +75,7 @@ void model_hess_max_template(int model, int nx, std::vector<std::pair<int, int>>
     case OCP_MODEL_CARTPOLE: hmax_from<CartPole>(ent, is_dyn); break;
     case OCP_MODEL_DINT: hmax_from<Dint>(ent, is_dyn); break;
     case OCP_MODEL_QUADROTOR: hmax_from<Quadrotor>(ent, is_dyn); break;
+    case OCP_MODEL_GODDARD: hmax_from<Goddard>(ent, is_dyn); break;
     case OCP_MODEL_HEAT1D:
       ent.clear();
       is_dyn.clear();
@@ -85,14 +91,19 @@ bool build_pattern(ocp* h, std::string& why) {
   Pattern& P = h->pat;
   P = Pattern();
   P.nx = h->nx; P.nu = h->nu; P.nz = h->nx + h->nu; P.N = h->N;
-  P.n = (int64_t)P.nz * (P.N + 1);
-  P.nb = (int64_t)P.nx * (h->has_final ? 2 : 1);
+  P.free_tf = h->free_tf ? 1 : 0;
+  P.n = (int64_t)P.nz * (P.N + 1) + P.free_tf;
+  if (h->has_final) {
+    if (h->fin_comp.empty()) for (int k = 0; k < P.nx; ++k) P.fin.push_back(k);
+    else P.fin = h->fin_comp;
+  }
+  P.nb = (int64_t)P.nx + (int64_t)P.fin.size();
   P.m = P.nb + (int64_t)P.nx * P.N;
   model_row_templates(h->model, h->nx, P.rows);
   if ((int)P.rows.size() != P.nx) { why = "no row template for this model"; return false; }
   P.jbase.assign(P.nx + 1, 0);
   P.jbase[0] = P.nb;
-  for (int k = 0; k < P.nx; ++k) P.jbase[k + 1] = P.jbase[k] + (int64_t)P.rows[k].count() * P.N;
+  for (int k = 0; k < P.nx; ++k) P.jbase[k + 1] = P.jbase[k] + (int64_t)P.row_count(k) * P.N;
   P.nnzj = P.jbase[P.nx];
   std::vector<std::pair<int, int>> ent;
   std::vector<int> dyn;
@@ -114,6 +125,21 @@ bool build_pattern(ocp* h, std::string& why) {
   P.hent.insert(P.hent.end(), eu.begin(), eu.end());
   P.hbase_u = (int64_t)P.hx * (P.N + 1);
   P.nnzh = (int64_t)(P.hx + P.hu) * (P.N + 1);
+  if (P.free_tf) {
+    // tf row: the columns where some f_k has a derivative, and the cost columns
+    std::vector<bool> col(P.nz, false);
+    for (int k = 0; k < P.nx; ++k) {
+      for (int e = 0; e < P.rows[k].rx; ++e)
+        if (!P.rows[k].jz[e]) col[P.rows[k].xv[e]] = true;
+      for (int e = 0; e < P.rows[k].ru; ++e) col[P.nx + P.rows[k].uv[e]] = true;
+    }
+    for (int v = 0; v < P.nz; ++v)
+      if ((v < P.nx ? h->q[v] : h->r[v - P.nx]) != 0.0) col[v] = true;
+    for (int v = 0; v < P.nz; ++v)
+      if (col[v]) { P.tcol.push_back(v); if (v < P.nx) ++P.tx; else ++P.tu; }
+    P.hbase_t = P.nnzh;
+    P.nnzh += (int64_t)(P.tx + P.tu) * (P.N + 1);
+  }
   const int64_t lim = (int64_t)1 << 31;
   if (P.n >= lim || P.m >= lim || P.nnzj >= lim || P.nnzh >= lim) {
     why = "problem too large for the int32 COO interface (n, m or nnz >= 2^31)";
@@ -130,8 +156,9 @@ struct JacStructArgs {
   int32_t* cols;
   const int32_t* tmpl;   // per component (RT_STRIDE ints): rx, ru, xv[RT_XV], uv[RT_UV]
   const int64_t* jbase;  // nx + 1
-  int64_t N, nb, nnzj, uoff;
-  int nx, nu, has_final;
+  const int32_t* fin;    // components of the final rows
+  int64_t N, nb, nnzj, uoff, n;
+  int nx, nu, free_tf;
 };
 
 __global__ void k_jac_structure(const __grid_constant__ JacStructArgs a) {
@@ -140,7 +167,7 @@ __global__ void k_jac_structure(const __grid_constant__ JacStructArgs a) {
     int64_t row, col;
     if (s < a.nb) {
       row = s;
-      col = (s < a.nx) ? s : (int64_t)a.nx * a.N + (s - a.nx);
+      col = (s < a.nx) ? s : (int64_t)a.nx * a.N + a.fin[s - a.nx];
     } else {
       int lo = 0, hi = a.nx - 1;  // last component with jbase <= s
       while (lo < hi) {
@@ -150,12 +177,13 @@ __global__ void k_jac_structure(const __grid_constant__ JacStructArgs a) {
       const int k = lo;
       const int32_t* t = a.tmpl + RT_STRIDE * k;
       const int rx = t[0], ru = t[1];
-      const int cnt = 2 * (rx + ru);
+      const int cnt = 2 * (rx + ru) + a.free_tf;
       const int64_t rel = s - a.jbase[k];
       const int64_t j = rel / cnt;
       const int e = (int)(rel - j * cnt);
       row = a.nb + (int64_t)k * a.N + j;
-      if (e < rx) col = (int64_t)a.nx * j + t[2 + e];
+      if (e == 2 * (rx + ru)) col = a.n - 1;  // the free final time closes the row
+      else if (e < rx) col = (int64_t)a.nx * j + t[2 + e];
       else if (e < 2 * rx) col = (int64_t)a.nx * (j + 1) + t[2 + (e - rx)];
       else if (e < 2 * rx + ru) col = a.uoff + (int64_t)a.nu * j + t[2 + RT_XV + (e - 2 * rx)];
       else col = a.uoff + (int64_t)a.nu * (j + 1) + t[2 + RT_XV + (e - 2 * rx - ru)];
@@ -169,8 +197,9 @@ struct HessStructArgs {
   int32_t* rows;
   int32_t* cols;
   const int32_t* hent;  // (a, b) pairs: hx X-block entries then hu U-block entries
-  int64_t N, hbase_u, nnzh, uoff;
-  int nx, nu, hx, hu;
+  const int32_t* tcol;  // tf-row columns: tx state then tu control local indices
+  int64_t N, hbase_u, hbase_t, nnzh, uoff, n;
+  int nx, nu, hx, hu, tx, tu;
 };
 
 __device__ __forceinline__ int64_t local_col(int64_t j, int v, int nx, int nu, int64_t uoff) {
@@ -182,6 +211,14 @@ __global__ void k_hess_structure(const __grid_constant__ HessStructArgs a) {
   for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < a.nnzh; s += stride) {
     int64_t j;
     int e;
+    if (s >= a.hbase_t) {  // the tf row: state columns of every node, then control columns
+      const int64_t r = s - a.hbase_t, xpart = (a.N + 1) * a.tx;
+      if (r < xpart) { j = r / a.tx; e = (int)(r - j * a.tx); }
+      else { j = (r - xpart) / a.tu; e = a.tx + (int)(r - xpart - j * a.tu); }
+      a.rows[s] = (int32_t)(a.n - 1);
+      a.cols[s] = (int32_t)local_col(j, a.tcol[e], a.nx, a.nu, a.uoff);
+      continue;
+    }
     if (s < a.hbase_u) { j = s / a.hx; e = (int)(s - j * a.hx); }
     else { const int64_t r = s - a.hbase_u; j = r / a.hu; e = a.hx + (int)(r - j * a.hu); }
     const int va = a.hent[2 * e], vb = a.hent[2 * e + 1];
@@ -192,9 +229,9 @@ __global__ void k_hess_structure(const __grid_constant__ HessStructArgs a) {
 
 ocp_status launch_jac_structure(const ocp* h, int32_t* rows, int32_t* cols, cudaStream_t s) {
   JacStructArgs a;
-  a.rows = rows; a.cols = cols; a.tmpl = h->d_rowtmpl; a.jbase = h->d_jbase;
-  a.N = h->N; a.nb = h->pat.nb; a.nnzj = h->pat.nnzj; a.uoff = (int64_t)h->nx * (h->N + 1);
-  a.nx = h->nx; a.nu = h->nu; a.has_final = h->has_final;
+  a.rows = rows; a.cols = cols; a.tmpl = h->d_rowtmpl; a.jbase = h->d_jbase; a.fin = h->d_fin;
+  a.N = h->N; a.nb = h->pat.nb; a.nnzj = h->pat.nnzj; a.uoff = (int64_t)h->nx * (h->N + 1); a.n = h->pat.n;
+  a.nx = h->nx; a.nu = h->nu; a.free_tf = h->pat.free_tf;
   const int64_t blocks = std::min<int64_t>((a.nnzj + 255) / 256, (int64_t)h->num_sms * 16);
   k_jac_structure<<<(int)std::max<int64_t>(blocks, 1), 256, 0, s>>>(a);
   return cudaGetLastError() == cudaSuccess ? OCP_OK : OCP_ECUDA;
@@ -202,9 +239,11 @@ ocp_status launch_jac_structure(const ocp* h, int32_t* rows, int32_t* cols, cuda
 
 ocp_status launch_hess_structure(const ocp* h, int32_t* rows, int32_t* cols, cudaStream_t s) {
   HessStructArgs a;
-  a.rows = rows; a.cols = cols; a.hent = h->d_hent;
+  a.rows = rows; a.cols = cols; a.hent = h->d_hent; a.tcol = h->d_tcol;
   a.N = h->N; a.hbase_u = h->pat.hbase_u; a.nnzh = h->pat.nnzh; a.uoff = (int64_t)h->nx * (h->N + 1);
-  a.nx = h->nx; a.nu = h->nu; a.hx = h->pat.hx; a.hu = h->pat.hu;
+  a.hbase_t = h->pat.free_tf ? h->pat.hbase_t : h->pat.nnzh;
+  a.n = h->pat.n;
+  a.nx = h->nx; a.nu = h->nu; a.hx = h->pat.hx; a.hu = h->pat.hu; a.tx = h->pat.tx; a.tu = h->pat.tu;
   const int64_t blocks = std::min<int64_t>((a.nnzh + 255) / 256, (int64_t)h->num_sms * 16);
   k_hess_structure<<<(int)std::max<int64_t>(blocks, 1), 256, 0, s>>>(a);
   return cudaGetLastError() == cudaSuccess ? OCP_OK : OCP_ECUDA;

@@ -36,6 +36,8 @@ extern "C" ocp_status ocp_eval_obj_noalloc(const ocp_dynamics* dyn, const ocp_co
   ocp prob;  // host-side description only; no device allocation
   ocp_status st = init_host(&prob, dyn, cost, nx, nu, N, T);
   if (st != OCP_OK) return st;
+  if (prob.model == OCP_MODEL_GODDARD)
+    return set_err(nullptr, OCP_EMODEL, "ocp_eval_obj_noalloc: the Goddard objective is a terminal cost set on a handle");
   const int64_t ntiles = objective_tiles(prob.model, N + 1);
   if (ntiles < 1 || ntiles > OCP_NOALLOC_MAX_TILES)
     return set_err(nullptr, OCP_EDIM,

@@ -14,7 +14,7 @@ import torch
 
 from . import build as _build
 
-MODEL_IDS = {"vdp": 1, "cartpole": 2, "heat": 3, "dint": 4, "quadrotor": 5}
+MODEL_IDS = {"vdp": 1, "cartpole": 2, "heat": 3, "dint": 4, "quadrotor": 5, "goddard": 6}
 STATUS = {0: "OCP_OK", 1: "OCP_EINVAL", 2: "OCP_EDIM", 3: "OCP_ENOMEM", 4: "OCP_ECUDA", 5: "OCP_EMODEL",
           6: "OCP_ETIMEOUT"}
 
@@ -44,6 +44,10 @@ _SIGS = {
     "ocp_destroy": [_P],
     "ocp_set_boundary": [_P, _P, _P],
     "ocp_set_tracking": [_P, _P, _P, _P],
+    "ocp_set_free_final_time": [_P, C.c_int],
+    "ocp_set_final_components": [_P, C.c_int, _P, _P],
+    "ocp_set_terminal_cost": [_P, _P],
+    "ocp_set_variable_bounds": [_P, _P, _P, _P, _P, _D, _D],
     "ocp_dims": [_P, C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_I64)],
     "ocp_bounds": [_P, _P, _P, _P, _P],
     "eval_obj": [_P, _P, _P, _P],
@@ -111,7 +115,8 @@ class OCP:
     """A transcribed optimal control problem (an `ocp_t` handle)."""
 
     def __init__(self, model: str, nx: int, nu: int, N: int, T: float, params, q, r, xref=None, uref=None,
-                 x0=None, xf=None, xslope=None, xamp=None, xfreq=None):
+                 x0=None, xf=None, xslope=None, xamp=None, xfreq=None, free_tf=False, xf_comp=None,
+                 mayer=None, bounds=None):
         L = lib()
         self._keep = []
 
@@ -128,8 +133,22 @@ class OCP:
         _check(L.ocp_create(C.byref(dyn), C.byref(cost), nx, nu, int(N), float(T), C.byref(h)))
         self.h = h
         self.model, self.nx, self.nu, self.N, self.T = model, nx, nu, int(N), float(T)
-        if x0 is not None or xf is not None:
+        if xf_comp is not None:   # final rows on the listed components, values xf
+            _check(L.ocp_set_boundary(h, arr(x0), None), h)
+            comps = (C.c_int32 * len(xf_comp))(*[int(k) for k in xf_comp])
+            self._keep.append(comps)
+            _check(L.ocp_set_final_components(h, len(xf_comp), C.cast(comps, C.c_void_p), arr(xf)), h)
+        elif x0 is not None or xf is not None:
             _check(L.ocp_set_boundary(h, arr(x0), arr(xf)), h)
+        if free_tf:
+            _check(L.ocp_set_free_final_time(h, 1), h)
+        if mayer is not None:
+            _check(L.ocp_set_terminal_cost(h, arr(mayer)), h)
+        if bounds is not None:
+            b = bounds
+            _check(L.ocp_set_variable_bounds(h, arr(b.get("xlo")), arr(b.get("xhi")), arr(b.get("ulo")),
+                                             arr(b.get("uhi")), float(b.get("tflo", -float("inf"))),
+                                             float(b.get("tfhi", float("inf")))), h)
         if xslope is not None or xamp is not None or xfreq is not None:
             # time-varying state reference xref_k + xslope_k t + xamp_k sin(xfreq_k t)
             _check(L.ocp_set_tracking(h, arr(xslope), arr(xamp), arr(xfreq)), h)
@@ -141,7 +160,8 @@ class OCP:
     @classmethod
     def from_workload(cls, w: dict) -> "OCP":
         return cls(w["model"], w["nx"], w["nu"], w["N"], w["T"], w["params"], w["q"], w["r"], w.get("xref"),
-                   w.get("uref"), w.get("x0"), w.get("xf"), w.get("xslope"), w.get("xamp"), w.get("xfreq"))
+                   w.get("uref"), w.get("x0"), w.get("xf"), w.get("xslope"), w.get("xamp"), w.get("xfreq"),
+                   bool(w.get("free_tf")), w.get("xf_comp"), w.get("mayer"), w.get("bounds"))
 
     def close(self):
         if getattr(self, "h", None):

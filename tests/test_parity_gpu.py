@@ -80,7 +80,8 @@ SMALL = [("vdp_n1e3", N) for N in (1, 2, 3, 254, 255, 256, 510, 1000, 1777)] + \
         [("cartpole_n1e5", N) for N in (1, 2, 126, 127, 128, 1000, 1303)] + \
         [("heat_n2e4", N) for N in (1, 2, 30, 31, 32, 100, 333)] + \
         [("dint", N) for N in (1, 2, 100, 997)] + \
-        [("quadrotor_n1e3", N) for N in (1, 2, 62, 63, 64, 126, 1000, 1777)]
+        [("quadrotor_n1e3", N) for N in (1, 2, 62, 63, 64, 126, 1000, 1777)] + \
+        [("goddard_n1e3", N) for N in (1, 2, 254, 255, 256, 510, 1000, 1777)]
 
 
 @pytest.mark.parametrize("name,N", SMALL)
@@ -124,22 +125,58 @@ def test_tracking_reset_returns_to_constant_reference(ocp):
     assert torch.equal(f0, f1) and not torch.equal(f0, f2)
 
 
+@pytest.mark.parametrize("N", [1, 300, 1000])
+def test_parity_goddard_fixed_horizon(ocp, N):
+    """The Goddard kernels with a fixed final time T (no tf unknown, no tf entries)."""
+    w = dict(synth.with_horizon(synth.workload("goddard_n1e3"), N), free_tf=False, T=0.2)
+    full_check(ocp, w)
+
+
+def test_goddard_bounds_and_entry_checks(ocp):
+    """ocp_bounds reports the variable bounds (tf last) and the final value of m; the setters
+    of the free final time, partial final rows and terminal cost belong to the Goddard model."""
+    w = synth.with_horizon(synth.workload("goddard_n1e3"), 10)
+    H = ocp.OCP.from_workload(w)
+    lv, uv, lc, uc = H.bounds()
+    b = w["bounds"]
+    N1 = 11
+    np.testing.assert_array_equal(lv[:3 * N1], np.tile(b["xlo"], N1))
+    np.testing.assert_array_equal(uv[:3 * N1], np.tile(b["xhi"], N1))
+    np.testing.assert_array_equal(lv[3 * N1:4 * N1], np.tile(b["ulo"], N1))
+    np.testing.assert_array_equal(uv[3 * N1:4 * N1], np.tile(b["uhi"], N1))
+    assert lv[-1] == b["tflo"] and uv[-1] == b["tfhi"] and lv.size == 4 * N1 + 1
+    np.testing.assert_array_equal(lc[:4], [1.0, 0.0, 1.0, 0.6])
+    np.testing.assert_array_equal(uc, lc)
+    assert np.all(lc[4:] == 0.0)
+    V = ocp.OCP.from_workload(synth.with_horizon(synth.workload("vdp_n1e3"), 10))
+    import ctypes as C
+    L = ocp.lib()
+    assert L.ocp_set_free_final_time(V.h, 1) == 5
+    assert L.ocp_set_terminal_cost(V.h, None) == 5
+    x = torch.zeros(H.n, dtype=torch.float64, device="cuda")
+    st = L.ocp_eval_all_range(H.h, 0, 5, C.c_void_p(x.data_ptr()), C.c_void_p(x.data_ptr()), 1.0,
+                              *([C.c_void_p(x.data_ptr())] * 5), None)
+    assert st == 5
+
+
 def test_parity_cost_structure_follows_weights(ocp):
     """A zero cost weight drops a diagonal Hessian entry that the dynamics do not need."""
     w = dict(synth.with_horizon(synth.workload("vdp_n1e3"), 50), q=[1.0, 0.0])
     full_check(ocp, w)
 
 
-@pytest.mark.parametrize("name", ["vdp_n1e3", "cartpole_n1e5", "heat_n2e4", "vdp_mu_n1e6", "quadrotor_n1e5"])
+@pytest.mark.parametrize("name", ["vdp_n1e3", "cartpole_n1e5", "heat_n2e4", "vdp_mu_n1e6", "quadrotor_n1e5",
+                                  "goddard_n1e5"])
 def test_parity_full_size_workloads(ocp, name):
     rep = full_check(ocp, synth.workload(name), products=(name != "vdp_mu_n1e6"))
     print(name, rep)
 
 
-def test_every_slot_written_once_and_nothing_beyond(ocp):
+@pytest.mark.parametrize("name", ["cartpole_n1e5", "goddard_n1e3"])
+def test_every_slot_written_once_and_nothing_beyond(ocp, name):
     """NaN-prefilled outputs with guard words after the end: every slot gets a finite value
     and no guard word changes."""
-    w = synth.with_horizon(synth.workload("cartpole_n1e5"), 1000)
+    w = synth.with_horizon(synth.workload(name), 1000)
     d = synth.draw(w)
     H = ocp.OCP.from_workload(w)
     G = 64
@@ -210,7 +247,8 @@ def test_dimension_and_argument_errors(ocp):
 
 
 @pytest.mark.parametrize("name,N", [("vdp_n1e3", 1000), ("vdp_n1e3", 254), ("cartpole_n1e5", 1303),
-                                    ("dint", 97), ("heat_n2e4", 77), ("quadrotor_n1e3", 1000)])
+                                    ("dint", 97), ("heat_n2e4", 77), ("quadrotor_n1e3", 1000),
+                                    ("goddard_n1e3", 1000)])
 def test_fused_step_equals_separate_calls(ocp, name, N):
     """ocp_eval_step (one pass: eval + Jv + J^T w + Hv) is bit-identical to the separate calls."""
     w = synth.with_horizon(synth.workload(name), N)
