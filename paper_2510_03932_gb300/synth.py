@@ -142,12 +142,13 @@ def workload(name: str) -> dict:
         N = {"goddard_n1e3": 1000, "goddard_n1e5": 100_000, "goddard_n1e6": 1_000_000}[name]
         inf = float("inf")
         # max r(tf)  s.t.  x(0) = (r0, v0, m0) = (1, 0, 1),  m(tf) = mf = 0.6,  0 <= u <= 1,
-        # r >= r0,  0 <= v <= vmax = 0.1;  Cd = 310, beta = 500, Tmax = 3.5, b = 2
+        # r >= r0,  0 <= v <= vmax = 0.1;  Cd = 310, beta = 500, Tmax = 3.5, b = 2; tf unbounded
+        # (declared a real variable)
         return dict(name=name, model="goddard", nx=3, nu=1, N=N, T=1.0, params=[310.0, 500.0, 3.5, 2.0],
                     q=[0.0] * 3, r=[0.0], xref=[0.0] * 3, uref=[0.0], x0=[1.0, 0.0, 1.0],
                     xf=[0.6], xf_comp=[2], mayer=[-1.0, 0.0, 0.0], free_tf=True,
                     bounds=dict(xlo=[1.0, 0.0, -inf], xhi=[inf, 0.1, inf], ulo=[0.0], uhi=[1.0],
-                                tflo=0.0, tfhi=inf),
+                                tflo=-inf, tfhi=inf),
                     seed={1000: 1010, 100_000: 1011, 1_000_000: 1012}[N], sigma=1.0, dist="goddard")
     raise KeyError(name)
 
