@@ -767,6 +767,31 @@ template <class S> void lagrangian_grad(const Prob& P, const S* p, const S* x, c
   for (int64_t i = 0; i < L.n; ++i) out[i] = sigma * g[i] + jty[i];
 }
 
+// KKT matrix of the interior-point step (paper Sec. 6: the solver assembles it in device
+// buffers from the derivative values), lower triangle in COO sorted by (row, col):
+//     [ H + diag(dx)        .      ]      dx_i = sigma_x_i + delta_w   (sigma_x may be absent)
+//     [ J             -delta_c I  ]
+// H and J are this oracle's own COO; every diagonal entry of the (1,1) block is present (added
+// where H has none).
+struct KEnt { int64_t r, c; double v; };
+inline void kkt_assemble(const Layout& L, const Coo<double>& H, const Coo<double>& J, const double* sigma_x,
+                         double delta_w, double delta_c, std::vector<KEnt>& K) {
+  std::vector<char> has_diag(L.n, 0);
+  for (size_t e = 0; e < H.val.size(); ++e) {
+    double v = H.val[e];
+    if (H.row[e] == H.col[e]) {
+      has_diag[H.row[e]] = 1;
+      v = v + ((sigma_x ? sigma_x[H.row[e]] : 0.0) + delta_w);
+    }
+    K.push_back({H.row[e], H.col[e], v});
+  }
+  for (int64_t i = 0; i < L.n; ++i)
+    if (!has_diag[i]) K.push_back({i, i, (sigma_x ? sigma_x[i] : 0.0) + delta_w});
+  for (size_t e = 0; e < J.val.size(); ++e) K.push_back({L.n + J.row[e], J.col[e], J.val[e]});
+  for (int64_t r = 0; r < L.m; ++r) K.push_back({L.n + r, L.n + r, -delta_c});
+  std::stable_sort(K.begin(), K.end(), [](const KEnt& a, const KEnt& b) { return a.r != b.r ? a.r < b.r : a.c < b.c; });
+}
+
 int check(const Prob& P) {
   if (P.N < 1 || !(P.T > 0.0)) return 2;
   // the tracking reference is tabulated at t_j = j T / N: not with a free final time
@@ -1018,6 +1043,27 @@ int orc_cs_jtprod_dmu(const Prob* P, const double* x, const double* w, double ep
   Coo<Cx> J; jacobian(*P, p.data(), X.data(), J);
   coo_mtv(J, W.data(), o.data(), L.n);
   for (int64_t i = 0; i < L.n; ++i) out[i] = o[i].imag() / eps;
+  return 0;
+}
+
+// KKT assembly (see kkt_assemble): nnz, then structure and values (rows/cols/vals may be null).
+int orc_kkt(const Prob* P, const double* x, const double* y, double sigma, const double* sigma_x, double delta_w,
+            double delta_c, int64_t* nnz, int32_t* rows, int32_t* cols, double* vals) {
+  int st = check(*P);
+  if (st) return st;
+  Layout L(*P);
+  std::vector<double> p(8); params_of(*P, p.data());
+  Coo<double> H, J;
+  hessian(*P, p.data(), x, y, sigma, H);
+  jacobian(*P, p.data(), x, J);
+  std::vector<KEnt> K;
+  kkt_assemble(L, H, J, sigma_x, delta_w, delta_c, K);
+  if (nnz) *nnz = (int64_t)K.size();
+  for (size_t e = 0; e < K.size(); ++e) {
+    if (rows) rows[e] = (int32_t)K[e].r;
+    if (cols) cols[e] = (int32_t)K[e].c;
+    if (vals) vals[e] = K[e].v;
+  }
   return 0;
 }
 

@@ -188,3 +188,16 @@ def model_f(P, z):
     o = np.empty(P.w["nx"])
     _check(lib().orc_model_f(P.ref(), _ptr(z), _ptr(o)))
     return o
+
+
+def kkt(P, x, y, sigma, sigma_x=None, delta_w=0.0, delta_c=0.0):
+    """KKT matrix [H + diag(sigma_x + delta_w), .; J, -delta_c I] (lower triangle, COO sorted)."""
+    x, y = _f64(x), _f64(y)
+    sx = None if sigma_x is None else _f64(sigma_x)
+    nnz = C.c_int64()
+    _check(lib().orc_kkt(P.ref(), _ptr(x), _ptr(y), C.c_double(sigma), _ptr(sx), C.c_double(delta_w),
+                         C.c_double(delta_c), C.byref(nnz), None, None, None))
+    rows = np.empty(nnz.value, np.int32); cols = np.empty(nnz.value, np.int32); vals = np.empty(nnz.value)
+    _check(lib().orc_kkt(P.ref(), _ptr(x), _ptr(y), C.c_double(sigma), _ptr(sx), C.c_double(delta_w),
+                         C.c_double(delta_c), None, _ptr(rows), _ptr(cols), _ptr(vals)))
+    return rows, cols, vals

@@ -451,6 +451,36 @@ def test_products_vs_complex_step_and_adjoint(name):
     np.testing.assert_allclose(Hv, O.cs_lagrangian_grad(P, x, v, y, sigma), rtol=1e-12, atol=1e-13)
 
 
+@pytest.mark.parametrize("name", MODELS)
+def test_kkt_assembly_structure_and_action(name):
+    """The KKT matrix [H + D, J^T; J, -delta_c I] (lower triangle): sorted, every diagonal
+    present once, nnz = nnz_H + nnz_J + m + (diagonals H lacks); its symmetric action on
+    (v, w) is (H v + D v + J^T w, J v - delta_c w) with the oracle's own products."""
+    w = small(name, 3 if name == "heat_n2e4" else 7)
+    P = O.Problem(w)
+    rng = np.random.default_rng(41)
+    x, y = rand_point(w, rng)
+    sx = rng.uniform(0.1, 2.0, P.n)
+    dw, dc = 1e-3, 1e-4
+    rows, cols, vals = O.kkt(P, x, y, 0.9, sx, dw, dc)
+    n, m = P.n, P.m
+    key = rows.astype(np.int64) * (1 << 32) + cols
+    assert np.all(np.diff(key) > 0) and np.all(rows >= cols)
+    diag = rows == cols
+    assert np.array_equal(np.sort(rows[diag]), np.arange(n + m))
+    hr, hc = O.hess_structure(P)
+    assert rows.size == P.nnzh + P.nnzj + m + (n - np.count_nonzero(hr == hc))
+    v, wv = rng.standard_normal(n), rng.standard_normal(m)
+    z = np.concatenate([v, wv])
+    Kz = np.zeros(n + m)
+    np.add.at(Kz, rows, vals * z[cols])
+    off = ~diag
+    np.add.at(Kz, cols[off], vals[off] * z[rows[off]])
+    top = O.hprod(P, x, y, 0.9, v) + (sx + dw) * v + O.jtprod(P, x, wv)
+    bot = O.jprod(P, x, v) - dc * wv
+    np.testing.assert_allclose(Kz, np.concatenate([top, bot]), rtol=1e-12, atol=1e-12)
+
+
 def test_dpar_vjp_vs_complex_step():
     w = small("vdp_n1e3", 17)
     P = O.Problem(w, mu=1.7)
