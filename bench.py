@@ -248,6 +248,20 @@ def run_ours(args, rank, world):
         jh.append((e0, e1))
     torch.cuda.synchronize(dev)
     jh_ms = float(np.mean([a.elapsed_time(b) for a, b in jh]))
+    # --- KKT assembly from the step's H and J values (HBM-bound gather), timed the same way
+    sig_x = torch.ones(n, dtype=torch.float64, device=dev)
+    kv = H.kkt_values(hv, jv, sig_x, 1e-8, 1e-8)
+    kk = []
+    for k in range(min(args.steps, 50)):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        H.kkt_values(hv, jv, sig_x, 1e-8, 1e-8, out=kv)
+        e1.record(stream)
+        kk.append((e0, e1))
+    torch.cuda.synchronize(dev)
+    kkt_ms = float(np.mean([a.elapsed_time(b) for a, b in kk]))
+    kkt_bytes = 8 * (nnzj + nnzh + n + kv.numel())
     # --- end to end: pinned host buffers, copies inside the timed region
     hx = torch.from_numpy(d["x"]).pin_memory(); hy = torch.from_numpy(d["y"]).pin_memory()
     hvn = torch.from_numpy(d["vn"]).pin_memory(); hvm = torch.from_numpy(d["vm"]).pin_memory()
@@ -304,6 +318,9 @@ def run_ours(args, rank, world):
         jac_hess_only=dict(ms=jh_ms, nnz_per_s=nnz / (jh_ms * 1e-3),
                            GBps=algorithmic_bytes(w, "jh") / (jh_ms * 1e-3) / 1e9,
                            frac=algorithmic_bytes(w, "jh") / (jh_ms * 1e-3) / 1e9 / hbm),
+        kkt_assembly=dict(ms=kkt_ms, nnz=kv.numel(), GBps=kkt_bytes / (kkt_ms * 1e-3) / 1e9,
+                          hbm_frac=kkt_bytes / (kkt_ms * 1e-3) / 1e9 / hbm,
+                          what="K = [H + diag(sigma_x + delta_w), J^T; J, -delta_c I] from the COO values"),
         e2e=dict(value=e2e_val, unit="nnz/s", h2d_bytes_per_step=8 * (n + m + n + m),
                  d2h_bytes_per_step=8 * sum(t.numel() for t in outs), ms=float(np.mean(e2e_ms))),
         gpu_launches=args.steps, clocks=clocks, wall_s=wall,

@@ -196,6 +196,21 @@ ocp_status ocp_eval_step(ocp_t* h, const double* x, const double* y, double sigm
                          const double* vm, double* f, double* c, double* g, double* jvals,
                          double* hvals, double* Jv, double* Jtv, double* Hv, void* stream);
 
+/* KKT matrix of the interior-point step (paper Sec. 6: the solver assembles the KKT system in
+ * device buffers from the derivative values), lower triangle, COO sorted by (row, col):
+ *     K = [ H + diag(sigma_x + delta_w)                ]    size (n + m) x (n + m)
+ *         [ J                          -delta_c I      ]
+ * with H and J the values of hess_coo_values and jac_coo_values (same x, y, sigma).  Every
+ * row ends with its diagonal entry (added to the (1,1) block where H has none).
+ * ocp_kkt_dims: the number of entries (host; OCP_EDIM when it does not fit int32).
+ * ocp_kkt_structure: rows and cols (int32 device arrays of length nnzk).
+ * ocp_kkt_values: kvals (device, length nnzk) from hvals (nnz_H) and jvals (nnz_J); sigma_x
+ *   (device, length n) may be NULL (zero); delta_w, delta_c are the regularisation scalars. */
+ocp_status ocp_kkt_dims(const ocp_t* h, int64_t* nnzk);
+ocp_status ocp_kkt_structure(ocp_t* h, int32_t* rows, int32_t* cols, void* stream);
+ocp_status ocp_kkt_values(ocp_t* h, const double* hvals, const double* jvals, const double* sigma_x,
+                          double delta_w, double delta_c, double* kvals, void* stream);
+
 /* Parameter derivative for the Van der Pol model (mu = params[0]):
  *   dmu = (dc/dmu)^T w   (device scalar),  optionally together with J^T w into Jtw (may be NULL).
  * Other models: OCP_EMODEL. */

@@ -95,7 +95,9 @@ static bool aligned8(const void* p) { return ((uintptr_t)p & 7u) == 0; }
 
 static ocp_status upload_tables(ocp* h) {
   cudaFree(h->d_rowtmpl); cudaFree(h->d_jbase); cudaFree(h->d_hent); cudaFree(h->d_fin); cudaFree(h->d_tcol);
+  cudaFree(h->d_kcbase);
   h->d_rowtmpl = nullptr; h->d_jbase = nullptr; h->d_hent = nullptr; h->d_fin = nullptr; h->d_tcol = nullptr;
+  h->d_kcbase = nullptr;
   const Pattern& P = h->pat;
   std::vector<int32_t> rt((size_t)RT_STRIDE * P.nx, -1);
   for (int k = 0; k < P.nx; ++k) {
@@ -127,6 +129,10 @@ static ocp_status upload_tables(ocp* h) {
     return cuda_err(h, e, "cudaMemcpy");
   if ((e = cudaMemcpy(h->d_tcol, tcol.data(), tcol.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
     return cuda_err(h, e, "cudaMemcpy");
+  if ((e = cudaMalloc(&h->d_kcbase, P.kcbase.size() * sizeof(int64_t))) != cudaSuccess)
+    return cuda_err(h, e, "cudaMalloc");
+  if ((e = cudaMemcpy(h->d_kcbase, P.kcbase.data(), P.kcbase.size() * 8, cudaMemcpyHostToDevice)) != cudaSuccess)
+    return cuda_err(h, e, "cudaMemcpy");
   return OCP_OK;
 }
 
@@ -145,6 +151,7 @@ static int model_nparams(int model) {
 static void free_handle(ocp* h) {
   if (!h) return;
   cudaFree(h->d_rowtmpl); cudaFree(h->d_jbase); cudaFree(h->d_hent); cudaFree(h->d_fin); cudaFree(h->d_tcol);
+  cudaFree(h->d_kcbase);
   cudaFree(h->d_partials); cudaFree(h->d_counter); cudaFree(h->d_xtrack);
   delete h;
 }

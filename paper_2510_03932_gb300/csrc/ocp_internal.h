@@ -55,6 +55,13 @@ struct Pattern {
   int64_t hbase_t = 0;                   // first slot of the tf row = (N+1) * (hx + hu)
   std::vector<int> fin;                  // components with a final row X_{N,k}, ascending
   int row_count(int k) const { return rows[k].count() + free_tf; }
+  // KKT matrix [H + D, J^T; J, -delta_c I] (lower triangle, sorted by (row, col)): per-node
+  // templates of the (1,1) rows, X then U, with the diagonal appended to rows where H has
+  // none; src = position in the node's H block or -1 for an added diagonal
+  struct KEnt { int src, a, b; };
+  std::vector<KEnt> kxt, kut;
+  int64_t kb_u = 0, kb_t = 0, kb_c = 0, nnzk = -1;  // slot bases; nnzk = -1: too large for int32
+  std::vector<int64_t> kcbase;           // KKT slot of the first defect row of component k (nx + 1)
 };
 
 }  // namespace ocpg
@@ -88,6 +95,7 @@ struct ocp {
   int32_t* d_hent = nullptr;     // 2 * (hx + hu)
   int32_t* d_fin = nullptr;      // components of the final rows (nb - nx)
   int32_t* d_tcol = nullptr;     // tf-row columns (tx + tu local indices)
+  int64_t* d_kcbase = nullptr;   // KKT slot bases of the defect rows (nx + 1)
   // scratch: per-CTA partial sums and the completion ticket of the last-block reduction
   double* d_partials = nullptr;
   unsigned* d_counter = nullptr;

@@ -140,7 +140,28 @@ bool build_pattern(ocp* h, std::string& why) {
     P.hbase_t = P.nnzh;
     P.nnzh += (int64_t)(P.tx + P.tu) * (P.N + 1);
   }
+  // KKT layout: rows of the (1,1) block node by node (X rows, then U rows), the tf row, then
+  // the constraint rows, each with its diagonal last (the largest column of a lower row)
+  for (int a = 0; a < P.nz; ++a) {
+    std::vector<Pattern::KEnt>& t = (a < P.nx) ? P.kxt : P.kut;
+    const int base = (a < P.nx) ? 0 : P.hx;
+    bool diag = false;
+    for (int e = (a < P.nx ? 0 : P.hx); e < (a < P.nx ? P.hx : P.hx + P.hu); ++e)
+      if (P.hent[e].first == a) {
+        t.push_back({e - base, a, P.hent[e].second});
+        diag = diag || (P.hent[e].second == a);
+      }
+    if (!diag) t.push_back({-1, a, a});
+  }
+  P.kb_u = (int64_t)P.kxt.size() * (P.N + 1);
+  P.kb_t = P.kb_u + (int64_t)P.kut.size() * (P.N + 1);
+  P.kb_c = P.kb_t + (P.free_tf ? (int64_t)(P.tx + P.tu) * (P.N + 1) + 1 : 0);
+  P.kcbase.assign(P.nx + 1, 0);
+  P.kcbase[0] = P.kb_c + 2 * P.nb;
+  for (int k = 0; k < P.nx; ++k) P.kcbase[k + 1] = P.kcbase[k] + (int64_t)(P.row_count(k) + 1) * P.N;
+  P.nnzk = P.kcbase[P.nx];
   const int64_t lim = (int64_t)1 << 31;
+  if (P.nnzk >= lim || P.n + P.m >= lim) P.nnzk = -1;
   if (P.n >= lim || P.m >= lim || P.nnzj >= lim || P.nnzh >= lim) {
     why = "problem too large for the int32 COO interface (n, m or nnz >= 2^31)";
     return false;

@@ -48,6 +48,9 @@ _SIGS = {
     "ocp_set_final_components": [_P, C.c_int, _P, _P],
     "ocp_set_terminal_cost": [_P, _P],
     "ocp_set_variable_bounds": [_P, _P, _P, _P, _P, _D, _D],
+    "ocp_kkt_dims": [_P, C.POINTER(_I64)],
+    "ocp_kkt_structure": [_P, _P, _P, _P],
+    "ocp_kkt_values": [_P, _P, _P, _P, _D, _D, _P, _P],
     "ocp_dims": [_P, C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_I64), C.POINTER(_I64)],
     "ocp_bounds": [_P, _P, _P, _P, _P],
     "eval_obj": [_P, _P, _P, _P],
@@ -226,6 +229,29 @@ class OCP:
         cols = torch.empty(self.nnzh, dtype=torch.int32, device=self.device)
         _check(lib().hess_coo_structure(self.h, _ptr(rows), _ptr(cols), _stream(stream)), self.h)
         return rows, cols
+
+    # ---- KKT matrix [H + diag(sigma_x + delta_w), J^T; J, -delta_c I] (lower triangle) -------
+    def kkt_nnz(self):
+        nz = _I64()
+        _check(lib().ocp_kkt_dims(self.h, C.byref(nz)), self.h)
+        return nz.value
+
+    def kkt_structure(self, stream=None):
+        nz = self.kkt_nnz()
+        rows = torch.empty(nz, dtype=torch.int32, device=self.device)
+        cols = torch.empty(nz, dtype=torch.int32, device=self.device)
+        _check(lib().ocp_kkt_structure(self.h, _ptr(rows), _ptr(cols), _stream(stream)), self.h)
+        return rows, cols
+
+    def kkt_values(self, hvals, jvals, sigma_x=None, delta_w=0.0, delta_c=0.0, out=None, stream=None):
+        hvals = self._vec(hvals, self.nnzh, "hvals")
+        jvals = self._vec(jvals, self.nnzj, "jvals")
+        if sigma_x is not None:
+            sigma_x = self._vec(sigma_x, self.n, "sigma_x")
+        out = self._out(out, self.kkt_nnz(), "kvals")
+        _check(lib().ocp_kkt_values(self.h, _ptr(hvals), _ptr(jvals), _ptr(sigma_x), float(delta_w), float(delta_c),
+                                    _ptr(out), _stream(stream)), self.h)
+        return out
 
     def jac_coo_values(self, x, out=None, stream=None):
         x = self._vec(x, self.n, "x")

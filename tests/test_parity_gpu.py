@@ -260,3 +260,48 @@ def test_fused_step_equals_separate_calls(ocp, name, N):
     torch.cuda.synchronize()
     for a, b in zip(outs, sep):
         assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("name,N", [("vdp_n1e3", 1000), ("cartpole_n1e5", 700), ("heat_n2e4", 40), ("dint", 97),
+                                    ("quadrotor_n1e3", 300), ("goddard_n1e3", 500),
+                                    ("goddard_fixed", 300)])
+def test_kkt_assembly(ocp, name, N):
+    """KKT structure bit-exact with the oracle's assembly; values are the GPU's own H and J
+    values moved bit for bit (plus sigma_x + delta_w on the diagonal) and pass the parity gate
+    against the oracle's KKT."""
+    if name == "goddard_fixed":
+        w = dict(synth.with_horizon(synth.workload("goddard_n1e3"), N), free_tf=False, T=0.2)
+    else:
+        w = synth.with_horizon(synth.workload(name), N)
+    d = synth.draw(w)
+    P = O.Problem(w)
+    H = ocp.OCP.from_workload(w)
+    x, y = dev(d["x"]), dev(d["y"])
+    rng = np.random.default_rng(5)
+    sx = rng.uniform(0.1, 2.0, H.n)
+    dw, dc = 1e-3, 1e-5
+    f, c, g, jv, hv = H.eval_all(x, y, 0.8)
+    kv = H.kkt_values(hv, jv, dev(sx), dw, dc)
+    kr, kc = H.kkt_structure()
+    orr, occ, ov = O.kkt(P, d["x"], d["y"], 0.8, sx, dw, dc)
+    torch.cuda.synchronize()
+    assert np.array_equal(host(kr), orr) and np.array_equal(host(kc), occ)
+    # the moved values: H and J entries bit for bit, diagonals of the (1,1) block with D added
+    kvh, jvh, hvh = host(kv), host(jv), host(hv)
+    n = H.n
+    hr, hc = (host(t) for t in H.hess_coo_structure())
+    jr, jc = (host(t) for t in H.jac_coo_structure())
+    key = lambda r, cc: r.astype(np.int64) * (1 << 32) + cc
+    kk = key(orr, occ)
+    pos_h = np.searchsorted(kk, key(hr, hc))
+    expect_h = np.where(hr == hc, hvh + (sx[hr] + dw), hvh)
+    assert np.array_equal(kvh[pos_h], expect_h)
+    pos_j = np.searchsorted(kk, key(jr + n, jc))
+    assert np.array_equal(kvh[pos_j], jvh)
+    # gate against the oracle's KKT with the running-error magnitudes of its H and J entries
+    ev = O.evaluate(P, d["x"], d["y"], 0.8, shadow=True)
+    mag = np.abs(ov)
+    mag[pos_h] = ev["hess_mag"] + np.where(hr == hc, np.abs(sx[hr] + dw), 0.0)
+    mag[pos_j] = ev["jac_mag"]
+    rep = {}
+    gate("kkt", kvh, ov, mag, rep)
