@@ -7,8 +7,8 @@
 // from the COO values of hess_coo_values and jac_coo_values.  The layout is fixed by the
 // pattern compiler: the rows of the (1,1) block node by node (X rows, then U rows, then the
 // free final time), then the constraint rows; every row ends with its diagonal, which is
-// added where H has none.  One thread per KKT slot decodes its source from the templates, so
-// consecutive threads read and write consecutive addresses (a gather with no index array).
+// added where H has none.  Each KKT slot's source is decoded from the templates (no index
+// array is read), so consecutive threads read and write consecutive addresses.
 #include <algorithm>
 #include <cstring>
 
@@ -17,6 +17,17 @@
 namespace ocpg {
 
 constexpr int KKT_TMAX = 256;   // entries of a node's X or U row template (with added diagonals)
+constexpr int KKT_MAXREG = 4 + 128;  // X, U, tf, boundary rows, and the defect rows of each component
+
+// A run of KKT slots with one layout: slot i of the region is KKT entry out + i; its period is
+// the template length (X, U) or the row length plus the diagonal (defects); src / stride give
+// the first source value and the source advance per period.
+struct KRegion {
+  int64_t out, src;
+  uint32_t len, period, stride;
+  int kind;
+  uint32_t block0;   // first block of the values kernel that works on this region
+};
 
 struct KktArgs {
   const double* __restrict__ hv;
@@ -35,6 +46,9 @@ struct KktArgs {
   int nx, nu, hx, hu, tx, tu, kx, ku, free_tf;
   int16_t ksrc[2 * KKT_TMAX];  // X template then U template: source position or -1
   int16_t ka[2 * KKT_TMAX], kb[2 * KKT_TMAX];
+  int nreg;
+  uint32_t nblocks;   // blocks of the values kernel
+  KRegion reg[KKT_MAXREG];
 };
 
 __device__ __forceinline__ int64_t kkt_col(const KktArgs& a, int64_t j, int v) {
@@ -51,52 +65,117 @@ __device__ __forceinline__ int kkt_comp(const KktArgs& a, int64_t s) {
   return lo;
 }
 
-template <bool VALUES>
-__global__ void k_kkt(const __grid_constant__ KktArgs a) {
+// Values: the KKT is cut into regions of uniform layout (the X rows of the nodes, the U rows,
+// the tf row, the boundary rows, the defect rows of each component), each with its own range
+// of blocks.  In the row regions a block takes KKT_ROWS consecutive periods (nodes or defect rows)
+// and its threads walk the block's output slots in order, so loads and stores are
+// coalesced; the period of a slot comes from a single-precision product (exact for the
+// block-local indices, see kkt_div) instead of an integer division, and the X / U templates
+// sit in shared memory.  Moved values are copied bit for bit; the (1,1) diagonal gets
+// sigma_x + delta_w, the constraint diagonal is -delta_c.
+constexpr int KKT_ROWS = 1024;
+enum { KR_X = 0, KR_U = 1, KR_TF = 2, KR_BND = 3, KR_DEF = 4 };
+
+// floor(i / P) for block-local i < KKT_ROWS * P, P <= 1024: (i + 1/2) / P lies at least 1/(2P) >=
+// 2^-11 from an integer; its single-precision value (below KKT_ROWS = 2^10, computed from
+// 1/P rounded to nearest and a product rounded toward zero) is off by less than 2^-12.
+__device__ __forceinline__ uint32_t kkt_div(uint32_t i, float invP) {
+  return (uint32_t)__fmul_rz((float)i + 0.5f, invP);
+}
+
+__global__ void __launch_bounds__(256) k_kkt_values(const __grid_constant__ KktArgs a) {
+  __shared__ int16_t s_src[KKT_TMAX], s_a[KKT_TMAX];
+  __shared__ uint8_t s_diag[KKT_TMAX];
+  // the region of this block: the last one whose first block is <= blockIdx.x
+  int lo = 0, hi = a.nreg - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (a.reg[mid].block0 <= blockIdx.x) lo = mid; else hi = mid - 1;
+  }
+  const KRegion R = a.reg[lo];
+  const uint32_t chunk = blockIdx.x - R.block0;
+  if (R.kind == KR_TF || R.kind == KR_BND) {  // short regions: slot by slot
+    const uint32_t i1 = min(R.len, (chunk + 1) * 256u * KKT_ROWS);
+    for (uint32_t i = chunk * 256u * KKT_ROWS + threadIdx.x; i < i1; i += blockDim.x) {
+      double v;
+      if (R.kind == KR_TF) {
+        if (i + 1 < R.len) v = __ldg(a.hv + R.src + i);
+        else v = (a.sx ? __ldg(a.sx + a.n - 1) : 0.0) + a.dw;
+      } else {
+        v = (i & 1) ? -a.dc : __ldg(a.jv + (i >> 1));
+      }
+      a.out[R.out + i] = v;
+    }
+    return;
+  }
+  const uint32_t P = R.period;
+  if (R.kind != KR_DEF) {  // the node template of the X or U rows
+    const int toff = (R.kind == KR_U) ? KKT_TMAX : 0;
+    for (uint32_t p = threadIdx.x; p < P; p += blockDim.x) {
+      s_src[p] = a.ksrc[toff + p];
+      s_a[p] = a.ka[toff + p];
+      s_diag[p] = a.ka[toff + p] == a.kb[toff + p];
+    }
+    __syncthreads();
+  }
+  const float invP = 1.0f / (float)P;
+  const uint32_t nper = R.len / P;   // nodes or defect rows of the region
+  const uint32_t c0 = chunk * KKT_ROWS;
+  const uint32_t nloc = min((uint32_t)KKT_ROWS, nper - c0) * P;
+  const double* src0 = ((R.kind == KR_DEF) ? a.jv : a.hv) + R.src + (int64_t)c0 * R.stride;
+  double* out0 = a.out + R.out + (int64_t)c0 * P;
+#pragma unroll 4
+  for (uint32_t i = threadIdx.x; i < nloc; i += blockDim.x) {
+    const uint32_t jl = kkt_div(i, invP);
+    const uint32_t e = i - jl * P;
+    double v;
+    if (R.kind == KR_DEF) {
+      v = (e + 1 == P) ? -a.dc : __ldg(src0 + (i - jl));   // i - jl: the diagonals before this slot
+    } else {
+      const int sp = s_src[e];
+      v = (sp >= 0) ? __ldg(src0 + (int64_t)R.stride * jl + sp) : 0.0;
+      if (s_diag[e]) {
+        const int64_t j = (int64_t)c0 + jl;
+        const int64_t row = (R.kind == KR_X) ? (int64_t)a.nx * j + s_a[e] : a.uoff + (int64_t)a.nu * j + (s_a[e] - a.nx);
+        v = v + ((a.sx ? __ldg(a.sx + row) : 0.0) + a.dw);
+      }
+    }
+    out0[i] = v;
+  }
+}
+
+// Structure: one thread per slot, (row, col) decoded from the same layout.
+__global__ void k_kkt_structure(const __grid_constant__ KktArgs a) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < a.nnzk; s += stride) {
-    double v = 0.0;
-    int64_t row = 0, col = 0;
-    bool diag = false;          // (1,1)-block diagonal: add sigma_x + delta_w
+    int64_t row, col;
     if (s < a.kb_t) {           // node rows of the (1,1) block
       const bool xs = s < a.kb_u;
       const int kt = xs ? a.kx : a.ku;
       const int64_t rel = xs ? s : s - a.kb_u;
       const int64_t j = rel / kt;
       const int p = (int)(rel - j * kt) + (xs ? 0 : KKT_TMAX);
-      const int src = a.ksrc[p];
       row = kkt_col(a, j, a.ka[p]);
       col = kkt_col(a, j, a.kb[p]);
-      diag = a.ka[p] == a.kb[p];
-      if (VALUES && src >= 0) v = __ldg(a.hv + (xs ? (int64_t)a.hx * j : a.hbase_u + (int64_t)a.hu * j) + src);
     } else if (s < a.kb_c) {    // the free final time's row: H's tf row, then its diagonal
       const int64_t r = s - a.kb_t, tlen = (int64_t)(a.tx + a.tu) * (a.N + 1);
       row = a.n - 1;
       if (r < tlen) {
-        if (VALUES) v = __ldg(a.hv + a.hbase_t + r);
-        if (!VALUES) {
-          const int64_t xpart = (a.N + 1) * a.tx;
-          int64_t j;
-          int e;
-          if (r < xpart) { j = r / a.tx; e = (int)(r - j * a.tx); }
-          else { j = (r - xpart) / a.tu; e = a.tx + (int)(r - xpart - j * a.tu); }
-          col = kkt_col(a, j, a.tcol[e]);
-        }
+        const int64_t xpart = (a.N + 1) * a.tx;
+        int64_t j;
+        int e;
+        if (r < xpart) { j = r / a.tx; e = (int)(r - j * a.tx); }
+        else { j = (r - xpart) / a.tu; e = a.tx + (int)(r - xpart - j * a.tu); }
+        col = kkt_col(a, j, a.tcol[e]);
       } else {
         col = a.n - 1;
-        diag = true;
       }
-    } else if (s < a.kcbase[0]) {  // boundary rows: the unit entry, then -delta_c
+    } else if (s < a.kcbase[0]) {  // boundary rows: the unit entry, then the diagonal
       const int64_t r = (s - a.kb_c) >> 1;
       row = a.n + r;
-      if ((s - a.kb_c) & 1) {
-        col = row;
-        v = -a.dc;
-      } else {
-        col = (r < a.nx) ? r : (int64_t)a.nx * a.N + a.fin[r - a.nx];
-        if (VALUES) v = __ldg(a.jv + r);
-      }
-    } else {                       // defect rows: the Jacobian row, then -delta_c
+      if ((s - a.kb_c) & 1) col = row;
+      else col = (r < a.nx) ? r : (int64_t)a.nx * a.N + a.fin[r - a.nx];
+    } else {                       // defect rows: the Jacobian row, then the diagonal
       const int k = kkt_comp(a, s);
       const int32_t* t = a.tmpl + RT_STRIDE * k;
       const int rx = t[0], ru = t[1];
@@ -105,27 +184,15 @@ __global__ void k_kkt(const __grid_constant__ KktArgs a) {
       const int64_t j = rel / (cnt + 1);
       const int e = (int)(rel - j * (cnt + 1));
       row = a.n + a.nb + (int64_t)k * a.N + j;
-      if (e == cnt) {
-        col = row;
-        v = -a.dc;
-      } else {
-        if (VALUES) v = __ldg(a.jv + a.jbase[k] + j * cnt + e);
-        if (!VALUES) {
-          if (e == 2 * (rx + ru)) col = a.n - 1;
-          else if (e < rx) col = (int64_t)a.nx * j + t[2 + e];
-          else if (e < 2 * rx) col = (int64_t)a.nx * (j + 1) + t[2 + (e - rx)];
-          else if (e < 2 * rx + ru) col = a.uoff + (int64_t)a.nu * j + t[2 + RT_XV + (e - 2 * rx)];
-          else col = a.uoff + (int64_t)a.nu * (j + 1) + t[2 + RT_XV + (e - 2 * rx - ru)];
-        }
-      }
+      if (e == cnt) col = row;
+      else if (e == 2 * (rx + ru)) col = a.n - 1;
+      else if (e < rx) col = (int64_t)a.nx * j + t[2 + e];
+      else if (e < 2 * rx) col = (int64_t)a.nx * (j + 1) + t[2 + (e - rx)];
+      else if (e < 2 * rx + ru) col = a.uoff + (int64_t)a.nu * j + t[2 + RT_XV + (e - 2 * rx)];
+      else col = a.uoff + (int64_t)a.nu * (j + 1) + t[2 + RT_XV + (e - 2 * rx - ru)];
     }
-    if (VALUES) {
-      if (diag) v = v + ((a.sx ? __ldg(a.sx + row) : 0.0) + a.dw);
-      a.out[s] = v;
-    } else {
-      a.rows[s] = (int32_t)row;
-      a.cols[s] = (int32_t)col;
-    }
+    a.rows[s] = (int32_t)row;
+    a.cols[s] = (int32_t)col;
   }
 }
 
@@ -146,6 +213,31 @@ static ocp_status kkt_fill(const ocp* h, KktArgs& a) {
     a.ka[KKT_TMAX + i] = (int16_t)P.kut[i].a;
     a.kb[KKT_TMAX + i] = (int16_t)P.kut[i].b;
   }
+  if (h->nx + 4 > KKT_MAXREG) return OCP_EDIM;
+  auto add = [&](int kind, int64_t out, int64_t len, uint32_t period, int64_t src, uint32_t stride) {
+    if (len <= 0) return;
+    KRegion& r = a.reg[a.nreg++];
+    r.kind = kind; r.out = out; r.len = (uint32_t)len; r.period = period; r.src = src; r.stride = stride;
+  };
+  add(KR_X, 0, P.kb_u, (uint32_t)a.kx, 0, (uint32_t)P.hx);
+  add(KR_U, P.kb_u, P.kb_t - P.kb_u, (uint32_t)a.ku, P.hbase_u, (uint32_t)P.hu);
+  add(KR_TF, P.kb_t, P.kb_c - P.kb_t, 1, P.hbase_t, 1);
+  add(KR_BND, P.kb_c, 2 * P.nb, 2, 0, 1);
+  for (int k = 0; k < h->nx; ++k)
+    add(KR_DEF, P.kcbase[k], P.kcbase[k + 1] - P.kcbase[k], (uint32_t)(P.row_count(k) + 1), P.jbase[k],
+        (uint32_t)P.row_count(k));
+  // blocks of the values kernel: KKT_ROWS periods of a row region per block, or
+  // blockDim * KKT_ROWS slots of a short region
+  uint32_t b = 0;
+  for (int r = 0; r < a.nreg; ++r) {
+    KRegion& R = a.reg[r];
+    if (R.period > 1024) return OCP_EDIM;  // kkt_div's exactness bound
+    R.block0 = b;
+    const int64_t nb = (R.kind == KR_TF || R.kind == KR_BND) ? ((int64_t)R.len + 256 * KKT_ROWS - 1) / (256 * KKT_ROWS)
+                                                              : ((int64_t)(R.len / R.period) + KKT_ROWS - 1) / KKT_ROWS;
+    b += (uint32_t)nb;
+  }
+  a.nblocks = b;
   return OCP_OK;
 }
 
@@ -173,7 +265,7 @@ ocp_status ocp_kkt_structure(ocp_t* h, int32_t* rows, int32_t* cols, void* strea
   KktArgs a;
   if (kkt_fill(h, a) != OCP_OK) return set_err(h, OCP_EDIM, "KKT matrix too large for the int32 interface");
   a.rows = rows; a.cols = cols;
-  k_kkt<false><<<kkt_grid(h, a.nnzk), 256, 0, (cudaStream_t)stream>>>(a);
+  k_kkt_structure<<<kkt_grid(h, a.nnzk), 256, 0, (cudaStream_t)stream>>>(a);
   return cuda_err(h, cudaGetLastError(), "KKT structure launch");
 }
 
@@ -186,7 +278,7 @@ ocp_status ocp_kkt_values(ocp_t* h, const double* hvals, const double* jvals, co
   KktArgs a;
   if (kkt_fill(h, a) != OCP_OK) return set_err(h, OCP_EDIM, "KKT matrix too large for the int32 interface");
   a.hv = hvals; a.jv = jvals; a.sx = sigma_x; a.out = kvals; a.dw = delta_w; a.dc = delta_c;
-  k_kkt<true><<<kkt_grid(h, a.nnzk), 256, 0, (cudaStream_t)stream>>>(a);
+  k_kkt_values<<<a.nblocks, 256, 0, (cudaStream_t)stream>>>(a);
   return cuda_err(h, cudaGetLastError(), "KKT values launch");
 }
 
