@@ -132,6 +132,9 @@ struct Prob {
   const int32_t* fin_comp;
   // linear terminal (Mayer) cost sum_k mayer_k X_{N,k} added to the objective (nullable, nx)
   const double* mayer;
+  // one-step scheme: 0 trapezoidal (controls on N+1 nodes), 1 forward Euler (paper Sec. 3:
+  // controls U_0..U_{N-1}, rectangle-rule cost)
+  int32_t scheme, pad2;
 };
 
 template <class S> struct JEnt { int k, v; S val; };      // d f_k / d z_v
@@ -525,7 +528,8 @@ inline double cost_hess_diag(const Prob& P, int a) {  // d2 f0 / d z_a^2 (consta
 // ---------------------------------------------------------------------------------------
 struct Layout {
   int nx, nu, nz;
-  int64_t N, n, m, nb, tau;   // tau: column of the free final time, or -1
+  bool euler;
+  int64_t N, nun, n, m, nb, tau;   // nun: nodes with controls; tau: column of tf, or -1
   std::vector<int> fin;       // components with a final row, ascending
   explicit Layout(const Prob& P) {
     nx = P.nx; nu = P.nu; nz = nx + nu; N = P.N;
@@ -533,7 +537,9 @@ struct Layout {
       if (P.fin_comp) fin.assign(P.fin_comp, P.fin_comp + P.nfin);
       else for (int k = 0; k < nx; ++k) fin.push_back(k);
     }
-    n = (int64_t)nz * (N + 1) + (P.free_tf ? 1 : 0);
+    euler = P.scheme == 1;
+    nun = euler ? N : N + 1;
+    n = (int64_t)nx * (N + 1) + (int64_t)nu * nun + (P.free_tf ? 1 : 0);
     tau = P.free_tf ? n - 1 : -1;
     nb = (int64_t)nx + (int64_t)fin.size();
     m = nb + (int64_t)nx * N;
@@ -567,8 +573,131 @@ inline double omega(const Prob& P, int64_t j) {
 
 template <class S> void params_of(const Prob& P, S* p) { for (int i = 0; i < 8; ++i) p[i] = S(P.par[i]); }
 
+// Sparse matrices in COO, one entry per structural nonzero, sorted by (row, col).
+template <class S> struct Coo { std::vector<int64_t> row, col; std::vector<S> val; };
+
+// ---- Forward Euler (paper Sec. 3): defects X_{i+1} - X_i - h f(X_i, U_i), i = 0..N-1, the
+// cost g(X_N) + sum_{i<N} h f0(X_i, U_i), unknowns X_0..X_N, U_0..U_{N-1}.  Row (k, i) involves
+// z_i (through f) and X_{i+1,k} (identity); node i's Hessian block collects its own rows only.
+// With a free final time, dc/dtf = -f_k(z_i) / N and dF/dtf = sum_{i<N} f0(z_i) / N.
+template <class S> S euler_objective(const Prob& P, const S* x) {
+  Layout L(P);
+  const S h = step_h(P, L, x);
+  std::vector<S> z(L.nz);
+  Neumaier<S> acc;
+  for (int64_t j = 0; j < L.N; ++j) {
+    gather_node(L, x, j, z.data());
+    acc.add(h * cost_f0(P, z.data(), node_time(P, j)));
+  }
+  if (P.mayer)
+    for (int k = 0; k < L.nx; ++k) acc.add(S(P.mayer[k]) * x[L.colX(L.N, k)]);
+  return acc.result();
+}
+
+template <class S> void euler_constraints(const Prob& P, const S* p, const S* x, S* c) {
+  Layout L(P);
+  const S h = step_h(P, L, x);
+  for (int k = 0; k < L.nx; ++k) c[k] = x[L.colX(0, k)];
+  for (size_t i = 0; i < L.fin.size(); ++i) c[L.nx + i] = x[L.colX(L.N, L.fin[i])];
+  std::vector<S> f(L.nx), z(L.nz);
+  for (int64_t j = 0; j < L.N; ++j) {
+    gather_node(L, x, j, z.data());
+    model_f(P, p, z.data(), f.data());
+    for (int k = 0; k < L.nx; ++k) c[L.defect_row(k, j)] = (x[L.colX(j + 1, k)] - x[L.colX(j, k)]) - h * f[k];
+  }
+}
+
+template <class S> void euler_gradient(const Prob& P, const S* x, S* g) {
+  Layout L(P);
+  const S h = step_h(P, L, x);
+  std::vector<S> z(L.nz), gz(L.nz);
+  Neumaier<S> gt;
+  for (int64_t j = 0; j < L.N; ++j) {
+    gather_node(L, x, j, z.data());
+    cost_grad(P, z.data(), node_time(P, j), gz.data());
+    for (int v = 0; v < L.nz; ++v) g[L.col(j, v)] = h * gz[v];
+    if (L.tau >= 0) gt.add(cost_f0(P, z.data(), node_time(P, j)) / S((double)L.N));
+  }
+  for (int k = 0; k < L.nx; ++k) g[L.colX(L.N, k)] = S(P.mayer ? P.mayer[k] : 0.0);
+  if (L.tau >= 0) g[L.tau] = gt.result();
+}
+
+template <class S> void euler_jacobian(const Prob& P, const S* p, const S* x, Coo<S>& J) {
+  Layout L(P);
+  const S h = step_h(P, L, x);
+  std::vector<std::vector<JEnt<S>>> nodeJ((size_t)L.N);
+  std::vector<S> f((size_t)L.nx * L.N), z(L.nz);
+  for (int64_t j = 0; j < L.N; ++j) {
+    gather_node(L, x, j, z.data());
+    model_jac(P, p, z.data(), nodeJ[j]);
+    model_f(P, p, z.data(), &f[(size_t)L.nx * j]);
+  }
+  auto emit = [&](int64_t r, int64_t c, S v) { J.row.push_back(r); J.col.push_back(c); J.val.push_back(v); };
+  for (int k = 0; k < L.nx; ++k) emit(k, L.colX(0, k), S(1.0));
+  for (size_t i = 0; i < L.fin.size(); ++i) emit(L.nx + (int64_t)i, L.colX(L.N, L.fin[i]), S(1.0));
+  std::vector<std::pair<int64_t, S>> ent;
+  for (int k = 0; k < L.nx; ++k)
+    for (int64_t j = 0; j < L.N; ++j) {
+      ent.clear();
+      for (auto& e : nodeJ[j]) if (e.k == k) ent.push_back({L.col(j, e.v), S(0.0) - h * e.val});
+      ent.push_back({L.colX(j, k), S(-1.0)});
+      ent.push_back({L.colX(j + 1, k), S(1.0)});
+      if (L.tau >= 0) ent.push_back({L.tau, S(0.0) - f[(size_t)L.nx * j + k] / S((double)L.N)});
+      std::stable_sort(ent.begin(), ent.end(), [](const auto& a, const auto& b) { return a.first < b.first; });
+      const int64_t r = L.defect_row(k, j);
+      for (size_t i = 0; i < ent.size();) {
+        S v = ent[i].second;
+        size_t t = i + 1;
+        while (t < ent.size() && ent[t].first == ent[i].first) { v = v + ent[t].second; ++t; }
+        emit(r, ent[i].first, v);
+        i = t;
+      }
+    }
+}
+
+template <class S> void euler_hessian(const Prob& P, const S* p, const S* x, const S* y, S sigma, Coo<S>& H) {
+  Layout L(P);
+  const S h = step_h(P, L, x);
+  std::vector<S> z(L.nz), gz(L.nz);
+  std::vector<HEnt<S>> he;
+  std::vector<JEnt<S>> je;
+  struct Trip { int64_t r, c; S v; };
+  std::vector<Trip> all;
+  for (int64_t j = 0; j < L.N; ++j) {
+    gather_node(L, x, j, z.data());
+    he.clear();
+    model_hess(P, p, z.data(), he);
+    std::map<std::pair<int, int>, S> blk;
+    for (int a = 0; a < L.nz; ++a)
+      if (cost_hess_diag(P, a) != 0.0) blk[{a, a}] = sigma * h * S(cost_hess_diag(P, a));
+    for (auto& e : he) {
+      if (!blk.count({e.a, e.b})) blk[{e.a, e.b}] = S(0.0);
+      blk[{e.a, e.b}] = blk[{e.a, e.b}] + y[L.defect_row(e.k, j)] * (S(0.0) - h * e.val);
+    }
+    for (auto& kv : blk) all.push_back({L.col(j, kv.first.first), L.col(j, kv.first.second), kv.second});
+    if (L.tau >= 0) {
+      std::map<int, S> trow;
+      cost_grad(P, z.data(), node_time(P, j), gz.data());
+      for (int v = 0; v < L.nz; ++v)
+        if (cost_hess_diag(P, v) != 0.0) trow[v] = sigma * gz[v] / S((double)L.N);
+      je.clear();
+      model_jac(P, p, z.data(), je);
+      for (auto& e : je) {
+        if (!trow.count(e.v)) trow[e.v] = S(0.0);
+        trow[e.v] = trow[e.v] + y[L.defect_row(e.k, j)] * (S(0.0) - e.val / S((double)L.N));
+      }
+      for (auto& kv : trow) all.push_back({L.tau, L.col(j, kv.first), kv.second});
+    }
+  }
+  std::stable_sort(all.begin(), all.end(), [](const Trip& a, const Trip& b) {
+    return a.r != b.r ? a.r < b.r : a.c < b.c;
+  });
+  for (auto& t : all) { H.row.push_back(t.r); H.col.push_back(t.c); H.val.push_back(t.v); }
+}
+
 // Objective F = sum_j w_j f0(z_j) (trapezoidal Lagrange cost) + sum_k mayer_k X_{N,k}
 template <class S> S objective(const Prob& P, const S* x) {
+  if (P.scheme == 1) return euler_objective(P, x);
   Layout L(P);
   const S h = step_h(P, L, x);
   std::vector<S> z(L.nz);
@@ -584,6 +713,7 @@ template <class S> S objective(const Prob& P, const S* x) {
 
 // Constraints: initial rows, final rows, then trapezoidal defects, component-major.
 template <class S> void constraints(const Prob& P, const S* p, const S* x, S* c) {
+  if (P.scheme == 1) return euler_constraints(P, p, x, c);
   Layout L(P);
   const S h = step_h(P, L, x);
   for (int k = 0; k < L.nx; ++k) c[k] = x[L.colX(0, k)];
@@ -603,6 +733,7 @@ template <class S> void constraints(const Prob& P, const S* p, const S* x, S* c)
 // Gradient of F: node-local w_j grad f0, the Mayer weights at X_N, and with a free final time
 // dF/dtf = sum_j omega_j f0(z_j) (the Lagrange cost is linear in tf through w_j = tf omega_j).
 template <class S> void gradient(const Prob& P, const S* x, S* g) {
+  if (P.scheme == 1) return euler_gradient(P, x, g);
   Layout L(P);
   const S h = step_h(P, L, x);
   std::vector<S> z(L.nz), gz(L.nz);
@@ -619,9 +750,9 @@ template <class S> void gradient(const Prob& P, const S* x, S* g) {
 }
 
 // Jacobian in COO, one entry per structural nonzero, sorted by (row, col).
-template <class S> struct Coo { std::vector<int64_t> row, col; std::vector<S> val; };
 
 template <class S> void jacobian(const Prob& P, const S* p, const S* x, Coo<S>& J) {
+  if (P.scheme == 1) return euler_jacobian(P, p, x, J);
   Layout L(P);
   const S h = step_h(P, L, x);
   // derivative entries and values of f at every node
@@ -668,6 +799,7 @@ template <class S> void jacobian(const Prob& P, const S* p, const S* x, Coo<S>& 
 // there is no (tf, tf) entry); its structural columns are those of the model's Jacobian
 // entries and of the non-zero cost weights.
 template <class S> void hessian(const Prob& P, const S* p, const S* x, const S* y, S sigma, Coo<S>& H) {
+  if (P.scheme == 1) return euler_hessian(P, p, x, y, sigma, H);
   Layout L(P);
   const S h = step_h(P, L, x);
   std::vector<S> z(L.nz), gz(L.nz);
@@ -743,14 +875,15 @@ template <class S> S dpar_vjp(const Prob& P, const S* p, const S* x, const S* w)
   Layout L(P);
   const S h = step_h(P, L, x);
   std::vector<S> d((size_t)L.nx * (L.N + 1)), z(L.nz);
-  for (int64_t j = 0; j <= L.N; ++j) {
+  for (int64_t j = 0; j < L.nun; ++j) {  // (Euler: node N has no control and no f term)
     gather_node(L, x, j, z.data());
     vdp_dpar(p, z.data(), &d[(size_t)L.nx * j]);
   }
   Neumaier<S> acc;
   for (int k = 0; k < L.nx; ++k)
     for (int64_t j = 0; j < L.N; ++j) {
-      const S dc = S(0.0) - h * (d[(size_t)L.nx * j + k] + d[(size_t)L.nx * (j + 1) + k]) / S(2.0);
+      const S dc = L.euler ? S(0.0) - h * d[(size_t)L.nx * j + k]
+                           : S(0.0) - h * (d[(size_t)L.nx * j + k] + d[(size_t)L.nx * (j + 1) + k]) / S(2.0);
       acc.add(w[L.defect_row(k, j)] * dc);
     }
   return acc.result();
@@ -794,6 +927,7 @@ inline void kkt_assemble(const Layout& L, const Coo<double>& H, const Coo<double
 
 int check(const Prob& P) {
   if (P.N < 1 || !(P.T > 0.0)) return 2;
+  if (P.scheme != 0 && P.scheme != 1) return 2;
   // the tracking reference is tabulated at t_j = j T / N: not with a free final time
   if (P.free_tf && (P.xslope || P.xamp)) return 2;
   if (P.has_final && P.fin_comp) {
@@ -843,7 +977,9 @@ int orc_dims(const Prob* P, int64_t* n, int64_t* m, int64_t* nnzj, int64_t* nnzh
     for (auto& e : je) if (e.k == k) cols.push_back(e.v);
     cols.push_back(k);
     std::sort(cols.begin(), cols.end());
-    perrow += 2 * (int64_t)(std::unique(cols.begin(), cols.end()) - cols.begin());
+    const int64_t side = (int64_t)(std::unique(cols.begin(), cols.end()) - cols.begin());
+    // trapezoid: both nodes' sides; Euler: node i's side plus the identity on X_{i+1,k}
+    perrow += L.euler ? side + 1 : 2 * side;
   }
   // a free final time adds one entry (the tf column) to every defect row
   *nnzj = L.nb + perrow * L.N + (L.tau >= 0 ? (int64_t)L.nx * L.N : 0);
@@ -852,13 +988,13 @@ int orc_dims(const Prob* P, int64_t* n, int64_t* m, int64_t* nnzj, int64_t* nnzh
   for (int a = 0; a < L.nz; ++a) if (cost_hess_diag(*P, a) != 0.0) keys.push_back({a, a});
   for (auto& e : he) keys.push_back({e.a, e.b});
   std::sort(keys.begin(), keys.end());
-  *nnzh = (int64_t)(std::unique(keys.begin(), keys.end()) - keys.begin()) * (L.N + 1);
+  *nnzh = (int64_t)(std::unique(keys.begin(), keys.end()) - keys.begin()) * L.nun;
   if (L.tau >= 0) {  // the tf row: model Jacobian columns and cost columns of every node
     std::vector<int> tc;
     for (auto& e : je) tc.push_back(e.v);
     for (int a = 0; a < L.nz; ++a) if (cost_hess_diag(*P, a) != 0.0) tc.push_back(a);
     std::sort(tc.begin(), tc.end());
-    *nnzh += (int64_t)(std::unique(tc.begin(), tc.end()) - tc.begin()) * (L.N + 1);
+    *nnzh += (int64_t)(std::unique(tc.begin(), tc.end()) - tc.begin()) * L.nun;
   }
   return 0;
 }

@@ -20,7 +20,8 @@ class _Prob(C.Structure):
                 ("N", C.c_int64), ("T", C.c_double), ("par", C.c_double * 8), ("npar", C.c_int32),
                 ("pad", C.c_int32), ("q", C.c_void_p), ("r", C.c_void_p), ("xref", C.c_void_p),
                 ("uref", C.c_void_p), ("xslope", C.c_void_p), ("xamp", C.c_void_p), ("xfreq", C.c_void_p),
-                ("free_tf", C.c_int32), ("nfin", C.c_int32), ("fin_comp", C.c_void_p), ("mayer", C.c_void_p)]
+                ("free_tf", C.c_int32), ("nfin", C.c_int32), ("fin_comp", C.c_void_p), ("mayer", C.c_void_p),
+                ("scheme", C.c_int32), ("pad2", C.c_int32)]
 
 
 _lib = None
@@ -72,6 +73,7 @@ class Problem:
             p.fin_comp = _ptr(self._fin)
         self._mayer = None if w.get("mayer") is None else np.ascontiguousarray(w["mayer"], dtype=np.float64)
         p.mayer = _ptr(self._mayer)
+        p.scheme = {"trapezoid": 0, "euler": 1}[w.get("scheme", "trapezoid")]
         self.s = p
         n, m, nj, nh = (C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64())
         st = lib().orc_dims(C.byref(p), C.byref(n), C.byref(m), C.byref(nj), C.byref(nh))

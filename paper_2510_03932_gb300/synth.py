@@ -65,7 +65,7 @@ DIST = {
 
 
 def draw_instance(seed: int, kind: str, nx: int, nu: int, N: int, m: int,
-                  stream: Stream | None = None, free_tf: bool = False) -> dict:
+                  stream: Stream | None = None, free_tf: bool = False, unodes: int | None = None) -> dict:
     """x = [X (node-major, nx per node); U (nu per node) (; tf)], y ~ N(0,1), vn ~ U(-1,1),
     vm ~ N(0,1).  X is uniform on one range, or on a range per state component ("xc")."""
     s = stream if stream is not None else Stream(seed)
@@ -76,7 +76,7 @@ def draw_instance(seed: int, kind: str, nx: int, nu: int, N: int, m: int,
         X = (lo + (hi - lo) * s.uniform(nx * (N + 1)).reshape(N + 1, nx)).ravel()
     else:
         X = s.uniform(nx * (N + 1), *d["x"])
-    U = s.uniform(nu * (N + 1), *d["u"])
+    U = s.uniform(nu * ((N + 1) if unodes is None else unodes), *d["u"])
     parts = [X, U]
     if free_tf:
         parts.append(s.uniform(1, *d["tf"]))
@@ -167,17 +167,22 @@ def final_rows(w: dict) -> int:
     return w["nx"] if w.get("xf") is not None else 0
 
 
+def control_nodes(w: dict) -> int:
+    """Nodes carrying a control: N + 1 (trapezoidal scheme) or N (forward Euler)."""
+    return w["N"] if w.get("scheme") == "euler" else w["N"] + 1
+
+
 def dims(w: dict):
-    """(n, m) of the transcription: n = (nx+nu)(N+1) (+1 for a free final time);
-    m = nx + final rows + nx N."""
-    n = (w["nx"] + w["nu"]) * (w["N"] + 1) + (1 if w.get("free_tf") else 0)
+    """(n, m) of the transcription: n = nx (N+1) + nu (controlled nodes) (+1 for a free final
+    time); m = nx + final rows + nx N."""
+    n = w["nx"] * (w["N"] + 1) + w["nu"] * control_nodes(w) + (1 if w.get("free_tf") else 0)
     return n, w["nx"] + final_rows(w) + w["nx"] * w["N"]
 
 
 def draw(w: dict, seed: int | None = None) -> dict:
     n, m = dims(w)
     return draw_instance(w["seed"] if seed is None else seed, w["dist"], w["nx"], w["nu"], w["N"], m,
-                         free_tf=bool(w.get("free_tf")))
+                         free_tf=bool(w.get("free_tf")), unodes=control_nodes(w))
 
 
 def batch_workloads(count=256, nmin=500, nmax=50000, seed=1004):

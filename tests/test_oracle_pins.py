@@ -14,11 +14,17 @@ from conftest import read_golden
 from oracle import oracle as O
 from paper_2510_03932_gb300 import synth
 
-MODELS = ["vdp_n1e3", "cartpole_n1e5", "heat_n2e4", "dint", "quadrotor_n1e3", "goddard_n1e3"]
+MODELS = ["vdp_n1e3", "cartpole_n1e5", "heat_n2e4", "dint", "quadrotor_n1e3", "goddard_n1e3",
+          "vdp_n1e3:euler", "cartpole_n1e5:euler", "dint:euler", "quadrotor_n1e3:euler", "heat_n2e4:euler"]
 
 
 def small(name, N):
-    return synth.with_horizon(synth.workload(name), N)
+    """A workload at horizon N; the suffix ":euler" selects the forward Euler scheme."""
+    base, _, scheme = name.partition(":")
+    w = synth.with_horizon(synth.workload(base), N)
+    if scheme:
+        w["scheme"] = scheme
+    return w
 
 
 def rand_point(w, rng):
@@ -29,7 +35,7 @@ def rand_point(w, rng):
         X = np.concatenate([rng.uniform(lo, hi, N1)[:, None] for lo, hi in d["xc"]], axis=1).ravel()
     else:
         X = rng.uniform(*d["x"], w["nx"] * N1)
-    parts = [X, rng.uniform(*d["u"], w["nu"] * N1)]
+    parts = [X, rng.uniform(*d["u"], w["nu"] * synth.control_nodes(w))]
     if w.get("free_tf"):
         parts.append(rng.uniform(*d["tf"], 1))
     return np.concatenate(parts), rng.standard_normal(m)
@@ -42,7 +48,11 @@ def rand_point(w, rng):
 NODE_COUNTS = {"vdp": (10, 4), "cartpole": (22, 7), "heat": (382, 65), "dint": (8, 1), "quadrotor": (68, 20),
                # Goddard: rows r {r, v | r, v | tf}, v {r, v, m | r, v, m | u | u | tf}, m {m | m | u | u | tf};
                # Hessian block (r,r) (v,r) (v,v) (m,r) (m,v) (m,m) (u,m) plus the tf row on r, v, m, u
-               "goddard": (19, 11)}
+               "goddard": (19, 11),
+               # forward Euler: one node's side of each row plus the identity on X_{i+1,k}; the
+               # Hessian blocks of the N nodes that carry a control
+               "vdp:euler": (7, 4), "cartpole:euler": (15, 7), "dint:euler": (6, 1), "quadrotor:euler": (43, 20),
+               "heat:euler": (255, 65)}
 
 
 @pytest.mark.parametrize("name", MODELS)
@@ -52,11 +62,13 @@ def test_counts_closed_form(name, N):
     P = O.Problem(w)
     nx, nu = w["nx"], w["nu"]
     nb = nx + synth.final_rows(w)
-    jn, hn = NODE_COUNTS[w["model"]]
-    assert P.n == (nx + nu) * (N + 1) + (1 if w.get("free_tf") else 0)
+    euler = w.get("scheme") == "euler"
+    jn, hn = NODE_COUNTS[w["model"] + (":euler" if euler else "")]
+    nun = N if euler else N + 1
+    assert P.n == nx * (N + 1) + nu * nun + (1 if w.get("free_tf") else 0)
     assert P.m == nb + nx * N
     assert P.nnzj == nb + jn * N
-    assert P.nnzh == hn * (N + 1)
+    assert P.nnzh == hn * nun
 
 
 @pytest.mark.parametrize("name", MODELS)
@@ -89,7 +101,7 @@ def dense_hess_cs(P, x, y, sigma):
 @pytest.mark.parametrize("name", MODELS)
 def test_structure_matches_bruteforce_detection(name):
     """An entry is structural iff it is nonzero at one of 8 random points (complex step)."""
-    w = small(name, 2 if name == "heat_n2e4" else 3)
+    w = small(name, 2 if name.startswith("heat") else 3)
     P = O.Problem(w)
     rng = np.random.default_rng(7)
     jmask = np.zeros((P.m, P.n), bool)
@@ -111,7 +123,7 @@ def test_structure_matches_bruteforce_detection(name):
 # ---------------------------------------------------------------------------------------
 @pytest.mark.parametrize("name", MODELS)
 def test_jacobian_gradient_hessian_vs_complex_step(name):
-    w = small(name, 2 if name == "heat_n2e4" else 4)
+    w = small(name, 2 if name.startswith("heat") else 4)
     P = O.Problem(w)
     rng = np.random.default_rng(11)
     x, y = rand_point(w, rng)
@@ -429,12 +441,50 @@ def test_goddard_mayer_objective_and_final_row():
     assert jr[3] == 3 and jc[3] == 3 * 6 + 2 and ev["jac"][3] == 1.0
 
 
+@pytest.mark.parametrize("N", [10, 100, 1000])
+def test_euler_local_error_and_rectangle_cost_closed_forms(N):
+    """Forward Euler on the double integrator (paper Sec. 3 scheme).  At the exact solution of
+    x1' = x2, x2' = u with u = 1, x(0) = 0 (x1 = t^2/2, x2 = t) the defects are the local
+    truncation errors h^2 x1''/2 = h^2/2 and 0.  The rectangle rule of 1/2 u^2 with
+    u_i = a + b t_i (left end points) sums to h/2 [N a^2 + a b h N (N-1) + b^2 h^2 (N-1) N (2N-1) / 6]."""
+    w = small("dint:euler", N)
+    P = O.Problem(w)
+    h = 1.0 / N
+    t = np.arange(N + 1) * h
+    X = np.stack([t**2 / 2, t], 1).ravel()
+    x = np.concatenate([X, np.ones(N)])
+    ev = O.evaluate(P, x, np.zeros(P.m), 1.0)
+    nb = 4
+    np.testing.assert_allclose(ev["c"][nb:nb + N], h * h / 2, rtol=1e-9, atol=1e-16)
+    np.testing.assert_allclose(ev["c"][nb + N:], 0.0, atol=1e-15)
+    a, b = 0.7, -1.3
+    x = np.concatenate([X, a + b * t[:N]])
+    F = O.evaluate(P, x, np.zeros(P.m), 1.0)["f"]
+    expect = h / 2 * (N * a * a + a * b * h * N * (N - 1) + b * b * h * h * (N - 1) * N * (2 * N - 1) / 6)
+    assert abs(F - expect) < 1e-13 * abs(expect)
+    # the Jacobian of the linear dynamics: -1 / +1 identities and -h couplings, no U_N column
+    jr, jc = O.jac_structure(P)
+    assert set(np.unique(ev["jac"])) <= {1.0, -1.0, -h}
+    assert jc.max() < P.n and P.n == 2 * (N + 1) + N
+
+
+def test_euler_vdp_mu_derivative_vs_complex_step():
+    w = small("vdp_n1e3:euler", 13)
+    P = O.Problem(w, mu=1.4)
+    rng = np.random.default_rng(43)
+    x, _ = rand_point(w, rng)
+    wv = rng.standard_normal(P.m)
+    got = O.dpar_vjp(P, x, wv)
+    ref = wv @ O.cs_cons(P, x, np.zeros(P.n), dmu=1.0)
+    assert abs(got - ref) <= 1e-13 * (1 + abs(ref))
+
+
 # ---------------------------------------------------------------------------------------
 # Products and the parameter derivative
 # ---------------------------------------------------------------------------------------
 @pytest.mark.parametrize("name", MODELS)
 def test_products_vs_complex_step_and_adjoint(name):
-    w = small(name, 3 if name == "heat_n2e4" else 9)
+    w = small(name, 3 if name.startswith("heat") else 9)
     P = O.Problem(w)
     rng = np.random.default_rng(13)
     x, y = rand_point(w, rng)
@@ -456,7 +506,7 @@ def test_kkt_assembly_structure_and_action(name):
     """The KKT matrix [H + D, J^T; J, -delta_c I] (lower triangle): sorted, every diagonal
     present once, nnz = nnz_H + nnz_J + m + (diagonals H lacks); its symmetric action on
     (v, w) is (H v + D v + J^T w, J v - delta_c w) with the oracle's own products."""
-    w = small(name, 3 if name == "heat_n2e4" else 7)
+    w = small(name, 3 if name.startswith("heat") else 7)
     P = O.Problem(w)
     rng = np.random.default_rng(41)
     x, y = rand_point(w, rng)
