@@ -64,7 +64,8 @@ _COUNT_CACHE = {}
 
 
 def _counts(w):
-    key = (w["model"], w["nx"], w["N"], tuple(w["q"]), tuple(w["r"]), w.get("xf") is not None)
+    key = (ops_model(w), w["nx"], w["N"], tuple(w["q"]), tuple(w["r"]), w.get("xf") is not None,
+           w.get("scheme", "trapezoid"), bool(w.get("free_tf")), tuple(w.get("xf_comp") or ()))
     if key not in _COUNT_CACHE:
         from paper_2510_03932_gb300 import ocp
         H = ocp.OCP.from_workload(w)
@@ -73,21 +74,36 @@ def _counts(w):
     return _COUNT_CACHE[key]
 
 
-# FP64 instructions (DFMA, DADD, DMUL per thread) each kernel executes per node.  Van der Pol:
-# counted from the kernel source and equal to ncu's sm__sass_thread_inst_executed_op_{dfma,dadd,
-# dmul} counts divided by N+1 (the objective's tile reduction adds 1.5 per node).  Quadrotor:
-# ncu's sm__inst_executed_pipe_fp64 x 32 / (N+1) at N = 1e5, which includes the FP64 work of
-# the three sincos calls and the 1/cos division (about 130 per node).  Goddard: the same
-# measurement (exp and the divisions 1/m, 1/r included), free final time.
+# FP64 arithmetic instructions (DFMA + DADD + DMUL per thread) each kernel executes per node:
+# ncu's sm__sass_thread_inst_executed_op_{dfma,dadd,dmul}_pred_on counts divided by N+1 (for
+# Van der Pol also counted from the kernel source; the objective's tile reduction adds 1.5 per
+# node).  The quadrotor's include the arithmetic of its three sincos calls and 1/cos x8, the
+# Goddard's that of exp and two divisions.  Measured at N = 1e5 (quadrotor, Goddard) and 1e6.
 FP64_OPS_PER_NODE = {("vdp", "eval_all"): 26.5, ("vdp", "jh"): 10.0, ("vdp", "jprod"): 14.0,
                      ("vdp", "jtprod"): 12.0, ("vdp", "hprod"): 11.0, ("vdp", "step"): 51.6,
-                     ("quadrotor", "eval_all"): 275.4, ("quadrotor", "jh"): 199.1, ("quadrotor", "jprod"): 180.9,
-                     ("quadrotor", "jtprod"): 172.1, ("quadrotor", "hprod"): 214.1, ("quadrotor", "step"): 432.9,
-                     ("goddard", "eval_all"): 114.5, ("goddard", "jh"): 101.4, ("goddard", "jprod"): 78.3,
-                     ("goddard", "jtprod"): 81.4, ("goddard", "hprod"): 107.5, ("goddard", "step"): 171.8}
+                     ("quadrotor", "eval_all"): 259.3, ("quadrotor", "jh"): 183.9, ("quadrotor", "jprod"): 165.5,
+                     ("quadrotor", "jtprod"): 157.0, ("quadrotor", "hprod"): 199.0, ("quadrotor", "step"): 414.8,
+                     ("goddard", "eval_all"): 110.3, ("goddard", "jh"): 100.3, ("goddard", "jprod"): 77.3,
+                     ("goddard", "jtprod"): 77.2, ("goddard", "hprod"): 106.2, ("goddard", "step"): 164.4,
+                     ("vdp:euler", "eval_all"): 22.5, ("vdp:euler", "jh"): 9.0, ("vdp:euler", "jprod"): 11.0,
+                     ("vdp:euler", "jtprod"): 10.0, ("vdp:euler", "hprod"): 10.0, ("vdp:euler", "step"): 42.5}
 # Rows of the paper's workloads beyond the headline problem, measured the same way (fused
 # step with an L2 flush between steps) and reported under "widened".
-WIDENED = ["quadrotor_n1e6", "goddard_n1e6"]
+WIDENED = ["quadrotor_n1e6", "goddard_n1e6", "vdp_mu_n1e6:euler"]
+
+
+def ops_model(w):
+    """Key of FP64_OPS_PER_NODE: the model, with the scheme when it is not the trapezoid."""
+    return w["model"] + (":euler" if w.get("scheme") == "euler" else "")
+
+
+def named_workload(name):
+    """A workload by name; the suffix ":euler" selects the forward Euler scheme."""
+    base, _, scheme = name.partition(":")
+    w = synth.workload(base)
+    if scheme:
+        w = dict(w, scheme=scheme, name=name)
+    return w
 # DRAM bytes (read + write) of one launch of the fused step at the bench workload, from an ncu
 # capture of the same kernel version (dram__bytes_read.sum + dram__bytes_write.sum; writes
 # still dirty in L2 when the kernel ends are not counted).  Remove an entry when its kernel
@@ -164,7 +180,7 @@ def run_ours(args, rank, world):
 
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    w = synth.workload(args.workload)
+    w = named_workload(args.workload)
     d = synth.draw(w, seed=w["seed"] + rank)
     H = ocp.OCP.from_workload(w)
     n, m, nnzj, nnzh = H.n, H.m, H.nnzj, H.nnzh
@@ -290,7 +306,7 @@ def run_ours(args, rank, world):
     achieved = ab / (step_mean * 1e-3) / 1e9
     clk = (clocks or {}).get("sm_mhz") or 2070.0
     fp64_peak = FP64_INST_PER_CLK_PER_SM * NUM_SMS * clk * 1e6 / 1e9   # G FP64 inst/s
-    ops = FP64_OPS_PER_NODE.get((w["model"], "step"))
+    ops = FP64_OPS_PER_NODE.get((ops_model(w), "step"))
     fp64_ach = ops * (w["N"] + 1) / (step_mean * 1e-3) / 1e9 if ops else None
     res = dict(
         metric=METRIC, value=nnz * args.steps * world / (tot_ms * 1e-3), unit="nnz/s", n_gpus=world,
@@ -312,8 +328,8 @@ def run_ours(args, rank, world):
         separate_calls_ms=float(kern_ms.sum()),
         kernels={nm: dict(ms=float(kern_ms[i]), GBps=algorithmic_bytes(w, nm) / (kern_ms[i] * 1e-3) / 1e9,
                           hbm_frac=algorithmic_bytes(w, nm) / (kern_ms[i] * 1e-3) / 1e9 / hbm,
-                          fp64_frac=(FP64_OPS_PER_NODE[(w["model"], nm)] * (w["N"] + 1) / (kern_ms[i] * 1e-3) / 1e9
-                                     / fp64_peak) if (w["model"], nm) in FP64_OPS_PER_NODE else None)
+                          fp64_frac=(FP64_OPS_PER_NODE[(ops_model(w), nm)] * (w["N"] + 1) / (kern_ms[i] * 1e-3) / 1e9
+                                     / fp64_peak) if (ops_model(w), nm) in FP64_OPS_PER_NODE else None)
                  for i, nm in enumerate(names)},
         jac_hess_only=dict(ms=jh_ms, nnz_per_s=nnz / (jh_ms * 1e-3),
                            GBps=algorithmic_bytes(w, "jh") / (jh_ms * 1e-3) / 1e9,
@@ -334,7 +350,7 @@ def run_widened(name, steps, warmup):
     from paper_2510_03932_gb300 import ocp
 
     dev = torch.device("cuda", torch.cuda.current_device())
-    w = synth.workload(name)
+    w = named_workload(name)
     d = synth.draw(w)
     H = ocp.OCP.from_workload(w)
     x, y, vn, vm = (torch.from_numpy(d[k]).to(dev) for k in ("x", "y", "vn", "vm"))
@@ -375,7 +391,7 @@ def run_widened(name, steps, warmup):
                jac_hess_only=dict(ms=ms["jh"], nnz_per_s=nnz / (ms["jh"] * 1e-3)), kernels={})
     for nm in ("step", "eval_all", "jh", "jprod", "jtprod", "hprod"):
         ab = algorithmic_bytes(w, nm)
-        ops = FP64_OPS_PER_NODE.get((w["model"], nm))
+        ops = FP64_OPS_PER_NODE.get((ops_model(w), nm))
         out["kernels"][nm] = dict(
             ms=ms[nm], hbm_frac=ab / (ms[nm] * 1e-3) / 1e9 / hbm,
             fp64_frac=(ops * (w["N"] + 1) / (ms[nm] * 1e-3) / 1e9 / fp64_peak) if ops else None)
@@ -483,7 +499,7 @@ def run_profile(args):
     import torch
     from paper_2510_03932_gb300 import ocp
 
-    w = synth.workload(args.workload)
+    w = named_workload(args.workload)
     d = synth.draw(w)
     H = ocp.OCP.from_workload(w)
     x, y = torch.from_numpy(d["x"]).cuda(), torch.from_numpy(d["y"]).cuda()
@@ -551,7 +567,7 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        w = synth.workload(args.workload)
+        w = named_workload(args.workload)
         for _ in range(max(0, min(args.warmup, 1))):
             oracle_step_time(w, 0.0)
         vals = [oracle_step_time(w, max(1.0, args.cpu_budget / max(1, args.steps)))[0] for _ in range(args.steps)]
@@ -574,7 +590,7 @@ def main():
         res["widened"] = {nm: run_widened(nm, min(args.steps, 200), max(args.warmup, 3)) for nm in WIDENED
                           if nm != args.workload}
     if rank == 0:
-        _, cb = oracle_step_time(synth.workload(args.workload), args.cpu_budget)
+        _, cb = oracle_step_time(named_workload(args.workload), args.cpu_budget)
         res["cpu_baseline"] = cb
         print(json.dumps(res))
     if world > 1:

@@ -91,6 +91,9 @@ enum {
  * time-varying. */
 enum { OCP_COST_DIAG_QUADRATIC = 0 };
 
+/* One-step schemes of the transcription (paper Sec. 3 / Sec. 5). */
+enum { OCP_SCHEME_TRAPEZOID = 0, OCP_SCHEME_EULER = 1 };
+
 typedef struct { int model; const double* params; int nparams; } ocp_dynamics;
 typedef struct { int kind; const double* q; const double* r; const double* xref; const double* uref; } ocp_cost;
 
@@ -121,6 +124,19 @@ ocp_status ocp_set_boundary(ocp_t* h, const double* x0, const double* xf);
  * table it saw: re-create the batch after changing the reference.  Errors: OCP_EMODEL for
  * HEAT1D, OCP_EINVAL for non-finite coefficients, OCP_ENOMEM / OCP_ECUDA. */
 ocp_status ocp_set_tracking(ocp_t* h, const double* xslope, const double* xamp, const double* xfreq);
+
+/* Scheme (paper Sec. 3: the transcription is parametrised by the one-step scheme).
+ * OCP_SCHEME_TRAPEZOID (default): as described at the top of this file.
+ * OCP_SCHEME_EULER: forward Euler,  defect (k, j) = (X_{j+1,k} - X_{j,k}) - h f_k(X_j, U_j),
+ *   j = 0..N-1; cost sum_{j<N} h f0(z_j) (rectangle rule); the unknowns are X_0..X_N and
+ *   U_0..U_{N-1} (n = nx (N+1) + nu N, U_j at nx (N+1) + nu j).  Row (k, j) lists its entries
+ *   on X_j (the model's template, identity merged), then X_{j+1,k}, then U_j; the Hessian has
+ *   the blocks of nodes 0..N-1 only (X rows of those nodes, then their U rows), built from the
+ *   own rows' multipliers y_{k,j}.
+ * Rebuilds the pattern.  Euler is provided for VDP, CARTPOLE, DINT and QUADROTOR (OCP_EMODEL
+ * otherwise); node ranges, the batched form, the parameter derivatives and the objective
+ * kernels of the differentiation form are provided for the trapezoidal scheme only. */
+ocp_status ocp_set_scheme(ocp_t* h, int scheme);
 
 /* Free final time (Goddard; paper appendix "tf in R, variable"): enable != 0 appends tf to the
  * unknowns (n grows by one, tf = x[n-1]) and the grid becomes t_j = j tf / N; T of ocp_create

@@ -281,6 +281,8 @@ ocp_status ocp_batch_create(ocp_t* const* items, int count, ocp_batch_t** out) {
   for (int i = 0; i < count; ++i) {
     if (!items[i]) return set_err(nullptr, OCP_EINVAL, "NULL problem in the batch");
     if (items[i]->model != model) return set_err(nullptr, OCP_EMODEL, "all problems of a batch must share the model");
+    if (items[i]->scheme != OCP_SCHEME_TRAPEZOID)
+      return set_err(nullptr, OCP_EMODEL, "batched evaluation is provided for the trapezoidal scheme");
     if (items[i]->device != items[0]->device) return set_err(nullptr, OCP_EINVAL, "problems on different devices");
   }
   ocp_batch* b = new (std::nothrow) ocp_batch();

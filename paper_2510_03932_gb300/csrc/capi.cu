@@ -283,7 +283,7 @@ ocp_status ocp_dims(const ocp_t* h, int64_t* n, int64_t* m, int64_t* nnzj, int64
 
 ocp_status ocp_bounds(const ocp_t* h, double* lvar, double* uvar, double* lcon, double* ucon) {
   if (!h) return OCP_EINVAL;
-  const int64_t nxN = (int64_t)h->nx * (h->N + 1), nX = nxN + (int64_t)h->nu * (h->N + 1);
+  const int64_t nxN = (int64_t)h->nx * (h->N + 1), nX = nxN + (int64_t)h->nu * h->pat.nun;
   for (int64_t i = 0; i < h->pat.n; ++i) {
     double lo, hi;
     if (i < nxN) { lo = h->xlo[i % h->nx]; hi = h->xhi[i % h->nx]; }
@@ -537,6 +537,15 @@ static ocp_status rebuild(ocp* h) {
   std::string why;
   if (!build_pattern(h, why)) return set_err(h, OCP_EDIM, why);
   return upload_tables(h);
+}
+
+ocp_status ocp_set_scheme(ocp_t* h, int scheme) {
+  if (!h) return OCP_EINVAL;
+  if (scheme != OCP_SCHEME_TRAPEZOID && scheme != OCP_SCHEME_EULER) return set_err(h, OCP_EINVAL, "unknown scheme");
+  if (scheme == OCP_SCHEME_EULER && (h->model == OCP_MODEL_HEAT1D || h->model == OCP_MODEL_GODDARD))
+    return set_err(h, OCP_EMODEL, "the Euler scheme is provided for the VDP, CARTPOLE, DINT and QUADROTOR models");
+  h->scheme = scheme;
+  return rebuild(h);
 }
 
 ocp_status ocp_set_free_final_time(ocp_t* h, int enable) {

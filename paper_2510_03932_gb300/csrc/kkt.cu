@@ -17,7 +17,7 @@
 namespace ocpg {
 
 constexpr int KKT_TMAX = 256;   // entries of a node's X or U row template (with added diagonals)
-constexpr int KKT_MAXREG = 4 + 128;  // X, U, tf, boundary rows, and the defect rows of each component
+constexpr int KKT_MAXREG = 5 + 128;  // X, X_N, U, tf, boundary rows, and the defect rows of each component
 
 // A run of KKT slots with one layout: slot i of the region is KKT entry out + i; its period is
 // the template length (X, U) or the row length plus the diagonal (defects); src / stride give
@@ -41,9 +41,9 @@ struct KktArgs {
   const int32_t* tmpl;     // Jacobian row templates (RT_STRIDE ints per component)
   const int32_t* fin;      // components of the final rows
   const int32_t* tcol;     // tf-row columns
-  int64_t N, n, m, nb, uoff, hbase_u, hbase_t, kb_u, kb_t, kb_c, nnzk;
+  int64_t N, n, m, nb, uoff, hbase_u, hbase_t, kb_xn, kb_u, kb_t, kb_c, nnzk;
   double dw, dc;
-  int nx, nu, hx, hu, tx, tu, kx, ku, free_tf;
+  int nx, nu, hx, hu, tx, tu, kx, ku, free_tf, euler;
   int16_t ksrc[2 * KKT_TMAX];  // X template then U template: source position or -1
   int16_t ka[2 * KKT_TMAX], kb[2 * KKT_TMAX];
   int nreg;
@@ -74,7 +74,7 @@ __device__ __forceinline__ int kkt_comp(const KktArgs& a, int64_t s) {
 // sit in shared memory.  Moved values are copied bit for bit; the (1,1) diagonal gets
 // sigma_x + delta_w, the constraint diagonal is -delta_c.
 constexpr int KKT_ROWS = 1024;
-enum { KR_X = 0, KR_U = 1, KR_TF = 2, KR_BND = 3, KR_DEF = 4 };
+enum { KR_X = 0, KR_U = 1, KR_TF = 2, KR_BND = 3, KR_DEF = 4, KR_XN = 5 };
 
 // floor(i / P) for block-local i < KKT_ROWS * P, P <= 1024: (i + 1/2) / P lies at least 1/(2P) >=
 // 2^-11 from an integer; its single-precision value (below KKT_ROWS = 2^10, computed from
@@ -94,13 +94,15 @@ __global__ void __launch_bounds__(256) k_kkt_values(const __grid_constant__ KktA
   }
   const KRegion R = a.reg[lo];
   const uint32_t chunk = blockIdx.x - R.block0;
-  if (R.kind == KR_TF || R.kind == KR_BND) {  // short regions: slot by slot
+  if (R.kind == KR_TF || R.kind == KR_BND || R.kind == KR_XN) {  // short regions: slot by slot
     const uint32_t i1 = min(R.len, (chunk + 1) * 256u * KKT_ROWS);
     for (uint32_t i = chunk * 256u * KKT_ROWS + threadIdx.x; i < i1; i += blockDim.x) {
       double v;
       if (R.kind == KR_TF) {
         if (i + 1 < R.len) v = __ldg(a.hv + R.src + i);
         else v = (a.sx ? __ldg(a.sx + a.n - 1) : 0.0) + a.dw;
+      } else if (R.kind == KR_XN) {  // Euler: the X rows of node N hold only their diagonal
+        v = (a.sx ? __ldg(a.sx + (int64_t)a.nx * a.N + i) : 0.0) + a.dw;
       } else {
         v = (i & 1) ? -a.dc : __ldg(a.jv + (i >> 1));
       }
@@ -149,7 +151,9 @@ __global__ void k_kkt_structure(const __grid_constant__ KktArgs a) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < a.nnzk; s += stride) {
     int64_t row, col;
-    if (s < a.kb_t) {           // node rows of the (1,1) block
+    if (s >= a.kb_xn && s < a.kb_u) {  // Euler: diagonal of the X rows of node N
+      row = col = (int64_t)a.nx * a.N + (s - a.kb_xn);
+    } else if (s < a.kb_t) {    // node rows of the (1,1) block
       const bool xs = s < a.kb_u;
       const int kt = xs ? a.kx : a.ku;
       const int64_t rel = xs ? s : s - a.kb_u;
@@ -179,13 +183,17 @@ __global__ void k_kkt_structure(const __grid_constant__ KktArgs a) {
       const int k = kkt_comp(a, s);
       const int32_t* t = a.tmpl + RT_STRIDE * k;
       const int rx = t[0], ru = t[1];
-      const int cnt = 2 * (rx + ru) + a.free_tf;
+      const int cnt = a.euler ? rx + 1 + ru : 2 * (rx + ru) + a.free_tf;
       const int64_t rel = s - a.kcbase[k];
       const int64_t j = rel / (cnt + 1);
       const int e = (int)(rel - j * (cnt + 1));
       row = a.n + a.nb + (int64_t)k * a.N + j;
       if (e == cnt) col = row;
-      else if (e == 2 * (rx + ru)) col = a.n - 1;
+      else if (a.euler) {
+        if (e < rx) col = (int64_t)a.nx * j + t[2 + e];
+        else if (e == rx) col = (int64_t)a.nx * (j + 1) + k;
+        else col = a.uoff + (int64_t)a.nu * j + t[2 + RT_XV + (e - rx - 1)];
+      } else if (e == 2 * (rx + ru)) col = a.n - 1;
       else if (e < rx) col = (int64_t)a.nx * j + t[2 + e];
       else if (e < 2 * rx) col = (int64_t)a.nx * (j + 1) + t[2 + (e - rx)];
       else if (e < 2 * rx + ru) col = a.uoff + (int64_t)a.nu * j + t[2 + RT_XV + (e - 2 * rx)];
@@ -207,19 +215,22 @@ static ocp_status kkt_fill(const ocp* h, KktArgs& a) {
   a.kb_u = P.kb_u; a.kb_t = P.kb_t; a.kb_c = P.kb_c; a.nnzk = P.nnzk;
   a.nx = h->nx; a.nu = h->nu; a.hx = P.hx; a.hu = P.hu; a.tx = P.tx; a.tu = P.tu;
   a.kx = (int)P.kxt.size(); a.ku = (int)P.kut.size(); a.free_tf = P.free_tf;
+  a.euler = P.scheme == OCP_SCHEME_EULER;
+  a.kb_xn = (int64_t)a.kx * P.nun;
   for (int i = 0; i < a.kx; ++i) { a.ksrc[i] = (int16_t)P.kxt[i].src; a.ka[i] = (int16_t)P.kxt[i].a; a.kb[i] = (int16_t)P.kxt[i].b; }
   for (int i = 0; i < a.ku; ++i) {
     a.ksrc[KKT_TMAX + i] = (int16_t)P.kut[i].src;
     a.ka[KKT_TMAX + i] = (int16_t)P.kut[i].a;
     a.kb[KKT_TMAX + i] = (int16_t)P.kut[i].b;
   }
-  if (h->nx + 4 > KKT_MAXREG) return OCP_EDIM;
+  if (h->nx + 5 > KKT_MAXREG) return OCP_EDIM;
   auto add = [&](int kind, int64_t out, int64_t len, uint32_t period, int64_t src, uint32_t stride) {
     if (len <= 0) return;
     KRegion& r = a.reg[a.nreg++];
     r.kind = kind; r.out = out; r.len = (uint32_t)len; r.period = period; r.src = src; r.stride = stride;
   };
-  add(KR_X, 0, P.kb_u, (uint32_t)a.kx, 0, (uint32_t)P.hx);
+  add(KR_X, 0, a.kb_xn, (uint32_t)a.kx, 0, (uint32_t)P.hx);
+  add(KR_XN, a.kb_xn, P.kb_u - a.kb_xn, 1, 0, 1);
   add(KR_U, P.kb_u, P.kb_t - P.kb_u, (uint32_t)a.ku, P.hbase_u, (uint32_t)P.hu);
   add(KR_TF, P.kb_t, P.kb_c - P.kb_t, 1, P.hbase_t, 1);
   add(KR_BND, P.kb_c, 2 * P.nb, 2, 0, 1);
@@ -233,7 +244,8 @@ static ocp_status kkt_fill(const ocp* h, KktArgs& a) {
     KRegion& R = a.reg[r];
     if (R.period > 1024) return OCP_EDIM;  // kkt_div's exactness bound
     R.block0 = b;
-    const int64_t nb = (R.kind == KR_TF || R.kind == KR_BND) ? ((int64_t)R.len + 256 * KKT_ROWS - 1) / (256 * KKT_ROWS)
+    const bool short_r = R.kind == KR_TF || R.kind == KR_BND || R.kind == KR_XN;
+    const int64_t nb = short_r ? ((int64_t)R.len + 256 * KKT_ROWS - 1) / (256 * KKT_ROWS)
                                                               : ((int64_t)(R.len / R.period) + KKT_ROWS - 1) / KKT_ROWS;
     b += (uint32_t)nb;
   }

@@ -807,8 +807,226 @@ ocp_status launch_eval_t(ocp* h, const EvalCall& c, cudaStream_t s) {
   return cuda_err(h, cudaGetLastError(), "k_node_eval launch");
 }
 
+// ======================================================================================
+// Forward Euler scheme (paper Sec. 3): defect (k, j) = X_{j+1,k} - X_{j,k} - h f_k(z_j) for
+// j < N, cost sum_{j<N} h f0(z_j), controls U_0..U_{N-1}.  A row uses only its own node's f,
+// so one thread per node evaluates its rows completely (tiles of TILE nodes do not overlap);
+// node N contributes only X_N (identity entries, boundary rows).  The model runs with
+// K.hh = h, so pa = x + h f, mjx = -h df/dx and hd = -h sum_k y_{k,j} d2f_k + sigma h d2f0.
+// Row (k, j) lists the entries on X_j (the template, identity merged), X_{j+1,k}, then U_j.
+// ======================================================================================
+template <class M>
+__host__ __device__ constexpr int euler_count(int k) { return M::RX(k) + 1 + M::RU(k); }
+template <class M>
+__host__ __device__ constexpr int euler_total() {
+  int s = 0;
+  for (int k = 0; k < M::NX; ++k) s += euler_count<M>(k);
+  return s;
+}
+template <class M>
+__host__ __device__ constexpr int euler_off(int k) {
+  int s = 0;
+  for (int q = 0; q < k; ++q) s += euler_count<M>(q);
+  return s;
+}
+
+template <class M, int TILE, unsigned OUT>
+__global__ void __launch_bounds__(TILE) k_euler(const __grid_constant__ NodeArgs<M> a) {
+  constexpr int NX = M::NX, NZ = M::NZ;
+  constexpr bool WF = OUT & O_F, WC = OUT & O_C, WG = OUT & O_G, WJ = OUT & O_J, WH = OUT & O_H;
+  constexpr bool WJV = OUT & O_JV, WJTV = OUT & O_JTV, WHV = OUT & O_HV;
+  constexpr bool NEEDJ = WJ || WJV || WJTV, NEEDH = WH || WHV;
+  constexpr HTmpl<M> HT{};
+  constexpr int NHD = (M::NHD > 0) ? M::NHD : 1;
+  extern __shared__ __align__(16) double sm[];   // staged rows: component k at euler_off(k) * TILE
+  __shared__ double red[TILE];
+  const bool sF = WF && a.f, sC = WC && a.c, sG = WG && a.g, sJ = WJ && a.jv, sH = WH && a.hv;
+  const bool doH = sH || WHV;
+  const int t = threadIdx.x;
+  ModelConst K = a.K;
+  if (a.p0_dev) M::device_param(K, __ldg(a.p0_dev));
+  const int64_t N = a.N;
+  const int64_t xN = (int64_t)NX * N;  // first entry of X_N
+  for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
+    const int64_t r0 = tile * TILE;
+    const int64_t j = r0 + t;
+    const int nrows = (int)min((int64_t)TILE, max(N - r0, (int64_t)0));
+    double objterm = 0.0;
+    if (j < N) {
+      double z[NZ], yb[NX], cqd[NZ], pa[NX], pb[NX], mjx[NX][M::MAXRX], mju[NX][M::MAXRU], hd[NHD];
+      load_node<M>(a, j, z);
+      if (NEEDH) {  // own rows' multipliers y_{k,j} (not the sum of two rows)
+#pragma unroll
+        for (int k = 0; k < NX; ++k) yb[k] = (doH && M::HK(k)) ? __ldg(a.y + a.nb + (int64_t)k * N + j) : 0.0;
+        node_cq<M>(a, false, cqd);
+      }
+      M::template eval<WC, NEEDJ, NEEDH>(K, z, yb, cqd, pa, pb, mjx, mju, hd);
+      if (sC) {
+#pragma unroll
+        for (int k = 0; k < NX; ++k) a.c[a.nb + (int64_t)k * N + j] = fsub(K, __ldg(a.x + NX * (j + 1) + k), pa[k]);
+      }
+      if (sJ) {
+#pragma unroll
+        for (int k = 0; k < NX; ++k) {
+          double* rp = sm + euler_off<M>(k) * TILE + t * euler_count<M>(k);
+#pragma unroll
+          for (int e = 0; e < M::MAXRX; ++e)
+            if (e < M::RX(k)) rp[e] = (M::XV(k, e) == k) ? fma(mjx[k][e], K.one, -1.0) : mjx[k][e];
+          rp[M::RX(k)] = 1.0;
+#pragma unroll
+          for (int e = 0; e < M::MAXRU; ++e)
+            if (e < M::RU(k)) rp[M::RX(k) + 1 + e] = mju[k][e];
+        }
+      }
+      double vz[NZ];
+      if (WJV || WHV) load_vz<M>(a, a.v, j, vz);
+      if (WJV) {
+        double A[NX], Bm[NX], mdp[NX];
+        jv_node<M, false>(K, mjx, mju, mdp, 0.0, vz, A, Bm);
+#pragma unroll
+        for (int k = 0; k < NX; ++k)
+          a.ojv[a.nb + (int64_t)k * N + j] = fadd(K, Bm[k], __ldg(a.v + NX * (j + 1) + k));
+        if (j == 0) {
+#pragma unroll
+          for (int k = 0; k < NX; ++k) a.ojv[k] = vz[k];
+        }
+      }
+      if (WJTV) {  // own rows only: wbar = w_{k,j}
+        double wl[NX], wr[NX], o[NZ];
+#pragma unroll
+        for (int k = 0; k < NX; ++k) {
+          const double* row = a.wv + a.nb + (int64_t)k * N;
+          wl[k] = (j >= 1) ? __ldg(row + j - 1) : 0.0;
+          wr[k] = __ldg(row + j);
+        }
+        jtv_node<M>(a, a.wv, j, j == 0, mjx, mju, wl, wr, wr, o);
+        store_nz<M>(a, a.ojtv, j, o);
+      }
+      if (WHV) {
+        double o[NZ];
+        hv_node<M>(a, hd, cqd, vz, o);
+        store_nz<M>(a, a.ohv, j, o);
+      }
+      if (sH) {
+#pragma unroll
+        for (int e = 0; e < HT.n; ++e) {
+          const int p = a.hpos[e];
+          if (p >= 0) {
+            const double val = (HT.dyn[e] >= 0) ? hd[HT.dyn[e] >= 0 ? HT.dyn[e] : 0] : cqd[HT.a[e]];
+            if (HT.a[e] < NX) a.hv[j * a.hx + p] = val;
+            else a.hv[a.hbase_u + j * a.hu + p] = val;
+          }
+        }
+      }
+      if (sG || sF) {
+        if (a.has_ref) objterm = sG ? node_grad<M, true, true>(a, z, false, j) : node_grad<M, true, false>(a, z, false, j);
+        else objterm = sG ? node_grad<M, false, true>(a, z, false, j) : node_grad<M, false, false>(a, z, false, j);
+      }
+      if (j == 0) {
+#pragma unroll
+        for (int k = 0; k < NX; ++k) {
+          if (sC) a.c[k] = z[k];
+          if (sJ) a.jv[k] = 1.0;
+        }
+      }
+    } else if (j == N) {  // the last node: states only
+      if (sG) {
+#pragma unroll
+        for (int k = 0; k < NX; ++k) a.g[xN + k] = 0.0;
+      }
+      if (a.has_final) {
+#pragma unroll
+        for (int k = 0; k < NX; ++k) {
+          if (sC) a.c[NX + k] = __ldg(a.x + xN + k);
+          if (sJ) a.jv[NX + k] = 1.0;
+          if (WJV) a.ojv[NX + k] = __ldg(a.v + xN + k);
+        }
+      }
+      if (WJTV) {
+#pragma unroll
+        for (int k = 0; k < NX; ++k) {
+          double o = __ldg(a.wv + a.nb + (int64_t)k * N + N - 1);
+          if (a.has_final) o = fadd(K, o, __ldg(a.wv + NX + k));
+          a.ojtv[xN + k] = o;
+        }
+      }
+      if (WHV) {
+#pragma unroll
+        for (int k = 0; k < NX; ++k) a.ohv[xN + k] = 0.0;
+      }
+    }
+    if (sJ) {  // coalesced copy-out of the staged rows
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < NX; ++k) {
+        const int cnt = euler_count<M>(k);
+        const double* src = sm + euler_off<M>(k) * TILE;
+        double* dst = a.jv + a.jbase[k] + r0 * cnt;
+        const int total = nrows * cnt;
+        for (int i = t; i < total; i += TILE) dst[i] = src[i];
+      }
+    }
+    if (sF) {
+      const double ts = tile_sum<TILE>(objterm, red, K.one);
+      if (t == 0) a.partials[tile] = ts;
+    }
+    __syncthreads();
+  }
+  if (sF) finish_tiles<TILE>(a.partials, a.ntiles, a.counter, a.f, 0.5, red);
+}
+
+template <class M, int TILE, unsigned OUT>
+ocp_status launch_euler_t(ocp* h, NodeArgs<M>& a, cudaStream_t s) {
+  a.ntiles = (h->N + 1 + TILE - 1) / TILE;
+  if (a.ntiles > h->max_partials) return set_err(h, OCP_EDIM, "too many tiles for the reduction scratch");
+  const size_t smem = (OUT & O_J) ? sizeof(double) * (size_t)euler_total<M>() * TILE : 0;
+  auto kern = k_euler<M, TILE, OUT>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_err(h, e, "cudaFuncSetAttribute(euler)");
+  }
+  kern<<<(int)a.ntiles, TILE, smem, s>>>(a);
+  return cuda_err(h, cudaGetLastError(), "k_euler launch");
+}
+
+template <class M>
+void fill_euler_args(const ocp* h, double sigma, NodeArgs<M>& a) {
+  fill_args<M>(h, sigma, a);
+  M::host_consts(h->params.data(), h->h, a.K);   // the scheme's step is h (not h/2)
+  a.B = 0;
+  a.E = h->N + 1;
+}
+
+template <class M, int TILE>
+ocp_status euler_eval_dispatch(ocp* h, unsigned out, const EvalCall& c, cudaStream_t s) {
+  if (c.range) return set_err(h, OCP_EMODEL, "node ranges are provided for the trapezoidal scheme");
+  NodeArgs<M> a;
+  fill_euler_args<M>(h, c.sigma, a);
+  a.x = c.x; a.y = c.y; a.f = c.f; a.c = c.c; a.g = c.g; a.jv = c.jv; a.hv = c.hv;
+  a.v = c.vn; a.wv = c.vm; a.ojv = c.ojv; a.ojtv = c.ojtv; a.ohv = c.ohv;
+  switch (out) {
+    case O_STEP: return launch_euler_t<M, TILE, O_STEP>(h, a, s);
+    case O_J | O_H: return launch_euler_t<M, TILE, O_J | O_H>(h, a, s);
+    default: return launch_euler_t<M, TILE, O_ALL>(h, a, s);  // subsets: NULL outputs are skipped
+  }
+}
+
+template <class M, int TILE>
+ocp_status euler_prod_dispatch(ocp* h, const ProdCall& c, cudaStream_t s) {
+  if (c.dmu || c.pdir != 0.0 || c.pdir_dev || c.mixw)
+    return set_err(h, OCP_EMODEL, "parameter derivatives are provided for the trapezoidal scheme");
+  NodeArgs<M> a;
+  fill_euler_args<M>(h, c.sigma, a);
+  a.x = c.x; a.y = c.y;
+  if (c.kind == P_JPROD) { a.v = c.v; a.ojv = c.out; return launch_euler_t<M, TILE, O_JV>(h, a, s); }
+  if (c.kind == P_JTPROD) { a.wv = c.v; a.ojtv = c.out; return launch_euler_t<M, TILE, O_JTV>(h, a, s); }
+  a.v = c.v; a.ohv = c.out;
+  return launch_euler_t<M, TILE, O_HV>(h, a, s);
+}
+
 template <class M, int TILE>
 ocp_status node_eval_dispatch(ocp* h, unsigned out, const EvalCall& c, cudaStream_t s) {
+  if (h->scheme == OCP_SCHEME_EULER) return euler_eval_dispatch<M, TILE>(h, out, c, s);
   switch (out) {
     case O_F: return launch_eval_t<M, TILE, 1, O_F>(h, c, s);
     case O_C: return launch_eval_t<M, TILE, 1, O_C>(h, c, s);
@@ -823,6 +1041,7 @@ ocp_status node_eval_dispatch(ocp* h, unsigned out, const EvalCall& c, cudaStrea
 
 template <class M, int TILE>
 ocp_status node_prod_dispatch(ocp* h, const ProdCall& c, cudaStream_t s) {
+  if (h->scheme == OCP_SCHEME_EULER) return euler_prod_dispatch<M, TILE>(h, c, s);
   NodeArgs<M> a;
   fill_args<M>(h, c.sigma, a);
   a.x = c.x; a.y = c.y; a.v = c.v; a.out = c.out; a.dmu = c.dmu;

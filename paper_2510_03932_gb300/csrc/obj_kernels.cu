@@ -81,6 +81,8 @@ ocp_status obj_launch(ocp* h, bool hvp, const double* x, const double* s, const 
   if (nz > OBJ_MAXV) return set_err(h, OCP_EDIM, "too many variables per node for the objective kernel");
   if (h->model == OCP_MODEL_GODDARD)
     return set_err(h, OCP_EMODEL, "the objective kernels cover running costs (Goddard has a terminal cost)");
+  if (h->scheme != OCP_SCHEME_TRAPEZOID)
+    return set_err(h, OCP_EMODEL, "the objective kernels use the trapezoidal weights");
   ObjArgs a;
   memset(&a, 0, sizeof(a));
   a.x = x; a.v = v; a.s = s; a.out = out; a.dot = dot;

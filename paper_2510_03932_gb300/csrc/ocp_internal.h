@@ -50,11 +50,15 @@ struct Pattern {
   // row (its tf column) and a Hessian row of tf against the node variables tcol (local
   // indices: tx state columns, then tu control columns) of every node
   int free_tf = 0;
+  int scheme = 0;                        // OCP_SCHEME_TRAPEZOID or OCP_SCHEME_EULER
+  int64_t nun = 0;                       // nodes with controls and Hessian blocks (N+1, or N for Euler)
   int tx = 0, tu = 0;
   std::vector<int> tcol;
   int64_t hbase_t = 0;                   // first slot of the tf row = (N+1) * (hx + hu)
   std::vector<int> fin;                  // components with a final row X_{N,k}, ascending
-  int row_count(int k) const { return rows[k].count() + free_tf; }
+  int row_count(int k) const {
+    return scheme == OCP_SCHEME_EULER ? rows[k].rx + 1 + rows[k].ru : rows[k].count() + free_tf;
+  }
   // KKT matrix [H + D, J^T; J, -delta_c I] (lower triangle, sorted by (row, col)): per-node
   // templates of the (1,1) rows, X then U, with the diagonal appended to rows where H has
   // none; src = position in the node's H block or -1 for an added diagonal
@@ -76,6 +80,7 @@ struct ocp {
   // has_final), a free final time and a linear terminal cost sum_k mayer_k X_{N,k}
   std::vector<int> fin_comp;
   bool free_tf = false;
+  int scheme = OCP_SCHEME_TRAPEZOID;
   std::vector<double> mayer;
   // variable bounds reported by ocp_bounds (default -inf / +inf)
   std::vector<double> xlo, xhi, ulo, uhi;

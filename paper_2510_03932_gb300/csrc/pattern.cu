@@ -92,7 +92,9 @@ bool build_pattern(ocp* h, std::string& why) {
   P = Pattern();
   P.nx = h->nx; P.nu = h->nu; P.nz = h->nx + h->nu; P.N = h->N;
   P.free_tf = h->free_tf ? 1 : 0;
-  P.n = (int64_t)P.nz * (P.N + 1) + P.free_tf;
+  P.scheme = h->scheme;
+  P.nun = (P.scheme == OCP_SCHEME_EULER) ? P.N : P.N + 1;
+  P.n = (int64_t)P.nx * (P.N + 1) + (int64_t)P.nu * P.nun + P.free_tf;
   if (h->has_final) {
     if (h->fin_comp.empty()) for (int k = 0; k < P.nx; ++k) P.fin.push_back(k);
     else P.fin = h->fin_comp;
@@ -123,8 +125,8 @@ bool build_pattern(ocp* h, std::string& why) {
   P.hu = pu;
   P.hent = ex;
   P.hent.insert(P.hent.end(), eu.begin(), eu.end());
-  P.hbase_u = (int64_t)P.hx * (P.N + 1);
-  P.nnzh = (int64_t)(P.hx + P.hu) * (P.N + 1);
+  P.hbase_u = (int64_t)P.hx * P.nun;
+  P.nnzh = (int64_t)(P.hx + P.hu) * P.nun;
   if (P.free_tf) {
     // tf row: the columns where some f_k has a derivative, and the cost columns
     std::vector<bool> col(P.nz, false);
@@ -138,7 +140,7 @@ bool build_pattern(ocp* h, std::string& why) {
     for (int v = 0; v < P.nz; ++v)
       if (col[v]) { P.tcol.push_back(v); if (v < P.nx) ++P.tx; else ++P.tu; }
     P.hbase_t = P.nnzh;
-    P.nnzh += (int64_t)(P.tx + P.tu) * (P.N + 1);
+    P.nnzh += (int64_t)(P.tx + P.tu) * P.nun;
   }
   // KKT layout: rows of the (1,1) block node by node (X rows, then U rows), the tf row, then
   // the constraint rows, each with its diagonal last (the largest column of a lower row)
@@ -153,9 +155,10 @@ bool build_pattern(ocp* h, std::string& why) {
       }
     if (!diag) t.push_back({-1, a, a});
   }
-  P.kb_u = (int64_t)P.kxt.size() * (P.N + 1);
-  P.kb_t = P.kb_u + (int64_t)P.kut.size() * (P.N + 1);
-  P.kb_c = P.kb_t + (P.free_tf ? (int64_t)(P.tx + P.tu) * (P.N + 1) + 1 : 0);
+  // (Euler: the X rows of node N carry only their diagonal)
+  P.kb_u = (int64_t)P.kxt.size() * P.nun + (P.scheme == OCP_SCHEME_EULER ? P.nx : 0);
+  P.kb_t = P.kb_u + (int64_t)P.kut.size() * P.nun;
+  P.kb_c = P.kb_t + (P.free_tf ? (int64_t)(P.tx + P.tu) * P.nun + 1 : 0);
   P.kcbase.assign(P.nx + 1, 0);
   P.kcbase[0] = P.kb_c + 2 * P.nb;
   for (int k = 0; k < P.nx; ++k) P.kcbase[k + 1] = P.kcbase[k] + (int64_t)(P.row_count(k) + 1) * P.N;
@@ -179,7 +182,7 @@ struct JacStructArgs {
   const int64_t* jbase;  // nx + 1
   const int32_t* fin;    // components of the final rows
   int64_t N, nb, nnzj, uoff, n;
-  int nx, nu, free_tf;
+  int nx, nu, free_tf, euler;
 };
 
 __global__ void k_jac_structure(const __grid_constant__ JacStructArgs a) {
@@ -198,12 +201,16 @@ __global__ void k_jac_structure(const __grid_constant__ JacStructArgs a) {
       const int k = lo;
       const int32_t* t = a.tmpl + RT_STRIDE * k;
       const int rx = t[0], ru = t[1];
-      const int cnt = 2 * (rx + ru) + a.free_tf;
+      const int cnt = a.euler ? rx + 1 + ru : 2 * (rx + ru) + a.free_tf;
       const int64_t rel = s - a.jbase[k];
       const int64_t j = rel / cnt;
       const int e = (int)(rel - j * cnt);
       row = a.nb + (int64_t)k * a.N + j;
-      if (e == 2 * (rx + ru)) col = a.n - 1;  // the free final time closes the row
+      if (a.euler) {  // X_j template, X_{j+1,k}, U_j template
+        if (e < rx) col = (int64_t)a.nx * j + t[2 + e];
+        else if (e == rx) col = (int64_t)a.nx * (j + 1) + k;
+        else col = a.uoff + (int64_t)a.nu * j + t[2 + RT_XV + (e - rx - 1)];
+      } else if (e == 2 * (rx + ru)) col = a.n - 1;  // the free final time closes the row
       else if (e < rx) col = (int64_t)a.nx * j + t[2 + e];
       else if (e < 2 * rx) col = (int64_t)a.nx * (j + 1) + t[2 + (e - rx)];
       else if (e < 2 * rx + ru) col = a.uoff + (int64_t)a.nu * j + t[2 + RT_XV + (e - 2 * rx)];
@@ -252,7 +259,7 @@ ocp_status launch_jac_structure(const ocp* h, int32_t* rows, int32_t* cols, cuda
   JacStructArgs a;
   a.rows = rows; a.cols = cols; a.tmpl = h->d_rowtmpl; a.jbase = h->d_jbase; a.fin = h->d_fin;
   a.N = h->N; a.nb = h->pat.nb; a.nnzj = h->pat.nnzj; a.uoff = (int64_t)h->nx * (h->N + 1); a.n = h->pat.n;
-  a.nx = h->nx; a.nu = h->nu; a.free_tf = h->pat.free_tf;
+  a.nx = h->nx; a.nu = h->nu; a.free_tf = h->pat.free_tf; a.euler = h->pat.scheme == OCP_SCHEME_EULER;
   const int64_t blocks = std::min<int64_t>((a.nnzj + 255) / 256, (int64_t)h->num_sms * 16);
   k_jac_structure<<<(int)std::max<int64_t>(blocks, 1), 256, 0, s>>>(a);
   return cudaGetLastError() == cudaSuccess ? OCP_OK : OCP_ECUDA;

@@ -33,6 +33,17 @@ def host(t):
     return t.detach().cpu().numpy()
 
 
+def named(name, N=None):
+    """A workload by name (":euler" selects the forward Euler scheme), optionally at horizon N."""
+    base, _, scheme = name.partition(":")
+    w = synth.workload(base)
+    if N is not None:
+        w = synth.with_horizon(w, N)
+    if scheme:
+        w = dict(w, scheme=scheme)
+    return w
+
+
 def full_check(ocp, w, report=None, products=True):
     """Everything the C-ABI computes for workload w versus the oracle."""
     d = synth.draw(w)
@@ -81,12 +92,16 @@ SMALL = [("vdp_n1e3", N) for N in (1, 2, 3, 254, 255, 256, 510, 1000, 1777)] + \
         [("heat_n2e4", N) for N in (1, 2, 30, 31, 32, 100, 333)] + \
         [("dint", N) for N in (1, 2, 100, 997)] + \
         [("quadrotor_n1e3", N) for N in (1, 2, 62, 63, 64, 126, 1000, 1777)] + \
-        [("goddard_n1e3", N) for N in (1, 2, 254, 255, 256, 510, 1000, 1777)]
+        [("goddard_n1e3", N) for N in (1, 2, 254, 255, 256, 510, 1000, 1777)] + \
+        [("vdp_n1e3:euler", N) for N in (1, 2, 255, 256, 257, 1000)] + \
+        [("cartpole_n1e5:euler", N) for N in (1, 127, 128, 129, 1303)] + \
+        [("dint:euler", N) for N in (1, 2, 100, 997)] + \
+        [("quadrotor_n1e3:euler", N) for N in (1, 63, 64, 65, 700)]
 
 
 @pytest.mark.parametrize("name,N", SMALL)
 def test_parity_small_horizons(ocp, name, N):
-    full_check(ocp, synth.with_horizon(synth.workload(name), N))
+    full_check(ocp, named(name, N))
 
 
 def test_parity_vdp_mu_variants(ocp):
@@ -166,17 +181,17 @@ def test_parity_cost_structure_follows_weights(ocp):
 
 
 @pytest.mark.parametrize("name", ["vdp_n1e3", "cartpole_n1e5", "heat_n2e4", "vdp_mu_n1e6", "quadrotor_n1e5",
-                                  "goddard_n1e5"])
+                                  "goddard_n1e5", "cartpole_n1e5:euler", "quadrotor_n1e5:euler"])
 def test_parity_full_size_workloads(ocp, name):
-    rep = full_check(ocp, synth.workload(name), products=(name != "vdp_mu_n1e6"))
+    rep = full_check(ocp, named(name), products=(name != "vdp_mu_n1e6"))
     print(name, rep)
 
 
-@pytest.mark.parametrize("name", ["cartpole_n1e5", "goddard_n1e3"])
+@pytest.mark.parametrize("name", ["cartpole_n1e5", "goddard_n1e3", "cartpole_n1e5:euler"])
 def test_every_slot_written_once_and_nothing_beyond(ocp, name):
     """NaN-prefilled outputs with guard words after the end: every slot gets a finite value
     and no guard word changes."""
-    w = synth.with_horizon(synth.workload(name), 1000)
+    w = named(name, 1000)
     d = synth.draw(w)
     H = ocp.OCP.from_workload(w)
     G = 64
@@ -248,10 +263,11 @@ def test_dimension_and_argument_errors(ocp):
 
 @pytest.mark.parametrize("name,N", [("vdp_n1e3", 1000), ("vdp_n1e3", 254), ("cartpole_n1e5", 1303),
                                     ("dint", 97), ("heat_n2e4", 77), ("quadrotor_n1e3", 1000),
-                                    ("goddard_n1e3", 1000)])
+                                    ("goddard_n1e3", 1000), ("vdp_n1e3:euler", 1000),
+                                    ("quadrotor_n1e3:euler", 300)])
 def test_fused_step_equals_separate_calls(ocp, name, N):
     """ocp_eval_step (one pass: eval + Jv + J^T w + Hv) is bit-identical to the separate calls."""
-    w = synth.with_horizon(synth.workload(name), N)
+    w = named(name, N)
     d = synth.draw(w)
     H = ocp.OCP.from_workload(w)
     x, y, vn, vm = dev(d["x"]), dev(d["y"]), dev(d["vn"]), dev(d["vm"])
@@ -264,7 +280,7 @@ def test_fused_step_equals_separate_calls(ocp, name, N):
 
 @pytest.mark.parametrize("name,N", [("vdp_n1e3", 1000), ("cartpole_n1e5", 700), ("heat_n2e4", 40), ("dint", 97),
                                     ("quadrotor_n1e3", 300), ("goddard_n1e3", 500),
-                                    ("goddard_fixed", 300)])
+                                    ("goddard_fixed", 300), ("vdp_n1e3:euler", 600), ("quadrotor_n1e3:euler", 200)])
 def test_kkt_assembly(ocp, name, N):
     """KKT structure bit-exact with the oracle's assembly; values are the GPU's own H and J
     values moved bit for bit (plus sigma_x + delta_w on the diagonal) and pass the parity gate
@@ -272,7 +288,7 @@ def test_kkt_assembly(ocp, name, N):
     if name == "goddard_fixed":
         w = dict(synth.with_horizon(synth.workload("goddard_n1e3"), N), free_tf=False, T=0.2)
     else:
-        w = synth.with_horizon(synth.workload(name), N)
+        w = named(name, N)
     d = synth.draw(w)
     P = O.Problem(w)
     H = ocp.OCP.from_workload(w)
@@ -305,3 +321,25 @@ def test_kkt_assembly(ocp, name, N):
     mag[pos_j] = ev["jac_mag"]
     rep = {}
     gate("kkt", kvh, ov, mag, rep)
+
+
+def test_euler_scheme_entry_checks(ocp):
+    """Euler is refused where it is not provided: the heat and Goddard models, node ranges,
+    the batched form and the parameter derivatives."""
+    import ctypes as C
+    L = ocp.lib()
+    Hh = ocp.OCP.from_workload(synth.with_horizon(synth.workload("heat_n2e4"), 5))
+    assert L.ocp_set_scheme(Hh.h, 1) == 5
+    assert L.ocp_set_scheme(Hh.h, 7) == 1
+    V = ocp.OCP.from_workload(named("vdp_n1e3:euler", 50))
+    x = torch.zeros(V.n, dtype=torch.float64, device="cuda")
+    y = torch.zeros(V.m, dtype=torch.float64, device="cuda")
+    st = L.ocp_eval_all_range(V.h, 0, 5, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), 1.0,
+                              *([C.c_void_p(x.data_ptr())] * 5), None)
+    assert st == 5
+    d = torch.zeros(1, dtype=torch.float64, device="cuda")
+    st = L.ocp_vjp_param(V.h, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), C.c_void_p(x.data_ptr()),
+                         C.c_void_p(d.data_ptr()), None)
+    assert st == 5
+    with pytest.raises(ocp.OcpError):
+        ocp.OCPBatch([V])
