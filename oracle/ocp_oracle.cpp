@@ -134,7 +134,15 @@ struct Prob {
   const double* mayer;
   // one-step scheme: 0 trapezoidal (controls on N+1 nodes), 1 forward Euler (paper Sec. 3:
   // controls U_0..U_{N-1}, rectangle-rule cost)
-  int32_t scheme, pad2;
+  int32_t scheme;
+  // path inequalities (paper Sec. 3) c_p(z_i) <= 0 at every node with a control, p < npath:
+  //   c_p(z) = sum_v [ path_a[p,v] (z_v - path_b[p,v])^2 + path_l[p,v] z_v ] - path_r[p]
+  // (arrays npath x (nx+nu) row-major, and npath)
+  int32_t npath;
+  const double* path_a;
+  const double* path_b;
+  const double* path_l;
+  const double* path_r;
 };
 
 template <class S> struct JEnt { int k, v; S val; };      // d f_k / d z_v
@@ -530,6 +538,7 @@ struct Layout {
   int nx, nu, nz;
   bool euler;
   int64_t N, nun, n, m, nb, tau;   // nun: nodes with controls; tau: column of tf, or -1
+  int npath;
   std::vector<int> fin;       // components with a final row, ascending
   explicit Layout(const Prob& P) {
     nx = P.nx; nu = P.nu; nz = nx + nu; N = P.N;
@@ -542,16 +551,74 @@ struct Layout {
     n = (int64_t)nx * (N + 1) + (int64_t)nu * nun + (P.free_tf ? 1 : 0);
     tau = P.free_tf ? n - 1 : -1;
     nb = (int64_t)nx + (int64_t)fin.size();
-    m = nb + (int64_t)nx * N;
+    npath = P.npath;
+    m = nb + (int64_t)nx * N + (int64_t)npath * nun;
   }
+  int64_t path_row(int p, int64_t i) const { return nb + (int64_t)nx * N + (int64_t)p * nun + i; }
   int64_t colX(int64_t j, int k) const { return k + (int64_t)nx * j; }
   int64_t colU(int64_t j, int i) const { return (int64_t)nx * (N + 1) + i + (int64_t)nu * j; }
   int64_t col(int64_t j, int v) const { return v < nx ? colX(j, v) : colU(j, v - nx); }
   int64_t defect_row(int k, int64_t j) const { return nb + (int64_t)k * N + j; }
 };
 
+// Path inequalities: value, first derivatives (support: a or l non-zero) and the diagonal
+// second derivatives 2 a_v (support: a non-zero) of row p at node z.
+inline bool path_in(const Prob& P, int p, int v) {
+  const int nz = P.nx + P.nu;
+  return P.path_a[p * nz + v] != 0.0 || P.path_l[p * nz + v] != 0.0;
+}
+template <class S> S path_value(const Prob& P, int p, const S* z) {
+  const int nz = P.nx + P.nu;
+  S c = S(0.0);
+  for (int v = 0; v < nz; ++v) {
+    const double av = P.path_a[p * nz + v], lv = P.path_l[p * nz + v];
+    if (av != 0.0) { const S d = z[v] - S(P.path_b[p * nz + v]); c = c + S(av) * d * d; }
+    if (lv != 0.0) c = c + S(lv) * z[v];
+  }
+  return c - S(P.path_r[p]);
+}
+template <class S> S path_deriv(const Prob& P, int p, int v, const S* z) {
+  const int nz = P.nx + P.nu;
+  const double av = P.path_a[p * nz + v], lv = P.path_l[p * nz + v];
+  return S(2.0 * av) * (z[v] - S(P.path_b[p * nz + v])) + S(lv);
+}
+
 template <class S> void gather_node(const Layout& L, const S* x, int64_t j, S* z) {
   for (int v = 0; v < L.nz; ++v) z[v] = x[L.col(j, v)];
+}
+
+// path rows: values at the nodes with a control, after the defects
+template <class S> void path_rows(const Prob& P, const Layout& L, const S* x, S* c) {
+  std::vector<S> z(L.nz);
+  for (int64_t i = 0; i < L.nun; ++i) {
+    gather_node(L, x, i, z.data());
+    for (int p = 0; p < L.npath; ++p) c[L.path_row(p, i)] = path_value(P, p, z.data());
+  }
+}
+
+// path rows of the Jacobian (appended after the defect rows: highest rows, columns ascending)
+template <class S> void path_jacobian(const Prob& P, const Layout& L, const S* x, std::vector<int64_t>& R,
+                                      std::vector<int64_t>& Cc, std::vector<S>& V) {
+  std::vector<S> z(L.nz);
+  for (int p = 0; p < L.npath; ++p)
+    for (int64_t i = 0; i < L.nun; ++i) {
+      gather_node(L, x, i, z.data());
+      for (int v = 0; v < L.nz; ++v)
+        if (path_in(P, p, v)) { R.push_back(L.path_row(p, i)); Cc.push_back(L.col(i, v)); V.push_back(path_deriv(P, p, v, z.data())); }
+    }
+}
+
+// path rows' Hessian terms of node i: y_{p,i} 2 a_{p,v} on the diagonal (v, v)
+template <class S> void path_hessian(const Prob& P, const Layout& L, const S* y, int64_t i,
+                                     std::map<std::pair<int, int>, S>& blk) {
+  const int nz = L.nz;
+  for (int p = 0; p < L.npath; ++p)
+    for (int v = 0; v < nz; ++v) {
+      const double av = P.path_a[p * nz + v];
+      if (av == 0.0) continue;
+      if (!blk.count({v, v})) blk[{v, v}] = S(0.0);
+      blk[{v, v}] = blk[{v, v}] + y[L.path_row(p, i)] * S(2.0 * av);
+    }
 }
 
 // step h = T / N, or tf / N with the free final time tf = x[tau]
@@ -605,6 +672,7 @@ template <class S> void euler_constraints(const Prob& P, const S* p, const S* x,
     model_f(P, p, z.data(), f.data());
     for (int k = 0; k < L.nx; ++k) c[L.defect_row(k, j)] = (x[L.colX(j + 1, k)] - x[L.colX(j, k)]) - h * f[k];
   }
+  path_rows(P, L, x, c);
 }
 
 template <class S> void euler_gradient(const Prob& P, const S* x, S* g) {
@@ -653,6 +721,7 @@ template <class S> void euler_jacobian(const Prob& P, const S* p, const S* x, Co
         i = t;
       }
     }
+  path_jacobian(P, L, x, J.row, J.col, J.val);
 }
 
 template <class S> void euler_hessian(const Prob& P, const S* p, const S* x, const S* y, S sigma, Coo<S>& H) {
@@ -674,6 +743,7 @@ template <class S> void euler_hessian(const Prob& P, const S* p, const S* x, con
       if (!blk.count({e.a, e.b})) blk[{e.a, e.b}] = S(0.0);
       blk[{e.a, e.b}] = blk[{e.a, e.b}] + y[L.defect_row(e.k, j)] * (S(0.0) - h * e.val);
     }
+    path_hessian(P, L, y, j, blk);
     for (auto& kv : blk) all.push_back({L.col(j, kv.first.first), L.col(j, kv.first.second), kv.second});
     if (L.tau >= 0) {
       std::map<int, S> trow;
@@ -728,6 +798,7 @@ template <class S> void constraints(const Prob& P, const S* p, const S* x, S* c)
       const S fj = f[(size_t)L.nx * j + k], fj1 = f[(size_t)L.nx * (j + 1) + k];
       c[L.defect_row(k, j)] = (x[L.colX(j + 1, k)] - x[L.colX(j, k)]) - h * (fj + fj1) / S(2.0);
     }
+  path_rows(P, L, x, c);
 }
 
 // Gradient of F: node-local w_j grad f0, the Mayer weights at X_N, and with a free final time
@@ -789,6 +860,7 @@ template <class S> void jacobian(const Prob& P, const S* p, const S* x, Coo<S>& 
         i = t;
       }
     }
+  path_jacobian(P, L, x, J.row, J.col, J.val);
 }
 
 // Lagrangian Hessian sigma * Hess F + sum_r y_r Hess c_r, lower triangle, sorted by (row, col).
@@ -829,6 +901,7 @@ template <class S> void hessian(const Prob& P, const S* p, const S* x, const S* 
         blk[{e.a, e.b}] = blk[{e.a, e.b}] + yr * (S(0.0) - h * e.val / S(2.0));
       }
     }
+    path_hessian(P, L, y, j, blk);
     for (auto& kv : blk) all.push_back({L.col(j, kv.first.first), L.col(j, kv.first.second), kv.second});
     if (L.tau >= 0) {
       std::map<int, S> trow;
@@ -928,6 +1001,7 @@ inline void kkt_assemble(const Layout& L, const Coo<double>& H, const Coo<double
 int check(const Prob& P) {
   if (P.N < 1 || !(P.T > 0.0)) return 2;
   if (P.scheme != 0 && P.scheme != 1) return 2;
+  if (P.npath < 0 || (P.npath > 0 && (!P.path_a || !P.path_b || !P.path_l || !P.path_r))) return 2;
   // the tracking reference is tabulated at t_j = j T / N: not with a free final time
   if (P.free_tf && (P.xslope || P.xamp)) return 2;
   if (P.has_final && P.fin_comp) {
@@ -983,10 +1057,16 @@ int orc_dims(const Prob* P, int64_t* n, int64_t* m, int64_t* nnzj, int64_t* nnzh
   }
   // a free final time adds one entry (the tf column) to every defect row
   *nnzj = L.nb + perrow * L.N + (L.tau >= 0 ? (int64_t)L.nx * L.N : 0);
+  for (int pp = 0; pp < L.npath; ++pp)
+    for (int v = 0; v < L.nz; ++v)
+      if (path_in(*P, pp, v)) *nnzj += L.nun;
   std::vector<HEnt<double>> he; model_hess(*P, p.data(), z.data(), he);
   std::vector<std::pair<int, int>> keys;
   for (int a = 0; a < L.nz; ++a) if (cost_hess_diag(*P, a) != 0.0) keys.push_back({a, a});
   for (auto& e : he) keys.push_back({e.a, e.b});
+  for (int pp = 0; pp < L.npath; ++pp)
+    for (int v = 0; v < L.nz; ++v)
+      if (P->path_a[pp * L.nz + v] != 0.0) keys.push_back({v, v});
   std::sort(keys.begin(), keys.end());
   *nnzh = (int64_t)(std::unique(keys.begin(), keys.end()) - keys.begin()) * L.nun;
   if (L.tau >= 0) {  // the tf row: model Jacobian columns and cost columns of every node

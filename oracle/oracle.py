@@ -21,7 +21,8 @@ class _Prob(C.Structure):
                 ("pad", C.c_int32), ("q", C.c_void_p), ("r", C.c_void_p), ("xref", C.c_void_p),
                 ("uref", C.c_void_p), ("xslope", C.c_void_p), ("xamp", C.c_void_p), ("xfreq", C.c_void_p),
                 ("free_tf", C.c_int32), ("nfin", C.c_int32), ("fin_comp", C.c_void_p), ("mayer", C.c_void_p),
-                ("scheme", C.c_int32), ("pad2", C.c_int32)]
+                ("scheme", C.c_int32), ("npath", C.c_int32), ("path_a", C.c_void_p), ("path_b", C.c_void_p),
+                ("path_l", C.c_void_p), ("path_r", C.c_void_p)]
 
 
 _lib = None
@@ -74,6 +75,13 @@ class Problem:
         self._mayer = None if w.get("mayer") is None else np.ascontiguousarray(w["mayer"], dtype=np.float64)
         p.mayer = _ptr(self._mayer)
         p.scheme = {"trapezoid": 0, "euler": 1}[w.get("scheme", "trapezoid")]
+        # path inequalities sum_v [a (z_v - b)^2 + l z_v] - r <= 0 (lists of rows over z = (x, u))
+        self._path = None
+        if w.get("path"):
+            pa = w["path"]
+            self._path = [np.ascontiguousarray(pa[k], dtype=np.float64) for k in ("a", "b", "l", "r")]
+            p.npath = len(pa["r"])
+            p.path_a, p.path_b, p.path_l, p.path_r = (_ptr(a) for a in self._path)
         self.s = p
         n, m, nj, nh = (C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64())
         st = lib().orc_dims(C.byref(p), C.byref(n), C.byref(m), C.byref(nj), C.byref(nh))

@@ -153,6 +153,42 @@ def workload(name: str) -> dict:
     raise KeyError(name)
 
 
+# Path inequalities (paper Sec. 3: c(X_i, U_i) <= 0 at every node with a control), written as
+# sum_v [a_v (z_v - b_v)^2 + l_v z_v] - r <= 0 over z = (x, u): one list entry per row.
+def _path_rows(nz, rows):
+    a = [[0.0] * nz for _ in rows]
+    b = [[0.0] * nz for _ in rows]
+    lin = [[0.0] * nz for _ in rows]
+    r = []
+    for i, (terms, rr) in enumerate(rows):
+        for v, (av, bv, lv) in terms.items():
+            a[i][v], b[i][v], lin[i][v] = av, bv, lv
+        r.append(rr)
+    return dict(a=a, b=b, l=lin, r=r)
+
+
+PATHS = {
+    # x2 >= -0.4 (the constrained Van der Pol problem) and u^2 <= 1
+    "vdp": [({1: (0.0, 0.0, -1.0)}, 0.4), ({2: (1.0, 0.0, 0.0)}, 1.0)],
+    # the cart within an ellipse in (p, theta), and F^2 <= 100
+    "cartpole": [({0: (0.25, 0.0, 0.0), 2: (1.0, 0.0, 0.0)}, 1.0), ({4: (1.0, 0.0, 0.0)}, 100.0)],
+    "dint": [({2: (1.0, 0.0, 0.0)}, 4.0)],
+    # altitude band (x5 - 1)^2 <= 1, a keep-out disc around (x1, x3) = (0.5, 0.5) of radius 0.2,
+    # and the tilt proxy x7^2 + x8^2 <= 0.5
+    "quadrotor": [({4: (1.0, 1.0, 0.0)}, 1.0), ({0: (-1.0, 0.5, 0.0), 2: (-1.0, 0.5, 0.0)}, -0.04),
+                  ({6: (1.0, 0.0, 0.0), 7: (1.0, 0.0, 0.0)}, 0.5)],
+    # the speed limit v <= vmax as a constraint, and the thrust energy u^2 <= 1
+    "goddard": [({1: (0.0, 0.0, 1.0)}, 0.1), ({3: (1.0, 0.0, 0.0)}, 1.0)],
+    # the boundary control u^2 <= 1 and the first cell above 0 (x_1 >= 0)
+    "heat": [({64: (1.0, 0.0, 0.0)}, 1.0), ({0: (0.0, 0.0, -1.0)}, 0.0)],
+}
+
+
+def with_path(w: dict) -> dict:
+    """The workload with its model's path inequalities attached (key "path")."""
+    return dict(w, path=_path_rows(w["nx"] + w["nu"], PATHS[w["model"]]))
+
+
 def with_horizon(w: dict, N: int) -> dict:
     """The same workload at another horizon (parity cases at oracle-friendly sizes)."""
     w = dict(w)
@@ -174,9 +210,10 @@ def control_nodes(w: dict) -> int:
 
 def dims(w: dict):
     """(n, m) of the transcription: n = nx (N+1) + nu (controlled nodes) (+1 for a free final
-    time); m = nx + final rows + nx N."""
+    time); m = nx + final rows + nx N + path rows (one per inequality and controlled node)."""
     n = w["nx"] * (w["N"] + 1) + w["nu"] * control_nodes(w) + (1 if w.get("free_tf") else 0)
-    return n, w["nx"] + final_rows(w) + w["nx"] * w["N"]
+    npath = len(w["path"]["r"]) if w.get("path") else 0
+    return n, w["nx"] + final_rows(w) + w["nx"] * w["N"] + npath * control_nodes(w)
 
 
 def draw(w: dict, seed: int | None = None) -> dict:

@@ -16,14 +16,21 @@ from paper_2510_03932_gb300 import synth
 
 MODELS = ["vdp_n1e3", "cartpole_n1e5", "heat_n2e4", "dint", "quadrotor_n1e3", "goddard_n1e3",
           "vdp_n1e3:euler", "cartpole_n1e5:euler", "dint:euler", "quadrotor_n1e3:euler", "heat_n2e4:euler"]
+# with path inequalities (counts are checked separately)
+PATHED = ["vdp_n1e3+path", "cartpole_n1e5+path", "quadrotor_n1e3+path", "goddard_n1e3+path", "heat_n2e4+path",
+          "vdp_n1e3:euler+path", "quadrotor_n1e3:euler+path"]
 
 
 def small(name, N):
-    """A workload at horizon N; the suffix ":euler" selects the forward Euler scheme."""
+    """A workload at horizon N; the suffix ":euler" selects the forward Euler scheme and "+path"
+    attaches the model's path inequalities."""
+    name, plus, _ = name.partition("+")
     base, _, scheme = name.partition(":")
     w = synth.with_horizon(synth.workload(base), N)
     if scheme:
         w["scheme"] = scheme
+    if plus:
+        w = synth.with_path(w)
     return w
 
 
@@ -98,7 +105,7 @@ def dense_hess_cs(P, x, y, sigma):
     return np.array(cols).T  # n x n
 
 
-@pytest.mark.parametrize("name", MODELS)
+@pytest.mark.parametrize("name", MODELS + PATHED)
 def test_structure_matches_bruteforce_detection(name):
     """An entry is structural iff it is nonzero at one of 8 random points (complex step)."""
     w = small(name, 2 if name.startswith("heat") else 3)
@@ -121,7 +128,7 @@ def test_structure_matches_bruteforce_detection(name):
 # ---------------------------------------------------------------------------------------
 # Derivative values against complex step of the residual / objective / Lagrangian gradient
 # ---------------------------------------------------------------------------------------
-@pytest.mark.parametrize("name", MODELS)
+@pytest.mark.parametrize("name", MODELS + PATHED)
 def test_jacobian_gradient_hessian_vs_complex_step(name):
     w = small(name, 2 if name.startswith("heat") else 4)
     P = O.Problem(w)
@@ -479,10 +486,48 @@ def test_euler_vdp_mu_derivative_vs_complex_step():
     assert abs(got - ref) <= 1e-13 * (1 + abs(ref))
 
 
+@pytest.mark.parametrize("name", PATHED)
+def test_path_rows_counts_and_boundary_points(name):
+    """Path inequalities add one row per inequality and controlled node after the defects, with
+    one Jacobian entry per variable in the row's support and Hessian diagonals for its squared
+    terms.  On their boundary the rows vanish: x2 = -0.4 for the Van der Pol half-space, points
+    (2 cos phi, sin phi) of the cart-pole ellipse, points of the quadrotor's keep-out circle."""
+    w = small(name, 6)
+    wp = {k: v for k, v in w.items() if k != "path"}
+    P, P0 = O.Problem(w), O.Problem(wp)
+    nun = synth.control_nodes(w)
+    pa = np.array(w["path"]["a"]); pl = np.array(w["path"]["l"])
+    supp = (pa != 0) | (pl != 0)
+    assert P.n == P0.n and P.m == P0.m + len(w["path"]["r"]) * nun
+    assert P.nnzj == P0.nnzj + int(supp.sum()) * nun
+    hr0, hc0 = O.hess_structure(P0)
+    hr, hc = O.hess_structure(P)
+    assert set(zip(hr0, hc0)) <= set(zip(hr, hc))
+    rng = np.random.default_rng(47)
+    x, _ = rand_point(w, rng)
+    nx, N = w["nx"], w["N"]
+    uoff = nx * (N + 1)
+    base = P.m - len(w["path"]["r"]) * nun
+    if w["model"] == "vdp":
+        x[1::2][:N + 1] = -0.4  # x2 at every node
+        c = O.evaluate(P, x, np.zeros(P.m), 1.0)["c"]
+        assert np.all(c[base:base + nun] == 0.0)
+    if w["model"] == "cartpole":
+        phi = rng.uniform(0, 2 * np.pi, N + 1)
+        x[0:uoff:4] = 2 * np.cos(phi); x[2:uoff:4] = np.sin(phi)
+        c = O.evaluate(P, x, np.zeros(P.m), 1.0)["c"]
+        np.testing.assert_allclose(c[base:base + nun], 0.0, atol=4e-16)
+    if w["model"] == "quadrotor":
+        phi = rng.uniform(0, 2 * np.pi, N + 1)
+        x[0:uoff:9] = 0.5 + 0.2 * np.cos(phi); x[2:uoff:9] = 0.5 + 0.2 * np.sin(phi)
+        c = O.evaluate(P, x, np.zeros(P.m), 1.0)["c"]
+        np.testing.assert_allclose(c[base + nun:base + 2 * nun], 0.0, atol=4e-16)
+
+
 # ---------------------------------------------------------------------------------------
 # Products and the parameter derivative
 # ---------------------------------------------------------------------------------------
-@pytest.mark.parametrize("name", MODELS)
+@pytest.mark.parametrize("name", MODELS + PATHED)
 def test_products_vs_complex_step_and_adjoint(name):
     w = small(name, 3 if name.startswith("heat") else 9)
     P = O.Problem(w)
@@ -501,7 +546,7 @@ def test_products_vs_complex_step_and_adjoint(name):
     np.testing.assert_allclose(Hv, O.cs_lagrangian_grad(P, x, v, y, sigma), rtol=1e-12, atol=1e-13)
 
 
-@pytest.mark.parametrize("name", MODELS)
+@pytest.mark.parametrize("name", MODELS + PATHED)
 def test_kkt_assembly_structure_and_action(name):
     """The KKT matrix [H + D, J^T; J, -delta_c I] (lower triangle): sorted, every diagonal
     present once, nnz = nnz_H + nnz_J + m + (diagonals H lacks); its symmetric action on
