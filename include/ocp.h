@@ -15,6 +15,7 @@
  *     rows nx..nb-1        : X_{N,k}                (final rows: every component, or those set
  *                                                   by ocp_set_final_components; nb = nx + count)
  *     row  nb + k*N + j    : (X_{j+1,k} - X_{j,k}) - h/2 (f_k(z_j) + f_k(z_{j+1})),  z_j = (X_j, U_j)
+ *     then the path inequalities, if any (ocp_set_path_constraints)
  * Objective (Sec. 5 trapezoidal cost): F = sum_j w_j f0(z_j), w_0 = w_N = h/2, else w_j = h.
  * Lagrangian Hessian: H = sigma * Hess F + sum_r y_r Hess c_r (lower triangle stored).
  * Sparse matrices are COO, 0-based, one entry per structural nonzero (a derivative that is
@@ -137,6 +138,20 @@ ocp_status ocp_set_tracking(ocp_t* h, const double* xslope, const double* xamp, 
  * otherwise); node ranges, the batched form, the parameter derivatives and the objective
  * kernels of the differentiation form are provided for the trapezoidal scheme only. */
 ocp_status ocp_set_scheme(ocp_t* h, int scheme);
+
+/* Path inequalities (paper Sec. 3: c(X_i, U_i) <= 0, i over the nodes with a control), in the
+ * quadratic-plus-linear family
+ *     c_p(z) = sum_v [ a[p,v] (z_v - b[p,v])^2 + l[p,v] z_v ] - r[p] <= 0,   z = (x, u) of the node,
+ * (half-spaces, bounds, ellipsoids, keep-out regions with a < 0).  Host arrays a, b, l of
+ * npath x (nx+nu) (row-major) and r of npath; npath = 0 removes them (at most 16).  The rows
+ * come after the defects: row nb + nx N + p nun + i (nun = N+1, or N for Euler), bounds
+ * (-inf, 0] in ocp_bounds.  Row (p, i) has one Jacobian entry per variable with a or l non-zero
+ * (columns ascending); the squared terms add 2 a y on the Hessian diagonal of node i (the
+ * entry becomes structural if it was not).  Every evaluation and product includes them (a
+ * kernel after the model's on the same stream).  Rebuilds the pattern.  Not in the batched
+ * form.  Errors: OCP_EINVAL (bad counts, NULL or non-finite arrays, an empty row). */
+ocp_status ocp_set_path_constraints(ocp_t* h, int npath, const double* a, const double* b, const double* l,
+                                    const double* r);
 
 /* Free final time (Goddard; paper appendix "tf in R, variable"): enable != 0 appends tf to the
  * unknowns (n grows by one, tf = x[n-1]) and the grid becomes t_j = j tf / N; T of ocp_create

@@ -133,7 +133,7 @@ static ocp_status upload_tables(ocp* h) {
     return cuda_err(h, e, "cudaMalloc");
   if ((e = cudaMemcpy(h->d_kcbase, P.kcbase.data(), P.kcbase.size() * 8, cudaMemcpyHostToDevice)) != cudaSuccess)
     return cuda_err(h, e, "cudaMemcpy");
-  return OCP_OK;
+  return path_upload(h);
 }
 
 static int model_nparams(int model) {
@@ -152,6 +152,7 @@ static void free_handle(ocp* h) {
   if (!h) return;
   cudaFree(h->d_rowtmpl); cudaFree(h->d_jbase); cudaFree(h->d_hent); cudaFree(h->d_fin); cudaFree(h->d_tcol);
   cudaFree(h->d_kcbase);
+  cudaFree(h->d_poff); cudaFree(h->d_pv); cudaFree(h->d_pcoef); cudaFree(h->d_pbase);
   cudaFree(h->d_partials); cudaFree(h->d_counter); cudaFree(h->d_xtrack);
   delete h;
 }
@@ -283,6 +284,7 @@ ocp_status ocp_dims(const ocp_t* h, int64_t* n, int64_t* m, int64_t* nnzj, int64
 
 ocp_status ocp_bounds(const ocp_t* h, double* lvar, double* uvar, double* lcon, double* ucon) {
   if (!h) return OCP_EINVAL;
+  const double inf = std::numeric_limits<double>::infinity();
   const int64_t nxN = (int64_t)h->nx * (h->N + 1), nX = nxN + (int64_t)h->nu * h->pat.nun;
   for (int64_t i = 0; i < h->pat.n; ++i) {
     double lo, hi;
@@ -293,20 +295,21 @@ ocp_status ocp_bounds(const ocp_t* h, double* lvar, double* uvar, double* lcon, 
     if (uvar) uvar[i] = hi;
   }
   const int64_t nfin = h->pat.nb - h->nx;
+  const int64_t prow0 = h->pat.nb + (int64_t)h->nx * h->N;  // path inequalities: (-inf, 0]
   for (int64_t i = 0; i < h->pat.m; ++i) {
-    double v = 0.0;
-    if (i < h->nx) v = h->x0[i];
-    else if (i < h->nx + nfin) v = h->xf[i - h->nx];
-    if (lcon) lcon[i] = v;
-    if (ucon) ucon[i] = v;
+    double lo = 0.0, hi = 0.0;
+    if (i < h->nx) lo = hi = h->x0[i];
+    else if (i < h->nx + nfin) lo = hi = h->xf[i - h->nx];
+    else if (i >= prow0) lo = -inf;
+    if (lcon) lcon[i] = lo;
+    if (ucon) ucon[i] = hi;
   }
   return OCP_OK;
 }
 
 }  // extern "C"
 
-ocp_status ocpg::dispatch_eval(ocp* h, unsigned out, const EvalCall& c, void* stream) {
-  cudaStream_t s = (cudaStream_t)stream;
+static ocp_status model_eval(ocp* h, unsigned out, const EvalCall& c, cudaStream_t s) {
   switch (h->model) {
     case OCP_MODEL_VDP: return node_eval_vdp(h, out, c, s);
     case OCP_MODEL_CARTPOLE: return node_eval_cartpole(h, out, c, s);
@@ -318,8 +321,15 @@ ocp_status ocpg::dispatch_eval(ocp* h, unsigned out, const EvalCall& c, void* st
   return set_err(h, OCP_EMODEL, "unknown model");
 }
 
-static ocp_status dispatch_prod(ocp* h, const ProdCall& c, void* stream) {
+// The model's kernel, then (same stream) the path rows and their updates.
+ocp_status ocpg::dispatch_eval(ocp* h, unsigned out, const EvalCall& c, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
+  ocp_status st = model_eval(h, out, c, s);
+  if (st == OCP_OK && h->pat.npath > 0) st = path_eval(h, out, c, s);
+  return st;
+}
+
+static ocp_status model_prod(ocp* h, const ProdCall& c, cudaStream_t s) {
   switch (h->model) {
     case OCP_MODEL_VDP: return node_prod_vdp(h, c, s);
     case OCP_MODEL_CARTPOLE: return node_prod_cartpole(h, c, s);
@@ -329,6 +339,13 @@ static ocp_status dispatch_prod(ocp* h, const ProdCall& c, void* stream) {
     case OCP_MODEL_HEAT1D: return heat_prod(h, c, s);
   }
   return set_err(h, OCP_EMODEL, "unknown model");
+}
+
+static ocp_status dispatch_prod(ocp* h, const ProdCall& c, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  ocp_status st = model_prod(h, c, s);
+  if (st == OCP_OK && h->pat.npath > 0) st = path_prod(h, c, s);
+  return st;
 }
 
 static ocp_status need(ocp* h, const void* p, const char* name) {
@@ -537,6 +554,28 @@ static ocp_status rebuild(ocp* h) {
   std::string why;
   if (!build_pattern(h, why)) return set_err(h, OCP_EDIM, why);
   return upload_tables(h);
+}
+
+ocp_status ocp_set_path_constraints(ocp_t* h, int npath, const double* a, const double* b, const double* l,
+                                    const double* r) {
+  if (!h) return OCP_EINVAL;
+  const int nz = h->nx + h->nu;
+  if (npath < 0 || npath > 16) return set_err(h, OCP_EINVAL, "between 0 and 16 path inequalities");
+  if (npath > 0 && (!a || !b || !l || !r)) return set_err(h, OCP_EINVAL, "a, b, l and r are required");
+  for (int i = 0; i < npath * nz; ++i)
+    if (!std::isfinite(a[i]) || !std::isfinite(b[i]) || !std::isfinite(l[i]))
+      return set_err(h, OCP_EINVAL, "path coefficients must be finite");
+  for (int p = 0; p < npath; ++p) {
+    bool any = false;
+    for (int v = 0; v < nz; ++v) any = any || a[p * nz + v] != 0.0 || l[p * nz + v] != 0.0;
+    if (!any) return set_err(h, OCP_EINVAL, "a path inequality without any variable");
+  }
+  h->npath = npath;
+  h->path_a.assign(a, a + (size_t)npath * nz);
+  h->path_b.assign(b, b + (size_t)npath * nz);
+  h->path_l.assign(l, l + (size_t)npath * nz);
+  h->path_r.assign(r, r + npath);
+  return rebuild(h);
 }
 
 ocp_status ocp_set_scheme(ocp_t* h, int scheme) {

@@ -44,6 +44,7 @@ struct GodArgs {
   int64_t N, nb, uoff, tau, ntiles;  // tau: index of tf in x (n - 1)
   int64_t jbase[3];                  // first slot of the defect rows of each component
   int64_t hbase_u, hbase_t;          // Hessian slots: U block, tf row
+  int hu, hpos_um;                   // U block entries per node; position of (u, m) in it
   double hh_fixed;                   // h / 2 of a fixed horizon
   double kappa;                      // 1 / (2N)
   double Cd, beta, Tmax, bT;         // bT = b Tmax
@@ -247,7 +248,9 @@ __global__ void __launch_bounds__(GT) k_god(const __grid_constant__ GodArgs a) {
           if (sH) {
 #pragma unroll
             for (int e = 0; e < 6; ++e) a.hv[6 * j + e] = hd[e];
-            a.hv[a.hbase_u + j] = hd[6];
+            // U block: (u, m), and (u, u) when a path inequality needs it (zero here; the path
+            // rows add their part)
+            for (int e = 0; e < a.hu; ++e) a.hv[a.hbase_u + (int64_t)a.hu * j + e] = (e == a.hpos_um) ? hd[6] : 0.0;
             if (FREE) {
               a.hv[a.hbase_t + 3 * j] = tr;
               a.hv[a.hbase_t + 3 * j + 1] = tv;
@@ -374,6 +377,10 @@ static void fill_god(const ocp* h, GodArgs& a) {
   for (int k = 0; k < 3; ++k) a.jbase[k] = P.jbase[k];
   a.hbase_u = P.hbase_u;
   a.hbase_t = P.hbase_t;
+  a.hu = P.hu;
+  a.hpos_um = 0;
+  for (int e = 0; e < P.hu; ++e)
+    if (P.hent[P.hx + e].first == 3 && P.hent[P.hx + e].second == 2) a.hpos_um = e;
   a.hh_fixed = h->hh;
   a.kappa = 1.0 / (2.0 * (double)h->N);
   a.Cd = h->params[0];

@@ -17,7 +17,7 @@
 namespace ocpg {
 
 constexpr int KKT_TMAX = 256;   // entries of a node's X or U row template (with added diagonals)
-constexpr int KKT_MAXREG = 5 + 128;  // X, X_N, U, tf, boundary rows, and the defect rows of each component
+constexpr int KKT_MAXREG = 5 + 128 + 16;  // X, X_N, U, tf, boundary rows, defect rows per component, path rows
 
 // A run of KKT slots with one layout: slot i of the region is KKT entry out + i; its period is
 // the template length (X, U) or the row length plus the diagonal (defects); src / stride give
@@ -41,9 +41,13 @@ struct KktArgs {
   const int32_t* tmpl;     // Jacobian row templates (RT_STRIDE ints per component)
   const int32_t* fin;      // components of the final rows
   const int32_t* tcol;     // tf-row columns
+  const int64_t* kpbase;   // KKT slots of the path rows (npath + 1)
+  const int32_t* poff;     // path rows: support of row p = pv[poff[p] .. poff[p+1])
+  const int32_t* pv;
   int64_t N, n, m, nb, uoff, hbase_u, hbase_t, kb_xn, kb_u, kb_t, kb_c, nnzk;
   double dw, dc;
-  int nx, nu, hx, hu, tx, tu, kx, ku, free_tf, euler;
+  int nx, nu, hx, hu, tx, tu, kx, ku, free_tf, euler, npath;
+  int64_t nun, prow0;
   int16_t ksrc[2 * KKT_TMAX];  // X template then U template: source position or -1
   int16_t ka[2 * KKT_TMAX], kb[2 * KKT_TMAX];
   int nreg;
@@ -179,6 +183,15 @@ __global__ void k_kkt_structure(const __grid_constant__ KktArgs a) {
       row = a.n + r;
       if ((s - a.kb_c) & 1) col = row;
       else col = (r < a.nx) ? r : (int64_t)a.nx * a.N + a.fin[r - a.nx];
+    } else if (a.npath > 0 && s >= a.kpbase[0]) {  // path rows: their entries, then the diagonal
+      int p = 0;
+      while (p + 1 < a.npath && a.kpbase[p + 1] <= s) ++p;
+      const int cnt = a.poff[p + 1] - a.poff[p];
+      const int64_t rel = s - a.kpbase[p];
+      const int64_t i = rel / (cnt + 1);
+      const int e = (int)(rel - i * (cnt + 1));
+      row = a.n + a.prow0 + (int64_t)p * a.nun + i;
+      col = (e == cnt) ? row : kkt_col(a, i, a.pv[a.poff[p] + e]);
     } else {                       // defect rows: the Jacobian row, then the diagonal
       const int k = kkt_comp(a, s);
       const int32_t* t = a.tmpl + RT_STRIDE * k;
@@ -217,13 +230,15 @@ static ocp_status kkt_fill(const ocp* h, KktArgs& a) {
   a.kx = (int)P.kxt.size(); a.ku = (int)P.kut.size(); a.free_tf = P.free_tf;
   a.euler = P.scheme == OCP_SCHEME_EULER;
   a.kb_xn = (int64_t)a.kx * P.nun;
+  a.npath = P.npath; a.nun = P.nun; a.prow0 = P.nb + (int64_t)h->nx * h->N;
+  a.kpbase = h->d_pbase + (P.npath + 1); a.poff = h->d_poff; a.pv = h->d_pv;
   for (int i = 0; i < a.kx; ++i) { a.ksrc[i] = (int16_t)P.kxt[i].src; a.ka[i] = (int16_t)P.kxt[i].a; a.kb[i] = (int16_t)P.kxt[i].b; }
   for (int i = 0; i < a.ku; ++i) {
     a.ksrc[KKT_TMAX + i] = (int16_t)P.kut[i].src;
     a.ka[KKT_TMAX + i] = (int16_t)P.kut[i].a;
     a.kb[KKT_TMAX + i] = (int16_t)P.kut[i].b;
   }
-  if (h->nx + 5 > KKT_MAXREG) return OCP_EDIM;
+  if (h->nx + 5 + P.npath > KKT_MAXREG) return OCP_EDIM;
   auto add = [&](int kind, int64_t out, int64_t len, uint32_t period, int64_t src, uint32_t stride) {
     if (len <= 0) return;
     KRegion& r = a.reg[a.nreg++];
@@ -237,6 +252,9 @@ static ocp_status kkt_fill(const ocp* h, KktArgs& a) {
   for (int k = 0; k < h->nx; ++k)
     add(KR_DEF, P.kcbase[k], P.kcbase[k + 1] - P.kcbase[k], (uint32_t)(P.row_count(k) + 1), P.jbase[k],
         (uint32_t)P.row_count(k));
+  for (int p = 0; p < P.npath; ++p)  // path rows: the same layout (entries, then the diagonal)
+    add(KR_DEF, P.kpbase[p], P.kpbase[p + 1] - P.kpbase[p], (uint32_t)(P.psupp[p].size() + 1), P.jpbase[p],
+        (uint32_t)P.psupp[p].size());
   // blocks of the values kernel: KKT_ROWS periods of a row region per block, or
   // blockDim * KKT_ROWS slots of a short region
   uint32_t b = 0;

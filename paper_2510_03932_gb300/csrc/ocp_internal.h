@@ -66,6 +66,13 @@ struct Pattern {
   std::vector<KEnt> kxt, kut;
   int64_t kb_u = 0, kb_t = 0, kb_c = 0, nnzk = -1;  // slot bases; nnzk = -1: too large for int32
   std::vector<int64_t> kcbase;           // KKT slot of the first defect row of component k (nx + 1)
+  // path inequalities: rows nb + nx N + p nun + i; row (p, i) has its entries on the
+  // variables psupp[p] (local, ascending) of node i, at jpbase[p] + i * psupp[p].size()
+  int npath = 0;
+  std::vector<std::vector<int>> psupp;
+  std::vector<int64_t> jpbase;           // npath + 1
+  std::vector<int64_t> kpbase;           // KKT slots of the path rows (npath + 1)
+  std::vector<int> hdiag;                // position of (v, v) in its node block (X or U), or -1
 };
 
 }  // namespace ocpg
@@ -85,6 +92,9 @@ struct ocp {
   // variable bounds reported by ocp_bounds (default -inf / +inf)
   std::vector<double> xlo, xhi, ulo, uhi;
   double tflo = 0, tfhi = 0;
+  // path inequalities sum_v [a (z_v - b)^2 + l z_v] - r <= 0 (npath x (nx+nu), row-major)
+  int npath = 0;
+  std::vector<double> path_a, path_b, path_l, path_r;
   const double* p0_dev = nullptr;  // device scalar overriding params[0] (or null)
   // time-varying state reference: xref_k + xslope_k t_j + xamp_k sin(xfreq_k t_j) for the
   // components trk_comp (ntrk of them), tabulated once per node in d_xtrack[(N+1) x ntrk]
@@ -101,6 +111,12 @@ struct ocp {
   int32_t* d_fin = nullptr;      // components of the final rows (nb - nx)
   int32_t* d_tcol = nullptr;     // tf-row columns (tx + tu local indices)
   int64_t* d_kcbase = nullptr;   // KKT slot bases of the defect rows (nx + 1)
+  // path inequalities on the device: per row p the terms poff[p]..poff[p+1]-1 with variable
+  // pv, coefficients pa, pb, pl; pr[p]; and the supports for the structure kernels
+  int32_t* d_poff = nullptr;
+  int32_t* d_pv = nullptr;
+  double* d_pcoef = nullptr;     // pa, pb, pl of every term (3 per term), then pr (npath)
+  int64_t* d_pbase = nullptr;    // jpbase (npath + 1) then kpbase (npath + 1)
   // scratch: per-CTA partial sums and the completion ticket of the last-block reduction
   double* d_partials = nullptr;
   unsigned* d_counter = nullptr;
@@ -181,6 +197,12 @@ void model_hess_max_template(int model, int nx, std::vector<std::pair<int, int>>
 
 ocp_status obj_launch(ocp* h, bool hvp, const double* x, const double* s, const double* v, double* out,
                       double* dot, cudaStream_t st);
+
+// Path inequalities: rows, Jacobian entries and the updates of H, J^T w and H v that belong
+// to them, after the model's own kernel on the same stream (see path_kernels.cu).
+ocp_status path_eval(ocp* h, unsigned out, const EvalCall& c, cudaStream_t s);
+ocp_status path_prod(ocp* h, const ProdCall& c, cudaStream_t s);
+ocp_status path_upload(ocp* h);
 
 
 }  // namespace ocpg

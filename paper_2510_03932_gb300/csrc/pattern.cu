@@ -95,18 +95,28 @@ bool build_pattern(ocp* h, std::string& why) {
   P.scheme = h->scheme;
   P.nun = (P.scheme == OCP_SCHEME_EULER) ? P.N : P.N + 1;
   P.n = (int64_t)P.nx * (P.N + 1) + (int64_t)P.nu * P.nun + P.free_tf;
+  P.npath = h->npath;
   if (h->has_final) {
     if (h->fin_comp.empty()) for (int k = 0; k < P.nx; ++k) P.fin.push_back(k);
     else P.fin = h->fin_comp;
   }
   P.nb = (int64_t)P.nx + (int64_t)P.fin.size();
-  P.m = P.nb + (int64_t)P.nx * P.N;
+  P.m = P.nb + (int64_t)P.nx * P.N + (int64_t)P.npath * P.nun;
   model_row_templates(h->model, h->nx, P.rows);
   if ((int)P.rows.size() != P.nx) { why = "no row template for this model"; return false; }
   P.jbase.assign(P.nx + 1, 0);
   P.jbase[0] = P.nb;
   for (int k = 0; k < P.nx; ++k) P.jbase[k + 1] = P.jbase[k] + (int64_t)P.row_count(k) * P.N;
   P.nnzj = P.jbase[P.nx];
+  // path rows after the defect rows: one entry per variable of the row's support
+  P.psupp.assign(P.npath, std::vector<int>());
+  P.jpbase.assign(P.npath + 1, P.nnzj);
+  for (int p = 0; p < P.npath; ++p) {
+    for (int v = 0; v < P.nz; ++v)
+      if (h->path_a[p * P.nz + v] != 0.0 || h->path_l[p * P.nz + v] != 0.0) P.psupp[p].push_back(v);
+    P.jpbase[p + 1] = P.jpbase[p] + (int64_t)P.psupp[p].size() * P.nun;
+  }
+  P.nnzj = P.jpbase[P.npath];
   std::vector<std::pair<int, int>> ent;
   std::vector<int> dyn;
   model_hess_max_template(h->model, h->nx, ent, dyn);
@@ -116,7 +126,9 @@ bool build_pattern(ocp* h, std::string& why) {
   for (size_t e = 0; e < ent.size(); ++e) {
     const int a = ent[e].first, b = ent[e].second;
     const double coef = a < P.nx ? h->q[a] : h->r[a - P.nx];
-    const bool present = dyn[e] || (a == b && coef != 0.0);
+    bool path_sq = false;  // a squared path term needs the diagonal
+    for (int p = 0; p < P.npath && a == b; ++p) path_sq = path_sq || h->path_a[p * P.nz + a] != 0.0;
+    const bool present = dyn[e] || (a == b && (coef != 0.0 || path_sq));
     if (!present) continue;
     if (a < P.nx) { P.hpos[e] = (int8_t)(px < 127 ? px : 127); ++px; ex.push_back(ent[e]); }
     else { P.hpos[e] = (int8_t)pu; ++pu; eu.push_back(ent[e]); }
@@ -125,6 +137,11 @@ bool build_pattern(ocp* h, std::string& why) {
   P.hu = pu;
   P.hent = ex;
   P.hent.insert(P.hent.end(), eu.begin(), eu.end());
+  P.hdiag.assign(P.nz, -1);
+  for (int e = 0; e < P.hx; ++e)
+    if (P.hent[e].first == P.hent[e].second) P.hdiag[P.hent[e].first] = e;
+  for (int e = 0; e < P.hu; ++e)
+    if (P.hent[P.hx + e].first == P.hent[P.hx + e].second) P.hdiag[P.hent[P.hx + e].first] = e;
   P.hbase_u = (int64_t)P.hx * P.nun;
   P.nnzh = (int64_t)(P.hx + P.hu) * P.nun;
   if (P.free_tf) {
@@ -162,7 +179,9 @@ bool build_pattern(ocp* h, std::string& why) {
   P.kcbase.assign(P.nx + 1, 0);
   P.kcbase[0] = P.kb_c + 2 * P.nb;
   for (int k = 0; k < P.nx; ++k) P.kcbase[k + 1] = P.kcbase[k] + (int64_t)(P.row_count(k) + 1) * P.N;
-  P.nnzk = P.kcbase[P.nx];
+  P.kpbase.assign(P.npath + 1, P.kcbase[P.nx]);
+  for (int p = 0; p < P.npath; ++p) P.kpbase[p + 1] = P.kpbase[p] + (int64_t)(P.psupp[p].size() + 1) * P.nun;
+  P.nnzk = P.kpbase[P.npath];
   const int64_t lim = (int64_t)1 << 31;
   if (P.nnzk >= lim || P.n + P.m >= lim) P.nnzk = -1;
   if (P.n >= lim || P.m >= lim || P.nnzj >= lim || P.nnzh >= lim) {
@@ -181,8 +200,11 @@ struct JacStructArgs {
   const int32_t* tmpl;   // per component (RT_STRIDE ints): rx, ru, xv[RT_XV], uv[RT_UV]
   const int64_t* jbase;  // nx + 1
   const int32_t* fin;    // components of the final rows
-  int64_t N, nb, nnzj, uoff, n;
-  int nx, nu, free_tf, euler;
+  const int64_t* pbase;  // path rows: first slot of row p (npath + 1)
+  const int32_t* poff;   // path rows: support of row p = pv[poff[p] .. poff[p+1])
+  const int32_t* pv;
+  int64_t N, nb, nnzj, uoff, n, nun, prow0;   // prow0: first path row
+  int nx, nu, free_tf, euler, npath;
 };
 
 __global__ void k_jac_structure(const __grid_constant__ JacStructArgs a) {
@@ -192,6 +214,15 @@ __global__ void k_jac_structure(const __grid_constant__ JacStructArgs a) {
     if (s < a.nb) {
       row = s;
       col = (s < a.nx) ? s : (int64_t)a.nx * a.N + a.fin[s - a.nx];
+    } else if (a.npath > 0 && s >= a.pbase[0]) {  // path rows
+      int p = 0;
+      while (p + 1 < a.npath && a.pbase[p + 1] <= s) ++p;
+      const int cnt = a.poff[p + 1] - a.poff[p];
+      const int64_t rel = s - a.pbase[p];
+      const int64_t i = rel / cnt;
+      const int v = a.pv[a.poff[p] + (int)(rel - i * cnt)];
+      row = a.prow0 + (int64_t)p * a.nun + i;
+      col = v < a.nx ? (int64_t)a.nx * i + v : a.uoff + (int64_t)a.nu * i + (v - a.nx);
     } else {
       int lo = 0, hi = a.nx - 1;  // last component with jbase <= s
       while (lo < hi) {
@@ -260,6 +291,8 @@ ocp_status launch_jac_structure(const ocp* h, int32_t* rows, int32_t* cols, cuda
   a.rows = rows; a.cols = cols; a.tmpl = h->d_rowtmpl; a.jbase = h->d_jbase; a.fin = h->d_fin;
   a.N = h->N; a.nb = h->pat.nb; a.nnzj = h->pat.nnzj; a.uoff = (int64_t)h->nx * (h->N + 1); a.n = h->pat.n;
   a.nx = h->nx; a.nu = h->nu; a.free_tf = h->pat.free_tf; a.euler = h->pat.scheme == OCP_SCHEME_EULER;
+  a.pbase = h->d_pbase; a.poff = h->d_poff; a.pv = h->d_pv; a.npath = h->pat.npath;
+  a.nun = h->pat.nun; a.prow0 = h->pat.nb + (int64_t)h->nx * h->N;
   const int64_t blocks = std::min<int64_t>((a.nnzj + 255) / 256, (int64_t)h->num_sms * 16);
   k_jac_structure<<<(int)std::max<int64_t>(blocks, 1), 256, 0, s>>>(a);
   return cudaGetLastError() == cudaSuccess ? OCP_OK : OCP_ECUDA;

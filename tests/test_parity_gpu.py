@@ -34,13 +34,17 @@ def host(t):
 
 
 def named(name, N=None):
-    """A workload by name (":euler" selects the forward Euler scheme), optionally at horizon N."""
+    """A workload by name (":euler" selects the forward Euler scheme, "+path" attaches the
+    model's path inequalities), optionally at horizon N."""
+    name, plus, _ = name.partition("+")
     base, _, scheme = name.partition(":")
     w = synth.workload(base)
     if N is not None:
         w = synth.with_horizon(w, N)
     if scheme:
         w = dict(w, scheme=scheme)
+    if plus:
+        w = synth.with_path(w)
     return w
 
 
@@ -96,7 +100,10 @@ SMALL = [("vdp_n1e3", N) for N in (1, 2, 3, 254, 255, 256, 510, 1000, 1777)] + \
         [("vdp_n1e3:euler", N) for N in (1, 2, 255, 256, 257, 1000)] + \
         [("cartpole_n1e5:euler", N) for N in (1, 127, 128, 129, 1303)] + \
         [("dint:euler", N) for N in (1, 2, 100, 997)] + \
-        [("quadrotor_n1e3:euler", N) for N in (1, 63, 64, 65, 700)]
+        [("quadrotor_n1e3:euler", N) for N in (1, 63, 64, 65, 700)] + \
+        [(nm + "+path", N) for nm in ("vdp_n1e3", "cartpole_n1e5", "dint", "quadrotor_n1e3", "goddard_n1e3",
+                                       "heat_n2e4", "vdp_n1e3:euler", "quadrotor_n1e3:euler")
+         for N in (1, 300)]
 
 
 @pytest.mark.parametrize("name,N", SMALL)
@@ -181,7 +188,8 @@ def test_parity_cost_structure_follows_weights(ocp):
 
 
 @pytest.mark.parametrize("name", ["vdp_n1e3", "cartpole_n1e5", "heat_n2e4", "vdp_mu_n1e6", "quadrotor_n1e5",
-                                  "goddard_n1e5", "cartpole_n1e5:euler", "quadrotor_n1e5:euler"])
+                                  "goddard_n1e5", "cartpole_n1e5:euler", "quadrotor_n1e5:euler",
+                                  "quadrotor_n1e5+path"])
 def test_parity_full_size_workloads(ocp, name):
     rep = full_check(ocp, named(name), products=(name != "vdp_mu_n1e6"))
     print(name, rep)
@@ -220,11 +228,11 @@ def test_deterministic_run_to_run(ocp):
 
 
 @pytest.mark.parametrize("name,N,S", [("vdp_n1e3", 5000, 3), ("cartpole_n1e5", 2000, 4), ("heat_n2e4", 500, 3),
-                                      ("dint", 300, 2), ("quadrotor_n1e3", 700, 3)])
+                                      ("dint", 300, 2), ("quadrotor_n1e3", 700, 3), ("cartpole_n1e5+path", 900, 3)])
 def test_virtual_shards_match_unsharded(ocp, name, N, S):
     """S contiguous node shards, each reading a one-node halo, reproduce the unsharded
     evaluation slot for slot; the objective is the sum of the shard partials."""
-    w = synth.with_horizon(synth.workload(name), N)
+    w = named(name, N)
     d = synth.draw(w)
     H = ocp.OCP.from_workload(w)
     x, y = dev(d["x"]), dev(d["y"])
@@ -264,7 +272,8 @@ def test_dimension_and_argument_errors(ocp):
 @pytest.mark.parametrize("name,N", [("vdp_n1e3", 1000), ("vdp_n1e3", 254), ("cartpole_n1e5", 1303),
                                     ("dint", 97), ("heat_n2e4", 77), ("quadrotor_n1e3", 1000),
                                     ("goddard_n1e3", 1000), ("vdp_n1e3:euler", 1000),
-                                    ("quadrotor_n1e3:euler", 300)])
+                                    ("quadrotor_n1e3:euler", 300), ("cartpole_n1e5+path", 700),
+                                    ("goddard_n1e3+path", 500), ("heat_n2e4+path", 40)])
 def test_fused_step_equals_separate_calls(ocp, name, N):
     """ocp_eval_step (one pass: eval + Jv + J^T w + Hv) is bit-identical to the separate calls."""
     w = named(name, N)
@@ -280,7 +289,8 @@ def test_fused_step_equals_separate_calls(ocp, name, N):
 
 @pytest.mark.parametrize("name,N", [("vdp_n1e3", 1000), ("cartpole_n1e5", 700), ("heat_n2e4", 40), ("dint", 97),
                                     ("quadrotor_n1e3", 300), ("goddard_n1e3", 500),
-                                    ("goddard_fixed", 300), ("vdp_n1e3:euler", 600), ("quadrotor_n1e3:euler", 200)])
+                                    ("goddard_fixed", 300), ("vdp_n1e3:euler", 600), ("quadrotor_n1e3:euler", 200),
+                                    ("quadrotor_n1e3+path", 300), ("vdp_n1e3:euler+path", 400)])
 def test_kkt_assembly(ocp, name, N):
     """KKT structure bit-exact with the oracle's assembly; values are the GPU's own H and J
     values moved bit for bit (plus sigma_x + delta_w on the diagonal) and pass the parity gate
@@ -343,3 +353,20 @@ def test_euler_scheme_entry_checks(ocp):
     assert st == 5
     with pytest.raises(ocp.OcpError):
         ocp.OCPBatch([V])
+
+
+def test_path_rows_bounds_and_checks(ocp):
+    """Path rows are inequalities (-inf, 0] after the equality rows; bad arguments are refused."""
+    import ctypes as C
+    w = named("vdp_n1e3+path", 20)
+    H = ocp.OCP.from_workload(w)
+    lv, uv, lc, uc = H.bounds()
+    npath, nun = len(w["path"]["r"]), 21
+    assert np.all(np.isneginf(lc[-npath * nun:])) and np.all(uc[-npath * nun:] == 0.0)
+    assert np.all(lc[:-npath * nun] == uc[:-npath * nun])
+    L = ocp.lib()
+    z = (C.c_double * 3)(0.0, 0.0, 0.0)
+    r = (C.c_double * 1)(1.0)
+    assert L.ocp_set_path_constraints(H.h, 1, C.cast(z, C.c_void_p), C.cast(z, C.c_void_p), C.cast(z, C.c_void_p),
+                                      C.cast(r, C.c_void_p)) == 1  # a row without any variable
+    assert L.ocp_set_path_constraints(H.h, 17, None, None, None, None) == 1
