@@ -75,18 +75,21 @@ def _counts(w):
 
 
 # FP64 arithmetic instructions (DFMA + DADD + DMUL per thread) each kernel executes per node:
-# ncu's sm__sass_thread_inst_executed_op_{dfma,dadd,dmul}_pred_on counts divided by N+1 (for
-# Van der Pol also counted from the kernel source; the objective's tile reduction adds 1.5 per
-# node).  The quadrotor's include the arithmetic of its three sincos calls and 1/cos x8, the
-# Goddard's that of exp and two divisions.  Measured at N = 1e5 (quadrotor, Goddard) and 1e6.
-FP64_OPS_PER_NODE = {("vdp", "eval_all"): 26.5, ("vdp", "jh"): 10.0, ("vdp", "jprod"): 14.0,
-                     ("vdp", "jtprod"): 12.0, ("vdp", "hprod"): 11.0, ("vdp", "step"): 51.6,
-                     ("quadrotor", "eval_all"): 259.3, ("quadrotor", "jh"): 183.9, ("quadrotor", "jprod"): 165.5,
-                     ("quadrotor", "jtprod"): 157.0, ("quadrotor", "hprod"): 199.0, ("quadrotor", "step"): 414.8,
+# ncu's sm__sass_thread_inst_executed_op_{dfma,dadd,dmul}_pred_on counts divided by N+1 (the
+# objective's tile reduction is part of them).  The cart-pole's include a sincos and a division, the quadrotor's three sincos calls and
+# 1/cos x8, the Goddard's exp and two divisions.  Measured at N = 1e5 (cart-pole, quadrotor,
+# Goddard) and 1e6 (Van der Pol).
+FP64_OPS_PER_NODE = {("vdp", "eval_all"): 26.6, ("vdp", "jh"): 10.0, ("vdp", "jprod"): 13.0,
+                     ("vdp", "jtprod"): 12.0, ("vdp", "hprod"): 11.0, ("vdp", "step"): 50.6,
+                     ("cartpole", "eval_all"): 133.9, ("cartpole", "jh"): 110.9, ("cartpole", "jprod"): 81.6,
+                     ("cartpole", "jtprod"): 78.0, ("cartpole", "hprod"): 114.0, ("cartpole", "step"): 181.0,
+                     ("quadrotor", "eval_all"): 260.3, ("quadrotor", "jh"): 180.8, ("quadrotor", "jprod"): 165.5,
+                     ("quadrotor", "jtprod"): 157.0, ("quadrotor", "hprod"): 199.0, ("quadrotor", "step"): 398.8,
                      ("goddard", "eval_all"): 110.3, ("goddard", "jh"): 100.3, ("goddard", "jprod"): 77.3,
                      ("goddard", "jtprod"): 77.2, ("goddard", "hprod"): 106.2, ("goddard", "step"): 164.4,
-                     ("vdp:euler", "eval_all"): 22.5, ("vdp:euler", "jh"): 9.0, ("vdp:euler", "jprod"): 11.0,
-                     ("vdp:euler", "jtprod"): 10.0, ("vdp:euler", "hprod"): 10.0, ("vdp:euler", "step"): 42.5}
+                     ("vdp:euler", "eval_all"): 21.5, ("vdp:euler", "jh"): 8.0, ("vdp:euler", "jprod"): 11.0,
+                     ("vdp:euler", "jtprod"): 10.0, ("vdp:euler", "hprod"): 10.0, ("vdp:euler", "step"): 41.5}
+
 # Rows of the paper's workloads beyond the headline problem, measured the same way (fused
 # step with an L2 flush between steps) and reported under "widened".
 WIDENED = ["quadrotor_n1e6", "goddard_n1e6", "vdp_mu_n1e6:euler"]
@@ -104,11 +107,13 @@ def named_workload(name):
     if scheme:
         w = dict(w, scheme=scheme, name=name)
     return w
+
+
 # DRAM bytes (read + write) of one launch of the fused step at the bench workload, from an ncu
 # capture of the same kernel version (dram__bytes_read.sum + dram__bytes_write.sum; writes
 # still dirty in L2 when the kernel ends are not counted).  Remove an entry when its kernel
 # changes.
-TRAFFIC = {("vdp_mu_n1e6", "step"): 228.05e6}
+TRAFFIC = {("vdp_mu_n1e6", "step"): 227.65e6}
 FP64_INST_PER_CLK_PER_SM = 2.0   # measured: DFMA throughput of one SM (DADD/DMUL are ~15% slower)
 NUM_SMS = 152
 

@@ -128,8 +128,9 @@ __global__ void __launch_bounds__(256) k_kkt_values(const __grid_constant__ KktA
   const uint32_t nper = R.len / P;   // nodes or defect rows of the region
   const uint32_t c0 = chunk * KKT_ROWS;
   const uint32_t nloc = min((uint32_t)KKT_ROWS, nper - c0) * P;
-  const double* src0 = ((R.kind == KR_DEF) ? a.jv : a.hv) + R.src + (int64_t)c0 * R.stride;
-  double* out0 = a.out + R.out + (int64_t)c0 * P;
+  // (the output never aliases the inputs: loads of later slots may be issued before stores)
+  const double* __restrict__ src0 = ((R.kind == KR_DEF) ? a.jv : a.hv) + R.src + (int64_t)c0 * R.stride;
+  double* __restrict__ out0 = a.out + R.out + (int64_t)c0 * P;
 #pragma unroll 4
   for (uint32_t i = threadIdx.x; i < nloc; i += blockDim.x) {
     const uint32_t jl = kkt_div(i, invP);
