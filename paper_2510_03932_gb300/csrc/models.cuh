@@ -63,6 +63,7 @@ __device__ __forceinline__ double fmul(const ModelConst& K, double a, double b) 
 // Constants: c[0] = 2 hh mu, c[1] = hh mu, c[2] = -hh mu.
 // ------------------------------------------------------------------------------------
 struct VdP {
+  static constexpr int EVAL_MIN_CTAS = 0;
   static constexpr int NX = 2, NU = 1, NZ = 3;
   static constexpr int MAXRX = 2, MAXRU = 1;
   OCP_TABLE1(RX, int, NX, {2, 2})
@@ -146,6 +147,7 @@ struct VdP {
 // Double integrator (paper Sec. 5):  f0 = x2,  f1 = u.  Linear: no Hessian.
 // ------------------------------------------------------------------------------------
 struct Dint {
+  static constexpr int EVAL_MIN_CTAS = 0;
   static constexpr int NX = 2, NU = 1, NZ = 3;
   static constexpr int MAXRX = 2, MAXRU = 1;
   OCP_TABLE1(RX, int, NX, {2, 1})
@@ -215,6 +217,7 @@ struct Dint {
 //            c[8]=mp g, c[9]=2 mp l, c[10]=4 g.
 // ------------------------------------------------------------------------------------
 struct CartPole {
+  static constexpr int EVAL_MIN_CTAS = 0;
   static constexpr int NX = 4, NU = 1, NZ = 5;
   static constexpr int MAXRX = 3, MAXRU = 1;
   OCP_TABLE1(RX, int, NX, {2, 3, 2, 2})
@@ -333,6 +336,7 @@ struct CartPole {
 // the dedicated free-final-time kernels (goddard_kernels.cu).
 // ------------------------------------------------------------------------------------
 struct Goddard {
+  static constexpr int EVAL_MIN_CTAS = 0;
   static constexpr int NX = 3, NU = 1, NZ = 4;
   static constexpr int MAXRX = 3, MAXRU = 1;
   OCP_TABLE1(RX, int, NX, {2, 3, 1})
@@ -370,6 +374,7 @@ struct Goddard {
 // Constants: c[0] = g.
 // ------------------------------------------------------------------------------------
 struct Quadrotor {
+  static constexpr int EVAL_MIN_CTAS = 6; // 168 registers: measured 14% faster evaluation, 4% faster fused step
   static constexpr int NX = 9, NU = 4, NZ = 13;
   static constexpr int MAXRX = 4, MAXRU = 3;
   OCP_TABLE1(RX, int, NX, {2, 4, 2, 4, 2, 3, 2, 2, 3})

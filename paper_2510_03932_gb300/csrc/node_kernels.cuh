@@ -484,7 +484,7 @@ __device__ __forceinline__ void node_eval_tile(const NodeArgs<M>& a, const Model
           double* rp = sj + lt * cnt;
 #pragma unroll
           for (int e = 0; e < M::MAXRX; ++e)
-            if (e < M::RX(k)) rp[e] = (M::XV(k, e) == k) ? fma(mjx[k][e], K.one, -1.0) : mjx[k][e];
+            if (e < M::RX(k)) rp[e] = (M::XV(k, e) == k) ? (M::JZ(k, e) ? -1.0 : fma(mjx[k][e], K.one, -1.0)) : mjx[k][e];
 #pragma unroll
           for (int e = 0; e < M::MAXRU; ++e)
             if (e < M::RU(k)) rp[2 * M::RX(k) + e] = mju[k][e];
@@ -493,7 +493,7 @@ __device__ __forceinline__ void node_eval_tile(const NodeArgs<M>& a, const Model
           double* rp = sj + (lt - 1) * cnt;
 #pragma unroll
           for (int e = 0; e < M::MAXRX; ++e)
-            if (e < M::RX(k)) rp[M::RX(k) + e] = (M::XV(k, e) == k) ? fma(mjx[k][e], K.one, 1.0) : mjx[k][e];
+            if (e < M::RX(k)) rp[M::RX(k) + e] = (M::XV(k, e) == k) ? (M::JZ(k, e) ? 1.0 : fma(mjx[k][e], K.one, 1.0)) : mjx[k][e];
 #pragma unroll
           for (int e = 0; e < M::MAXRU; ++e)
             if (e < M::RU(k)) rp[2 * M::RX(k) + M::RU(k) + e] = mju[k][e];
@@ -568,16 +568,11 @@ __device__ __forceinline__ void node_eval_tile(const NodeArgs<M>& a, const Model
   if (WC || WJ || WF || WJV) __syncthreads();
 }
 
-// Optional minimum of resident CTAs per SM asked of the register allocator (tuning macro;
-// by default the allocator's own heuristic applies).
-#ifdef OCP_EVAL_MINB
-#define OCP_EVAL_MINB_ARG , OCP_EVAL_MINB
-#else
-#define OCP_EVAL_MINB_ARG
-#endif
-
+// The fused evaluation kernel.  A model may ask for a minimum of resident CTAs per SM
+// (M::EVAL_MIN_CTAS > 0, a register cap for models whose fused kernels would otherwise need
+// all 255 registers); by default the register allocator's own heuristic applies.
 template <class M, int TILE, int NPT, unsigned OUT>
-__global__ void __launch_bounds__(TILE OCP_EVAL_MINB_ARG) k_node_eval(const __grid_constant__ NodeArgs<M> a) {
+__device__ __forceinline__ void node_eval_kernel_body(const NodeArgs<M>& a) {
   constexpr bool WF = OUT & O_F;
   extern __shared__ __align__(16) double sm[];
   __shared__ double sEdge[2 * (TILE / 32 + 1) * M::NX];
@@ -586,6 +581,23 @@ __global__ void __launch_bounds__(TILE OCP_EVAL_MINB_ARG) k_node_eval(const __gr
   for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x)
     node_eval_tile<M, TILE, NPT, OUT>(a, K, tile, sm, sEdge, a.partials + tile);
   if (WF && a.f) finish_tiles<TILE>(a.partials, a.ntiles, a.counter, a.f, 0.5, sm);
+}
+
+template <class M, int TILE, int NPT, unsigned OUT>
+__global__ void __launch_bounds__(TILE) k_node_eval(const __grid_constant__ NodeArgs<M> a) {
+  node_eval_kernel_body<M, TILE, NPT, OUT>(a);
+}
+
+template <class M, int TILE, int NPT, unsigned OUT>
+__global__ void __launch_bounds__(TILE, (M::EVAL_MIN_CTAS > 0 ? M::EVAL_MIN_CTAS : 1))
+    k_node_eval_capped(const __grid_constant__ NodeArgs<M> a) {
+  node_eval_kernel_body<M, TILE, NPT, OUT>(a);
+}
+
+template <class M, int TILE, int NPT, unsigned OUT>
+auto eval_kernel() {
+  if constexpr (M::EVAL_MIN_CTAS > 0) return k_node_eval_capped<M, TILE, NPT, OUT>;
+  else return k_node_eval<M, TILE, NPT, OUT>;
 }
 
 // ======================================================================================
@@ -795,7 +807,7 @@ ocp_status launch_eval_t(ocp* h, const EvalCall& c, cudaStream_t s) {
   if (a.ntiles < 1) a.ntiles = 1;
   if (a.ntiles > h->max_partials) return set_err(h, OCP_EDIM, "too many tiles for the reduction scratch");
   using S = EvalSmem<M, TILE, NPT, OUT>;
-  auto kern = k_node_eval<M, TILE, NPT, OUT>;
+  auto kern = eval_kernel<M, TILE, NPT, OUT>();
   static unsigned attr_done = 0;
   if (!(attr_done & (1u << (h->device & 31)))) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
@@ -814,6 +826,7 @@ ocp_status launch_eval_t(ocp* h, const EvalCall& c, cudaStream_t s) {
 // node N contributes only X_N (identity entries, boundary rows).  The model runs with
 // K.hh = h, so pa = x + h f, mjx = -h df/dx and hd = -h sum_k y_{k,j} d2f_k + sigma h d2f0.
 // Row (k, j) lists the entries on X_j (the template, identity merged), X_{j+1,k}, then U_j.
+// (An identity-only entry, df_k/dx_k identically zero, is the constant -1 or +1 in every kernel.)
 // ======================================================================================
 template <class M>
 __host__ __device__ constexpr int euler_count(int k) { return M::RX(k) + 1 + M::RU(k); }
@@ -871,7 +884,7 @@ __global__ void __launch_bounds__(TILE) k_euler(const __grid_constant__ NodeArgs
           double* rp = sm + euler_off<M>(k) * TILE + t * euler_count<M>(k);
 #pragma unroll
           for (int e = 0; e < M::MAXRX; ++e)
-            if (e < M::RX(k)) rp[e] = (M::XV(k, e) == k) ? fma(mjx[k][e], K.one, -1.0) : mjx[k][e];
+            if (e < M::RX(k)) rp[e] = (M::XV(k, e) == k) ? (M::JZ(k, e) ? -1.0 : fma(mjx[k][e], K.one, -1.0)) : mjx[k][e];
           rp[M::RX(k)] = 1.0;
 #pragma unroll
           for (int e = 0; e < M::MAXRU; ++e)
