@@ -269,6 +269,39 @@ def run_ours(args, rank, world):
         jh.append((e0, e1))
     torch.cuda.synchronize(dev)
     jh_ms = float(np.mean([a.elapsed_time(b) for a, b in jh]))
+    # --- the same step replayed from a CUDA graph (flushed), and hot (no flush, labelled)
+    graph_ms = None
+    try:
+        gs = torch.cuda.Stream(dev)
+        gs.wait_stream(stream)
+        with torch.cuda.stream(gs):
+            for _ in range(2):
+                step()
+        stream.wait_stream(gs)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            step()
+        gt = []
+        for k in range(min(args.steps, 50)):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            graph.replay()
+            e1.record(stream)
+            gt.append((e0, e1))
+        torch.cuda.synchronize(dev)
+        graph_ms = float(np.mean([a.elapsed_time(b) for a, b in gt]))
+    except Exception:
+        graph_ms = None
+    ht = []
+    for k in range(min(args.steps, 50)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        ht.append((e0, e1))
+    torch.cuda.synchronize(dev)
+    hot_ms = float(np.mean([a.elapsed_time(b) for a, b in ht[3:]]))
     # --- KKT assembly from the step's H and J values (HBM-bound gather), timed the same way
     sig_x = torch.ones(n, dtype=torch.float64, device=dev)
     kv = H.kkt_values(hv, jv, sig_x, 1e-8, 1e-8)
@@ -339,6 +372,8 @@ def run_ours(args, rank, world):
         jac_hess_only=dict(ms=jh_ms, nnz_per_s=nnz / (jh_ms * 1e-3),
                            GBps=algorithmic_bytes(w, "jh") / (jh_ms * 1e-3) / 1e9,
                            frac=algorithmic_bytes(w, "jh") / (jh_ms * 1e-3) / 1e9 / hbm),
+        step_graph_replay_ms=graph_ms,
+        step_hot_ms=hot_ms,   # no L2 flush between steps (the 296 MB step does not fit L2)
         kkt_assembly=dict(ms=kkt_ms, nnz=kv.numel(), GBps=kkt_bytes / (kkt_ms * 1e-3) / 1e9,
                           hbm_frac=kkt_bytes / (kkt_ms * 1e-3) / 1e9 / hbm,
                           what="K = [H + diag(sigma_x + delta_w), J^T; J, -delta_c I] from the COO values"),
@@ -478,9 +513,22 @@ def run_forms(args, hbm):
     def plain_step():
         H.eval_cons(xg.detach())
         H.vjp_param(xg.detach(), wv)
+
+    # the same autograd step with forward and backward captured in CUDA graphs (the Python
+    # and autograd bookkeeping leave the timed path)
+    graphed = None
+    try:
+        gfn = torch.cuda.make_graphed_callables(lambda xx, mm: A.constraints(H, xx, mm), (xg, mu))
+
+        def graphed():
+            cc = gfn(xg, mu)
+            return torch.autograd.grad(cc, (xg, mu), grad_outputs=wv)
+    except Exception as e:  # graph capture unavailable: report the eager form only
+        graph_err = "%s: %s" % (type(e).__name__, e)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     res = {}
-    for nm, fn in (("autograd", ad_step), ("plain", plain_step)):
+    fns = [("autograd", ad_step), ("plain", plain_step)] + ([("graphed", graphed)] if graphed else [])
+    for nm, fn in fns:
         for _ in range(3):
             fn()
         ts = []
@@ -496,6 +544,10 @@ def run_forms(args, hbm):
     out["adjoint"] = dict(workload="vdp_mu_n1e6", step="c(x;mu) forward + (J^T w, dc/dmu^T w) backward",
                           autograd_ms=res["autograd"], plain_ms=res["plain"],
                           overhead=res["autograd"] / res["plain"])
+    if "graphed" in res:
+        out["adjoint"].update(autograd_graphed_ms=res["graphed"], graphed_overhead=res["graphed"] / res["plain"])
+    else:
+        out["adjoint"]["graphed_error"] = graph_err
     return out
 
 
