@@ -571,6 +571,10 @@ def run_profile(args):
         "hprod": lambda: H.hprod(x, y, 1.0, vn, Hv),
         "step": lambda: H.eval_step(x, y, 1.0, vn, vm, (f, c, g, jv, hv, Jv, Jtv, Hv)),
     }
+    if args.profile_kernel == "kkt":  # KKT assembly from this H and J (sigma_x = 1)
+        sx = torch.ones(H.n, dtype=torch.float64, device="cuda")
+        kv = H.kkt_values(hv, jv, sx, 1e-8, 1e-8)
+        calls = {"kkt": lambda: H.kkt_values(hv, jv, sx, 1e-8, 1e-8, out=kv)}
     fns = list(calls.values()) if args.profile_kernel == "all" else [calls[args.profile_kernel]]
     for _ in range(args.warmup + args.steps):
         for fn in fns:
@@ -641,7 +645,7 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip the batched and differentiation forms")
     ap.add_argument("--no-widened", action="store_true", help="skip the further workloads (quadrotor, Goddard)")
     ap.add_argument("--profile-kernel", default=None,
-                    choices=["eval_all", "jh", "jprod", "jtprod", "hprod", "step", "all"],
+                    choices=["eval_all", "jh", "jprod", "jtprod", "hprod", "step", "kkt", "all"],
                     help="only launch this call warmup+steps times (for ncu captures)")
     args = ap.parse_args()
     if args.profile_kernel:
