@@ -78,6 +78,7 @@ __device__ __forceinline__ int kkt_comp(const KktArgs& a, int64_t s) {
 // sit in shared memory.  Moved values are copied bit for bit; the (1,1) diagonal gets
 // sigma_x + delta_w, the constraint diagonal is -delta_c.
 constexpr int KKT_ROWS = 1024;
+constexpr int KKT_BATCH = 4;
 enum { KR_X = 0, KR_U = 1, KR_TF = 2, KR_BND = 3, KR_DEF = 4, KR_XN = 5 };
 
 // floor(i / P) for block-local i < KKT_ROWS * P, P <= 1024: (i + 1/2) / P lies at least 1/(2P) >=
@@ -131,23 +132,33 @@ __global__ void __launch_bounds__(256) k_kkt_values(const __grid_constant__ KktA
   // (the output never aliases the inputs: loads of later slots may be issued before stores)
   const double* __restrict__ src0 = ((R.kind == KR_DEF) ? a.jv : a.hv) + R.src + (int64_t)c0 * R.stride;
   double* __restrict__ out0 = a.out + R.out + (int64_t)c0 * P;
-#pragma unroll 4
-  for (uint32_t i = threadIdx.x; i < nloc; i += blockDim.x) {
-    const uint32_t jl = kkt_div(i, invP);
-    const uint32_t e = i - jl * P;
-    double v;
-    if (R.kind == KR_DEF) {
-      v = (e + 1 == P) ? -a.dc : __ldg(src0 + (i - jl));   // i - jl: the diagonals before this slot
-    } else {
-      const int sp = s_src[e];
-      v = (sp >= 0) ? __ldg(src0 + (int64_t)R.stride * jl + sp) : 0.0;
-      if (s_diag[e]) {
-        const int64_t j = (int64_t)c0 + jl;
-        const int64_t row = (R.kind == KR_X) ? (int64_t)a.nx * j + s_a[e] : a.uoff + (int64_t)a.nu * j + (s_a[e] - a.nx);
-        v = v + ((a.sx ? __ldg(a.sx + row) : 0.0) + a.dw);
+  // KKT_BATCH slots per thread per pass: their loads are issued before any store
+  for (uint32_t i0 = threadIdx.x; i0 < nloc; i0 += KKT_BATCH * 256u) {
+    double v[KKT_BATCH];
+#pragma unroll
+    for (int q = 0; q < KKT_BATCH; ++q) {
+      const uint32_t i = i0 + q * 256u;
+      v[q] = 0.0;
+      if (i >= nloc) continue;
+      const uint32_t jl = kkt_div(i, invP);
+      const uint32_t e = i - jl * P;
+      if (R.kind == KR_DEF) {
+        v[q] = (e + 1 == P) ? -a.dc : __ldg(src0 + (i - jl));   // i - jl: the diagonals before this slot
+      } else {
+        const int sp = s_src[e];
+        v[q] = (sp >= 0) ? __ldg(src0 + (int64_t)R.stride * jl + sp) : 0.0;
+        if (s_diag[e]) {
+          const int64_t j = (int64_t)c0 + jl;
+          const int64_t row = (R.kind == KR_X) ? (int64_t)a.nx * j + s_a[e] : a.uoff + (int64_t)a.nu * j + (s_a[e] - a.nx);
+          v[q] = v[q] + ((a.sx ? __ldg(a.sx + row) : 0.0) + a.dw);
+        }
       }
     }
-    out0[i] = v;
+#pragma unroll
+    for (int q = 0; q < KKT_BATCH; ++q) {
+      const uint32_t i = i0 + q * 256u;
+      if (i < nloc) out0[i] = v[q];
+    }
   }
 }
 
