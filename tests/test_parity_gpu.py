@@ -273,7 +273,8 @@ def test_dimension_and_argument_errors(ocp):
                                     ("dint", 97), ("heat_n2e4", 77), ("quadrotor_n1e3", 1000),
                                     ("goddard_n1e3", 1000), ("vdp_n1e3:euler", 1000),
                                     ("quadrotor_n1e3:euler", 300), ("cartpole_n1e5+path", 700),
-                                    ("goddard_n1e3+path", 500), ("heat_n2e4+path", 40)])
+                                    ("goddard_n1e3+path", 500), ("heat_n2e4+path", 40),
+                                    ("heat_n2e4", 20000), ("heat_n2e4", 2), ("heat_n2e4", 31)])
 def test_fused_step_equals_separate_calls(ocp, name, N):
     """ocp_eval_step (one pass: eval + Jv + J^T w + Hv) is bit-identical to the separate calls."""
     w = named(name, N)
