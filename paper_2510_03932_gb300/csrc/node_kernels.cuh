@@ -186,6 +186,17 @@ __device__ __forceinline__ void load_node(const NodeArgs<M>& a, int64_t j, doubl
   for (int i = 0; i < M::NU; ++i) z[M::NX + i] = __ldg(a.x + a.uoff + M::NU * j + i);
 }
 
+// The model constants of a launch.  With PAR (a device-resident parameter bound by
+// ocp_bind_param0) the parameter-dependent constants are recomputed from it.  PAR is a
+// template argument rather than a run-time test: a branch this short is if-converted, and
+// its predicated-off FP64 instructions would still take FP64 pipe slots in every warp.
+template <class M, bool PAR>
+__device__ __forceinline__ ModelConst launch_consts(const NodeArgs<M>& a) {
+  ModelConst K = a.K;
+  if constexpr (PAR) M::device_param(K, __ldg(a.p0_dev));
+  return K;
+}
+
 // ybar_k = w_{k,j-1} + w_{k,j} over the defect rows of component k (zero outside 0..N-1)
 template <class M>
 __device__ __forceinline__ void load_bar(const NodeArgs<M>& a, const double* w, int64_t j, double (&wb)[M::NX],
@@ -571,33 +582,32 @@ __device__ __forceinline__ void node_eval_tile(const NodeArgs<M>& a, const Model
 // The fused evaluation kernel.  A model may ask for a minimum of resident CTAs per SM
 // (M::EVAL_MIN_CTAS > 0, a register cap for models whose fused kernels would otherwise need
 // all 255 registers); by default the register allocator's own heuristic applies.
-template <class M, int TILE, int NPT, unsigned OUT>
+template <class M, int TILE, int NPT, unsigned OUT, bool PAR>
 __device__ __forceinline__ void node_eval_kernel_body(const NodeArgs<M>& a) {
   constexpr bool WF = OUT & O_F;
   extern __shared__ __align__(16) double sm[];
   __shared__ double sEdge[2 * (TILE / 32 + 1) * M::NX];
-  ModelConst K = a.K;
-  if (a.p0_dev) M::device_param(K, __ldg(a.p0_dev));
+  ModelConst K = launch_consts<M, PAR>(a);
   for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x)
     node_eval_tile<M, TILE, NPT, OUT>(a, K, tile, sm, sEdge, a.partials + tile);
   if (WF && a.f) finish_tiles<TILE>(a.partials, a.ntiles, a.counter, a.f, 0.5, sm);
 }
 
-template <class M, int TILE, int NPT, unsigned OUT>
+template <class M, int TILE, int NPT, unsigned OUT, bool PAR>
 __global__ void __launch_bounds__(TILE) k_node_eval(const __grid_constant__ NodeArgs<M> a) {
-  node_eval_kernel_body<M, TILE, NPT, OUT>(a);
+  node_eval_kernel_body<M, TILE, NPT, OUT, PAR>(a);
 }
 
-template <class M, int TILE, int NPT, unsigned OUT>
+template <class M, int TILE, int NPT, unsigned OUT, bool PAR>
 __global__ void __launch_bounds__(TILE, (M::EVAL_MIN_CTAS > 0 ? M::EVAL_MIN_CTAS : 1))
     k_node_eval_capped(const __grid_constant__ NodeArgs<M> a) {
-  node_eval_kernel_body<M, TILE, NPT, OUT>(a);
+  node_eval_kernel_body<M, TILE, NPT, OUT, PAR>(a);
 }
 
-template <class M, int TILE, int NPT, unsigned OUT>
+template <class M, int TILE, int NPT, unsigned OUT, bool PAR>
 auto eval_kernel() {
-  if constexpr (M::EVAL_MIN_CTAS > 0) return k_node_eval_capped<M, TILE, NPT, OUT>;
-  else return k_node_eval<M, TILE, NPT, OUT>;
+  if constexpr (M::EVAL_MIN_CTAS > 0) return k_node_eval_capped<M, TILE, NPT, OUT, PAR>;
+  else return k_node_eval<M, TILE, NPT, OUT, PAR>;
 }
 
 // ======================================================================================
@@ -605,14 +615,13 @@ auto eval_kernel() {
 // p_k(j) = -hh grad f_k(z_j) . v_{z_j}  (+ -hh df_k/dmu(z_j) * pdir for the parameter).
 // Same overlapping tiles as the evaluation; the right-node term comes from lane+1.
 // ======================================================================================
-template <class M, int TILE, bool PDIR>
+template <class M, int TILE, bool PDIR, bool PAR>
 __global__ void __launch_bounds__(TILE) k_node_jprod(const __grid_constant__ NodeArgs<M> a) {
   constexpr int NX = M::NX, NZ = M::NZ;
   constexpr int NHD = (M::NHD > 0) ? M::NHD : 1;
   __shared__ double sEdge[(TILE / 32 + 1) * NX];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  ModelConst K = a.K;
-  if (a.p0_dev) M::device_param(K, __ldg(a.p0_dev));
+  ModelConst K = launch_consts<M, PAR>(a);
   double pd = 0.0;
   if (PDIR) pd = a.pdir_dev ? __ldg(a.pdir_dev) : a.pdir;
   for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
@@ -667,13 +676,12 @@ __global__ void __launch_bounds__(TILE) k_node_jprod(const __grid_constant__ Nod
 //                     (+ w of the boundary rows at j = 0 / N);  (J^T w)_{U_j,i} likewise.
 // With DPAR, also (dc/dmu)^T w = sum_j sum_k wbar_k mdp_k(z_j) (deterministic reduction).
 // ======================================================================================
-template <class M, int TILE, bool DPAR>
+template <class M, int TILE, bool DPAR, bool PAR>
 __global__ void __launch_bounds__(TILE) k_node_jtprod(const __grid_constant__ NodeArgs<M> a) {
   constexpr int NX = M::NX, NZ = M::NZ;
   constexpr int NHD = (M::NHD > 0) ? M::NHD : 1;
   __shared__ double red[TILE];
-  ModelConst K = a.K;
-  if (a.p0_dev) M::device_param(K, __ldg(a.p0_dev));
+  ModelConst K = launch_consts<M, PAR>(a);
   const int64_t nchunks = (a.N + TILE) / TILE;
   for (int64_t chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
     const int64_t j = chunk * TILE + threadIdx.x;
@@ -710,14 +718,13 @@ __global__ void __launch_bounds__(TILE) k_node_jtprod(const __grid_constant__ No
 // With MIX (autograd double backward), also adds mixs * m_j, m_j = sum_k mixwbar_k
 // (-hh d2 f_k / dmu dz)(z_j), and reduces sum_j m_j . v_{z_j} into *dmu.
 // ======================================================================================
-template <class M, int TILE, bool MIX>
+template <class M, int TILE, bool MIX, bool PAR>
 __global__ void __launch_bounds__(TILE) k_node_hprod(const __grid_constant__ NodeArgs<M> a) {
   constexpr int NX = M::NX, NZ = M::NZ;
   constexpr int NHD = (M::NHD > 0) ? M::NHD : 1;
   constexpr HTmpl<M> HT{};
   __shared__ double red[TILE];
-  ModelConst K = a.K;
-  if (a.p0_dev) M::device_param(K, __ldg(a.p0_dev));
+  ModelConst K = launch_consts<M, PAR>(a);
   double ms = 0.0;
   if (MIX) ms = a.mixs ? __ldg(a.mixs) : 0.0;
   const int64_t nchunks = (a.N + TILE) / TILE;
@@ -793,8 +800,8 @@ void fill_args(const ocp* h, double sigma, NodeArgs<M>& a) {
   for (int i = 0; i < h->ntrk; ++i) a.trk[h->trk_comp[i]] = (int8_t)i;
 }
 
-template <class M, int TILE, int NPT, unsigned OUT>
-ocp_status launch_eval_t(ocp* h, const EvalCall& c, cudaStream_t s) {
+template <class M, int TILE, int NPT, unsigned OUT, bool PAR>
+ocp_status launch_eval_k(ocp* h, const EvalCall& c, cudaStream_t s) {
   NodeArgs<M> a;
   fill_args<M>(h, c.sigma, a);
   a.x = c.x; a.y = c.y; a.f = c.f; a.c = c.c; a.g = c.g; a.jv = c.jv; a.hv = c.hv;
@@ -807,7 +814,7 @@ ocp_status launch_eval_t(ocp* h, const EvalCall& c, cudaStream_t s) {
   if (a.ntiles < 1) a.ntiles = 1;
   if (a.ntiles > h->max_partials) return set_err(h, OCP_EDIM, "too many tiles for the reduction scratch");
   using S = EvalSmem<M, TILE, NPT, OUT>;
-  auto kern = eval_kernel<M, TILE, NPT, OUT>();
+  auto kern = eval_kernel<M, TILE, NPT, OUT, PAR>();
   static unsigned attr_done = 0;
   if (!(attr_done & (1u << (h->device & 31)))) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::bytes);
@@ -817,6 +824,14 @@ ocp_status launch_eval_t(ocp* h, const EvalCall& c, cudaStream_t s) {
   const int grid = occupancy_grid(h, (const void*)kern, TILE, S::bytes, a.ntiles);
   kern<<<grid, TILE, S::bytes, s>>>(a);
   return cuda_err(h, cudaGetLastError(), "k_node_eval launch");
+}
+
+template <class M, int TILE, int NPT, unsigned OUT>
+ocp_status launch_eval_t(ocp* h, const EvalCall& c, cudaStream_t s) {
+  if constexpr (M::HAS_DPARAM) {
+    if (h->p0_dev) return launch_eval_k<M, TILE, NPT, OUT, true>(h, c, s);
+  }
+  return launch_eval_k<M, TILE, NPT, OUT, false>(h, c, s);
 }
 
 // ======================================================================================
@@ -843,7 +858,7 @@ __host__ __device__ constexpr int euler_off(int k) {
   return s;
 }
 
-template <class M, int TILE, unsigned OUT>
+template <class M, int TILE, unsigned OUT, bool PAR>
 __global__ void __launch_bounds__(TILE) k_euler(const __grid_constant__ NodeArgs<M> a) {
   constexpr int NX = M::NX, NZ = M::NZ;
   constexpr bool WF = OUT & O_F, WC = OUT & O_C, WG = OUT & O_G, WJ = OUT & O_J, WH = OUT & O_H;
@@ -856,8 +871,7 @@ __global__ void __launch_bounds__(TILE) k_euler(const __grid_constant__ NodeArgs
   const bool sF = WF && a.f, sC = WC && a.c, sG = WG && a.g, sJ = WJ && a.jv, sH = WH && a.hv;
   const bool doH = sH || WHV;
   const int t = threadIdx.x;
-  ModelConst K = a.K;
-  if (a.p0_dev) M::device_param(K, __ldg(a.p0_dev));
+  ModelConst K = launch_consts<M, PAR>(a);
   const int64_t N = a.N;
   const int64_t xN = (int64_t)NX * N;  // first entry of X_N
   for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
@@ -988,18 +1002,26 @@ __global__ void __launch_bounds__(TILE) k_euler(const __grid_constant__ NodeArgs
   if (sF) finish_tiles<TILE>(a.partials, a.ntiles, a.counter, a.f, 0.5, red);
 }
 
-template <class M, int TILE, unsigned OUT>
-ocp_status launch_euler_t(ocp* h, NodeArgs<M>& a, cudaStream_t s) {
+template <class M, int TILE, unsigned OUT, bool PAR>
+ocp_status launch_euler_k(ocp* h, NodeArgs<M>& a, cudaStream_t s) {
   a.ntiles = (h->N + 1 + TILE - 1) / TILE;
   if (a.ntiles > h->max_partials) return set_err(h, OCP_EDIM, "too many tiles for the reduction scratch");
   const size_t smem = (OUT & O_J) ? sizeof(double) * (size_t)euler_total<M>() * TILE : 0;
-  auto kern = k_euler<M, TILE, OUT>;
+  auto kern = k_euler<M, TILE, OUT, PAR>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_err(h, e, "cudaFuncSetAttribute(euler)");
   }
   kern<<<(int)a.ntiles, TILE, smem, s>>>(a);
   return cuda_err(h, cudaGetLastError(), "k_euler launch");
+}
+
+template <class M, int TILE, unsigned OUT>
+ocp_status launch_euler_t(ocp* h, NodeArgs<M>& a, cudaStream_t s) {
+  if constexpr (M::HAS_DPARAM) {
+    if (a.p0_dev) return launch_euler_k<M, TILE, OUT, true>(h, a, s);
+  }
+  return launch_euler_k<M, TILE, OUT, false>(h, a, s);
 }
 
 template <class M>
@@ -1052,6 +1074,27 @@ ocp_status node_eval_dispatch(ocp* h, unsigned out, const EvalCall& c, cudaStrea
   }
 }
 
+template <class M, int TILE, bool PAR>
+cudaError_t node_prod_launch(ocp* h, const ProdCall& c, const NodeArgs<M>& a, cudaStream_t s) {
+  auto go = [&](auto kern, int64_t units) {
+    const int grid = occupancy_grid(h, (const void*)kern, TILE, 0, units);
+    kern<<<grid, TILE, 0, s>>>(a);
+  };
+  if (c.kind == P_JPROD) {
+    if (c.pdir != 0.0 || c.pdir_dev) go(k_node_jprod<M, TILE, true, PAR>, a.ntiles);
+    else go(k_node_jprod<M, TILE, false, PAR>, a.ntiles);
+  } else if (c.kind == P_JTPROD) {
+    const int64_t blocks = (h->N + TILE) / TILE;
+    if (c.dmu) go(k_node_jtprod<M, TILE, true, PAR>, blocks);
+    else go(k_node_jtprod<M, TILE, false, PAR>, blocks);
+  } else {
+    const int64_t blocks = (h->N + 1 + TILE - 1) / TILE;
+    if (c.mixw && c.mixs) go(k_node_hprod<M, TILE, true, PAR>, blocks);
+    else go(k_node_hprod<M, TILE, false, PAR>, blocks);
+  }
+  return cudaGetLastError();
+}
+
 template <class M, int TILE>
 ocp_status node_prod_dispatch(ocp* h, const ProdCall& c, cudaStream_t s) {
   if (h->scheme == OCP_SCHEME_EULER) return euler_prod_dispatch<M, TILE>(h, c, s);
@@ -1060,44 +1103,12 @@ ocp_status node_prod_dispatch(ocp* h, const ProdCall& c, cudaStream_t s) {
   a.x = c.x; a.y = c.y; a.v = c.v; a.out = c.out; a.dmu = c.dmu;
   a.pdir = c.pdir; a.pdir_dev = c.pdir_dev; a.mixw = c.mixw; a.mixs = c.mixs;
   a.B = 0; a.E = h->N + 1;
+  if (c.kind == P_JPROD) a.ntiles = (h->N + 1 + (TILE - 2)) / (TILE - 1);
   cudaError_t e;
-  if (c.kind == P_JPROD) {
-    a.ntiles = (h->N + 1 + (TILE - 2)) / (TILE - 1);
-    const bool pd = (c.pdir != 0.0) || (c.pdir_dev != nullptr);
-    if (pd) {
-      auto k = k_node_jprod<M, TILE, true>;
-      int grid = occupancy_grid(h, (const void*)k, TILE, 0, a.ntiles);
-      k<<<grid, TILE, 0, s>>>(a);
-    } else {
-      auto k = k_node_jprod<M, TILE, false>;
-      int grid = occupancy_grid(h, (const void*)k, TILE, 0, a.ntiles);
-      k<<<grid, TILE, 0, s>>>(a);
-    }
-    e = cudaGetLastError();
-  } else if (c.kind == P_JTPROD) {
-    const int64_t blocks = (h->N + TILE) / TILE;
-    if (c.dmu) {
-      auto k = k_node_jtprod<M, TILE, true>;
-      int grid = occupancy_grid(h, (const void*)k, TILE, 0, blocks);
-      k<<<grid, TILE, 0, s>>>(a);
-    } else {
-      auto k = k_node_jtprod<M, TILE, false>;
-      int grid = occupancy_grid(h, (const void*)k, TILE, 0, blocks);
-      k<<<grid, TILE, 0, s>>>(a);
-    }
-    e = cudaGetLastError();
+  if constexpr (M::HAS_DPARAM) {
+    e = a.p0_dev ? node_prod_launch<M, TILE, true>(h, c, a, s) : node_prod_launch<M, TILE, false>(h, c, a, s);
   } else {
-    const int64_t blocks = (h->N + 1 + TILE - 1) / TILE;
-    if (c.mixw && c.mixs) {
-      auto k = k_node_hprod<M, TILE, true>;
-      int grid = occupancy_grid(h, (const void*)k, TILE, 0, blocks);
-      k<<<grid, TILE, 0, s>>>(a);
-    } else {
-      auto k = k_node_hprod<M, TILE, false>;
-      int grid = occupancy_grid(h, (const void*)k, TILE, 0, blocks);
-      k<<<grid, TILE, 0, s>>>(a);
-    }
-    e = cudaGetLastError();
+    e = node_prod_launch<M, TILE, false>(h, c, a, s);
   }
   return cuda_err(h, e, "node product launch");
 }
