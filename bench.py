@@ -85,8 +85,8 @@ FP64_OPS_PER_NODE = {("vdp", "eval_all"): 26.6, ("vdp", "jh"): 10.0, ("vdp", "jp
                      ("cartpole", "jtprod"): 78.0, ("cartpole", "hprod"): 114.0, ("cartpole", "step"): 181.0,
                      ("quadrotor", "eval_all"): 260.3, ("quadrotor", "jh"): 180.8, ("quadrotor", "jprod"): 165.5,
                      ("quadrotor", "jtprod"): 157.0, ("quadrotor", "hprod"): 199.0, ("quadrotor", "step"): 398.8,
-                     ("goddard", "eval_all"): 110.3, ("goddard", "jh"): 100.3, ("goddard", "jprod"): 77.3,
-                     ("goddard", "jtprod"): 77.2, ("goddard", "hprod"): 106.2, ("goddard", "step"): 164.4,
+                     ("goddard", "eval_all"): 101.2, ("goddard", "jh"): 91.3, ("goddard", "jprod"): 68.3,
+                     ("goddard", "jtprod"): 68.2, ("goddard", "hprod"): 95.2, ("goddard", "step"): 155.4,
                      ("vdp:euler", "eval_all"): 21.5, ("vdp:euler", "jh"): 8.0, ("vdp:euler", "jprod"): 11.0,
                      ("vdp:euler", "jtprod"): 10.0, ("vdp:euler", "hprod"): 10.0, ("vdp:euler", "step"): 41.5}
 

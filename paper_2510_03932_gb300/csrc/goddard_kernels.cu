@@ -104,8 +104,13 @@ __global__ void __launch_bounds__(GT) k_god(const __grid_constant__ GodArgs a) {
   const bool doH = sH || WHV;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   const int64_t N = a.N;
+  __shared__ double sHH;
   double hh = a.hh_fixed;
-  if (FREE) hh = (__ldg(a.x + a.tau) / (double)N) * 0.5;
+  if (FREE) {  // hh = tf / (2N): one division per CTA (a per-thread division costs every node)
+    if (t == 0) sHH = (__ldg(a.x + a.tau) / (double)N) * 0.5;
+    __syncthreads();
+    hh = sHH;
+  }
   const double mhh = -hh, mk = -a.kappa;
   double vt = 0.0;  // tf component of the direction
   if (FREE && (WJV || WHV)) vt = __ldg(a.vn + a.tau);
@@ -119,6 +124,9 @@ __global__ void __launch_bounds__(GT) k_god(const __grid_constant__ GodArgs a) {
     const int64_t j = r0 + t;
     const bool act = j <= row_end;
     const bool own = t < nown;
+    // the tile holds node 0 or node N (CTA-uniform): boundary-only FP64 work sits behind this
+    // branch, since predicated-off FP64 instructions still take pipe slots in every warp
+    const bool bnd = (r0 == 0) || (own_end == N + 1);
     double pa[3] = {0.0, 0.0, 0.0}, pb[3] = {0.0, 0.0, 0.0};
     double jA[3] = {0.0, 0.0, 0.0}, jB[3] = {0.0, 0.0, 0.0}, fk[3] = {0.0, 0.0, 0.0};
     double accJ = 0.0, accH = 0.0;
@@ -203,14 +211,16 @@ __global__ void __launch_bounds__(GT) k_god(const __grid_constant__ GodArgs a) {
           o[1] = fma(wb[1], jvv, fma(wb[0], mhh, gsub(a, wl[1], wr[1])));
           o[2] = fma(wb[1], jm, gsub(a, wl[2], wr[2]));
           o[3] = fma(wb[2], jmu, gmul(a, wb[1], ju));
-          if (j == 0) {
+          if (bnd) {
+            if (j == 0) {
 #pragma unroll
-            for (int k = 0; k < 3; ++k) o[k] = gadd(a, o[k], __ldg(a.vm + k));
-          }
-          if (j == N) {
+              for (int k = 0; k < 3; ++k) o[k] = gadd(a, o[k], __ldg(a.vm + k));
+            }
+            if (j == N) {
 #pragma unroll
-            for (int k = 0; k < 3; ++k)
-              if (a.finpos[k] >= 0) o[k] = gadd(a, o[k], __ldg(a.vm + 3 + a.finpos[k]));
+              for (int k = 0; k < 3; ++k)
+                if (a.finpos[k] >= 0) o[k] = gadd(a, o[k], __ldg(a.vm + 3 + a.finpos[k]));
+            }
           }
           a.ojtv[3 * j] = o[0]; a.ojtv[3 * j + 1] = o[1]; a.ojtv[3 * j + 2] = o[2];
           a.ojtv[a.uoff + j] = o[3];
@@ -281,7 +291,7 @@ __global__ void __launch_bounds__(GT) k_god(const __grid_constant__ GodArgs a) {
           a.g[a.uoff + j] = 0.0;
           if (FREE && j == 0) a.g[a.tau] = 0.0;
         }
-        if (sF && j == N) *a.f = fma(a.mayer[0], r, fma(a.mayer[1], v, gmul(a, a.mayer[2], m)));
+        if (sF && bnd && j == N) *a.f = fma(a.mayer[0], r, fma(a.mayer[1], v, gmul(a, a.mayer[2], m)));
         if (j == 0) {
 #pragma unroll
           for (int k = 0; k < 3; ++k) {

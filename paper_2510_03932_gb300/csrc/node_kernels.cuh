@@ -926,7 +926,7 @@ __global__ void __launch_bounds__(TILE) k_euler(const __grid_constant__ NodeArgs
           wl[k] = (j >= 1) ? __ldg(row + j - 1) : 0.0;
           wr[k] = __ldg(row + j);
         }
-        jtv_node<M>(a, a.wv, j, j == 0, mjx, mju, wl, wr, wr, o);
+        jtv_node<M>(a, a.wv, j, tile == 0, mjx, mju, wl, wr, wr, o);  // CTA-uniform boundary flag
         store_nz<M>(a, a.ojtv, j, o);
       }
       if (WHV) {
@@ -956,7 +956,7 @@ __global__ void __launch_bounds__(TILE) k_euler(const __grid_constant__ NodeArgs
           if (sJ) a.jv[k] = 1.0;
         }
       }
-    } else if (j == N) {  // the last node: states only
+    } else if (r0 + TILE > N && j == N) {  // the last node: states only (CTA-uniform test first)
       if (sG) {
 #pragma unroll
         for (int k = 0; k < NX; ++k) a.g[xN + k] = 0.0;
