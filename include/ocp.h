@@ -227,6 +227,21 @@ ocp_status ocp_eval_step(ocp_t* h, const double* x, const double* y, double sigm
                          const double* vm, double* f, double* c, double* g, double* jvals,
                          double* hvals, double* Jv, double* Jtv, double* Hv, void* stream);
 
+/* ocp_eval_step with every array in HOST memory (x, y, vn, vm read; f, c, g, jvals, hvals, Jv,
+ * Jtv, Hv written, same lengths and layouts as ocp_eval_step; f is one double).  The handle
+ * keeps device copies of all arrays (allocated on the first call and when the dimensions
+ * change, about 8 (5n + 4m + nnz_J + nnz_H) bytes, freed by ocp_destroy): the inputs are
+ * copied in on an internal stream, the step runs on `stream`, the outputs are copied out on a
+ * second internal stream, and `stream` waits for the last copy.  The call returns once the
+ * work is enqueued; synchronize `stream` before reading the outputs.  Host arrays should be
+ * page-locked (pinned) for asynchronous copies; pageable memory works but the copies then
+ * block the calling thread.  Results are bit-identical to ocp_eval_step.  Calls on one handle
+ * must be ordered on one stream (they share the device copies).  All pointers are required
+ * and 8-byte aligned (OCP_EINVAL otherwise). */
+ocp_status ocp_eval_step_host(ocp_t* h, const double* x, const double* y, double sigma, const double* vn,
+                              const double* vm, double* f, double* c, double* g, double* jvals,
+                              double* hvals, double* Jv, double* Jtv, double* Hv, void* stream);
+
 /* KKT matrix of the interior-point step (paper Sec. 6: the solver assembles the KKT system in
  * device buffers from the derivative values), lower triangle, COO sorted by (row, col):
  *     K = [ H + diag(sigma_x + delta_w)                ]    size (n + m) x (n + m)

@@ -150,6 +150,7 @@ static int model_nparams(int model) {
 
 static void free_handle(ocp* h) {
   if (!h) return;
+  ocpg::host_step_free(h);
   cudaFree(h->d_rowtmpl); cudaFree(h->d_jbase); cudaFree(h->d_hent); cudaFree(h->d_fin); cudaFree(h->d_tcol);
   cudaFree(h->d_kcbase);
   cudaFree(h->d_poff); cudaFree(h->d_pv); cudaFree(h->d_pcoef); cudaFree(h->d_pbase);

@@ -37,6 +37,8 @@ struct RowTemplate {
 // Host pattern: sizes, slot offsets and the node templates (paper Sec. 5: the generators
 // make one row per state component per interval; the pattern compiler lays out the COO
 // slots of every (component, interval) row and of every node's Hessian block).
+struct HostStep;  // see host_step.cu
+
 struct Pattern {
   int nx = 0, nu = 0, nz = 0;
   int64_t N = 0, n = 0, m = 0, nb = 0, nnzj = 0, nnzh = 0;
@@ -121,6 +123,8 @@ struct ocp {
   double* d_partials = nullptr;
   unsigned* d_counter = nullptr;
   int max_partials = 0;
+  // device mirrors, copy streams and events of ocp_eval_step_host (allocated on first use)
+  ocpg::HostStep* hstep = nullptr;
   std::string err;
 };
 
@@ -203,6 +207,8 @@ ocp_status obj_launch(ocp* h, bool hvp, const double* x, const double* s, const 
 ocp_status path_eval(ocp* h, unsigned out, const EvalCall& c, cudaStream_t s);
 ocp_status path_prod(ocp* h, const ProdCall& c, cudaStream_t s);
 ocp_status path_upload(ocp* h);
+// Releases what ocp_eval_step_host allocated (called by ocp_destroy).
+void host_step_free(ocp* h);
 
 
 }  // namespace ocpg

@@ -67,6 +67,7 @@ _SIGS = {
     "hprod": [_P, _P, _P, _D, _P, _P, _P],
     "ocp_eval_all": [_P, _P, _P, _D, _P, _P, _P, _P, _P, _P],
     "ocp_eval_step": [_P, _P, _P, _D, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P],
+    "ocp_eval_step_host": [_P, _P, _P, _D, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P],
     "ocp_eval_all_range": [_P, _I64, _I64, _P, _P, _D, _P, _P, _P, _P, _P, _P],
     "ocp_vjp_param": [_P, _P, _P, _P, _P, _P],
     "ocp_set_param0": [_P, _D],
@@ -319,6 +320,31 @@ class OCP:
                     self._out(None, self.m, "Jv"), self._out(None, self.n, "Jtv"), self._out(None, self.n, "Hv"))
         _check(lib().ocp_eval_step(self.h, _ptr(x), _ptr(y), float(sigma), _ptr(vn), _ptr(vm),
                                    *[_ptr(t) for t in outs], _stream(stream)), self.h)
+        return outs
+
+    def _hvec(self, t, size, name):
+        if t is None:
+            raise ValueError("%s is required" % name)
+        if t.dtype != torch.float64 or t.is_cuda or not t.is_contiguous():
+            raise TypeError("%s must be a contiguous float64 CPU tensor (pinned for overlapped copies)" % name)
+        if t.numel() != size:
+            raise ValueError("%s has %d elements, expected %d" % (name, t.numel(), size))
+        return t
+
+    def eval_step_host(self, x, y, sigma, vn, vm, outs=None, stream=None):
+        """The fused step with host (CPU) tensors in and out, through ocp_eval_step_host: the
+        library copies the inputs to its device copies, runs the step and copies the outputs
+        back, on its own copy streams joined to `stream` (default: the current stream).  The
+        outputs are complete once `stream` is synchronized."""
+        x = self._hvec(x, self.n, "x"); y = self._hvec(y, self.m, "y")
+        vn = self._hvec(vn, self.n, "vn"); vm = self._hvec(vm, self.m, "vm")
+        sizes = ((1, "f"), (self.m, "c"), (self.n, "g"), (self.nnzj, "jvals"), (self.nnzh, "hvals"),
+                 (self.m, "Jv"), (self.n, "Jtv"), (self.n, "Hv"))
+        if outs is None:
+            outs = tuple(torch.empty(k, dtype=torch.float64).pin_memory() for k, _ in sizes)
+        outs = tuple(self._hvec(t, k, nm) for t, (k, nm) in zip(outs, sizes))
+        _check(lib().ocp_eval_step_host(self.h, _ptr(x), _ptr(y), float(sigma), _ptr(vn), _ptr(vm),
+                                        *[_ptr(t) for t in outs], _stream(stream)), self.h)
         return outs
 
     def eval_all_range(self, node_begin, node_end, x, y, sigma, f, c, g, jvals, hvals, stream=None):

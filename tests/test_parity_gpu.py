@@ -288,6 +288,44 @@ def test_fused_step_equals_separate_calls(ocp, name, N):
         assert torch.equal(a, b)
 
 
+@pytest.mark.parametrize("name,N,pinned", [("vdp_n1e3", 1000, True), ("vdp_n1e3", 3000, True), ("vdp_n1e3", 1, True),
+                                           ("vdp_n1e3", 254, False), ("cartpole_n1e5", 1303, True),
+                                           ("quadrotor_n1e3", 700, True), ("dint", 97, True),
+                                           ("vdp_n1e3+path", 1000, True), ("cartpole_n1e5+path", 900, True),
+                                           ("heat_n2e4", 77, True), ("goddard_n1e3", 500, True),
+                                           ("vdp_n1e3:euler", 600, True), ("vdp_mu_n1e6", None, True)])
+def test_host_step_equals_device_step(ocp, name, N, pinned):
+    """ocp_eval_step_host (host arrays in and out, node ranges pipelined over copy streams)
+    returns bit for bit what ocp_eval_step returns on device arrays, on a second call with new
+    inputs too, and on a side stream."""
+    w = named(name, N)
+    H = ocp.OCP.from_workload(w)
+    side = torch.cuda.Stream()
+    for rep, seed in enumerate((1, 2)):
+        d = synth.draw(w, seed=w["seed"] + seed)
+        hin = [torch.from_numpy(d[k]) for k in ("x", "y", "vn", "vm")]
+        if pinned:
+            hin = [t.pin_memory() for t in hin]
+        ref = H.eval_step(*(t.cuda() for t in hin[:2]), 0.7, *(t.cuda() for t in hin[2:]))
+        torch.cuda.synchronize()
+        outs = None if pinned else tuple(torch.empty(t.numel(), dtype=torch.float64) for t in ref)
+        st = side if rep == 1 else None
+        got = H.eval_step_host(hin[0], hin[1], 0.7, hin[2], hin[3], outs=outs, stream=st)
+        (side if rep == 1 else torch.cuda.current_stream()).synchronize()
+        for a, b in zip(got, ref):
+            assert torch.equal(a, b.cpu())
+    H.close()
+
+
+def test_host_step_rejects_device_tensors(ocp):
+    w = named("vdp_n1e3", 100)
+    H = ocp.OCP.from_workload(w)
+    d = synth.draw(w)
+    with pytest.raises(TypeError):
+        H.eval_step_host(dev(d["x"]), torch.from_numpy(d["y"]), 1.0, torch.from_numpy(d["vn"]), torch.from_numpy(d["vm"]))
+    H.close()
+
+
 @pytest.mark.parametrize("name,N", [("vdp_n1e3", 1000), ("cartpole_n1e5", 700), ("heat_n2e4", 40), ("dint", 97),
                                     ("quadrotor_n1e3", 300), ("goddard_n1e3", 500),
                                     ("goddard_fixed", 300), ("vdp_n1e3:euler", 600), ("quadrotor_n1e3:euler", 200),
