@@ -12,8 +12,8 @@
 // by one node (the CTA owns 31 of its 32 nodes); node-local products use disjoint tiles.
 // The states of the tile's nodes are staged in shared memory with a padded row (n+1 doubles)
 // so that lanes reading different nodes hit different banks; node-major outputs (Hessian
-// diagonal, gradient, J^T w, H v) are staged the same way and stored with consecutive
-// threads on consecutive addresses.  Component-major outputs (defects, Jacobian rows, Jv)
+// diagonal, J^T w, H v) are staged the same way and stored with consecutive threads on
+// consecutive addresses, except the gradient, stored by each lane for its eight cells.  Component-major outputs (defects, Jacobian rows, Jv)
 // are consecutive across lanes and are stored directly or through a per-warp row buffer.
 #include <cstring>
 
@@ -45,6 +45,12 @@ struct HeatArgs {
   double ref[HEAT_MAXC + 1];
 };
 
+// Doubles of the first shared-memory region of k_heat_eval: the staged states (32 rows of n+1),
+// and at least the 256 the objective's reductions use when they reuse it.
+__host__ __device__ __forceinline__ int heat_xlen(int n) {
+  return HT_LANES * (n + 1) > HT_THREADS ? HT_LANES * (n + 1) : HT_THREADS;
+}
+
 __device__ __forceinline__ int64_t heat_jbase(const HeatArgs& a, int k) { return a.nb + (int64_t)6 * k * a.N; }
 
 // a + b, a - b, a * b as FMAs against run-time 1 and -0 (same rounding; faster on GB300's FP64 pipe)
@@ -75,12 +81,14 @@ __global__ void __launch_bounds__(HT_THREADS) k_heat_eval(const __grid_constant_
   const bool WF = CF && a.f, WC = CC && a.c, WG = CG && a.g, WJ = CJ && a.jv, WH = CH && a.hv;
   extern __shared__ __align__(16) double sm[];
   const int n = a.n, ld = n + 1;
-  // shared memory: states, then only the staging buffers this variant needs
+  // shared memory: states, then only the staging buffers this variant needs.  The gradient
+  // is stored straight from the cell loop (a lane's eight cells of a group fill whole 32-byte
+  // sectors) and the objective's reduction reuses the states' buffer once the tile's stores
+  // are done: the full evaluation fits five CTAs per SM (one wave of 646 tiles at N = 2e4).
   double* sX = sm;                                             // 32 * ld
-  double* sN = sX + HT_LANES * ld;                             // Hessian diagonal, 31 * ld
-  double* sG = sN + (CH ? (HT_LANES - 1) * ld : 0);            // gradient, 31 * ld
-  double* sJ = sG + (CG ? (HT_LANES - 1) * ld : 0);            // per-warp row buffer 8 * 31 * 6
-  double* red = sJ + (CJ ? HT_WARPS * (HT_LANES - 1) * 6 : 0); // reduction, 256
+  double* sN = sX + heat_xlen(n);                              // Hessian diagonal, 31 * ld
+  double* sJ = sN + (CH ? (HT_LANES - 1) * ld : 0);            // per-warp row buffer 8 * 31 * 6
+  double* red = sX;                                            // reduction, 256 (after the stores)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double objacc = 0.0;
 
@@ -164,19 +172,17 @@ __global__ void __launch_bounds__(HT_THREADS) k_heat_eval(const __grid_constant_
           if (own && j == 0) a.c[k] = xk;
           if (own && a.has_final && j == a.N) a.c[n + k] = xk;
         }
-        if (own) {
-          if (WH) {
-            const double yl = (j >= 1) ? __ldg(a.y + a.nb + (int64_t)k * a.N + j - 1) : 0.0;
-            const double yr = (j < a.N) ? __ldg(a.y + a.nb + (int64_t)k * a.N + j) : 0.0;
-            const double ty = hmul(a, a.h6, hadd(a, yl, yr));
-            sN[t * ld + k] = fma(ty, xk, endp ? a.cq_end[k] : a.cq_in[k]);
-          }
-          if (WG || WF) {
-            const double d = a.has_ref ? hsub(a, xk, a.ref[k]) : xk;
-            const double gk = hmul(a, endp ? a.gq_end[k] : a.gq_in[k], d);
-            if (WF) objacc = fma(gk, d, objacc);
-            if (WG) sG[t * ld + k] = gk;
-          }
+        if (own && WH) {
+          const double yl = (j >= 1) ? __ldg(a.y + a.nb + (int64_t)k * a.N + j - 1) : 0.0;
+          const double yr = (j < a.N) ? __ldg(a.y + a.nb + (int64_t)k * a.N + j) : 0.0;
+          const double ty = hmul(a, a.h6, hadd(a, yl, yr));
+          sN[t * ld + k] = fma(ty, xk, endp ? a.cq_end[k] : a.cq_in[k]);
+        }
+        if (own && (WG || WF)) {
+          const double d = a.has_ref ? hsub(a, xk, a.ref[k]) : xk;
+          const double gk = hmul(a, endp ? a.gq_end[k] : a.gq_in[k], d);
+          if (WF) objacc = fma(gk, d, objacc);
+          if (WG) a.g[(int64_t)n * j + k] = gk;
         }
       }
     }
@@ -189,15 +195,8 @@ __global__ void __launch_bounds__(HT_THREADS) k_heat_eval(const __grid_constant_
         dst[i] = sN[tt * ld + k];
       }
     }
-    if (WG) {
-      const int total = nown * n;
-      double* dst = a.g + (int64_t)n * r0;
-      for (int i = threadIdx.x; i < total; i += HT_THREADS) {
-        const int tt = i / n, k = i - tt * n;
-        dst[i] = sG[tt * ld + k];
-      }
-    }
     if (WF) {
+      __syncthreads();  // red is the states' buffer, read by the loop above
       const double ts = tile_sum<HT_THREADS>(objacc, red, a.one);
       if (threadIdx.x == 0) a.partials[tile] = ts;
       objacc = 0.0;
@@ -386,9 +385,8 @@ static ocp_status heat_eval_t(ocp* h, const EvalCall& c, cudaStream_t s) {
   a.ntiles = (nodes + (HT_LANES - 2)) / (HT_LANES - 1);
   if (a.ntiles < 1) a.ntiles = 1;
   const int ld = h->nx + 1;
-  const size_t smem = sizeof(double) * ((size_t)HT_LANES * ld + ((OUT & O_H) ? (HT_LANES - 1) * ld : 0) +
-                                        ((OUT & O_G) ? (HT_LANES - 1) * ld : 0) +
-                                        ((OUT & O_J) ? HT_WARPS * (HT_LANES - 1) * 6 : 0) + HT_THREADS);
+  const size_t smem = sizeof(double) * ((size_t)heat_xlen(h->nx) + ((OUT & O_H) ? (HT_LANES - 1) * ld : 0) +
+                                        ((OUT & O_J) ? HT_WARPS * (HT_LANES - 1) * 6 : 0));
   auto kern = k_heat_eval<OUT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_err(h, e, "cudaFuncSetAttribute(heat)");

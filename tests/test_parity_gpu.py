@@ -111,6 +111,24 @@ def test_parity_small_horizons(ocp, name, N):
     full_check(ocp, named(name, N))
 
 
+@pytest.mark.parametrize("cells,N", [(2, 40), (3, 31), (7, 33), (8, 64), (13, 100), (128, 45)])
+def test_parity_heat_cell_counts(ocp, cells, N):
+    """The heat model with other cell counts, from the smallest (whose staged states are
+    shorter than the kernel's reduction buffer) to the largest; a step of the eval and the
+    products and eval_obj == eval_all's objective bit for bit."""
+    w = dict(synth.with_horizon(synth.workload("heat_n2e4"), N), nx=cells, params=[float(cells)],
+             q=[1.0] * cells, xref=[0.5] * cells, x0=[0.0] * cells)
+    full_check(ocp, w)
+    d = synth.draw(w)
+    H = ocp.OCP.from_workload(w)
+    x, y = dev(d["x"]), dev(d["y"])
+    f_all = H.eval_all(x, y, 1.0)[0]
+    f_obj = H.eval_obj(x)
+    torch.cuda.synchronize()
+    assert torch.equal(f_all, f_obj)
+    H.close()
+
+
 def test_parity_vdp_mu_variants(ocp):
     w = dict(synth.with_horizon(synth.workload("vdp_n1e3"), 300), params=[2.5])
     full_check(ocp, w)
