@@ -38,6 +38,7 @@ struct HeatArgs {
   int n, has_final, has_ref, hu;
   double hh, mhh, mhidx2;   // hh, -hh, -hh/dx^2
   double d_in, d_last;      // hh * 2/dx^2, hh * 1/dx^2  (diagonal constant of -hh df_k/dx_k)
+  double di_m1, di_p1, dl_m1, dl_p1;  // d_in - 1, d_in + 1, d_last - 1, d_last + 1
   double h3, h6, hidx2;     // 3 hh, 6 hh, hh/dx^2
   double one, mz;           // 1.0 and -0.0 at run time: sums and products are issued as FMAs
   double cq_in[HEAT_MAXC + 1], cq_end[HEAT_MAXC + 1];
@@ -135,19 +136,23 @@ __global__ void __launch_bounds__(HT_THREADS) k_heat_eval(const __grid_constant_
         // -hh df_k/dx_k = hh (2/dx^2 + 3 x^2)  (or 1/dx^2 at the Neumann end)
         const bool last = (k == n - 1);
         if (WJ) {
-          const double dk = fma(a.h3, x2, last ? a.d_last : a.d_in);
+          // the entries on x_k: -1 + dk (left node) and +1 + dk (right node), dk = 3 hh x_k^2 + d,
+          // as fma(3 hh x_k, x_k, d -+ 1)
+          const double h3x = hmul(a, a.h3, xk);
+          const double jl = fma(h3x, xk, last ? a.dl_m1 : a.di_m1);
+          const double jr = fma(h3x, xk, last ? a.dl_p1 : a.di_p1);
           const int cnt = last ? 4 : 6;
           const int rx = (k == 0 || last) ? 2 : 3;
           const int ru = (k == 0) ? 1 : 0;
           const int kd = (k == 0) ? 0 : 1;  // position of cell k among the row's X cells
           if (act && t < nrows) {
             double* rp = sJw + t * cnt;
-            for (int e = 0; e < rx; ++e) rp[e] = (e == kd) ? fma(dk, a.one, -1.0) : a.mhidx2;
+            for (int e = 0; e < rx; ++e) rp[e] = (e == kd) ? jl : a.mhidx2;
             if (ru) rp[2 * rx] = a.mhidx2;
           }
           if (act && t >= 1 && t - 1 < nrows) {
             double* rp = sJw + (t - 1) * cnt;
-            for (int e = 0; e < rx; ++e) rp[rx + e] = (e == kd) ? fma(dk, a.one, 1.0) : a.mhidx2;
+            for (int e = 0; e < rx; ++e) rp[rx + e] = (e == kd) ? jr : a.mhidx2;
             if (ru) rp[2 * rx + 1] = a.mhidx2;
           }
           __syncwarp();
@@ -359,6 +364,10 @@ static void heat_fill(const ocp* h, double sigma, HeatArgs& a) {
   a.hidx2 = h->hh * idx2;
   a.d_in = h->hh * (2.0 * idx2);
   a.d_last = h->hh * idx2;
+  a.di_m1 = a.d_in - 1.0;
+  a.di_p1 = a.d_in + 1.0;
+  a.dl_m1 = a.d_last - 1.0;
+  a.dl_p1 = a.d_last + 1.0;
   a.h3 = 3.0 * h->hh;
   a.h6 = 6.0 * h->hh;
   a.one = 1.0;

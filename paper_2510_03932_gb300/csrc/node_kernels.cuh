@@ -529,6 +529,8 @@ __device__ __forceinline__ void node_eval_tile(const NodeArgs<M>& a, const Model
       if (lane == 0) sEdge[EO + warp * NX + k] = jA[0][k];
     }
   }
+  // the staged Jacobian rows are read by the TMA engine (async proxy) after the barrier
+  if (WJ) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   if (WC || WJ || WJV) __syncthreads();
   if (WJV) {
     constexpr int EO = (TILE / 32 + 1) * NX;
@@ -561,15 +563,35 @@ __device__ __forceinline__ void node_eval_tile(const NodeArgs<M>& a, const Model
       }
     }
   }
-  // ---- coalesced copy-out of the staged Jacobian rows
+  // ---- copy-out of the staged Jacobian rows: the tile's rows of component k are one
+  // contiguous range in shared memory and in jvals.  A range whose two ends are 16-byte
+  // aligned with a multiple of 16 bytes goes out as one bulk copy by the TMA engine (issued
+  // by thread 0); any other range is copied by all threads, coalesced.
   if (sJ) {
+    bool bulk = false;
 #pragma unroll
     for (int k = 0; k < NX; ++k) {
       const int cnt = row_count<M>(k);
       const double* src = sm + jrow_off<M>(k) * R;
       double* dst = a.jv + a.jbase[k] + r0 * cnt;
       const int total = nrows * cnt;
-      for (int i = t; i < total; i += TILE) dst[i] = src[i];
+      const unsigned bytes = 8u * (unsigned)total;
+      const bool aligned = total > 0 && ((reinterpret_cast<uintptr_t>(dst) | reinterpret_cast<uintptr_t>(src) | bytes) & 15u) == 0;
+      if (aligned) {
+        if (t == 0) {
+          const unsigned saddr = static_cast<unsigned>(__cvta_generic_to_shared(src));
+          asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
+                       :: "l"(dst), "r"(saddr), "r"(bytes) : "memory");
+        }
+        bulk = true;
+      } else {
+        for (int i = t; i < total; i += TILE) dst[i] = src[i];
+      }
+    }
+    // the staged rows must have been read before the shared memory is reused or released
+    if (bulk && t == 0) {
+      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+      asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
     }
   }
   if (sF) {
