@@ -1004,15 +1004,31 @@ __global__ void __launch_bounds__(TILE) k_euler(const __grid_constant__ NodeArgs
         for (int k = 0; k < NX; ++k) a.ohv[xN + k] = 0.0;
       }
     }
-    if (sJ) {  // coalesced copy-out of the staged rows
+    if (sJ) {  // copy-out of the staged rows: TMA bulk copies where aligned, else coalesced
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
+      bool bulk = false;
 #pragma unroll
       for (int k = 0; k < NX; ++k) {
         const int cnt = euler_count<M>(k);
         const double* src = sm + euler_off<M>(k) * TILE;
         double* dst = a.jv + a.jbase[k] + r0 * cnt;
         const int total = nrows * cnt;
-        for (int i = t; i < total; i += TILE) dst[i] = src[i];
+        const unsigned bytes = 8u * (unsigned)total;
+        if (total > 0 && ((reinterpret_cast<uintptr_t>(dst) | reinterpret_cast<uintptr_t>(src) | bytes) & 15u) == 0) {
+          if (t == 0) {
+            const unsigned saddr = static_cast<unsigned>(__cvta_generic_to_shared(src));
+            asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
+                         :: "l"(dst), "r"(saddr), "r"(bytes) : "memory");
+          }
+          bulk = true;
+        } else {
+          for (int i = t; i < total; i += TILE) dst[i] = src[i];
+        }
+      }
+      if (bulk && t == 0) {  // the rows must have been read before the next tile restages them
+        asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
       }
     }
     if (sF) {
