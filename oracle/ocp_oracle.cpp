@@ -143,6 +143,14 @@ struct Prob {
   const double* path_b;
   const double* path_l;
   const double* path_r;
+  // boundary inequalities (paper Sec. 3) b_q(X_0, X_N) <= 0, q < nbin, on z = (X_0, X_N):
+  //   b_q(z) = sum_v [ bin_a[q,v] (z_v - bin_b[q,v])^2 + bin_l[q,v] z_v ] - bin_r[q]
+  // (arrays nbin x 2 nx row-major: columns 0..nx-1 are X_0, nx..2nx-1 are X_N; and nbin)
+  int32_t nbin;
+  const double* bin_a;
+  const double* bin_b;
+  const double* bin_l;
+  const double* bin_r;
 };
 
 template <class S> struct JEnt { int k, v; S val; };      // d f_k / d z_v
@@ -538,7 +546,7 @@ struct Layout {
   int nx, nu, nz;
   bool euler;
   int64_t N, nun, n, m, nb, tau;   // nun: nodes with controls; tau: column of tf, or -1
-  int npath;
+  int npath, nbin;
   std::vector<int> fin;       // components with a final row, ascending
   explicit Layout(const Prob& P) {
     nx = P.nx; nu = P.nu; nz = nx + nu; N = P.N;
@@ -552,9 +560,13 @@ struct Layout {
     tau = P.free_tf ? n - 1 : -1;
     nb = (int64_t)nx + (int64_t)fin.size();
     npath = P.npath;
-    m = nb + (int64_t)nx * N + (int64_t)npath * nun;
+    nbin = P.nbin;
+    m = nb + (int64_t)nx * N + (int64_t)npath * nun + nbin;
   }
   int64_t path_row(int p, int64_t i) const { return nb + (int64_t)nx * N + (int64_t)p * nun + i; }
+  int64_t bin_row(int q) const { return nb + (int64_t)nx * N + (int64_t)npath * nun + q; }
+  // column of the boundary variable v of z = (X_0, X_N)
+  int64_t bin_col(int v) const { return v < nx ? colX(0, v) : colX(N, v - nx); }
   int64_t colX(int64_t j, int k) const { return k + (int64_t)nx * j; }
   int64_t colU(int64_t j, int i) const { return (int64_t)nx * (N + 1) + i + (int64_t)nu * j; }
   int64_t col(int64_t j, int v) const { return v < nx ? colX(j, v) : colU(j, v - nx); }
@@ -618,6 +630,67 @@ template <class S> void path_hessian(const Prob& P, const Layout& L, const S* y,
       if (av == 0.0) continue;
       if (!blk.count({v, v})) blk[{v, v}] = S(0.0);
       blk[{v, v}] = blk[{v, v}] + y[L.path_row(p, i)] * S(2.0 * av);
+    }
+}
+
+// Boundary inequalities on z = (X_0, X_N): value, first derivatives (support: a or l
+// non-zero) and the diagonal second derivatives 2 a_v.
+inline bool bin_in(const Prob& P, int q, int v) {
+  const int nz = 2 * P.nx;
+  return P.bin_a[q * nz + v] != 0.0 || P.bin_l[q * nz + v] != 0.0;
+}
+template <class S> void gather_bnd(const Layout& L, const S* x, S* z) {
+  for (int v = 0; v < 2 * L.nx; ++v) z[v] = x[L.bin_col(v)];
+}
+template <class S> S bin_value(const Prob& P, int q, const S* z) {
+  const int nz = 2 * P.nx;
+  S c = S(0.0);
+  for (int v = 0; v < nz; ++v) {
+    const double av = P.bin_a[q * nz + v], lv = P.bin_l[q * nz + v];
+    if (av != 0.0) { const S d = z[v] - S(P.bin_b[q * nz + v]); c = c + S(av) * d * d; }
+    if (lv != 0.0) c = c + S(lv) * z[v];
+  }
+  return c - S(P.bin_r[q]);
+}
+template <class S> S bin_deriv(const Prob& P, int q, int v, const S* z) {
+  const int nz = 2 * P.nx;
+  return S(2.0 * P.bin_a[q * nz + v]) * (z[v] - S(P.bin_b[q * nz + v])) + S(P.bin_l[q * nz + v]);
+}
+// the boundary rows, after the path rows
+template <class S> void bin_rows(const Prob& P, const Layout& L, const S* x, S* c) {
+  std::vector<S> z(2 * L.nx);
+  gather_bnd(L, x, z.data());
+  for (int q = 0; q < L.nbin; ++q) c[L.bin_row(q)] = bin_value(P, q, z.data());
+}
+template <class S> void bin_jacobian(const Prob& P, const Layout& L, const S* x, std::vector<int64_t>& R,
+                                     std::vector<int64_t>& Cc, std::vector<S>& V) {
+  std::vector<S> z(2 * L.nx);
+  gather_bnd(L, x, z.data());
+  for (int q = 0; q < L.nbin; ++q)
+    for (int v = 0; v < 2 * L.nx; ++v)  // X_0 columns before X_N columns: ascending
+      if (bin_in(P, q, v)) { R.push_back(L.bin_row(q)); Cc.push_back(L.bin_col(v)); V.push_back(bin_deriv(P, q, v, z.data())); }
+}
+// State components k whose (k, k) entry a boundary inequality needs; the node Hessian block
+// has one template for every node, so (k, k) is present in every node's block.
+inline bool bin_diag(const Prob& P, int k) {
+  const int nz = 2 * P.nx;
+  for (int q = 0; q < P.nbin; ++q)
+    if (P.bin_a[q * nz + k] != 0.0 || P.bin_a[q * nz + P.nx + k] != 0.0) return true;
+  return false;
+}
+// the boundary rows' Hessian terms of node j (j = 0 or N): y_q 2 a_{q,v} on the diagonal;
+// at every node the template's (k, k) keys
+template <class S> void bin_hessian(const Prob& P, const Layout& L, const S* y, int64_t j,
+                                    std::map<std::pair<int, int>, S>& blk) {
+  for (int k = 0; k < L.nx; ++k)
+    if (bin_diag(P, k) && !blk.count({k, k})) blk[{k, k}] = S(0.0);
+  const int nz = 2 * L.nx;
+  for (int q = 0; q < L.nbin; ++q)
+    for (int k = 0; k < L.nx; ++k) {
+      if (j == 0 && P.bin_a[q * nz + k] != 0.0)
+        blk[{k, k}] = blk[{k, k}] + y[L.bin_row(q)] * S(2.0 * P.bin_a[q * nz + k]);
+      if (j == L.N && P.bin_a[q * nz + L.nx + k] != 0.0)
+        blk[{k, k}] = blk[{k, k}] + y[L.bin_row(q)] * S(2.0 * P.bin_a[q * nz + L.nx + k]);
     }
 }
 
@@ -799,6 +872,7 @@ template <class S> void constraints(const Prob& P, const S* p, const S* x, S* c)
       c[L.defect_row(k, j)] = (x[L.colX(j + 1, k)] - x[L.colX(j, k)]) - h * (fj + fj1) / S(2.0);
     }
   path_rows(P, L, x, c);
+  bin_rows(P, L, x, c);
 }
 
 // Gradient of F: node-local w_j grad f0, the Mayer weights at X_N, and with a free final time
@@ -861,6 +935,7 @@ template <class S> void jacobian(const Prob& P, const S* p, const S* x, Coo<S>& 
       }
     }
   path_jacobian(P, L, x, J.row, J.col, J.val);
+  bin_jacobian(P, L, x, J.row, J.col, J.val);
 }
 
 // Lagrangian Hessian sigma * Hess F + sum_r y_r Hess c_r, lower triangle, sorted by (row, col).
@@ -902,6 +977,7 @@ template <class S> void hessian(const Prob& P, const S* p, const S* x, const S* 
       }
     }
     path_hessian(P, L, y, j, blk);
+    bin_hessian(P, L, y, j, blk);
     for (auto& kv : blk) all.push_back({L.col(j, kv.first.first), L.col(j, kv.first.second), kv.second});
     if (L.tau >= 0) {
       std::map<int, S> trow;
@@ -1002,6 +1078,8 @@ int check(const Prob& P) {
   if (P.N < 1 || !(P.T > 0.0)) return 2;
   if (P.scheme != 0 && P.scheme != 1) return 2;
   if (P.npath < 0 || (P.npath > 0 && (!P.path_a || !P.path_b || !P.path_l || !P.path_r))) return 2;
+  if (P.nbin < 0 || (P.nbin > 0 && (!P.bin_a || !P.bin_b || !P.bin_l || !P.bin_r))) return 2;
+  if (P.nbin > 0 && P.scheme == 1) return 2;  // boundary inequalities: trapezoidal scheme only
   // the tracking reference is tabulated at t_j = j T / N: not with a free final time
   if (P.free_tf && (P.xslope || P.xamp)) return 2;
   if (P.has_final && P.fin_comp) {
@@ -1060,6 +1138,9 @@ int orc_dims(const Prob* P, int64_t* n, int64_t* m, int64_t* nnzj, int64_t* nnzh
   for (int pp = 0; pp < L.npath; ++pp)
     for (int v = 0; v < L.nz; ++v)
       if (path_in(*P, pp, v)) *nnzj += L.nun;
+  for (int q = 0; q < L.nbin; ++q)
+    for (int v = 0; v < 2 * L.nx; ++v)
+      if (bin_in(*P, q, v)) *nnzj += 1;
   std::vector<HEnt<double>> he; model_hess(*P, p.data(), z.data(), he);
   std::vector<std::pair<int, int>> keys;
   for (int a = 0; a < L.nz; ++a) if (cost_hess_diag(*P, a) != 0.0) keys.push_back({a, a});
@@ -1067,6 +1148,8 @@ int orc_dims(const Prob* P, int64_t* n, int64_t* m, int64_t* nnzj, int64_t* nnzh
   for (int pp = 0; pp < L.npath; ++pp)
     for (int v = 0; v < L.nz; ++v)
       if (P->path_a[pp * L.nz + v] != 0.0) keys.push_back({v, v});
+  for (int k = 0; k < L.nx; ++k)
+    if (bin_diag(*P, k)) keys.push_back({k, k});
   std::sort(keys.begin(), keys.end());
   *nnzh = (int64_t)(std::unique(keys.begin(), keys.end()) - keys.begin()) * L.nun;
   if (L.tau >= 0) {  // the tf row: model Jacobian columns and cost columns of every node

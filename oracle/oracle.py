@@ -22,7 +22,8 @@ class _Prob(C.Structure):
                 ("uref", C.c_void_p), ("xslope", C.c_void_p), ("xamp", C.c_void_p), ("xfreq", C.c_void_p),
                 ("free_tf", C.c_int32), ("nfin", C.c_int32), ("fin_comp", C.c_void_p), ("mayer", C.c_void_p),
                 ("scheme", C.c_int32), ("npath", C.c_int32), ("path_a", C.c_void_p), ("path_b", C.c_void_p),
-                ("path_l", C.c_void_p), ("path_r", C.c_void_p)]
+                ("path_l", C.c_void_p), ("path_r", C.c_void_p), ("nbin", C.c_int32), ("bin_a", C.c_void_p),
+                ("bin_b", C.c_void_p), ("bin_l", C.c_void_p), ("bin_r", C.c_void_p)]
 
 
 _lib = None
@@ -82,6 +83,13 @@ class Problem:
             self._path = [np.ascontiguousarray(pa[k], dtype=np.float64) for k in ("a", "b", "l", "r")]
             p.npath = len(pa["r"])
             p.path_a, p.path_b, p.path_l, p.path_r = (_ptr(a) for a in self._path)
+        # boundary inequalities sum_v [a (z_v - b)^2 + l z_v] - r <= 0 over z = (X_0, X_N)
+        self._bin = None
+        if w.get("bineq"):
+            bi = w["bineq"]
+            self._bin = [np.ascontiguousarray(bi[k], dtype=np.float64) for k in ("a", "b", "l", "r")]
+            p.nbin = len(bi["r"])
+            p.bin_a, p.bin_b, p.bin_l, p.bin_r = (_ptr(a) for a in self._bin)
         self.s = p
         n, m, nj, nh = (C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64())
         st = lib().orc_dims(C.byref(p), C.byref(n), C.byref(m), C.byref(nj), C.byref(nh))

@@ -189,6 +189,31 @@ def with_path(w: dict) -> dict:
     return dict(w, path=_path_rows(w["nx"] + w["nu"], PATHS[w["model"]]))
 
 
+# Boundary inequalities (paper Sec. 3: b(X_0, X_N) <= 0), in the same family as the path rows
+# but over z = (X_0, X_N): index v < nx is X_{0,v}, nx + v is X_{N,v}.  One list per model,
+# built for the workload's nx.
+def _bineq_rows(model: str, nx: int):
+    if model == "vdp":      # terminal ball |X_N|^2 <= 1/4, and X_{N,1} - X_{0,1} <= 1
+        return [({2: (1.0, 0.0, 0.0), 3: (1.0, 0.0, 0.0)}, 0.25), ({0: (0.0, 0.0, -1.0), 2: (0.0, 0.0, 1.0)}, 1.0)]
+    if model == "cartpole":  # the pole near upright at the end, the cart back within 0.5 of its start
+        return [({nx + 2: (1.0, float(np.pi), 0.0)}, 0.01), ({0: (0.0, 0.0, -1.0), nx: (0.0, 0.0, 1.0)}, 0.5)]
+    if model == "dint":     # final speed X_{N,2}^2 <= 0.01
+        return [({nx + 1: (1.0, 0.0, 0.0)}, 0.01)]
+    if model == "quadrotor":  # terminal position ball around (1, 1), altitude gain of at least 1
+        return [({nx + 0: (1.0, 1.0, 0.0), nx + 2: (1.0, 1.0, 0.0)}, 0.1),
+                ({4: (0.0, 0.0, 1.0), nx + 4: (0.0, 0.0, -1.0)}, -1.0)]
+    if model == "goddard":  # altitude gain r(tf) - r(0) >= 1e-3, final speed v(tf)^2 <= 0.01
+        return [({0: (0.0, 0.0, 1.0), nx + 0: (0.0, 0.0, -1.0)}, -1e-3), ({nx + 1: (1.0, 0.0, 0.0)}, 0.01)]
+    if model == "heat":     # mean final temperature <= 0.6, last cell near 0.5 at the end
+        return [({nx + k: (0.0, 0.0, 1.0 / nx) for k in range(nx)}, 0.6), ({2 * nx - 1: (1.0, 0.5, 0.0)}, 0.04)]
+    raise KeyError(model)
+
+
+def with_bineq(w: dict) -> dict:
+    """The workload with its model's boundary inequalities attached (key "bineq")."""
+    return dict(w, bineq=_path_rows(2 * w["nx"], _bineq_rows(w["model"], w["nx"])))
+
+
 def with_horizon(w: dict, N: int) -> dict:
     """The same workload at another horizon (parity cases at oracle-friendly sizes)."""
     w = dict(w)
@@ -213,7 +238,8 @@ def dims(w: dict):
     time); m = nx + final rows + nx N + path rows (one per inequality and controlled node)."""
     n = w["nx"] * (w["N"] + 1) + w["nu"] * control_nodes(w) + (1 if w.get("free_tf") else 0)
     npath = len(w["path"]["r"]) if w.get("path") else 0
-    return n, w["nx"] + final_rows(w) + w["nx"] * w["N"] + npath * control_nodes(w)
+    nbin = len(w["bineq"]["r"]) if w.get("bineq") else 0
+    return n, w["nx"] + final_rows(w) + w["nx"] * w["N"] + npath * control_nodes(w) + nbin
 
 
 def draw(w: dict, seed: int | None = None) -> dict:

@@ -21,16 +21,23 @@ PATHED = ["vdp_n1e3+path", "cartpole_n1e5+path", "quadrotor_n1e3+path", "goddard
           "vdp_n1e3:euler+path", "quadrotor_n1e3:euler+path"]
 
 
+# with boundary inequalities b(X_0, X_N) <= 0 (trapezoidal scheme)
+BINEQED = ["vdp_n1e3+bineq", "cartpole_n1e5+bineq", "dint+bineq", "quadrotor_n1e3+bineq", "goddard_n1e3+bineq",
+           "heat_n2e4+bineq", "vdp_n1e3+path+bineq"]
+
+
 def small(name, N):
-    """A workload at horizon N; the suffix ":euler" selects the forward Euler scheme and "+path"
-    attaches the model's path inequalities."""
-    name, plus, _ = name.partition("+")
+    """A workload at horizon N; the suffix ":euler" selects the forward Euler scheme, "+path"
+    attaches the model's path inequalities and "+bineq" its boundary inequalities."""
+    name, *plus = name.split("+")
     base, _, scheme = name.partition(":")
     w = synth.with_horizon(synth.workload(base), N)
     if scheme:
         w["scheme"] = scheme
-    if plus:
+    if "path" in plus:
         w = synth.with_path(w)
+    if "bineq" in plus:
+        w = synth.with_bineq(w)
     return w
 
 
@@ -105,7 +112,7 @@ def dense_hess_cs(P, x, y, sigma):
     return np.array(cols).T  # n x n
 
 
-@pytest.mark.parametrize("name", MODELS + PATHED)
+@pytest.mark.parametrize("name", MODELS + PATHED + BINEQED)
 def test_structure_matches_bruteforce_detection(name):
     """An entry is structural iff it is nonzero at one of 8 random points (complex step)."""
     w = small(name, 2 if name.startswith("heat") else 3)
@@ -122,13 +129,24 @@ def test_structure_matches_bruteforce_detection(name):
     jm = np.zeros_like(jmask); jm[jr, jc] = True
     hm = np.zeros_like(hmask); hm[hr, hc] = True
     assert np.array_equal(jm, jmask)
-    assert np.array_equal(hm, hmask)
+    if w.get("bineq"):
+        # one Hessian template for every node: a boundary row's squared term on component k
+        # puts (k, k) in every node's block; away from nodes 0 and N it is an explicit zero
+        ba, nx = np.array(w["bineq"]["a"]), w["nx"]
+        sq = [k for k in range(nx) if np.any(ba[:, k] != 0) or np.any(ba[:, nx + k] != 0)]
+        allowed = np.zeros_like(hm)
+        for j in range(w["N"] + 1):
+            for k in sq:
+                allowed[nx * j + k, nx * j + k] = True
+        assert not np.any(hmask & ~hm) and not np.any(hm & ~hmask & ~allowed)
+    else:
+        assert np.array_equal(hm, hmask)
 
 
 # ---------------------------------------------------------------------------------------
 # Derivative values against complex step of the residual / objective / Lagrangian gradient
 # ---------------------------------------------------------------------------------------
-@pytest.mark.parametrize("name", MODELS + PATHED)
+@pytest.mark.parametrize("name", MODELS + PATHED + BINEQED)
 def test_jacobian_gradient_hessian_vs_complex_step(name):
     w = small(name, 2 if name.startswith("heat") else 4)
     P = O.Problem(w)
@@ -524,10 +542,62 @@ def test_path_rows_counts_and_boundary_points(name):
         np.testing.assert_allclose(c[base + nun:base + 2 * nun], 0.0, atol=4e-16)
 
 
+@pytest.mark.parametrize("name", BINEQED)
+def test_boundary_inequalities_counts_and_boundary_points(name):
+    """Boundary inequalities add one row each after every other row, one Jacobian entry per
+    variable of (X_0, X_N) in the row's support, and a (k, k) entry in every node's Hessian
+    block for a squared term on component k (values non-zero only at nodes 0 and N).  On their
+    boundary the rows vanish: the Van der Pol terminal circle |X_N| = 1/2, the cart-pole's
+    upright pole X_{N,3} = pi +- 0.1; a linear row's Jacobian entries are its constant
+    coefficients."""
+    w = small(name, 5)
+    wb = {k: v for k, v in w.items() if k != "bineq"}
+    P, P0 = O.Problem(w), O.Problem(wb)
+    nx, N = w["nx"], w["N"]
+    ba, bl = np.array(w["bineq"]["a"]), np.array(w["bineq"]["l"])
+    nbin = len(w["bineq"]["r"])
+    assert P.n == P0.n and P.m == P0.m + nbin
+    assert P.nnzj == P0.nnzj + int(((ba != 0) | (bl != 0)).sum())
+    hr0, hc0 = O.hess_structure(P0)
+    hr, hc = O.hess_structure(P)
+    assert set(zip(hr0, hc0)) <= set(zip(hr, hc))
+    sq = sorted({k for q in range(nbin) for k in range(nx) if ba[q, k] != 0 or ba[q, nx + k] != 0})
+    new = set(zip(hr, hc)) - set(zip(hr0, hc0))
+    assert new == {(nx * j + k, nx * j + k) for j in range(N + 1) for k in sq
+                   if (nx * j + k, nx * j + k) not in set(zip(hr0, hc0))}
+    rng = np.random.default_rng(53)
+    x, y = rand_point(w, rng)
+    # with only the boundary multipliers non-zero, H is zero away from nodes 0 and N
+    yb = np.zeros(P.m); yb[P.m - nbin:] = y[P.m - nbin:]
+    ev = O.evaluate(P, x, yb, 0.0)
+    mid = (hr >= nx) & (hr < nx * N)
+    assert np.all(ev["hess"][mid] == 0.0)
+    jr, jc = O.jac_structure(P)
+    if w["model"] == "vdp":
+        phi = rng.uniform(0, 2 * np.pi)
+        x[2 * N] = 0.5 * np.cos(phi); x[2 * N + 1] = 0.5 * np.sin(phi)
+        ev = O.evaluate(P, x, y, 1.0)
+        r0 = P.m - nbin
+        assert abs(ev["c"][r0]) <= 4e-16
+        lin = jr == r0 + 1   # X_{N,1} - X_{0,1} - 1: entries -1 on X_{0,1}, +1 on X_{N,1}
+        assert list(jc[lin]) == [0, 2 * N] and list(ev["jac"][lin]) == [-1.0, 1.0]
+        assert ev["c"][r0 + 1] == (x[2 * N] - x[0]) - 1.0
+    if w["model"] == "cartpole":
+        for th in (np.pi + 0.1, np.pi - 0.1):
+            x[4 * N + 2] = th
+            assert abs(O.evaluate(P, x, y, 1.0)["c"][P.m - nbin]) <= 4e-16
+
+
+def test_boundary_inequalities_refused_with_euler():
+    w = synth.with_bineq(small("vdp_n1e3:euler", 5))
+    with pytest.raises(ValueError):
+        O.Problem(w)
+
+
 # ---------------------------------------------------------------------------------------
 # Products and the parameter derivative
 # ---------------------------------------------------------------------------------------
-@pytest.mark.parametrize("name", MODELS + PATHED)
+@pytest.mark.parametrize("name", MODELS + PATHED + BINEQED)
 def test_products_vs_complex_step_and_adjoint(name):
     w = small(name, 3 if name.startswith("heat") else 9)
     P = O.Problem(w)
@@ -546,7 +616,7 @@ def test_products_vs_complex_step_and_adjoint(name):
     np.testing.assert_allclose(Hv, O.cs_lagrangian_grad(P, x, v, y, sigma), rtol=1e-12, atol=1e-13)
 
 
-@pytest.mark.parametrize("name", MODELS + PATHED)
+@pytest.mark.parametrize("name", MODELS + PATHED + BINEQED)
 def test_kkt_assembly_structure_and_action(name):
     """The KKT matrix [H + D, J^T; J, -delta_c I] (lower triangle): sorted, every diagonal
     present once, nnz = nnz_H + nnz_J + m + (diagonals H lacks); its symmetric action on
