@@ -16,6 +16,7 @@
  *                                                   by ocp_set_final_components; nb = nx + count)
  *     row  nb + k*N + j    : (X_{j+1,k} - X_{j,k}) - h/2 (f_k(z_j) + f_k(z_{j+1})),  z_j = (X_j, U_j)
  *     then the path inequalities, if any (ocp_set_path_constraints)
+ *     then the boundary inequalities, if any (ocp_set_boundary_inequalities)
  * Objective (Sec. 5 trapezoidal cost): F = sum_j w_j f0(z_j), w_0 = w_N = h/2, else w_j = h.
  * Lagrangian Hessian: H = sigma * Hess F + sum_r y_r Hess c_r (lower triangle stored).
  * Sparse matrices are COO, 0-based, one entry per structural nonzero (a derivative that is
@@ -152,6 +153,23 @@ ocp_status ocp_set_scheme(ocp_t* h, int scheme);
  * form.  Errors: OCP_EINVAL (bad counts, NULL or non-finite arrays, an empty row). */
 ocp_status ocp_set_path_constraints(ocp_t* h, int npath, const double* a, const double* b, const double* l,
                                     const double* r);
+
+/* Boundary inequalities (paper Sec. 3: b(X_0, X_N) <= 0) in the same family over the first
+ * and the last state, z = (X_0, X_N) (2 nx variables: v < nx is X_{0,v}, nx + v is X_{N,v}):
+ *     b_q(z) = sum_v [ a[q,v] (z_v - b[q,v])^2 + l[q,v] z_v ] - r[q] <= 0
+ * (terminal sets, coupling of the start and the end).  Host arrays a, b, l of nbin x 2nx
+ * (row-major) and r of nbin; nbin = 0 removes them (at most 16).  The rows come last: row
+ * nb + nx N + npath nun + q, bounds (-inf, 0] in ocp_bounds.  Row q has one Jacobian entry per
+ * variable with a or l non-zero, X_0 columns before X_N columns (slots after the path rows'
+ * entries); a squared term on component k adds 2 a y_q to the (k, k) Hessian entry of node 0
+ * or node N, and (k, k) becomes structural in every node's block (the node blocks share one
+ * template; the entry is zero at the other nodes).  Every evaluation, product and the KKT
+ * assembly include them (one small kernel after the model's and the path rows' on the same
+ * stream).  Trapezoidal scheme only (OCP_EMODEL with Euler, here or in ocp_set_scheme); not in
+ * node ranges or the batched form (OCP_EMODEL).  Rebuilds the pattern.  Errors: OCP_EINVAL (bad
+ * count, NULL or non-finite arrays, a row without variables). */
+ocp_status ocp_set_boundary_inequalities(ocp_t* h, int nbin, const double* a, const double* b, const double* l,
+                                         const double* r);
 
 /* Free final time (Goddard; paper appendix "tf in R, variable"): enable != 0 appends tf to the
  * unknowns (n grows by one, tf = x[n-1]) and the grid becomes t_j = j tf / N; T of ocp_create

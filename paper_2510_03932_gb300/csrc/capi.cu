@@ -133,7 +133,8 @@ static ocp_status upload_tables(ocp* h) {
     return cuda_err(h, e, "cudaMalloc");
   if ((e = cudaMemcpy(h->d_kcbase, P.kcbase.data(), P.kcbase.size() * 8, cudaMemcpyHostToDevice)) != cudaSuccess)
     return cuda_err(h, e, "cudaMemcpy");
-  return path_upload(h);
+  ocp_status st = path_upload(h);
+  return st == OCP_OK ? bin_upload(h) : st;
 }
 
 static int model_nparams(int model) {
@@ -154,6 +155,7 @@ static void free_handle(ocp* h) {
   cudaFree(h->d_rowtmpl); cudaFree(h->d_jbase); cudaFree(h->d_hent); cudaFree(h->d_fin); cudaFree(h->d_tcol);
   cudaFree(h->d_kcbase);
   cudaFree(h->d_poff); cudaFree(h->d_pv); cudaFree(h->d_pcoef); cudaFree(h->d_pbase);
+  cudaFree(h->d_boff); cudaFree(h->d_bv); cudaFree(h->d_bcoef); cudaFree(h->d_bbase);
   cudaFree(h->d_partials); cudaFree(h->d_counter); cudaFree(h->d_xtrack);
   delete h;
 }
@@ -296,7 +298,8 @@ ocp_status ocp_bounds(const ocp_t* h, double* lvar, double* uvar, double* lcon, 
     if (uvar) uvar[i] = hi;
   }
   const int64_t nfin = h->pat.nb - h->nx;
-  const int64_t prow0 = h->pat.nb + (int64_t)h->nx * h->N;  // path inequalities: (-inf, 0]
+  // path inequalities, then the boundary inequalities: (-inf, 0]
+  const int64_t prow0 = h->pat.nb + (int64_t)h->nx * h->N;
   for (int64_t i = 0; i < h->pat.m; ++i) {
     double lo = 0.0, hi = 0.0;
     if (i < h->nx) lo = hi = h->x0[i];
@@ -322,11 +325,13 @@ static ocp_status model_eval(ocp* h, unsigned out, const EvalCall& c, cudaStream
   return set_err(h, OCP_EMODEL, "unknown model");
 }
 
-// The model's kernel, then (same stream) the path rows and their updates.
+// The model's kernel, then (same stream) the path rows, then the boundary inequalities, with
+// their updates.
 ocp_status ocpg::dispatch_eval(ocp* h, unsigned out, const EvalCall& c, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   ocp_status st = model_eval(h, out, c, s);
   if (st == OCP_OK && h->pat.npath > 0) st = path_eval(h, out, c, s);
+  if (st == OCP_OK && h->pat.nbin > 0) st = bin_eval(h, out, c, s);
   return st;
 }
 
@@ -346,6 +351,7 @@ static ocp_status dispatch_prod(ocp* h, const ProdCall& c, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   ocp_status st = model_prod(h, c, s);
   if (st == OCP_OK && h->pat.npath > 0) st = path_prod(h, c, s);
+  if (st == OCP_OK && h->pat.nbin > 0) st = bin_prod(h, c, s);
   return st;
 }
 
@@ -483,6 +489,8 @@ ocp_status ocp_eval_all_range(ocp_t* h, int64_t node_begin, int64_t node_end, co
     return set_err(h, OCP_EDIM, "node range outside [0, N+1) or empty");
   if (h->model == OCP_MODEL_GODDARD)
     return set_err(h, OCP_EMODEL, "node ranges are not provided for the Goddard model (tf couples every node)");
+  if (h->nbin > 0)
+    return set_err(h, OCP_EMODEL, "node ranges are not provided with boundary inequalities (they couple nodes 0 and N)");
   NEED(x); NEED(y); NEED(f); NEED(cv); NEED(g); NEED(jvals); NEED(hvals);
   EvalCall c;
   c.B = node_begin; c.E = node_end; c.range = true;
@@ -579,9 +587,36 @@ ocp_status ocp_set_path_constraints(ocp_t* h, int npath, const double* a, const 
   return rebuild(h);
 }
 
+ocp_status ocp_set_boundary_inequalities(ocp_t* h, int nbin, const double* a, const double* b, const double* l,
+                                         const double* r) {
+  if (!h) return OCP_EINVAL;
+  const int bz = 2 * h->nx;
+  if (nbin < 0 || nbin > 16) return set_err(h, OCP_EINVAL, "between 0 and 16 boundary inequalities");
+  if (nbin > 0 && (!a || !b || !l || !r)) return set_err(h, OCP_EINVAL, "a, b, l and r are required");
+  if (nbin > 0 && h->scheme == OCP_SCHEME_EULER)
+    return set_err(h, OCP_EMODEL, "boundary inequalities are provided for the trapezoidal scheme");
+  for (int i = 0; i < nbin * bz; ++i)
+    if (!std::isfinite(a[i]) || !std::isfinite(b[i]) || !std::isfinite(l[i]))
+      return set_err(h, OCP_EINVAL, "boundary inequality coefficients must be finite");
+  for (int q = 0; q < nbin; ++q) {
+    if (!std::isfinite(r[q])) return set_err(h, OCP_EINVAL, "boundary inequality coefficients must be finite");
+    bool any = false;
+    for (int v = 0; v < bz; ++v) any = any || a[q * bz + v] != 0.0 || l[q * bz + v] != 0.0;
+    if (!any) return set_err(h, OCP_EINVAL, "a boundary inequality without any variable");
+  }
+  h->nbin = nbin;
+  h->bin_a.assign(a, a + (size_t)nbin * bz);
+  h->bin_b.assign(b, b + (size_t)nbin * bz);
+  h->bin_l.assign(l, l + (size_t)nbin * bz);
+  h->bin_r.assign(r, r + nbin);
+  return rebuild(h);
+}
+
 ocp_status ocp_set_scheme(ocp_t* h, int scheme) {
   if (!h) return OCP_EINVAL;
   if (scheme != OCP_SCHEME_TRAPEZOID && scheme != OCP_SCHEME_EULER) return set_err(h, OCP_EINVAL, "unknown scheme");
+  if (scheme == OCP_SCHEME_EULER && h->nbin > 0)
+    return set_err(h, OCP_EMODEL, "boundary inequalities are provided for the trapezoidal scheme");
   if (scheme == OCP_SCHEME_EULER && (h->model == OCP_MODEL_HEAT1D || h->model == OCP_MODEL_GODDARD))
     return set_err(h, OCP_EMODEL, "the Euler scheme is provided for the VDP, CARTPOLE, DINT and QUADROTOR models");
   h->scheme = scheme;

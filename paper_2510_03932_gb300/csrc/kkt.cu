@@ -17,7 +17,8 @@
 namespace ocpg {
 
 constexpr int KKT_TMAX = 256;   // entries of a node's X or U row template (with added diagonals)
-constexpr int KKT_MAXREG = 5 + 128 + 16;  // X, X_N, U, tf, boundary rows, defect rows per component, path rows
+constexpr int KKT_MAXREG = 5 + 128 + 16 + 16;  // X, X_N, U, tf, boundary rows, defect rows per component,
+                                                // path rows, boundary-inequality rows
 
 // A run of KKT slots with one layout: slot i of the region is KKT entry out + i; its period is
 // the template length (X, U) or the row length plus the diagonal (defects); src / stride give
@@ -44,9 +45,12 @@ struct KktArgs {
   const int64_t* kpbase;   // KKT slots of the path rows (npath + 1)
   const int32_t* poff;     // path rows: support of row p = pv[poff[p] .. poff[p+1])
   const int32_t* pv;
+  const int64_t* kbbase;   // KKT slots of the boundary-inequality rows (nbin + 1)
+  const int32_t* boff;     // their supports: bv[boff[q] .. boff[q+1]) (local indices of (X_0, X_N))
+  const int32_t* bv;
   int64_t N, n, m, nb, uoff, hbase_u, hbase_t, kb_xn, kb_u, kb_t, kb_c, nnzk;
   double dw, dc;
-  int nx, nu, hx, hu, tx, tu, kx, ku, free_tf, euler, npath;
+  int nx, nu, hx, hu, tx, tu, kx, ku, free_tf, euler, npath, nbin;
   int64_t nun, prow0;
   int16_t ksrc[2 * KKT_TMAX];  // X template then U template: source position or -1
   int16_t ka[2 * KKT_TMAX], kb[2 * KKT_TMAX];
@@ -195,6 +199,17 @@ __global__ void k_kkt_structure(const __grid_constant__ KktArgs a) {
       row = a.n + r;
       if ((s - a.kb_c) & 1) col = row;
       else col = (r < a.nx) ? r : (int64_t)a.nx * a.N + a.fin[r - a.nx];
+    } else if (a.nbin > 0 && s >= a.kbbase[0]) {  // boundary-inequality rows: entries, diagonal
+      int q = 0;
+      while (q + 1 < a.nbin && a.kbbase[q + 1] <= s) ++q;
+      const int cnt = a.boff[q + 1] - a.boff[q];
+      const int e = (int)(s - a.kbbase[q]);
+      row = a.n + a.prow0 + (int64_t)a.npath * a.nun + q;
+      if (e == cnt) col = row;
+      else {
+        const int v = a.bv[a.boff[q] + e];
+        col = v < a.nx ? v : (int64_t)a.nx * a.N + (v - a.nx);
+      }
     } else if (a.npath > 0 && s >= a.kpbase[0]) {  // path rows: their entries, then the diagonal
       int p = 0;
       while (p + 1 < a.npath && a.kpbase[p + 1] <= s) ++p;
@@ -244,13 +259,14 @@ static ocp_status kkt_fill(const ocp* h, KktArgs& a) {
   a.kb_xn = (int64_t)a.kx * P.nun;
   a.npath = P.npath; a.nun = P.nun; a.prow0 = P.nb + (int64_t)h->nx * h->N;
   a.kpbase = h->d_pbase + (P.npath + 1); a.poff = h->d_poff; a.pv = h->d_pv;
+  a.nbin = P.nbin; a.kbbase = h->d_bbase + (P.nbin + 1); a.boff = h->d_boff; a.bv = h->d_bv;
   for (int i = 0; i < a.kx; ++i) { a.ksrc[i] = (int16_t)P.kxt[i].src; a.ka[i] = (int16_t)P.kxt[i].a; a.kb[i] = (int16_t)P.kxt[i].b; }
   for (int i = 0; i < a.ku; ++i) {
     a.ksrc[KKT_TMAX + i] = (int16_t)P.kut[i].src;
     a.ka[KKT_TMAX + i] = (int16_t)P.kut[i].a;
     a.kb[KKT_TMAX + i] = (int16_t)P.kut[i].b;
   }
-  if (h->nx + 5 + P.npath > KKT_MAXREG) return OCP_EDIM;
+  if (h->nx + 5 + P.npath + P.nbin > KKT_MAXREG) return OCP_EDIM;
   auto add = [&](int kind, int64_t out, int64_t len, uint32_t period, int64_t src, uint32_t stride) {
     if (len <= 0) return;
     KRegion& r = a.reg[a.nreg++];
@@ -267,6 +283,9 @@ static ocp_status kkt_fill(const ocp* h, KktArgs& a) {
   for (int p = 0; p < P.npath; ++p)  // path rows: the same layout (entries, then the diagonal)
     add(KR_DEF, P.kpbase[p], P.kpbase[p + 1] - P.kpbase[p], (uint32_t)(P.psupp[p].size() + 1), P.jpbase[p],
         (uint32_t)P.psupp[p].size());
+  for (int q = 0; q < P.nbin; ++q)  // boundary-inequality rows: one row each (entries, then the diagonal)
+    add(KR_DEF, P.kbbase[q], P.kbbase[q + 1] - P.kbbase[q], (uint32_t)(P.bsupp[q].size() + 1), P.jbbase[q],
+        (uint32_t)P.bsupp[q].size());
   // blocks of the values kernel: KKT_ROWS periods of a row region per block, or
   // blockDim * KKT_ROWS slots of a short region
   uint32_t b = 0;

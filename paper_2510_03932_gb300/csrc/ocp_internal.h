@@ -75,6 +75,13 @@ struct Pattern {
   std::vector<int64_t> jpbase;           // npath + 1
   std::vector<int64_t> kpbase;           // KKT slots of the path rows (npath + 1)
   std::vector<int> hdiag;                // position of (v, v) in its node block (X or U), or -1
+  // boundary inequalities b_q(X_0, X_N) <= 0: rows nb + nx N + npath nun + q (after the path
+  // rows); row q has its entries on the variables bsupp[q] of z = (X_0, X_N) (local, ascending:
+  // v < nx is X_{0,v}, nx + v is X_{N,v}) at jbbase[q]..; KKT slots kbbase[q]..
+  int nbin = 0;
+  std::vector<std::vector<int>> bsupp;
+  std::vector<int64_t> jbbase;           // nbin + 1
+  std::vector<int64_t> kbbase;           // nbin + 1
 };
 
 }  // namespace ocpg
@@ -97,6 +104,10 @@ struct ocp {
   // path inequalities sum_v [a (z_v - b)^2 + l z_v] - r <= 0 (npath x (nx+nu), row-major)
   int npath = 0;
   std::vector<double> path_a, path_b, path_l, path_r;
+  // boundary inequalities sum_v [a (z_v - b)^2 + l z_v] - r <= 0 on z = (X_0, X_N)
+  // (nbin x 2 nx, row-major)
+  int nbin = 0;
+  std::vector<double> bin_a, bin_b, bin_l, bin_r;
   const double* p0_dev = nullptr;  // device scalar overriding params[0] (or null)
   // time-varying state reference: xref_k + xslope_k t_j + xamp_k sin(xfreq_k t_j) for the
   // components trk_comp (ntrk of them), tabulated once per node in d_xtrack[(N+1) x ntrk]
@@ -119,6 +130,12 @@ struct ocp {
   int32_t* d_pv = nullptr;
   double* d_pcoef = nullptr;     // pa, pb, pl of every term (3 per term), then pr (npath)
   int64_t* d_pbase = nullptr;    // jpbase (npath + 1) then kpbase (npath + 1)
+  // boundary inequalities on the device: row q's terms boff[q]..boff[q+1]-1 with variable bv
+  // (local index of z = (X_0, X_N)) and coefficients a, b, l; then r (nbin)
+  int32_t* d_boff = nullptr;
+  int32_t* d_bv = nullptr;
+  double* d_bcoef = nullptr;
+  int64_t* d_bbase = nullptr;    // jbbase (nbin + 1) then kbbase (nbin + 1)
   // scratch: per-CTA partial sums and the completion ticket of the last-block reduction
   double* d_partials = nullptr;
   unsigned* d_counter = nullptr;
@@ -207,6 +224,11 @@ ocp_status obj_launch(ocp* h, bool hvp, const double* x, const double* s, const 
 ocp_status path_eval(ocp* h, unsigned out, const EvalCall& c, cudaStream_t s);
 ocp_status path_prod(ocp* h, const ProdCall& c, cudaStream_t s);
 ocp_status path_upload(ocp* h);
+// Boundary inequalities: their rows, Jacobian entries and the updates of H (nodes 0 and N),
+// J^T w and H v, after the path rows' kernel on the same stream (see bineq_kernels.cu).
+ocp_status bin_eval(ocp* h, unsigned out, const EvalCall& c, cudaStream_t s);
+ocp_status bin_prod(ocp* h, const ProdCall& c, cudaStream_t s);
+ocp_status bin_upload(ocp* h);
 // Releases what ocp_eval_step_host allocated (called by ocp_destroy).
 void host_step_free(ocp* h);
 

@@ -96,12 +96,13 @@ bool build_pattern(ocp* h, std::string& why) {
   P.nun = (P.scheme == OCP_SCHEME_EULER) ? P.N : P.N + 1;
   P.n = (int64_t)P.nx * (P.N + 1) + (int64_t)P.nu * P.nun + P.free_tf;
   P.npath = h->npath;
+  P.nbin = h->nbin;
   if (h->has_final) {
     if (h->fin_comp.empty()) for (int k = 0; k < P.nx; ++k) P.fin.push_back(k);
     else P.fin = h->fin_comp;
   }
   P.nb = (int64_t)P.nx + (int64_t)P.fin.size();
-  P.m = P.nb + (int64_t)P.nx * P.N + (int64_t)P.npath * P.nun;
+  P.m = P.nb + (int64_t)P.nx * P.N + (int64_t)P.npath * P.nun + P.nbin;
   model_row_templates(h->model, h->nx, P.rows);
   if ((int)P.rows.size() != P.nx) { why = "no row template for this model"; return false; }
   P.jbase.assign(P.nx + 1, 0);
@@ -117,6 +118,17 @@ bool build_pattern(ocp* h, std::string& why) {
     P.jpbase[p + 1] = P.jpbase[p] + (int64_t)P.psupp[p].size() * P.nun;
   }
   P.nnzj = P.jpbase[P.npath];
+  // boundary-inequality rows after the path rows: one entry per variable of (X_0, X_N) in the
+  // row's support, X_0 columns before X_N columns
+  const int bz = 2 * P.nx;
+  P.bsupp.assign(P.nbin, std::vector<int>());
+  P.jbbase.assign(P.nbin + 1, P.nnzj);
+  for (int q = 0; q < P.nbin; ++q) {
+    for (int v = 0; v < bz; ++v)
+      if (h->bin_a[q * bz + v] != 0.0 || h->bin_l[q * bz + v] != 0.0) P.bsupp[q].push_back(v);
+    P.jbbase[q + 1] = P.jbbase[q] + (int64_t)P.bsupp[q].size();
+  }
+  P.nnzj = P.jbbase[P.nbin];
   std::vector<std::pair<int, int>> ent;
   std::vector<int> dyn;
   model_hess_max_template(h->model, h->nx, ent, dyn);
@@ -126,8 +138,11 @@ bool build_pattern(ocp* h, std::string& why) {
   for (size_t e = 0; e < ent.size(); ++e) {
     const int a = ent[e].first, b = ent[e].second;
     const double coef = a < P.nx ? h->q[a] : h->r[a - P.nx];
-    bool path_sq = false;  // a squared path term needs the diagonal
+    bool path_sq = false;  // a squared path or boundary term needs the diagonal
     for (int p = 0; p < P.npath && a == b; ++p) path_sq = path_sq || h->path_a[p * P.nz + a] != 0.0;
+    // (one template for every node: a boundary term's diagonal is present at every node)
+    for (int q = 0; q < P.nbin && a == b && a < P.nx; ++q)
+      path_sq = path_sq || h->bin_a[q * bz + a] != 0.0 || h->bin_a[q * bz + P.nx + a] != 0.0;
     const bool present = dyn[e] || (a == b && (coef != 0.0 || path_sq));
     if (!present) continue;
     if (a < P.nx) { P.hpos[e] = (int8_t)(px < 127 ? px : 127); ++px; ex.push_back(ent[e]); }
@@ -181,7 +196,9 @@ bool build_pattern(ocp* h, std::string& why) {
   for (int k = 0; k < P.nx; ++k) P.kcbase[k + 1] = P.kcbase[k] + (int64_t)(P.row_count(k) + 1) * P.N;
   P.kpbase.assign(P.npath + 1, P.kcbase[P.nx]);
   for (int p = 0; p < P.npath; ++p) P.kpbase[p + 1] = P.kpbase[p] + (int64_t)(P.psupp[p].size() + 1) * P.nun;
-  P.nnzk = P.kpbase[P.npath];
+  P.kbbase.assign(P.nbin + 1, P.kpbase[P.npath]);
+  for (int q = 0; q < P.nbin; ++q) P.kbbase[q + 1] = P.kbbase[q] + (int64_t)P.bsupp[q].size() + 1;
+  P.nnzk = P.kbbase[P.nbin];
   const int64_t lim = (int64_t)1 << 31;
   if (P.nnzk >= lim || P.n + P.m >= lim) P.nnzk = -1;
   if (P.n >= lim || P.m >= lim || P.nnzj >= lim || P.nnzh >= lim) {
@@ -203,8 +220,11 @@ struct JacStructArgs {
   const int64_t* pbase;  // path rows: first slot of row p (npath + 1)
   const int32_t* poff;   // path rows: support of row p = pv[poff[p] .. poff[p+1])
   const int32_t* pv;
+  const int64_t* bbase;  // boundary-inequality rows: first slot of row q (nbin + 1)
+  const int32_t* boff;   // their supports: bv[boff[q] .. boff[q+1]) (local indices of (X_0, X_N))
+  const int32_t* bv;
   int64_t N, nb, nnzj, uoff, n, nun, prow0;   // prow0: first path row
-  int nx, nu, free_tf, euler, npath;
+  int nx, nu, free_tf, euler, npath, nbin;
 };
 
 __global__ void k_jac_structure(const __grid_constant__ JacStructArgs a) {
@@ -214,6 +234,12 @@ __global__ void k_jac_structure(const __grid_constant__ JacStructArgs a) {
     if (s < a.nb) {
       row = s;
       col = (s < a.nx) ? s : (int64_t)a.nx * a.N + a.fin[s - a.nx];
+    } else if (a.nbin > 0 && s >= a.bbase[0]) {  // boundary-inequality rows
+      int q = 0;
+      while (q + 1 < a.nbin && a.bbase[q + 1] <= s) ++q;
+      const int v = a.bv[a.boff[q] + (int)(s - a.bbase[q])];
+      row = a.prow0 + (int64_t)a.npath * a.nun + q;
+      col = v < a.nx ? v : (int64_t)a.nx * a.N + (v - a.nx);
     } else if (a.npath > 0 && s >= a.pbase[0]) {  // path rows
       int p = 0;
       while (p + 1 < a.npath && a.pbase[p + 1] <= s) ++p;
@@ -293,6 +319,7 @@ ocp_status launch_jac_structure(const ocp* h, int32_t* rows, int32_t* cols, cuda
   a.nx = h->nx; a.nu = h->nu; a.free_tf = h->pat.free_tf; a.euler = h->pat.scheme == OCP_SCHEME_EULER;
   a.pbase = h->d_pbase; a.poff = h->d_poff; a.pv = h->d_pv; a.npath = h->pat.npath;
   a.nun = h->pat.nun; a.prow0 = h->pat.nb + (int64_t)h->nx * h->N;
+  a.bbase = h->d_bbase; a.boff = h->d_boff; a.bv = h->d_bv; a.nbin = h->pat.nbin;
   const int64_t blocks = std::min<int64_t>((a.nnzj + 255) / 256, (int64_t)h->num_sms * 16);
   k_jac_structure<<<(int)std::max<int64_t>(blocks, 1), 256, 0, s>>>(a);
   return cudaGetLastError() == cudaSuccess ? OCP_OK : OCP_ECUDA;

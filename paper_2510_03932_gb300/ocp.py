@@ -47,6 +47,7 @@ _SIGS = {
     "ocp_set_free_final_time": [_P, C.c_int],
     "ocp_set_scheme": [_P, C.c_int],
     "ocp_set_path_constraints": [_P, C.c_int, _P, _P, _P, _P],
+    "ocp_set_boundary_inequalities": [_P, C.c_int, _P, _P, _P, _P],
     "ocp_set_final_components": [_P, C.c_int, _P, _P],
     "ocp_set_terminal_cost": [_P, _P],
     "ocp_set_variable_bounds": [_P, _P, _P, _P, _P, _D, _D],
@@ -122,7 +123,7 @@ class OCP:
 
     def __init__(self, model: str, nx: int, nu: int, N: int, T: float, params, q, r, xref=None, uref=None,
                  x0=None, xf=None, xslope=None, xamp=None, xfreq=None, free_tf=False, xf_comp=None,
-                 mayer=None, bounds=None, scheme="trapezoid", path=None):
+                 mayer=None, bounds=None, scheme="trapezoid", path=None, bineq=None):
         L = lib()
         self._keep = []
 
@@ -152,6 +153,10 @@ class OCP:
             flat = lambda rows: [float(v) for row in rows for v in row]
             _check(L.ocp_set_path_constraints(h, len(path["r"]), arr(flat(path["a"])), arr(flat(path["b"])),
                                               arr(flat(path["l"])), arr(path["r"])), h)
+        if bineq:  # rows sum_v [a (z_v - b)^2 + l z_v] - r <= 0 over z = (X_0, X_N)
+            flat = lambda rows: [float(v) for row in rows for v in row]
+            _check(L.ocp_set_boundary_inequalities(h, len(bineq["r"]), arr(flat(bineq["a"])), arr(flat(bineq["b"])),
+                                                   arr(flat(bineq["l"])), arr(bineq["r"])), h)
         if free_tf:
             _check(L.ocp_set_free_final_time(h, 1), h)
         if mayer is not None:
@@ -174,7 +179,7 @@ class OCP:
         return cls(w["model"], w["nx"], w["nu"], w["N"], w["T"], w["params"], w["q"], w["r"], w.get("xref"),
                    w.get("uref"), w.get("x0"), w.get("xf"), w.get("xslope"), w.get("xamp"), w.get("xfreq"),
                    bool(w.get("free_tf")), w.get("xf_comp"), w.get("mayer"), w.get("bounds"),
-                   w.get("scheme", "trapezoid"), w.get("path"))
+                   w.get("scheme", "trapezoid"), w.get("path"), w.get("bineq"))
 
     def close(self):
         if getattr(self, "h", None):

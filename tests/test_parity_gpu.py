@@ -35,16 +35,18 @@ def host(t):
 
 def named(name, N=None):
     """A workload by name (":euler" selects the forward Euler scheme, "+path" attaches the
-    model's path inequalities), optionally at horizon N."""
-    name, plus, _ = name.partition("+")
+    model's path inequalities, "+bineq" its boundary inequalities), optionally at horizon N."""
+    name, *plus = name.split("+")
     base, _, scheme = name.partition(":")
     w = synth.workload(base)
     if N is not None:
         w = synth.with_horizon(w, N)
     if scheme:
         w = dict(w, scheme=scheme)
-    if plus:
+    if "path" in plus:
         w = synth.with_path(w)
+    if "bineq" in plus:
+        w = synth.with_bineq(w)
     return w
 
 
@@ -103,7 +105,10 @@ SMALL = [("vdp_n1e3", N) for N in (1, 2, 3, 254, 255, 256, 510, 1000, 1777)] + \
         [("quadrotor_n1e3:euler", N) for N in (1, 63, 64, 65, 700)] + \
         [(nm + "+path", N) for nm in ("vdp_n1e3", "cartpole_n1e5", "dint", "quadrotor_n1e3", "goddard_n1e3",
                                        "heat_n2e4", "vdp_n1e3:euler", "quadrotor_n1e3:euler")
-         for N in (1, 300)]
+         for N in (1, 300)] + \
+        [(nm + "+bineq", N) for nm in ("vdp_n1e3", "cartpole_n1e5", "dint", "quadrotor_n1e3", "goddard_n1e3",
+                                        "heat_n2e4", "vdp_n1e3+path")
+         for N in (1, 2, 300)]
 
 
 @pytest.mark.parametrize("name,N", SMALL)
@@ -292,7 +297,9 @@ def test_dimension_and_argument_errors(ocp):
                                     ("goddard_n1e3", 1000), ("vdp_n1e3:euler", 1000),
                                     ("quadrotor_n1e3:euler", 300), ("cartpole_n1e5+path", 700),
                                     ("goddard_n1e3+path", 500), ("heat_n2e4+path", 40),
-                                    ("heat_n2e4", 20000), ("heat_n2e4", 2), ("heat_n2e4", 31)])
+                                    ("heat_n2e4", 20000), ("heat_n2e4", 2), ("heat_n2e4", 31),
+                                    ("vdp_n1e3+bineq", 700), ("goddard_n1e3+bineq", 500), ("heat_n2e4+bineq", 40),
+                                    ("dint+path+bineq", 97)])
 def test_fused_step_equals_separate_calls(ocp, name, N):
     """ocp_eval_step (one pass: eval + Jv + J^T w + Hv) is bit-identical to the separate calls."""
     w = named(name, N)
@@ -311,7 +318,8 @@ def test_fused_step_equals_separate_calls(ocp, name, N):
                                            ("quadrotor_n1e3", 700, True), ("dint", 97, True),
                                            ("vdp_n1e3+path", 1000, True), ("cartpole_n1e5+path", 900, True),
                                            ("heat_n2e4", 77, True), ("goddard_n1e3", 500, True),
-                                           ("vdp_n1e3:euler", 600, True), ("vdp_mu_n1e6", None, True)])
+                                           ("vdp_n1e3:euler", 600, True), ("vdp_mu_n1e6", None, True),
+                                           ("quadrotor_n1e3+bineq", 300, True)])
 def test_host_step_equals_device_step(ocp, name, N, pinned):
     """ocp_eval_step_host (host arrays in and out, node ranges pipelined over copy streams)
     returns bit for bit what ocp_eval_step returns on device arrays, on a second call with new
@@ -347,7 +355,9 @@ def test_host_step_rejects_device_tensors(ocp):
 @pytest.mark.parametrize("name,N", [("vdp_n1e3", 1000), ("cartpole_n1e5", 700), ("heat_n2e4", 40), ("dint", 97),
                                     ("quadrotor_n1e3", 300), ("goddard_n1e3", 500),
                                     ("goddard_fixed", 300), ("vdp_n1e3:euler", 600), ("quadrotor_n1e3:euler", 200),
-                                    ("quadrotor_n1e3+path", 300), ("vdp_n1e3:euler+path", 400)])
+                                    ("quadrotor_n1e3+path", 300), ("vdp_n1e3:euler+path", 400),
+                                    ("vdp_n1e3+bineq", 300), ("dint+path+bineq", 97), ("goddard_n1e3+bineq", 200),
+                                    ("heat_n2e4+bineq", 30)])
 def test_kkt_assembly(ocp, name, N):
     """KKT structure bit-exact with the oracle's assembly; values are the GPU's own H and J
     values moved bit for bit (plus sigma_x + delta_w on the diagonal) and pass the parity gate
@@ -410,6 +420,39 @@ def test_euler_scheme_entry_checks(ocp):
     assert st == 5
     with pytest.raises(ocp.OcpError):
         ocp.OCPBatch([V])
+
+
+def test_boundary_inequalities_bounds_checks_and_refusals(ocp):
+    """Boundary-inequality rows are (-inf, 0] and come last; bad arguments are refused; Euler,
+    node ranges and the batched form refuse them."""
+    import ctypes as C
+    w = named("cartpole_n1e5+bineq", 20)
+    H = ocp.OCP.from_workload(w)
+    lv, uv, lc, uc = H.bounds()
+    nbin = len(w["bineq"]["r"])
+    assert np.all(np.isneginf(lc[-nbin:])) and np.all(uc[-nbin:] == 0.0)
+    assert np.all(lc[:-nbin] == uc[:-nbin])
+    L = ocp.lib()
+    z = (C.c_double * 8)(*([0.0] * 8))
+    r = (C.c_double * 1)(1.0)
+    assert L.ocp_set_boundary_inequalities(H.h, 1, C.cast(z, C.c_void_p), C.cast(z, C.c_void_p),
+                                           C.cast(z, C.c_void_p), C.cast(r, C.c_void_p)) == 1  # no variable
+    assert L.ocp_set_boundary_inequalities(H.h, 17, None, None, None, None) == 1
+    assert L.ocp_set_scheme(H.h, 1) == 5  # OCP_EMODEL: Euler with boundary inequalities
+    d = synth.draw(w)
+    x, y = dev(d["x"]), dev(d["y"])
+    f, c, g, jv, hv = H.eval_all(x, y, 1.0)
+    assert L.ocp_eval_all_range(H.h, 0, 10, ocp._ptr(x), ocp._ptr(y), 1.0, ocp._ptr(f), ocp._ptr(c), ocp._ptr(g),
+                                ocp._ptr(jv), ocp._ptr(hv), None) == 5
+    with pytest.raises(ocp.OcpError):
+        ocp.OCPBatch([H])
+    # removing them restores the plain problem
+    assert L.ocp_set_boundary_inequalities(H.h, 0, None, None, None, None) == 0
+    P0 = O.Problem({k: v for k, v in w.items() if k != "bineq"})
+    n, m, nj, nh = (C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64())
+    assert L.ocp_dims(H.h, C.byref(n), C.byref(m), C.byref(nj), C.byref(nh)) == 0
+    assert (n.value, m.value, nj.value, nh.value) == (P0.n, P0.m, P0.nnzj, P0.nnzh)
+    H.close()
 
 
 def test_path_rows_bounds_and_checks(ocp):
