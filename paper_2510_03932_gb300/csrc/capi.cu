@@ -94,6 +94,7 @@ ocp_status fill_tracking(ocp* h) {
 static bool aligned8(const void* p) { return ((uintptr_t)p & 7u) == 0; }
 
 static ocp_status upload_tables(ocp* h) {
+  ocpg::scatter_map_free(h);  // built from the previous pattern
   cudaFree(h->d_rowtmpl); cudaFree(h->d_jbase); cudaFree(h->d_hent); cudaFree(h->d_fin); cudaFree(h->d_tcol);
   cudaFree(h->d_kcbase);
   h->d_rowtmpl = nullptr; h->d_jbase = nullptr; h->d_hent = nullptr; h->d_fin = nullptr; h->d_tcol = nullptr;
@@ -152,6 +153,7 @@ static int model_nparams(int model) {
 static void free_handle(ocp* h) {
   if (!h) return;
   ocpg::host_step_free(h);
+  ocpg::scatter_map_free(h);
   cudaFree(h->d_rowtmpl); cudaFree(h->d_jbase); cudaFree(h->d_hent); cudaFree(h->d_fin); cudaFree(h->d_tcol);
   cudaFree(h->d_kcbase);
   cudaFree(h->d_poff); cudaFree(h->d_pv); cudaFree(h->d_pcoef); cudaFree(h->d_pbase);

@@ -37,7 +37,8 @@ struct RowTemplate {
 // Host pattern: sizes, slot offsets and the node templates (paper Sec. 5: the generators
 // make one row per state component per interval; the pattern compiler lays out the COO
 // slots of every (component, interval) row and of every node's Hessian block).
-struct HostStep;  // see host_step.cu
+struct HostStep;    // see host_step.cu
+struct ScatterMap;  // see scatter_map.cu
 
 struct Pattern {
   int nx = 0, nu = 0, nz = 0;
@@ -142,6 +143,9 @@ struct ocp {
   int max_partials = 0;
   // device mirrors, copy streams and events of ocp_eval_step_host (allocated on first use)
   ocpg::HostStep* hstep = nullptr;
+  // the Jacobian's per-variable scatter map for ocp_jtprod_coo (built on first use, dropped
+  // when the pattern is rebuilt)
+  ocpg::ScatterMap* smap = nullptr;
   std::string err;
 };
 
@@ -229,6 +233,8 @@ ocp_status path_upload(ocp* h);
 ocp_status bin_eval(ocp* h, unsigned out, const EvalCall& c, cudaStream_t s);
 ocp_status bin_prod(ocp* h, const ProdCall& c, cudaStream_t s);
 ocp_status bin_upload(ocp* h);
+// Releases the scatter map (called on every pattern rebuild and by ocp_destroy).
+void scatter_map_free(ocp* h);
 // Releases what ocp_eval_step_host allocated (called by ocp_destroy).
 void host_step_free(ocp* h);
 

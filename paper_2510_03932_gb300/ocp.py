@@ -48,6 +48,8 @@ _SIGS = {
     "ocp_set_scheme": [_P, C.c_int],
     "ocp_set_path_constraints": [_P, C.c_int, _P, _P, _P, _P],
     "ocp_set_boundary_inequalities": [_P, C.c_int, _P, _P, _P, _P],
+    "ocp_jac_scatter_map": [_P, _P, _P, _P, _P],
+    "ocp_jtprod_coo": [_P, _P, _P, _P, _P],
     "ocp_set_final_components": [_P, C.c_int, _P, _P],
     "ocp_set_terminal_cost": [_P, _P],
     "ocp_set_variable_bounds": [_P, _P, _P, _P, _P, _D, _D],
@@ -351,6 +353,22 @@ class OCP:
         _check(lib().ocp_eval_step_host(self.h, _ptr(x), _ptr(y), float(sigma), _ptr(vn), _ptr(vm),
                                         *[_ptr(t) for t in outs], _stream(stream)), self.h)
         return outs
+
+    def jac_scatter_map(self, stream=None):
+        """(colptr, rows, slots): the Jacobian's COO in column order (int32 CUDA tensors)."""
+        colptr = torch.empty(self.n + 1, dtype=torch.int32, device=self.device)
+        rows = torch.empty(max(self.nnzj, 1), dtype=torch.int32, device=self.device)
+        slots = torch.empty(max(self.nnzj, 1), dtype=torch.int32, device=self.device)
+        _check(lib().ocp_jac_scatter_map(self.h, _ptr(colptr), _ptr(rows), _ptr(slots), _stream(stream)), self.h)
+        return colptr, rows[:self.nnzj], slots[:self.nnzj]
+
+    def jtprod_coo(self, jvals, w, out=None, stream=None):
+        """J^T w from stored Jacobian values (ocp_jtprod_coo)."""
+        jvals = self._vec(jvals, self.nnzj, "jvals")
+        w = self._vec(w, self.m, "w")
+        out = self._out(out, self.n, "Jtw")
+        _check(lib().ocp_jtprod_coo(self.h, _ptr(jvals), _ptr(w), _ptr(out), _stream(stream)), self.h)
+        return out
 
     def eval_all_range(self, node_begin, node_end, x, y, sigma, f, c, g, jvals, hvals, stream=None):
         _check(lib().ocp_eval_all_range(self.h, int(node_begin), int(node_end), _ptr(x), _ptr(y), float(sigma),
