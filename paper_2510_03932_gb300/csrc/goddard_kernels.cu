@@ -347,7 +347,8 @@ __global__ void __launch_bounds__(GT) k_god(const __grid_constant__ GodArgs a) {
       }
     }
     if (FREE && WJ) __syncthreads();
-    // ---- coalesced copy-out of the staged Jacobian rows
+    // ---- copy-out of the staged Jacobian rows, coalesced (row counts are odd here, so the
+    // ranges are not 16-byte aligned for a bulk copy)
     if (sJ) {
       const int cnt[3] = {CR, CV, CM};
       const int soff[3] = {0, OV, OM};

@@ -9,15 +9,16 @@
 // tiles in a fixed round-robin order.
 //
 // Data movement.  Each thread loads its node z_j = (X_j, U_j) and, for the Hessian, the
-// multiplier sums ybar_{j,k} = y_{k,j-1} + y_{k,j} (component-major, coalesced).  The
-// tile's Jacobian rows, Hessian blocks and gradient entries are staged in shared memory in
-// their final COO order and written out with consecutive threads on consecutive addresses;
-// defect rows are already consecutive in j and are stored directly.
+// multiplier sums ybar_{j,k} = y_{k,j-1} + y_{k,j} (component-major, coalesced).  The tile's
+// Jacobian rows are staged in shared memory in their final COO order (each component's rows
+// one contiguous range) and leave by TMA bulk copies; Hessian blocks, gradient entries and the
+// node-local products are stored directly by their thread; defect rows and Jv rows are
+// consecutive in j and stored directly.
 //
 // Objective.  Each thread accumulates 2 w_j f0(z_j) = sum_a g_a d_a (g the gradient entry,
-// d = z - ref) over its nodes; a fixed-shape tree reduces it per CTA, and the last CTA to
-// finish (completion ticket) sums the per-CTA partials in index order.  The result is
-// therefore deterministic for a given grid.
+// d = z - ref) over its nodes; a fixed-shape tree reduces it per tile into the tile's slot,
+// and the last CTA to finish (completion ticket) sums the slots in tile order.  The result is
+// therefore deterministic for a given tile size, whatever the grid.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
