@@ -347,8 +347,8 @@ __global__ void __launch_bounds__(GT) k_god(const __grid_constant__ GodArgs a) {
       }
     }
     if (FREE && WJ) __syncthreads();
-    // ---- copy-out of the staged Jacobian rows, coalesced (row counts are odd here, so the
-    // ranges are not 16-byte aligned for a bulk copy)
+    // ---- copy-out of the staged Jacobian rows, coalesced (with the free final time every row
+    // holds an odd number of entries, so a tile's range alternates its 16-byte phase)
     if (sJ) {
       const int cnt[3] = {CR, CV, CM};
       const int soff[3] = {0, OV, OM};
