@@ -74,6 +74,13 @@ def test_create_rejects_bad_arguments_on_the_host(lib):
     assert create(lib, 1, [1.0], 2, 1, kind=7)[0] == 5          # unknown cost kind
     assert create(lib, 3, [200.0], 200, 1)[0] == 2              # heat: ncell out of range
     assert create(lib, 1, [1.0], 2, 1, N=2**31)[0] == 2         # n >= 2^31 does not fit int32 COO
+    # the first horizon whose Jacobian no longer fits the int32 COO interface, while n still
+    # does: Van der Pol nnz_J = 2 + 10 N >= 2^31 from N = 214748365; heat-64 nnz_J = 64 + 382 N
+    assert create(lib, 1, [1.0], 2, 1, N=214748365)[0] == 2
+    assert create(lib, 3, [64.0], 64, 1, N=(2**31 - 64 + 381) // 382)[0] == 2
+    # one node fewer passes the host checks (here it stops at the missing device instead)
+    assert create(lib, 1, [1.0], 2, 1, N=214748364)[0] != 2
+    assert create(lib, 3, [64.0], 64, 1, N=(2**31 - 64 + 381) // 382 - 1)[0] != 2
 
 
 def test_null_handle_is_rejected(lib):
