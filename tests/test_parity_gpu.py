@@ -212,13 +212,14 @@ def test_parity_cost_structure_follows_weights(ocp):
 
 @pytest.mark.parametrize("name", ["vdp_n1e3", "cartpole_n1e5", "heat_n2e4", "vdp_mu_n1e6", "quadrotor_n1e5",
                                   "goddard_n1e5", "cartpole_n1e5:euler", "quadrotor_n1e5:euler",
-                                  "quadrotor_n1e5+path"])
+                                  "quadrotor_n1e5+path", "cartpole_n1e5+bineq", "goddard_n1e5+path+bineq"])
 def test_parity_full_size_workloads(ocp, name):
     rep = full_check(ocp, named(name), products=(name != "vdp_mu_n1e6"))
     print(name, rep)
 
 
-@pytest.mark.parametrize("name", ["cartpole_n1e5", "goddard_n1e3", "cartpole_n1e5:euler"])
+@pytest.mark.parametrize("name", ["cartpole_n1e5", "goddard_n1e3", "cartpole_n1e5:euler", "vdp_n1e3+path+bineq",
+                                  "goddard_n1e3+bineq", "heat_n2e4+bineq"])
 def test_every_slot_written_once_and_nothing_beyond(ocp, name):
     """NaN-prefilled outputs with guard words after the end: every slot gets a finite value
     and no guard word changes."""
