@@ -688,9 +688,17 @@ def main():
         cb = dict(value=v, unit="nnz/s", cores=cores, kind="oracle",
                   sample="%s: %d processes, each the full step (eval + 3 products) on its own %d-node shard, "
                          "%.1f s per step" % (w["name"], cores, Ns, budget))
+        from oracle import oracle as O
+        P = O.Problem(w)
+        nnz = P.nnzj + P.nnzh
         print(json.dumps(dict(metric=METRIC, value=v, unit="nnz/s", n_gpus=1, steps=args.steps, warmup=args.warmup,
-                              higher_is_better=True, impl="reference", dtype="f64", data="synthetic",
-                              config=dict(workload=args.workload, model=w["model"], N=w["N"]),
+                              # the time one step of the whole workload takes at the sampled rate
+                              ms_per_step=nnz / v * 1e3, higher_is_better=True, scaling="weak", vs_baseline=None,
+                              impl="reference", dtype="f64", data="synthetic",
+                              config=dict(workload=args.workload, model=w["model"], N=w["N"], n=P.n, m=P.m,
+                                          nnz_jac=P.nnzj, nnz_hess=P.nnzh,
+                                          step="the oracle's full step: F, c, grad, J, H, Jv, J^T w, Hv",
+                                          parallelism="host cores"),
                               cpu_baseline=cb, e2e=dict(value=v, unit="nnz/s", h2d_bytes_per_step=0,
                                                         d2h_bytes_per_step=0))))
         return
