@@ -473,6 +473,32 @@ def test_jtprod_from_stored_values(ocp, name, N):
     H.close()
 
 
+@pytest.mark.parametrize("name,N", [("vdp_n1e3", 1000), ("vdp_n1e3:euler", 1000), ("quadrotor_n1e3", 300),
+                                    ("vdp_mu_n1e6", None)])
+def test_jacobian_copy_out_paths_agree(ocp, name, N):
+    """The staged Jacobian rows leave by TMA bulk copies when a range is 16-byte aligned and by
+    the thread loop otherwise: jvals at an 8-byte offset (every range misaligned for Van der Pol)
+    gets the same values, bit for bit, in the plain evaluation and in the fused step."""
+    w = named(name, N)
+    d = synth.draw(w)
+    H = ocp.OCP.from_workload(w)
+    x, y, vn, vm = dev(d["x"]), dev(d["y"]), dev(d["vn"]), dev(d["vm"])
+    ref = H.eval_all(x, y, 1.0)[3]
+    buf = torch.full((H.nnzj + 2,), float("nan"), dtype=torch.float64, device="cuda")
+    shifted = buf[1:1 + H.nnzj]
+    assert shifted.data_ptr() % 16 == 8
+    H.jac_coo_values(x, shifted)
+    torch.cuda.synchronize()
+    assert torch.equal(shifted, ref) and torch.isnan(buf[0]) and torch.isnan(buf[-1])
+    outs = list(H.eval_step(x, y, 1.0, vn, vm))
+    outs[3] = shifted
+    shifted.fill_(float("nan"))
+    H.eval_step(x, y, 1.0, vn, vm, tuple(outs))
+    torch.cuda.synchronize()
+    assert torch.equal(shifted, ref)
+    H.close()
+
+
 def test_boundary_inequalities_bounds_checks_and_refusals(ocp):
     """Boundary-inequality rows are (-inf, 0] and come last; bad arguments are refused; Euler,
     node ranges and the batched form refuse them."""
