@@ -82,8 +82,8 @@ def _counts(w):
 # Goddard) and 1e6 (Van der Pol).
 FP64_OPS_PER_NODE = {("vdp", "eval_all"): 26.6, ("vdp", "jh"): 10.0, ("vdp", "jprod"): 13.0,
                      ("vdp", "jtprod"): 12.0, ("vdp", "hprod"): 11.0, ("vdp", "step"): 50.6,
-                     ("cartpole", "eval_all"): 133.9, ("cartpole", "jh"): 110.9, ("cartpole", "jprod"): 81.6,
-                     ("cartpole", "jtprod"): 78.0, ("cartpole", "hprod"): 114.0, ("cartpole", "step"): 181.0,
+                     ("cartpole", "eval_all"): 127.9, ("cartpole", "jh"): 103.8, ("cartpole", "jprod"): 81.6,
+                     ("cartpole", "jtprod"): 78.0, ("cartpole", "hprod"): 108.0, ("cartpole", "step"): 174.0,
                      ("quadrotor", "eval_all"): 260.3, ("quadrotor", "jh"): 180.8, ("quadrotor", "jprod"): 165.5,
                      ("quadrotor", "jtprod"): 157.0, ("quadrotor", "hprod"): 199.0, ("quadrotor", "step"): 398.8,
                      ("goddard", "eval_all"): 101.2, ("goddard", "jh"): 91.3, ("goddard", "jprod"): 68.3,

@@ -295,27 +295,30 @@ struct CartPole {
         mju[3][0] = fmul(K, mhh, thdd_F);
       }
       if (WH) {
+        // Every second derivative above is (numerator) / D: the multipliers carry the 1/D,
+        // m1 = -hh ybar_1 / D and m3 = -hh ybar_3 / D, and the numerators are combined directly.
+        const double m1 = fmul(K, fmul(K, mhh, yb[1]), iD), m3 = fmul(K, fmul(K, mhh, yb[3]), iD);
         const double pdd_w = fmul(K, A_w, iD);
         const double Dpp = fmul(K, mp2, c2s2);
-        const double my1 = fmul(K, mhh, yb[1]), my3 = fmul(K, mhh, yb[3]);
+        const double mDp2 = fmul(K, -2.0, Dp);
         // A_tt = -mp s (l w^2 + 4 g c)
         const double A_tt = fmul(K, -ms, fma(g4, c, lw2));
-        const double pdd_tt = fmul(K, fma(-pdd, Dpp, fma(fmul(K, -2.0, pdd_t), Dp, A_tt)), iD);
+        const double n_pdd_tt = fma(-pdd, Dpp, fma(pdd_t, mDp2, A_tt));
         const double A_tw = fmul(K, lw, c);
-        const double pdd_tw = fmul(K, fma(-pdd_w, Dp, A_tw), iD);
-        const double pdd_ww = fmul(K, fmul(K, mpl2, s), iD);
-        const double pdd_tF = fmul(K, fmul(K, -Dp, iD), iD);
+        const double n_pdd_tw = fma(-pdd_w, Dp, A_tw);
+        const double n_pdd_ww = fmul(K, mpl2, s);
+        const double n_pdd_tF = fmul(K, -Dp, iD);
         // B_tt = F c + 4 mp l w^2 s c + (mc+mp) g s
         const double B_tt = fma(F, c, fmul(K, s, fma(fmul(K, 4.0, mplw2), c, Mg)));
-        const double thdd_tt = fmul(K, fma(-thdd, Dpp, fma(fmul(K, -2.0, thdd_t), Dp, fmul(K, B_tt, il))), iD);
+        const double n_thdd_tt = fma(-thdd, Dpp, fma(thdd_t, mDp2, fmul(K, B_tt, il)));
         const double B_tw = fmul(K, -lw, c2s2);
-        const double thdd_tw = fmul(K, fma(-thdd_w, Dp, fmul(K, B_tw, il)), iD);
-        const double thdd_ww = fmul(K, fmul(K, -mp2, sc), iD);
-        const double thdd_tF = fmul(K, fma(-thdd_F, Dp, fmul(K, s, il)), iD);
-        hd[0] = fma(my1, pdd_tt, fma(my3, thdd_tt, cqd[2]));   // (th, th)
-        hd[1] = fma(my1, pdd_tw, fmul(K, my3, thdd_tw));       // (w, th)
-        hd[2] = fma(my1, pdd_ww, fma(my3, thdd_ww, cqd[3]));   // (w, w)
-        hd[3] = fma(my1, pdd_tF, fmul(K, my3, thdd_tF));       // (F, th)
+        const double n_thdd_tw = fma(-thdd_w, Dp, fmul(K, B_tw, il));
+        const double n_thdd_ww = fmul(K, -mp2, sc);
+        const double n_thdd_tF = fma(-thdd_F, Dp, fmul(K, s, il));
+        hd[0] = fma(m1, n_pdd_tt, fma(m3, n_thdd_tt, cqd[2]));   // (th, th)
+        hd[1] = fma(m1, n_pdd_tw, fmul(K, m3, n_thdd_tw));       // (w, th)
+        hd[2] = fma(m1, n_pdd_ww, fma(m3, n_thdd_ww, cqd[3]));   // (w, w)
+        hd[3] = fma(m1, n_pdd_tF, fmul(K, m3, n_thdd_tF));       // (F, th)
       }
     }
   }
