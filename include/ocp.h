@@ -264,15 +264,20 @@ ocp_status ocp_eval_step(ocp_t* h, const double* x, const double* y, double sigm
 
 /* ocp_eval_step with every array in HOST memory (x, y, vn, vm read; f, c, g, jvals, hvals, Jv,
  * Jtv, Hv written, same lengths and layouts as ocp_eval_step; f is one double).  The handle
- * keeps device copies of all arrays (allocated on the first call and when the dimensions
- * change, about 8 (5n + 4m + nnz_J + nnz_H) bytes, freed by ocp_destroy): the inputs are
- * copied in on an internal stream, the step runs on `stream`, the outputs are copied out on a
- * second internal stream, and `stream` waits for the last copy.  The call returns once the
- * work is enqueued; synchronize `stream` before reading the outputs.  Host arrays should be
- * page-locked (pinned) for asynchronous copies; pageable memory works but the copies then
- * block the calling thread.  Results are bit-identical to ocp_eval_step.  Calls on one handle
- * must be ordered on one stream (they share the device copies).  All pointers are required
- * and 8-byte aligned (OCP_EINVAL otherwise). */
+ * keeps two sets of device copies of all arrays (allocated on the first call and when the
+ * dimensions change, about 16 (5n + 4m + nnz_J + nnz_H) bytes in all, freed by ocp_destroy) and
+ * alternates between them: the inputs are copied in on an internal stream (once the call
+ * before the previous one has copied its outputs out of that set), the step runs on `stream`,
+ * the outputs are copied out on a second internal stream, and `stream` waits for that copy.
+ * So consecutive calls on one stream overlap one call's input copy with the previous call's
+ * output copy, and a call's outputs are complete when `stream` reaches its end (synchronize it
+ * before reading them).  The input copy waits only for the handle's earlier calls, not for
+ * other work on `stream`: the host inputs must be ready when the call is made, and must not
+ * change before the call's work on `stream` is complete.  Host arrays should be page-locked (pinned)
+ * for asynchronous copies; pageable memory works but the copies then block the calling
+ * thread.  Results are bit-identical to ocp_eval_step.  Calls on one handle must be ordered on
+ * one stream (they share the device copies).  All pointers are required and 8-byte aligned
+ * (OCP_EINVAL otherwise). */
 ocp_status ocp_eval_step_host(ocp_t* h, const double* x, const double* y, double sigma, const double* vn,
                               const double* vm, double* f, double* c, double* g, double* jvals,
                               double* hvals, double* Jv, double* Jtv, double* Hv, void* stream);

@@ -1,13 +1,16 @@
 // ocp_eval_step_host: the fused step of ocp_eval_step with every input and output in host
-// memory.  The library keeps device mirrors of the arrays (allocated on the first call and
-// whenever the problem's dimensions change) and runs: the four inputs copied in on its
-// host-to-device stream, ocp_eval_step on the caller's stream, the eight outputs copied out on
-// its device-to-host stream, each stage waiting for the previous one by an event, and the
-// caller's stream waiting for the last copy.  Each array moves in one copy: on GB300 a
-// pipeline over node ranges (inputs of one range in flight while the previous one is
-// evaluated and the one before it copied out) took 1.73-2.02 ms per step at Van der Pol
-// N = 1e6 with 2 to 16 ranges, against 1.64 ms for whole arrays (the extra copies and waits
-// cost more than the partial overlap of the two directions saved).
+// memory.  The library keeps two sets of device mirrors of the arrays (allocated on the first
+// call and whenever the problem's dimensions change) and alternates between them: call k
+// copies its four inputs into set k mod 2 on its host-to-device stream (after the copy-out of
+// call k-2, which used that set, has finished), runs ocp_eval_step on the caller's stream,
+// copies the eight outputs out on its device-to-host stream, and makes the caller's stream
+// wait for that copy-out.  Consecutive calls on one stream therefore overlap the input copy of
+// call k+1 with the output copy of call k (the host link carries both directions at once),
+// while each call's outputs are complete when the caller's stream reaches its end.  Each array
+// moves in one copy: a pipeline over node ranges within one call (inputs of one range in
+// flight while the previous one is evaluated and the one before it copied out) measured
+// 1.73-2.02 ms per step at Van der Pol N = 1e6 with 2 to 16 ranges, against 1.64 ms for whole
+// arrays (the extra copies and waits cost more than the partial overlap they bought).
 #include <cstring>
 
 #include "ocp_internal.h"
@@ -16,20 +19,23 @@ namespace ocpg {
 
 struct HostStep {
   int64_t n = 0, m = 0, nnzj = 0, nnzh = 0;
-  double* buf = nullptr;  // one allocation for all mirrors
-  double* arr[12] = {};   // x, y, vn, vm, f, c, g, jvals, hvals, Jv, Jtv, Hv
+  double* buf[2] = {};          // one allocation per set of mirrors
+  double* arr[2][12] = {};      // x, y, vn, vm, f, c, g, jvals, hvals, Jv, Jtv, Hv
+  int next = 0;                 // the set the next call uses
   cudaStream_t sh = nullptr, sd = nullptr;  // host-to-device and device-to-host copy streams
-  cudaEvent_t start = nullptr, in = nullptr, comp = nullptr, done = nullptr;
+  cudaEvent_t in[2] = {}, comp[2] = {}, done[2] = {};
 };
 
 void host_step_free(ocp* h) {
   HostStep* s = h ? h->hstep : nullptr;
   if (!s) return;
-  cudaFree(s->buf);
+  for (int b = 0; b < 2; ++b) {
+    cudaFree(s->buf[b]);
+    for (cudaEvent_t e : {s->in[b], s->comp[b], s->done[b]})
+      if (e) cudaEventDestroy(e);
+  }
   if (s->sh) cudaStreamDestroy(s->sh);
   if (s->sd) cudaStreamDestroy(s->sd);
-  for (cudaEvent_t e : {s->start, s->in, s->comp, s->done})
-    if (e) cudaEventDestroy(e);
   delete s;
   h->hstep = nullptr;
 }
@@ -40,39 +46,50 @@ static void step_sizes(const Pattern& P, int64_t (&sz)[12]) {
   for (int i = 0; i < 12; ++i) sz[i] = v[i];
 }
 
-// Streams, events and mirrors for the handle's current dimensions.
+// Streams, events and both sets of mirrors for the handle's current dimensions.
 static ocp_status host_step_ready(ocp* h) {
   const Pattern& P = h->pat;
   HostStep* s = h->hstep;
-  if (s && s->buf && s->n == P.n && s->m == P.m && s->nnzj == P.nnzj && s->nnzh == P.nnzh) return OCP_OK;
+  if (s && s->buf[0] && s->buf[1] && s->n == P.n && s->m == P.m && s->nnzj == P.nnzj && s->nnzh == P.nnzh)
+    return OCP_OK;
   if (!s) {
     s = new HostStep();
     h->hstep = s;
     cudaError_t e = cudaStreamCreateWithFlags(&s->sh, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->sd, cudaStreamNonBlocking);
-    for (cudaEvent_t* ev : {&s->start, &s->in, &s->comp, &s->done})
-      if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    for (int b = 0; b < 2; ++b)
+      for (cudaEvent_t* ev : {&s->in[b], &s->comp[b], &s->done[b]})
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
     if (e != cudaSuccess) {
       host_step_free(h);
       return cuda_err(h, e, "host step streams and events");
     }
+  } else {
+    // earlier calls may still be copying from the old mirrors
+    cudaError_t e = cudaStreamSynchronize(s->sd);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->sh);
+    if (e != cudaSuccess) return cuda_err(h, e, "host step: wait before resizing");
   }
-  cudaFree(s->buf);
-  s->buf = nullptr;
+  for (int b = 0; b < 2; ++b) {
+    cudaFree(s->buf[b]);
+    s->buf[b] = nullptr;
+  }
   s->n = s->m = s->nnzj = s->nnzh = 0;
   int64_t sz[12], total = 0;
   step_sizes(P, sz);
   auto up = [](int64_t k) { return (k + 31) / 32 * 32; };  // each mirror on a 256-byte boundary
   for (int64_t k : sz) total += up(k);
-  cudaError_t e = cudaMalloc(&s->buf, sizeof(double) * (size_t)total);
-  if (e != cudaSuccess) {
-    s->buf = nullptr;
-    return cuda_err(h, e, "cudaMalloc(host step mirrors)");
-  }
-  double* p = s->buf;
-  for (int i = 0; i < 12; ++i) {
-    s->arr[i] = p;
-    p += up(sz[i]);
+  for (int b = 0; b < 2; ++b) {
+    cudaError_t e = cudaMalloc(&s->buf[b], sizeof(double) * (size_t)total);
+    if (e != cudaSuccess) {
+      s->buf[b] = nullptr;
+      return cuda_err(h, e, "cudaMalloc(host step mirrors)");
+    }
+    double* p = s->buf[b];
+    for (int i = 0; i < 12; ++i) {
+      s->arr[b][i] = p;
+      p += up(sz[i]);
+    }
   }
   s->n = P.n; s->m = P.m; s->nnzj = P.nnzj; s->nnzh = P.nnzh;
   return OCP_OK;
@@ -98,25 +115,27 @@ extern "C" ocp_status ocp_eval_step_host(ocp_t* h, const double* x, const double
   ocp_status st = host_step_ready(h);
   if (st != OCP_OK) return st;
   HostStep* S = h->hstep;
+  const int b = S->next;
+  double* const* A = S->arr[b];
   int64_t sz[12];
   step_sizes(h->pat, sz);
   cudaStream_t s0 = (cudaStream_t)stream;
-  // inputs after the caller's earlier work on `stream`
-  cudaError_t e = cudaEventRecord(S->start, s0);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(S->sh, S->start, 0);
+  // inputs into this call's set, once the call that used it last has copied its outputs out
+  cudaError_t e = cudaStreamWaitEvent(S->sh, S->done[b], 0);
   for (int i = 0; i < 4 && e == cudaSuccess; ++i)
-    e = cudaMemcpyAsync(S->arr[i], in[i], sizeof(double) * (size_t)sz[i], cudaMemcpyHostToDevice, S->sh);
-  if (e == cudaSuccess) e = cudaEventRecord(S->in, S->sh);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(s0, S->in, 0);
+    e = cudaMemcpyAsync(A[i], in[i], sizeof(double) * (size_t)sz[i], cudaMemcpyHostToDevice, S->sh);
+  if (e == cudaSuccess) e = cudaEventRecord(S->in[b], S->sh);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s0, S->in[b], 0);
   if (e != cudaSuccess) return cuda_err(h, e, "host step: inputs");
-  double* const* A = S->arr;
   st = ocp_eval_step(h, A[0], A[1], sigma, A[2], A[3], A[4], A[5], A[6], A[7], A[8], A[9], A[10], A[11], s0);
   if (st != OCP_OK) return st;
-  e = cudaEventRecord(S->comp, s0);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(S->sd, S->comp, 0);
+  e = cudaEventRecord(S->comp[b], s0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(S->sd, S->comp[b], 0);
   for (int i = 0; i < 8 && e == cudaSuccess; ++i)
-    e = cudaMemcpyAsync(out[i], S->arr[4 + i], sizeof(double) * (size_t)sz[4 + i], cudaMemcpyDeviceToHost, S->sd);
-  if (e == cudaSuccess) e = cudaEventRecord(S->done, S->sd);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(s0, S->done, 0);
-  return e == cudaSuccess ? OCP_OK : cuda_err(h, e, "host step: outputs");
+    e = cudaMemcpyAsync(out[i], A[4 + i], sizeof(double) * (size_t)sz[4 + i], cudaMemcpyDeviceToHost, S->sd);
+  if (e == cudaSuccess) e = cudaEventRecord(S->done[b], S->sd);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s0, S->done[b], 0);
+  if (e != cudaSuccess) return cuda_err(h, e, "host step: outputs");
+  S->next = b ^ 1;
+  return OCP_OK;
 }

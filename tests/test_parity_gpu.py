@@ -344,6 +344,24 @@ def test_host_step_equals_device_step(ocp, name, N, pinned):
     H.close()
 
 
+def test_host_step_back_to_back_calls(ocp):
+    """Four host steps on one stream without synchronizing in between (the two device copies
+    alternate, the input copy of one call overlapping the output copy of the previous one),
+    with different inputs and outputs: each matches the device step of its own inputs."""
+    w = named("cartpole_n1e5", 5000)
+    H = ocp.OCP.from_workload(w)
+    draws = [synth.draw(w, seed=w["seed"] + 10 + i) for i in range(4)]
+    hins = [[torch.from_numpy(d[k]).pin_memory() for k in ("x", "y", "vn", "vm")] for d in draws]
+    outs = [H.eval_step_host(hi[0], hi[1], 0.9, hi[2], hi[3]) for hi in hins]
+    torch.cuda.synchronize()
+    for hi, got in zip(hins, outs):
+        ref = H.eval_step(*(t.cuda() for t in hi[:2]), 0.9, *(t.cuda() for t in hi[2:]))
+        torch.cuda.synchronize()
+        for a, b in zip(got, ref):
+            assert torch.equal(a, b.cpu())
+    H.close()
+
+
 def test_host_step_rejects_device_tensors(ocp):
     w = named("vdp_n1e3", 100)
     H = ocp.OCP.from_workload(w)
