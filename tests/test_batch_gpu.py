@@ -101,6 +101,41 @@ def test_batch_against_oracle_graph_and_autotune(ocp):
         gate("h%d" % i, hh[B.hoff[i]:B.hoff[i + 1]], r["hess"], r["hess_mag"])
 
 
+def test_batch_full_workload_as_benchmarked(ocp):
+    """The benchmark's batch (256 cart-pole instances, N ~ U{500..50000}, 6.5e6 nodes) in the
+    benchmark's launch configuration (autotuned, replayed from a CUDA graph): eight instances
+    (the shortest, the longest and six drawn at random) against the oracle through the parity
+    gate and bit for bit against the plain evaluator."""
+    ws = synth.batch_workloads()
+    probs, B, draws, x, y = make(ocp, ws)
+    f, c, g, jv, hv = B.outputs()
+    B.autotune(x, y, 1.0, f, None, g, jv, hv)
+    s = torch.cuda.Stream()
+    for t in (f, g, jv, hv):
+        t.fill_(float("nan"))
+    torch.cuda.synchronize()
+    B.graph_capture(x, y, 1.0, f, None, g, jv, hv, stream=s)
+    B.graph_launch(stream=s)
+    s.synchronize()
+    Ns = np.array([w["N"] for w in ws])
+    rng = np.random.default_rng(2026)
+    pick = sorted({int(np.argmin(Ns)), int(np.argmax(Ns))} | set(rng.choice(len(ws), 6, replace=False).tolist()))
+    fh, gh, jh, hh = (t.cpu().numpy() for t in (f, g, jv, hv))
+    for i in pick:
+        w, d = ws[i], draws[i]
+        r = O.evaluate(O.Problem(w), d["x"], d["y"], 1.0, shadow=True)
+        gate("f%d" % i, fh[i:i + 1], np.array([r["f"]]), np.array([r["f_mag"]]))
+        gate("g%d" % i, gh[B.xoff[i]:B.xoff[i + 1]], r["g"], r["g_mag"])
+        gate("j%d" % i, jh[B.joff[i]:B.joff[i + 1]], r["jac"], r["jac_mag"])
+        gate("h%d" % i, hh[B.hoff[i]:B.hoff[i + 1]], r["hess"], r["hess_mag"])
+        pf, pc, pg, pj, ph = (t.cpu().numpy() for t in probs[i].eval_all(torch.from_numpy(d["x"]).cuda(),
+                                                                         torch.from_numpy(d["y"]).cuda(), 1.0))
+        assert np.array_equal(gh[B.xoff[i]:B.xoff[i + 1]], pg)
+        assert np.array_equal(jh[B.joff[i]:B.joff[i + 1]], pj)
+        assert np.array_equal(hh[B.hoff[i]:B.hoff[i + 1]], ph)
+    assert np.isfinite(gh).all() and np.isfinite(jh).all() and np.isfinite(hh).all() and np.isfinite(fh).all()
+
+
 def test_batch_rejects_mixed_models(ocp):
     a = ocp.OCP.from_workload(synth.with_horizon(synth.workload("vdp_n1e3"), 10))
     b = ocp.OCP.from_workload(synth.with_horizon(synth.workload("cartpole_n1e5"), 10))
