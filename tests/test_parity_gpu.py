@@ -214,7 +214,7 @@ def test_parity_cost_structure_follows_weights(ocp):
                                   "goddard_n1e5", "cartpole_n1e5:euler", "quadrotor_n1e5:euler",
                                   "quadrotor_n1e5+path", "cartpole_n1e5+bineq", "goddard_n1e5+path+bineq"])
 def test_parity_full_size_workloads(ocp, name):
-    rep = full_check(ocp, named(name), products=(name != "vdp_mu_n1e6"))
+    rep = full_check(ocp, named(name))
     print(name, rep)
 
 
