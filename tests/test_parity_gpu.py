@@ -139,6 +139,17 @@ def test_parity_vdp_mu_variants(ocp):
     full_check(ocp, w)
 
 
+@pytest.mark.parametrize("name,N,change", [("vdp_n1e3", 300, dict(params=[0.0])),   # mu = 0: linear in x2
+                                           ("vdp_n1e3", 300, dict(sigma=0.0)),      # no objective term in H
+                                           ("cartpole_n1e5", 200, dict(sigma=0.0)),
+                                           ("quadrotor_n1e3", 100, dict(sigma=0.0)),
+                                           ("heat_n2e4", 40, dict(sigma=0.0))])
+def test_parity_degenerate_cases(ocp, name, N, change):
+    """Degenerate instances: a vanishing parameter keeps every structural entry (values zero),
+    and sigma = 0 removes the objective from the Lagrangian Hessian."""
+    full_check(ocp, dict(synth.with_horizon(synth.workload(name), N), **change))
+
+
 def test_parity_reference_offsets(ocp):
     """Non-zero tracking references (cart-pole with xref/uref) and sigma != 1."""
     w = dict(synth.with_horizon(synth.workload("cartpole_n1e5"), 400), xref=[0.1, -0.2, 0.3, 0.0], uref=[1.5],
