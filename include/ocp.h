@@ -225,7 +225,8 @@ ocp_status hess_coo_values(ocp_t* h, const double* x, const double* y, double si
                            void* stream);
 
 /* The Jacobian's per-variable scatter map: the COO of jac_coo_structure in column order (CSC
- * of the COO value array).  For column c, the entries t in colptr[c] .. colptr[c+1]-1 have row
+ * of the COO value array; the paper's Sec. 5 Jacobian of the generated constraints, viewed by
+ * unknowns).  For column c, the entries t in colptr[c] .. colptr[c+1]-1 have row
  * rows[t] and value jvals[slots[t]], rows ascending.  colptr: int32 device array of n + 1;
  * rows, slots: int32 device arrays of nnz_J.  Built from the pattern compiler's per-variable
  * templates (for each unknown of a node, the rows and entry positions that reference it), one
@@ -233,7 +234,8 @@ ocp_status hess_coo_values(ocp_t* h, const double* x, const double* y, double si
  * Errors: OCP_EINVAL (NULL arrays), OCP_ENOMEM/OCP_ECUDA. */
 ocp_status ocp_jac_scatter_map(ocp_t* h, int32_t* colptr, int32_t* rows, int32_t* slots, void* stream);
 
-/* J^T w from STORED Jacobian values (jvals from jac_coo_values or ocp_eval_all, length nnz_J;
+/* J^T w from STORED Jacobian values (the paper defines no products: this is the gather a
+ * solver holding J values needs; jvals from jac_coo_values or ocp_eval_all, length nnz_J;
  * w of length m; Jtw of length n, device arrays): the gather over the scatter map, each
  * column's entries added in row order (deterministic); the free final time's column by one
  * CTA's fixed-order reduction.  The handle keeps the map (about 8 bytes per J entry, built on
@@ -242,7 +244,9 @@ ocp_status ocp_jac_scatter_map(ocp_t* h, int32_t* colptr, int32_t* rows, int32_t
 ocp_status ocp_jtprod_coo(ocp_t* h, const double* jvals, const double* w, double* Jtw, void* stream);
 
 /* Matrix-free products at x:  Jv (v: n -> m),  J^T v (v: m -> n),  H v (v: n -> n, full
- * symmetric H for multipliers y and weight sigma).  Output arrays must not alias inputs. */
+ * symmetric H for multipliers y and weight sigma) of the Sec. 5 Jacobian and Lagrangian
+ * Hessian (not formed: each node's derivatives are recomputed from x).  Output arrays must not
+ * alias inputs. */
 ocp_status jprod(ocp_t* h, const double* x, const double* v, double* Jv, void* stream);
 ocp_status jtprod(ocp_t* h, const double* x, const double* v, double* Jtv, void* stream);
 ocp_status hprod(ocp_t* h, const double* x, const double* y, double sigma, const double* v,
