@@ -197,6 +197,12 @@ ocp_status ocp_set_terminal_cost(ocp_t* h, const double* mayer);
 ocp_status ocp_set_variable_bounds(ocp_t* h, const double* xlo, const double* xhi, const double* ulo,
                                    const double* uhi, double tflo, double tfhi);
 
+/* Start point (the generated model's `init`, Sec. 5: one value per state and per control
+ * component, repeated at every node): writes x (DEVICE array of n) with X_{j,k} = xs[k],
+ * U_{j,i} = us[i] and, with a free final time, tf.  xs, us: host arrays of nx and nu (NULL:
+ * zeros).  Asynchronous on `stream`.  Errors: OCP_EINVAL (NULL or misaligned x). */
+ocp_status ocp_start_point(ocp_t* h, const double* xs, const double* us, double tf, double* x, void* stream);
+
 /* Sizes: n variables, m constraints, Jacobian and (lower) Hessian nonzeros.  Host outputs. */
 ocp_status ocp_dims(const ocp_t* h, int64_t* n, int64_t* m, int64_t* nnzj, int64_t* nnzh);
 

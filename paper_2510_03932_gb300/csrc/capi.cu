@@ -52,6 +52,20 @@ int64_t objective_tiles(int model, int64_t nodes) {
 // Time-varying state reference, tabulated once per node: for the tracked components i,
 //   out[ntrk j + i] = (xref + xslope t_j) + xamp sin(xfreq t_j),  t_j = j h
 // (plain operations in this order, no FMA).  One thread per table entry.
+// The start point: one value per state and control component at every node, then tf.
+struct StartArgs {
+  double* x;
+  int64_t nX, nXU, n;     // ends of the X block, of the U block, of x
+  int nx, nu;
+  double tf;
+  double xs[128], us[8];
+};
+__global__ void k_start_point(const __grid_constant__ StartArgs a) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.n; i += stride)
+    a.x[i] = i < a.nX ? a.xs[i % a.nx] : (i < a.nXU ? a.us[(i - a.nX) % a.nu] : a.tf);
+}
+
 struct TrackArgs {
   double* out;
   int64_t N;
@@ -612,6 +626,24 @@ ocp_status ocp_set_boundary_inequalities(ocp_t* h, int nbin, const double* a, co
   h->bin_l.assign(l, l + (size_t)nbin * bz);
   h->bin_r.assign(r, r + nbin);
   return rebuild(h);
+}
+
+ocp_status ocp_start_point(ocp_t* h, const double* xs, const double* us, double tf, double* x, void* stream) {
+  if (!h) return OCP_EINVAL;
+  NEED(x);
+  if (h->nx > 128 || h->nu > 8) return set_err(h, OCP_EDIM, "start point: too many components");
+  StartArgs a;
+  memset(&a, 0, sizeof(a));
+  a.x = x;
+  a.nX = (int64_t)h->nx * (h->N + 1);
+  a.nXU = a.nX + (int64_t)h->nu * h->pat.nun;
+  a.n = h->pat.n;
+  a.nx = h->nx; a.nu = h->nu; a.tf = tf;
+  for (int k = 0; k < h->nx; ++k) a.xs[k] = xs ? xs[k] : 0.0;
+  for (int i = 0; i < h->nu; ++i) a.us[i] = us ? us[i] : 0.0;
+  const int64_t blocks = std::min<int64_t>((a.n + 255) / 256, (int64_t)h->num_sms * 8);
+  k_start_point<<<(int)std::max<int64_t>(blocks, 1), 256, 0, (cudaStream_t)stream>>>(a);
+  return cuda_err(h, cudaGetLastError(), "k_start_point launch");
 }
 
 ocp_status ocp_set_scheme(ocp_t* h, int scheme) {

@@ -49,6 +49,7 @@ _SIGS = {
     "ocp_set_path_constraints": [_P, C.c_int, _P, _P, _P, _P],
     "ocp_set_boundary_inequalities": [_P, C.c_int, _P, _P, _P, _P],
     "ocp_jac_scatter_map": [_P, _P, _P, _P, _P],
+    "ocp_start_point": [_P, _P, _P, _D, _P, _P],
     "ocp_jtprod_coo": [_P, _P, _P, _P, _P],
     "ocp_set_final_components": [_P, C.c_int, _P, _P],
     "ocp_set_terminal_cost": [_P, _P],
@@ -353,6 +354,16 @@ class OCP:
         _check(lib().ocp_eval_step_host(self.h, _ptr(x), _ptr(y), float(sigma), _ptr(vn), _ptr(vm),
                                         *[_ptr(t) for t in outs], _stream(stream)), self.h)
         return outs
+
+    def start_point(self, xs=None, us=None, tf=0.0, out=None, stream=None):
+        """x with X_{j,k} = xs[k], U_{j,i} = us[i] at every node (and tf), on the device."""
+        out = self._out(out, self.n, "x")
+        ax = None if xs is None else (C.c_double * self.nx)(*[float(t) for t in xs])
+        au = None if us is None else (C.c_double * self.nu)(*[float(t) for t in us])
+        px = None if ax is None else C.cast(ax, C.c_void_p)
+        pu = None if au is None else C.cast(au, C.c_void_p)
+        _check(lib().ocp_start_point(self.h, px, pu, float(tf), _ptr(out), _stream(stream)), self.h)
+        return out
 
     def jac_scatter_map(self, stream=None):
         """(colptr, rows, slots): the Jacobian's COO in column order (int32 CUDA tensors)."""

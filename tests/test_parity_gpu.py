@@ -373,6 +373,27 @@ def test_host_step_back_to_back_calls(ocp):
     H.close()
 
 
+@pytest.mark.parametrize("name,N", [("dint", 20), ("quadrotor_n1e3", 7), ("goddard_n1e3", 9), ("vdp_n1e3:euler", 5)])
+def test_start_point(ocp, name, N):
+    """The generated model's start values (Sec. 5 `init`): every X_{j,k} = xs[k], U_{j,i} =
+    us[i], and tf last when it is free."""
+    w = named(name, N)
+    H = ocp.OCP.from_workload(w)
+    nx, nu = w["nx"], w["nu"]
+    xs = [0.1 * (k + 1) for k in range(nx)]
+    us = [-0.5 * (i + 1) for i in range(nu)]
+    x = H.start_point(xs, us, 0.2).cpu().numpy()
+    nun = synth.control_nodes(w)
+    X = x[:nx * (N + 1)].reshape(N + 1, nx)
+    U = x[nx * (N + 1):nx * (N + 1) + nu * nun].reshape(nun, nu)
+    assert np.all(X == np.array(xs)) and np.all(U == np.array(us))
+    assert x.size == nx * (N + 1) + nu * nun + (1 if w.get("free_tf") else 0)
+    if w.get("free_tf"):
+        assert x[-1] == 0.2
+    assert np.all(H.start_point().cpu().numpy()[:nx * (N + 1) + nu * nun] == 0.0)
+    H.close()
+
+
 def test_host_step_rejects_device_tensors(ocp):
     w = named("vdp_n1e3", 100)
     H = ocp.OCP.from_workload(w)
