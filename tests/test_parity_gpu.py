@@ -134,6 +134,35 @@ def test_parity_heat_cell_counts(ocp, cells, N):
     H.close()
 
 
+def _random_case(i):
+    """Seeded combination i of model, scheme, horizon, cell count, final rows, path rows,
+    boundary inequalities and sigma."""
+    rng = np.random.default_rng(9000 + i)
+    model = ["vdp_n1e3", "cartpole_n1e5", "dint", "quadrotor_n1e3", "heat_n2e4", "goddard_n1e3"][i % 6]
+    N = int(rng.integers(1, 700)) if model != "heat_n2e4" else int(rng.integers(1, 80))
+    w = synth.with_horizon(synth.workload(model), N)
+    if model == "heat_n2e4" and rng.random() < 0.5:
+        cells = int(rng.integers(2, 40))
+        w = dict(w, nx=cells, params=[float(cells)], q=[1.0] * cells, xref=[0.5] * cells, x0=[0.0] * cells)
+    euler = model not in ("heat_n2e4", "goddard_n1e3") and rng.random() < 0.35
+    if euler:
+        w = dict(w, scheme="euler")
+    if model not in ("goddard_n1e3", "dint") and rng.random() < 0.4:
+        w = dict(w, xf=[0.0] * w["nx"])
+    if rng.random() < 0.5 and (model != "heat_n2e4" or w["nx"] == 64):
+        w = synth.with_path(w)
+    if not euler and rng.random() < 0.5:
+        w = synth.with_bineq(w)
+    return dict(w, sigma=float(rng.choice([0.0, 0.37, 1.0, 2.5])))
+
+
+@pytest.mark.parametrize("i", range(40))
+def test_parity_random_combinations(ocp, i):
+    """Forty seeded combinations of the options, each through the full comparison with the
+    oracle (structure bit-exact, values, the single-output calls, the products)."""
+    full_check(ocp, _random_case(i))
+
+
 def test_parity_vdp_mu_variants(ocp):
     w = dict(synth.with_horizon(synth.workload("vdp_n1e3"), 300), params=[2.5])
     full_check(ocp, w)
