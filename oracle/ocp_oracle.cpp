@@ -151,6 +151,13 @@ struct Prob {
   const double* bin_b;
   const double* bin_l;
   const double* bin_r;
+  // boundary cost (paper Sec. 3, the Bolza term g(X_0, X_N)) added to the objective:
+  //   g(z) = sum_v [ bol_a[v] (z_v - bol_b[v])^2 + bol_l[v] z_v ],  z = (X_0, X_N)
+  // (arrays of 2 nx; has_bol = 0: none)
+  int32_t has_bol;
+  const double* bol_a;
+  const double* bol_b;
+  const double* bol_l;
 };
 
 template <class S> struct JEnt { int k, v; S val; };      // d f_k / d z_v
@@ -694,6 +701,41 @@ template <class S> void bin_hessian(const Prob& P, const Layout& L, const S* y, 
     }
 }
 
+// Boundary cost g(X_0, X_N): value, gradient entries and the template diagonals (a squared
+// term on X_{0,k} or X_{N,k} puts (k, k) in every node block, like the boundary rows).
+template <class S> S bol_value(const Prob& P, const Layout& L, const S* x) {
+  S g = S(0.0);
+  for (int v = 0; v < 2 * L.nx; ++v) {
+    const S z = x[L.bin_col(v)];
+    const double av = P.bol_a[v], lv = P.bol_l[v];
+    if (av != 0.0) { const S d = z - S(P.bol_b[v]); g = g + S(av) * d * d; }
+    if (lv != 0.0) g = g + S(lv) * z;
+  }
+  return g;
+}
+template <class S> void bol_gradient(const Prob& P, const Layout& L, const S* x, S* g) {
+  for (int v = 0; v < 2 * L.nx; ++v) {
+    const double av = P.bol_a[v], lv = P.bol_l[v];
+    if (av == 0.0 && lv == 0.0) continue;
+    const int64_t col = L.bin_col(v);
+    g[col] = g[col] + (S(2.0 * av) * (x[col] - S(P.bol_b[v])) + S(lv));
+  }
+}
+inline bool bol_diag(const Prob& P, int k) {
+  return P.has_bol && (P.bol_a[k] != 0.0 || P.bol_a[P.nx + k] != 0.0);
+}
+// sigma times its Hessian in node j's block (j = 0 or N), and the template keys at every node
+template <class S> void bol_hessian(const Prob& P, const Layout& L, S sigma, int64_t j,
+                                    std::map<std::pair<int, int>, S>& blk) {
+  if (!P.has_bol) return;
+  for (int k = 0; k < L.nx; ++k) {
+    if (!bol_diag(P, k)) continue;
+    if (!blk.count({k, k})) blk[{k, k}] = S(0.0);
+    if (j == 0 && P.bol_a[k] != 0.0) blk[{k, k}] = blk[{k, k}] + sigma * S(2.0 * P.bol_a[k]);
+    if (j == L.N && P.bol_a[L.nx + k] != 0.0) blk[{k, k}] = blk[{k, k}] + sigma * S(2.0 * P.bol_a[L.nx + k]);
+  }
+}
+
 // step h = T / N, or tf / N with the free final time tf = x[tau]
 template <class S> S step_h(const Prob& P, const Layout& L, const S* x) {
   if (L.tau >= 0) return x[L.tau] / S((double)P.N);
@@ -731,6 +773,7 @@ template <class S> S euler_objective(const Prob& P, const S* x) {
   }
   if (P.mayer)
     for (int k = 0; k < L.nx; ++k) acc.add(S(P.mayer[k]) * x[L.colX(L.N, k)]);
+  if (P.has_bol) acc.add(bol_value(P, L, x));
   return acc.result();
 }
 
@@ -760,6 +803,7 @@ template <class S> void euler_gradient(const Prob& P, const S* x, S* g) {
     if (L.tau >= 0) gt.add(cost_f0(P, z.data(), node_time(P, j)) / S((double)L.N));
   }
   for (int k = 0; k < L.nx; ++k) g[L.colX(L.N, k)] = S(P.mayer ? P.mayer[k] : 0.0);
+  if (P.has_bol) bol_gradient(P, L, x, g);
   if (L.tau >= 0) g[L.tau] = gt.result();
 }
 
@@ -817,6 +861,7 @@ template <class S> void euler_hessian(const Prob& P, const S* p, const S* x, con
       blk[{e.a, e.b}] = blk[{e.a, e.b}] + y[L.defect_row(e.k, j)] * (S(0.0) - h * e.val);
     }
     path_hessian(P, L, y, j, blk);
+    bol_hessian(P, L, sigma, j, blk);
     for (auto& kv : blk) all.push_back({L.col(j, kv.first.first), L.col(j, kv.first.second), kv.second});
     if (L.tau >= 0) {
       std::map<int, S> trow;
@@ -851,6 +896,7 @@ template <class S> S objective(const Prob& P, const S* x) {
   }
   if (P.mayer)
     for (int k = 0; k < L.nx; ++k) acc.add(S(P.mayer[k]) * x[L.colX(L.N, k)]);
+  if (P.has_bol) acc.add(bol_value(P, L, x));
   return acc.result();
 }
 
@@ -891,6 +937,7 @@ template <class S> void gradient(const Prob& P, const S* x, S* g) {
   }
   if (P.mayer)
     for (int k = 0; k < L.nx; ++k) g[L.colX(L.N, k)] = g[L.colX(L.N, k)] + S(P.mayer[k]);
+  if (P.has_bol) bol_gradient(P, L, x, g);
   if (L.tau >= 0) g[L.tau] = gt.result();
 }
 
@@ -978,6 +1025,7 @@ template <class S> void hessian(const Prob& P, const S* p, const S* x, const S* 
     }
     path_hessian(P, L, y, j, blk);
     bin_hessian(P, L, y, j, blk);
+    bol_hessian(P, L, sigma, j, blk);
     for (auto& kv : blk) all.push_back({L.col(j, kv.first.first), L.col(j, kv.first.second), kv.second});
     if (L.tau >= 0) {
       std::map<int, S> trow;
@@ -1080,6 +1128,10 @@ int check(const Prob& P) {
   if (P.npath < 0 || (P.npath > 0 && (!P.path_a || !P.path_b || !P.path_l || !P.path_r))) return 2;
   if (P.nbin < 0 || (P.nbin > 0 && (!P.bin_a || !P.bin_b || !P.bin_l || !P.bin_r))) return 2;
   if (P.nbin > 0 && P.scheme == 1) return 2;  // boundary inequalities: trapezoidal scheme only
+  if (P.has_bol && (!P.bol_a || !P.bol_b || !P.bol_l)) return 2;
+  if (P.has_bol && P.scheme == 1)  // Euler: node N has no Hessian block, so no squared X_N term
+    for (int k = 0; k < P.nx; ++k)
+      if (P.bol_a[P.nx + k] != 0.0) return 2;
   // the tracking reference is tabulated at t_j = j T / N: not with a free final time
   if (P.free_tf && (P.xslope || P.xamp)) return 2;
   if (P.has_final && P.fin_comp) {
@@ -1150,6 +1202,8 @@ int orc_dims(const Prob* P, int64_t* n, int64_t* m, int64_t* nnzj, int64_t* nnzh
       if (P->path_a[pp * L.nz + v] != 0.0) keys.push_back({v, v});
   for (int k = 0; k < L.nx; ++k)
     if (bin_diag(*P, k)) keys.push_back({k, k});
+  for (int k = 0; k < L.nx; ++k)
+    if (bol_diag(*P, k)) keys.push_back({k, k});
   std::sort(keys.begin(), keys.end());
   *nnzh = (int64_t)(std::unique(keys.begin(), keys.end()) - keys.begin()) * L.nun;
   if (L.tau >= 0) {  // the tf row: model Jacobian columns and cost columns of every node

@@ -23,7 +23,8 @@ class _Prob(C.Structure):
                 ("free_tf", C.c_int32), ("nfin", C.c_int32), ("fin_comp", C.c_void_p), ("mayer", C.c_void_p),
                 ("scheme", C.c_int32), ("npath", C.c_int32), ("path_a", C.c_void_p), ("path_b", C.c_void_p),
                 ("path_l", C.c_void_p), ("path_r", C.c_void_p), ("nbin", C.c_int32), ("bin_a", C.c_void_p),
-                ("bin_b", C.c_void_p), ("bin_l", C.c_void_p), ("bin_r", C.c_void_p)]
+                ("bin_b", C.c_void_p), ("bin_l", C.c_void_p), ("bin_r", C.c_void_p), ("has_bol", C.c_int32),
+                ("bol_a", C.c_void_p), ("bol_b", C.c_void_p), ("bol_l", C.c_void_p)]
 
 
 _lib = None
@@ -90,6 +91,13 @@ class Problem:
             self._bin = [np.ascontiguousarray(bi[k], dtype=np.float64) for k in ("a", "b", "l", "r")]
             p.nbin = len(bi["r"])
             p.bin_a, p.bin_b, p.bin_l, p.bin_r = (_ptr(a) for a in self._bin)
+        # boundary cost sum_v [a (z_v - b)^2 + l z_v] over z = (X_0, X_N), added to F
+        self._bol = None
+        if w.get("bolza"):
+            bo = w["bolza"]
+            self._bol = [np.ascontiguousarray(bo[k], dtype=np.float64) for k in ("a", "b", "l")]
+            p.has_bol = 1
+            p.bol_a, p.bol_b, p.bol_l = (_ptr(a) for a in self._bol)
         self.s = p
         n, m, nj, nh = (C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64())
         st = lib().orc_dims(C.byref(p), C.byref(n), C.byref(m), C.byref(nj), C.byref(nh))

@@ -214,6 +214,22 @@ def with_bineq(w: dict) -> dict:
     return dict(w, bineq=_path_rows(2 * w["nx"], _bineq_rows(w["model"], w["nx"])))
 
 
+# Boundary cost (paper Sec. 3, the Bolza term g(X_0, X_N)) in the same family over
+# z = (X_0, X_N): a terminal penalty 1.5 |X_N - b|^2 towards b_k = 0.1 (k + 1), a small quadratic
+# and linear term on X_{0,1}, and a linear reward on X_{N,nx}.  With the Euler scheme (no
+# Hessian block at node N) the X_N terms are linear only.
+def with_bolza(w: dict) -> dict:
+    nx = w["nx"]
+    euler = w.get("scheme") == "euler"
+    a = [0.0] * (2 * nx); b = [0.0] * (2 * nx); lin = [0.0] * (2 * nx)
+    a[0], lin[0] = 0.5, -0.25
+    for k in range(nx):
+        if not euler:
+            a[nx + k], b[nx + k] = 1.5, 0.1 * (k + 1)
+    lin[2 * nx - 1] = 0.3
+    return dict(w, bolza=dict(a=a, b=b, l=lin))
+
+
 def with_horizon(w: dict, N: int) -> dict:
     """The same workload at another horizon (parity cases at oracle-friendly sizes)."""
     w = dict(w)

@@ -24,6 +24,9 @@ PATHED = ["vdp_n1e3+path", "cartpole_n1e5+path", "quadrotor_n1e3+path", "goddard
 # with boundary inequalities b(X_0, X_N) <= 0 (trapezoidal scheme)
 BINEQED = ["vdp_n1e3+bineq", "cartpole_n1e5+bineq", "dint+bineq", "quadrotor_n1e3+bineq", "goddard_n1e3+bineq",
            "heat_n2e4+bineq", "vdp_n1e3+path+bineq"]
+# with the boundary cost g(X_0, X_N) added to the objective
+BOLZAED = ["vdp_n1e3+bolza", "cartpole_n1e5+bolza", "dint+bolza", "quadrotor_n1e3+bolza", "goddard_n1e3+bolza",
+           "heat_n2e4+bolza", "vdp_n1e3:euler+bolza", "dint:euler+path+bolza", "vdp_n1e3+bineq+bolza"]
 
 
 def small(name, N):
@@ -38,6 +41,8 @@ def small(name, N):
         w = synth.with_path(w)
     if "bineq" in plus:
         w = synth.with_bineq(w)
+    if "bolza" in plus:
+        w = synth.with_bolza(w)
     return w
 
 
@@ -112,7 +117,7 @@ def dense_hess_cs(P, x, y, sigma):
     return np.array(cols).T  # n x n
 
 
-@pytest.mark.parametrize("name", MODELS + PATHED + BINEQED)
+@pytest.mark.parametrize("name", MODELS + PATHED + BINEQED + BOLZAED)
 def test_structure_matches_bruteforce_detection(name):
     """An entry is structural iff it is nonzero at one of 8 random points (complex step)."""
     w = small(name, 2 if name.startswith("heat") else 3)
@@ -129,10 +134,14 @@ def test_structure_matches_bruteforce_detection(name):
     jm = np.zeros_like(jmask); jm[jr, jc] = True
     hm = np.zeros_like(hmask); hm[hr, hc] = True
     assert np.array_equal(jm, jmask)
-    if w.get("bineq"):
-        # one Hessian template for every node: a boundary row's squared term on component k
-        # puts (k, k) in every node's block; away from nodes 0 and N it is an explicit zero
-        ba, nx = np.array(w["bineq"]["a"]), w["nx"]
+    if w.get("bineq") or w.get("bolza"):
+        # one Hessian template for every node: a boundary row's or the boundary cost's squared
+        # term on component k puts (k, k) in every node's block; away from nodes 0 and N it is
+        # an explicit zero
+        nx = w["nx"]
+        ba = np.array(w["bineq"]["a"]) if w.get("bineq") else np.zeros((0, 2 * nx))
+        if w.get("bolza"):
+            ba = np.vstack([ba, np.array(w["bolza"]["a"])[None, :]])
         sq = [k for k in range(nx) if np.any(ba[:, k] != 0) or np.any(ba[:, nx + k] != 0)]
         allowed = np.zeros_like(hm)
         for j in range(w["N"] + 1):
@@ -146,7 +155,7 @@ def test_structure_matches_bruteforce_detection(name):
 # ---------------------------------------------------------------------------------------
 # Derivative values against complex step of the residual / objective / Lagrangian gradient
 # ---------------------------------------------------------------------------------------
-@pytest.mark.parametrize("name", MODELS + PATHED + BINEQED)
+@pytest.mark.parametrize("name", MODELS + PATHED + BINEQED + BOLZAED)
 def test_jacobian_gradient_hessian_vs_complex_step(name):
     w = small(name, 2 if name.startswith("heat") else 4)
     P = O.Problem(w)
@@ -588,6 +597,40 @@ def test_boundary_inequalities_counts_and_boundary_points(name):
             assert abs(O.evaluate(P, x, y, 1.0)["c"][P.m - nbin]) <= 4e-16
 
 
+@pytest.mark.parametrize("name", ["vdp_n1e3", "quadrotor_n1e3", "goddard_n1e3", "heat_n2e4"])
+def test_boundary_cost_at_its_target_and_counts(name):
+    """The boundary cost adds no row and no Jacobian entry, and its (k, k) template diagonals;
+    at z = b with l = 0 it adds nothing to F and to the gradient (the penalty's minimum), and a
+    step delta along X_{N,k} adds a_k delta^2 (+ l delta for a linear term) to F."""
+    w = small(name, 6)
+    nx, N = w["nx"], w["N"]
+    wq = synth.with_bolza(w)
+    lin = [0.0] * (2 * nx)
+    wq = dict(wq, bolza=dict(wq["bolza"], l=lin, a=[0.0] * nx + wq["bolza"]["a"][nx:]))
+    P, P0 = O.Problem(wq), O.Problem(w)
+    assert (P.n, P.m, P.nnzj) == (P0.n, P0.m, P0.nnzj) and P.nnzh >= P0.nnzh
+    rng = np.random.default_rng(61)
+    x, y = rand_point(w, rng)
+    bN = np.array(wq["bolza"]["b"][nx:])
+    x[nx * N:nx * N + nx] = bN
+    e1, e0 = O.evaluate(P, x, y, 1.0), O.evaluate(P0, x, y, 1.0)
+    assert e1["f"] == e0["f"]
+    assert np.array_equal(e1["g"], e0["g"])
+    for k in range(nx):
+        xd = x.copy(); xd[nx * N + k] += 0.125
+        df = O.evaluate(P, xd, y, 1.0)["f"] - O.evaluate(P0, xd, y, 1.0)["f"]
+        assert abs(df - 1.5 * 0.125 ** 2) <= 1e-13 * (1 + abs(e0["f"]))
+
+
+def test_boundary_cost_refused_with_euler_on_the_last_state():
+    w = small("vdp_n1e3:euler", 5)
+    wb = synth.with_bolza(w)
+    O.Problem(wb)   # linear X_N terms are accepted
+    a = list(wb["bolza"]["a"]); a[-1] = 1.0
+    with pytest.raises(ValueError):
+        O.Problem(dict(wb, bolza=dict(wb["bolza"], a=a)))
+
+
 def test_boundary_inequalities_refused_with_euler():
     w = synth.with_bineq(small("vdp_n1e3:euler", 5))
     with pytest.raises(ValueError):
@@ -597,7 +640,7 @@ def test_boundary_inequalities_refused_with_euler():
 # ---------------------------------------------------------------------------------------
 # Products and the parameter derivative
 # ---------------------------------------------------------------------------------------
-@pytest.mark.parametrize("name", MODELS + PATHED + BINEQED)
+@pytest.mark.parametrize("name", MODELS + PATHED + BINEQED + BOLZAED)
 def test_products_vs_complex_step_and_adjoint(name):
     w = small(name, 3 if name.startswith("heat") else 9)
     P = O.Problem(w)
@@ -616,7 +659,7 @@ def test_products_vs_complex_step_and_adjoint(name):
     np.testing.assert_allclose(Hv, O.cs_lagrangian_grad(P, x, v, y, sigma), rtol=1e-12, atol=1e-13)
 
 
-@pytest.mark.parametrize("name", MODELS + PATHED + BINEQED)
+@pytest.mark.parametrize("name", MODELS + PATHED + BINEQED + BOLZAED)
 def test_kkt_assembly_structure_and_action(name):
     """The KKT matrix [H + D, J^T; J, -delta_c I] (lower triangle): sorted, every diagonal
     present once, nnz = nnz_H + nnz_J + m + (diagonals H lacks); its symmetric action on
