@@ -188,6 +188,19 @@ ocp_status ocp_set_free_final_time(ocp_t* h, int enable);
  * ocp_set_boundary). */
 ocp_status ocp_set_final_components(ocp_t* h, int count, const int32_t* comps, const double* values);
 
+/* Boundary cost (paper Sec. 3: the Bolza term g(X_0, X_N) of the objective), for every model:
+ *     F += g(z) = sum_v [ a[v] (z_v - b[v])^2 + l[v] z_v ],   z = (X_0, X_N)
+ * (terminal penalties, start-end couplings).  Host arrays a, b, l of 2 nx (v < nx is X_{0,v},
+ * nx + v is X_{N,v}); all three NULL remove it.  The gradient gains dg/dz at X_0 and X_N; the
+ * Hessian gains sigma 2 a[v] on the (k, k) entry of node 0 or node N, and (k, k) becomes
+ * structural in every node's block (zero at the other nodes).  Every evaluation, hprod and the
+ * KKT assembly include it (one small kernel after the others on the same stream).  With the
+ * Euler scheme the X_N terms must be linear (node N has no Hessian block): OCP_EMODEL here or
+ * in ocp_set_scheme otherwise.  Not in node ranges, the batched form or the objective-only
+ * kernels of the differentiation form (OCP_EMODEL).  Rebuilds the pattern.  Errors: OCP_EINVAL
+ * (some but not all arrays NULL, non-finite values). */
+ocp_status ocp_set_boundary_cost(ocp_t* h, const double* a, const double* b, const double* l);
+
 /* Terminal (Mayer) cost added to the objective: F += sum_k mayer_k X_{N,k} (host array of nx;
  * NULL removes it).  Goddard "r(tf) -> max" is mayer = (-1, 0, 0).  Other models: OCP_EMODEL. */
 ocp_status ocp_set_terminal_cost(ocp_t* h, const double* mayer);

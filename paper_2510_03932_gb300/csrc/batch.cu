@@ -285,6 +285,7 @@ ocp_status ocp_batch_create(ocp_t* const* items, int count, ocp_batch_t** out) {
       return set_err(nullptr, OCP_EMODEL, "batched evaluation is provided for the trapezoidal scheme");
     if (items[i]->npath > 0) return set_err(nullptr, OCP_EMODEL, "batched evaluation has no path inequalities");
     if (items[i]->nbin > 0) return set_err(nullptr, OCP_EMODEL, "batched evaluation has no boundary inequalities");
+    if (items[i]->has_bol) return set_err(nullptr, OCP_EMODEL, "batched evaluation has no boundary cost");
     if (items[i]->device != items[0]->device) return set_err(nullptr, OCP_EINVAL, "problems on different devices");
   }
   ocp_batch* b = new (std::nothrow) ocp_batch();

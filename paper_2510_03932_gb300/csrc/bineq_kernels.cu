@@ -1,3 +1,5 @@
+// Boundary terms on (X_0, X_N): the inequalities b(X_0, X_N) <= 0 and the boundary cost g(X_0,
+// X_N) of the objective (both paper Sec. 3).
 // Boundary inequalities (paper Sec. 3: b(X_0, X_N) <= 0) in the quadratic-plus-linear family
 //     b_q(z) = sum_v [ a_{q,v} (z_v - b_{q,v})^2 + l_{q,v} z_v ] - r_q ,   z = (X_0, X_N),
 // rows nb + nx N + npath nun + q after the path rows.  Derivatives:
@@ -152,6 +154,92 @@ ocp_status bin_upload(ocp* h) {
       (e = cudaMemcpy(h->d_bbase, base.data(), base.size() * 8, cudaMemcpyHostToDevice)) != cudaSuccess)
     return cuda_err(h, e, "cudaMemcpy(boundary inequality tables)");
   return OCP_OK;
+}
+
+// ======================================================================================
+// Boundary cost (paper Sec. 3, the Bolza term g(X_0, X_N)) added to the objective:
+//     g(z) = sum_v [ a_v (z_v - b_v)^2 + l_v z_v ],   z = (X_0, X_N),
+// dg/dz_v = 2 a_v (z_v - b_v) + l_v,  d2g/dz_v^2 = 2 a_v (sigma times that in H).  One thread,
+// after the model's kernel and the constraint rows' kernels on the same stream: it adds g to
+// f, its gradient to g, sigma 2 a_v to the Hessian diagonals of nodes 0 and N and
+// sigma 2 a_v v_z to H v, in term order.
+// ======================================================================================
+struct BolArgs {
+  const double* __restrict__ x;
+  const double* __restrict__ vn;
+  double *f, *g, *hv, *ohv;
+  double sigma;
+  int64_t N, xN;
+  int nx, nt, hx;
+  int16_t v[256];         // terms: local index of z (v < nx: X_0, else X_N)
+  int16_t hd[256];        // position of (k, k) in the node's X block
+  double a[256], b[256], l[256];
+};
+
+template <bool WF, bool WG, bool WH, bool WHV>
+__global__ void __launch_bounds__(32) k_bol(const __grid_constant__ BolArgs a) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double gs = 0.0;
+  for (int t = 0; t < a.nt; ++t) {
+    const int v = a.v[t];
+    const bool fin = v >= a.nx;
+    const int k = fin ? v - a.nx : v;
+    const int64_t col = fin ? a.xN + k : (int64_t)k;
+    const double z = a.x[col];
+    const double d = z - a.b[t];
+    if (WF) gs = gs + (a.a[t] * d * d + a.l[t] * z);
+    if (WG) a.g[col] = a.g[col] + (2.0 * a.a[t] * d + a.l[t]);
+    if (a.a[t] != 0.0) {
+      const double h2 = a.sigma * (2.0 * a.a[t]);
+      if (WH) {
+        const int64_t slot = (fin ? a.N * a.hx : 0) + a.hd[k];
+        a.hv[slot] = a.hv[slot] + h2;
+      }
+      if (WHV) a.ohv[col] = a.ohv[col] + h2 * a.vn[col];
+    }
+  }
+  if (WF) a.f[0] = a.f[0] + gs;
+}
+
+static ocp_status bol_fill(const ocp* h, double sigma, BolArgs& a) {
+  const Pattern& P = h->pat;
+  memset(&a, 0, sizeof(a));
+  if (2 * h->nx > 256) return OCP_EDIM;
+  a.sigma = sigma; a.N = h->N; a.xN = (int64_t)h->nx * h->N; a.nx = h->nx; a.hx = P.hx;
+  for (int v = 0; v < 2 * h->nx; ++v) {
+    if (h->bol_a[v] == 0.0 && h->bol_l[v] == 0.0) continue;
+    a.v[a.nt] = (int16_t)v;
+    a.a[a.nt] = h->bol_a[v]; a.b[a.nt] = h->bol_b[v]; a.l[a.nt] = h->bol_l[v];
+    ++a.nt;
+  }
+  for (int k = 0; k < h->nx; ++k) a.hd[k] = (int16_t)P.hdiag[k];
+  return OCP_OK;
+}
+
+ocp_status bol_eval(ocp* h, const EvalCall& c, cudaStream_t s) {
+  if (!h->has_bol) return OCP_OK;
+  if (c.range) return set_err(h, OCP_EMODEL, "node ranges are not provided with a boundary cost");
+  BolArgs a;
+  if (bol_fill(h, c.sigma, a) != OCP_OK) return set_err(h, OCP_EDIM, "too many states for the boundary cost");
+  a.x = c.x; a.vn = c.vn; a.f = c.f; a.g = c.g; a.hv = c.hv; a.ohv = c.ohv;
+  const bool F = c.f, G = c.g, H = c.hv, HV = c.ohv;
+  if (F && G && H && HV) k_bol<true, true, true, true><<<1, 32, 0, s>>>(a);
+  else {
+    if (F) k_bol<true, false, false, false><<<1, 32, 0, s>>>(a);
+    if (G) k_bol<false, true, false, false><<<1, 32, 0, s>>>(a);
+    if (H) k_bol<false, false, true, false><<<1, 32, 0, s>>>(a);
+    if (HV) k_bol<false, false, false, true><<<1, 32, 0, s>>>(a);
+  }
+  return cuda_err(h, cudaGetLastError(), "boundary cost launch");
+}
+
+ocp_status bol_prod(ocp* h, const ProdCall& c, cudaStream_t s) {
+  if (!h->has_bol || c.kind != P_HPROD) return OCP_OK;
+  BolArgs a;
+  if (bol_fill(h, c.sigma, a) != OCP_OK) return set_err(h, OCP_EDIM, "too many states for the boundary cost");
+  a.x = c.x; a.vn = c.v; a.ohv = c.out;
+  k_bol<false, false, false, true><<<1, 32, 0, s>>>(a);
+  return cuda_err(h, cudaGetLastError(), "boundary cost launch");
 }
 
 }  // namespace ocpg

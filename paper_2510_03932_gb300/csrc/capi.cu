@@ -348,6 +348,7 @@ ocp_status ocpg::dispatch_eval(ocp* h, unsigned out, const EvalCall& c, void* st
   ocp_status st = model_eval(h, out, c, s);
   if (st == OCP_OK && h->pat.npath > 0) st = path_eval(h, out, c, s);
   if (st == OCP_OK && h->pat.nbin > 0) st = bin_eval(h, out, c, s);
+  if (st == OCP_OK && h->has_bol) st = bol_eval(h, c, s);
   return st;
 }
 
@@ -368,6 +369,7 @@ static ocp_status dispatch_prod(ocp* h, const ProdCall& c, void* stream) {
   ocp_status st = model_prod(h, c, s);
   if (st == OCP_OK && h->pat.npath > 0) st = path_prod(h, c, s);
   if (st == OCP_OK && h->pat.nbin > 0) st = bin_prod(h, c, s);
+  if (st == OCP_OK && h->has_bol) st = bol_prod(h, c, s);
   return st;
 }
 
@@ -507,6 +509,8 @@ ocp_status ocp_eval_all_range(ocp_t* h, int64_t node_begin, int64_t node_end, co
     return set_err(h, OCP_EMODEL, "node ranges are not provided for the Goddard model (tf couples every node)");
   if (h->nbin > 0)
     return set_err(h, OCP_EMODEL, "node ranges are not provided with boundary inequalities (they couple nodes 0 and N)");
+  if (h->has_bol)
+    return set_err(h, OCP_EMODEL, "node ranges are not provided with a boundary cost (it couples nodes 0 and N)");
   NEED(x); NEED(y); NEED(f); NEED(cv); NEED(g); NEED(jvals); NEED(hvals);
   EvalCall c;
   c.B = node_begin; c.E = node_end; c.range = true;
@@ -557,6 +561,7 @@ ocp_status ocp_hprod_param(ocp_t* h, const double* x, const double* y, double si
 ocp_status ocp_eval_grad_scaled(ocp_t* h, const double* x, const double* s, double* g, void* stream) {
   if (!h) return OCP_EINVAL;
   NEED(x); NEED(s); NEED(g);
+  if (h->has_bol) return set_err(h, OCP_EMODEL, "the objective-only kernels do not include a boundary cost");
   return obj_launch(h, false, x, s, nullptr, g, nullptr, (cudaStream_t)stream);
 }
 
@@ -564,6 +569,7 @@ ocp_status ocp_obj_hvp(ocp_t* h, const double* x, const double* s, const double*
                        void* stream) {
   if (!h) return OCP_EINVAL;
   NEED(x); NEED(s); NEED(v); NEED(Hv); OPT(dot);
+  if (h->has_bol) return set_err(h, OCP_EMODEL, "the objective-only kernels do not include a boundary cost");
   return obj_launch(h, true, x, s, v, Hv, dot, (cudaStream_t)stream);
 }
 
@@ -646,8 +652,33 @@ ocp_status ocp_start_point(ocp_t* h, const double* xs, const double* us, double 
   return cuda_err(h, cudaGetLastError(), "k_start_point launch");
 }
 
+ocp_status ocp_set_boundary_cost(ocp_t* h, const double* a, const double* b, const double* l) {
+  if (!h) return OCP_EINVAL;
+  const int bz = 2 * h->nx;
+  if (!a && !b && !l) {
+    h->has_bol = false;
+    h->bol_a.clear(); h->bol_b.clear(); h->bol_l.clear();
+    return rebuild(h);
+  }
+  if (!a || !b || !l) return set_err(h, OCP_EINVAL, "a, b and l are required (all NULL removes the cost)");
+  for (int v = 0; v < bz; ++v)
+    if (!std::isfinite(a[v]) || !std::isfinite(b[v]) || !std::isfinite(l[v]))
+      return set_err(h, OCP_EINVAL, "boundary cost coefficients must be finite");
+  if (h->scheme == OCP_SCHEME_EULER)
+    for (int k = 0; k < h->nx; ++k)
+      if (a[h->nx + k] != 0.0)
+        return set_err(h, OCP_EMODEL, "with the Euler scheme the boundary cost is linear in X_N");
+  h->has_bol = true;
+  h->bol_a.assign(a, a + bz); h->bol_b.assign(b, b + bz); h->bol_l.assign(l, l + bz);
+  return rebuild(h);
+}
+
 ocp_status ocp_set_scheme(ocp_t* h, int scheme) {
   if (!h) return OCP_EINVAL;
+  if (scheme == OCP_SCHEME_EULER && h->has_bol)
+    for (int k = 0; k < h->nx; ++k)
+      if (h->bol_a[h->nx + k] != 0.0)
+        return set_err(h, OCP_EMODEL, "with the Euler scheme the boundary cost is linear in X_N");
   if (scheme != OCP_SCHEME_TRAPEZOID && scheme != OCP_SCHEME_EULER) return set_err(h, OCP_EINVAL, "unknown scheme");
   if (scheme == OCP_SCHEME_EULER && h->nbin > 0)
     return set_err(h, OCP_EMODEL, "boundary inequalities are provided for the trapezoidal scheme");

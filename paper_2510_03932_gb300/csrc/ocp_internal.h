@@ -109,6 +109,9 @@ struct ocp {
   // (nbin x 2 nx, row-major)
   int nbin = 0;
   std::vector<double> bin_a, bin_b, bin_l, bin_r;
+  // boundary cost sum_v [a (z_v - b)^2 + l z_v] on z = (X_0, X_N) added to the objective (2 nx)
+  bool has_bol = false;
+  std::vector<double> bol_a, bol_b, bol_l;
   const double* p0_dev = nullptr;  // device scalar overriding params[0] (or null)
   // time-varying state reference: xref_k + xslope_k t_j + xamp_k sin(xfreq_k t_j) for the
   // components trk_comp (ntrk of them), tabulated once per node in d_xtrack[(N+1) x ntrk]
@@ -233,6 +236,9 @@ ocp_status path_upload(ocp* h);
 ocp_status bin_eval(ocp* h, unsigned out, const EvalCall& c, cudaStream_t s);
 ocp_status bin_prod(ocp* h, const ProdCall& c, cudaStream_t s);
 ocp_status bin_upload(ocp* h);
+// The boundary cost: its value, gradient and Hessian terms after the other kernels.
+ocp_status bol_eval(ocp* h, const EvalCall& c, cudaStream_t s);
+ocp_status bol_prod(ocp* h, const ProdCall& c, cudaStream_t s);
 // Releases the scatter map (called on every pattern rebuild and by ocp_destroy).
 void scatter_map_free(ocp* h);
 // Releases what ocp_eval_step_host allocated (called by ocp_destroy).

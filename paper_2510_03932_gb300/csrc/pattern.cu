@@ -143,6 +143,8 @@ bool build_pattern(ocp* h, std::string& why) {
     // (one template for every node: a boundary term's diagonal is present at every node)
     for (int q = 0; q < P.nbin && a == b && a < P.nx; ++q)
       path_sq = path_sq || h->bin_a[q * bz + a] != 0.0 || h->bin_a[q * bz + P.nx + a] != 0.0;
+    if (h->has_bol && a == b && a < P.nx)  // the boundary cost's squared terms likewise
+      path_sq = path_sq || h->bol_a[a] != 0.0 || h->bol_a[P.nx + a] != 0.0;
     const bool present = dyn[e] || (a == b && (coef != 0.0 || path_sq));
     if (!present) continue;
     if (a < P.nx) { P.hpos[e] = (int8_t)(px < 127 ? px : 127); ++px; ex.push_back(ent[e]); }

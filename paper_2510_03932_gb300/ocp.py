@@ -48,6 +48,7 @@ _SIGS = {
     "ocp_set_scheme": [_P, C.c_int],
     "ocp_set_path_constraints": [_P, C.c_int, _P, _P, _P, _P],
     "ocp_set_boundary_inequalities": [_P, C.c_int, _P, _P, _P, _P],
+    "ocp_set_boundary_cost": [_P, _P, _P, _P],
     "ocp_jac_scatter_map": [_P, _P, _P, _P, _P],
     "ocp_start_point": [_P, _P, _P, _D, _P, _P],
     "ocp_jtprod_coo": [_P, _P, _P, _P, _P],
@@ -126,7 +127,7 @@ class OCP:
 
     def __init__(self, model: str, nx: int, nu: int, N: int, T: float, params, q, r, xref=None, uref=None,
                  x0=None, xf=None, xslope=None, xamp=None, xfreq=None, free_tf=False, xf_comp=None,
-                 mayer=None, bounds=None, scheme="trapezoid", path=None, bineq=None):
+                 mayer=None, bounds=None, scheme="trapezoid", path=None, bineq=None, bolza=None):
         L = lib()
         self._keep = []
 
@@ -160,6 +161,8 @@ class OCP:
             flat = lambda rows: [float(v) for row in rows for v in row]
             _check(L.ocp_set_boundary_inequalities(h, len(bineq["r"]), arr(flat(bineq["a"])), arr(flat(bineq["b"])),
                                                    arr(flat(bineq["l"])), arr(bineq["r"])), h)
+        if bolza:  # F += sum_v [a (z_v - b)^2 + l z_v] over z = (X_0, X_N)
+            _check(L.ocp_set_boundary_cost(h, arr(bolza["a"]), arr(bolza["b"]), arr(bolza["l"])), h)
         if free_tf:
             _check(L.ocp_set_free_final_time(h, 1), h)
         if mayer is not None:
@@ -182,7 +185,7 @@ class OCP:
         return cls(w["model"], w["nx"], w["nu"], w["N"], w["T"], w["params"], w["q"], w["r"], w.get("xref"),
                    w.get("uref"), w.get("x0"), w.get("xf"), w.get("xslope"), w.get("xamp"), w.get("xfreq"),
                    bool(w.get("free_tf")), w.get("xf_comp"), w.get("mayer"), w.get("bounds"),
-                   w.get("scheme", "trapezoid"), w.get("path"), w.get("bineq"))
+                   w.get("scheme", "trapezoid"), w.get("path"), w.get("bineq"), w.get("bolza"))
 
     def close(self):
         if getattr(self, "h", None):

@@ -47,6 +47,8 @@ def named(name, N=None):
         w = synth.with_path(w)
     if "bineq" in plus:
         w = synth.with_bineq(w)
+    if "bolza" in plus:
+        w = synth.with_bolza(w)
     return w
 
 
@@ -108,6 +110,10 @@ SMALL = [("vdp_n1e3", N) for N in (1, 2, 3, 254, 255, 256, 510, 1000, 1777)] + \
          for N in (1, 300)] + \
         [(nm + "+bineq", N) for nm in ("vdp_n1e3", "cartpole_n1e5", "dint", "quadrotor_n1e3", "goddard_n1e3",
                                         "heat_n2e4", "vdp_n1e3+path")
+         for N in (1, 2, 300)] + \
+        [(nm + "+bolza", N) for nm in ("vdp_n1e3", "cartpole_n1e5", "dint", "quadrotor_n1e3", "goddard_n1e3",
+                                        "heat_n2e4", "vdp_n1e3:euler", "quadrotor_n1e3:euler+path",
+                                        "cartpole_n1e5+path+bineq")
          for N in (1, 2, 300)]
 
 
@@ -153,6 +159,8 @@ def _random_case(i):
         w = synth.with_path(w)
     if not euler and rng.random() < 0.5:
         w = synth.with_bineq(w)
+    if rng.random() < 0.4:
+        w = synth.with_bolza(w)
     return dict(w, sigma=float(rng.choice([0.0, 0.37, 1.0, 2.5])))
 
 
@@ -340,7 +348,8 @@ def test_dimension_and_argument_errors(ocp):
                                     ("goddard_n1e3+path", 500), ("heat_n2e4+path", 40),
                                     ("heat_n2e4", 20000), ("heat_n2e4", 2), ("heat_n2e4", 31),
                                     ("vdp_n1e3+bineq", 700), ("goddard_n1e3+bineq", 500), ("heat_n2e4+bineq", 40),
-                                    ("dint+path+bineq", 97)])
+                                    ("dint+path+bineq", 97), ("vdp_n1e3+bolza", 700), ("goddard_n1e3+bolza", 300),
+                                    ("heat_n2e4+bolza", 40), ("vdp_n1e3:euler+bolza", 500)])
 def test_fused_step_equals_separate_calls(ocp, name, N):
     """ocp_eval_step (one pass: eval + Jv + J^T w + Hv) is bit-identical to the separate calls."""
     w = named(name, N)
@@ -437,7 +446,7 @@ def test_host_step_rejects_device_tensors(ocp):
                                     ("goddard_fixed", 300), ("vdp_n1e3:euler", 600), ("quadrotor_n1e3:euler", 200),
                                     ("quadrotor_n1e3+path", 300), ("vdp_n1e3:euler+path", 400),
                                     ("vdp_n1e3+bineq", 300), ("dint+path+bineq", 97), ("goddard_n1e3+bineq", 200),
-                                    ("heat_n2e4+bineq", 30)])
+                                    ("heat_n2e4+bineq", 30), ("dint+bolza", 97), ("quadrotor_n1e3+bolza", 60)])
 def test_kkt_assembly(ocp, name, N):
     """KKT structure bit-exact with the oracle's assembly; values are the GPU's own H and J
     values moved bit for bit (plus sigma_x + delta_w on the diagonal) and pass the parity gate
@@ -609,6 +618,37 @@ def test_boundary_inequalities_bounds_checks_and_refusals(ocp):
     assert L.ocp_dims(H.h, C.byref(n), C.byref(m), C.byref(nj), C.byref(nh)) == 0
     assert (n.value, m.value, nj.value, nh.value) == (P0.n, P0.m, P0.nnzj, P0.nnzh)
     H.close()
+
+
+def test_boundary_cost_checks_and_refusals(ocp):
+    """The boundary cost: bad arguments refused, squared X_N terms refused with Euler (here and
+    when switching the scheme), node ranges, the batched form and the objective-only kernels
+    refuse it; removing it restores the plain objective bit for bit."""
+    import ctypes as C
+    w = named("cartpole_n1e5+bolza", 30)
+    H = ocp.OCP.from_workload(w)
+    d = synth.draw(w)
+    x, y = dev(d["x"]), dev(d["y"])
+    L = ocp.lib()
+    a = (C.c_double * 8)(*([1.0] * 8))
+    assert L.ocp_set_boundary_cost(H.h, C.cast(a, C.c_void_p), None, None) == 1
+    assert L.ocp_set_scheme(H.h, 1) == 5
+    f, c, g, jv, hv = H.eval_all(x, y, 1.0)
+    assert L.ocp_eval_all_range(H.h, 0, 10, ocp._ptr(x), ocp._ptr(y), 1.0, ocp._ptr(f), ocp._ptr(c), ocp._ptr(g),
+                                ocp._ptr(jv), ocp._ptr(hv), None) == 5
+    s = torch.ones(1, dtype=torch.float64, device="cuda")
+    assert L.ocp_eval_grad_scaled(H.h, ocp._ptr(x), ocp._ptr(s), ocp._ptr(g), None) == 5
+    with pytest.raises(ocp.OcpError):
+        ocp.OCPBatch([H])
+    assert L.ocp_set_boundary_cost(H.h, None, None, None) == 0
+    H0 = ocp.OCP.from_workload({k: v for k, v in w.items() if k != "bolza"})
+    torch.cuda.synchronize()
+    assert torch.equal(H.eval_obj(x), H0.eval_obj(x))
+    E = ocp.OCP.from_workload(named("vdp_n1e3:euler", 20))
+    a6 = (C.c_double * 4)(0.0, 0.0, 0.0, 1.0)
+    z4 = (C.c_double * 4)(0.0, 0.0, 0.0, 0.0)
+    assert L.ocp_set_boundary_cost(E.h, C.cast(a6, C.c_void_p), C.cast(z4, C.c_void_p), C.cast(z4, C.c_void_p)) == 5
+    H.close(); H0.close(); E.close()
 
 
 def test_path_rows_bounds_and_checks(ocp):
