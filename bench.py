@@ -1,13 +1,12 @@
 """Benchmark: Jacobian + Hessian COO nonzeros per second (FP64) of the trapezoidal
 transcription evaluator on GB300, with the HBM roofline fraction of the dominant kernel.
 
-One step = one pass of the hot path on one problem: the fused evaluation (objective,
-constraints, gradient, Jacobian and Hessian values) followed by the three products Jv,
-J^T v and H v.  value = (nnz_J + nnz_H) * steps * ranks / (max over ranks of the summed
+One step = one pass of the hot path on one problem (ocp_eval_step, one launch): objective,
+constraints, gradient, Jacobian and Hessian values and the three products Jv, J^T v and H v.  value = (nnz_J + nnz_H) * steps * ranks / (max over ranks of the summed
 step times).  Inputs are resident in HBM; between timed steps the L2 is flushed by
 writing a 512 MB buffer (outside the timed events).  `e2e` repeats the step through the
-host-buffer call ocp_eval_step_host (pinned host arrays in and out, every host<->device copy
-inside the timed region).
+host-buffer call ocp_eval_step_host_async (pinned host arrays in and out, every host<->device
+copy inside the timed region, joined by ocp_host_step_wait before the end event).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
 
@@ -322,8 +321,10 @@ def run_ours(args, rank, world):
     kkt_ms = float(np.mean([a.elapsed_time(b) for a, b in kk]))
     kkt_bytes = 8 * (nnzj + nnzh + n + kv.numel())
     # --- end to end: pinned host buffers, copies inside the timed region.  The step goes through
-    # ocp_eval_step_host (host arrays in and out; the library pipelines node ranges over its copy
-    # streams); the same copies issued whole around the device step are timed beside it.
+    # ocp_eval_step_host_async (host arrays in and out, copied whole on the library's copy
+    # streams; the next step overlaps the previous step's output copy) with one
+    # ocp_host_step_wait before the end event; the joined ocp_eval_step_host and the same copies
+    # issued around the device step are timed beside it.
     hx = torch.from_numpy(d["x"]).pin_memory(); hy = torch.from_numpy(d["y"]).pin_memory()
     hvn = torch.from_numpy(d["vn"]).pin_memory(); hvm = torch.from_numpy(d["vm"]).pin_memory()
     outs = [f, c, g, jv, hv, Jv, Jtv, Hv]
@@ -332,6 +333,9 @@ def run_ours(args, rank, world):
 
     def host_step():
         H.eval_step_host(hx, hy, sigma, hvn, hvm, houts, stream)
+
+    def host_step_async():
+        H.eval_step_host(hx, hy, sigma, hvn, hvm, houts, stream, wait=False)
 
     def copy_then_step():
         x.copy_(hx, non_blocking=True); y.copy_(hy, non_blocking=True)
@@ -359,21 +363,25 @@ def run_ours(args, rank, world):
     def time_e2e_stream(fn, k):
         # k steps back to back on one stream (each with its own copies in and out; the inputs
         # and outputs, 296 MB a step at the default workload, exceed the L2): consecutive
-        # calls overlap one step's input copy with the previous step's output copy
+        # calls overlap one step's input copy with the previous step's output copy; every
+        # output copy is joined to the stream before the end event
         for _ in range(2):
             fn()
+        H.host_step_wait(stream)
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(k):
             fn()
+        H.host_step_wait(stream)
         e1.record(stream)
         torch.cuda.synchronize(dev)
         return e0.elapsed_time(e1) / k
 
     e2e_sync_ms = float(np.mean(time_e2e(host_step)))
     e2e_whole_ms = float(np.mean(time_e2e(copy_then_step)))
-    e2e_ms = [time_e2e_stream(host_step, e2e_steps)]
+    e2e_joined_ms = time_e2e_stream(host_step, e2e_steps)
+    e2e_ms = [time_e2e_stream(host_step_async, e2e_steps)]
     nnz = nnzj + nnzh
     e2e_val = nnz * world / (float(np.mean(e2e_ms)) * 1e-3)
     hbm, peak_kind = peaks()
@@ -417,7 +425,9 @@ def run_ours(args, rank, world):
                           what="K = [H + diag(sigma_x + delta_w), J^T; J, -delta_c I] from the COO values"),
         e2e=dict(value=e2e_val, unit="nnz/s", h2d_bytes_per_step=8 * (n + m + n + m),
                  d2h_bytes_per_step=8 * sum(t.numel() for t in outs), ms=float(np.mean(e2e_ms)),
-                 call="ocp_eval_step_host, %d steps back to back on one stream" % e2e_steps,
+                 call="ocp_eval_step_host_async, %d steps back to back on one stream, then "
+                      "ocp_host_step_wait" % e2e_steps,
+                 joined_calls_ms=e2e_joined_ms,
                  synchronized_step_ms=e2e_sync_ms, whole_copies_around_device_step_ms=e2e_whole_ms),
         gpu_launches=args.steps, clocks=clocks, wall_s=wall,
     )

@@ -305,6 +305,23 @@ ocp_status ocp_eval_step_host(ocp_t* h, const double* x, const double* y, double
                               const double* vm, double* f, double* c, double* g, double* jvals,
                               double* hvals, double* Jv, double* Jtv, double* Hv, void* stream);
 
+/* ocp_eval_step_host without the last wait: `stream` does NOT wait for this call's output copy,
+ * so the next call's step can run while these outputs are still being copied to the host (the
+ * handle's two sets of device copies keep the calls apart).  The outputs are complete once
+ * ocp_host_step_wait(h, stream) has been called after the last such call and `stream` has
+ * reached that point; until then they must not be read, and an output array must not be handed
+ * to a call that is not ordered after this one by that wait or by the handle (calls on one
+ * handle write their outputs in call order).  Inputs, ordering and errors as
+ * ocp_eval_step_host; results bit-identical to ocp_eval_step. */
+ocp_status ocp_eval_step_host_async(ocp_t* h, const double* x, const double* y, double sigma,
+                                    const double* vn, const double* vm, double* f, double* c, double* g,
+                                    double* jvals, double* hvals, double* Jv, double* Jtv, double* Hv,
+                                    void* stream);
+
+/* Make `stream` wait for the output copies of every earlier ocp_eval_step_host(_async) call on
+ * this handle (nothing to wait for: returns OCP_OK).  OCP_EINVAL for a NULL handle. */
+ocp_status ocp_host_step_wait(ocp_t* h, void* stream);
+
 /* KKT matrix of the interior-point step (paper Sec. 6: the solver assembles the KKT system in
  * device buffers from the derivative values), lower triangle, COO sorted by (row, col):
  *     K = [ H + diag(sigma_x + delta_w)                ]    size (n + m) x (n + m)

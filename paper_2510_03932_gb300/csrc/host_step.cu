@@ -11,6 +11,9 @@
 // flight while the previous one is evaluated and the one before it copied out) measured
 // 1.73-2.02 ms per step at Van der Pol N = 1e6 with 2 to 16 ranges, against 1.64 ms for whole
 // arrays (the extra copies and waits cost more than the partial overlap they bought).
+// ocp_eval_step_host_async leaves out the caller's wait for the copy-out, so the next call's step
+// runs while this call's outputs are still crossing the host link; ocp_host_step_wait joins
+// the copies later.
 #include <cstring>
 
 #include "ocp_internal.h"
@@ -29,6 +32,9 @@ struct HostStep {
 void host_step_free(ocp* h) {
   HostStep* s = h ? h->hstep : nullptr;
   if (!s) return;
+  // copies of earlier calls may still read the mirrors or write the caller's host arrays
+  if (s->sd) cudaStreamSynchronize(s->sd);
+  if (s->sh) cudaStreamSynchronize(s->sh);
   for (int b = 0; b < 2; ++b) {
     cudaFree(s->buf[b]);
     for (cudaEvent_t e : {s->in[b], s->comp[b], s->done[b]})
@@ -99,10 +105,10 @@ static ocp_status host_step_ready(ocp* h) {
 
 using namespace ocpg;
 
-extern "C" ocp_status ocp_eval_step_host(ocp_t* h, const double* x, const double* y, double sigma,
-                                         const double* vn, const double* vm, double* f, double* cv, double* g,
-                                         double* jvals, double* hvals, double* Jv, double* Jtv, double* Hv,
-                                         void* stream) {
+// One host step; with `join` the caller's stream waits for the copy-out of this call.
+static ocp_status host_step_run(ocp_t* h, const double* x, const double* y, double sigma, const double* vn,
+                                const double* vm, double* f, double* cv, double* g, double* jvals,
+                                double* hvals, double* Jv, double* Jtv, double* Hv, void* stream, bool join) {
   if (!h) return OCP_EINVAL;
   const double* in[4] = {x, y, vn, vm};
   double* out[8] = {f, cv, g, jvals, hvals, Jv, Jtv, Hv};
@@ -134,8 +140,33 @@ extern "C" ocp_status ocp_eval_step_host(ocp_t* h, const double* x, const double
   for (int i = 0; i < 8 && e == cudaSuccess; ++i)
     e = cudaMemcpyAsync(out[i], A[4 + i], sizeof(double) * (size_t)sz[4 + i], cudaMemcpyDeviceToHost, S->sd);
   if (e == cudaSuccess) e = cudaEventRecord(S->done[b], S->sd);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(s0, S->done[b], 0);
+  if (e == cudaSuccess && join) e = cudaStreamWaitEvent(s0, S->done[b], 0);
   if (e != cudaSuccess) return cuda_err(h, e, "host step: outputs");
   S->next = b ^ 1;
+  return OCP_OK;
+}
+
+extern "C" ocp_status ocp_eval_step_host(ocp_t* h, const double* x, const double* y, double sigma,
+                                         const double* vn, const double* vm, double* f, double* cv, double* g,
+                                         double* jvals, double* hvals, double* Jv, double* Jtv, double* Hv,
+                                         void* stream) {
+  return host_step_run(h, x, y, sigma, vn, vm, f, cv, g, jvals, hvals, Jv, Jtv, Hv, stream, true);
+}
+
+extern "C" ocp_status ocp_eval_step_host_async(ocp_t* h, const double* x, const double* y, double sigma,
+                                               const double* vn, const double* vm, double* f, double* cv,
+                                               double* g, double* jvals, double* hvals, double* Jv, double* Jtv,
+                                               double* Hv, void* stream) {
+  return host_step_run(h, x, y, sigma, vn, vm, f, cv, g, jvals, hvals, Jv, Jtv, Hv, stream, false);
+}
+
+extern "C" ocp_status ocp_host_step_wait(ocp_t* h, void* stream) {
+  if (!h) return OCP_EINVAL;
+  HostStep* S = h->hstep;
+  if (!S) return OCP_OK;
+  // the copy-out stream is serial, so its last recorded event covers every earlier copy; an
+  // event never recorded counts as complete
+  cudaError_t e = cudaStreamWaitEvent((cudaStream_t)stream, S->done[S->next ^ 1], 0);
+  if (e != cudaSuccess) return cuda_err(h, e, "host step: wait");
   return OCP_OK;
 }

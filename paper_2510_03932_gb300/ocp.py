@@ -73,6 +73,8 @@ _SIGS = {
     "ocp_eval_all": [_P, _P, _P, _D, _P, _P, _P, _P, _P, _P],
     "ocp_eval_step": [_P, _P, _P, _D, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P],
     "ocp_eval_step_host": [_P, _P, _P, _D, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P],
+    "ocp_eval_step_host_async": [_P, _P, _P, _D, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P],
+    "ocp_host_step_wait": [_P, _P],
     "ocp_eval_all_range": [_P, _I64, _I64, _P, _P, _D, _P, _P, _P, _P, _P, _P],
     "ocp_vjp_param": [_P, _P, _P, _P, _P, _P],
     "ocp_set_param0": [_P, _D],
@@ -342,11 +344,13 @@ class OCP:
             raise ValueError("%s has %d elements, expected %d" % (name, t.numel(), size))
         return t
 
-    def eval_step_host(self, x, y, sigma, vn, vm, outs=None, stream=None):
+    def eval_step_host(self, x, y, sigma, vn, vm, outs=None, stream=None, wait=True):
         """The fused step with host (CPU) tensors in and out, through ocp_eval_step_host: the
         library copies the inputs to its device copies, runs the step and copies the outputs
         back, on its own copy streams joined to `stream` (default: the current stream).  The
-        outputs are complete once `stream` is synchronized."""
+        outputs are complete once `stream` is synchronized.  With wait=False
+        (ocp_eval_step_host_async) `stream` does not wait for the output copy, so the next
+        step overlaps it; call host_step_wait before synchronizing and reading the outputs."""
         x = self._hvec(x, self.n, "x"); y = self._hvec(y, self.m, "y")
         vn = self._hvec(vn, self.n, "vn"); vm = self._hvec(vm, self.m, "vm")
         sizes = ((1, "f"), (self.m, "c"), (self.n, "g"), (self.nnzj, "jvals"), (self.nnzh, "hvals"),
@@ -354,9 +358,14 @@ class OCP:
         if outs is None:
             outs = tuple(torch.empty(k, dtype=torch.float64).pin_memory() for k, _ in sizes)
         outs = tuple(self._hvec(t, k, nm) for t, (k, nm) in zip(outs, sizes))
-        _check(lib().ocp_eval_step_host(self.h, _ptr(x), _ptr(y), float(sigma), _ptr(vn), _ptr(vm),
-                                        *[_ptr(t) for t in outs], _stream(stream)), self.h)
+        fn = lib().ocp_eval_step_host if wait else lib().ocp_eval_step_host_async
+        _check(fn(self.h, _ptr(x), _ptr(y), float(sigma), _ptr(vn), _ptr(vm),
+                  *[_ptr(t) for t in outs], _stream(stream)), self.h)
         return outs
+
+    def host_step_wait(self, stream=None):
+        """Make `stream` wait for the output copies of every earlier host step on this handle."""
+        _check(lib().ocp_host_step_wait(self.h, _stream(stream)), self.h)
 
     def start_point(self, xs=None, us=None, tf=0.0, out=None, stream=None):
         """x with X_{j,k} = xs[k], U_{j,i} = us[i] at every node (and tf), on the device."""

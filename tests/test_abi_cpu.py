@@ -87,3 +87,6 @@ def test_null_handle_is_rejected(lib):
     lib.eval_obj.restype = C.c_int
     lib.eval_obj.argtypes = [C.c_void_p] * 4
     assert lib.eval_obj(None, None, None, None) == 1
+    lib.ocp_host_step_wait.restype = C.c_int
+    lib.ocp_host_step_wait.argtypes = [C.c_void_p] * 2
+    assert lib.ocp_host_step_wait(None, None) == 1

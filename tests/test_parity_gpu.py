@@ -371,7 +371,7 @@ def test_fused_step_equals_separate_calls(ocp, name, N):
                                            ("vdp_n1e3:euler", 600, True), ("vdp_mu_n1e6", None, True),
                                            ("quadrotor_n1e3+bineq", 300, True)])
 def test_host_step_equals_device_step(ocp, name, N, pinned):
-    """ocp_eval_step_host (host arrays in and out, node ranges pipelined over copy streams)
+    """ocp_eval_step_host (host arrays in and out, copied whole on the handle's copy streams)
     returns bit for bit what ocp_eval_step returns on device arrays, on a second call with new
     inputs too, and on a side stream."""
     w = named(name, N)
@@ -408,6 +408,36 @@ def test_host_step_back_to_back_calls(ocp):
         torch.cuda.synchronize()
         for a, b in zip(got, ref):
             assert torch.equal(a, b.cpu())
+    H.close()
+
+
+@pytest.mark.parametrize("name,N", [("cartpole_n1e5", 5000), ("quadrotor_n1e3+bolza", 300), ("heat_n2e4", 50)])
+def test_host_step_async_back_to_back(ocp, name, N):
+    """Five ocp_eval_step_host_async calls on one stream with no wait in between (each step may
+    run while the previous outputs are still being copied out), the last two on the same output
+    arrays, then one ocp_host_step_wait: every call's outputs match the device step of its own
+    inputs bit for bit, and the shared arrays hold the last call's."""
+    w = named(name, N)
+    H = ocp.OCP.from_workload(w)
+    draws = [synth.draw(w, seed=w["seed"] + 20 + i) for i in range(5)]
+    hins = [[torch.from_numpy(d[k]).pin_memory() for k in ("x", "y", "vn", "vm")] for d in draws]
+    outs = [H.eval_step_host(hi[0], hi[1], 0.6, hi[2], hi[3], wait=False) for hi in hins[:4]]
+    outs[3] = H.eval_step_host(*hins[4][:2], 0.6, *hins[4][2:], outs=outs[3], wait=False)
+    H.host_step_wait()
+    torch.cuda.synchronize()
+    for hi, got in zip(hins[:3] + hins[4:], outs):
+        ref = H.eval_step(*(t.cuda() for t in hi[:2]), 0.6, *(t.cuda() for t in hi[2:]))
+        torch.cuda.synchronize()
+        for a, b in zip(got, ref):
+            assert torch.equal(a, b.cpu())
+    H.close()
+
+
+def test_host_step_wait_without_calls(ocp):
+    """ocp_host_step_wait on a handle that never ran a host step has nothing to wait for."""
+    H = ocp.OCP.from_workload(named("dint", 10))
+    H.host_step_wait()
+    torch.cuda.synchronize()
     H.close()
 
 
