@@ -88,7 +88,10 @@ FP64_OPS_PER_NODE = {("vdp", "eval_all"): 26.6, ("vdp", "jh"): 10.0, ("vdp", "jp
                      ("goddard", "eval_all"): 101.2, ("goddard", "jh"): 91.3, ("goddard", "jprod"): 68.3,
                      ("goddard", "jtprod"): 68.2, ("goddard", "hprod"): 95.2, ("goddard", "step"): 155.4,
                      ("vdp:euler", "eval_all"): 21.5, ("vdp:euler", "jh"): 8.0, ("vdp:euler", "jprod"): 11.0,
-                     ("vdp:euler", "jtprod"): 10.0, ("vdp:euler", "hprod"): 10.0, ("vdp:euler", "step"): 41.5}
+                     ("vdp:euler", "jtprod"): 10.0, ("vdp:euler", "hprod"): 10.0, ("vdp:euler", "step"): 41.5,
+                     # heat, 64 cells: the step is its four kernels in sequence
+                     ("heat64", "eval_all"): 1257.3, ("heat64", "jh"): 390.4, ("heat64", "jprod"): 523.4,
+                     ("heat64", "jtprod"): 463.0, ("heat64", "hprod"): 257.0, ("heat64", "step"): 2500.7}
 
 # Rows of the paper's workloads beyond the headline problem (and the cart-pole at the
 # headline horizon), measured the same way (fused step with an L2 flush between steps) and
@@ -100,8 +103,10 @@ CONFIGS = ["vdp_n1e3", "cartpole_n1e5", "heat_n2e4"]
 
 
 def ops_model(w):
-    """Key of FP64_OPS_PER_NODE: the model, with the scheme when it is not the trapezoid."""
-    return w["model"] + (":euler" if w.get("scheme") == "euler" else "")
+    """Key of FP64_OPS_PER_NODE: the model (heat with its cell count), with the scheme when it
+    is not the trapezoid."""
+    m = w["model"] + ("%d" % w["nx"] if w["model"] == "heat" else "")
+    return m + (":euler" if w.get("scheme") == "euler" else "")
 
 
 def named_workload(name):
