@@ -16,6 +16,7 @@
 // consecutive addresses, except the gradient, stored by each lane for its eight cells.  Component-major outputs (defects, Jacobian rows, Jv)
 // are consecutive across lanes and are stored directly or through a per-warp row buffer.
 #include <cstring>
+#include <type_traits>
 
 #include "node_kernels.cuh"
 #include "ocp_internal.h"
@@ -75,8 +76,61 @@ __device__ __forceinline__ void heat_stage(const HeatArgs& a, const double* __re
 // ======================================================================================
 // Fused evaluation
 // ======================================================================================
+
+// Jacobian rows of cell k for the tile's nodes, staged in the warp's row buffer and stored:
+// the entries on x_k are -1 + dk (left node) and +1 + dk (right node), dk = 3 hh x_k^2 + d
+// (d = hh 2/dx^2, or hh/dx^2 at the Neumann end), written fma(3 hh, x_k^2, d -+ 1); every
+// other entry is the constant -hh/dx^2.
+__device__ __forceinline__ void heat_jrows(const HeatArgs& a, int k, bool LAST, int t, int lane, bool act, int nrows,
+                                           int64_t r0, double x2, double* sJw) {
+  const double jl = fma(a.h3, x2, LAST ? a.dl_m1 : a.di_m1);
+  const double jr = fma(a.h3, x2, LAST ? a.dl_p1 : a.di_p1);
+  const int cnt = LAST ? 4 : 6;
+  const int rx = (k == 0 || LAST) ? 2 : 3;
+  const int ru = (k == 0) ? 1 : 0;
+  const int kd = (k == 0) ? 0 : 1;  // position of cell k among the row's X cells
+  if (act && t < nrows) {
+    double* rp = sJw + t * cnt;
+    for (int e = 0; e < rx; ++e) rp[e] = (e == kd) ? jl : a.mhidx2;
+    if (ru) rp[2 * rx] = a.mhidx2;
+  }
+  if (act && t >= 1 && t - 1 < nrows) {
+    double* rp = sJw + (t - 1) * cnt;
+    for (int e = 0; e < rx; ++e) rp[rx + e] = (e == kd) ? jr : a.mhidx2;
+    if (ru) rp[2 * rx + 1] = a.mhidx2;
+  }
+  __syncwarp();
+  double* dst = a.jv + heat_jbase(a, k) + r0 * cnt;
+  const int total = nrows * cnt;
+  for (int i = lane; i < total; i += 32) dst[i] = sJw[i];
+  __syncwarp();
+}
+
+// boundary rows X_{0,k} (and X_{N,k}): one constant entry each
+__device__ __forceinline__ void heat_jbound(const HeatArgs& a, int k, int64_t j) {
+  if (j == 0) a.jv[k] = 1.0;
+  if (a.has_final && j == a.N) a.jv[a.n + k] = 1.0;
+}
+
+// Hessian diagonal of cell k at node j: 6 hh ybar_k x_k + the objective's sigma w q_k
+__device__ __forceinline__ double heat_hdiag(const HeatArgs& a, int k, int64_t j, bool endp, double xk) {
+  const double yl = (j >= 1) ? __ldg(a.y + a.nb + (int64_t)k * a.N + j - 1) : 0.0;
+  const double yr = (j < a.N) ? __ldg(a.y + a.nb + (int64_t)k * a.N + j) : 0.0;
+  const double ty = hmul(a, a.h6, hadd(a, yl, yr));
+  return fma(ty, xk, endp ? a.cq_end[k] : a.cq_in[k]);
+}
+
+// gradient entry of cell k at node j and its objective term
+__device__ __forceinline__ void heat_grad(const HeatArgs& a, int k, int64_t j, bool endp, double xk, bool WG, bool WF,
+                                          double& objacc) {
+  const double d = a.has_ref ? hsub(a, xk, a.ref[k]) : xk;
+  const double gk = hmul(a, endp ? a.gq_end[k] : a.gq_in[k], d);
+  if (WF) objacc = fma(gk, d, objacc);
+  if (WG) a.g[(int64_t)a.n * j + k] = gk;
+}
+
 template <unsigned OUT>
-__global__ void __launch_bounds__(HT_THREADS) k_heat_eval(const __grid_constant__ HeatArgs a) {
+__global__ void __launch_bounds__(HT_THREADS, (OUT & O_C) ? 5 : 8) k_heat_eval(const __grid_constant__ HeatArgs a) {
   constexpr bool CF = OUT & O_F, CC = OUT & O_C, CG = OUT & O_G, CJ = OUT & O_J, CH = OUT & O_H;
   // the full kernel also serves output subsets: NULL outputs are skipped
   const bool WF = CF && a.f, WC = CC && a.c, WG = CG && a.g, WJ = CJ && a.jv, WH = CH && a.hv;
@@ -123,52 +177,25 @@ __global__ void __launch_bounds__(HT_THREADS) k_heat_eval(const __grid_constant_
 
     const int ngroups = (n + 7) / 8;
     double* sJw = sJ + warp * (HT_LANES - 1) * 6;
-    for (int gi = warp; gi < ngroups; gi += HT_WARPS) {
-      const int k0 = gi * 8, k1 = min(k0 + 8, n);
-      for (int k = k0; k < k1; ++k) {
+    if constexpr (CC) {
+      // One cell k of the tile's nodes; LAST: k is the Neumann end n-1.  The end cell is
+      // peeled out of the loop so that its Laplacian and diagonal constant are compile-time
+      // choices: a run-time select between two FP64 results issues both on every cell.
+      auto cell = [&](const int k, auto last_tag) {
+        constexpr bool LAST = decltype(last_tag)::value;
         double xk = 0.0, xl = 0.0, xr = 0.0;
         if (act) {
           xk = sX[t * ld + k];
           xl = (k == 0) ? sX[t * ld + n] : sX[t * ld + k - 1];
-          xr = (k == n - 1) ? xk : sX[t * ld + k + 1];
+          xr = LAST ? xk : sX[t * ld + k + 1];
         }
         const double x2 = hmul(a, xk, xk);
-        // -hh df_k/dx_k = hh (2/dx^2 + 3 x^2)  (or 1/dx^2 at the Neumann end)
-        const bool last = (k == n - 1);
-        if (WJ) {
-          // the entries on x_k: -1 + dk (left node) and +1 + dk (right node), dk = 3 hh x_k^2 + d,
-          // as fma(3 hh x_k, x_k, d -+ 1)
-          const double h3x = hmul(a, a.h3, xk);
-          const double jl = fma(h3x, xk, last ? a.dl_m1 : a.di_m1);
-          const double jr = fma(h3x, xk, last ? a.dl_p1 : a.di_p1);
-          const int cnt = last ? 4 : 6;
-          const int rx = (k == 0 || last) ? 2 : 3;
-          const int ru = (k == 0) ? 1 : 0;
-          const int kd = (k == 0) ? 0 : 1;  // position of cell k among the row's X cells
-          if (act && t < nrows) {
-            double* rp = sJw + t * cnt;
-            for (int e = 0; e < rx; ++e) rp[e] = (e == kd) ? jl : a.mhidx2;
-            if (ru) rp[2 * rx] = a.mhidx2;
-          }
-          if (act && t >= 1 && t - 1 < nrows) {
-            double* rp = sJw + (t - 1) * cnt;
-            for (int e = 0; e < rx; ++e) rp[rx + e] = (e == kd) ? jr : a.mhidx2;
-            if (ru) rp[2 * rx + 1] = a.mhidx2;
-          }
-          __syncwarp();
-          double* dst = a.jv + heat_jbase(a, k) + r0 * cnt;
-          const int total = nrows * cnt;
-          for (int i = lane; i < total; i += 32) dst[i] = sJw[i];
-          __syncwarp();
-        }
-        if (WJ && own) {  // boundary rows X_{0,k} (and X_{N,k}): one constant entry each
-          if (j == 0) a.jv[k] = 1.0;
-          if (a.has_final && j == a.N) a.jv[n + k] = 1.0;
-        }
+        if (WJ) heat_jrows(a, k, LAST, t, lane, act, nrows, r0, x2, sJw);
+        if (WJ && own) heat_jbound(a, k, j);
         if (WC) {
           // hh f_k = hh (lap / dx^2 - x^3)
           // pa = x + hh f, pb = x - hh f, with hh f = hh/dx^2 lap - hh x^3
-          const double lap = last ? hsub(a, xl, xk) : fma(-2.0, xk, hadd(a, xl, xr));
+          const double lap = LAST ? hsub(a, xl, xk) : fma(-2.0, xk, hadd(a, xl, xr));
           const double x3 = hmul(a, x2, xk);
           const double pa = fma(a.hidx2, lap, fma(a.mhh, x3, xk));
           const double pb = fma(-a.hidx2, lap, fma(a.hh, x3, xk));
@@ -177,17 +204,28 @@ __global__ void __launch_bounds__(HT_THREADS) k_heat_eval(const __grid_constant_
           if (own && j == 0) a.c[k] = xk;
           if (own && a.has_final && j == a.N) a.c[n + k] = xk;
         }
-        if (own && WH) {
-          const double yl = (j >= 1) ? __ldg(a.y + a.nb + (int64_t)k * a.N + j - 1) : 0.0;
-          const double yr = (j < a.N) ? __ldg(a.y + a.nb + (int64_t)k * a.N + j) : 0.0;
-          const double ty = hmul(a, a.h6, hadd(a, yl, yr));
-          sN[t * ld + k] = fma(ty, xk, endp ? a.cq_end[k] : a.cq_in[k]);
-        }
-        if (own && (WG || WF)) {
-          const double d = a.has_ref ? hsub(a, xk, a.ref[k]) : xk;
-          const double gk = hmul(a, endp ? a.gq_end[k] : a.gq_in[k], d);
-          if (WF) objacc = fma(gk, d, objacc);
-          if (WG) a.g[(int64_t)n * j + k] = gk;
+        if (own && WH) sN[t * ld + k] = heat_hdiag(a, k, j, endp, xk);
+        if (own && (WG || WF)) heat_grad(a, k, j, endp, xk, WG, WF, objacc);
+      };
+      for (int gi = warp; gi < ngroups; gi += HT_WARPS) {
+        const int k0 = gi * 8, k1 = min(k0 + 8, n);
+        const int kin = min(k1, n - 1);  // interior cells of the group: k0 .. kin-1
+#pragma unroll 1
+        for (int k = k0; k < kin; ++k) cell(k, std::false_type{});
+        if (k1 == n) cell(n - 1, std::true_type{});
+      }
+    } else {
+      // without the constraints one loop body for every cell (smaller and measured faster)
+      for (int gi = warp; gi < ngroups; gi += HT_WARPS) {
+        const int k0 = gi * 8, k1 = min(k0 + 8, n);
+        for (int k = k0; k < k1; ++k) {
+          const bool last = (k == n - 1);
+          double xk = 0.0;
+          if (act) xk = sX[t * ld + k];
+          if (WJ) heat_jrows(a, k, last, t, lane, act, nrows, r0, hmul(a, xk, xk), sJw);
+          if (WJ && own) heat_jbound(a, k, j);
+          if (own && WH) sN[t * ld + k] = heat_hdiag(a, k, j, endp, xk);
+          if (own && (WG || WF)) heat_grad(a, k, j, endp, xk, WG, WF, objacc);
         }
       }
     }
