@@ -90,8 +90,8 @@ FP64_OPS_PER_NODE = {("vdp", "eval_all"): 26.6, ("vdp", "jh"): 10.0, ("vdp", "jp
                      ("vdp:euler", "eval_all"): 21.5, ("vdp:euler", "jh"): 8.0, ("vdp:euler", "jprod"): 11.0,
                      ("vdp:euler", "jtprod"): 10.0, ("vdp:euler", "hprod"): 10.0, ("vdp:euler", "step"): 41.5,
                      # heat, 64 cells: the step is its four kernels in sequence
-                     ("heat64", "eval_all"): 1257.3, ("heat64", "jh"): 390.4, ("heat64", "jprod"): 523.4,
-                     ("heat64", "jtprod"): 463.0, ("heat64", "hprod"): 257.0, ("heat64", "step"): 2500.7}
+                     ("heat64", "eval_all"): 1121.6, ("heat64", "jh"): 390.4, ("heat64", "jprod"): 523.4,
+                     ("heat64", "jtprod"): 463.0, ("heat64", "hprod"): 257.0, ("heat64", "step"): 2365.0}
 
 # Rows of the paper's workloads beyond the headline problem (and the cart-pole at the
 # headline horizon), measured the same way (fused step with an L2 flush between steps) and
