@@ -155,10 +155,8 @@ class OCP:
             _check(L.ocp_set_boundary(h, arr(x0), arr(xf)), h)
         if scheme != "trapezoid":
             _check(L.ocp_set_scheme(h, {"trapezoid": 0, "euler": 1}[scheme]), h)
-        if path:  # rows sum_v [a (z_v - b)^2 + l z_v] - r <= 0
-            flat = lambda rows: [float(v) for row in rows for v in row]
-            _check(L.ocp_set_path_constraints(h, len(path["r"]), arr(flat(path["a"])), arr(flat(path["b"])),
-                                              arr(flat(path["l"])), arr(path["r"])), h)
+        if path:
+            self.set_path_constraints(path, _dims=False)
         if bineq:  # rows sum_v [a (z_v - b)^2 + l z_v] - r <= 0 over z = (X_0, X_N)
             flat = lambda rows: [float(v) for row in rows for v in row]
             _check(L.ocp_set_boundary_inequalities(h, len(bineq["r"]), arr(flat(bineq["a"])), arr(flat(bineq["b"])),
@@ -181,6 +179,24 @@ class OCP:
         _check(L.ocp_dims(h, C.byref(n), C.byref(m), C.byref(nj), C.byref(nh)), h)
         self.n, self.m, self.nnzj, self.nnzh = n.value, m.value, nj.value, nh.value
         self.device = torch.device("cuda", torch.cuda.current_device())
+
+    def set_path_constraints(self, path, _dims=True):
+        """ocp_set_path_constraints: rows sum_v [a (z_v - b)^2 + l z_v] - r <= 0 at every node
+        (path = dict of a, b, l: one list per row over z = (X_i, U_i); r: one value per row)."""
+        keep = []
+
+        def arr(v):
+            a = (C.c_double * len(v))(*[float(e) for e in v])
+            keep.append(a)
+            return C.cast(a, C.c_void_p)
+
+        flat = lambda rows: [float(v) for row in rows for v in row]
+        _check(lib().ocp_set_path_constraints(self.h, len(path["r"]), arr(flat(path["a"])), arr(flat(path["b"])),
+                                              arr(flat(path["l"])), arr(path["r"])), self.h)
+        if _dims:
+            n, m, nj, nh = _I64(), _I64(), _I64(), _I64()
+            _check(lib().ocp_dims(self.h, C.byref(n), C.byref(m), C.byref(nj), C.byref(nh)), self.h)
+            self.n, self.m, self.nnzj, self.nnzh = n.value, m.value, nj.value, nh.value
 
     @classmethod
     def from_workload(cls, w: dict) -> "OCP":

@@ -433,6 +433,49 @@ def test_host_step_async_back_to_back(ocp, name, N):
     H.close()
 
 
+def test_host_step_async_then_resize(ocp):
+    """Asynchronous host steps, then path rows added to the same handle (m and the nonzero
+    counts grow: the device copies are reallocated once the earlier copies are over), then more
+    asynchronous steps: every output matches the device step of a handle built that way."""
+    w, wp = named("vdp_n1e3", 400), named("vdp_n1e3+path", 400)
+    H = ocp.OCP.from_workload(w)
+    H0, Hp = ocp.OCP.from_workload(w), ocp.OCP.from_workload(wp)
+    pin = lambda d: [torch.from_numpy(d[k]).pin_memory() for k in ("x", "y", "vn", "vm")]
+    d1, d2 = pin(synth.draw(w, seed=31)), pin(synth.draw(wp, seed=32))
+    got1 = H.eval_step_host(d1[0], d1[1], 0.8, d1[2], d1[3], wait=False)
+    H.set_path_constraints(wp["path"])
+    assert (H.n, H.m, H.nnzj, H.nnzh) == (Hp.n, Hp.m, Hp.nnzj, Hp.nnzh) and H.m > H0.m
+    got2 = H.eval_step_host(d2[0], d2[1], 0.8, d2[2], d2[3], wait=False)
+    H.host_step_wait()
+    torch.cuda.synchronize()
+    for Href, hi, got in ((H0, d1, got1), (Hp, d2, got2)):
+        ref = Href.eval_step(*(t.cuda() for t in hi[:2]), 0.8, *(t.cuda() for t in hi[2:]))
+        torch.cuda.synchronize()
+        for a, b in zip(got, ref):
+            assert torch.equal(a, b.cpu())
+    for h in (H, H0, Hp):
+        h.close()
+
+
+def test_host_step_async_then_destroy(ocp):
+    """ocp_destroy right after asynchronous host steps waits for their copies: the host outputs
+    are complete afterwards, with no wait or synchronize in between."""
+    w = named("cartpole_n1e5", 3000)
+    H = ocp.OCP.from_workload(w)
+    hins = [[torch.from_numpy(synth.draw(w, seed=40 + i)[k]).pin_memory() for k in ("x", "y", "vn", "vm")]
+            for i in range(2)]
+    outs = [H.eval_step_host(hi[0], hi[1], 1.1, hi[2], hi[3], wait=False) for hi in hins]
+    H.close()
+    snap = [[t.clone() for t in o] for o in outs]
+    Hr = ocp.OCP.from_workload(w)
+    for hi, got in zip(hins, snap):
+        ref = Hr.eval_step(*(t.cuda() for t in hi[:2]), 1.1, *(t.cuda() for t in hi[2:]))
+        torch.cuda.synchronize()
+        for a, b in zip(got, ref):
+            assert torch.equal(a, b.cpu())
+    Hr.close()
+
+
 def test_host_step_wait_without_calls(ocp):
     """ocp_host_step_wait on a handle that never ran a host step has nothing to wait for."""
     H = ocp.OCP.from_workload(named("dint", 10))
