@@ -90,3 +90,56 @@ def test_null_handle_is_rejected(lib):
     lib.ocp_host_step_wait.restype = C.c_int
     lib.ocp_host_step_wait.argtypes = [C.c_void_p] * 2
     assert lib.ocp_host_step_wait(None, None) == 1
+
+
+def declared_signatures():
+    """name -> list of parameter kinds ("ptr", "double", "int64", "int") from include/*.h"""
+    sigs = {}
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not fn.endswith(".h"):
+            continue
+        text = open(os.path.join(ROOT, "include", fn)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s+\**([a-z_][a-z0-9_]*)\s*\(([^)]*)\)\s*;",
+                             text, re.M):
+            params = [p.strip() for p in m.group(2).split(",") if p.strip() and p.strip() != "void"]
+            kinds = []
+            for p in params:
+                if "*" in p:
+                    kinds.append("ptr")
+                elif re.search(r"\bdouble\b", p):
+                    kinds.append("double")
+                elif re.search(r"\bint64_t\b", p):
+                    kinds.append("int64")
+                else:
+                    kinds.append("int")
+            sigs[m.group(1)] = kinds
+    return sigs
+
+
+def _kind(t):
+    if t in (C.c_void_p,) or (isinstance(t, type) and issubclass(t, C._Pointer)):
+        return "ptr"
+    if t is C.c_double:
+        return "double"
+    if t is C.c_int64:
+        return "int64"
+    if t in (C.c_int, C.c_int32):
+        return "int"
+    return "?"
+
+
+def test_binding_argument_lists_match_the_header():
+    """Every ctypes argument list of the Python binding has the arity and the argument kinds
+    (pointer, double, int64, int) of the C declaration it binds."""
+    from paper_2510_03932_gb300 import ocp as O
+
+    decl = declared_signatures()
+    tables = dict(O._SIGS)
+    tables.update(O._BATCH_SIGS)
+    checked = 0
+    for name, argt in tables.items():
+        assert name in decl, name
+        assert [_kind(t) for t in argt] == decl[name], (name, [_kind(t) for t in argt], decl[name])
+        checked += 1
+    assert checked >= 40
