@@ -17,7 +17,9 @@
  *     row  nb + k*N + j    : (X_{j+1,k} - X_{j,k}) - h/2 (f_k(z_j) + f_k(z_{j+1})),  z_j = (X_j, U_j)
  *     then the path inequalities, if any (ocp_set_path_constraints)
  *     then the boundary inequalities, if any (ocp_set_boundary_inequalities)
- * Objective (Sec. 5 trapezoidal cost): F = sum_j w_j f0(z_j), w_0 = w_N = h/2, else w_j = h.
+ * Objective (Sec. 5 trapezoidal cost): F = sum_j w_j f0(z_j), w_0 = w_N = h/2, else w_j = h,
+ *   plus the terminal cost (ocp_set_terminal_cost) and the boundary cost g(X_0, X_N)
+ *   (ocp_set_boundary_cost), if set.
  * Lagrangian Hessian: H = sigma * Hess F + sum_r y_r Hess c_r (lower triangle stored).
  * Sparse matrices are COO, 0-based, one entry per structural nonzero (a derivative that is
  * not identically zero, whatever its value at x, y, sigma), sorted by (row, col).
