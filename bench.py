@@ -481,10 +481,12 @@ def run_widened(name, steps, warmup):
     # device-side spin before each call (no memory traffic) keeps the GPU busy while the host
     # enqueues the events and the call, as the flush does in the timing above.
     hot = {}
+    spin = getattr(torch.cuda, "_sleep", None)   # without it the hot times include launch gaps
     for nm in ("step", "jh"):
         evs = []
         for _ in range(max(3, steps // 4)):
-            torch.cuda._sleep(100000)
+            if spin is not None:
+                spin(100000)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             calls[nm]()
