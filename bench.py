@@ -78,7 +78,9 @@ def _counts(w):
 # ncu's sm__sass_thread_inst_executed_op_{dfma,dadd,dmul}_pred_on counts divided by N+1 (the
 # objective's tile reduction is part of them).  The cart-pole's include a sincos and a division, the quadrotor's three sincos calls and
 # 1/cos x8, the Goddard's exp and two divisions.  Measured at N = 1e5 (cart-pole, quadrotor,
-# Goddard) and 1e6 (Van der Pol).
+# Goddard) and 1e6 (Van der Pol).  Each model's counts hold for the kernel sources whose tag
+# (kernel_source_tag) is in FP64_OPS_SRC; when the sources change the counts are stale and the
+# bench reports no FP64 fraction for that model until they are measured again.
 FP64_OPS_PER_NODE = {("vdp", "eval_all"): 26.6, ("vdp", "jh"): 10.0, ("vdp", "jprod"): 13.0,
                      ("vdp", "jtprod"): 12.0, ("vdp", "hprod"): 11.0, ("vdp", "step"): 50.6,
                      ("cartpole", "eval_all"): 127.9, ("cartpole", "jh"): 103.8, ("cartpole", "jprod"): 81.6,
@@ -92,6 +94,41 @@ FP64_OPS_PER_NODE = {("vdp", "eval_all"): 26.6, ("vdp", "jh"): 10.0, ("vdp", "jp
                      # heat, 64 cells: the step is its four kernels in sequence
                      ("heat64", "eval_all"): 1121.6, ("heat64", "jh"): 390.4, ("heat64", "jprod"): 523.4,
                      ("heat64", "jtprod"): 463.0, ("heat64", "hprod"): 257.0, ("heat64", "step"): 2365.0}
+
+# The kernel sources of each model key (paths under the package's csrc/): the tile body and
+# the helpers it includes, the model's device functor, the translation unit that instantiates
+# its kernels.
+_COMMON = ["node_kernels.cuh", "model_base.cuh", "ocp_internal.h"]
+KERNEL_SOURCES = {
+    "vdp": _COMMON + ["model_vdp.cuh", "node_vdp.cu"],
+    "vdp:euler": _COMMON + ["model_vdp.cuh", "node_vdp.cu"],
+    "cartpole": _COMMON + ["model_cartpole.cuh", "node_cartpole.cu"],
+    "quadrotor": _COMMON + ["model_quad.cuh", "node_quad.cu"],
+    "goddard": _COMMON + ["goddard_kernels.cu"],
+    "heat64": _COMMON + ["heat_kernels.cu"],
+}
+# Tags of the sources the FP64_OPS_PER_NODE counts (and TRAFFIC) were measured on.
+FP64_OPS_SRC = {"vdp": "ebe15e385cf4", "vdp:euler": "ebe15e385cf4", "cartpole": "47619928cb1c",
+                "quadrotor": "685b21a7bc91", "goddard": "8b0d5888e3fd", "heat64": "046250673feb"}
+
+
+def kernel_source_tag(key):
+    """First 12 hex digits of the SHA-256 of the model's kernel sources (KERNEL_SOURCES)."""
+    import hashlib
+    hsh = hashlib.sha256()
+    for rel in KERNEL_SOURCES[key]:
+        with open(os.path.join(ROOT, "paper_2510_03932_gb300", "csrc", rel), "rb") as fh:
+            hsh.update(rel.encode() + b"\0" + fh.read() + b"\0")
+    return hsh.hexdigest()[:12]
+
+
+def fp64_ops(key, kern):
+    """The measured FP64 instructions per node of this kernel, or None when the model's
+    kernel sources changed since the measurement (or it was never measured)."""
+    if key not in FP64_OPS_SRC or kernel_source_tag(key) != FP64_OPS_SRC[key]:
+        return None
+    return FP64_OPS_PER_NODE.get((key, kern))
+
 
 # Rows of the paper's workloads beyond the headline problem (and the cart-pole at the
 # headline horizon), measured the same way (fused step with an L2 flush between steps) and
@@ -118,13 +155,23 @@ def named_workload(name):
     return w
 
 
-# DRAM bytes (read + write) of one launch of the fused step at the bench workload, from an ncu
-# capture of the same kernel version (dram__bytes_read.sum + dram__bytes_write.sum; writes
-# still dirty in L2 when the kernel ends are not counted).  Remove an entry when its kernel
-# changes.
-TRAFFIC = {("vdp_mu_n1e6", "step"): 227.90e6}
-FP64_INST_PER_CLK_PER_SM = 2.0   # measured: DFMA throughput of one SM (DADD/DMUL are ~15% slower)
+# DRAM bytes (read + write) of one launch at a workload, from an ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum; writes still dirty in L2 when the kernel ends
+# are not counted), with the source tag of the kernel it was captured on (see traffic()).
+TRAFFIC = {("vdp_mu_n1e6", "step"): (227.90e6, "ebe15e385cf4")}
+# Each SM's FP64 pipe completes 2 FP64 instructions (one lane each) per clock: the recipe's
+# nominal 1.25 TFLOP/s FP64 of GB300 is 6.25e11 FMA/s = 1.99 per clock per SM at 152 SMs and
+# 2070 MHz.  bench.py measures the rate live (measure_fp64_rate) and reports it beside the peak.
+FP64_INST_PER_CLK_PER_SM = 2.0
 NUM_SMS = 152
+
+
+def traffic(name, kern, key):
+    """Measured DRAM bytes of one launch, or None once the kernel's sources have changed."""
+    v = TRAFFIC.get((name, kern))
+    if v is None or kernel_source_tag(key) != v[1]:
+        return None
+    return v[0]
 
 
 def peaks():
@@ -186,6 +233,56 @@ class ClockSampler:
         os.unlink(self.path)
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def bench_config(name, w, n, m, nnzj, nnzh, world):
+    """The `config` object of the JSON line (the same keys for both arms)."""
+    return dict(workload=name, model=w["model"], N=w["N"], n=n, m=m, nnz_jac=nnzj, nnz_hess=nnzh,
+                step="one pass of the hot path: F, c, grad, J, H, Jv, J^T w, Hv",
+                l2="inputs and outputs (296 MB at the default workload) exceed the L2; flushed between steps",
+                parallelism="replicas" if world > 1 else "single")
+
+
+def measure_fp64_rate(dev, nsm, seconds=0.25):
+    """FP64 instructions per clock per SM of DFMA, DADD and DMUL, from the library's throughput
+    probe (ocp_probe_fp64): 8 CTAs of 256 threads per SM, each launch about `seconds` long,
+    timed with CUDA events on the launching stream, with the SM clock sampled meanwhile."""
+    import torch
+    from paper_2510_03932_gb300 import ocp
+
+    blocks, threads = 8 * nsm, 256
+    out = torch.zeros(blocks * threads, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ocp.probe_fp64(0, blocks, threads, 256, out, stream)   # warm-up
+    torch.cuda.synchronize(dev)
+    # size the launches from a short one: about `seconds` each at the rate it shows
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    nops = ocp.probe_fp64(0, blocks, threads, 4096, out, stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    rate = nops / (e0.elapsed_time(e1) * 1e-3)
+    iters = int(max(1024, min(1 << 24, rate * seconds / (blocks * threads * 8))))
+    sampler = ClockSampler(dev.index)
+    sampler.start()
+    res = {}
+    for op, name in ((0, "dfma"), (1, "dadd"), (2, "dmul")):
+        ms = []
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            nops = ocp.probe_fp64(op, blocks, threads, iters, out, stream)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms.append(e0.elapsed_time(e1))
+        res[name] = nops / (float(np.median(ms)) * 1e-3)
+    clocks = sampler.stop()
+    clk = clocks.get("sm_mhz") or 2070.0
+    per = {k: v / (clk * 1e6 * nsm) for k, v in res.items()}
+    return dict(kernel="ocp_probe_fp64 (8 independent chains per thread, %d x %d threads, %d iterations)"
+                       % (blocks, threads, iters),
+                dfma_per_clk_per_sm=per["dfma"], dadd_per_clk_per_sm=per["dadd"], dmul_per_clk_per_sm=per["dmul"],
+                dfma_G_per_s=res["dfma"] / 1e9, sm_mhz=clk, clocks=clocks)
 
 
 def run_ours(args, rank, world):
@@ -394,31 +491,40 @@ def run_ours(args, rank, world):
     ab = algorithmic_bytes(w, "step")
     achieved = ab / (step_mean * 1e-3) / 1e9
     clk = (clocks or {}).get("sm_mhz") or 2070.0
-    fp64_peak = FP64_INST_PER_CLK_PER_SM * NUM_SMS * clk * 1e6 / 1e9   # G FP64 inst/s
-    ops = FP64_OPS_PER_NODE.get((ops_model(w), "step"))
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp64_peak = FP64_INST_PER_CLK_PER_SM * nsm * clk * 1e6 / 1e9   # G FP64 inst/s
+    key = ops_model(w)
+    ops = fp64_ops(key, "step")
     fp64_ach = ops * (w["N"] + 1) / (step_mean * 1e-3) / 1e9 if ops else None
+    probe = measure_fp64_rate(dev, nsm)
+    jh_bytes = algorithmic_bytes(w, "jh")
+    jh_gbps = jh_bytes / (jh_ms * 1e-3) / 1e9
     res = dict(
         metric=METRIC, value=nnz * args.steps * world / (tot_ms * 1e-3), unit="nnz/s", n_gpus=world,
         steps=args.steps, warmup=args.warmup, ms_per_step=tot_ms / args.steps, higher_is_better=True,
         scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
-        config=dict(workload=args.workload, model=w["model"], N=w["N"], n=n, m=m, nnz_jac=nnzj, nnz_hess=nnzh,
-                    step="ocp_eval_step: F, c, grad, J, H, Jv, J^T w, Hv in one pass",
-                    l2="flushed between steps (512 MB write)",
-                    parallelism="replicas" if world > 1 else "single"),
+        config=bench_config(args.workload, w, n, m, nnzj, nnzh, world),
         roofline=dict(bound="alu", achieved=fp64_ach, peak=fp64_peak, unit="G FP64 inst/s",
-                      frac=(fp64_ach / fp64_peak) if fp64_ach else None, traffic=TRAFFIC.get((w["name"], "step")),
+                      frac=(fp64_ach / fp64_peak) if fp64_ach else None,
+                      traffic=traffic(w["name"], "step", key),
                       kernel="k_node_eval<step> (fused step: F, c, grad, J, H, Jv, J^T w, Hv)",
-                      fp64_inst_per_node=ops,
-                      peak_basis="%.0f FP64 inst/clk/SM x %d SMs x %.0f MHz (median SM clock under load)"
-                                 % (FP64_INST_PER_CLK_PER_SM, NUM_SMS, clk)),
+                      fp64_inst_per_node=ops, fp64_counts_source_tag=kernel_source_tag(key),
+                      fp64_counts_current=ops is not None,
+                      peak_basis="%.0f FP64 inst/clk/SM (GB300's nominal 1.25 TFLOP/s FP64) x %d SMs x %.0f MHz "
+                                 "(median SM clock under load)" % (FP64_INST_PER_CLK_PER_SM, nsm, clk),
+                      peak_probe=probe,
+                      # the Jacobian + Hessian values alone (one launch), against the HBM roofline
+                      jac_hess=dict(bound="hbm", ms=jh_ms, nnz_per_s=nnz / (jh_ms * 1e-3), achieved=jh_gbps,
+                                    peak=hbm, unit="GB/s", frac=jh_gbps / hbm, algorithmic_bytes=jh_bytes,
+                                    peak_source=peak_kind, l2="flushed between calls (512 MB write)")),
         roofline_hbm=dict(bound="hbm", achieved=achieved, peak=hbm, unit="GB/s", frac=achieved / hbm,
                           peak_source=peak_kind, algorithmic_bytes=ab,
-                          traffic=TRAFFIC.get((w["name"], "step"))),
+                          traffic=traffic(w["name"], "step", key)),
         separate_calls_ms=float(kern_ms.sum()),
         kernels={nm: dict(ms=float(kern_ms[i]), GBps=algorithmic_bytes(w, nm) / (kern_ms[i] * 1e-3) / 1e9,
                           hbm_frac=algorithmic_bytes(w, nm) / (kern_ms[i] * 1e-3) / 1e9 / hbm,
-                          fp64_frac=(FP64_OPS_PER_NODE[(ops_model(w), nm)] * (w["N"] + 1) / (kern_ms[i] * 1e-3) / 1e9
-                                     / fp64_peak) if (ops_model(w), nm) in FP64_OPS_PER_NODE else None)
+                          fp64_frac=(fp64_ops(key, nm) * (w["N"] + 1) / (kern_ms[i] * 1e-3) / 1e9
+                                     / fp64_peak) if fp64_ops(key, nm) else None)
                  for i, nm in enumerate(names)},
         jac_hess_only=dict(ms=jh_ms, nnz_per_s=nnz / (jh_ms * 1e-3),
                            GBps=algorithmic_bytes(w, "jh") / (jh_ms * 1e-3) / 1e9,
@@ -505,7 +611,7 @@ def run_widened(name, steps, warmup):
                hot=dict(hot, note="no L2 flush between calls"))
     for nm in ("step", "eval_all", "jh", "jprod", "jtprod", "hprod"):
         ab = algorithmic_bytes(w, nm)
-        ops = FP64_OPS_PER_NODE.get((ops_model(w), nm))
+        ops = fp64_ops(ops_model(w), nm)
         out["kernels"][nm] = dict(
             ms=ms[nm], hbm_frac=ab / (ms[nm] * 1e-3) / 1e9 / hbm,
             fp64_frac=(ops * (w["N"] + 1) / (ms[nm] * 1e-3) / 1e9 / fp64_peak) if ops else None)
@@ -749,10 +855,7 @@ def main():
                               # the time one step of the whole workload takes at the sampled rate
                               ms_per_step=nnz / v * 1e3, higher_is_better=True, scaling="weak", vs_baseline=None,
                               impl="reference", dtype="f64", data="synthetic",
-                              config=dict(workload=args.workload, model=w["model"], N=w["N"], n=P.n, m=P.m,
-                                          nnz_jac=P.nnzj, nnz_hess=P.nnzh,
-                                          step="the oracle's full step: F, c, grad, J, H, Jv, J^T w, Hv",
-                                          parallelism="host cores"),
+                              config=bench_config(args.workload, w, P.n, P.m, P.nnzj, P.nnzh, 1),
                               cpu_baseline=cb, e2e=dict(value=v, unit="nnz/s", h2d_bytes_per_step=0,
                                                         d2h_bytes_per_step=0))))
         return

@@ -1,0 +1,34 @@
+/*
+ * ocp_probe.h — measurement helper of the evaluator library (not part of the paper's method).
+ *
+ * The evaluation kernels of ocp.h are bound by the GPU's FP64 pipe, so their roofline is an
+ * FP64 instruction rate.  This call runs a throughput kernel of one FP64 operation kind so that
+ * a benchmark can measure that rate on the GPU it runs on, at the clocks of the same run,
+ * instead of quoting a data-sheet figure.
+ */
+#ifndef OCP_GB300_PROBE_H
+#define OCP_GB300_PROBE_H
+
+#include <stdint.h>
+
+#include "ocp.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* FP64 throughput probe.  op: 0 = fused multiply-add (DFMA), 1 = add (DADD), 2 = multiply
+ * (DMUL).  Launches `blocks` CTAs of `threads` threads (threads a multiple of 32, at most
+ * 1024); each thread runs 8 independent dependency chains of `iters` operations of that kind,
+ * so one launch executes blocks * threads * 8 * iters FP64 operations (plus 7 adds per thread
+ * that combine the chains).  Each thread writes one double to `out` (device, at least
+ * blocks * threads doubles; the values are meaningless).  The call
+ * is asynchronous on `stream`; the caller times it (e.g. with CUDA events on that stream).
+ * Errors: OCP_EINVAL for a bad op, size or pointer; OCP_ECUDA for a failed launch, with
+ * ocp_last_error(NULL). */
+ocp_status ocp_probe_fp64(int op, int blocks, int threads, int iters, double* out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OCP_GB300_PROBE_H */

@@ -23,6 +23,8 @@
 #include <cstring>
 #include <vector>
 
+#include "model_cartpole.cuh"
+#include "model_vdp.cuh"
 #include "node_kernels.cuh"
 #include "ocp_internal.h"
 

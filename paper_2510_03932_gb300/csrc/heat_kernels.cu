@@ -431,6 +431,7 @@ static ocp_status heat_eval_t(ocp* h, const EvalCall& c, cudaStream_t s) {
   const int64_t nodes = c.E - c.B;
   a.ntiles = (nodes + (HT_LANES - 2)) / (HT_LANES - 1);
   if (a.ntiles < 1) a.ntiles = 1;
+  if (a.ntiles > h->max_partials) return set_err(h, OCP_EDIM, "too many tiles for the reduction scratch");
   const int ld = h->nx + 1;
   const size_t smem = sizeof(double) * ((size_t)heat_xlen(h->nx) + ((OUT & O_H) ? (HT_LANES - 1) * ld : 0) +
                                         ((OUT & O_J) ? HT_WARPS * (HT_LANES - 1) * 6 : 0));

@@ -1,0 +1,144 @@
+// Device model of the cart-pole dynamics (the conventions of every model are stated in
+// model_base.cuh).
+#pragma once
+#include "model_base.cuh"
+
+namespace ocpg {
+
+// ------------------------------------------------------------------------------------
+// Cart-pole, point-mass pole, theta from the downward vertical.  z = (p, pd, th, w, F).
+//   D = mc + mp s^2,  A = F + mp s (l w^2 + g c),  B = -F c - s (mp l w^2 c + (mc+mp) g)
+//   pdd = A / D,  thdd = B / (l D)
+// Derivatives from  pdd D = A  and  thdd (l D) = B  differentiated in place (D depends on th
+// only; D' = 2 mp s c, D'' = 2 mp (c^2 - s^2)):
+//   pdd_t  = (A_t - pdd D') / D            A_t  = mp (l w^2 c + g (c^2 - s^2))
+//   pdd_w  = A_w / D                       A_w  = 2 mp l w s
+//   pdd_F  = 1 / D
+//   pdd_tt = (A_tt - 2 pdd_t D' - pdd D'') / D     A_tt = -mp s (l w^2 + 4 g c)
+//   pdd_tw = (A_tw - pdd_w D') / D                 A_tw = 2 mp l w c
+//   pdd_ww = 2 mp l s / D,   pdd_tF = -pdd_F D' / D
+//   thdd_t  = (B_t / l - thdd D') / D      B_t = F s - mp l w^2 (c^2 - s^2) - (mc+mp) g c
+//   thdd_w  = B_w / (l D)                  B_w = -2 mp l w c s
+//   thdd_F  = -c / (l D)
+//   thdd_tt = (B_tt / l - 2 thdd_t D' - thdd D'') / D   B_tt = F c + 4 mp l w^2 s c + (mc+mp) g s
+//   thdd_tw = (B_tw / l - thdd_w D') / D                B_tw = -2 mp l w (c^2 - s^2)
+//   thdd_ww = -2 mp c s / D,   thdd_tF = (s / l - thdd_F D') / D
+// Constants: c[0]=mc, c[1]=mp, c[2]=l, c[3]=g, c[4]=(mc+mp) g, c[5]=1/l, c[6]=mp l, c[7]=2 mp,
+//            c[8]=mp g, c[9]=2 mp l, c[10]=4 g.
+// ------------------------------------------------------------------------------------
+struct CartPole {
+  static constexpr int EVAL_MIN_CTAS = 0;
+  static constexpr int NX = 4, NU = 1, NZ = 5;
+  static constexpr int MAXRX = 3, MAXRU = 1;
+  OCP_TABLE1(RX, int, NX, {2, 3, 2, 2})
+  OCP_TABLE1(RU, int, NX, {0, 1, 0, 1})
+  OCP_TABLE2(XV, int, NX, MAXRX, {{0, 1, -1}, {1, 2, 3}, {2, 3, -1}, {2, 3, -1}})
+  OCP_TABLE2(UV, int, NX, MAXRU, {{-1}, {0}, {-1}, {0}})
+  OCP_TABLE2(JZ, bool, NX, MAXRX, {{true, false, false}, {true, false, false}, {true, false, false},
+                                   {false, false, false}})
+  OCP_TABLE1(HK, bool, NX, {false, true, false, true})
+  static constexpr int NHD = 4;
+  OCP_TABLE1(HA, int, NHD, {2, 3, 3, 4})
+  OCP_TABLE1(HB, int, NHD, {2, 2, 3, 2})
+  static constexpr bool HAS_DPARAM = false;
+
+  static void host_consts(const double* p, double hh, ModelConst& mc) {
+    mc.hh = hh;
+    mc.mhh = -hh;
+    mc.one = 1.0;
+    mc.mz = -0.0;
+    const double m_c = p[0], m_p = p[1], l = p[2], g = p[3];
+    mc.c[0] = m_c; mc.c[1] = m_p; mc.c[2] = l; mc.c[3] = g;
+    mc.c[4] = (m_c + m_p) * g; mc.c[5] = 1.0 / l; mc.c[6] = m_p * l; mc.c[7] = 2.0 * m_p;
+    mc.c[8] = m_p * g; mc.c[9] = 2.0 * m_p * l; mc.c[10] = 4.0 * g;
+  }
+  __device__ __forceinline__ static void device_param(ModelConst&, double) {}
+
+  template <bool WC, bool WJ, bool WH>
+  __device__ __forceinline__ static void eval(const ModelConst& K, const double (&z)[NZ], const double (&yb)[NX],
+                                              const double (&cqd)[NZ], double (&pa)[NX], double (&pb)[NX],
+                                              double (&mjx)[NX][MAXRX], double (&mju)[NX][MAXRU],
+                                              double (&hd)[NHD]) {
+    const double mcm = K.c[0], mp = K.c[1], l = K.c[2], g = K.c[3], Mg = K.c[4], il = K.c[5];
+    const double mpl = K.c[6], mp2 = K.c[7], mpg = K.c[8], mpl2 = K.c[9], g4 = K.c[10];
+    const double hh = K.hh, mhh = K.mhh;
+    const double p = z[0], pd = z[1], th = z[2], w = z[3], F = z[4];
+    double s, c;
+    sincos(th, &s, &c);
+    const double ms = fmul(K, mp, s);
+    const double D = fma(ms, s, mcm);
+    const double iD = 1.0 / D;
+    const double iDl = fmul(K, iD, il);
+    const double w2 = fmul(K, w, w);
+    const double lw2 = fmul(K, l, w2);
+    const double A = fma(ms, fma(g, c, lw2), F);
+    const double pdd = fmul(K, A, iD);
+    const double mplw2 = fmul(K, mpl, w2);
+    const double B = fma(-s, fma(mplw2, c, Mg), fmul(K, -F, c));
+    const double thdd = fmul(K, B, iDl);
+    if (WC) {
+      pa[0] = fma(hh, pd, p);   pb[0] = fma(mhh, pd, p);
+      pa[1] = fma(hh, pdd, pd); pb[1] = fma(mhh, pdd, pd);
+      pa[2] = fma(hh, w, th);   pb[2] = fma(mhh, w, th);
+      pa[3] = fma(hh, thdd, w); pb[3] = fma(mhh, thdd, w);
+    }
+    if (WJ || WH) {
+      const double sc = fmul(K, s, c);
+      const double c2s2 = fma(c, c, fmul(K, -s, s));
+      const double Dp = fmul(K, mp2, sc);
+      const double A_t = fma(mplw2, c, fmul(K, mpg, c2s2));
+      const double pdd_t = fmul(K, fma(-pdd, Dp, A_t), iD);
+      const double lw = fmul(K, mpl2, w);          // 2 mp l w
+      const double A_w = fmul(K, lw, s);
+      const double B_t = fma(F, s, -fma(mplw2, c2s2, fmul(K, Mg, c)));
+      const double thdd_t = fmul(K, fma(B_t, il, fmul(K, -thdd, Dp)), iD);
+      const double B_w = fmul(K, -lw, sc);
+      const double thdd_w = fmul(K, B_w, iDl);
+      const double thdd_F = fmul(K, -c, iDl);
+      if (WJ) {
+        const double mhiD = fmul(K, mhh, iD);
+        mjx[0][0] = 0.0; mjx[0][1] = mhh; mjx[0][2] = 0.0;
+        mjx[1][0] = 0.0; mjx[1][1] = fmul(K, mhh, pdd_t); mjx[1][2] = fmul(K, mhiD, A_w);
+        mju[1][0] = mhiD;
+        mjx[2][0] = 0.0; mjx[2][1] = mhh; mjx[2][2] = 0.0;
+        mjx[3][0] = fmul(K, mhh, thdd_t); mjx[3][1] = fmul(K, mhh, thdd_w);
+        mju[3][0] = fmul(K, mhh, thdd_F);
+      }
+      if (WH) {
+        // Every second derivative above is (numerator) / D: the multipliers carry the 1/D,
+        // m1 = -hh ybar_1 / D and m3 = -hh ybar_3 / D, and the numerators are combined directly.
+        const double m1 = fmul(K, fmul(K, mhh, yb[1]), iD), m3 = fmul(K, fmul(K, mhh, yb[3]), iD);
+        const double pdd_w = fmul(K, A_w, iD);
+        const double Dpp = fmul(K, mp2, c2s2);
+        const double mDp2 = fmul(K, -2.0, Dp);
+        // A_tt = -mp s (l w^2 + 4 g c)
+        const double A_tt = fmul(K, -ms, fma(g4, c, lw2));
+        const double n_pdd_tt = fma(-pdd, Dpp, fma(pdd_t, mDp2, A_tt));
+        const double A_tw = fmul(K, lw, c);
+        const double n_pdd_tw = fma(-pdd_w, Dp, A_tw);
+        const double n_pdd_ww = fmul(K, mpl2, s);
+        const double n_pdd_tF = fmul(K, -Dp, iD);
+        // B_tt = F c + 4 mp l w^2 s c + (mc+mp) g s
+        const double B_tt = fma(F, c, fmul(K, s, fma(fmul(K, 4.0, mplw2), c, Mg)));
+        const double n_thdd_tt = fma(-thdd, Dpp, fma(thdd_t, mDp2, fmul(K, B_tt, il)));
+        const double B_tw = fmul(K, -lw, c2s2);
+        const double n_thdd_tw = fma(-thdd_w, Dp, fmul(K, B_tw, il));
+        const double n_thdd_ww = fmul(K, -mp2, sc);
+        const double n_thdd_tF = fma(-thdd_F, Dp, fmul(K, s, il));
+        hd[0] = fma(m1, n_pdd_tt, fma(m3, n_thdd_tt, cqd[2]));   // (th, th)
+        hd[1] = fma(m1, n_pdd_tw, fmul(K, m3, n_thdd_tw));       // (w, th)
+        hd[2] = fma(m1, n_pdd_ww, fma(m3, n_thdd_ww, cqd[3]));   // (w, w)
+        hd[3] = fma(m1, n_pdd_tF, fmul(K, m3, n_thdd_tF));       // (F, th)
+      }
+    }
+  }
+  __device__ __forceinline__ static void dparam(const ModelConst&, const double (&)[NZ], double (&mdp)[NX]) {
+    mdp[0] = mdp[1] = mdp[2] = mdp[3] = 0.0;
+  }
+  __device__ __forceinline__ static void dparam_grad(const ModelConst&, const double (&)[NZ], const double (&)[NX],
+                                                     double (&out)[NZ]) {
+    for (int v = 0; v < NZ; ++v) out[v] = 0.0;
+  }
+};
+
+}  // namespace ocpg

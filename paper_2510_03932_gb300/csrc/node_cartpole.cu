@@ -1,4 +1,5 @@
 // Instantiation of the node-model kernels for the CartPole model.
+#include "model_cartpole.cuh"
 #include "node_kernels.cuh"
 
 namespace ocpg {

@@ -1,4 +1,5 @@
 // Instantiation of the node-model kernels for the Dint model.
+#include "model_dint.cuh"
 #include "node_kernels.cuh"
 
 namespace ocpg {

@@ -23,7 +23,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "models.cuh"
+#include "model_base.cuh"
 #include "ocp_internal.h"
 
 namespace ocpg {

@@ -1,4 +1,5 @@
 // Instantiation of the node-model kernels for the quadrotor model.
+#include "model_quad.cuh"
 #include "node_kernels.cuh"
 
 namespace ocpg {

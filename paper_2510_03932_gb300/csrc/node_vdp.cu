@@ -1,4 +1,5 @@
 // Instantiation of the node-model kernels for the VdP model.
+#include "model_vdp.cuh"
 #include "node_kernels.cuh"
 
 namespace ocpg {

@@ -84,6 +84,7 @@ _SIGS = {
     "ocp_eval_grad_scaled": [_P, _P, _P, _P, _P],
     "ocp_obj_hvp": [_P, _P, _P, _P, _P, _P, _P],
     "ocp_eval_obj_noalloc": [C.POINTER(_Dyn), C.POINTER(_Cost), C.c_int, C.c_int, _I64, _D, _P, _P, _P],
+    "ocp_probe_fp64": [C.c_int, C.c_int, C.c_int, C.c_int, _P, _P],
     "ocp_last_error": [_P],
 }
 
@@ -106,6 +107,17 @@ def lib():
         L.ocp_last_error.restype = C.c_char_p
         _lib = L
     return _lib
+
+
+def probe_fp64(op, blocks, threads, iters, out, stream=None):
+    """Launch the FP64 throughput probe of include/ocp_probe.h (op 0 DFMA, 1 DADD, 2 DMUL) on
+    `stream`; `out` is a CUDA float64 tensor of at least blocks * threads elements.  Returns
+    the number of FP64 operations the launch executes."""
+    if out.dtype != torch.float64 or not out.is_cuda or out.numel() < blocks * threads:
+        raise ValueError("out must be a CUDA float64 tensor of at least blocks * threads elements")
+    _check(lib().ocp_probe_fp64(int(op), int(blocks), int(threads), int(iters), C.c_void_p(out.data_ptr()),
+                                _stream(stream)))
+    return blocks * threads * (8 * iters + 7)
 
 
 def _stream(stream):

@@ -39,6 +39,26 @@ def test_fp64_peak_from_unit_counts():
     assert bench.FP64_INST_PER_CLK_PER_SM * bench.NUM_SMS * 2070e6 / 1e9 == pytest.approx(629.28)
 
 
+def test_fp64_counts_are_tagged_with_the_kernel_sources_they_were_measured_on():
+    """Every measured FP64-instruction count and DRAM-traffic figure carries the tag of the
+    kernel sources it was measured on; a change to those sources without a new measurement
+    (and a new tag) fails here, so the bench can never divide by a stale count silently."""
+    for key, tag in bench.FP64_OPS_SRC.items():
+        assert bench.kernel_source_tag(key) == tag, (
+            "kernel sources of %r changed since its FP64 counts were measured: re-measure them "
+            "(profiles/fp64_ops_per_node.md) and update FP64_OPS_SRC" % key)
+    for (name, kern), (_, tag) in bench.TRAFFIC.items():
+        key = bench.ops_model(bench.named_workload(name))
+        assert bench.kernel_source_tag(key) == tag, (name, kern)
+
+
+def test_stale_counts_are_not_used(monkeypatch):
+    monkeypatch.setitem(bench.FP64_OPS_SRC, "vdp", "000000000000")
+    assert bench.fp64_ops("vdp", "step") is None
+    monkeypatch.setitem(bench.TRAFFIC, ("vdp_mu_n1e6", "step"), (1.0, "000000000000"))
+    assert bench.traffic("vdp_mu_n1e6", "step", "vdp") is None
+
+
 def test_fp64_table_covers_every_reported_workload():
     names = ["vdp_mu_n1e6"] + bench.WIDENED + bench.CONFIGS
     for name in names:
@@ -71,6 +91,10 @@ def test_reference_arm_prints_the_contract_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == dict(value=d["value"], unit="nnz/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0)
+    # the same config object as the GPU arm's line
+    w = bench.named_workload("vdp_n1e3")
+    P = O.Problem(w)
+    assert d["config"] == bench.bench_config("vdp_n1e3", w, P.n, P.m, P.nnzj, P.nnzh, 1)
 
 
 def test_reference_arm_other_ranks_exit_quietly():
