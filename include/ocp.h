@@ -386,7 +386,13 @@ ocp_status ocp_eval_all_range(ocp_t* h, int64_t node_begin, int64_t node_end, co
  * integrator, x 127 for the cart-pole, x 63 for the quadrotor, x 31 for the heat model; the
  * constant reference only) returns OCP_EDIM without
  * launching.  The first call on a device looks up the array's device address with that device
- * current; make that first call before any stream capture.  Every call on a device shares the
+ * current (and caches it for the life of the process); make that first call before any stream
+ * capture.  CUDA loads the library's kernels lazily by default, so the first call of each model
+ * on a device also makes the driver load them, which allocates device memory inside the
+ * driver: a caller that must not allocate after start-up makes one warm-up call per model and
+ * device at start-up (or sets CUDA_MODULE_LOADING=EAGER).  After cudaDeviceReset the cached
+ * address is stale: do not call this entry point in a process that has reset a device it used
+ * it on.  Every call on a device shares the
  * array and the last call's contents stay in it: calls that overlap on the GPU race.  Errors
  * as ocp_create and eval_obj, reported by ocp_last_error(NULL).  Calls neither cudaMalloc nor
  * cudaFree. */

@@ -11,6 +11,9 @@
 // process exits.  Every call on a device shares it, so calls that overlap on the GPU race
 // (issue them on one stream, or wait between them).  The array keeps the last call's
 // contents; the ticket that must start at zero is cleared by each call before its launch.
+// The array's device address is looked up once per device and cached for the life of the
+// process; it is stale after cudaDeviceReset, so the entry point is not for processes that
+// reset a device they used it on.
 #include <cstring>
 #include <mutex>
 

@@ -5,6 +5,9 @@ tests/parity.py (1e-12 relative + 1e-14 absolute, or 1e-12 of the oracle's runni
 magnitude for entries with cancellation).  Small horizons span several tiles and a ragged
 tail; the full-size workloads are compared entry by entry as well.
 """
+import json
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -262,8 +265,19 @@ def test_parity_cost_structure_follows_weights(ocp):
                                   "goddard_n1e5", "cartpole_n1e5:euler", "quadrotor_n1e5:euler",
                                   "quadrotor_n1e5+path", "cartpole_n1e5+bineq", "goddard_n1e5+path+bineq"])
 def test_parity_full_size_workloads(ocp, name):
+    """Every output of the full-size workloads through the gate.  Entries that pass only by the
+    cancellation clause (error within 1e-12 of the magnitude of the cancelling terms, not of the
+    value) are counted per output: they must stay rare, at most 1% of the output's entries, so
+    that a general loss of accuracy cannot hide behind the clause.  With OCP_PARITY_REPORT set,
+    the counts are appended to that file (one JSON line per workload)."""
     rep = full_check(ocp, named(name))
-    print(name, rep)
+    path = os.environ.get("OCP_PARITY_REPORT")
+    if path:
+        with open(path, "a") as fh:
+            fh.write(json.dumps(dict(workload=name, outputs=rep)) + "\n")
+    for out, r in rep.items():
+        assert r["fail"] == 0
+        assert r["cancellation"] <= 0.01 * r["n"], (name, out, r)
 
 
 @pytest.mark.parametrize("name", ["cartpole_n1e5", "goddard_n1e3", "cartpole_n1e5:euler", "vdp_n1e3+path+bineq",

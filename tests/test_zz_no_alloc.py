@@ -4,8 +4,12 @@ Such callers (a real-time control loop that must not allocate after start-up, a 
 whose allocator owns all device memory) get the objective from a file-scope device scratch
 array instead of handle-owned scratch.  This test calls that entry point through the C-ABI
 twice in a row, on two different inputs, and compares each result with the handle-based
-eval_obj within the parity tolerance; it also checks that a horizon too large for the
-static array is refused before any launch.  It is collected last so that a run stopping at
+eval_obj within the parity tolerance, for every model the entry point serves (Van der Pol,
+cart-pole, heat, double integrator, quadrotor: tiles of 256, 128, 32 and 64 nodes).  After a
+warm-up call (the first call on a device loads the library's kernels and looks up the
+array's address) it checks that the device's free memory is the same before and after two
+more calls, i.e. that the entry point allocates nothing.  It also checks that a horizon too
+large for the static array is refused before any launch.  It is collected last so that a run stopping at
 the first failure has run every other test first.
 """
 import ctypes as C
@@ -39,13 +43,23 @@ def _desc(ocp, w, keep):
     return dyn, cost
 
 
-@pytest.mark.parametrize("name,N", [("vdp_n1e3", 1000), ("cartpole_n1e5", 5000), ("heat_n2e4", 300)])
+CASES = [("vdp_n1e3", 1000), ("cartpole_n1e5", 5000), ("heat_n2e4", 300), ("dint", 700),
+         ("quadrotor_n1e3", 3000)]
+
+
+def _plain(w):
+    """The workload with a constant state reference (the entry point takes the cost weights and
+    the constant reference of ocp_create only)."""
+    return dict(w, xslope=None, xamp=None, xfreq=None)
+
+
+@pytest.mark.parametrize("name,N", CASES)
 def test_noalloc_objective_matches_eval_obj_twice(name, N):
     if not torch.cuda.is_available():
         pytest.skip("needs a GPU")
     from paper_2510_03932_gb300 import ocp
     fn = _entry(ocp)
-    w = synth.with_horizon(synth.workload(name), N)
+    w = _plain(synth.with_horizon(synth.workload(name), N))
     H = ocp.OCP.from_workload(w)
     keep = []
     dyn, cost = _desc(ocp, w, keep)
@@ -63,6 +77,30 @@ def test_noalloc_objective_matches_eval_obj_twice(name, N):
     for g, r in zip(got, refs):
         assert abs(g - r) <= 1e-12 * abs(r) + 1e-14, (g, r)
     H.close()
+
+
+@pytest.mark.parametrize("name,N", CASES)
+def test_noalloc_calls_leave_device_memory_unchanged(name, N):
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2510_03932_gb300 import ocp
+    fn = _entry(ocp)
+    w = _plain(synth.with_horizon(synth.workload(name), N))
+    keep = []
+    dyn, cost = _desc(ocp, w, keep)
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    x = torch.from_numpy(synth.draw(w)["x"]).cuda()
+    f = torch.zeros(2, dtype=torch.float64, device="cuda")
+    args = (C.byref(dyn), C.byref(cost), w["nx"], w["nu"], w["N"], w["T"], C.c_void_p(x.data_ptr()))
+    assert fn(*args, C.c_void_p(f[0:1].data_ptr()), stream) == 0   # warm-up: module load, address lookup
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for k in range(2):
+        assert fn(*args, C.c_void_p(f[k:k + 1].data_ptr()), stream) == 0
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
+    assert float(f[0]) == float(f[1])   # same input, same reduction order: bit-identical
 
 
 def test_noalloc_rejects_horizons_beyond_the_static_scratch():
