@@ -244,9 +244,10 @@ def bench_config(name, w, n, m, nnzj, nnzh, world):
 
 
 def measure_fp64_rate(dev, nsm, seconds=0.25):
-    """FP64 instructions per clock per SM of DFMA, DADD and DMUL, from the library's throughput
-    probe (ocp_probe_fp64): 8 CTAs of 256 threads per SM, each launch about `seconds` long,
-    timed with CUDA events on the launching stream, with the SM clock sampled meanwhile."""
+    """FP64 instructions per clock per SM of DFMA (register operands; multiplier from the
+    constant bank), DADD and DMUL, from the library's throughput probe (ocp_probe_fp64): 8 CTAs
+    of 256 threads per SM, each launch about `seconds` long, timed with CUDA events on the
+    launching stream, with the SM clock sampled meanwhile."""
     import torch
     from paper_2510_03932_gb300 import ocp
 
@@ -266,7 +267,7 @@ def measure_fp64_rate(dev, nsm, seconds=0.25):
     sampler = ClockSampler(dev.index)
     sampler.start()
     res = {}
-    for op, name in ((0, "dfma"), (1, "dadd"), (2, "dmul")):
+    for op, name in ((0, "dfma"), (1, "dadd"), (2, "dmul"), (3, "dfma_const_multiplier")):
         ms = []
         for _ in range(3):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -282,6 +283,7 @@ def measure_fp64_rate(dev, nsm, seconds=0.25):
     return dict(kernel="ocp_probe_fp64 (8 independent chains per thread, %d x %d threads, %d iterations)"
                        % (blocks, threads, iters),
                 dfma_per_clk_per_sm=per["dfma"], dadd_per_clk_per_sm=per["dadd"], dmul_per_clk_per_sm=per["dmul"],
+                dfma_const_multiplier_per_clk_per_sm=per["dfma_const_multiplier"],
                 dfma_G_per_s=res["dfma"] / 1e9, sm_mhz=clk, clocks=clocks)
 
 
@@ -542,6 +544,105 @@ def run_ours(args, rank, world):
                  synchronized_step_ms=e2e_sync_ms, whole_copies_around_device_step_ms=e2e_whole_ms),
         gpu_launches=args.steps, clocks=clocks, wall_s=wall,
     )
+    return res
+
+
+def run_sharded(args, rank, world):
+    """One problem split over the ranks (ShardedOCP): every rank evaluates its own contiguous
+    node shard of the workload on its own GPU (ocp_eval_step_range) and the partial objectives
+    are combined in rank order (all_gather of one double per rank, ocp_sum_ordered).  value =
+    the whole problem's nnz_J + nnz_H per step / the max over ranks of the step time (strong
+    scaling).  e2e: each step also copies the rank's inputs in from pinned host memory and its
+    owned output slots (and f) back."""
+    import torch
+    import torch.distributed as dist
+    from paper_2510_03932_gb300.shard import ShardedOCP
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    w = named_workload(args.workload)
+    d = synth.draw(w)
+    S = ShardedOCP(w, rank=rank, world=world)
+    H = S.H
+    n, m, nnzj, nnzh = H.n, H.m, H.nnzj, H.nnzh
+    sigma = w["sigma"]
+    x, y, vn, vm = (torch.from_numpy(d[k]).to(dev) for k in ("x", "y", "vn", "vm"))
+    outs = tuple(torch.zeros(k, dtype=torch.float64, device=dev) for k in (1, m, n, nnzj, nnzh, m, n, n))
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        S.eval_step(x, y, sigma, vn, vm, outs)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(dev.index) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    dist.barrier()
+    torch.cuda.synchronize(dev)
+    evs = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize(dev)
+    dist.barrier()
+    clocks = sampler.stop() if sampler else None
+    tot = torch.tensor([sum(a.elapsed_time(b) for a, b in evs)], dtype=torch.float64, device=dev)
+    dist.all_reduce(tot, op=dist.ReduceOp.MAX)
+    tot_ms = float(tot.item())
+    # end to end: the rank's inputs in (whole arrays: the shard reads its range and a halo) and
+    # its owned output slots out, from and to pinned host memory
+    hin = [torch.from_numpy(d[k]).pin_memory() for k in ("x", "y", "vn", "vm")]
+    din = (x, y, vn, vm)
+    slot_of = ("c", "g", "jac", "hess", "c", "g", "g")
+    own = [(o, S.owned[sl]) for o, sl in zip(outs[1:], slot_of)]
+    hout = [[torch.empty(s1 - s0, dtype=torch.float64).pin_memory() for s0, s1 in sl] for _, sl in own]
+    hf = torch.empty(1, dtype=torch.float64).pin_memory()
+
+    def e2e_step():
+        for hsrc, dd in zip(hin, din):
+            dd.copy_(hsrc, non_blocking=True)
+        step()
+        for (o, sl), hs in zip(own, hout):
+            for (s0, s1), hbuf in zip(sl, hs):
+                hbuf.copy_(o[s0:s1], non_blocking=True)
+        hf.copy_(outs[0], non_blocking=True)
+
+    e2e_steps = max(3, min(args.steps, 10))
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize(dev)
+    dist.barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    e2 = torch.tensor([e0.elapsed_time(e1) / e2e_steps], dtype=torch.float64, device=dev)
+    dist.all_reduce(e2, op=dist.ReduceOp.MAX)
+    nnz = nnzj + nnzh
+    res = dict(
+        metric=METRIC, value=nnz * args.steps / (tot_ms * 1e-3), unit="nnz/s", n_gpus=world,
+        steps=args.steps, warmup=args.warmup, ms_per_step=tot_ms / args.steps, higher_is_better=True,
+        scaling="strong", vs_baseline=None, dtype="f64", data="synthetic",
+        config=dict(bench_config(args.workload, w, n, m, nnzj, nnzh, world),
+                    parallelism="node shards over %d ranks (rank-ordered objective combination)" % world),
+        shard=dict(nodes=[S.a, S.b], note="rank 0's node range; each rank runs ocp_eval_step_range on its own"),
+        e2e=dict(value=nnz / (float(e2.item()) * 1e-3), unit="nnz/s",
+                 h2d_bytes_per_step=sum(8 * t.numel() for t in hin),
+                 d2h_bytes_per_step=8 + sum(8 * sum(s1 - s0 for s0, s1 in sl) for _, sl in own),
+                 ms=float(e2.item()), note="max over ranks; per rank: whole inputs in, owned slots out"),
+        gpu_launches=2 * args.steps, clocks=clocks,
+    )
+    S.close()
     return res
 
 
@@ -814,6 +915,15 @@ def oracle_parallel(w, budget_s, cores=None, pool=None, rounds=1):
     return (vals[0] if rounds == 1 else vals), cores, Ns
 
 
+def _free_port():
+    import socket
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -823,6 +933,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=10.0)
     ap.add_argument("--no-forms", action="store_true", help="skip the batched and differentiation forms")
+    ap.add_argument("--shard", action="store_true",
+                    help="split ONE problem over the ranks (node shards, strong scaling) instead of replicas")
     ap.add_argument("--no-widened", action="store_true", help="skip the further workloads (quadrotor, Goddard)")
     ap.add_argument("--profile-kernel", default=None,
                     choices=["eval_all", "jh", "jprod", "jtprod", "hprod", "step", "kkt", "all"],
@@ -858,6 +970,16 @@ def main():
                               config=bench_config(args.workload, w, P.n, P.m, P.nnzj, P.nnzh, 1),
                               cpu_baseline=cb, e2e=dict(value=v, unit="nnz/s", h2d_bytes_per_step=0,
                                                         d2h_bytes_per_step=0))))
+        return
+    if args.shard:
+        import torch
+        if world == 1 and "MASTER_ADDR" not in os.environ:
+            os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(_free_port()), RANK="0", WORLD_SIZE="1")
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0))))
+        res = run_sharded(args, rank, world)
+        if rank == 0:
+            print(json.dumps(res))
+        torch.distributed.destroy_process_group()
         return
     if world > 1:
         import torch

@@ -374,6 +374,46 @@ ocp_status ocp_eval_all_range(ocp_t* h, int64_t node_begin, int64_t node_end, co
                               const double* y, double sigma, double* f, double* c, double* g,
                               double* jvals, double* hvals, void* stream);
 
+/* The fused step (ocp_eval_step) on the nodes [node_begin, node_end) only: one contiguous
+ * node shard of a problem split over several devices (the paper's Discussion, Sec. 8, names
+ * multi-GPU execution as a future extension; every node's terms are independent given its
+ * neighbours, Sec. 3).  The
+ * arrays are the full-size arrays of ocp_eval_step in the global layout; the call writes the
+ * outputs the shard owns: c, J values and Jv on the defect rows j in [node_begin,
+ * min(node_end, N)) (and the boundary rows of node 0 / node N if the shard holds them), g,
+ * H values, J^T w and Hv on its nodes, and f = the shard's partial objective (the sum over
+ * its nodes of w_j f0(z_j)).  It reads x and vn on the nodes node_begin..min(node_end, N) (a
+ * one-node halo on the right) and y and vm on the defect rows node_begin-1..node_end-1 (the
+ * row to its left), plus the boundary rows it writes.  The objective of the whole problem is
+ * the sum of the shards' partials (added in rank order for a deterministic result).
+ * Node models (Van der Pol, cart-pole, double integrator, quadrotor), trapezoidal scheme,
+ * path inequalities allowed; boundary inequalities, a boundary cost, the Goddard and heat
+ * models and the Euler scheme return OCP_EMODEL; an empty or out-of-range node range OCP_EDIM. */
+ocp_status ocp_eval_step_range(ocp_t* h, int64_t node_begin, int64_t node_end, const double* x,
+                               const double* y, double sigma, const double* vn, const double* vm,
+                               double* f, double* c, double* g, double* jvals, double* hvals,
+                               double* Jv, double* Jtv, double* Hv, void* stream);
+
+/* ocp_vjp_param on the nodes [node_begin, node_end) only: J^T w on those nodes' entries of Jtw
+ * and dmu = their share of (dc/dmu)^T w (the shards' shares add up to the whole product).
+ * Reads x on the nodes of the range and w on the defect rows node_begin-1..node_end-1 and the
+ * boundary rows of the nodes it holds.  Van der Pol only; the same restrictions and errors as
+ * ocp_eval_step_range. */
+ocp_status ocp_vjp_param_range(ocp_t* h, int64_t node_begin, int64_t node_end, const double* x,
+                               const double* w, double* Jtw, double* dmu, void* stream);
+
+/* out = parts[0] + parts[1] + ... + parts[count-1], added in index order (device arrays; one
+ * thread): the rank-ordered combination of the shards' partial sums of ocp_eval_step_range and
+ * ocp_vjp_param_range, which gives every rank the same bits.  Errors: OCP_EINVAL, OCP_ECUDA
+ * (ocp_last_error(NULL)). */
+ocp_status ocp_sum_ordered(const double* parts, int count, double* out, void* stream);
+
+/* Layout of the COO values (host query): nb boundary rows; row_count[k] (nx entries) values per
+ * defect row of component k, whose N rows are consecutive from the slot of component k-1's last
+ * row (the boundary rows' nb values first); hx and hu values per node in the Hessian's X block
+ * (node-major, first) and U block. */
+ocp_status ocp_value_layout(const ocp_t* h, int64_t* nb, int32_t* row_count, int32_t* hx, int32_t* hu);
+
 /* Objective F(x) without any device allocation, for callers that cannot call cudaMalloc at
  * evaluation time: a real-time control loop that must not allocate after start-up (cudaMalloc
  * can synchronize the device and its latency is unbounded), or a framework whose allocator

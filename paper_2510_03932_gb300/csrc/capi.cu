@@ -389,6 +389,14 @@ static EvalCall full_call(const ocp* h) {
   return c;
 }
 
+// Sum of `count` doubles in index order by one thread (the rank-ordered combination of the
+// shards' partial objectives and parameter derivatives: the same bits on every rank).
+__global__ void k_sum_ordered(const double* parts, int count, double* out) {
+  double s = 0.0;
+  for (int i = 0; i < count; ++i) s = s + parts[i];
+  *out = s;
+}
+
 extern "C" {
 
 ocp_status eval_obj(ocp_t* h, const double* x, double* f, void* stream) {
@@ -516,6 +524,67 @@ ocp_status ocp_eval_all_range(ocp_t* h, int64_t node_begin, int64_t node_end, co
   c.B = node_begin; c.E = node_end; c.range = true;
   c.x = x; c.y = y; c.sigma = sigma; c.f = f; c.c = cv; c.g = g; c.jv = jvals; c.hv = hvals;
   return dispatch_eval(h, O_ALL, c, stream);
+}
+
+// The node ranges of the sharded evaluation: [B, E) inside [0, N+1), node models with the
+// trapezoidal scheme, nothing that couples node 0 with node N.
+static ocp_status check_range(ocp* h, int64_t B, int64_t E, bool products) {
+  if (B < 0 || E > h->N + 1 || B >= E) return set_err(h, OCP_EDIM, "node range outside [0, N+1) or empty");
+  if (h->model == OCP_MODEL_GODDARD)
+    return set_err(h, OCP_EMODEL, "node ranges are not provided for the Goddard model (tf couples every node)");
+  if (products && h->model == OCP_MODEL_HEAT1D)
+    return set_err(h, OCP_EMODEL, "node ranges of the fused step are provided for the node models, not the heat model");
+  if (h->scheme != OCP_SCHEME_TRAPEZOID)
+    return set_err(h, OCP_EMODEL, "node ranges are provided for the trapezoidal scheme");
+  if (h->nbin > 0)
+    return set_err(h, OCP_EMODEL, "node ranges are not provided with boundary inequalities (they couple nodes 0 and N)");
+  if (h->has_bol)
+    return set_err(h, OCP_EMODEL, "node ranges are not provided with a boundary cost (it couples nodes 0 and N)");
+  return OCP_OK;
+}
+
+ocp_status ocp_eval_step_range(ocp_t* h, int64_t node_begin, int64_t node_end, const double* x, const double* y,
+                               double sigma, const double* vn, const double* vm, double* f, double* cv, double* g,
+                               double* jvals, double* hvals, double* Jv, double* Jtv, double* Hv, void* stream) {
+  if (!h) return OCP_EINVAL;
+  ocp_status st = check_range(h, node_begin, node_end, true);
+  if (st != OCP_OK) return st;
+  NEED(x); NEED(y); NEED(vn); NEED(vm); NEED(f); NEED(cv); NEED(g); NEED(jvals); NEED(hvals);
+  NEED(Jv); NEED(Jtv); NEED(Hv);
+  EvalCall c;
+  c.B = node_begin; c.E = node_end; c.range = true;
+  c.x = x; c.y = y; c.sigma = sigma; c.f = f; c.c = cv; c.g = g; c.jv = jvals; c.hv = hvals;
+  c.vn = vn; c.vm = vm; c.ojv = Jv; c.ojtv = Jtv; c.ohv = Hv;
+  return dispatch_eval(h, O_STEP, c, stream);
+}
+
+ocp_status ocp_vjp_param_range(ocp_t* h, int64_t node_begin, int64_t node_end, const double* x, const double* w,
+                               double* Jtw, double* dmu, void* stream) {
+  if (!h) return OCP_EINVAL;
+  if (h->model != OCP_MODEL_VDP) return set_err(h, OCP_EMODEL, "parameter derivative is provided for the Van der Pol model");
+  ocp_status st = check_range(h, node_begin, node_end, true);
+  if (st != OCP_OK) return st;
+  NEED(x); NEED(w); NEED(dmu); NEED(Jtw);
+  ProdCall c;
+  c.kind = P_JTPROD; c.x = x; c.v = w; c.out = Jtw; c.dmu = dmu;
+  c.B = node_begin; c.E = node_end;
+  return dispatch_prod(h, c, stream);
+}
+
+ocp_status ocp_sum_ordered(const double* parts, int count, double* out, void* stream) {
+  if (!parts || !out || count < 1) return set_err(nullptr, OCP_EINVAL, "ocp_sum_ordered: parts, out and count >= 1 required");
+  if (((uintptr_t)parts & 7u) || ((uintptr_t)out & 7u)) return set_err(nullptr, OCP_EINVAL, "ocp_sum_ordered: unaligned pointer");
+  k_sum_ordered<<<1, 1, 0, (cudaStream_t)stream>>>(parts, count, out);
+  return cuda_err(nullptr, cudaGetLastError(), "k_sum_ordered launch");
+}
+
+ocp_status ocp_value_layout(const ocp_t* h, int64_t* nb, int32_t* row_count, int32_t* hx, int32_t* hu) {
+  if (!h || !nb || !row_count || !hx || !hu) return OCP_EINVAL;
+  *nb = h->pat.nb;
+  for (int k = 0; k < h->nx; ++k) row_count[k] = (int32_t)h->pat.row_count(k);
+  *hx = h->pat.hx;
+  *hu = h->pat.hu;
+  return OCP_OK;
 }
 
 ocp_status ocp_vjp_param(ocp_t* h, const double* x, const double* w, double* Jtw, double* dmu, void* stream) {

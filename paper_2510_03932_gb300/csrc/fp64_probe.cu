@@ -1,9 +1,11 @@
 // FP64 throughput probe (measurement helper; see include/ocp_probe.h).
 //
 // Each thread runs 8 independent dependency chains of one FP64 operation kind.  The operands
-// are kernel parameters (1.0 and a small increment), unknown to the compiler, so no chain can
-// be folded; the library is built without automatic FMA contraction, so an add stays a DADD
-// and a multiply a DMUL.  Eight chains per thread and a few warps per scheduler give the FP64
+// derive from kernel parameters (1.0 and a small increment), unknown to the compiler, so no
+// chain can be folded; the library is built without automatic FMA contraction, so an add stays
+// a DADD and a multiply a DMUL.  The FMA comes in two forms: with its multiplier in a register
+// (computed at run time) and with its multiplier read directly from the parameters (the
+// constant bank), which the pipe issues at different rates.  Eight chains per thread and a few warps per scheduler give the FP64
 // pipe more independent work than its latency needs, so the launch measures its issue rate.
 #include <cuda_runtime.h>
 
@@ -17,16 +19,20 @@ constexpr int kChains = 8;
 template <int OP>
 __global__ void k_probe_fp64(double* out, int iters, double one, double eps) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  double a[kChains];
+  double a[kChains], b[kChains];
 #pragma unroll
-  for (int k = 0; k < kChains; ++k) a[k] = (double)(k + 1) * eps + (double)threadIdx.x;
+  for (int k = 0; k < kChains; ++k) {
+    a[k] = (double)(k + 1) * eps + (double)threadIdx.x;
+    b[k] = fma(eps, (double)k, one);   // about 1, computed at run time: held in a register
+  }
 #pragma unroll 4
   for (int it = 0; it < iters; ++it) {
 #pragma unroll
     for (int k = 0; k < kChains; ++k) {
-      if (OP == 0) a[k] = fma(a[k], one, eps);
-      else if (OP == 1) a[k] = a[k] + eps;
-      else a[k] = a[k] * one;
+      if (OP == 0) a[k] = fma(a[k], b[k], eps);        // multiplier in a register
+      else if (OP == 1) a[k] = a[k] + b[k];
+      else if (OP == 2) a[k] = a[k] * b[k];
+      else a[k] = fma(a[k], one, eps);                 // multiplier a kernel parameter
     }
   }
   double s = a[0];
@@ -38,7 +44,7 @@ __global__ void k_probe_fp64(double* out, int iters, double one, double eps) {
 }  // namespace
 
 extern "C" ocp_status ocp_probe_fp64(int op, int blocks, int threads, int iters, double* out, void* stream) {
-  if (op < 0 || op > 2) return ocpg::set_err(nullptr, OCP_EINVAL, "ocp_probe_fp64: op must be 0, 1 or 2");
+  if (op < 0 || op > 3) return ocpg::set_err(nullptr, OCP_EINVAL, "ocp_probe_fp64: op must be 0, 1, 2 or 3");
   if (blocks < 1 || blocks > (1 << 20) || threads < 32 || threads > 1024 || (threads & 31) || iters < 1 ||
       iters > (1 << 24))
     return ocpg::set_err(nullptr, OCP_EINVAL, "ocp_probe_fp64: blocks, threads or iters out of range");
@@ -47,6 +53,7 @@ extern "C" ocp_status ocp_probe_fp64(int op, int blocks, int threads, int iters,
   const double one = 1.0, eps = 1.0e-9;
   if (op == 0) k_probe_fp64<0><<<blocks, threads, 0, s>>>(out, iters, one, eps);
   else if (op == 1) k_probe_fp64<1><<<blocks, threads, 0, s>>>(out, iters, one, eps);
-  else k_probe_fp64<2><<<blocks, threads, 0, s>>>(out, iters, one, eps);
+  else if (op == 2) k_probe_fp64<2><<<blocks, threads, 0, s>>>(out, iters, one, eps);
+  else k_probe_fp64<3><<<blocks, threads, 0, s>>>(out, iters, one, eps);
   return ocpg::cuda_err(nullptr, cudaGetLastError(), "ocp_probe_fp64 launch");
 }

@@ -44,6 +44,14 @@ __device__ __forceinline__ double fadd(const ModelConst& K, double a, double b) 
 __device__ __forceinline__ double fsub(const ModelConst& K, double a, double b) { return fma(-b, K.one, a); }
 __device__ __forceinline__ double fmul(const ModelConst& K, double a, double b) { return fma(a, b, K.mz); }
 
+// Operand sources matter as well (measured with the library's FP64 throughput probe, all
+// operands independent): an FMA whose multiplier is a register issues at the pipe's full rate,
+// 2 per clock per SM, but at about 5/6 of it when the multiplier is read from the constant bank
+// (a kernel parameter used directly), and DADD and DMUL run at 5/6 too.  Taking the constants
+// through shared memory puts them in registers, but in these kernels the extra registers cost
+// more occupancy than the faster FMAs gain (measured on the fused step: whole argument block
+// 110.6-127.9 us, model constants only 109.3-112.9 us, the constant 1 alone 108.7 us, against
+// 106.0 us from the constant bank), so the kernels read their constants from the parameters.
 #define OCP_TABLE1(NAME, TYPE, N, ...)                       \
   __host__ __device__ static constexpr TYPE NAME(int k) {    \
     constexpr TYPE t[N] = __VA_ARGS__;                       \

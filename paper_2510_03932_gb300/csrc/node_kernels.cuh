@@ -200,14 +200,14 @@ __device__ __forceinline__ ModelConst launch_consts(const NodeArgs<M>& a) {
 
 // ybar_k = w_{k,j-1} + w_{k,j} over the defect rows of component k (zero outside 0..N-1)
 template <class M>
-__device__ __forceinline__ void load_bar(const NodeArgs<M>& a, const double* w, int64_t j, double (&wb)[M::NX],
+__device__ __forceinline__ void load_bar(const NodeArgs<M>& a, const ModelConst& K, const double* w, int64_t j, double (&wb)[M::NX],
                                          double (&wl)[M::NX], double (&wr)[M::NX]) {
 #pragma unroll
   for (int k = 0; k < M::NX; ++k) {
     const double* row = w + a.nb + (int64_t)k * a.N;
     wl[k] = (j >= 1) ? __ldg(row + j - 1) : 0.0;
     wr[k] = (j < a.N) ? __ldg(row + j) : 0.0;
-    wb[k] = fadd(a.K, wl[k], wr[k]);
+    wb[k] = fadd(K, wl[k], wr[k]);
   }
 }
 
@@ -221,14 +221,15 @@ __device__ __forceinline__ void node_cq(const NodeArgs<M>& a, bool endp, double 
 }
 
 template <class M>
-__device__ __forceinline__ void load_ybar(const NodeArgs<M>& a, const double* w, int64_t j, double (&wb)[M::NX]) {
+__device__ __forceinline__ void load_ybar(const NodeArgs<M>& a, const ModelConst& K, const double* w, int64_t j,
+                                          double (&wb)[M::NX]) {
 #pragma unroll
   for (int k = 0; k < M::NX; ++k) {
     if (M::HK(k)) {
       const double* row = w + a.nb + (int64_t)k * a.N;
       const double wl = (j >= 1) ? __ldg(row + j - 1) : 0.0;
       const double wr = (j < a.N) ? __ldg(row + j) : 0.0;
-      wb[k] = fadd(a.K, wl, wr);
+      wb[k] = fadd(K, wl, wr);
     } else {
       wb[k] = 0.0;
     }
@@ -238,20 +239,21 @@ __device__ __forceinline__ void load_ybar(const NodeArgs<M>& a, const double* w,
 // gradient entries g_v = 2 w_j q_v (z_v - ref_v); returns 2 w_j f0(z_j) = sum_v g_v (z_v - ref_v)
 // (ref_v of a tracked state component is read from the per-node table xtrack)
 template <class M, bool REF, bool WG>
-__device__ __forceinline__ double node_grad(const NodeArgs<M>& a, const double (&z)[M::NZ], bool endp, int64_t j) {
+__device__ __forceinline__ double node_grad(const NodeArgs<M>& a, const ModelConst& K, const double (&z)[M::NZ], bool endp,
+                                           int64_t j) {
   double s = 0.0;
 #pragma unroll
   for (int v = 0; v < M::NZ; ++v) {
     double rv = a.ref[v];
     if (REF && v < M::NX && a.xtrack && a.trk[v < M::NX ? v : 0] >= 0)
       rv = __ldg(a.xtrack + (int64_t)a.ntrk * j + a.trk[v < M::NX ? v : 0]);
-    const double d = REF ? fsub(a.K, z[v], rv) : z[v];
-    const double gv = fmul(a.K, endp ? a.gq_end[v] : a.gq_in[v], d);
+    const double d = REF ? fsub(K, z[v], rv) : z[v];
+    const double gv = fmul(K, endp ? a.gq_end[v] : a.gq_in[v], d);
     if (WG) {
       if (v < M::NX) a.g[(int64_t)M::NX * j + v] = gv;
       else a.g[a.uoff + (int64_t)M::NU * j + (v - M::NX)] = gv;
     }
-    s = (v == 0) ? fmul(a.K, gv, d) : fma(gv, d, s);
+    s = (v == 0) ? fmul(K, gv, d) : fma(gv, d, s);
   }
   return s;
 }
@@ -299,14 +301,14 @@ __device__ __forceinline__ void jv_node(const ModelConst& K, const double (&mjx)
 // J^T w at node j: (w_{a,j-1} - w_{a,j}) + sum_k wbar_k mjx_{k,a}, the control entries
 // sum_k wbar_k mju_{k,i}, plus the boundary rows' w at j = 0 / N (bnd: this CTA may hold them).
 template <class M>
-__device__ __forceinline__ void jtv_node(const NodeArgs<M>& a, const double* w, int64_t j, bool bnd,
+__device__ __forceinline__ void jtv_node(const NodeArgs<M>& a, const ModelConst& K, const double* w, int64_t j, bool bnd,
                                          const double (&mjx)[M::NX][M::MAXRX], const double (&mju)[M::NX][M::MAXRU],
                                          const double (&wl)[M::NX], const double (&wr)[M::NX],
                                          const double (&wb)[M::NX], double (&o)[M::NZ]) {
   constexpr int NX = M::NX;
   // every state entry accumulates its terms in increasing k (one pass over the row templates)
 #pragma unroll
-  for (int v = 0; v < NX; ++v) o[v] = fsub(a.K, wl[v], wr[v]);
+  for (int v = 0; v < NX; ++v) o[v] = fsub(K, wl[v], wr[v]);
 #pragma unroll
   for (int k = 0; k < NX; ++k)
 #pragma unroll
@@ -315,8 +317,8 @@ __device__ __forceinline__ void jtv_node(const NodeArgs<M>& a, const double* w, 
   if (bnd) {  // only CTAs holding node 0 or node N (uniform branch)
 #pragma unroll
     for (int v = 0; v < NX; ++v) {
-      if (j == 0) o[v] = fadd(a.K, o[v], __ldg(w + v));
-      if (a.has_final && j == a.N) o[v] = fadd(a.K, o[v], __ldg(w + NX + v));
+      if (j == 0) o[v] = fadd(K, o[v], __ldg(w + v));
+      if (a.has_final && j == a.N) o[v] = fadd(K, o[v], __ldg(w + NX + v));
     }
   }
 #pragma unroll
@@ -327,14 +329,14 @@ __device__ __forceinline__ void jtv_node(const NodeArgs<M>& a, const double* w, 
     for (int k = 0; k < NX; ++k)
 #pragma unroll
       for (int e = 0; e < M::MAXRU; ++e)
-        if (e < M::RU(k) && M::UV(k, e) == i) { s = first ? fmul(a.K, wb[k], mju[k][e]) : fma(wb[k], mju[k][e], s); first = false; }
+        if (e < M::RU(k) && M::UV(k, e) == i) { s = first ? fmul(K, wb[k], mju[k][e]) : fma(wb[k], mju[k][e], s); first = false; }
     o[NX + i] = s;
   }
 }
 
 // H v at node j: the full symmetric block (structural entries only) times v_{z_j}.
 template <class M>
-__device__ __forceinline__ void hv_node(const NodeArgs<M>& a, const double* hd, const double (&cqd)[M::NZ],
+__device__ __forceinline__ void hv_node(const NodeArgs<M>& a, const ModelConst& K, const double* hd, const double (&cqd)[M::NZ],
                                         const double (&vz)[M::NZ], double (&o)[M::NZ]) {
   constexpr HTmpl<M> HT{};
   bool first[M::NZ];
@@ -345,10 +347,10 @@ __device__ __forceinline__ void hv_node(const NodeArgs<M>& a, const double* hd, 
     if (a.hpos[e] >= 0) {
       const int aa = HT.a[e], bb = HT.b[e];
       const double val = (HT.dyn[e] >= 0) ? hd[HT.dyn[e] >= 0 ? HT.dyn[e] : 0] : cqd[aa];
-      o[aa] = first[aa] ? fmul(a.K, val, vz[bb]) : fma(val, vz[bb], o[aa]);
+      o[aa] = first[aa] ? fmul(K, val, vz[bb]) : fma(val, vz[bb], o[aa]);
       first[aa] = false;
       if (aa != bb) {
-        o[bb] = first[bb] ? fmul(a.K, val, vz[aa]) : fma(val, vz[aa], o[bb]);
+        o[bb] = first[bb] ? fmul(K, val, vz[aa]) : fma(val, vz[aa], o[bb]);
         first[bb] = false;
       }
     }
@@ -417,7 +419,7 @@ __device__ __forceinline__ void node_eval_tile(const NodeArgs<M>& a, const Model
     if (act) {
       load_node<M>(a, j, z);
       if (NEEDH) {
-        load_ybar<M>(a, a.y, j, yb);
+        load_ybar<M>(a, K, a.y, j, yb);
         node_cq<M>(a, endp, cqd);
       }
       M::template eval<WC, NEEDJ, NEEDH>(K, z, yb, cqd, pa[q], pb[q], mjx, mju, hd);
@@ -430,13 +432,13 @@ __device__ __forceinline__ void node_eval_tile(const NodeArgs<M>& a, const Model
     if (own) {
       if (WHV) {
         double o[NZ];
-        hv_node<M>(a, hd, cqd, vz, o);
+        hv_node<M>(a, K, hd, cqd, vz, o);
         store_nz<M>(a, a.ohv, j, o);
       }
       if (WJTV) {
         double wb[NX], wl[NX], wr[NX], o[NZ];
-        load_bar<M>(a, a.wv, j, wb, wl, wr);
-        jtv_node<M>(a, a.wv, j, bnd, mjx, mju, wl, wr, wb, o);
+        load_bar<M>(a, K, a.wv, j, wb, wl, wr);
+        jtv_node<M>(a, K, a.wv, j, bnd, mjx, mju, wl, wr, wb, o);
         store_nz<M>(a, a.ojtv, j, o);
       }
       if (WJV && bnd) {
@@ -466,8 +468,8 @@ __device__ __forceinline__ void node_eval_tile(const NodeArgs<M>& a, const Model
       // ---- gradient and objective term
       if (sG || sF) {
         double s2;
-        if (a.has_ref) s2 = sG ? node_grad<M, true, true>(a, z, endp, j) : node_grad<M, true, false>(a, z, endp, j);
-        else s2 = sG ? node_grad<M, false, true>(a, z, endp, j) : node_grad<M, false, false>(a, z, endp, j);
+        if (a.has_ref) s2 = sG ? node_grad<M, true, true>(a, K, z, endp, j) : node_grad<M, true, false>(a, K, z, endp, j);
+        else s2 = sG ? node_grad<M, false, true>(a, K, z, endp, j) : node_grad<M, false, false>(a, K, z, endp, j);
         objterm = (q == 0) ? s2 : fadd(K, objterm, s2);
       }
       // ---- boundary rows X_{0,k} (and X_{N,k}): constraint value and the constant Jacobian entry
@@ -610,7 +612,7 @@ __device__ __forceinline__ void node_eval_kernel_body(const NodeArgs<M>& a) {
   constexpr bool WF = OUT & O_F;
   extern __shared__ __align__(16) double sm[];
   __shared__ double sEdge[2 * (TILE / 32 + 1) * M::NX];
-  ModelConst K = launch_consts<M, PAR>(a);
+  const ModelConst K = launch_consts<M, PAR>(a);
   for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x)
     node_eval_tile<M, TILE, NPT, OUT>(a, K, tile, sm, sEdge, a.partials + tile);
   if (WF && a.f) finish_tiles<TILE>(a.partials, a.ntiles, a.counter, a.f, 0.5, sm);
@@ -705,19 +707,19 @@ __global__ void __launch_bounds__(TILE) k_node_jtprod(const __grid_constant__ No
   constexpr int NHD = (M::NHD > 0) ? M::NHD : 1;
   __shared__ double red[TILE];
   ModelConst K = launch_consts<M, PAR>(a);
-  const int64_t nchunks = (a.N + TILE) / TILE;
+  const int64_t nchunks = (a.E - a.B + TILE - 1) / TILE;   // the nodes [B, E) in chunks of TILE
   for (int64_t chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
-    const int64_t j = chunk * TILE + threadIdx.x;
-    const bool bnd = (chunk == 0) || (chunk == nchunks - 1);
+    const int64_t j0 = a.B + chunk * TILE, j = j0 + threadIdx.x;
+    const bool bnd = (j0 == 0) || (j0 + TILE > a.N);  // chunk may hold node 0 or node N (uniform)
     double acc_mu = 0.0;
-    if (j <= a.N) {
+    if (j < a.E) {
       double z[NZ], yb[NX], cqd[NZ], pa[NX], pb[NX], mjx[NX][M::MAXRX], mju[NX][M::MAXRU], hd[NHD];
       double wb[NX], wl[NX], wr[NX];
       load_node<M>(a, j, z);
-      load_bar<M>(a, a.v, j, wb, wl, wr);
+      load_bar<M>(a, K, a.v, j, wb, wl, wr);
       M::template eval<false, true, false>(K, z, yb, cqd, pa, pb, mjx, mju, hd);
       double o[NZ];
-      jtv_node<M>(a, a.v, j, bnd, mjx, mju, wl, wr, wb, o);
+      jtv_node<M>(a, K, a.v, j, bnd, mjx, mju, wl, wr, wb, o);
       store_nz<M>(a, a.out, j, o);
       if (DPAR) {
         double mdp[NX];
@@ -757,7 +759,7 @@ __global__ void __launch_bounds__(TILE) k_node_hprod(const __grid_constant__ Nod
     if (j <= a.N) {
       double z[NZ], vz[NZ], yb[NX], cqd[NZ], pa[NX], pb[NX], mjx[NX][M::MAXRX], mju[NX][M::MAXRU], hd[NHD];
       load_node<M>(a, j, z);
-      load_ybar<M>(a, a.y, j, yb);
+      load_ybar<M>(a, K, a.y, j, yb);
       const bool endp = (j == 0) || (j == a.N);
       node_cq<M>(a, endp, cqd);
 #pragma unroll
@@ -766,10 +768,10 @@ __global__ void __launch_bounds__(TILE) k_node_hprod(const __grid_constant__ Nod
       for (int i = 0; i < M::NU; ++i) vz[NX + i] = __ldg(a.v + a.uoff + M::NU * j + i);
       M::template eval<false, false, true>(K, z, yb, cqd, pa, pb, mjx, mju, hd);
       double o[NZ];
-      hv_node<M>(a, hd, cqd, vz, o);
+      hv_node<M>(a, K, hd, cqd, vz, o);
       if (MIX) {
         double mb[NX], mg[NZ], wl[NX], wr[NX];
-        load_bar<M>(a, a.mixw, j, mb, wl, wr);
+        load_bar<M>(a, K, a.mixw, j, mb, wl, wr);
         M::dparam_grad(K, z, mb, mg);
 #pragma unroll
         for (int v = 0; v < NZ; ++v) {
@@ -949,12 +951,12 @@ __global__ void __launch_bounds__(TILE) k_euler(const __grid_constant__ NodeArgs
           wl[k] = (j >= 1) ? __ldg(row + j - 1) : 0.0;
           wr[k] = __ldg(row + j);
         }
-        jtv_node<M>(a, a.wv, j, tile == 0, mjx, mju, wl, wr, wr, o);  // CTA-uniform boundary flag
+        jtv_node<M>(a, K, a.wv, j, tile == 0, mjx, mju, wl, wr, wr, o);  // CTA-uniform boundary flag
         store_nz<M>(a, a.ojtv, j, o);
       }
       if (WHV) {
         double o[NZ];
-        hv_node<M>(a, hd, cqd, vz, o);
+        hv_node<M>(a, K, hd, cqd, vz, o);
         store_nz<M>(a, a.ohv, j, o);
       }
       if (sH) {
@@ -969,8 +971,8 @@ __global__ void __launch_bounds__(TILE) k_euler(const __grid_constant__ NodeArgs
         }
       }
       if (sG || sF) {
-        if (a.has_ref) objterm = sG ? node_grad<M, true, true>(a, z, false, j) : node_grad<M, true, false>(a, z, false, j);
-        else objterm = sG ? node_grad<M, false, true>(a, z, false, j) : node_grad<M, false, false>(a, z, false, j);
+        if (a.has_ref) objterm = sG ? node_grad<M, true, true>(a, K, z, false, j) : node_grad<M, true, false>(a, K, z, false, j);
+        else objterm = sG ? node_grad<M, false, true>(a, K, z, false, j) : node_grad<M, false, false>(a, K, z, false, j);
       }
       if (j == 0) {
 #pragma unroll
@@ -1123,7 +1125,7 @@ cudaError_t node_prod_launch(ocp* h, const ProdCall& c, const NodeArgs<M>& a, cu
     if (c.pdir != 0.0 || c.pdir_dev) go(k_node_jprod<M, TILE, true, PAR>, a.ntiles);
     else go(k_node_jprod<M, TILE, false, PAR>, a.ntiles);
   } else if (c.kind == P_JTPROD) {
-    const int64_t blocks = (h->N + TILE) / TILE;
+    const int64_t blocks = (a.E - a.B + TILE - 1) / TILE;
     if (c.dmu) go(k_node_jtprod<M, TILE, true, PAR>, blocks);
     else go(k_node_jtprod<M, TILE, false, PAR>, blocks);
   } else {
@@ -1142,6 +1144,7 @@ ocp_status node_prod_dispatch(ocp* h, const ProdCall& c, cudaStream_t s) {
   a.x = c.x; a.y = c.y; a.v = c.v; a.out = c.out; a.dmu = c.dmu;
   a.pdir = c.pdir; a.pdir_dev = c.pdir_dev; a.mixw = c.mixw; a.mixs = c.mixs;
   a.B = 0; a.E = h->N + 1;
+  if (c.kind == P_JTPROD) { a.B = c.B; a.E = c.E < 0 ? h->N + 1 : c.E; }
   if (c.kind == P_JPROD) a.ntiles = (h->N + 1 + (TILE - 2)) / (TILE - 1);
   cudaError_t e;
   if constexpr (M::HAS_DPARAM) {

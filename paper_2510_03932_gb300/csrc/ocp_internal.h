@@ -191,6 +191,9 @@ struct ProdCall {
   const double* pdir_dev = nullptr;  // jprod: same with a device scalar
   const double* mixw = nullptr; // hprod: adds (d2 c / dp0 dx)^T mixw * mixs
   const double* mixs = nullptr; // device scalar
+  // jtprod only: the nodes [B, E) whose entries are written (E < 0: every node); dmu then
+  // receives the partial sum over these nodes
+  int64_t B = 0, E = -1;
 };
 
 // Per-model dispatchers (node models: VDP, CARTPOLE, DINT, QUADROTOR; HEAT1D separate).

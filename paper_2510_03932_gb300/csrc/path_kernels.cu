@@ -121,7 +121,8 @@ ocp_status path_eval(ocp* h, unsigned out, const EvalCall& c, cudaStream_t s) {
 ocp_status path_prod(ocp* h, const ProdCall& c, cudaStream_t s) {
   if (h->pat.npath == 0) return OCP_OK;
   PathArgs a;
-  if (path_fill(h, a, 0, h->N + 1) != OCP_OK) return set_err(h, OCP_EDIM, "too many variables per node for path rows");
+  const int64_t B = (c.kind == P_JTPROD) ? c.B : 0, E = (c.kind == P_JTPROD && c.E >= 0) ? c.E : h->N + 1;
+  if (path_fill(h, a, B, E) != OCP_OK) return set_err(h, OCP_EDIM, "too many variables per node for path rows");
   a.x = c.x; a.y = c.y;
   cudaError_t e;
   if (c.kind == P_JPROD) { a.vn = c.v; a.ojv = c.out; e = path_go<false, false, false, true, false, false>(h, a, s); }

@@ -76,6 +76,10 @@ _SIGS = {
     "ocp_eval_step_host_async": [_P, _P, _P, _D, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P],
     "ocp_host_step_wait": [_P, _P],
     "ocp_eval_all_range": [_P, _I64, _I64, _P, _P, _D, _P, _P, _P, _P, _P, _P],
+    "ocp_eval_step_range": [_P, _I64, _I64, _P, _P, _D, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P],
+    "ocp_vjp_param_range": [_P, _I64, _I64, _P, _P, _P, _P, _P],
+    "ocp_sum_ordered": [_P, C.c_int, _P, _P],
+    "ocp_value_layout": [_P, C.POINTER(_I64), _P, C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
     "ocp_vjp_param": [_P, _P, _P, _P, _P, _P],
     "ocp_set_param0": [_P, _D],
     "ocp_bind_param0": [_P, _P],
@@ -118,6 +122,17 @@ def probe_fp64(op, blocks, threads, iters, out, stream=None):
     _check(lib().ocp_probe_fp64(int(op), int(blocks), int(threads), int(iters), C.c_void_p(out.data_ptr()),
                                 _stream(stream)))
     return blocks * threads * (8 * iters + 7)
+
+
+def sum_ordered(parts, out, stream=None):
+    """ocp_sum_ordered: out[0] = parts[0] + parts[1] + ... in index order (CUDA float64 tensors)."""
+    if parts.dtype != torch.float64 or not parts.is_cuda or not parts.is_contiguous() or parts.numel() < 1:
+        raise TypeError("parts must be a non-empty contiguous float64 CUDA tensor")
+    if out.dtype != torch.float64 or not out.is_cuda or out.numel() != 1:
+        raise TypeError("out must be a one-element float64 CUDA tensor")
+    _check(lib().ocp_sum_ordered(C.c_void_p(parts.data_ptr()), int(parts.numel()), C.c_void_p(out.data_ptr()),
+                                 _stream(stream)))
+    return out
 
 
 def _stream(stream):
@@ -362,6 +377,37 @@ class OCP:
         _check(lib().ocp_eval_step(self.h, _ptr(x), _ptr(y), float(sigma), _ptr(vn), _ptr(vm),
                                    *[_ptr(t) for t in outs], _stream(stream)), self.h)
         return outs
+
+    def eval_step_range(self, node_begin, node_end, x, y, sigma, vn, vm, outs, stream=None):
+        """ocp_eval_step_range: the fused step on the nodes [node_begin, node_end) only, into the
+        full-size buffers `outs` = (f, c, g, jvals, hvals, Jv, Jtv, Hv); f receives the range's
+        partial objective."""
+        x = self._vec(x, self.n, "x"); y = self._vec(y, self.m, "y")
+        vn = self._vec(vn, self.n, "vn"); vm = self._vec(vm, self.m, "vm")
+        sizes = (1, self.m, self.n, self.nnzj, self.nnzh, self.m, self.n, self.n)
+        names = ("f", "c", "g", "jvals", "hvals", "Jv", "Jtv", "Hv")
+        outs = tuple(self._vec(o, s, nm) for o, s, nm in zip(outs, sizes, names))
+        _check(lib().ocp_eval_step_range(self.h, int(node_begin), int(node_end), _ptr(x), _ptr(y), float(sigma),
+                                         _ptr(vn), _ptr(vm), *[_ptr(o) for o in outs], _stream(stream)), self.h)
+        return outs
+
+    def vjp_param_range(self, node_begin, node_end, x, w, Jtw, dmu, stream=None):
+        """ocp_vjp_param_range: J^T w on the nodes [node_begin, node_end) and their share of
+        (dc/dmu)^T w (Van der Pol)."""
+        x = self._vec(x, self.n, "x"); w = self._vec(w, self.m, "w")
+        Jtw = self._vec(Jtw, self.n, "Jtw"); dmu = self._vec(dmu, 1, "dmu")
+        _check(lib().ocp_vjp_param_range(self.h, int(node_begin), int(node_end), _ptr(x), _ptr(w), _ptr(Jtw),
+                                         _ptr(dmu), _stream(stream)), self.h)
+        return Jtw, dmu
+
+    def value_layout(self):
+        """ocp_value_layout: nb, values per defect row of each component, Hessian values per node
+        in the X and U blocks."""
+        nb, hx, hu = _I64(), C.c_int32(), C.c_int32()
+        rc = (C.c_int32 * self.nx)()
+        _check(lib().ocp_value_layout(self.h, C.byref(nb), C.cast(rc, _P), C.byref(hx), C.byref(hu)), self.h)
+        return dict(nx=self.nx, nu=self.nu, N=self.N, nb=nb.value, has_final=nb.value > self.nx,
+                    jcount=[int(v) for v in rc], hx=hx.value, hu=hu.value)
 
     def _hvec(self, t, size, name):
         if t is None:

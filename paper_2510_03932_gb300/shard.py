@@ -1,10 +1,12 @@
-"""Host logic for splitting one transcription over S devices (contiguous node shards).
+"""One transcription split over S devices (contiguous node shards), one rank per device.
 
 Shard s owns nodes [a_s, b_s) of 0..N and the defect rows j in [a_s, min(b_s, N)); it reads
 x on nodes a_s..min(b_s, N) (a one-node halo on the right) and y on rows a_s-1..b_s-1 (the
 multipliers of the row to its left).  Every output slot belongs to exactly one shard, so the
-shards' outputs are concatenated without exchange; the objective is the sum of the shard
-partials, added in rank order.  On the device a shard is one ocp_eval_all_range call.
+shards' outputs are concatenated without exchange; the objective and the parameter derivative
+(dc/dmu)^T w are sums of the shard partials, added in rank order.  On the device a shard is one
+ocp_eval_step_range (or ocp_eval_all_range, ocp_vjp_param_range) call; ShardedOCP runs a rank's
+shard and combines the partials through torch.distributed.
 """
 from __future__ import annotations
 
@@ -34,9 +36,9 @@ def shard_slots(layout: dict, a: int, b: int):
     if a == 0:
         out["c"].append((0, nx))
         out["jac"].append((0, nx))
-    if layout["has_final"] and a <= N < b:
-        out["c"].append((nx, 2 * nx))
-        out["jac"].append((nx, 2 * nx))
+    if nb > nx and a <= N < b:   # final rows X_{N,k} (every component or a subset)
+        out["c"].append((nx, nb))
+        out["jac"].append((nx, nb))
     base = nb
     for k in range(nx):
         cnt = layout["jcount"][k]
@@ -60,3 +62,85 @@ def combine_objective(partials):
     for p in partials:
         total += float(p)
     return total
+
+
+class ShardedOCP:
+    """One problem evaluated by every rank of a torch.distributed process group, each rank on
+    its own node shard and device.
+
+    Every rank holds the inputs in the global layout (it reads only its shard and the one-node
+    halo) and full-size output buffers of which it writes the slots `owned` lists.  The two
+    cross-node sums are combined by gathering one double per rank (all_gather: device tensors
+    with NCCL, host tensors with gloo) and adding the partials in rank order on the device
+    (ocp_sum_ordered), so every rank ends with the same bits.  Nothing else moves between
+    ranks.  The objective of the whole problem equals the unsharded one within rounding (the
+    partials group the terms differently); every other output slot is bit-identical to the
+    unsharded evaluation's.
+    """
+
+    def __init__(self, w: dict, group=None, rank: int | None = None, world: int | None = None):
+        import torch.distributed as dist
+
+        from . import ocp
+        self.group = group
+        self.rank = dist.get_rank(group) if rank is None else rank
+        self.world = dist.get_world_size(group) if world is None else world
+        self.H = ocp.OCP.from_workload(w)
+        self.a, self.b = node_shards(self.H.N, self.world)[self.rank]
+        self.layout = self.H.value_layout()
+        self.owned = shard_slots(self.layout, self.a, self.b)
+
+    def close(self):
+        self.H.close()
+
+    def combine(self, part, out=None, stream=None):
+        """Sum over the ranks of the one-element CUDA tensor `part`, in rank order, into `out`."""
+        import torch
+        import torch.distributed as dist
+
+        from . import ocp
+        out = part if out is None else out
+        if dist.get_backend(self.group) == "nccl":
+            parts = torch.empty(self.world, dtype=torch.float64, device=part.device)
+            dist.all_gather_into_tensor(parts, part.reshape(1), group=self.group)
+        else:
+            host = part.detach().reshape(1).cpu()
+            gathered = [torch.empty_like(host) for _ in range(self.world)]
+            dist.all_gather(gathered, host, group=self.group)
+            parts = torch.cat(gathered).to(part.device)
+        return ocp.sum_ordered(parts, out, stream)
+
+    def eval_step(self, x, y, sigma, vn, vm, outs, stream=None):
+        """This rank's shard of the fused step into the full-size buffers `outs` = (f, c, g,
+        jvals, hvals, Jv, Jtv, Hv); f becomes the objective of the whole problem."""
+        outs = self.H.eval_step_range(self.a, self.b, x, y, sigma, vn, vm, outs, stream)
+        self.combine(outs[0], stream=stream)
+        return outs
+
+    def vjp_param(self, x, w, Jtw, dmu, stream=None):
+        """This rank's entries of J^T w and the whole (dc/dmu)^T w (Van der Pol)."""
+        self.H.vjp_param_range(self.a, self.b, x, w, Jtw, dmu, stream)
+        self.combine(dmu, stream=stream)
+        return Jtw, dmu
+
+    # the product outputs share the slots of c (Jv) and g (J^T w, H v)
+    _SLOTS = {"c": "c", "g": "g", "jac": "jac", "hess": "hess", "Jv": "c", "Jtv": "g", "Hv": "g"}
+
+    def gather(self, name, t):
+        """The complete output `name` (c, g, jac, hess, Jv, Jtv or Hv) on every rank, assembled
+        from the ranks' owned slots (for checks; moves the whole array).  Path-inequality rows
+        are not part of the slot bookkeeping."""
+        import torch
+        import torch.distributed as dist
+        slots = self.owned[self._SLOTS[name]]
+        host = t.detach().cpu()
+        mine = torch.cat([host[s0:s1] for s0, s1 in slots]) if slots else host[:0]
+        everyone = [None] * self.world
+        dist.all_gather_object(everyone, (slots, mine), group=self.group)
+        full = torch.full_like(host, float("nan"))
+        for slots, vals in everyone:
+            k = 0
+            for s0, s1 in slots:
+                full[s0:s1] = vals[k:k + s1 - s0]
+                k += s1 - s0
+        return full
