@@ -83,11 +83,11 @@ def _counts(w):
 # bench reports no FP64 fraction for that model until they are measured again.
 FP64_OPS_PER_NODE = {("vdp", "eval_all"): 26.6, ("vdp", "jh"): 10.0, ("vdp", "jprod"): 13.0,
                      ("vdp", "jtprod"): 12.0, ("vdp", "hprod"): 11.0, ("vdp", "step"): 50.6,
-                     ("cartpole", "eval_all"): 127.9, ("cartpole", "jh"): 103.8, ("cartpole", "jprod"): 81.6,
+                     ("cartpole", "eval_all"): 126.9, ("cartpole", "jh"): 103.8, ("cartpole", "jprod"): 81.6,
                      ("cartpole", "jtprod"): 78.0, ("cartpole", "hprod"): 108.0, ("cartpole", "step"): 174.0,
-                     ("quadrotor", "eval_all"): 260.3, ("quadrotor", "jh"): 180.8, ("quadrotor", "jprod"): 165.5,
-                     ("quadrotor", "jtprod"): 157.0, ("quadrotor", "hprod"): 199.0, ("quadrotor", "step"): 398.8,
-                     ("goddard", "eval_all"): 101.2, ("goddard", "jh"): 91.3, ("goddard", "jprod"): 68.3,
+                     ("quadrotor", "eval_all"): 251.2, ("quadrotor", "jh"): 177.7, ("quadrotor", "jprod"): 165.4,
+                     ("quadrotor", "jtprod"): 156.0, ("quadrotor", "hprod"): 199.0, ("quadrotor", "step"): 398.8,
+                     ("goddard", "eval_all"): 101.3, ("goddard", "jh"): 91.2, ("goddard", "jprod"): 68.3,
                      ("goddard", "jtprod"): 68.2, ("goddard", "hprod"): 95.2, ("goddard", "step"): 155.4,
                      ("vdp:euler", "eval_all"): 21.5, ("vdp:euler", "jh"): 8.0, ("vdp:euler", "jprod"): 11.0,
                      ("vdp:euler", "jtprod"): 10.0, ("vdp:euler", "hprod"): 10.0, ("vdp:euler", "step"): 41.5,
@@ -108,8 +108,8 @@ KERNEL_SOURCES = {
     "heat64": _COMMON + ["heat_kernels.cu"],
 }
 # Tags of the sources the FP64_OPS_PER_NODE counts (and TRAFFIC) were measured on.
-FP64_OPS_SRC = {"vdp": "ebe15e385cf4", "vdp:euler": "ebe15e385cf4", "cartpole": "47619928cb1c",
-                "quadrotor": "685b21a7bc91", "goddard": "8b0d5888e3fd", "heat64": "046250673feb"}
+FP64_OPS_SRC = {"vdp": "cd813b12904d", "vdp:euler": "cd813b12904d", "cartpole": "d12f7a727dda",
+                "quadrotor": "89f823db6a42", "goddard": "7408fe42372d", "heat64": "2020db6c2fc0"}
 
 
 def kernel_source_tag(key):
@@ -158,7 +158,7 @@ def named_workload(name):
 # DRAM bytes (read + write) of one launch at a workload, from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum; writes still dirty in L2 when the kernel ends
 # are not counted), with the source tag of the kernel it was captured on (see traffic()).
-TRAFFIC = {("vdp_mu_n1e6", "step"): (227.90e6, "ebe15e385cf4")}
+TRAFFIC = {("vdp_mu_n1e6", "step"): (227.47e6, "cd813b12904d")}
 # Each SM's FP64 pipe completes 2 FP64 instructions (one lane each) per clock: the recipe's
 # nominal 1.25 TFLOP/s FP64 of GB300 is 6.25e11 FMA/s = 1.99 per clock per SM at 152 SMs and
 # 2070 MHz.  bench.py measures the rate live (measure_fp64_rate) and reports it beside the peak.
@@ -806,9 +806,26 @@ def run_forms(args, hbm):
             return torch.autograd.grad(cc, (xg, mu), grad_outputs=wv)
     except Exception as e:  # graph capture unavailable: report the eager form only
         graph_err = "%s: %s" % (type(e).__name__, e)
+    # the whole step (forward and backward) captured once in one CUDA graph over the static x,
+    # mu and w, as a training loop that replays its step would: no input copy, no Python
+    whole = None
+    try:
+        cs = torch.cuda.Stream()
+        cs.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(cs):
+            for _ in range(3):
+                ad_step()
+        torch.cuda.current_stream().wait_stream(cs)
+        wg = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(wg):
+            whole_out = ad_step()   # noqa: F841 (the graph's outputs stay alive with it)
+        whole = wg.replay
+    except Exception as e:
+        whole_err = "%s: %s" % (type(e).__name__, e)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     res = {}
-    fns = [("autograd", ad_step), ("plain", plain_step)] + ([("graphed", graphed)] if graphed else [])
+    fns = ([("autograd", ad_step), ("plain", plain_step)] + ([("graphed", graphed)] if graphed else [])
+           + ([("whole_graph", whole)] if whole else []))
     for nm, fn in fns:
         for _ in range(3):
             fn()
@@ -829,6 +846,12 @@ def run_forms(args, hbm):
         out["adjoint"].update(autograd_graphed_ms=res["graphed"], graphed_overhead=res["graphed"] / res["plain"])
     else:
         out["adjoint"]["graphed_error"] = graph_err
+    if "whole_graph" in res:
+        out["adjoint"].update(whole_step_graph_ms=res["whole_graph"],
+                              whole_step_graph_overhead=res["whole_graph"] / res["plain"],
+                              whole_step_graph="forward + backward captured in one CUDA graph over static x, mu, w")
+    else:
+        out["adjoint"]["whole_step_graph_error"] = whole_err
     return out
 
 

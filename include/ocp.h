@@ -345,6 +345,14 @@ ocp_status ocp_kkt_values(ocp_t* h, const double* hvals, const double* jvals, co
 ocp_status ocp_vjp_param(ocp_t* h, const double* x, const double* w, double* Jtw, double* dmu,
                          void* stream);
 
+/* eval_cons and ocp_vjp_param with params[0] (Van der Pol mu) read from the device scalar p0
+ * for this call only (NULL: the handle's current value or binding): one call each for the
+ * forward and backward of the differentiation form, c(x; mu) and (J^T w, (dc/dmu)^T w), with
+ * mu a device tensor.  Other models: OCP_EMODEL when p0 is given (ocp_vjp_param_p: always). */
+ocp_status ocp_eval_cons_p(ocp_t* h, const double* x, const double* p0, double* c, void* stream);
+ocp_status ocp_vjp_param_p(ocp_t* h, const double* x, const double* w, const double* p0, double* Jtw,
+                           double* dmu, void* stream);
+
 /* Set the value of params[0] (e.g. Van der Pol mu) without rebuilding the pattern. */
 ocp_status ocp_set_param0(ocp_t* h, double value);
 

@@ -5,7 +5,8 @@
 
 Every forward and backward step is one launch of the CUDA library; node states are
 recomputed from x in each kernel, never stored.  Derivatives:
-  constraints   backward:  (J^T w, (dc/dmu)^T w)                 ocp_vjp_param / jtprod
+  constraints   forward:   c(x; mu)                              ocp_eval_cons_p
+                backward:  (J^T w, (dc/dmu)^T w)                 ocp_vjp_param_p / jtprod
                 double backward, for cotangents (gx, gmu) of that pair:
                   w-bar  = J gx + (dc/dmu) gmu                    ocp_jprod_param
                   x-bar  = (sum_r w_r Hess c_r) gx + gmu m(x, w)   ocp_hprod_param (sigma = 0)
@@ -33,8 +34,7 @@ class _ConsVJP(torch.autograd.Function):
         ctx.save_for_backward(x, mu, w)
         w = w.contiguous()
         if H.model == "vdp":
-            with H.param0(mu.reshape(1)):
-                gx, gmu = H.vjp_param(x, w)
+            gx, gmu = H.vjp_param_p(x, w, mu.reshape(1))
             return gx, gmu.reshape(mu.shape)
         return H.jtprod(x, w), torch.zeros_like(mu)
 
@@ -60,15 +60,19 @@ class _Constraints(torch.autograd.Function):
     def forward(ctx, H: OCP, x, mu):
         ctx.H = H
         ctx.save_for_backward(x, mu)
-        if H.model == "vdp":
-            with H.param0(mu.reshape(1)):
-                return H.eval_cons(x)
-        return H.eval_cons(x)
+        return H.eval_cons_p(x, mu.reshape(1) if H.model == "vdp" else None)
 
     @staticmethod
     def backward(ctx, gc):
         x, mu = ctx.saved_tensors
-        gx, gmu = _ConsVJP.apply(ctx.H, x, mu, gc.contiguous())
+        H = ctx.H
+        if torch.is_grad_enabled():   # create_graph: the backward itself is differentiated
+            gx, gmu = _ConsVJP.apply(H, x, mu, gc.contiguous())
+        elif H.model == "vdp":        # one launch: J^T w and (dc/dmu)^T w
+            gx, gmu = H.vjp_param_p(x, gc.contiguous(), mu.reshape(1))
+            gmu = gmu.reshape(mu.shape)
+        else:
+            gx, gmu = H.jtprod(x, gc.contiguous()), torch.zeros_like(mu)
         return None, gx, gmu
 
 

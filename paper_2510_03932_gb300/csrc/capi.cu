@@ -587,6 +587,36 @@ ocp_status ocp_value_layout(const ocp_t* h, int64_t* nb, int32_t* row_count, int
   return OCP_OK;
 }
 
+// The handle reads params[0] from the device scalar p0 for the duration of one call (the
+// launch copies the pointer into its arguments, so the previous binding returns right after).
+struct ParamScope {
+  ocp* h;
+  const double* prev;
+  ParamScope(ocp* hh, const double* p0) : h(hh), prev(hh->p0_dev) { if (p0) h->p0_dev = p0; }
+  ~ParamScope() { h->p0_dev = prev; }
+};
+
+ocp_status ocp_eval_cons_p(ocp_t* h, const double* x, const double* p0, double* cv, void* stream) {
+  if (!h) return OCP_EINVAL;
+  NEED(x); NEED(cv); OPT(p0);
+  if (p0 && h->model != OCP_MODEL_VDP) return set_err(h, OCP_EMODEL, "a device parameter is provided for the Van der Pol model");
+  ParamScope ps(h, p0);
+  EvalCall c = full_call(h);
+  c.x = x; c.c = cv;
+  return dispatch_eval(h, O_C, c, stream);
+}
+
+ocp_status ocp_vjp_param_p(ocp_t* h, const double* x, const double* w, const double* p0, double* Jtw, double* dmu,
+                           void* stream) {
+  if (!h) return OCP_EINVAL;
+  if (h->model != OCP_MODEL_VDP) return set_err(h, OCP_EMODEL, "parameter derivative is provided for the Van der Pol model");
+  NEED(x); NEED(w); NEED(dmu); NEED(Jtw); OPT(p0);
+  ParamScope ps(h, p0);
+  ProdCall c;
+  c.kind = P_JTPROD; c.x = x; c.v = w; c.out = Jtw; c.dmu = dmu;
+  return dispatch_prod(h, c, stream);
+}
+
 ocp_status ocp_vjp_param(ocp_t* h, const double* x, const double* w, double* Jtw, double* dmu, void* stream) {
   if (!h) return OCP_EINVAL;
   if (h->model != OCP_MODEL_VDP) return set_err(h, OCP_EMODEL, "parameter derivative is provided for the Van der Pol model");

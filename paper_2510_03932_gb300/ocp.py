@@ -81,6 +81,8 @@ _SIGS = {
     "ocp_sum_ordered": [_P, C.c_int, _P, _P],
     "ocp_value_layout": [_P, C.POINTER(_I64), _P, C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
     "ocp_vjp_param": [_P, _P, _P, _P, _P, _P],
+    "ocp_eval_cons_p": [_P, _P, _P, _P, _P],
+    "ocp_vjp_param_p": [_P, _P, _P, _P, _P, _P, _P],
     "ocp_set_param0": [_P, _D],
     "ocp_bind_param0": [_P, _P],
     "ocp_jprod_param": [_P, _P, _P, _P, _P, _P],
@@ -135,8 +137,13 @@ def sum_ordered(parts, out, stream=None):
     return out
 
 
+_raw_stream = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+
+
 def _stream(stream):
     if stream is None:
+        if _raw_stream is not None:   # the current stream's handle without a Stream object
+            return _raw_stream(torch.cuda.current_device())
         stream = torch.cuda.current_stream()
     return C.c_void_p(stream.cuda_stream)
 
@@ -478,6 +485,24 @@ class OCP:
         Jtw = self._out(Jtw, self.n, "Jtw")
         dmu = self._out(dmu, 1, "dmu")
         _check(lib().ocp_vjp_param(self.h, _ptr(x), _ptr(w), _ptr(Jtw), _ptr(dmu), _stream(stream)), self.h)
+        return Jtw, dmu
+
+    def eval_cons_p(self, x, p0, out=None, stream=None):
+        """c(x) with params[0] (Van der Pol mu) read from the one-element CUDA tensor p0 for this
+        call (ocp_eval_cons_p; p0 None: the handle's value)."""
+        x = self._vec(x, self.n, "x"); p0 = self._scalar(p0, "p0")
+        out = self._out(out, self.m, "c")
+        _check(lib().ocp_eval_cons_p(self.h, _ptr(x), _ptr(p0), _ptr(out), _stream(stream)), self.h)
+        return out
+
+    def vjp_param_p(self, x, w, p0, Jtw=None, dmu=None, stream=None):
+        """(J^T w, (dc/dmu)^T w) with mu read from the CUDA scalar p0 for this call
+        (ocp_vjp_param_p)."""
+        x = self._vec(x, self.n, "x"); w = self._vec(w, self.m, "w"); p0 = self._scalar(p0, "p0")
+        Jtw = self._out(Jtw, self.n, "Jtw")
+        dmu = self._out(dmu, 1, "dmu")
+        _check(lib().ocp_vjp_param_p(self.h, _ptr(x), _ptr(w), _ptr(p0), _ptr(Jtw), _ptr(dmu), _stream(stream)),
+               self.h)
         return Jtw, dmu
 
     def set_param0(self, value: float):

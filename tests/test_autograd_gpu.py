@@ -103,3 +103,56 @@ def test_param_binding_is_scoped(mods):
     torch.cuda.synchronize()
     assert torch.equal(c_after, c_host)
     assert not torch.equal(c_dev, c_host)
+
+
+def test_first_order_backward_equals_differentiable_backward(mods):
+    """Without create_graph the backward is one direct launch (ocp_vjp_param_p); with it, the
+    differentiable _ConsVJP Function.  Both run the same kernel: bit-identical results."""
+    ocp, A = mods
+    w, d = small("vdp_n1e3", 700, params=[0.8])
+    H = ocp.OCP.from_workload(w)
+    x = torch.from_numpy(d["x"]).cuda().requires_grad_(True)
+    mu = torch.tensor([0.8], dtype=torch.float64, device="cuda", requires_grad=True)
+    wv = torch.from_numpy(d["vm"]).cuda()
+    g1 = torch.autograd.grad(A.constraints(H, x, mu), (x, mu), grad_outputs=wv)
+    g2 = torch.autograd.grad(A.constraints(H, x, mu), (x, mu), grad_outputs=wv, create_graph=True)
+    assert torch.equal(g1[0], g2[0].detach()) and torch.equal(g1[1], g2[1].detach())
+    # mu read from the device tensor: a different mu changes both outputs
+    mu2 = torch.tensor([1.1], dtype=torch.float64, device="cuda", requires_grad=True)
+    g3 = torch.autograd.grad(A.constraints(H, x, mu2), (x, mu2), grad_outputs=wv)
+    assert not torch.equal(g1[0], g3[0])
+    H.close()
+
+
+def test_whole_step_graph_replay_matches_eager(mods):
+    """Forward and backward captured once in a CUDA graph over static x, mu, w; a replay after
+    new values are copied into them equals the eager step bit for bit."""
+    ocp, A = mods
+    w, d = small("vdp_n1e3", 2000, params=[1.0])
+    H = ocp.OCP.from_workload(w)
+    xs = torch.from_numpy(d["x"]).cuda().requires_grad_(True)
+    mus = torch.tensor([1.0], dtype=torch.float64, device="cuda", requires_grad=True)
+    ws = torch.from_numpy(d["vm"]).cuda()
+
+    def step():
+        return torch.autograd.grad(A.constraints(H, xs, mus), (xs, mus), grad_outputs=ws)
+
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        for _ in range(3):
+            step()
+    torch.cuda.current_stream().wait_stream(s)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        gx, gmu = step()
+    d2 = synth.draw(w, seed=w["seed"] + 5)
+    with torch.no_grad():
+        xs.copy_(torch.from_numpy(d2["x"]))
+        mus.fill_(0.7)
+        ws.copy_(torch.from_numpy(d2["vm"]))
+    g.replay()
+    torch.cuda.synchronize()
+    ex, emu = step()
+    assert torch.equal(gx, ex) and torch.equal(gmu, emu)
+    H.close()
