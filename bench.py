@@ -98,7 +98,7 @@ FP64_OPS_PER_NODE = {("vdp", "eval_all"): 26.6, ("vdp", "jh"): 10.0, ("vdp", "jp
 # The kernel sources of each model key (paths under the package's csrc/): the tile body and
 # the helpers it includes, the model's device functor, the translation unit that instantiates
 # its kernels.
-_COMMON = ["node_kernels.cuh", "model_base.cuh", "ocp_internal.h"]
+_COMMON = ["node_kernels.cuh", "model_base.cuh", "kernel_config.h"]
 KERNEL_SOURCES = {
     "vdp": _COMMON + ["model_vdp.cuh", "node_vdp.cu"],
     "vdp:euler": _COMMON + ["model_vdp.cuh", "node_vdp.cu"],
@@ -108,8 +108,8 @@ KERNEL_SOURCES = {
     "heat64": _COMMON + ["heat_kernels.cu"],
 }
 # Tags of the sources the FP64_OPS_PER_NODE counts (and TRAFFIC) were measured on.
-FP64_OPS_SRC = {"vdp": "cd813b12904d", "vdp:euler": "cd813b12904d", "cartpole": "d12f7a727dda",
-                "quadrotor": "89f823db6a42", "goddard": "7408fe42372d", "heat64": "2020db6c2fc0"}
+FP64_OPS_SRC = {"vdp": "21d91bd08c73", "vdp:euler": "21d91bd08c73", "cartpole": "562799f88bbb",
+                "quadrotor": "bdc6cdbee3b3", "goddard": "42f15ba48a09", "heat64": "f1980677f8c3"}
 
 
 def kernel_source_tag(key):
@@ -158,7 +158,7 @@ def named_workload(name):
 # DRAM bytes (read + write) of one launch at a workload, from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum; writes still dirty in L2 when the kernel ends
 # are not counted), with the source tag of the kernel it was captured on (see traffic()).
-TRAFFIC = {("vdp_mu_n1e6", "step"): (227.47e6, "cd813b12904d")}
+TRAFFIC = {("vdp_mu_n1e6", "step"): (227.47e6, "21d91bd08c73")}
 # Each SM's FP64 pipe completes 2 FP64 instructions (one lane each) per clock: the recipe's
 # nominal 1.25 TFLOP/s FP64 of GB300 is 6.25e11 FMA/s = 1.99 per clock per SM at 152 SMs and
 # 2070 MHz.  bench.py measures the rate live (measure_fp64_rate) and reports it beside the peak.

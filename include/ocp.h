@@ -447,6 +447,18 @@ ocp_status ocp_value_layout(const ocp_t* h, int64_t* nb, int32_t* row_count, int
 ocp_status ocp_eval_obj_noalloc(const ocp_dynamics* dyn, const ocp_cost* cost, int nx, int nu, int64_t N,
                                 double T, const double* x, double* f, void* stream);
 
+/* Host-side fault injection, for testing the error paths of callers and of the library (the
+ * paper has no counterpart).  spec: "alloc:K" makes the K-th device allocation of the library
+ * from now on fail (the call reports OCP_ENOMEM), "upload:K" the K-th host-to-device upload of
+ * its tables (OCP_ECUDA), "dims" the next pattern build (OCP_EDIM, as for a problem too large
+ * for the int32 ABI); "" disarms.  The failure is made on the host before any CUDA call; each
+ * specification fires once.  The environment variable OCP_FAULT with the same syntax arms a
+ * fault at the library's first allocation or upload.  The failing call's message ends with
+ * "(injected by OCP_FAULT)".  A handle being created is released; a setter that fails after it
+ * has started to rebuild the pattern leaves the handle unusable: every later call on it but
+ * ocp_destroy and ocp_last_error returns OCP_EINVAL.  Errors: OCP_EINVAL for a bad spec. */
+ocp_status ocp_set_fault(const char* spec);
+
 /* Message of the last failure on this handle (NULL: of the last failed create). */
 const char* ocp_last_error(const ocp_t* h);
 

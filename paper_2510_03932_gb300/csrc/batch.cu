@@ -175,14 +175,19 @@ struct ocp_batch_impl {
   int64_t partials_cap = 0;
   unsigned* d_counter = nullptr;
   cudaGraphExec_t graph = nullptr;
+  // set when the tile offsets failed to reach the device after a configuration change: the
+  // device tables then disagree with the host's and every evaluation refuses the batch until
+  // a configuration is set successfully
+  bool unusable = false;
   std::string err;
 };
 
 struct ocp_batch : ocp_batch_impl {};
 
 static ocp_status berr(ocp_batch* b, ocp_status st, const std::string& m) {
-  if (b) b->err = m;
-  return set_err(nullptr, st, m);
+  const ocp_status s = set_err(nullptr, st, m);  // (marks a fault injected by OCP_FAULT)
+  if (b) b->err = ocp_last_error(nullptr);
+  return s;
 }
 
 template <class M>
@@ -194,9 +199,9 @@ static ocp_status batch_upload_inst(ocp_batch* b) {
     inst[i].E = b->items[i]->N + 1;
     inst[i].p0_dev = nullptr;
   }
-  cudaError_t e = cudaMalloc(&b->d_inst, sizeof(NodeArgs<M>) * b->count);
+  cudaError_t e = ocpg::dev_malloc(&b->d_inst, sizeof(NodeArgs<M>) * b->count);
   if (e != cudaSuccess) return berr(b, OCP_ENOMEM, "cudaMalloc(batch instances)");
-  e = cudaMemcpy(b->d_inst, inst.data(), sizeof(NodeArgs<M>) * b->count, cudaMemcpyHostToDevice);
+  e = ocpg::dev_upload(b->d_inst, inst.data(), sizeof(NodeArgs<M>) * b->count);
   if (e != cudaSuccess) return berr(b, OCP_ECUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(e));
   // allow the largest shared-memory request of every configuration once
   for (const auto& cf : kConfigs) {
@@ -213,8 +218,12 @@ static ocp_status batch_tiles(ocp_batch* b) {
   for (int i = 0; i < b->count; ++i) b->tileoff[i + 1] = b->tileoff[i] + (b->items[i]->N + 1 + owned - 1) / owned;
   b->ntiles = b->tileoff[b->count];
   if (b->ntiles > b->partials_cap) return berr(b, OCP_EDIM, "tile count exceeds the partial-sum buffer");
-  cudaError_t e = cudaMemcpy(b->d_tileoff, b->tileoff.data(), sizeof(int64_t) * (b->count + 1), cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) return berr(b, OCP_ECUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(e));
+  cudaError_t e = ocpg::dev_upload(b->d_tileoff, b->tileoff.data(), sizeof(int64_t) * (b->count + 1));
+  if (e != cudaSuccess) {
+    b->unusable = true;
+    return berr(b, OCP_ECUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(e));
+  }
+  b->unusable = false;   // a later successful configuration makes the batch usable again
   return OCP_OK;
 }
 
@@ -274,6 +283,7 @@ static void batch_free(ocp_batch* b) {
 extern "C" {
 
 ocp_status ocp_batch_create(ocp_t* const* items, int count, ocp_batch_t** out) {
+  OCP_RANGE();
   if (!out) return set_err(nullptr, OCP_EINVAL, "out is NULL");
   *out = nullptr;
   if (!items || count < 1) return set_err(nullptr, OCP_EINVAL, "need at least one problem");
@@ -282,6 +292,7 @@ ocp_status ocp_batch_create(ocp_t* const* items, int count, ocp_batch_t** out) {
     return set_err(nullptr, OCP_EMODEL, "batched evaluation is provided for the cart-pole and Van der Pol models");
   for (int i = 0; i < count; ++i) {
     if (!items[i]) return set_err(nullptr, OCP_EINVAL, "NULL problem in the batch");
+    if (items[i]->unusable) return set_err(nullptr, OCP_EINVAL, "a problem of the batch is unusable after a failed setter");
     if (items[i]->model != model) return set_err(nullptr, OCP_EMODEL, "all problems of a batch must share the model");
     if (items[i]->scheme != OCP_SCHEME_TRAPEZOID)
       return set_err(nullptr, OCP_EMODEL, "batched evaluation is provided for the trapezoidal scheme");
@@ -305,18 +316,19 @@ ocp_status ocp_batch_create(ocp_t* const* items, int count, ocp_batch_t** out) {
     cap += (items[i]->N + 1 + 62) / 63;  // tiles of the smallest configuration (64 threads, 1 node)
   }
   b->partials_cap = cap;
-  cudaError_t e;
-  auto up = [&](int64_t** d, const std::vector<int64_t>& h) -> bool {
-    if (cudaMalloc(d, sizeof(int64_t) * h.size()) != cudaSuccess) return false;
-    return cudaMemcpy(*d, h.data(), sizeof(int64_t) * h.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+  cudaError_t e = cudaSuccess;
+  auto up = [&](int64_t** d, const std::vector<int64_t>& h) -> cudaError_t {
+    const cudaError_t r = ocpg::dev_malloc(d, sizeof(int64_t) * h.size());
+    return r != cudaSuccess ? r : ocpg::dev_upload(*d, h.data(), sizeof(int64_t) * h.size());
   };
-  if (!up(&b->d_xoff, b->xoff) || !up(&b->d_coff, b->coff) || !up(&b->d_joff, b->joff) || !up(&b->d_hoff, b->hoff) ||
-      cudaMalloc(&b->d_tileoff, sizeof(int64_t) * (count + 1)) != cudaSuccess ||
-      cudaMalloc(&b->d_partials, sizeof(double) * cap) != cudaSuccess ||
-      cudaMalloc(&b->d_counter, sizeof(unsigned) * (4 + count)) != cudaSuccess ||
+  if ((e = up(&b->d_xoff, b->xoff)) != cudaSuccess || (e = up(&b->d_coff, b->coff)) != cudaSuccess ||
+      (e = up(&b->d_joff, b->joff)) != cudaSuccess || (e = up(&b->d_hoff, b->hoff)) != cudaSuccess ||
+      (e = ocpg::dev_malloc(&b->d_tileoff, sizeof(int64_t) * (count + 1))) != cudaSuccess ||
+      (e = ocpg::dev_malloc(&b->d_partials, sizeof(double) * cap)) != cudaSuccess ||
+      (e = ocpg::dev_malloc(&b->d_counter, sizeof(unsigned) * (4 + count))) != cudaSuccess ||
       (e = cudaMemset(b->d_counter, 0, sizeof(unsigned) * (4 + count))) != cudaSuccess) {
     batch_free(b);
-    return set_err(nullptr, OCP_ENOMEM, "device allocation failed for the batch");
+    return cuda_err(nullptr, e, "batch tables");   // OCP_ENOMEM for a failed allocation
   }
   ocp_status st = (model == OCP_MODEL_CARTPOLE) ? batch_upload_inst<CartPole>(b) : batch_upload_inst<VdP>(b);
   if (st == OCP_OK) st = batch_tiles(b);
@@ -328,6 +340,7 @@ ocp_status ocp_batch_create(ocp_t* const* items, int count, ocp_batch_t** out) {
 void ocp_batch_destroy(ocp_batch_t* b) { batch_free(b); }
 
 ocp_status ocp_batch_offsets(const ocp_batch_t* b, int64_t* xoff, int64_t* coff, int64_t* joff, int64_t* hoff) {
+  OCP_RANGE();
   if (!b) return OCP_EINVAL;
   for (int i = 0; i <= b->count; ++i) {
     if (xoff) xoff[i] = b->xoff[i];
@@ -339,6 +352,7 @@ ocp_status ocp_batch_offsets(const ocp_batch_t* b, int64_t* xoff, int64_t* coff,
 }
 
 ocp_status ocp_batch_set_config(ocp_batch_t* b, int nodes_per_thread, int threads, int ctas_per_sm) {
+  OCP_RANGE();
   if (!b) return OCP_EINVAL;
   if ((nodes_per_thread != 1 && nodes_per_thread != 2) || (threads != 64 && threads != 128 && threads != 256) ||
       ctas_per_sm < 0)
@@ -351,6 +365,7 @@ ocp_status ocp_batch_set_config(ocp_batch_t* b, int nodes_per_thread, int thread
 }
 
 ocp_status ocp_batch_get_config(const ocp_batch_t* b, int* nodes_per_thread, int* threads, int* ctas_per_sm) {
+  OCP_RANGE();
   if (!b) return OCP_EINVAL;
   if (nodes_per_thread) *nodes_per_thread = b->npt;
   if (threads) *threads = b->threads;
@@ -360,7 +375,9 @@ ocp_status ocp_batch_get_config(const ocp_batch_t* b, int* nodes_per_thread, int
 
 ocp_status ocp_batch_eval_all(ocp_batch_t* b, const double* x, const double* y, double sigma, double* f, double* c,
                               double* g, double* jvals, double* hvals, void* stream) {
+  OCP_RANGE();
   if (!b) return OCP_EINVAL;
+  if (b->unusable) return berr(b, OCP_EINVAL, "batch unusable after a failed configuration change");
   if (!x) return berr(b, OCP_EINVAL, "x is NULL");
   if (hvals && !y) return berr(b, OCP_EINVAL, "y is required for Hessian values");
   return dispatch_batch(b, x, y, sigma, f, c, g, jvals, hvals, (cudaStream_t)stream);
@@ -368,7 +385,9 @@ ocp_status ocp_batch_eval_all(ocp_batch_t* b, const double* x, const double* y, 
 
 ocp_status ocp_batch_autotune(ocp_batch_t* b, const double* x, const double* y, double sigma, double* f, double* c,
                               double* g, double* jvals, double* hvals, void* stream, double* best_ms) {
+  OCP_RANGE();
   if (!b) return OCP_EINVAL;
+  if (b->unusable) return berr(b, OCP_EINVAL, "batch unusable after a failed configuration change");
   cudaStream_t s = (cudaStream_t)stream;
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
@@ -406,7 +425,9 @@ ocp_status ocp_batch_autotune(ocp_batch_t* b, const double* x, const double* y, 
 
 ocp_status ocp_batch_graph_capture(ocp_batch_t* b, const double* x, const double* y, double sigma, double* f, double* c,
                                    double* g, double* jvals, double* hvals, void* stream) {
+  OCP_RANGE();
   if (!b) return OCP_EINVAL;
+  if (b->unusable) return berr(b, OCP_EINVAL, "batch unusable after a failed configuration change");
   if (!stream) return berr(b, OCP_EINVAL, "graph capture needs a created (non-default) stream");
   cudaStream_t s = (cudaStream_t)stream;
   if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
@@ -424,7 +445,9 @@ ocp_status ocp_batch_graph_capture(ocp_batch_t* b, const double* x, const double
 }
 
 ocp_status ocp_batch_graph_launch(ocp_batch_t* b, void* stream) {
+  OCP_RANGE();
   if (!b) return OCP_EINVAL;
+  if (b->unusable) return berr(b, OCP_EINVAL, "batch unusable after a failed configuration change");
   if (!b->graph) return berr(b, OCP_EINVAL, "no captured graph");
   cudaError_t e = cudaGraphLaunch(b->graph, (cudaStream_t)stream);
   if (e != cudaSuccess) return berr(b, OCP_ECUDA, std::string("cudaGraphLaunch: ") + cudaGetErrorString(e));

@@ -143,15 +143,15 @@ ocp_status bin_upload(ocp* h) {
   if (bv.empty()) bv.push_back(0);
   if (coef.empty()) coef.push_back(0.0);
   cudaError_t e;
-  if ((e = cudaMalloc(&h->d_boff, boff.size() * 4)) != cudaSuccess ||
-      (e = cudaMalloc(&h->d_bv, bv.size() * 4)) != cudaSuccess ||
-      (e = cudaMalloc(&h->d_bcoef, coef.size() * 8)) != cudaSuccess ||
-      (e = cudaMalloc(&h->d_bbase, base.size() * 8)) != cudaSuccess)
+  if ((e = ocpg::dev_malloc(&h->d_boff, boff.size() * 4)) != cudaSuccess ||
+      (e = ocpg::dev_malloc(&h->d_bv, bv.size() * 4)) != cudaSuccess ||
+      (e = ocpg::dev_malloc(&h->d_bcoef, coef.size() * 8)) != cudaSuccess ||
+      (e = ocpg::dev_malloc(&h->d_bbase, base.size() * 8)) != cudaSuccess)
     return cuda_err(h, e, "cudaMalloc(boundary inequality tables)");
-  if ((e = cudaMemcpy(h->d_boff, boff.data(), boff.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (e = cudaMemcpy(h->d_bv, bv.data(), bv.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (e = cudaMemcpy(h->d_bcoef, coef.data(), coef.size() * 8, cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (e = cudaMemcpy(h->d_bbase, base.data(), base.size() * 8, cudaMemcpyHostToDevice)) != cudaSuccess)
+  if ((e = ocpg::dev_upload(h->d_boff, boff.data(), boff.size() * 4)) != cudaSuccess ||
+      (e = ocpg::dev_upload(h->d_bv, bv.data(), bv.size() * 4)) != cudaSuccess ||
+      (e = ocpg::dev_upload(h->d_bcoef, coef.data(), coef.size() * 8)) != cudaSuccess ||
+      (e = ocpg::dev_upload(h->d_bbase, base.data(), base.size() * 8)) != cudaSuccess)
     return cuda_err(h, e, "cudaMemcpy(boundary inequality tables)");
   return OCP_OK;
 }

@@ -17,14 +17,22 @@ static thread_local std::string g_create_err;
 namespace ocpg {
 
 ocp_status set_err(ocp* h, ocp_status st, const std::string& msg) {
-  if (h) h->err = msg;
-  else g_create_err = msg;
+  const std::string m = take_injected() ? msg + " (injected by OCP_FAULT)" : msg;
+  if (h) h->err = m;
+  else g_create_err = m;
   return st;
 }
 
 ocp_status cuda_err(ocp* h, cudaError_t e, const char* what) {
   if (e == cudaSuccess) return OCP_OK;
-  return set_err(h, OCP_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  return set_err(h, e == cudaErrorMemoryAllocation ? OCP_ENOMEM : OCP_ECUDA,
+                 std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+ocp_status unusable_err(const ocp* h) {
+  ocp* m = const_cast<ocp*>(h);
+  if (m->err.rfind("handle unusable", 0) != 0) m->err = "handle unusable after a failed setter: " + m->err;
+  return OCP_EINVAL;
 }
 
 // One CTA per tile: the hardware block scheduler balances the tail.  (Results do not depend
@@ -126,30 +134,39 @@ static ocp_status upload_tables(ocp* h) {
   for (auto& e : P.hent) { he.push_back(e.first); he.push_back(e.second); }
   if (he.empty()) he.push_back(0);
   cudaError_t e;
-  if ((e = cudaMalloc(&h->d_rowtmpl, rt.size() * sizeof(int32_t))) != cudaSuccess) return cuda_err(h, e, "cudaMalloc");
-  if ((e = cudaMalloc(&h->d_jbase, P.jbase.size() * sizeof(int64_t))) != cudaSuccess) return cuda_err(h, e, "cudaMalloc");
-  if ((e = cudaMalloc(&h->d_hent, he.size() * sizeof(int32_t))) != cudaSuccess) return cuda_err(h, e, "cudaMalloc");
-  if ((e = cudaMemcpy(h->d_rowtmpl, rt.data(), rt.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
+  if ((e = ocpg::dev_malloc(&h->d_rowtmpl, rt.size() * sizeof(int32_t))) != cudaSuccess) return cuda_err(h, e, "cudaMalloc");
+  if ((e = ocpg::dev_malloc(&h->d_jbase, P.jbase.size() * sizeof(int64_t))) != cudaSuccess) return cuda_err(h, e, "cudaMalloc");
+  if ((e = ocpg::dev_malloc(&h->d_hent, he.size() * sizeof(int32_t))) != cudaSuccess) return cuda_err(h, e, "cudaMalloc");
+  if ((e = ocpg::dev_upload(h->d_rowtmpl, rt.data(), rt.size() * 4)) != cudaSuccess)
     return cuda_err(h, e, "cudaMemcpy");
-  if ((e = cudaMemcpy(h->d_jbase, P.jbase.data(), P.jbase.size() * 8, cudaMemcpyHostToDevice)) != cudaSuccess)
+  if ((e = ocpg::dev_upload(h->d_jbase, P.jbase.data(), P.jbase.size() * 8)) != cudaSuccess)
     return cuda_err(h, e, "cudaMemcpy");
-  if ((e = cudaMemcpy(h->d_hent, he.data(), he.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
+  if ((e = ocpg::dev_upload(h->d_hent, he.data(), he.size() * 4)) != cudaSuccess)
     return cuda_err(h, e, "cudaMemcpy");
   std::vector<int32_t> fin(P.fin.begin(), P.fin.end()), tcol(P.tcol.begin(), P.tcol.end());
   if (fin.empty()) fin.push_back(0);
   if (tcol.empty()) tcol.push_back(0);
-  if ((e = cudaMalloc(&h->d_fin, fin.size() * sizeof(int32_t))) != cudaSuccess) return cuda_err(h, e, "cudaMalloc");
-  if ((e = cudaMalloc(&h->d_tcol, tcol.size() * sizeof(int32_t))) != cudaSuccess) return cuda_err(h, e, "cudaMalloc");
-  if ((e = cudaMemcpy(h->d_fin, fin.data(), fin.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
+  if ((e = ocpg::dev_malloc(&h->d_fin, fin.size() * sizeof(int32_t))) != cudaSuccess) return cuda_err(h, e, "cudaMalloc");
+  if ((e = ocpg::dev_malloc(&h->d_tcol, tcol.size() * sizeof(int32_t))) != cudaSuccess) return cuda_err(h, e, "cudaMalloc");
+  if ((e = ocpg::dev_upload(h->d_fin, fin.data(), fin.size() * 4)) != cudaSuccess)
     return cuda_err(h, e, "cudaMemcpy");
-  if ((e = cudaMemcpy(h->d_tcol, tcol.data(), tcol.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
+  if ((e = ocpg::dev_upload(h->d_tcol, tcol.data(), tcol.size() * 4)) != cudaSuccess)
     return cuda_err(h, e, "cudaMemcpy");
-  if ((e = cudaMalloc(&h->d_kcbase, P.kcbase.size() * sizeof(int64_t))) != cudaSuccess)
+  if ((e = ocpg::dev_malloc(&h->d_kcbase, P.kcbase.size() * sizeof(int64_t))) != cudaSuccess)
     return cuda_err(h, e, "cudaMalloc");
-  if ((e = cudaMemcpy(h->d_kcbase, P.kcbase.data(), P.kcbase.size() * 8, cudaMemcpyHostToDevice)) != cudaSuccess)
+  if ((e = ocpg::dev_upload(h->d_kcbase, P.kcbase.data(), P.kcbase.size() * 8)) != cudaSuccess)
     return cuda_err(h, e, "cudaMemcpy");
   ocp_status st = path_upload(h);
   return st == OCP_OK ? bin_upload(h) : st;
+}
+
+// Rebuilds the pattern and its device tables after a setter changed the problem; a failure
+// part-way leaves the handle unusable.
+static ocp_status rebuild(ocp* h) {
+  std::string why;
+  ocp_status st = build_pattern(h, why) ? upload_tables(h) : set_err(h, OCP_EDIM, why);
+  if (st != OCP_OK) h->unusable = true;
+  return st;
 }
 
 static int model_nparams(int model) {
@@ -245,6 +262,7 @@ extern "C" {
 
 ocp_status ocp_create(const ocp_dynamics* dyn, const ocp_cost* cost, int nx, int nu, int64_t N, double T,
                       ocp_t** out) {
+  OCP_RANGE();
   if (!out) return set_err(nullptr, OCP_EINVAL, "out is NULL");
   *out = nullptr;
   ocp* h = new (std::nothrow) ocp();
@@ -261,8 +279,8 @@ ocp_status ocp_create(const ocp_dynamics* dyn, const ocp_cost* cost, int nx, int
   }
   // one partial per tile of the smallest tile (31 owned nodes), plus slack
   h->max_partials = (int)((N + 1) / 31 + 2);
-  if ((e = cudaMalloc(&h->d_partials, sizeof(double) * h->max_partials)) != cudaSuccess ||
-      (e = cudaMalloc(&h->d_counter, sizeof(unsigned))) != cudaSuccess ||
+  if ((e = ocpg::dev_malloc(&h->d_partials, sizeof(double) * h->max_partials)) != cudaSuccess ||
+      (e = ocpg::dev_malloc(&h->d_counter, sizeof(unsigned))) != cudaSuccess ||
       (e = cudaMemset(h->d_counter, 0, sizeof(unsigned))) != cudaSuccess) {
     free_handle(h);
     return set_err(nullptr, OCP_ENOMEM, std::string("device allocation failed: ") + cudaGetErrorString(e));
@@ -276,7 +294,9 @@ ocp_status ocp_create(const ocp_dynamics* dyn, const ocp_cost* cost, int nx, int
 void ocp_destroy(ocp_t* h) { free_handle(h); }
 
 ocp_status ocp_set_boundary(ocp_t* h, const double* x0, const double* xf) {
+  OCP_RANGE();
   if (!h) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
   h->x0.assign(h->nx, 0.0);
   if (x0) h->x0.assign(x0, x0 + h->nx);
   const bool fin = xf != nullptr;
@@ -285,15 +305,15 @@ ocp_status ocp_set_boundary(ocp_t* h, const double* x0, const double* xf) {
   if (fin != h->has_final || !h->fin_comp.empty()) {
     h->has_final = fin;
     h->fin_comp.clear();
-    std::string why;
-    if (!build_pattern(h, why)) return set_err(h, OCP_EDIM, why);
-    return upload_tables(h);
+    return rebuild(h);
   }
   return OCP_OK;
 }
 
 ocp_status ocp_dims(const ocp_t* h, int64_t* n, int64_t* m, int64_t* nnzj, int64_t* nnzh) {
+  OCP_RANGE();
   if (!h) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
   if (n) *n = h->pat.n;
   if (m) *m = h->pat.m;
   if (nnzj) *nnzj = h->pat.nnzj;
@@ -302,7 +322,9 @@ ocp_status ocp_dims(const ocp_t* h, int64_t* n, int64_t* m, int64_t* nnzj, int64
 }
 
 ocp_status ocp_bounds(const ocp_t* h, double* lvar, double* uvar, double* lcon, double* ucon) {
+  OCP_RANGE();
   if (!h) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
   const double inf = std::numeric_limits<double>::infinity();
   const int64_t nxN = (int64_t)h->nx * (h->N + 1), nX = nxN + (int64_t)h->nu * h->pat.nun;
   for (int64_t i = 0; i < h->pat.n; ++i) {
@@ -400,7 +422,9 @@ __global__ void k_sum_ordered(const double* parts, int count, double* out) {
 extern "C" {
 
 ocp_status eval_obj(ocp_t* h, const double* x, double* f, void* stream) {
+  OCP_RANGE();
   if (!h) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
   NEED(x); NEED(f);
   EvalCall c = full_call(h);
   c.x = x; c.f = f;
@@ -408,7 +432,9 @@ ocp_status eval_obj(ocp_t* h, const double* x, double* f, void* stream) {
 }
 
 ocp_status eval_cons(ocp_t* h, const double* x, double* cv, void* stream) {
+  OCP_RANGE();
   if (!h) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
   NEED(x); NEED(cv);
   EvalCall c = full_call(h);
   c.x = x; c.c = cv;
@@ -416,7 +442,9 @@ ocp_status eval_cons(ocp_t* h, const double* x, double* cv, void* stream) {
 }
 
 ocp_status eval_grad(ocp_t* h, const double* x, double* g, void* stream) {
+  OCP_RANGE();
   if (!h) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
   NEED(x); NEED(g);
   EvalCall c = full_call(h);
   c.x = x; c.g = g;
@@ -424,12 +452,16 @@ ocp_status eval_grad(ocp_t* h, const double* x, double* g, void* stream) {
 }
 
 ocp_status jac_coo_structure(const ocp_t* h, int32_t* rows, int32_t* cols, void* stream) {
+  OCP_RANGE();
   if (!h || !rows || !cols) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
   return launch_jac_structure(h, rows, cols, (cudaStream_t)stream);
 }
 
 ocp_status jac_coo_values(ocp_t* h, const double* x, double* vals, void* stream) {
+  OCP_RANGE();
   if (!h) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
   NEED(x); NEED(vals);
   EvalCall c = full_call(h);
   c.x = x; c.jv = vals;
@@ -437,12 +469,16 @@ ocp_status jac_coo_values(ocp_t* h, const double* x, double* vals, void* stream)
 }
 
 ocp_status hess_coo_structure(const ocp_t* h, int32_t* rows, int32_t* cols, void* stream) {
+  OCP_RANGE();
   if (!h || !rows || !cols) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
   return launch_hess_structure(h, rows, cols, (cudaStream_t)stream);
 }
 
 ocp_status hess_coo_values(ocp_t* h, const double* x, const double* y, double sigma, double* vals, void* stream) {
+  OCP_RANGE();
   if (!h) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
   NEED(x); NEED(y); NEED(vals);
   EvalCall c = full_call(h);
   c.x = x; c.y = y; c.sigma = sigma; c.hv = vals;
@@ -450,7 +486,9 @@ ocp_status hess_coo_values(ocp_t* h, const double* x, const double* y, double si
 }
 
 ocp_status jprod(ocp_t* h, const double* x, const double* v, double* Jv, void* stream) {
+  OCP_RANGE();
   if (!h) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
   NEED(x); NEED(v); NEED(Jv);
   ProdCall c;
   c.kind = P_JPROD; c.x = x; c.v = v; c.out = Jv;
@@ -458,7 +496,9 @@ ocp_status jprod(ocp_t* h, const double* x, const double* v, double* Jv, void* s
 }
 
 ocp_status jtprod(ocp_t* h, const double* x, const double* v, double* Jtv, void* stream) {
+  OCP_RANGE();
   if (!h) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
   NEED(x); NEED(v); NEED(Jtv);
   ProdCall c;
   c.kind = P_JTPROD; c.x = x; c.v = v; c.out = Jtv;
@@ -467,7 +507,9 @@ ocp_status jtprod(ocp_t* h, const double* x, const double* v, double* Jtv, void*
 
 ocp_status hprod(ocp_t* h, const double* x, const double* y, double sigma, const double* v, double* Hv,
                  void* stream) {
+  OCP_RANGE();
   if (!h) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
   NEED(x); NEED(y); NEED(v); NEED(Hv);
   ProdCall c;
   c.kind = P_HPROD; c.x = x; c.y = y; c.sigma = sigma; c.v = v; c.out = Hv;
@@ -476,7 +518,9 @@ ocp_status hprod(ocp_t* h, const double* x, const double* y, double sigma, const
 
 ocp_status ocp_eval_all(ocp_t* h, const double* x, const double* y, double sigma, double* f, double* cv, double* g,
                         double* jvals, double* hvals, void* stream) {
+  OCP_RANGE();
   if (!h) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
   NEED(x);
   OPT(f); OPT(cv); OPT(g); OPT(jvals); OPT(hvals);
   if (hvals) NEED(y);
@@ -491,7 +535,9 @@ ocp_status ocp_eval_all(ocp_t* h, const double* x, const double* y, double sigma
 ocp_status ocp_eval_step(ocp_t* h, const double* x, const double* y, double sigma, const double* vn, const double* vm,
                          double* f, double* cv, double* g, double* jvals, double* hvals, double* Jv, double* Jtv,
                          double* Hv, void* stream) {
+  OCP_RANGE();
   if (!h) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
   NEED(x); NEED(y); NEED(vn); NEED(vm); NEED(f); NEED(cv); NEED(g); NEED(jvals); NEED(hvals);
   NEED(Jv); NEED(Jtv); NEED(Hv);
   if (h->model == OCP_MODEL_HEAT1D) {  // the heat model runs its four kernels in sequence
@@ -510,7 +556,9 @@ ocp_status ocp_eval_step(ocp_t* h, const double* x, const double* y, double sigm
 ocp_status ocp_eval_all_range(ocp_t* h, int64_t node_begin, int64_t node_end, const double* x, const double* y,
                               double sigma, double* f, double* cv, double* g, double* jvals, double* hvals,
                               void* stream) {
+  OCP_RANGE();
   if (!h) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
   if (node_begin < 0 || node_end > h->N + 1 || node_begin >= node_end)
     return set_err(h, OCP_EDIM, "node range outside [0, N+1) or empty");
   if (h->model == OCP_MODEL_GODDARD)
@@ -546,7 +594,9 @@ static ocp_status check_range(ocp* h, int64_t B, int64_t E, bool products) {
 ocp_status ocp_eval_step_range(ocp_t* h, int64_t node_begin, int64_t node_end, const double* x, const double* y,
                                double sigma, const double* vn, const double* vm, double* f, double* cv, double* g,
                                double* jvals, double* hvals, double* Jv, double* Jtv, double* Hv, void* stream) {
+  OCP_RANGE();
   if (!h) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
   ocp_status st = check_range(h, node_begin, node_end, true);
   if (st != OCP_OK) return st;
   NEED(x); NEED(y); NEED(vn); NEED(vm); NEED(f); NEED(cv); NEED(g); NEED(jvals); NEED(hvals);
@@ -560,7 +610,9 @@ ocp_status ocp_eval_step_range(ocp_t* h, int64_t node_begin, int64_t node_end, c
 
 ocp_status ocp_vjp_param_range(ocp_t* h, int64_t node_begin, int64_t node_end, const double* x, const double* w,
                                double* Jtw, double* dmu, void* stream) {
+  OCP_RANGE();
   if (!h) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
   if (h->model != OCP_MODEL_VDP) return set_err(h, OCP_EMODEL, "parameter derivative is provided for the Van der Pol model");
   ocp_status st = check_range(h, node_begin, node_end, true);
   if (st != OCP_OK) return st;
@@ -572,6 +624,7 @@ ocp_status ocp_vjp_param_range(ocp_t* h, int64_t node_begin, int64_t node_end, c
 }
 
 ocp_status ocp_sum_ordered(const double* parts, int count, double* out, void* stream) {
+  OCP_RANGE();
   if (!parts || !out || count < 1) return set_err(nullptr, OCP_EINVAL, "ocp_sum_ordered: parts, out and count >= 1 required");
   if (((uintptr_t)parts & 7u) || ((uintptr_t)out & 7u)) return set_err(nullptr, OCP_EINVAL, "ocp_sum_ordered: unaligned pointer");
   k_sum_ordered<<<1, 1, 0, (cudaStream_t)stream>>>(parts, count, out);
@@ -579,7 +632,9 @@ ocp_status ocp_sum_ordered(const double* parts, int count, double* out, void* st
 }
 
 ocp_status ocp_value_layout(const ocp_t* h, int64_t* nb, int32_t* row_count, int32_t* hx, int32_t* hu) {
+  OCP_RANGE();
   if (!h || !nb || !row_count || !hx || !hu) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
   *nb = h->pat.nb;
   for (int k = 0; k < h->nx; ++k) row_count[k] = (int32_t)h->pat.row_count(k);
   *hx = h->pat.hx;
@@ -597,7 +652,9 @@ struct ParamScope {
 };
 
 ocp_status ocp_eval_cons_p(ocp_t* h, const double* x, const double* p0, double* cv, void* stream) {
+  OCP_RANGE();
   if (!h) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
   NEED(x); NEED(cv); OPT(p0);
   if (p0 && h->model != OCP_MODEL_VDP) return set_err(h, OCP_EMODEL, "a device parameter is provided for the Van der Pol model");
   ParamScope ps(h, p0);
@@ -608,7 +665,9 @@ ocp_status ocp_eval_cons_p(ocp_t* h, const double* x, const double* p0, double* 
 
 ocp_status ocp_vjp_param_p(ocp_t* h, const double* x, const double* w, const double* p0, double* Jtw, double* dmu,
                            void* stream) {
+  OCP_RANGE();
   if (!h) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
   if (h->model != OCP_MODEL_VDP) return set_err(h, OCP_EMODEL, "parameter derivative is provided for the Van der Pol model");
   NEED(x); NEED(w); NEED(dmu); NEED(Jtw); OPT(p0);
   ParamScope ps(h, p0);
@@ -618,7 +677,9 @@ ocp_status ocp_vjp_param_p(ocp_t* h, const double* x, const double* w, const dou
 }
 
 ocp_status ocp_vjp_param(ocp_t* h, const double* x, const double* w, double* Jtw, double* dmu, void* stream) {
+  OCP_RANGE();
   if (!h) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
   if (h->model != OCP_MODEL_VDP) return set_err(h, OCP_EMODEL, "parameter derivative is provided for the Van der Pol model");
   NEED(x); NEED(w); NEED(dmu); NEED(Jtw);
   ProdCall c;
@@ -627,7 +688,9 @@ ocp_status ocp_vjp_param(ocp_t* h, const double* x, const double* w, double* Jtw
 }
 
 ocp_status ocp_bind_param0(ocp_t* h, const double* p0_dev) {
+  OCP_RANGE();
   if (!h) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
   if (p0_dev && h->model != OCP_MODEL_VDP)
     return set_err(h, OCP_EMODEL, "a device parameter is provided for the Van der Pol model");
   OPT(p0_dev);
@@ -636,7 +699,9 @@ ocp_status ocp_bind_param0(ocp_t* h, const double* p0_dev) {
 }
 
 ocp_status ocp_jprod_param(ocp_t* h, const double* x, const double* v, const double* s, double* Jv, void* stream) {
+  OCP_RANGE();
   if (!h) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
   NEED(x); NEED(v); NEED(Jv); OPT(s);
   if (s && h->model != OCP_MODEL_VDP) return set_err(h, OCP_EMODEL, "parameter direction: Van der Pol model only");
   ProdCall c;
@@ -646,7 +711,9 @@ ocp_status ocp_jprod_param(ocp_t* h, const double* x, const double* v, const dou
 
 ocp_status ocp_hprod_param(ocp_t* h, const double* x, const double* y, double sigma, const double* v, const double* s,
                            double* Hv, double* dmu, void* stream) {
+  OCP_RANGE();
   if (!h) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
   NEED(x); NEED(y); NEED(v); NEED(Hv); OPT(s); OPT(dmu);
   if ((s || dmu) && h->model != OCP_MODEL_VDP)
     return set_err(h, OCP_EMODEL, "mixed parameter term: Van der Pol model only");
@@ -658,7 +725,9 @@ ocp_status ocp_hprod_param(ocp_t* h, const double* x, const double* y, double si
 }
 
 ocp_status ocp_eval_grad_scaled(ocp_t* h, const double* x, const double* s, double* g, void* stream) {
+  OCP_RANGE();
   if (!h) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
   NEED(x); NEED(s); NEED(g);
   if (h->has_bol) return set_err(h, OCP_EMODEL, "the objective-only kernels do not include a boundary cost");
   return obj_launch(h, false, x, s, nullptr, g, nullptr, (cudaStream_t)stream);
@@ -666,29 +735,29 @@ ocp_status ocp_eval_grad_scaled(ocp_t* h, const double* x, const double* s, doub
 
 ocp_status ocp_obj_hvp(ocp_t* h, const double* x, const double* s, const double* v, double* Hv, double* dot,
                        void* stream) {
+  OCP_RANGE();
   if (!h) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
   NEED(x); NEED(s); NEED(v); NEED(Hv); OPT(dot);
   if (h->has_bol) return set_err(h, OCP_EMODEL, "the objective-only kernels do not include a boundary cost");
   return obj_launch(h, true, x, s, v, Hv, dot, (cudaStream_t)stream);
 }
 
 ocp_status ocp_set_param0(ocp_t* h, double value) {
+  OCP_RANGE();
   if (!h) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
   if (model_nparams(h->model) < 1) return set_err(h, OCP_EMODEL, "model has no parameters");
   if (h->model == OCP_MODEL_HEAT1D) return set_err(h, OCP_EMODEL, "the heat cell count is structural");
   h->params[0] = value;
   return OCP_OK;
 }
 
-static ocp_status rebuild(ocp* h) {
-  std::string why;
-  if (!build_pattern(h, why)) return set_err(h, OCP_EDIM, why);
-  return upload_tables(h);
-}
-
 ocp_status ocp_set_path_constraints(ocp_t* h, int npath, const double* a, const double* b, const double* l,
                                     const double* r) {
+  OCP_RANGE();
   if (!h) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
   const int nz = h->nx + h->nu;
   if (npath < 0 || npath > 16) return set_err(h, OCP_EINVAL, "between 0 and 16 path inequalities");
   if (npath > 0 && (!a || !b || !l || !r)) return set_err(h, OCP_EINVAL, "a, b, l and r are required");
@@ -710,7 +779,9 @@ ocp_status ocp_set_path_constraints(ocp_t* h, int npath, const double* a, const 
 
 ocp_status ocp_set_boundary_inequalities(ocp_t* h, int nbin, const double* a, const double* b, const double* l,
                                          const double* r) {
+  OCP_RANGE();
   if (!h) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
   const int bz = 2 * h->nx;
   if (nbin < 0 || nbin > 16) return set_err(h, OCP_EINVAL, "between 0 and 16 boundary inequalities");
   if (nbin > 0 && (!a || !b || !l || !r)) return set_err(h, OCP_EINVAL, "a, b, l and r are required");
@@ -734,7 +805,9 @@ ocp_status ocp_set_boundary_inequalities(ocp_t* h, int nbin, const double* a, co
 }
 
 ocp_status ocp_start_point(ocp_t* h, const double* xs, const double* us, double tf, double* x, void* stream) {
+  OCP_RANGE();
   if (!h) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
   NEED(x);
   if (h->nx > 128 || h->nu > 8) return set_err(h, OCP_EDIM, "start point: too many components");
   StartArgs a;
@@ -752,7 +825,9 @@ ocp_status ocp_start_point(ocp_t* h, const double* xs, const double* us, double 
 }
 
 ocp_status ocp_set_boundary_cost(ocp_t* h, const double* a, const double* b, const double* l) {
+  OCP_RANGE();
   if (!h) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
   const int bz = 2 * h->nx;
   if (!a && !b && !l) {
     h->has_bol = false;
@@ -773,7 +848,9 @@ ocp_status ocp_set_boundary_cost(ocp_t* h, const double* a, const double* b, con
 }
 
 ocp_status ocp_set_scheme(ocp_t* h, int scheme) {
+  OCP_RANGE();
   if (!h) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
   if (scheme == OCP_SCHEME_EULER && h->has_bol)
     for (int k = 0; k < h->nx; ++k)
       if (h->bol_a[h->nx + k] != 0.0)
@@ -788,7 +865,9 @@ ocp_status ocp_set_scheme(ocp_t* h, int scheme) {
 }
 
 ocp_status ocp_set_free_final_time(ocp_t* h, int enable) {
+  OCP_RANGE();
   if (!h) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
   if (h->model != OCP_MODEL_GODDARD)
     return set_err(h, OCP_EMODEL, "a free final time is provided for the Goddard model");
   h->free_tf = enable != 0;
@@ -796,7 +875,9 @@ ocp_status ocp_set_free_final_time(ocp_t* h, int enable) {
 }
 
 ocp_status ocp_set_final_components(ocp_t* h, int count, const int32_t* comps, const double* values) {
+  OCP_RANGE();
   if (!h) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
   if (h->model != OCP_MODEL_GODDARD)
     return set_err(h, OCP_EMODEL, "final rows on a subset of the state are provided for the Goddard model "
                                   "(ocp_set_boundary sets them on every component)");
@@ -813,7 +894,9 @@ ocp_status ocp_set_final_components(ocp_t* h, int count, const int32_t* comps, c
 }
 
 ocp_status ocp_set_terminal_cost(ocp_t* h, const double* mayer) {
+  OCP_RANGE();
   if (!h) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
   if (h->model != OCP_MODEL_GODDARD)
     return set_err(h, OCP_EMODEL, "a terminal cost is provided for the Goddard model");
   if (mayer) h->mayer.assign(mayer, mayer + h->nx);
@@ -823,7 +906,9 @@ ocp_status ocp_set_terminal_cost(ocp_t* h, const double* mayer) {
 
 ocp_status ocp_set_variable_bounds(ocp_t* h, const double* xlo, const double* xhi, const double* ulo,
                                    const double* uhi, double tflo, double tfhi) {
+  OCP_RANGE();
   if (!h) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
   const double inf = std::numeric_limits<double>::infinity();
   h->xlo.assign(h->nx, -inf); h->xhi.assign(h->nx, inf); h->ulo.assign(h->nu, -inf); h->uhi.assign(h->nu, inf);
   if (xlo) h->xlo.assign(xlo, xlo + h->nx);
@@ -836,7 +921,9 @@ ocp_status ocp_set_variable_bounds(ocp_t* h, const double* xlo, const double* xh
 }
 
 ocp_status ocp_set_tracking(ocp_t* h, const double* xslope, const double* xamp, const double* xfreq) {
+  OCP_RANGE();
   if (!h) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
   if (h->model == OCP_MODEL_HEAT1D || h->model == OCP_MODEL_GODDARD)
     return set_err(h, OCP_EMODEL, "a time-varying reference is provided for the node models with a running cost");
   const int nx = h->nx;
@@ -859,7 +946,7 @@ ocp_status ocp_set_tracking(ocp_t* h, const double* xslope, const double* xamp, 
   if (h->trk_comp.empty()) return OCP_OK;
   if ((int)h->trk_comp.size() > kMaxTrack) return set_err(h, OCP_EDIM, "too many tracked components");
   const size_t bytes = sizeof(double) * (size_t)(h->N + 1) * h->trk_comp.size();
-  cudaError_t e = cudaMalloc(&h->d_xtrack, bytes);
+  cudaError_t e = ocpg::dev_malloc(&h->d_xtrack, bytes);
   if (e != cudaSuccess) { h->d_xtrack = nullptr; h->trk_comp.clear(); return cuda_err(h, e, "cudaMalloc(tracking table)"); }
   h->ntrk = (int)h->trk_comp.size();
   h->has_ref = true;

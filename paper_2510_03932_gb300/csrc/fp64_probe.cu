@@ -44,6 +44,7 @@ __global__ void k_probe_fp64(double* out, int iters, double one, double eps) {
 }  // namespace
 
 extern "C" ocp_status ocp_probe_fp64(int op, int blocks, int threads, int iters, double* out, void* stream) {
+  OCP_RANGE();
   if (op < 0 || op > 3) return ocpg::set_err(nullptr, OCP_EINVAL, "ocp_probe_fp64: op must be 0, 1, 2 or 3");
   if (blocks < 1 || blocks > (1 << 20) || threads < 32 || threads > 1024 || (threads & 31) || iters < 1 ||
       iters > (1 << 24))

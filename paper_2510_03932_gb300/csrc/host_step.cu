@@ -86,7 +86,7 @@ static ocp_status host_step_ready(ocp* h) {
   auto up = [](int64_t k) { return (k + 31) / 32 * 32; };  // each mirror on a 256-byte boundary
   for (int64_t k : sz) total += up(k);
   for (int b = 0; b < 2; ++b) {
-    cudaError_t e = cudaMalloc(&s->buf[b], sizeof(double) * (size_t)total);
+    cudaError_t e = ocpg::dev_malloc(&s->buf[b], sizeof(double) * (size_t)total);
     if (e != cudaSuccess) {
       s->buf[b] = nullptr;
       return cuda_err(h, e, "cudaMalloc(host step mirrors)");
@@ -110,6 +110,7 @@ static ocp_status host_step_run(ocp_t* h, const double* x, const double* y, doub
                                 const double* vm, double* f, double* cv, double* g, double* jvals,
                                 double* hvals, double* Jv, double* Jtv, double* Hv, void* stream, bool join) {
   if (!h) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
   const double* in[4] = {x, y, vn, vm};
   double* out[8] = {f, cv, g, jvals, hvals, Jv, Jtv, Hv};
   const char* names[12] = {"x", "y", "vn", "vm", "f", "c", "g", "jvals", "hvals", "Jv", "Jtv", "Hv"};
@@ -150,6 +151,7 @@ extern "C" ocp_status ocp_eval_step_host(ocp_t* h, const double* x, const double
                                          const double* vn, const double* vm, double* f, double* cv, double* g,
                                          double* jvals, double* hvals, double* Jv, double* Jtv, double* Hv,
                                          void* stream) {
+  OCP_RANGE();
   return host_step_run(h, x, y, sigma, vn, vm, f, cv, g, jvals, hvals, Jv, Jtv, Hv, stream, true);
 }
 
@@ -157,11 +159,14 @@ extern "C" ocp_status ocp_eval_step_host_async(ocp_t* h, const double* x, const 
                                                const double* vn, const double* vm, double* f, double* cv,
                                                double* g, double* jvals, double* hvals, double* Jv, double* Jtv,
                                                double* Hv, void* stream) {
+  OCP_RANGE();
   return host_step_run(h, x, y, sigma, vn, vm, f, cv, g, jvals, hvals, Jv, Jtv, Hv, stream, false);
 }
 
 extern "C" ocp_status ocp_host_step_wait(ocp_t* h, void* stream) {
+  OCP_RANGE();
   if (!h) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
   HostStep* S = h->hstep;
   if (!S) return OCP_OK;
   // the copy-out stream is serial, so its last recorded event covers every earlier copy; an

@@ -314,14 +314,18 @@ using namespace ocpg;
 extern "C" {
 
 ocp_status ocp_kkt_dims(const ocp_t* h, int64_t* nnzk) {
+  OCP_RANGE();
   if (!h || !nnzk) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
   if (h->pat.nnzk < 0) return OCP_EDIM;
   *nnzk = h->pat.nnzk;
   return OCP_OK;
 }
 
 ocp_status ocp_kkt_structure(ocp_t* h, int32_t* rows, int32_t* cols, void* stream) {
+  OCP_RANGE();
   if (!h) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
   if (!rows || !cols) return set_err(h, OCP_EINVAL, "rows and cols are required");
   KktArgs a;
   if (kkt_fill(h, a) != OCP_OK) return set_err(h, OCP_EDIM, "KKT matrix too large for the int32 interface");
@@ -332,7 +336,9 @@ ocp_status ocp_kkt_structure(ocp_t* h, int32_t* rows, int32_t* cols, void* strea
 
 ocp_status ocp_kkt_values(ocp_t* h, const double* hvals, const double* jvals, const double* sigma_x,
                           double delta_w, double delta_c, double* kvals, void* stream) {
+  OCP_RANGE();
   if (!h) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
   if (!hvals || !jvals || !kvals) return set_err(h, OCP_EINVAL, "hvals, jvals and kvals are required");
   if (((uintptr_t)hvals | (uintptr_t)jvals | (uintptr_t)kvals | (uintptr_t)sigma_x) & 7u)
     return set_err(h, OCP_EINVAL, "arrays must be 8-byte aligned");

@@ -8,31 +8,21 @@
 #include <vector>
 
 #include "ocp.h"
+#include "kernel_config.h"
+
+#include <nvtx3/nvToolsExt.h>
 
 namespace ocpg {
 
-// Threads (= nodes) per CTA of the node-model kernels; a tile owns TILE-1 nodes.
-constexpr int TILE_VDP = 256, TILE_CARTPOLE = 128, TILE_DINT = 256, TILE_QUAD = 64;
-// Most state components with a time-varying reference (node models have at most 9 states).
-constexpr int kMaxTrack = 16;
-// Nodes per CTA of the heat-equation kernels (one per lane); a tile owns 31 nodes.
-constexpr int HEAT_TILE_NODES = 32;
-
-// Output selection bits of the fused evaluation kernels.
-enum : unsigned { O_F = 1u, O_C = 2u, O_G = 4u, O_J = 8u, O_H = 16u, O_ALL = 31u,
-                  // products evaluated in the same pass (the fused step)
-                  O_JV = 32u, O_JTV = 64u, O_HV = 128u, O_STEP = 255u };
-
-// Per-component Jacobian row template (local variable indices), as read from the model.
-constexpr int RT_XV = 6, RT_UV = 4;
-constexpr int RT_STRIDE = 2 + RT_XV + RT_UV;  // ints per row in the device table: rx, ru, xv[], uv[]
-struct RowTemplate {
-  int rx = 0, ru = 0;
-  int xv[RT_XV] = {-1, -1, -1, -1, -1, -1};
-  int uv[RT_UV] = {-1, -1, -1, -1};
-  bool jz[RT_XV] = {};  // entry xv[e] is the identity term alone (df_k/dx_v identically zero)
-  int count() const { return 2 * (rx + ru); }
+// NVTX range around each C-ABI call (named after the call), for timeline profilers; without a
+// profiler attached the push and pop are a few instructions each.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
 };
+#define OCP_RANGE() ::ocpg::NvtxRange ocp_nvtx_range_(__func__)
 
 // Host pattern: sizes, slot offsets and the node templates (paper Sec. 5: the generators
 // make one row per state component per interval; the pattern compiler lays out the COO
@@ -149,6 +139,9 @@ struct ocp {
   // the Jacobian's per-variable scatter map for ocp_jtprod_coo (built on first use, dropped
   // when the pattern is rebuilt)
   ocpg::ScatterMap* smap = nullptr;
+  // set when a setter failed after it had started to rebuild the pattern or its device tables:
+  // the handle is then inconsistent and every call but ocp_destroy / ocp_last_error refuses it
+  bool unusable = false;
   std::string err;
 };
 
@@ -156,6 +149,15 @@ struct ocp {
 namespace ocpg {
 
 ocp_status set_err(ocp* h, ocp_status st, const std::string& msg);
+// Refusal of a handle made unusable by a failed setter (OCP_EINVAL, message kept).
+ocp_status unusable_err(const ocp* h);
+// Device allocations and table uploads of the library (see fault.cu: host-side fault injection).
+cudaError_t dev_malloc_raw(void** p, size_t bytes);
+template <class T>
+cudaError_t dev_malloc(T** p, size_t bytes) { return dev_malloc_raw(reinterpret_cast<void**>(p), bytes); }
+cudaError_t dev_upload(void* dst, const void* src, size_t bytes);
+bool fault_dims();      // the armed 'dims' fault fires here (once)
+bool take_injected();   // whether the last failure on this thread was an injected one (clears it)
 ocp_status cuda_err(ocp* h, cudaError_t e, const char* what);
 int occupancy_grid(ocp* h, const void* kernel, int threads, size_t smem, int64_t work_tiles);
 

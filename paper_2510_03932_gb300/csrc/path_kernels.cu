@@ -154,15 +154,15 @@ ocp_status path_upload(ocp* h) {
   if (pv.empty()) pv.push_back(0);
   if (coef.empty()) coef.push_back(0.0);
   cudaError_t e;
-  if ((e = cudaMalloc(&h->d_poff, poff.size() * 4)) != cudaSuccess ||
-      (e = cudaMalloc(&h->d_pv, pv.size() * 4)) != cudaSuccess ||
-      (e = cudaMalloc(&h->d_pcoef, coef.size() * 8)) != cudaSuccess ||
-      (e = cudaMalloc(&h->d_pbase, base.size() * 8)) != cudaSuccess)
+  if ((e = ocpg::dev_malloc(&h->d_poff, poff.size() * 4)) != cudaSuccess ||
+      (e = ocpg::dev_malloc(&h->d_pv, pv.size() * 4)) != cudaSuccess ||
+      (e = ocpg::dev_malloc(&h->d_pcoef, coef.size() * 8)) != cudaSuccess ||
+      (e = ocpg::dev_malloc(&h->d_pbase, base.size() * 8)) != cudaSuccess)
     return cuda_err(h, e, "cudaMalloc(path tables)");
-  if ((e = cudaMemcpy(h->d_poff, poff.data(), poff.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (e = cudaMemcpy(h->d_pv, pv.data(), pv.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (e = cudaMemcpy(h->d_pcoef, coef.data(), coef.size() * 8, cudaMemcpyHostToDevice)) != cudaSuccess ||
-      (e = cudaMemcpy(h->d_pbase, base.data(), base.size() * 8, cudaMemcpyHostToDevice)) != cudaSuccess)
+  if ((e = ocpg::dev_upload(h->d_poff, poff.data(), poff.size() * 4)) != cudaSuccess ||
+      (e = ocpg::dev_upload(h->d_pv, pv.data(), pv.size() * 4)) != cudaSuccess ||
+      (e = ocpg::dev_upload(h->d_pcoef, coef.data(), coef.size() * 8)) != cudaSuccess ||
+      (e = ocpg::dev_upload(h->d_pbase, base.data(), base.size() * 8)) != cudaSuccess)
     return cuda_err(h, e, "cudaMemcpy(path tables)");
   return OCP_OK;
 }

@@ -203,7 +203,7 @@ bool build_pattern(ocp* h, std::string& why) {
   P.nnzk = P.kbbase[P.nbin];
   const int64_t lim = (int64_t)1 << 31;
   if (P.nnzk >= lim || P.n + P.m >= lim) P.nnzk = -1;
-  if (P.n >= lim || P.m >= lim || P.nnzj >= lim || P.nnzh >= lim) {
+  if (P.n >= lim || P.m >= lim || P.nnzj >= lim || P.nnzh >= lim || fault_dims()) {
     why = "problem too large for the int32 COO interface (n, m or nnz >= 2^31)";
     return false;
   }

@@ -201,7 +201,7 @@ static ocp_status build_map(ocp* h, int32_t* ptr, int32_t* rows, int32_t* slots,
   const size_t cb = sizeof(int32_t) * (size_t)std::max<int64_t>(P.n, 1);
   const size_t bb = sizeof(int64_t) * (size_t)(nblk + 1);
   char* scratch = nullptr;
-  cudaError_t e = cudaMalloc(&scratch, tb + cb + bb + 64);
+  cudaError_t e = ocpg::dev_malloc(&scratch, tb + cb + bb + 64);
   if (e != cudaSuccess) return cuda_err(h, e, "cudaMalloc(scatter map scratch)");
   int32_t* d_off = reinterpret_cast<int32_t*>(scratch);
   int32_t* d_k = d_off + off.size();
@@ -259,9 +259,9 @@ static ocp_status map_ready(ocp* h, cudaStream_t s) {
   scatter_map_free(h);
   ScatterMap* m = new ScatterMap();
   h->smap = m;
-  cudaError_t e = cudaMalloc(&m->ptr, sizeof(int32_t) * (size_t)(P.n + 1));
-  if (e == cudaSuccess) e = cudaMalloc(&m->rows, sizeof(int32_t) * (size_t)std::max<int64_t>(P.nnzj, 1));
-  if (e == cudaSuccess) e = cudaMalloc(&m->slots, sizeof(int32_t) * (size_t)std::max<int64_t>(P.nnzj, 1));
+  cudaError_t e = ocpg::dev_malloc(&m->ptr, sizeof(int32_t) * (size_t)(P.n + 1));
+  if (e == cudaSuccess) e = ocpg::dev_malloc(&m->rows, sizeof(int32_t) * (size_t)std::max<int64_t>(P.nnzj, 1));
+  if (e == cudaSuccess) e = ocpg::dev_malloc(&m->slots, sizeof(int32_t) * (size_t)std::max<int64_t>(P.nnzj, 1));
   if (e != cudaSuccess) {
     scatter_map_free(h);
     return cuda_err(h, e, "cudaMalloc(scatter map)");
@@ -310,13 +310,17 @@ using namespace ocpg;
 extern "C" {
 
 ocp_status ocp_jac_scatter_map(ocp_t* h, int32_t* colptr, int32_t* rows, int32_t* slots, void* stream) {
+  OCP_RANGE();
   if (!h) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
   if (!colptr || !rows || !slots) return set_err(h, OCP_EINVAL, "colptr, rows and slots are required");
   return build_map(h, colptr, rows, slots, (cudaStream_t)stream);
 }
 
 ocp_status ocp_jtprod_coo(ocp_t* h, const double* jvals, const double* w, double* Jtw, void* stream) {
+  OCP_RANGE();
   if (!h) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
   if (!jvals || !w || !Jtw) return set_err(h, OCP_EINVAL, "jvals, w and Jtw are required");
   if (((uintptr_t)jvals | (uintptr_t)w | (uintptr_t)Jtw) & 7u) return set_err(h, OCP_EINVAL, "arrays must be 8-byte aligned");
   cudaStream_t s = (cudaStream_t)stream;

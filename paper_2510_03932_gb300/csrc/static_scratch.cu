@@ -34,6 +34,7 @@ double* g_scratch_ptr[kMaxDevices] = {};
 
 extern "C" ocp_status ocp_eval_obj_noalloc(const ocp_dynamics* dyn, const ocp_cost* cost, int nx, int nu, int64_t N,
                                            double T, const double* x, double* f, void* stream) {
+  OCP_RANGE();
   if (!x || !f) return set_err(nullptr, OCP_EINVAL, "x and f are required");
   if (((uintptr_t)x & 7u) || ((uintptr_t)f & 7u)) return set_err(nullptr, OCP_EINVAL, "x or f is not 8-byte aligned");
   ocp prob;  // host-side description only; no device allocation

@@ -91,6 +91,7 @@ _SIGS = {
     "ocp_obj_hvp": [_P, _P, _P, _P, _P, _P, _P],
     "ocp_eval_obj_noalloc": [C.POINTER(_Dyn), C.POINTER(_Cost), C.c_int, C.c_int, _I64, _D, _P, _P, _P],
     "ocp_probe_fp64": [C.c_int, C.c_int, C.c_int, C.c_int, _P, _P],
+    "ocp_set_fault": [C.c_char_p],
     "ocp_last_error": [_P],
 }
 
@@ -124,6 +125,11 @@ def probe_fp64(op, blocks, threads, iters, out, stream=None):
     _check(lib().ocp_probe_fp64(int(op), int(blocks), int(threads), int(iters), C.c_void_p(out.data_ptr()),
                                 _stream(stream)))
     return blocks * threads * (8 * iters + 7)
+
+
+def set_fault(spec: str):
+    """ocp_set_fault: arm a host-side fault ("alloc:K", "upload:K", "dims"; "" disarms)."""
+    _check(lib().ocp_set_fault(spec.encode()))
 
 
 def sum_ordered(parts, out, stream=None):

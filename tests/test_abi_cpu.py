@@ -118,7 +118,7 @@ def declared_signatures():
 
 
 def _kind(t):
-    if t in (C.c_void_p,) or (isinstance(t, type) and issubclass(t, C._Pointer)):
+    if t in (C.c_void_p, C.c_char_p) or (isinstance(t, type) and issubclass(t, C._Pointer)):
         return "ptr"
     if t is C.c_double:
         return "double"
@@ -143,3 +143,41 @@ def test_binding_argument_lists_match_the_header():
         assert [_kind(t) for t in argt] == decl[name], (name, [_kind(t) for t in argt], decl[name])
         checked += 1
     assert checked >= 40
+
+
+def test_fault_specs_and_dims_fault_on_the_host(lib):
+    """ocp_set_fault parses its spec; an armed 'dims' fault makes the next ocp_create fail in
+    its pattern build (before any CUDA call) with OCP_EDIM and a message naming the injection,
+    and fires only once."""
+    lib.ocp_set_fault.restype = C.c_int
+    lib.ocp_set_fault.argtypes = [C.c_char_p]
+    lib.ocp_last_error.restype = C.c_char_p
+    lib.ocp_last_error.argtypes = [C.c_void_p]
+    for bad in (b"bogus", b"alloc:0", b"alloc:x", b"upload", b"alloc:-2"):
+        assert lib.ocp_set_fault(bad) == 1, bad
+    assert lib.ocp_set_fault(b"") == 0
+    assert lib.ocp_set_fault(b"dims") == 0
+    st, msg = create(lib, 1, [1.0], 2, 1)
+    assert st == 2 and "injected by OCP_FAULT" in msg, msg
+    # disarmed after firing: the same create no longer fails in its pattern build
+    assert lib.ocp_set_fault(b"") == 0
+    lib.ocp_set_fault(b"dims")
+    st, msg = create(lib, 1, [1.0], 2, 1, N=-1)   # rejected by validation, before the pattern build
+    assert st == 2 and "injected" not in msg, msg
+    st, msg = create(lib, 1, [1.0], 2, 1)         # the armed fault fires here
+    assert st == 2 and "injected by OCP_FAULT" in msg, msg
+    assert lib.ocp_set_fault(b"") == 0
+
+
+def test_fault_from_the_environment():
+    """OCP_FAULT arms the same faults at the library's first use in a fresh process."""
+    import subprocess
+    import sys
+    code = ("import ctypes as C, sys; sys.path.insert(0, %r)\n"
+            "from paper_2510_03932_gb300 import ocp\n"
+            "w = dict(model='vdp', nx=2, nu=1, N=10, T=1.0, params=[1.0], q=[1.0, 1.0], r=[1.0])\n"
+            "try:\n    ocp.OCP.from_workload(w)\nexcept ocp.OcpError as e:\n    print(e.status, str(e))\n" % ROOT)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300,
+                       env=dict(os.environ, OCP_FAULT="dims"))
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert r.stdout.startswith("2 ") and "injected by OCP_FAULT" in r.stdout, r.stdout
