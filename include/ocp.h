@@ -473,7 +473,11 @@ const char* ocp_last_error(const ocp_t* h);
  * Launch configuration: threads per CTA (64, 128, 256), nodes per thread (1 or 2: 32 or 64
  * nodes per warp), CTAs per SM of the persistent grid (0: as many as fit).
  * ocp_batch_autotune times every configuration on the caller's data (synchronizes the
- * stream) and keeps the fastest; best_ms (host, may be NULL) receives its time.
+ * stream) and keeps the fastest; best_ms (host, may be NULL) receives its time.  With the
+ * environment variable OCP_AUTOTUNE_CACHE naming a file, the result is appended to it, keyed
+ * by the batch's shape (model, instance count, total and largest horizon, requested outputs)
+ * and the GPU (SM count, compute capability); a later autotune of a batch of the same shape
+ * takes the stored configuration and time without timing anything.
  * ocp_batch_graph_capture records one ocp_batch_eval_all launch with these arguments in a
  * CUDA graph (stream must be a created stream, not the legacy default one);
  * ocp_batch_graph_launch replays it.  Changing the configuration drops the graph. */

@@ -20,7 +20,10 @@
 // CTAs per SM are chosen by ocp_batch_autotune, which times every candidate on the caller's
 // data.  ocp_batch_graph_capture records one launch in a CUDA graph for cheap replay.
 #include <algorithm>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "model_cartpole.cuh"
@@ -183,6 +186,53 @@ struct ocp_batch_impl {
 };
 
 struct ocp_batch : ocp_batch_impl {};
+
+// Autotuning cache (OCP_AUTOTUNE_CACHE = path of a text file): one line per tuned batch shape,
+// "key<TAB>threads npt ctas_per_sm ms", the key naming the model, the instance count, the total
+// and the largest horizon, the requested outputs and the GPU (SM count, compute capability).
+// A batch of a shape already in the file takes the stored configuration without timing; the
+// last line of a key wins.  Lines that do not parse are ignored.
+static std::mutex g_tune_mu;
+
+static std::string tune_key(const ocp_batch* b, unsigned outs) {
+  int64_t nodes = 0, maxn = 0;
+  for (const ocp* h : b->items) { nodes += h->N + 1; maxn = std::max<int64_t>(maxn, h->N + 1); }
+  int major = 0, minor = 0;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, b->device);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, b->device);
+  char buf[256];
+  std::snprintf(buf, sizeof(buf), "model=%d count=%d nodes=%lld maxnodes=%lld outputs=%u sms=%d cc=%d.%d", b->model,
+                b->count, (long long)nodes, (long long)maxn, outs, b->num_sms, major, minor);
+  return buf;
+}
+
+static bool tune_lookup(const char* path, const std::string& key, int& threads, int& npt, int& ctas, float& ms) {
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  FILE* fh = std::fopen(path, "r");
+  if (!fh) return false;
+  char line[512];
+  bool found = false;
+  while (std::fgets(line, sizeof(line), fh)) {
+    char* tab = std::strchr(line, '\t');
+    if (!tab || std::string(line, tab - line) != key) continue;
+    int t = 0, n = 0, c = 0;
+    float m = 0.f;
+    if (std::sscanf(tab + 1, "%d %d %d %f", &t, &n, &c, &m) == 4 && (t == 64 || t == 128 || t == 256) &&
+        (n == 1 || n == 2) && c >= 0) {
+      threads = t; npt = n; ctas = c; ms = m; found = true;
+    }
+  }
+  std::fclose(fh);
+  return found;
+}
+
+static void tune_store(const char* path, const std::string& key, int threads, int npt, int ctas, float ms) {
+  std::lock_guard<std::mutex> g(g_tune_mu);
+  FILE* fh = std::fopen(path, "a");
+  if (!fh) return;   // the cache is an optimisation: a write failure is not an error
+  std::fprintf(fh, "%s\t%d %d %d %.6f\n", key.c_str(), threads, npt, ctas, ms);
+  std::fclose(fh);
+}
 
 static ocp_status berr(ocp_batch* b, ocp_status st, const std::string& m) {
   const ocp_status s = set_err(nullptr, st, m);  // (marks a fault injected by OCP_FAULT)
@@ -388,6 +438,17 @@ ocp_status ocp_batch_autotune(ocp_batch_t* b, const double* x, const double* y, 
   OCP_RANGE();
   if (!b) return OCP_EINVAL;
   if (b->unusable) return berr(b, OCP_EINVAL, "batch unusable after a failed configuration change");
+  const char* cache = std::getenv("OCP_AUTOTUNE_CACHE");
+  const unsigned outs = (f ? 1u : 0u) | (c ? 2u : 0u) | (g ? 4u : 0u) | (jvals ? 8u : 0u) | (hvals ? 16u : 0u);
+  const std::string key = tune_key(b, outs);
+  {
+    int ct = 0, cn = 0, cc = 0;
+    float cms = 0.f;
+    if (cache && *cache && tune_lookup(cache, key, ct, cn, cc, cms)) {
+      if (best_ms) *best_ms = cms;
+      return ocp_batch_set_config(b, cn, ct, cc);
+    }
+  }
   cudaStream_t s = (cudaStream_t)stream;
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
@@ -420,6 +481,7 @@ ocp_status ocp_batch_autotune(ocp_batch_t* b, const double* x, const double* y, 
   cudaEventDestroy(e1);
   if (st != OCP_OK) return st;
   if (best_ms) *best_ms = best;
+  if (cache && *cache) tune_store(cache, key, bt, bn, bc, best);
   return ocp_batch_set_config(b, bn, bt, bc);
 }
 

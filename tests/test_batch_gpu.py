@@ -144,3 +144,43 @@ def test_batch_rejects_mixed_models(ocp):
     h = ocp.OCP.from_workload(synth.with_horizon(synth.workload("heat_n2e4"), 10))
     with pytest.raises(ocp.OcpError):
         ocp.OCPBatch([h])
+
+
+def test_autotune_cache_reuses_the_stored_configuration(tmp_path, monkeypatch):
+    """With OCP_AUTOTUNE_CACHE set, the first autotune writes its result, keyed by the batch
+    shape; a second batch of the same shape takes the stored configuration and time without
+    timing, and a different shape is tuned again."""
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2510_03932_gb300 import ocp
+    path = tmp_path / "tune.txt"
+    monkeypatch.setenv("OCP_AUTOTUNE_CACHE", str(path))
+
+    def make(ns):
+        ws = [synth.with_horizon(synth.workload("cartpole_n1e5"), n) for n in ns]
+        probs = [ocp.OCP.from_workload(w) for w in ws]
+        B = ocp.OCPBatch(probs)
+        ds = [synth.draw(w) for w in ws]
+        x = torch.from_numpy(np.concatenate([d["x"] for d in ds])).cuda()
+        y = torch.from_numpy(np.concatenate([d["y"] for d in ds])).cuda()
+        return probs, B, x, y
+
+    probs, B, x, y = make([900, 2000, 4100])
+    f, c, g, jv, hv = B.outputs()
+    ms1 = B.autotune(x, y, 1.0, f, None, g, jv, hv)
+    lines = path.read_text().splitlines()
+    assert len(lines) == 1 and "model=2 count=3" in lines[0]
+    cfg1 = B.get_config()
+    probs2, B2, x2, y2 = make([900, 2000, 4100])
+    f2, c2, g2, jv2, hv2 = B2.outputs()
+    ms2 = B2.autotune(x2, y2, 1.0, f2, None, g2, jv2, hv2)
+    assert B2.get_config() == cfg1 and abs(ms2 - ms1) <= 1e-6 * max(ms1, 1.0)
+    assert len(path.read_text().splitlines()) == 1   # nothing re-timed
+    B2.eval_all(x2, y2, 1.0, f2, None, g2, jv2, hv2)
+    torch.cuda.synchronize()
+    probs3, B3, x3, y3 = make([900, 2000])
+    f3, c3, g3, jv3, hv3 = B3.outputs()
+    B3.autotune(x3, y3, 1.0, f3, None, g3, jv3, hv3)
+    assert len(path.read_text().splitlines()) == 2
+    for P in probs + probs2 + probs3:
+        P.close()
