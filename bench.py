@@ -92,8 +92,8 @@ FP64_OPS_PER_NODE = {("vdp", "eval_all"): 26.6, ("vdp", "jh"): 10.0, ("vdp", "jp
                      ("vdp:euler", "eval_all"): 21.5, ("vdp:euler", "jh"): 8.0, ("vdp:euler", "jprod"): 11.0,
                      ("vdp:euler", "jtprod"): 10.0, ("vdp:euler", "hprod"): 10.0, ("vdp:euler", "step"): 41.5,
                      # heat, 64 cells: the step is its four kernels in sequence
-                     ("heat64", "eval_all"): 1121.6, ("heat64", "jh"): 390.4, ("heat64", "jprod"): 523.4,
-                     ("heat64", "jtprod"): 463.0, ("heat64", "hprod"): 257.0, ("heat64", "step"): 2365.0}
+                     ("heat64", "eval_all"): 1122.8, ("heat64", "jh"): 390.4, ("heat64", "jprod"): 523.4,
+                     ("heat64", "jtprod"): 463.0, ("heat64", "hprod"): 257.0, ("heat64", "step"): 2366.2}
 
 # The kernel sources of each model key (paths under the package's csrc/): the tile body and
 # the helpers it includes, the model's device functor, the translation unit that instantiates
@@ -109,7 +109,7 @@ KERNEL_SOURCES = {
 }
 # Tags of the sources the FP64_OPS_PER_NODE counts (and TRAFFIC) were measured on.
 FP64_OPS_SRC = {"vdp": "21d91bd08c73", "vdp:euler": "21d91bd08c73", "cartpole": "562799f88bbb",
-                "quadrotor": "bdc6cdbee3b3", "goddard": "42f15ba48a09", "heat64": "f1980677f8c3"}
+                "quadrotor": "bdc6cdbee3b3", "goddard": "42f15ba48a09", "heat64": "166c23ffcfb2"}
 
 
 def kernel_source_tag(key):
@@ -267,7 +267,7 @@ def measure_fp64_rate(dev, nsm, seconds=0.25):
     sampler = ClockSampler(dev.index)
     sampler.start()
     res = {}
-    for op, name in ((0, "dfma"), (1, "dadd"), (2, "dmul"), (3, "dfma_const_multiplier")):
+    for op, name in ((0, "dfma"), (1, "dadd"), (2, "dmul"), (3, "dfma_const_multiplier"), (4, "dfma_const_addend")):
         ms = []
         for _ in range(3):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -284,6 +284,7 @@ def measure_fp64_rate(dev, nsm, seconds=0.25):
                        % (blocks, threads, iters),
                 dfma_per_clk_per_sm=per["dfma"], dadd_per_clk_per_sm=per["dadd"], dmul_per_clk_per_sm=per["dmul"],
                 dfma_const_multiplier_per_clk_per_sm=per["dfma_const_multiplier"],
+                dfma_const_addend_per_clk_per_sm=per["dfma_const_addend"],
                 dfma_G_per_s=res["dfma"] / 1e9, sm_mhz=clk, clocks=clocks)
 
 

@@ -19,7 +19,7 @@ extern "C" {
 
 /* FP64 throughput probe.  op: 0 = fused multiply-add (DFMA) with every operand in a register,
  * 1 = add (DADD), 2 = multiply (DMUL), 3 = DFMA whose multiplier is a kernel parameter (read
- * from the constant bank).  Launches `blocks` CTAs of `threads` threads (threads a multiple of 32, at most
+ * from the constant bank), 4 = DFMA whose addend is a kernel parameter.  Launches `blocks` CTAs of `threads` threads (threads a multiple of 32, at most
  * 1024); each thread runs 8 independent dependency chains of `iters` operations of that kind,
  * so one launch executes blocks * threads * 8 * iters FP64 operations (plus 7 adds per thread
  * that combine the chains).  Each thread writes one double to `out` (device, at least

@@ -29,10 +29,11 @@ __global__ void k_probe_fp64(double* out, int iters, double one, double eps) {
   for (int it = 0; it < iters; ++it) {
 #pragma unroll
     for (int k = 0; k < kChains; ++k) {
-      if (OP == 0) a[k] = fma(a[k], b[k], eps);        // multiplier in a register
+      if (OP == 0) a[k] = fma(a[k], b[k], b[k]);       // every operand in a register
       else if (OP == 1) a[k] = a[k] + b[k];
       else if (OP == 2) a[k] = a[k] * b[k];
-      else a[k] = fma(a[k], one, eps);                 // multiplier a kernel parameter
+      else if (OP == 3) a[k] = fma(a[k], one, eps);    // multiplier a kernel parameter
+      else a[k] = fma(a[k], b[k], eps);                // addend a kernel parameter, multiplier a register
     }
   }
   double s = a[0];
@@ -45,7 +46,7 @@ __global__ void k_probe_fp64(double* out, int iters, double one, double eps) {
 
 extern "C" ocp_status ocp_probe_fp64(int op, int blocks, int threads, int iters, double* out, void* stream) {
   OCP_RANGE();
-  if (op < 0 || op > 3) return ocpg::set_err(nullptr, OCP_EINVAL, "ocp_probe_fp64: op must be 0, 1, 2 or 3");
+  if (op < 0 || op > 4) return ocpg::set_err(nullptr, OCP_EINVAL, "ocp_probe_fp64: op must be 0 to 4");
   if (blocks < 1 || blocks > (1 << 20) || threads < 32 || threads > 1024 || (threads & 31) || iters < 1 ||
       iters > (1 << 24))
     return ocpg::set_err(nullptr, OCP_EINVAL, "ocp_probe_fp64: blocks, threads or iters out of range");
@@ -55,6 +56,7 @@ extern "C" ocp_status ocp_probe_fp64(int op, int blocks, int threads, int iters,
   if (op == 0) k_probe_fp64<0><<<blocks, threads, 0, s>>>(out, iters, one, eps);
   else if (op == 1) k_probe_fp64<1><<<blocks, threads, 0, s>>>(out, iters, one, eps);
   else if (op == 2) k_probe_fp64<2><<<blocks, threads, 0, s>>>(out, iters, one, eps);
-  else k_probe_fp64<3><<<blocks, threads, 0, s>>>(out, iters, one, eps);
+  else if (op == 3) k_probe_fp64<3><<<blocks, threads, 0, s>>>(out, iters, one, eps);
+  else k_probe_fp64<4><<<blocks, threads, 0, s>>>(out, iters, one, eps);
   return ocpg::cuda_err(nullptr, cudaGetLastError(), "ocp_probe_fp64 launch");
 }

@@ -77,33 +77,39 @@ __device__ __forceinline__ void heat_stage(const HeatArgs& a, const double* __re
 // Fused evaluation
 // ======================================================================================
 
-// Jacobian rows of cell k for the tile's nodes, staged in the warp's row buffer and stored:
-// the entries on x_k are -1 + dk (left node) and +1 + dk (right node), dk = 3 hh x_k^2 + d
-// (d = hh 2/dx^2, or hh/dx^2 at the Neumann end), written fma(3 hh, x_k^2, d -+ 1); every
-// other entry is the constant -hh/dx^2.
-__device__ __forceinline__ void heat_jrows(const HeatArgs& a, int k, bool LAST, int t, int lane, bool act, int nrows,
-                                           int64_t r0, double x2, double* sJw) {
+// Jacobian rows of cell k for the tile's nodes: the entries on x_k are -1 + dk (left node) and
+// +1 + dk (right node), dk = 3 hh x_k^2 + d (d = hh 2/dx^2, or hh/dx^2 at the Neumann end),
+// written fma(3 hh, x_k^2, d -+ 1); every other entry is the constant c = -hh/dx^2.  Lane t
+// writes the whole row (k, r0 + t): its own left entry, the right entry of lane t+1 (shuffle),
+// the constants; entries by position (left X cells, right X cells, then the control's left
+// and right entries for k = 0):
+//   k = 0:        [jl, c, jr', c, c, c]        interior:  [c, jl, c, c, jr', c]
+//   k = n-1:      [c, jl, c, jr']
+// A row is 48 (or 32) bytes: three (two) 16-byte stores when the component's rows start on a
+// 16-byte boundary, scalar stores otherwise; consecutive lanes write consecutive rows.
+__device__ __forceinline__ void heat_jrows(const HeatArgs& a, int k, bool LAST, int t, bool act, int nrows,
+                                           int64_t r0, double x2) {
   const double jl = fma(a.h3, x2, LAST ? a.dl_m1 : a.di_m1);
   const double jr = fma(a.h3, x2, LAST ? a.dl_p1 : a.di_p1);
+  const double jrn = __shfl_down_sync(0xffffffffu, jr, 1);   // the right node's entry on x_k
+  if (!(act && t < nrows)) return;
+  const double c = a.mhidx2;
   const int cnt = LAST ? 4 : 6;
-  const int rx = (k == 0 || LAST) ? 2 : 3;
-  const int ru = (k == 0) ? 1 : 0;
-  const int kd = (k == 0) ? 0 : 1;  // position of cell k among the row's X cells
-  if (act && t < nrows) {
-    double* rp = sJw + t * cnt;
-    for (int e = 0; e < rx; ++e) rp[e] = (e == kd) ? jl : a.mhidx2;
-    if (ru) rp[2 * rx] = a.mhidx2;
+  double* rp = a.jv + heat_jbase(a, k) + (r0 + t) * cnt;
+  double v[6];
+  if (k == 0) { v[0] = jl; v[1] = c; v[2] = jrn; v[3] = c; v[4] = c; v[5] = c; }
+  else if (LAST) { v[0] = c; v[1] = jl; v[2] = c; v[3] = jrn; v[4] = c; v[5] = c; }
+  else { v[0] = c; v[1] = jl; v[2] = c; v[3] = c; v[4] = jrn; v[5] = c; }
+  if ((reinterpret_cast<uintptr_t>(rp) & 15u) == 0) {
+    double2* r2 = reinterpret_cast<double2*>(rp);
+    r2[0] = make_double2(v[0], v[1]);
+    r2[1] = make_double2(v[2], v[3]);
+    if (!LAST) r2[2] = make_double2(v[4], v[5]);
+  } else {
+#pragma unroll
+    for (int e = 0; e < 6; ++e)
+      if (e < cnt) rp[e] = v[e];
   }
-  if (act && t >= 1 && t - 1 < nrows) {
-    double* rp = sJw + (t - 1) * cnt;
-    for (int e = 0; e < rx; ++e) rp[rx + e] = (e == kd) ? jr : a.mhidx2;
-    if (ru) rp[2 * rx + 1] = a.mhidx2;
-  }
-  __syncwarp();
-  double* dst = a.jv + heat_jbase(a, k) + r0 * cnt;
-  const int total = nrows * cnt;
-  for (int i = lane; i < total; i += 32) dst[i] = sJw[i];
-  __syncwarp();
 }
 
 // boundary rows X_{0,k} (and X_{N,k}): one constant entry each
@@ -142,7 +148,6 @@ __global__ void __launch_bounds__(HT_THREADS, (OUT & O_C) ? 5 : 8) k_heat_eval(c
   // are done: the full evaluation fits five CTAs per SM (one wave of 646 tiles at N = 2e4).
   double* sX = sm;                                             // 32 * ld
   double* sN = sX + heat_xlen(n);                              // Hessian diagonal, 31 * ld
-  double* sJ = sN + (CH ? (HT_LANES - 1) * ld : 0);            // per-warp row buffer 8 * 31 * 6
   double* red = sX;                                            // reduction, 256 (after the stores)
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double objacc = 0.0;
@@ -162,6 +167,14 @@ __global__ void __launch_bounds__(HT_THREADS, (OUT & O_C) ? 5 : 8) k_heat_eval(c
     const bool endp = (j == 0) || (j == a.N);
     heat_stage(a, a.x, r0, nn, sX);
     __syncthreads();
+    // ---- Hessian diagonal of every owned (node, cell), elementwise: warps take whole cells
+    // (lanes = nodes, the multipliers' rows coalesced), so no load waits inside the cell loop
+    // (measured: the separate pass speeds up the full evaluation; J + H alone is faster with
+    // the diagonal computed in its cell loop)
+    if (CC && WH && own) {
+#pragma unroll 2
+      for (int k = warp; k < n; k += HT_WARPS) sN[t * ld + k] = heat_hdiag(a, k, j, endp, sX[t * ld + k]);
+    }
 
     // ---- control entries (warp 0): gradient, objective, Hessian (u,u)
     if (warp == 0 && own) {
@@ -176,7 +189,6 @@ __global__ void __launch_bounds__(HT_THREADS, (OUT & O_C) ? 5 : 8) k_heat_eval(c
     }
 
     const int ngroups = (n + 7) / 8;
-    double* sJw = sJ + warp * (HT_LANES - 1) * 6;
     if constexpr (CC) {
       // One cell k of the tile's nodes; LAST: k is the Neumann end n-1.  The end cell is
       // peeled out of the loop so that its Laplacian and diagonal constant are compile-time
@@ -190,7 +202,7 @@ __global__ void __launch_bounds__(HT_THREADS, (OUT & O_C) ? 5 : 8) k_heat_eval(c
           xr = LAST ? xk : sX[t * ld + k + 1];
         }
         const double x2 = hmul(a, xk, xk);
-        if (WJ) heat_jrows(a, k, LAST, t, lane, act, nrows, r0, x2, sJw);
+        if (WJ) heat_jrows(a, k, LAST, t, act, nrows, r0, x2);
         if (WJ && own) heat_jbound(a, k, j);
         if (WC) {
           // hh f_k = hh (lap / dx^2 - x^3)
@@ -204,7 +216,6 @@ __global__ void __launch_bounds__(HT_THREADS, (OUT & O_C) ? 5 : 8) k_heat_eval(c
           if (own && j == 0) a.c[k] = xk;
           if (own && a.has_final && j == a.N) a.c[n + k] = xk;
         }
-        if (own && WH) sN[t * ld + k] = heat_hdiag(a, k, j, endp, xk);
         if (own && (WG || WF)) heat_grad(a, k, j, endp, xk, WG, WF, objacc);
       };
       for (int gi = warp; gi < ngroups; gi += HT_WARPS) {
@@ -222,7 +233,7 @@ __global__ void __launch_bounds__(HT_THREADS, (OUT & O_C) ? 5 : 8) k_heat_eval(c
           const bool last = (k == n - 1);
           double xk = 0.0;
           if (act) xk = sX[t * ld + k];
-          if (WJ) heat_jrows(a, k, last, t, lane, act, nrows, r0, hmul(a, xk, xk), sJw);
+          if (WJ) heat_jrows(a, k, last, t, act, nrows, r0, hmul(a, xk, xk));
           if (WJ && own) heat_jbound(a, k, j);
           if (own && WH) sN[t * ld + k] = heat_hdiag(a, k, j, endp, xk);
           if (own && (WG || WF)) heat_grad(a, k, j, endp, xk, WG, WF, objacc);
@@ -300,7 +311,8 @@ __global__ void __launch_bounds__(HT_THREADS) k_heat_jprod(const __grid_constant
 // H v (node-local):    out_a = (2 sigma w q_a + 6 hh ybar_a x_a) v_a,  out_u = 2 sigma w r v_u
 // ======================================================================================
 template <bool JT>
-__global__ void __launch_bounds__(HT_THREADS) k_heat_local(const __grid_constant__ HeatArgs a) {
+// (at most 51 registers: five CTAs per SM, one wave of 626 tiles at N = 2e4; measured faster)
+__global__ void __launch_bounds__(HT_THREADS, 5) k_heat_local(const __grid_constant__ HeatArgs a) {
   extern __shared__ __align__(16) double sm[];
   const int n = a.n, ld = n + 1;
   double* sX = sm;
@@ -352,12 +364,20 @@ __global__ void __launch_bounds__(HT_THREADS) k_heat_local(const __grid_constant
           }
         }
       } else {
-        for (int k = k0; k < k1; ++k) {
-          if (act) {
+        // elementwise: the group's multiplier rows are loaded before any arithmetic needs them
+        double yl[8], yr[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int k = k0 + q;
+          yl[q] = (act && k < k1 && j >= 1) ? __ldg(a.y + a.nb + (int64_t)k * a.N + j - 1) : 0.0;
+          yr[q] = (act && k < k1 && j < a.N) ? __ldg(a.y + a.nb + (int64_t)k * a.N + j) : 0.0;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int k = k0 + q;
+          if (act && k < k1) {
             const double xk = sX[t * ld + k];
-            const double yl = (j >= 1) ? __ldg(a.y + a.nb + (int64_t)k * a.N + j - 1) : 0.0;
-            const double yr = (j < a.N) ? __ldg(a.y + a.nb + (int64_t)k * a.N + j) : 0.0;
-            const double hk = fma(hmul(a, a.h6, hadd(a, yl, yr)), xk, endp ? a.cq_end[k] : a.cq_in[k]);
+            const double hk = fma(hmul(a, a.h6, hadd(a, yl[q], yr[q])), xk, endp ? a.cq_end[k] : a.cq_in[k]);
             sX[t * ld + k] = hmul(a, hk, sV[t * ld + k]);  // in place: x no longer needed for cell k
           }
         }
@@ -433,8 +453,7 @@ static ocp_status heat_eval_t(ocp* h, const EvalCall& c, cudaStream_t s) {
   if (a.ntiles < 1) a.ntiles = 1;
   if (a.ntiles > h->max_partials) return set_err(h, OCP_EDIM, "too many tiles for the reduction scratch");
   const int ld = h->nx + 1;
-  const size_t smem = sizeof(double) * ((size_t)heat_xlen(h->nx) + ((OUT & O_H) ? (HT_LANES - 1) * ld : 0) +
-                                        ((OUT & O_J) ? HT_WARPS * (HT_LANES - 1) * 6 : 0));
+  const size_t smem = sizeof(double) * ((size_t)heat_xlen(h->nx) + ((OUT & O_H) ? (HT_LANES - 1) * ld : 0));
   auto kern = k_heat_eval<OUT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_err(h, e, "cudaFuncSetAttribute(heat)");
