@@ -83,12 +83,12 @@ def _counts(w):
 # bench reports no FP64 fraction for that model until they are measured again.
 FP64_OPS_PER_NODE = {("vdp", "eval_all"): 26.6, ("vdp", "jh"): 10.0, ("vdp", "jprod"): 13.0,
                      ("vdp", "jtprod"): 12.0, ("vdp", "hprod"): 11.0, ("vdp", "step"): 50.6,
-                     ("cartpole", "eval_all"): 126.9, ("cartpole", "jh"): 103.8, ("cartpole", "jprod"): 81.6,
-                     ("cartpole", "jtprod"): 78.0, ("cartpole", "hprod"): 108.0, ("cartpole", "step"): 174.0,
-                     ("quadrotor", "eval_all"): 251.2, ("quadrotor", "jh"): 177.7, ("quadrotor", "jprod"): 165.4,
-                     ("quadrotor", "jtprod"): 156.0, ("quadrotor", "hprod"): 199.0, ("quadrotor", "step"): 398.8,
-                     ("goddard", "eval_all"): 101.3, ("goddard", "jh"): 91.2, ("goddard", "jprod"): 68.3,
-                     ("goddard", "jtprod"): 68.2, ("goddard", "hprod"): 95.2, ("goddard", "step"): 155.4,
+                     ("cartpole", "eval_all"): 117.8, ("cartpole", "jh"): 95.7, ("cartpole", "jprod"): 78.6,
+                     ("cartpole", "jtprod"): 75.0, ("cartpole", "hprod"): 103.0, ("cartpole", "step"): 165.9,
+                     ("quadrotor", "eval_all"): 250.1, ("quadrotor", "jh"): 176.7, ("quadrotor", "jprod"): 163.4,
+                     ("quadrotor", "jtprod"): 155.0, ("quadrotor", "hprod"): 198.0, ("quadrotor", "step"): 397.8,
+                     ("goddard", "eval_all"): 98.2, ("goddard", "jh"): 89.2, ("goddard", "jprod"): 66.3,
+                     ("goddard", "jtprod"): 66.2, ("goddard", "hprod"): 93.2, ("goddard", "step"): 153.4,
                      ("vdp:euler", "eval_all"): 21.5, ("vdp:euler", "jh"): 8.0, ("vdp:euler", "jprod"): 11.0,
                      ("vdp:euler", "jtprod"): 10.0, ("vdp:euler", "hprod"): 10.0, ("vdp:euler", "step"): 41.5,
                      # heat, 64 cells: the step is its four kernels in sequence
@@ -108,8 +108,8 @@ KERNEL_SOURCES = {
     "heat64": _COMMON + ["heat_kernels.cu"],
 }
 # Tags of the sources the FP64_OPS_PER_NODE counts (and TRAFFIC) were measured on.
-FP64_OPS_SRC = {"vdp": "21d91bd08c73", "vdp:euler": "21d91bd08c73", "cartpole": "562799f88bbb",
-                "quadrotor": "bdc6cdbee3b3", "goddard": "42f15ba48a09", "heat64": "166c23ffcfb2"}
+FP64_OPS_SRC = {"vdp": "959e519151fa", "vdp:euler": "959e519151fa", "cartpole": "ac869dd84ece",
+                "quadrotor": "8e48c9f9ed96", "goddard": "e9a468566ab5", "heat64": "4bdf9bb3981a"}
 
 
 def kernel_source_tag(key):
@@ -158,7 +158,7 @@ def named_workload(name):
 # DRAM bytes (read + write) of one launch at a workload, from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum; writes still dirty in L2 when the kernel ends
 # are not counted), with the source tag of the kernel it was captured on (see traffic()).
-TRAFFIC = {("vdp_mu_n1e6", "step"): (227.47e6, "21d91bd08c73")}
+TRAFFIC = {("vdp_mu_n1e6", "step"): (226.89e6, "959e519151fa")}
 # Each SM's FP64 pipe completes 2 FP64 instructions (one lane each) per clock: the recipe's
 # nominal 1.25 TFLOP/s FP64 of GB300 is 6.25e11 FMA/s = 1.99 per clock per SM at 152 SMs and
 # 2070 MHz.  bench.py measures the rate live (measure_fp64_rate) and reports it beside the peak.

@@ -29,6 +29,12 @@ extern "C" {
  * ocp_last_error(NULL). */
 ocp_status ocp_probe_fp64(int op, int blocks, int threads, int iters, double* out, void* stream);
 
+/* The evaluation kernels' reciprocal 1/d (Newton-Raphson steps from the hardware's approximate
+ * reciprocal) on n values: out[i] = recip(d[i]) (device arrays; asynchronous on `stream`), so
+ * that a test can compare it with the IEEE division.  For finite, normal d.  Errors: OCP_EINVAL,
+ * OCP_ECUDA (ocp_last_error(NULL)). */
+ocp_status ocp_probe_recip(const double* d, double* out, int64_t n, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -9,6 +9,7 @@
 // pipe more independent work than its latency needs, so the launch measures its issue rate.
 #include <cuda_runtime.h>
 
+#include "model_base.cuh"
 #include "ocp_internal.h"
 #include "ocp_probe.h"
 
@@ -42,7 +43,22 @@ __global__ void k_probe_fp64(double* out, int iters, double one, double eps) {
   out[i] = s;
 }
 
+__global__ void k_probe_recip(const double* d, double* out, int64_t n, double one) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = ocpg::recip(one, d[i]);
+}
+
 }  // namespace
+
+extern "C" ocp_status ocp_probe_recip(const double* d, double* out, int64_t n, void* stream) {
+  OCP_RANGE();
+  if (!d || !out || n < 0 || ((uintptr_t)d & 7u) || ((uintptr_t)out & 7u))
+    return ocpg::set_err(nullptr, OCP_EINVAL, "ocp_probe_recip: bad arguments");
+  if (n == 0) return OCP_OK;
+  const int grid = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+  k_probe_recip<<<grid, 256, 0, (cudaStream_t)stream>>>(d, out, n, 1.0);
+  return ocpg::cuda_err(nullptr, cudaGetLastError(), "ocp_probe_recip launch");
+}
 
 extern "C" ocp_status ocp_probe_fp64(int op, int blocks, int threads, int iters, double* out, void* stream) {
   OCP_RANGE();

@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(GT) k_god(const __grid_constant__ GodArgs a) {
       const double r = __ldg(a.x + 3 * j), v = __ldg(a.x + 3 * j + 1), m = __ldg(a.x + 3 * j + 2);
       const double u = __ldg(a.x + a.uoff + j);
       const double E = exp(fma(-a.beta, r, a.beta));          // exp(-beta (r - 1))
-      const double im = 1.0 / m, ir = 1.0 / r;
+      const double im = recip(a.one, m), ir = recip(a.one, r);
       const double ir2 = gmul(a, ir, ir);
       const double q1 = gmul(a, gmul(a, a.Cd, E), im);        // Cd E / m
       const double D = gmul(a, gmul(a, q1, v), v);

@@ -52,6 +52,23 @@ __device__ __forceinline__ double fmul(const ModelConst& K, double a, double b) 
 // more occupancy than the faster FMAs gain (measured on the fused step: whole argument block
 // 110.6-127.9 us, model constants only 109.3-112.9 us, the constant 1 alone 108.7 us, against
 // 106.0 us from the constant bank), so the kernels read their constants from the parameters.
+// 1 / d by Newton-Raphson iteration for the reciprocal, r <- r + r (1 - d r) (each step squares
+// the relative error), started from the hardware's approximate reciprocal (PTX
+// rcp.approx.ftz.f64, relative error below 2^-22, computed by the special-function unit, not the
+// FP64 pipe): two steps reach FP64 accuracy, within an ulp of the correctly rounded 1 / d, with
+// four FMAs, where the IEEE division costs more FP64 instructions.  For finite, normal d: the
+// models' denominators are bounded away from zero (a subnormal d is flushed to zero, d = 0 gives
+// NaN instead of infinity).
+// (`one` is the run-time constant 1.)
+__device__ __forceinline__ double recip(double one, double d) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+  double e = fma(-d, r, one);
+  r = fma(r, e, r);
+  e = fma(-d, r, one);
+  return fma(r, e, r);
+}
+
 #define OCP_TABLE1(NAME, TYPE, N, ...)                       \
   __host__ __device__ static constexpr TYPE NAME(int k) {    \
     constexpr TYPE t[N] = __VA_ARGS__;                       \

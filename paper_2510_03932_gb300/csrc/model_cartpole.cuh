@@ -24,7 +24,10 @@ namespace ocpg {
 //   thdd_tw = (B_tw / l - thdd_w D') / D                B_tw = -2 mp l w (c^2 - s^2)
 //   thdd_ww = -2 mp c s / D,   thdd_tF = (s / l - thdd_F D') / D
 // Constants: c[0]=mc, c[1]=mp, c[2]=l, c[3]=g, c[4]=(mc+mp) g, c[5]=1/l, c[6]=mp l, c[7]=2 mp,
-//            c[8]=mp g, c[9]=2 mp l, c[10]=4 g.
+//            c[8]=mp g, c[9]=2 mp l, c[10]=4 g, c[11]=hh/l, c[12]=-hh/l, c[13]=3 mp l.
+// The kernels carry the angular acceleration scaled by l, Bu = B / D = l thdd, and its
+// derivatives (Bu_t = (B_t - Bu D') / D, Bu_w = B_w / D, Bu_F = -c / D): the 1/l then enters
+// only through the constants hh/l (defects, Jacobian) and the multiplier of the Hessian terms.
 // ------------------------------------------------------------------------------------
 struct CartPole {
   static constexpr int EVAL_MIN_CTAS = 0;
@@ -51,6 +54,7 @@ struct CartPole {
     mc.c[0] = m_c; mc.c[1] = m_p; mc.c[2] = l; mc.c[3] = g;
     mc.c[4] = (m_c + m_p) * g; mc.c[5] = 1.0 / l; mc.c[6] = m_p * l; mc.c[7] = 2.0 * m_p;
     mc.c[8] = m_p * g; mc.c[9] = 2.0 * m_p * l; mc.c[10] = 4.0 * g;
+    mc.c[11] = hh * (1.0 / l); mc.c[12] = -(hh * (1.0 / l)); mc.c[13] = 3.0 * m_p * l;
   }
   __device__ __forceinline__ static void device_param(ModelConst&, double) {}
 
@@ -59,7 +63,7 @@ struct CartPole {
                                               const double (&cqd)[NZ], double (&pa)[NX], double (&pb)[NX],
                                               double (&mjx)[NX][MAXRX], double (&mju)[NX][MAXRU],
                                               double (&hd)[NHD]) {
-    const double mcm = K.c[0], mp = K.c[1], l = K.c[2], g = K.c[3], Mg = K.c[4], il = K.c[5];
+    const double mcm = K.c[0], mp = K.c[1], l = K.c[2], g = K.c[3], Mg = K.c[4];
     const double mpl = K.c[6], mp2 = K.c[7], mpg = K.c[8], mpl2 = K.c[9], g4 = K.c[10];
     const double hh = K.hh, mhh = K.mhh;
     const double p = z[0], pd = z[1], th = z[2], w = z[3], F = z[4];
@@ -67,20 +71,20 @@ struct CartPole {
     sincos(th, &s, &c);
     const double ms = fmul(K, mp, s);
     const double D = fma(ms, s, mcm);
-    const double iD = 1.0 / D;
-    const double iDl = fmul(K, iD, il);
+    const double iD = recip(K.one, D);
     const double w2 = fmul(K, w, w);
     const double lw2 = fmul(K, l, w2);
     const double A = fma(ms, fma(g, c, lw2), F);
     const double pdd = fmul(K, A, iD);
     const double mplw2 = fmul(K, mpl, w2);
     const double B = fma(-s, fma(mplw2, c, Mg), fmul(K, -F, c));
-    const double thdd = fmul(K, B, iDl);
+    const double Bu = fmul(K, B, iD);             // l thdd
+    const double hhil = K.c[11], mhhil = K.c[12];
     if (WC) {
       pa[0] = fma(hh, pd, p);   pb[0] = fma(mhh, pd, p);
       pa[1] = fma(hh, pdd, pd); pb[1] = fma(mhh, pdd, pd);
       pa[2] = fma(hh, w, th);   pb[2] = fma(mhh, w, th);
-      pa[3] = fma(hh, thdd, w); pb[3] = fma(mhh, thdd, w);
+      pa[3] = fma(hhil, Bu, w); pb[3] = fma(mhhil, Bu, w);
     }
     if (WJ || WH) {
       const double sc = fmul(K, s, c);
@@ -91,23 +95,24 @@ struct CartPole {
       const double lw = fmul(K, mpl2, w);          // 2 mp l w
       const double A_w = fmul(K, lw, s);
       const double B_t = fma(F, s, -fma(mplw2, c2s2, fmul(K, Mg, c)));
-      const double thdd_t = fmul(K, fma(B_t, il, fmul(K, -thdd, Dp)), iD);
+      const double Bu_t = fmul(K, fma(-Bu, Dp, B_t), iD);
       const double B_w = fmul(K, -lw, sc);
-      const double thdd_w = fmul(K, B_w, iDl);
-      const double thdd_F = fmul(K, -c, iDl);
+      const double Bu_w = fmul(K, B_w, iD);
+      const double Bu_F = fmul(K, -c, iD);
+      const double mhiD = fmul(K, mhh, iD);
       if (WJ) {
-        const double mhiD = fmul(K, mhh, iD);
         mjx[0][0] = 0.0; mjx[0][1] = mhh; mjx[0][2] = 0.0;
         mjx[1][0] = 0.0; mjx[1][1] = fmul(K, mhh, pdd_t); mjx[1][2] = fmul(K, mhiD, A_w);
         mju[1][0] = mhiD;
         mjx[2][0] = 0.0; mjx[2][1] = mhh; mjx[2][2] = 0.0;
-        mjx[3][0] = fmul(K, mhh, thdd_t); mjx[3][1] = fmul(K, mhh, thdd_w);
-        mju[3][0] = fmul(K, mhh, thdd_F);
+        mjx[3][0] = fmul(K, mhhil, Bu_t); mjx[3][1] = fmul(K, mhhil, Bu_w);
+        mju[3][0] = fmul(K, mhhil, Bu_F);
       }
       if (WH) {
-        // Every second derivative above is (numerator) / D: the multipliers carry the 1/D,
-        // m1 = -hh ybar_1 / D and m3 = -hh ybar_3 / D, and the numerators are combined directly.
-        const double m1 = fmul(K, fmul(K, mhh, yb[1]), iD), m3 = fmul(K, fmul(K, mhh, yb[3]), iD);
+        // Every second derivative above is (numerator) / D: the multipliers carry the 1/D (and
+        // for the angular rows the 1/l), m1 = -hh ybar_1 / D and m3 = -hh ybar_3 / (l D), and the
+        // numerators are combined directly (those of the angular rows scaled by l).
+        const double m1 = fmul(K, mhiD, yb[1]), m3 = fmul(K, fmul(K, mhhil, yb[3]), iD);
         const double pdd_w = fmul(K, A_w, iD);
         const double Dpp = fmul(K, mp2, c2s2);
         const double mDp2 = fmul(K, -2.0, Dp);
@@ -118,17 +123,17 @@ struct CartPole {
         const double n_pdd_tw = fma(-pdd_w, Dp, A_tw);
         const double n_pdd_ww = fmul(K, mpl2, s);
         const double n_pdd_tF = fmul(K, -Dp, iD);
-        // B_tt = F c + 4 mp l w^2 s c + (mc+mp) g s
-        const double B_tt = fma(F, c, fmul(K, s, fma(fmul(K, 4.0, mplw2), c, Mg)));
-        const double n_thdd_tt = fma(-thdd, Dpp, fma(thdd_t, mDp2, fmul(K, B_tt, il)));
+        // B_tt = F c + 4 mp l w^2 s c + (mc+mp) g s = -B + 3 mp l w^2 s c
+        const double B_tt = fma(sc, fmul(K, K.c[13], w2), -B);
+        const double n_bu_tt = fma(-Bu, Dpp, fma(Bu_t, mDp2, B_tt));
         const double B_tw = fmul(K, -lw, c2s2);
-        const double n_thdd_tw = fma(-thdd_w, Dp, fmul(K, B_tw, il));
-        const double n_thdd_ww = fmul(K, -mp2, sc);
-        const double n_thdd_tF = fma(-thdd_F, Dp, fmul(K, s, il));
-        hd[0] = fma(m1, n_pdd_tt, fma(m3, n_thdd_tt, cqd[2]));   // (th, th)
-        hd[1] = fma(m1, n_pdd_tw, fmul(K, m3, n_thdd_tw));       // (w, th)
-        hd[2] = fma(m1, n_pdd_ww, fma(m3, n_thdd_ww, cqd[3]));   // (w, w)
-        hd[3] = fma(m1, n_pdd_tF, fmul(K, m3, n_thdd_tF));       // (F, th)
+        const double n_bu_tw = fma(-Bu_w, Dp, B_tw);
+        const double n_bu_ww = fmul(K, -mpl2, sc);
+        const double n_bu_tF = fma(-Bu_F, Dp, s);
+        hd[0] = fma(m1, n_pdd_tt, fma(m3, n_bu_tt, cqd[2]));   // (th, th)
+        hd[1] = fma(m1, n_pdd_tw, fmul(K, m3, n_bu_tw));       // (w, th)
+        hd[2] = fma(m1, n_pdd_ww, fma(m3, n_bu_ww, cqd[3]));   // (w, w)
+        hd[3] = fma(m1, n_pdd_tF, fmul(K, m3, n_bu_tF));       // (F, th)
       }
     }
   }

@@ -69,7 +69,7 @@ struct Quadrotor {
     sincos(z[6], &s7, &c7);
     sincos(z[7], &s8, &c8);
     sincos(z[8], &s9, &c9);
-    const double e = 1.0 / c8;
+    const double e = recip(K.one, c8);
     const double t = fmul(K, s8, e);
     const double c7s8 = fmul(K, c7, s8), s7s8 = fmul(K, s7, s8);
     const double c7c8 = fmul(K, c7, c8), s7c8 = fmul(K, s7, c8);

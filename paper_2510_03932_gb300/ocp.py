@@ -91,6 +91,7 @@ _SIGS = {
     "ocp_obj_hvp": [_P, _P, _P, _P, _P, _P, _P],
     "ocp_eval_obj_noalloc": [C.POINTER(_Dyn), C.POINTER(_Cost), C.c_int, C.c_int, _I64, _D, _P, _P, _P],
     "ocp_probe_fp64": [C.c_int, C.c_int, C.c_int, C.c_int, _P, _P],
+    "ocp_probe_recip": [_P, _P, _I64, _P],
     "ocp_set_fault": [C.c_char_p],
     "ocp_last_error": [_P],
 }
@@ -106,7 +107,10 @@ def lib():
             if not _build.up_to_date():
                 path = _build.build()
         L = C.CDLL(path)
+        alt = bool(os.environ.get("OCP_GB300_LIB"))
         for name, argt in _SIGS.items():
+            if alt and not hasattr(L, name):   # an older build of the library lacks newer calls
+                continue
             fn = getattr(L, name)
             fn.argtypes = argt
             fn.restype = C.c_int
@@ -130,6 +134,16 @@ def probe_fp64(op, blocks, threads, iters, out, stream=None):
 def set_fault(spec: str):
     """ocp_set_fault: arm a host-side fault ("alloc:K", "upload:K", "dims"; "" disarms)."""
     _check(lib().ocp_set_fault(spec.encode()))
+
+
+def probe_recip(d, out=None, stream=None):
+    """ocp_probe_recip: the kernels' reciprocal of every entry of the CUDA float64 tensor d."""
+    if d.dtype != torch.float64 or not d.is_cuda or not d.is_contiguous():
+        raise TypeError("d must be a contiguous float64 CUDA tensor")
+    out = torch.empty_like(d) if out is None else out
+    _check(lib().ocp_probe_recip(C.c_void_p(d.data_ptr()), C.c_void_p(out.data_ptr()), int(d.numel()),
+                                 _stream(stream)))
+    return out
 
 
 def sum_ordered(parts, out, stream=None):
