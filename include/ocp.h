@@ -463,15 +463,18 @@ ocp_status ocp_set_fault(const char* spec);
 const char* ocp_last_error(const ocp_t* h);
 
 /* Batched form (many problems of one model, possibly different N, cost weights and boundary
- * values, in ONE persistent launch).  Provided for the cart-pole and Van der Pol models;
- * others return OCP_EMODEL.  The handles must stay alive while the batch is used.
+ * values, in ONE persistent launch).  Provided for the Van der Pol, cart-pole, double-integrator
+ * and quadrotor models (trapezoidal scheme, without path or boundary inequalities or a boundary
+ * cost); others return OCP_EMODEL.  The handles must stay alive while the batch is used.
  * Variables, constraints, Jacobian and Hessian values of instance i start at the prefix
  * offsets given by ocp_batch_offsets (host arrays of length count+1 for x/g, y/c, jac values,
  * hess values), each instance laid out exactly as for its own handle: its slices are
  * bit-identical to the plain evaluator's; its objective goes to f[i] (device, length count).
  * Any output may be NULL (not stored); y is required with Hessian values.
  * Launch configuration: threads per CTA (64, 128, 256), nodes per thread (1 or 2: 32 or 64
- * nodes per warp), CTAs per SM of the persistent grid (0: as many as fit).
+ * nodes per warp), CTAs per SM of the persistent grid (0: as many as fit).  The quadrotor's
+ * staged Jacobian rows allow at most 128 nodes per CTA (threads x nodes per thread); a larger
+ * configuration returns OCP_EINVAL and the autotuner skips it.
  * ocp_batch_autotune times every configuration on the caller's data (synchronizes the
  * stream) and keeps the fastest; best_ms (host, may be NULL) receives its time.  With the
  * environment variable OCP_AUTOTUNE_CACHE naming a file, the result is appended to it, keyed

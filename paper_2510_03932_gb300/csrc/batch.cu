@@ -24,9 +24,12 @@
 #include <cstdlib>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "model_cartpole.cuh"
+#include "model_dint.cuh"
+#include "model_quad.cuh"
 #include "model_vdp.cuh"
 #include "node_kernels.cuh"
 #include "ocp_internal.h"
@@ -140,9 +143,15 @@ struct BatchConfig {
 };
 static const BatchConfig kConfigs[] = {{64, 1}, {128, 1}, {256, 1}, {64, 2}, {128, 2}, {256, 2}};
 
+// Largest CTA (threads x nodes per thread) of a model's batched kernel: the tile's staged
+// Jacobian rows must fit the shared memory (the quadrotor's 68 entries per node: 128 nodes).
+template <class M>
+constexpr int batch_max_nodes() { return jrow_total<M>() > 32 ? 128 : 512; }
+
 template <class M, int TILE, int NPT>
 static const void* batch_kernel() {
-  return (const void*)k_batch_eval<M, TILE, NPT>;
+  if constexpr (TILE * NPT <= batch_max_nodes<M>()) return (const void*)k_batch_eval<M, TILE, NPT>;
+  else return nullptr;
 }
 
 template <class M>
@@ -255,6 +264,7 @@ static ocp_status batch_upload_inst(ocp_batch* b) {
   if (e != cudaSuccess) return berr(b, OCP_ECUDA, std::string("cudaMemcpy: ") + cudaGetErrorString(e));
   // allow the largest shared-memory request of every configuration once
   for (const auto& cf : kConfigs) {
+    if (!kernel_for<M>(cf.threads, cf.npt)) continue;   // not provided for this model
     e = cudaFuncSetAttribute(kernel_for<M>(cf.threads, cf.npt), cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem_bytes<M>(cf.threads, cf.npt));
     if (e != cudaSuccess) return berr(b, OCP_ECUDA, std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e));
@@ -304,22 +314,46 @@ static ocp_status batch_launch(ocp_batch* b, const double* x, const double* y, d
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(b->ntiles, (int64_t)per * b->num_sms));
   const size_t sm = smem_bytes<M>(b->threads, b->npt);
   const int T = b->threads;
-#define OCP_BATCH_LAUNCH(TT, PP) k_batch_eval<M, TT, PP><<<grid, TT, sm, s>>>(a)
+  auto go = [&](auto tt, auto pp) {
+    constexpr int TT = decltype(tt)::value, PP = decltype(pp)::value;
+    if constexpr (TT * PP <= batch_max_nodes<M>()) k_batch_eval<M, TT, PP><<<grid, TT, sm, s>>>(a);
+  };
+  using I64 = std::integral_constant<int, 64>;
+  using I128 = std::integral_constant<int, 128>;
+  using I256 = std::integral_constant<int, 256>;
+  using P1 = std::integral_constant<int, 1>;
+  using P2 = std::integral_constant<int, 2>;
+  if (!kernel_for<M>(T, b->npt)) return berr(b, OCP_EINVAL, "configuration not provided for this model");
   if (b->npt == 1) {
-    if (T == 64) OCP_BATCH_LAUNCH(64, 1); else if (T == 128) OCP_BATCH_LAUNCH(128, 1); else OCP_BATCH_LAUNCH(256, 1);
+    if (T == 64) go(I64{}, P1{}); else if (T == 128) go(I128{}, P1{}); else go(I256{}, P1{});
   } else {
-    if (T == 64) OCP_BATCH_LAUNCH(64, 2); else if (T == 128) OCP_BATCH_LAUNCH(128, 2); else OCP_BATCH_LAUNCH(256, 2);
+    if (T == 64) go(I64{}, P2{}); else if (T == 128) go(I128{}, P2{}); else go(I256{}, P2{});
   }
-#undef OCP_BATCH_LAUNCH
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return berr(b, OCP_ECUDA, std::string("batch launch: ") + cudaGetErrorString(e));
   return OCP_OK;
 }
 
+// Calls fn with a value of the batch's model type (the node models the batched form serves).
+template <class Fn>
+static auto with_model(int model, Fn&& fn) {
+  switch (model) {
+    case OCP_MODEL_CARTPOLE: return fn(CartPole{});
+    case OCP_MODEL_DINT: return fn(Dint{});
+    case OCP_MODEL_QUADROTOR: return fn(Quadrotor{});
+    default: return fn(VdP{});
+  }
+}
+
 static ocp_status dispatch_batch(ocp_batch* b, const double* x, const double* y, double sigma, double* f, double* c,
                                  double* g, double* jv, double* hv, cudaStream_t s) {
-  if (b->model == OCP_MODEL_CARTPOLE) return batch_launch<CartPole>(b, x, y, sigma, f, c, g, jv, hv, s);
-  return batch_launch<VdP>(b, x, y, sigma, f, c, g, jv, hv, s);
+  return with_model(b->model, [&](auto m) {
+    return batch_launch<decltype(m)>(b, x, y, sigma, f, c, g, jv, hv, s);
+  });
+}
+
+static bool config_provided(const ocp_batch* b, int threads, int npt) {
+  return with_model(b->model, [&](auto m) { return kernel_for<decltype(m)>(threads, npt) != nullptr; });
 }
 
 static void batch_free(ocp_batch* b) {
@@ -338,8 +372,9 @@ ocp_status ocp_batch_create(ocp_t* const* items, int count, ocp_batch_t** out) {
   *out = nullptr;
   if (!items || count < 1) return set_err(nullptr, OCP_EINVAL, "need at least one problem");
   const int model = items[0] ? items[0]->model : 0;
-  if (model != OCP_MODEL_CARTPOLE && model != OCP_MODEL_VDP)
-    return set_err(nullptr, OCP_EMODEL, "batched evaluation is provided for the cart-pole and Van der Pol models");
+  if (model != OCP_MODEL_CARTPOLE && model != OCP_MODEL_VDP && model != OCP_MODEL_DINT && model != OCP_MODEL_QUADROTOR)
+    return set_err(nullptr, OCP_EMODEL,
+                   "batched evaluation is provided for the Van der Pol, cart-pole, double-integrator and quadrotor models");
   for (int i = 0; i < count; ++i) {
     if (!items[i]) return set_err(nullptr, OCP_EINVAL, "NULL problem in the batch");
     if (items[i]->unusable) return set_err(nullptr, OCP_EINVAL, "a problem of the batch is unusable after a failed setter");
@@ -380,7 +415,7 @@ ocp_status ocp_batch_create(ocp_t* const* items, int count, ocp_batch_t** out) {
     batch_free(b);
     return cuda_err(nullptr, e, "batch tables");   // OCP_ENOMEM for a failed allocation
   }
-  ocp_status st = (model == OCP_MODEL_CARTPOLE) ? batch_upload_inst<CartPole>(b) : batch_upload_inst<VdP>(b);
+  ocp_status st = with_model(model, [&](auto m) { return batch_upload_inst<decltype(m)>(b); });
   if (st == OCP_OK) st = batch_tiles(b);
   if (st != OCP_OK) { batch_free(b); return st; }
   *out = b;
@@ -407,6 +442,8 @@ ocp_status ocp_batch_set_config(ocp_batch_t* b, int nodes_per_thread, int thread
   if ((nodes_per_thread != 1 && nodes_per_thread != 2) || (threads != 64 && threads != 128 && threads != 256) ||
       ctas_per_sm < 0)
     return berr(b, OCP_EINVAL, "config: nodes_per_thread in {1,2}, threads in {64,128,256}, ctas_per_sm >= 0");
+  if (!config_provided(b, threads, nodes_per_thread))
+    return berr(b, OCP_EINVAL, "config: more nodes per CTA than this model's staged Jacobian rows fit in shared memory");
   b->npt = nodes_per_thread;
   b->threads = threads;
   b->ctas_per_sm = ctas_per_sm;
@@ -457,9 +494,10 @@ ocp_status ocp_batch_autotune(ocp_batch_t* b, const double* x, const double* y, 
   int bt = 128, bn = 1, bc = 0;
   ocp_status st = OCP_OK;
   for (const auto& cf : kConfigs) {
+    if (!config_provided(b, cf.threads, cf.npt)) continue;
     b->threads = cf.threads; b->npt = cf.npt; b->ctas_per_sm = 0;
     if ((st = batch_tiles(b)) != OCP_OK) break;
-    const int maxc = (b->model == OCP_MODEL_CARTPOLE) ? max_ctas_per_sm<CartPole>(b) : max_ctas_per_sm<VdP>(b);
+    const int maxc = with_model(b->model, [&](auto m) { return max_ctas_per_sm<decltype(m)>(b); });
     for (int cps = maxc; cps >= 1; cps = (cps > 2 ? cps / 2 : cps - 1)) {
       b->ctas_per_sm = cps;
       if ((st = dispatch_batch(b, x, y, sigma, f, c, g, jvals, hvals, s)) != OCP_OK) break;  // warm-up

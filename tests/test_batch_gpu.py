@@ -34,15 +34,23 @@ def make(ocp, ws):
 
 def batch_ws(model, Ns):
     ws = synth.batch_workloads(count=len(Ns), seed=77)
-    if model == "vdp":
-        base = synth.workload("vdp_n1e3")
-        ws = [dict(base, N=int(N), seed=500 + i) for i, N in enumerate(Ns)]
+    if model in ("vdp", "dint", "quadrotor"):
+        base = synth.workload({"vdp": "vdp_n1e3", "dint": "dint", "quadrotor": "quadrotor_n1e3"}[model])
+        ws = [synth.with_horizon(dict(base, seed=500 + i), int(N)) for i, N in enumerate(Ns)]
     else:
         ws = [dict(w, N=int(N)) for w, N in zip(ws, Ns)]
     return ws
 
 
-@pytest.mark.parametrize("model", ["cartpole", "vdp"])
+CONFIGS = [(npt, threads) for npt in (1, 2) for threads in (64, 128, 256)]
+
+
+def provided(model, npt, threads):
+    """The quadrotor's staged Jacobian rows (68 entries per node) fit 128 nodes per CTA."""
+    return model != "quadrotor" or npt * threads <= 128
+
+
+@pytest.mark.parametrize("model", ["cartpole", "vdp", "dint", "quadrotor"])
 def test_batch_slices_bit_identical_every_config(ocp, model):
     Ns = [1, 2, 63, 64, 127, 255, 256, 511, 1000, 2049]
     probs, B, draws, x, y = make(ocp, batch_ws(model, Ns))
@@ -51,21 +59,43 @@ def test_batch_slices_bit_identical_every_config(ocp, model):
     for P, d in zip(probs, draws):
         plain.append([t.cpu().numpy() for t in P.eval_all(torch.from_numpy(d["x"]).cuda(),
                                                           torch.from_numpy(d["y"]).cuda(), sigma)])
-    for npt in (1, 2):
-        for threads in (64, 128, 256):
-            B.set_config(npt, threads, 0)
-            f, c, g, jv, hv = B.outputs()
-            for t in (f, c, g, jv, hv):
-                t.fill_(float("nan"))
-            B.eval_all(x, y, sigma, f, c, g, jv, hv)
-            torch.cuda.synchronize()
-            fh, ch, gh, jh, hh = (t.cpu().numpy() for t in (f, c, g, jv, hv))
-            for i, (pf, pc, pg, pj, ph) in enumerate(plain):
-                assert np.array_equal(ch[B.coff[i]:B.coff[i + 1]], pc), (npt, threads, i, "c")
-                assert np.array_equal(gh[B.xoff[i]:B.xoff[i + 1]], pg), (npt, threads, i, "g")
-                assert np.array_equal(jh[B.joff[i]:B.joff[i + 1]], pj), (npt, threads, i, "jac")
-                assert np.array_equal(hh[B.hoff[i]:B.hoff[i + 1]], ph), (npt, threads, i, "hess")
-                assert abs(fh[i] - pf[0]) <= 1e-12 * abs(pf[0]), (npt, threads, i, "f")
+    for npt, threads in CONFIGS:
+        if not provided(model, npt, threads):
+            with pytest.raises(ocp.OcpError) as e:
+                B.set_config(npt, threads, 0)
+            assert e.value.status == 1
+            continue
+        B.set_config(npt, threads, 0)
+        f, c, g, jv, hv = B.outputs()
+        for t in (f, c, g, jv, hv):
+            t.fill_(float("nan"))
+        B.eval_all(x, y, sigma, f, c, g, jv, hv)
+        torch.cuda.synchronize()
+        fh, ch, gh, jh, hh = (t.cpu().numpy() for t in (f, c, g, jv, hv))
+        for i, (pf, pc, pg, pj, ph) in enumerate(plain):
+            assert np.array_equal(ch[B.coff[i]:B.coff[i + 1]], pc), (npt, threads, i, "c")
+            assert np.array_equal(gh[B.xoff[i]:B.xoff[i + 1]], pg), (npt, threads, i, "g")
+            assert np.array_equal(jh[B.joff[i]:B.joff[i + 1]], pj), (npt, threads, i, "jac")
+            assert np.array_equal(hh[B.hoff[i]:B.hoff[i + 1]], ph), (npt, threads, i, "hess")
+            assert abs(fh[i] - pf[0]) <= 1e-12 * abs(pf[0]), (npt, threads, i, "f")
+
+
+def test_batch_quadrotor_autotune_skips_configs_it_cannot_fit(ocp):
+    """The autotuner times only the configurations the quadrotor's shared memory allows and the
+    tuned batch still equals the plain evaluator slice for slice."""
+    ws = batch_ws("quadrotor", [1, 200, 1003, 64])
+    probs, B, draws, x, y = make(ocp, ws)
+    f, c, g, jv, hv = B.outputs()
+    assert B.autotune(x, y, 1.0, f, c, g, jv, hv) > 0
+    cfg = B.get_config()
+    assert cfg["nodes_per_thread"] * cfg["threads"] <= 128
+    B.eval_all(x, y, 1.0, f, c, g, jv, hv)
+    torch.cuda.synchronize()
+    for i, (P, d) in enumerate(zip(probs, draws)):
+        pc, pj = (t.cpu().numpy() for t in P.eval_all(torch.from_numpy(d["x"]).cuda(),
+                                                      torch.from_numpy(d["y"]).cuda(), 1.0)[2:4])
+        assert np.array_equal(g[B.xoff[i]:B.xoff[i + 1]].cpu().numpy(), pc)
+        assert np.array_equal(jv[B.joff[i]:B.joff[i + 1]].cpu().numpy(), pj)
 
 
 def test_batch_against_oracle_graph_and_autotune(ocp):
