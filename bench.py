@@ -4,7 +4,7 @@ transcription evaluator on GB300, with the HBM roofline fraction of the dominant
 One step = one pass of the hot path on one problem (ocp_eval_step, one launch): objective,
 constraints, gradient, Jacobian and Hessian values and the three products Jv, J^T v and H v.  value = (nnz_J + nnz_H) * steps * ranks / (max over ranks of the summed
 step times).  Inputs are resident in HBM; between timed steps the L2 is flushed by
-writing a 512 MB buffer (outside the timed events).  `e2e` repeats the step through the
+writing a 512 MB buffer and reading it back (outside the timed events; L2Flush).  `e2e` repeats the step through the
 host-buffer call ocp_eval_step_host_async (pinned host arrays in and out, every host<->device
 copy inside the timed region, joined by ocp_host_step_wait before the end event).
 
@@ -183,6 +183,23 @@ def peaks():
         return 6800.0, "fallback"
 
 
+class L2Flush:
+    """Between timed calls: write a 512 MB buffer (four times the 129 MB L2), then read it back
+    (a sum into one float), so that the next call finds none of its data in the L2 and no dirty
+    line of the flush left to write back to DRAM while it runs (a write alone leaves up to the
+    L2's size of dirty lines, whose write-back the next timed call would pay for)."""
+
+    def __init__(self, dev):
+        import torch
+        self.buf = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        self.acc = torch.empty((), dtype=torch.float32, device=dev)
+
+    def __call__(self):
+        import torch
+        self.buf.zero_()
+        torch.sum(self.buf, dim=0, out=self.acc)
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
 
@@ -239,7 +256,8 @@ def bench_config(name, w, n, m, nnzj, nnzh, world):
     """The `config` object of the JSON line (the same keys for both arms)."""
     return dict(workload=name, model=w["model"], N=w["N"], n=n, m=m, nnz_jac=nnzj, nnz_hess=nnzh,
                 step="one pass of the hot path: F, c, grad, J, H, Jv, J^T w, Hv",
-                l2="inputs and outputs (296 MB at the default workload) exceed the L2; flushed between steps",
+                l2="inputs and outputs (296 MB at the default workload) exceed the L2; between steps a 512 MB "
+                   "write and read-back leave it cold and clean (no dirty line of the flush to write back)",
                 parallelism="replicas" if world > 1 else "single")
 
 
@@ -311,7 +329,7 @@ def run_ours(args, rank, world):
     Jv = torch.empty(m, dtype=torch.float64, device=dev)
     Jtv = torch.empty(n, dtype=torch.float64, device=dev)
     Hv = torch.empty(n, dtype=torch.float64, device=dev)
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    flush = L2Flush(dev)
     stream = torch.cuda.current_stream(dev)
     names = ["eval_all", "jprod", "jtprod", "hprod"]
     outs = (f, c, g, jv, hv, Jv, Jtv, Hv)
@@ -332,7 +350,7 @@ def run_ours(args, rank, world):
         ev[4].record(stream)
 
     for _ in range(args.warmup):
-        flush.zero_()
+        flush()
         step()
     torch.cuda.synchronize(dev)
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(args.steps)]
@@ -344,7 +362,7 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     for k in range(args.steps):
-        flush.zero_()
+        flush()
         evs[k][0].record(stream)
         step()
         evs[k][1].record(stream)
@@ -362,7 +380,7 @@ def run_ours(args, rank, world):
     # --- the same work as four separate calls (per-kernel breakdown)
     sev = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(min(args.steps, 50))]
     for ev in sev:
-        flush.zero_()
+        flush()
         separate(ev)
     torch.cuda.synchronize(dev)
     per = np.array([[ev[i].elapsed_time(ev[i + 1]) for i in range(4)] for ev in sev])
@@ -370,7 +388,7 @@ def run_ours(args, rank, world):
     # --- J+H alone (the fused Jacobian+Hessian values launch), timed the same way
     jh = []
     for k in range(min(args.steps, 50)):
-        flush.zero_()
+        flush()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         H.eval_all(x, y, sigma, None, None, None, jv, hv, alloc=False)
@@ -392,7 +410,7 @@ def run_ours(args, rank, world):
             step()
         gt = []
         for k in range(min(args.steps, 50)):
-            flush.zero_()
+            flush()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             graph.replay()
@@ -416,7 +434,7 @@ def run_ours(args, rank, world):
     kv = H.kkt_values(hv, jv, sig_x, 1e-8, 1e-8)
     kk = []
     for k in range(min(args.steps, 50)):
-        flush.zero_()
+        flush()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         H.kkt_values(hv, jv, sig_x, 1e-8, 1e-8, out=kv)
@@ -452,7 +470,7 @@ def run_ours(args, rank, world):
     def time_e2e(fn):
         ms = []
         for k in range(e2e_steps + 2):
-            flush.zero_()
+            flush()
             # the host step's input copy does not wait for earlier work on the stream: the
             # flush must be over before the start event
             torch.cuda.synchronize(dev)
@@ -519,7 +537,7 @@ def run_ours(args, rank, world):
                       # the Jacobian + Hessian values alone (one launch), against the HBM roofline
                       jac_hess=dict(bound="hbm", ms=jh_ms, nnz_per_s=nnz / (jh_ms * 1e-3), achieved=jh_gbps,
                                     peak=hbm, unit="GB/s", frac=jh_gbps / hbm, algorithmic_bytes=jh_bytes,
-                                    peak_source=peak_kind, l2="flushed between calls (512 MB write)")),
+                                    peak_source=peak_kind, l2="flushed between calls (512 MB write, then read back)")),
         roofline_hbm=dict(bound="hbm", achieved=achieved, peak=hbm, unit="GB/s", frac=achieved / hbm,
                           peak_source=peak_kind, algorithmic_bytes=ab,
                           traffic=traffic(w["name"], "step", key)),
@@ -569,14 +587,14 @@ def run_sharded(args, rank, world):
     sigma = w["sigma"]
     x, y, vn, vm = (torch.from_numpy(d[k]).to(dev) for k in ("x", "y", "vn", "vm"))
     outs = tuple(torch.zeros(k, dtype=torch.float64, device=dev) for k in (1, m, n, nnzj, nnzh, m, n, n))
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    flush = L2Flush(dev)
     stream = torch.cuda.current_stream(dev)
 
     def step():
         S.eval_step(x, y, sigma, vn, vm, outs)
 
     for _ in range(args.warmup):
-        flush.zero_()
+        flush()
         step()
     torch.cuda.synchronize(dev)
     sampler = ClockSampler(dev.index) if rank == 0 else None
@@ -586,7 +604,7 @@ def run_sharded(args, rank, world):
     torch.cuda.synchronize(dev)
     evs = []
     for _ in range(args.steps):
-        flush.zero_()
+        flush()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         step()
@@ -660,7 +678,7 @@ def run_widened(name, steps, warmup):
     sigma = w["sigma"]
     f, c, g, jv, hv, Jv, Jtv, Hv = H.eval_step(x, y, sigma, vn, vm)
     outs = (f, c, g, jv, hv, Jv, Jtv, Hv)
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    flush = L2Flush(dev)
     stream = torch.cuda.current_stream(dev)
     calls = {
         "step": lambda: H.eval_step(x, y, sigma, vn, vm, outs),
@@ -676,7 +694,7 @@ def run_widened(name, steps, warmup):
             fn()
         evs = []
         for _ in range(steps if nm == "step" else max(3, steps // 4)):
-            flush.zero_()
+            flush()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             fn()
@@ -823,7 +841,7 @@ def run_forms(args, hbm):
         whole = wg.replay
     except Exception as e:
         whole_err = "%s: %s" % (type(e).__name__, e)
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    flush = L2Flush("cuda")
     res = {}
     fns = ([("autograd", ad_step), ("plain", plain_step)] + ([("graphed", graphed)] if graphed else [])
            + ([("whole_graph", whole)] if whole else []))
@@ -832,7 +850,7 @@ def run_forms(args, hbm):
             fn()
         ts = []
         for _ in range(20):
-            flush.zero_()
+            flush()
             a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a0.record()
             fn()
