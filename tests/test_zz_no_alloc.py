@@ -4,7 +4,7 @@ Such callers (a real-time control loop that must not allocate after start-up, a 
 whose allocator owns all device memory) get the objective from a file-scope device scratch
 array instead of handle-owned scratch.  This test calls that entry point through the C-ABI
 twice in a row, on two different inputs, and compares each result with the handle-based
-eval_obj within the parity tolerance, for every model the entry point serves (Van der Pol,
+eval_obj and with the CPU oracle's objective within the parity tolerance, for every model the entry point serves (Van der Pol,
 cart-pole, heat, double integrator, quadrotor: tiles of 256, 128, 32 and 64 nodes).  After a
 warm-up call (the first call on a device loads the library's kernels and looks up the
 array's address) it checks that the device's free memory is the same before and after two
@@ -76,6 +76,13 @@ def test_noalloc_objective_matches_eval_obj_twice(name, N):
     got = out.cpu().numpy()
     for g, r in zip(got, refs):
         assert abs(g - r) <= 1e-12 * abs(r) + 1e-14, (g, r)
+    # and against the CPU oracle's objective of the same inputs, through the parity gate
+    from oracle import oracle as O
+    P = O.Problem(w)
+    for g, seed in zip(got, [w["seed"], w["seed"] + 77]):
+        d = synth.draw(w, seed=seed)
+        ev = O.evaluate(P, d["x"], d["y"], w["sigma"], shadow=True)
+        assert abs(g - ev["f"]) <= 1e-12 * abs(ev["f"]) + 1e-14 or abs(g - ev["f"]) <= 1e-12 * ev["f_mag"], (g, ev["f"])
     H.close()
 
 
