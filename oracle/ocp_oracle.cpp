@@ -20,10 +20,11 @@
  *         H = sigma * Hess F + sum_r y_r Hess c_r   (lower triangle)
  *     as COO with one entry per structural nonzero, sorted by (row, col);
  *   - the products J v, J^T w, H v, defined as plain COO matrix-vector products;
- *   - (dc/dp)^T w for the first model parameter (the Van der Pol mu).
+ *   - (dc/dp)^T w for every dynamics parameter p (Van der Pol mu; cart-pole mc, mp, l, g;
+ *     Goddard Cd, beta, Tmax, b; quadrotor g): only the defect rows depend on p.
  *
  * Models: Van der Pol, cart-pole, the heat equation by the method of lines, the Sec. 5
- * double integrator and the quadrotor of the paper's appendix.  The running cost is a
+ * double integrator and the Goddard rocket and quadrotor of the paper's appendix.  The running cost is a
  * diagonal quadratic around a reference; the state reference may vary in time as
  * xref_k + xslope_k t + xamp_k sin(xfreq_k t) (the quadrotor's tracking terms), evaluated at
  * the node times t_j = j h.
@@ -491,6 +492,55 @@ template <class S> void quad_hess(const S* z, std::vector<HEnt<S>>& e) {
   e.push_back({8, 11, 7, q.s7 * q.e * q.e});
 }
 
+// Derivatives of the right-hand sides in the dynamics parameters, d[k * np + i] = df_k / dp_i,
+// from the model equations above (np parameters per model: Van der Pol mu; cart-pole mc, mp,
+// l, g; Goddard Cd, beta, Tmax, b; quadrotor g).
+//
+// Cart-pole, with A, B and D as in cp_f and E = l D:  p'' = A / D,  th'' = B / E, and
+//   A_mc = 0,  A_mp = s (l w^2 + g c),  A_l = mp s w^2,  A_g = mp s c;  D_mc = 1, D_mp = s^2;
+//   B_mc = -g s,  B_mp = -l w^2 c s - g s,  B_l = -mp w^2 c s,  B_g = -(mc + mp) s;
+//   E_mc = l,  E_mp = l s^2,  E_l = D,  E_g = 0;
+// so dp''/dq = A_q / D - A D_q / D^2 and dth''/dq = B_q / E - B E_q / E^2.
+template <class S> void cp_dpar(const S* p, const S* z, S* d) {
+  using std::cos; using std::sin;
+  const S mc = p[0], mp = p[1], l = p[2], g = p[3];
+  const S th = z[2], w = z[3], F = z[4];
+  const S s = sin(th), c = cos(th);
+  const S D = mc + mp * s * s, E = l * D;
+  const S A = F + mp * s * (l * w * w + g * c);
+  const S B = S(0.0) - F * c - mp * l * w * w * c * s - (mc + mp) * g * s;
+  const S D2 = D * D, E2 = E * E;
+  for (int i = 0; i < 16; ++i) d[i] = S(0.0);
+  d[4 * 1 + 0] = S(0.0) - A * S(1.0) / D2;
+  d[4 * 1 + 1] = s * (l * w * w + g * c) / D - A * (s * s) / D2;
+  d[4 * 1 + 2] = mp * s * w * w / D;
+  d[4 * 1 + 3] = mp * s * c / D;
+  d[4 * 3 + 0] = (S(0.0) - g * s) / E - B * l / E2;
+  d[4 * 3 + 1] = (S(0.0) - l * w * w * c * s - g * s) / E - B * (l * s * s) / E2;
+  d[4 * 3 + 2] = (S(0.0) - mp * w * w * c * s) / E - B * D / E2;
+  d[4 * 3 + 3] = (S(0.0) - (mc + mp) * s) / E;
+}
+// Goddard:  dv'/dCd = -v^2 exp(-beta (r - 1)) / m,  dv'/dbeta = Cd v^2 (r - 1) exp(-beta (r - 1)) / m,
+// dv'/dTmax = u / m;  dm'/dTmax = -b u,  dm'/db = -Tmax u;  r' = v has none.
+template <class S> void god_dpar(const S* p, const S* z, S* d) {
+  using std::exp;
+  const S Cd = p[0], beta = p[1], Tmax = p[2], b = p[3];
+  const S r = z[0], v = z[1], m = z[2], u = z[3];
+  const S E = exp(S(0.0) - beta * (r - S(1.0)));
+  for (int i = 0; i < 12; ++i) d[i] = S(0.0);
+  d[4 * 1 + 0] = S(0.0) - v * v * E / m;
+  d[4 * 1 + 1] = Cd * v * v * (r - S(1.0)) * E / m;
+  d[4 * 1 + 2] = u / m;
+  d[4 * 2 + 2] = S(0.0) - b * u;
+  d[4 * 2 + 3] = S(0.0) - Tmax * u;
+}
+// Quadrotor: only x6' = u1 R - g depends on g.
+template <class S> void quad_dpar(const S* z, S* d) {
+  (void)z;
+  for (int k = 0; k < 9; ++k) d[k] = S(0.0);
+  d[5] = S(-1.0);
+}
+
 // Dispatch ------------------------------------------------------------------------------
 template <class S> void model_f(const Prob& P, const S* p, const S* z, S* f) {
   switch (P.model) {
@@ -520,6 +570,26 @@ template <class S> void model_hess(const Prob& P, const S* p, const S* z, std::v
     case M_DINT: break;
     case M_QUAD: quad_hess(z, e); break;
     case M_GODDARD: god_hess(p, z, e); break;
+  }
+}
+
+// Number of dynamics parameters with a derivative (the heat cell count is structural; the
+// double integrator has none).
+inline int model_npar(const Prob& P) {
+  switch (P.model) {
+    case M_VDP: return 1;
+    case M_CARTPOLE: return 4;
+    case M_GODDARD: return 4;
+    case M_QUAD: return 1;
+  }
+  return 0;
+}
+template <class S> void model_dpar(const Prob& P, const S* p, const S* z, S* d) {
+  switch (P.model) {
+    case M_VDP: vdp_dpar(p, z, d); break;
+    case M_CARTPOLE: cp_dpar(p, z, d); break;
+    case M_GODDARD: god_dpar(p, z, d); break;
+    case M_QUAD: quad_dpar(z, d); break;
   }
 }
 
@@ -1067,23 +1137,28 @@ template <class S> void coo_symv_lower(const Coo<S>& A, const S* v, S* out, int6
   }
 }
 
-// (dc/dp0)^T w = sum over defect rows of w_r * ( -h (df_k/dp0(z_j) + df_k/dp0(z_{j+1})) / 2 )
-template <class S> S dpar_vjp(const Prob& P, const S* p, const S* x, const S* w) {
+// (dc/dp_i)^T w for every dynamics parameter i.  Only the defect rows depend on p:
+//   dc_{k,j}/dp_i = -h (df_k/dp_i(z_j) + df_k/dp_i(z_{j+1})) / 2   (Euler: -h df_k/dp_i(z_j)),
+// and each sum runs with compensation over k, then j.
+template <class S> void dpar_vjp(const Prob& P, const S* p, const S* x, const S* w, S* out) {
   Layout L(P);
+  const int np = model_npar(P);
   const S h = step_h(P, L, x);
-  std::vector<S> d((size_t)L.nx * (L.N + 1)), z(L.nz);
+  std::vector<S> d((size_t)L.nx * np * (L.N + 1)), z(L.nz);
   for (int64_t j = 0; j < L.nun; ++j) {  // (Euler: node N has no control and no f term)
     gather_node(L, x, j, z.data());
-    vdp_dpar(p, z.data(), &d[(size_t)L.nx * j]);
+    model_dpar(P, p, z.data(), &d[(size_t)L.nx * np * j]);
   }
-  Neumaier<S> acc;
-  for (int k = 0; k < L.nx; ++k)
-    for (int64_t j = 0; j < L.N; ++j) {
-      const S dc = L.euler ? S(0.0) - h * d[(size_t)L.nx * j + k]
-                           : S(0.0) - h * (d[(size_t)L.nx * j + k] + d[(size_t)L.nx * (j + 1) + k]) / S(2.0);
-      acc.add(w[L.defect_row(k, j)] * dc);
-    }
-  return acc.result();
+  auto D = [&](int64_t j, int k, int i) { return d[((size_t)L.nx * j + k) * np + i]; };
+  for (int i = 0; i < np; ++i) {
+    Neumaier<S> acc;
+    for (int k = 0; k < L.nx; ++k)
+      for (int64_t j = 0; j < L.N; ++j) {
+        const S dc = L.euler ? S(0.0) - h * D(j, k, i) : S(0.0) - h * (D(j, k, i) + D(j + 1, k, i)) / S(2.0);
+        acc.add(w[L.defect_row(k, j)] * dc);
+      }
+    out[i] = acc.result();
+  }
 }
 
 // Gradient of the Lagrangian sigma F + y^T c, from the analytic gradient and Jacobian.
@@ -1320,19 +1395,30 @@ int orc_hprod(const Prob* P, const double* x, const double* y, double sigma, con
   return 0;
 }
 
-// (dc/dmu)^T w for the Van der Pol model.
-int orc_dpar_vjp(const Prob* P, const double* x, const double* w, double* out, double* mag) {
+// Number of dynamics parameters with a derivative.
+int orc_npar(const Prob* P) { return model_npar(*P); }
+
+// (dc/dp)^T w for every dynamics parameter (out and mag hold orc_npar entries).
+int orc_dpar_vjp_all(const Prob* P, const double* x, const double* w, double* out, double* mag) {
   int st = check(*P);
   if (st) return st;
-  if (P->model != M_VDP) return 6;
+  const int np = model_npar(*P);
+  if (np == 0) return 6;
   Layout L(*P);
-  { std::vector<double> p(8); params_of(*P, p.data()); *out = dpar_vjp(*P, p.data(), x, w); }
+  { std::vector<double> p(8); params_of(*P, p.data()); dpar_vjp(*P, p.data(), x, w, out); }
   if (mag) {
-    std::vector<Sh> p(8); params_of(*P, p.data());
+    std::vector<Sh> p(8), o(np); params_of(*P, p.data());
     auto X = lift<Sh>(x, L.n); auto W = lift<Sh>(w, L.m);
-    *mag = shadow(dpar_vjp(*P, p.data(), X.data(), W.data()));
+    dpar_vjp(*P, p.data(), X.data(), W.data(), o.data());
+    for (int i = 0; i < np; ++i) mag[i] = shadow(o[i]);
   }
   return 0;
+}
+
+// (dc/dmu)^T w for the Van der Pol model.
+int orc_dpar_vjp(const Prob* P, const double* x, const double* w, double* out, double* mag) {
+  if (P->model != M_VDP) return check(*P) ? check(*P) : 6;
+  return orc_dpar_vjp_all(P, x, w, out, mag);
 }
 
 // Gradient of the Lagrangian (analytic), double.
@@ -1353,6 +1439,20 @@ int orc_cs_cons(const Prob* P, const double* x, const double* dx, double dmu, do
   for (int64_t i = 0; i < L.n; ++i) X[i] = Cx(x[i], eps * dx[i]);
   params_of(*P, p.data());
   p[0] = Cx(P->par[0], eps * dmu);
+  constraints(*P, p.data(), X.data(), c.data());
+  for (int64_t i = 0; i < L.m; ++i) out[i] = c[i].imag() / eps;
+  return 0;
+}
+
+// Complex step along (dx, dp): Im c(x + i eps dx; p + i eps dp) / eps, dp of orc_npar entries.
+int orc_cs_cons_p(const Prob* P, const double* x, const double* dx, const double* dp, double eps, double* out) {
+  int st = check(*P);
+  if (st) return st;
+  Layout L(*P);
+  std::vector<Cx> X(L.n), p(8), c(L.m);
+  for (int64_t i = 0; i < L.n; ++i) X[i] = Cx(x[i], eps * dx[i]);
+  params_of(*P, p.data());
+  for (int i = 0; i < model_npar(*P); ++i) p[i] = Cx(P->par[i], eps * dp[i]);
   constraints(*P, p.data(), X.data(), c.data());
   for (int64_t i = 0; i < L.m; ++i) out[i] = c[i].imag() / eps;
   return 0;

@@ -173,6 +173,21 @@ def dpar_vjp(P, x, w, shadow=False):
     return (o[0], m[0]) if shadow else o[0]
 
 
+def npar(P) -> int:
+    """Number of dynamics parameters with a derivative (Van der Pol 1, cart-pole 4, Goddard 4,
+    quadrotor 1, the others 0)."""
+    return int(lib().orc_npar(P.ref()))
+
+
+def dpar_vjp_all(P, x, w, shadow=False):
+    """(dc/dp)^T w for every dynamics parameter, with its magnitude shadow."""
+    x, w = _f64(x), _f64(w)
+    k = npar(P)
+    o = np.zeros(k); m = np.zeros(k)
+    _check(lib().orc_dpar_vjp_all(P.ref(), _ptr(x), _ptr(w), _ptr(o), _ptr(m)))
+    return (o, m) if shadow else o
+
+
 def lagrangian_grad(P, x, y, sigma):
     x, y = _f64(x), _f64(y)
     o = np.empty(P.n)
@@ -184,6 +199,14 @@ def cs_cons(P, x, dx, dmu=0.0, eps=1e-30):
     x, dx = _f64(x), _f64(dx)
     o = np.empty(P.m)
     _check(lib().orc_cs_cons(P.ref(), _ptr(x), _ptr(dx), C.c_double(dmu), C.c_double(eps), _ptr(o)))
+    return o
+
+
+def cs_cons_p(P, x, dx, dp, eps=1e-30):
+    """Complex step of c along (dx, dp), dp with one entry per dynamics parameter."""
+    x, dx, dp = _f64(x), _f64(dx), _f64(dp)
+    o = np.empty(P.m)
+    _check(lib().orc_cs_cons_p(P.ref(), _ptr(x), _ptr(dx), _ptr(dp), C.c_double(eps), _ptr(o)))
     return o
 
 
