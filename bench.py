@@ -88,7 +88,7 @@ FP64_OPS_PER_NODE = {("vdp", "eval_all"): 26.6, ("vdp", "jh"): 10.0, ("vdp", "jp
                      ("quadrotor", "eval_all"): 250.1, ("quadrotor", "jh"): 176.7, ("quadrotor", "jprod"): 163.4,
                      ("quadrotor", "jtprod"): 155.0, ("quadrotor", "hprod"): 198.0, ("quadrotor", "step"): 397.8,
                      ("goddard", "eval_all"): 98.2, ("goddard", "jh"): 89.2, ("goddard", "jprod"): 66.3,
-                     ("goddard", "jtprod"): 66.2, ("goddard", "hprod"): 93.2, ("goddard", "step"): 153.4,
+                     ("goddard", "jtprod"): 67.1, ("goddard", "hprod"): 93.1, ("goddard", "step"): 153.4,
                      ("vdp:euler", "eval_all"): 21.5, ("vdp:euler", "jh"): 8.0, ("vdp:euler", "jprod"): 11.0,
                      ("vdp:euler", "jtprod"): 10.0, ("vdp:euler", "hprod"): 10.0, ("vdp:euler", "step"): 41.5,
                      # heat, 64 cells: the step is its four kernels in sequence
@@ -108,8 +108,8 @@ KERNEL_SOURCES = {
     "heat64": _COMMON + ["heat_kernels.cu"],
 }
 # Tags of the sources the FP64_OPS_PER_NODE counts (and TRAFFIC) were measured on.
-FP64_OPS_SRC = {"vdp": "959e519151fa", "vdp:euler": "959e519151fa", "cartpole": "ac869dd84ece",
-                "quadrotor": "8e48c9f9ed96", "goddard": "e9a468566ab5", "heat64": "4bdf9bb3981a"}
+FP64_OPS_SRC = {"vdp": "bc6e02341ed5", "vdp:euler": "bc6e02341ed5", "cartpole": "617d024fcabf",
+                "quadrotor": "1438c421633e", "goddard": "ed2db7630e54", "heat64": "894a5428b343"}
 
 
 def kernel_source_tag(key):
@@ -158,7 +158,7 @@ def named_workload(name):
 # DRAM bytes (read + write) of one launch at a workload, from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum; writes still dirty in L2 when the kernel ends
 # are not counted), with the source tag of the kernel it was captured on (see traffic()).
-TRAFFIC = {("vdp_mu_n1e6", "step"): (226.89e6, "959e519151fa")}
+TRAFFIC = {("vdp_mu_n1e6", "step"): (227.35e6, "bc6e02341ed5")}
 # Each SM's FP64 pipe completes 2 FP64 instructions (one lane each) per clock: the recipe's
 # nominal 1.25 TFLOP/s FP64 of GB300 is 6.25e11 FMA/s = 1.99 per clock per SM at 152 SMs and
 # 2070 MHz.  bench.py measures the rate live (measure_fp64_rate) and reports it beside the peak.

@@ -340,8 +340,8 @@ ocp_status ocp_kkt_values(ocp_t* h, const double* hvals, const double* jvals, co
                           double delta_w, double delta_c, double* kvals, void* stream);
 
 /* Parameter derivative for the Van der Pol model (mu = params[0]):
- *   dmu = (dc/dmu)^T w   (device scalar),  optionally together with J^T w into Jtw (may be NULL).
- * Other models: OCP_EMODEL. */
+ *   dmu = (dc/dmu)^T w   (device scalar), together with J^T w into Jtw (both required).
+ * Other models: OCP_EMODEL (ocp_vjp_params covers every model with dynamics parameters). */
 ocp_status ocp_vjp_param(ocp_t* h, const double* x, const double* w, double* Jtw, double* dmu,
                          void* stream);
 
@@ -352,6 +352,34 @@ ocp_status ocp_vjp_param(ocp_t* h, const double* x, const double* w, double* Jtw
 ocp_status ocp_eval_cons_p(ocp_t* h, const double* x, const double* p0, double* c, void* stream);
 ocp_status ocp_vjp_param_p(ocp_t* h, const double* x, const double* w, const double* p0, double* Jtw,
                            double* dmu, void* stream);
+
+/* Derivatives in every dynamics parameter (paper Sec. 3: the dynamics f(x, u; p) enter the
+ * constraints only through the defect rows, Sec. 5 trapezoidal defects, so
+ *   dc_{k,j}/dp = -h (df_k/dp(z_j) + df_k/dp(z_{j+1})) / 2 ).
+ * The parameters with a derivative, in the order of ocp_dynamics.params:
+ *   Van der Pol (mu); cart-pole (m_c, m_p, l, g); Goddard (Cd, beta, Tmax, b); quadrotor (g).
+ * The double integrator has none and the heat model's parameter (its cell count) is structural.
+ * ocp_param_count: *np = the number of those parameters for the handle's model (0, 1 or 4).
+ * ocp_set_params: replace all of them (np = that count, host values, finite) without
+ *   rebuilding the pattern; OCP_EDIM for another count, OCP_EMODEL when the count is 0.
+ * ocp_eval_cons_params: c(x; p) with p read from device memory (np doubles) for this call only
+ *   (NULL: the handle's values, or the Van der Pol binding of ocp_bind_param0).
+ * ocp_vjp_params: J^T w into Jtw (length n) and dp = (dc/dp)^T w (device, np doubles, each a
+ *   fixed-order sum over the nodes: deterministic), with p as in ocp_eval_cons_params.
+ * Trapezoidal scheme only for ocp_vjp_params (OCP_EMODEL under forward Euler); models with
+ * np = 0 return OCP_EMODEL when p or dp is given.  All pointers 8-byte aligned; the call
+ * is asynchronous on `stream` and reads p when its kernels run. */
+ocp_status ocp_param_count(const ocp_t* h, int* np);
+/* ocp_bind_params: later calls on this handle read all np dynamics parameters from device
+ * memory p_dev (NULL unbinds; the memory must stay valid while bound).  Van der Pol: every call
+ * (as ocp_bind_param0).  The other models, trapezoidal scheme: the constraints (eval_cons,
+ * ocp_eval_cons_params), J v, J^T w (with ocp_vjp_params) and H v; their other calls return
+ * OCP_EMODEL while bound (under forward Euler: the constraints only). */
+ocp_status ocp_bind_params(ocp_t* h, const double* p_dev);
+ocp_status ocp_set_params(ocp_t* h, const double* p, int np);
+ocp_status ocp_eval_cons_params(ocp_t* h, const double* x, const double* p, double* c, void* stream);
+ocp_status ocp_vjp_params(ocp_t* h, const double* x, const double* w, const double* p, double* Jtw, double* dp,
+                          void* stream);
 
 /* Set the value of params[0] (e.g. Van der Pol mu) without rebuilding the pattern. */
 ocp_status ocp_set_param0(ocp_t* h, double value);

@@ -1,20 +1,25 @@
 """Differentiation form: torch.autograd.Functions over the transcription evaluator.
 
-  c = constraints(H, x, mu)    c(x; mu), the constraint vector (Van der Pol: mu = params[0])
+  c = constraints(H, x, p)     c(x; p), the constraint vector, p the model's dynamics parameters
+                               (Van der Pol mu; cart-pole m_c, m_p, l, g; Goddard Cd, beta,
+                               Tmax, b; quadrotor g; none for the double integrator and heat)
   F = objective(H, x)          the trapezoidal objective
 
 Every forward and backward step is one launch of the CUDA library; node states are
 recomputed from x in each kernel, never stored.  Derivatives:
-  constraints   forward:   c(x; mu)                              ocp_eval_cons_p
-                backward:  (J^T w, (dc/dmu)^T w)                 ocp_vjp_param_p / jtprod
-                double backward, for cotangents (gx, gmu) of that pair:
+  constraints   forward:   c(x; p)                               ocp_eval_cons_params
+                backward:  (J^T w, (dc/dp)^T w)                  ocp_vjp_params
+                double backward (Van der Pol), for cotangents (gx, gmu) of that pair:
                   w-bar  = J gx + (dc/dmu) gmu                    ocp_jprod_param
                   x-bar  = (sum_r w_r Hess c_r) gx + gmu m(x, w)   ocp_hprod_param (sigma = 0)
                   mu-bar = m(x, w) . gx                            (same launch)
-                where m(x, w) = sum_r w_r d2 c_r / dx dmu  (c is linear in mu: d2c/dmu2 = 0)
+                where m(x, w) = sum_r w_r d2 c_r / dx dmu  (c is linear in mu: d2c/dmu2 = 0);
+                the other models: w-bar = J gx and x-bar = (sum_r w_r Hess c_r) gx, the terms
+                in x alone (second derivatives in their parameters are not provided)
   objective     backward:  s grad F(x)                             ocp_eval_grad_scaled
                 double backward:  x-bar = s Hess F gx,  s-bar = grad F . gx   ocp_obj_hvp
-mu and the upstream scalars stay on the device: the kernels read them through pointers.
+The parameters and the upstream scalars stay on the device: the kernels read them through
+pointers.
 """
 from __future__ import annotations
 
@@ -31,11 +36,12 @@ class _ConsVJP(torch.autograd.Function):
     @staticmethod
     def forward(ctx, H: OCP, x, mu, w):
         ctx.H = H
+        ctx.set_materialize_grads(False)
         ctx.save_for_backward(x, mu, w)
         w = w.contiguous()
-        if H.model == "vdp":
-            gx, gmu = H.vjp_param_p(x, w, mu.reshape(1))
-            return gx, gmu.reshape(mu.shape)
+        if H.nparams > 0:
+            gx, gp = H.vjp_params(x, w, mu.reshape(-1))
+            return gx, gp.reshape(mu.shape)
         return H.jtprod(x, w), torch.zeros_like(mu)
 
     @staticmethod
@@ -50,9 +56,18 @@ class _ConsVJP(torch.autograd.Function):
                 dw = H.jprod_param(x, ggx, s)
                 dx = H.hprod_param(x, w.contiguous(), 0.0, ggx, s, dmu=dmu)
             return None, dx, dmu.reshape(mu.shape), dw
-        dw = H.jprod(x, ggx)
-        dx = H.hprod(x, w.contiguous(), 0.0, ggx)
-        return None, dx, torch.zeros_like(mu), dw
+        if H.nparams > 0 and (ggmu is not None or ctx.needs_input_grad[2]):
+            raise NotImplementedError("second derivatives in the dynamics parameters are provided for the "
+                                      "Van der Pol model; differentiate the %s model's J^T w in x only "
+                                      "(parameters without requires_grad)" % H.model)
+        if H.nparams > 0:
+            with H.params_bound(mu.reshape(-1)):
+                dw = H.jprod(x, ggx)
+                dx = H.hprod(x, w.contiguous(), 0.0, ggx)
+        else:
+            dw = H.jprod(x, ggx)
+            dx = H.hprod(x, w.contiguous(), 0.0, ggx)
+        return None, dx, None, dw
 
 
 class _Constraints(torch.autograd.Function):
@@ -60,7 +75,7 @@ class _Constraints(torch.autograd.Function):
     def forward(ctx, H: OCP, x, mu):
         ctx.H = H
         ctx.save_for_backward(x, mu)
-        return H.eval_cons_p(x, mu.reshape(1) if H.model == "vdp" else None)
+        return H.eval_cons_params(x, mu.reshape(-1) if H.nparams > 0 else None)
 
     @staticmethod
     def backward(ctx, gc):
@@ -68,8 +83,8 @@ class _Constraints(torch.autograd.Function):
         H = ctx.H
         if torch.is_grad_enabled():   # create_graph: the backward itself is differentiated
             gx, gmu = _ConsVJP.apply(H, x, mu, gc.contiguous())
-        elif H.model == "vdp":        # one launch: J^T w and (dc/dmu)^T w
-            gx, gmu = H.vjp_param_p(x, gc.contiguous(), mu.reshape(1))
+        elif H.nparams > 0:           # one launch: J^T w and (dc/dp)^T w
+            gx, gmu = H.vjp_params(x, gc.contiguous(), mu.reshape(-1))
             gmu = gmu.reshape(mu.shape)
         else:
             gx, gmu = H.jtprod(x, gc.contiguous()), torch.zeros_like(mu)
@@ -104,11 +119,13 @@ class _Objective(torch.autograd.Function):
         return None, _ObjGrad.apply(ctx.H, x, gF.reshape(1))
 
 
-def constraints(H: OCP, x: torch.Tensor, mu: torch.Tensor) -> torch.Tensor:
-    """c(x; mu) with backward J^T w (and (dc/dmu)^T w) and a double backward."""
-    if H.model == "vdp" and mu.numel() != 1:
-        raise ValueError("mu must be a one-element tensor")
-    return _Constraints.apply(H, x, mu)
+def constraints(H: OCP, x: torch.Tensor, p: torch.Tensor) -> torch.Tensor:
+    """c(x; p) with backward (J^T w, (dc/dp)^T w) and a double backward.  p holds the model's
+    H.nparams dynamics parameters (Van der Pol: mu alone); for models without parameters
+    (double integrator, heat) it is ignored and receives a zero gradient."""
+    if H.nparams > 0 and p.numel() != H.nparams:
+        raise ValueError("p must hold the %d dynamics parameters of the %s model" % (H.nparams, H.model))
+    return _Constraints.apply(H, x, p)
 
 
 def objective(H: OCP, x: torch.Tensor) -> torch.Tensor:

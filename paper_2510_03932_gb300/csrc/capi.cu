@@ -181,6 +181,18 @@ static int model_nparams(int model) {
   return -1;
 }
 
+// Dynamics parameters with a derivative (the leading entries of params): the heat model's
+// cell count is structural and the double integrator has none.
+static int model_nderiv(int model) {
+  switch (model) {
+    case OCP_MODEL_VDP: return 1;
+    case OCP_MODEL_CARTPOLE: return 4;
+    case OCP_MODEL_GODDARD: return 4;
+    case OCP_MODEL_QUADROTOR: return 1;
+  }
+  return 0;
+}
+
 static void free_handle(ocp* h) {
   if (!h) return;
   ocpg::host_step_free(h);
@@ -277,8 +289,10 @@ ocp_status ocp_create(const ocp_dynamics* dyn, const ocp_cost* cost, int nx, int
     free_handle(h);
     return cuda_err(nullptr, e, "cudaDeviceGetAttribute");
   }
-  // one partial per tile of the smallest tile (31 owned nodes), plus slack
-  h->max_partials = (int)((N + 1) / 31 + 2);
+  // one partial per tile of the smallest tile (31 owned nodes), plus slack: this also holds the
+  // four parameter sums per 128-node chunk of the cart-pole's and six series per 255-node tile
+  // of the Goddard model's (dc/dp)^T w
+  h->max_partials = (int)((N + 1) / 31 + 8);
   if ((e = ocpg::dev_malloc(&h->d_partials, sizeof(double) * h->max_partials)) != cudaSuccess ||
       (e = ocpg::dev_malloc(&h->d_counter, sizeof(unsigned))) != cudaSuccess ||
       (e = cudaMemset(h->d_counter, 0, sizeof(unsigned))) != cudaSuccess) {
@@ -676,6 +690,55 @@ ocp_status ocp_vjp_param_p(ocp_t* h, const double* x, const double* w, const dou
   return dispatch_prod(h, c, stream);
 }
 
+ocp_status ocp_param_count(const ocp_t* h, int* np) {
+  OCP_RANGE();
+  if (!h || !np) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
+  *np = model_nderiv(h->model);
+  return OCP_OK;
+}
+
+ocp_status ocp_set_params(ocp_t* h, const double* p, int np) {
+  OCP_RANGE();
+  if (!h) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
+  const int want = model_nderiv(h->model);
+  if (want == 0) return set_err(h, OCP_EMODEL, "the model has no dynamics parameters with a derivative");
+  if (np != want) return set_err(h, OCP_EDIM, "wrong number of dynamics parameters");
+  if (!p) return set_err(h, OCP_EINVAL, "p is NULL");
+  for (int i = 0; i < np; ++i)
+    if (!std::isfinite(p[i])) return set_err(h, OCP_EINVAL, "parameters must be finite");
+  for (int i = 0; i < np; ++i) h->params[i] = p[i];
+  return OCP_OK;
+}
+
+ocp_status ocp_eval_cons_params(ocp_t* h, const double* x, const double* p, double* cv, void* stream) {
+  OCP_RANGE();
+  if (!h) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
+  NEED(x); NEED(cv); OPT(p);
+  if (p && model_nderiv(h->model) == 0)
+    return set_err(h, OCP_EMODEL, "the model has no dynamics parameters with a derivative");
+  ParamScope ps(h, p);
+  EvalCall c = full_call(h);
+  c.x = x; c.c = cv;
+  return dispatch_eval(h, O_C, c, stream);
+}
+
+ocp_status ocp_vjp_params(ocp_t* h, const double* x, const double* w, const double* p, double* Jtw, double* dp,
+                          void* stream) {
+  OCP_RANGE();
+  if (!h) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
+  if (model_nderiv(h->model) == 0)
+    return set_err(h, OCP_EMODEL, "the model has no dynamics parameters with a derivative");
+  NEED(x); NEED(w); NEED(Jtw); NEED(dp); OPT(p);
+  ParamScope ps(h, p);
+  ProdCall c;
+  c.kind = P_JTPROD; c.x = x; c.v = w; c.out = Jtw; c.dmu = dp;
+  return dispatch_prod(h, c, stream);
+}
+
 ocp_status ocp_vjp_param(ocp_t* h, const double* x, const double* w, double* Jtw, double* dmu, void* stream) {
   OCP_RANGE();
   if (!h) return OCP_EINVAL;
@@ -695,6 +758,17 @@ ocp_status ocp_bind_param0(ocp_t* h, const double* p0_dev) {
     return set_err(h, OCP_EMODEL, "a device parameter is provided for the Van der Pol model");
   OPT(p0_dev);
   h->p0_dev = p0_dev;
+  return OCP_OK;
+}
+
+ocp_status ocp_bind_params(ocp_t* h, const double* p_dev) {
+  OCP_RANGE();
+  if (!h) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
+  if (p_dev && model_nderiv(h->model) == 0)
+    return set_err(h, OCP_EMODEL, "the model has no dynamics parameters with a derivative");
+  OPT(p_dev);
+  h->p0_dev = p_dev;
   return OCP_OK;
 }
 

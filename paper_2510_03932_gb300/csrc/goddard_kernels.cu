@@ -17,6 +17,9 @@
 //   d2v'/dr2 = -beta^2 D - 6/r^4,  d2v'/dv dr = -beta dv'/dv,  d2v'/dv2 = -2 Cd E / m,
 //   d2v'/dm dr = -beta D / m,  d2v'/dm dv = -(dv'/dv) / m,  d2v'/dm2 = 2 (u Tmax / m - D) / m^2,
 //   d2v'/du dm = -Tmax / m^2.
+// Parameter derivatives (p = (Cd, beta, Tmax, b)), for (dc/dp)^T w next to J^T w:
+//   dv'/dCd = -v^2 E / m,  dv'/dbeta = (r - 1) D,  dv'/dTmax = u / m,
+//   dm'/dTmax = -b u,  dm'/db = -Tmax u.
 //
 // Work decomposition as for the other node models: a CTA of GT threads evaluates GT
 // consecutive nodes and owns the first GT-1 (consecutive tiles overlap by one node), the
@@ -39,15 +42,17 @@ struct GodArgs {
   const double* __restrict__ vm;   // direction of J^T w (length m)
   double *f, *c, *g, *jv, *hv;
   double *ojv, *ojtv, *ohv;        // products
-  double* partials;                // 2 x ntiles tile sums (tf components of J^T w and H v)
+  double* partials;                // tile sums: tf components of J^T w and H v, then (dc/dp)^T w
   unsigned* counter;
+  const double* p_dev;             // G_PAR: (Cd, beta, Tmax, b) read from the device
+  double* dpar;                    // G_DP: (dc/dp)^T w, 4 doubles
   int64_t N, nb, uoff, tau, ntiles;  // tau: index of tf in x (n - 1)
   int64_t jbase[3];                  // first slot of the defect rows of each component
   int64_t hbase_u, hbase_t;          // Hessian slots: U block, tf row
   int hu, hpos_um;                   // U block entries per node; position of (u, m) in it
   double hh_fixed;                   // h / 2 of a fixed horizon
   double kappa;                      // 1 / (2N)
-  double Cd, beta, Tmax, bT;         // bT = b Tmax
+  double Cd, beta, Tmax, b, bT;      // bT = b Tmax
   double mayer[3];
   int finpos[3];                     // row of X_{N,k} among the final rows, or -1
   double one, mz;                    // 1.0 and -0.0 at run time (sums and products as FMAs)
@@ -58,9 +63,15 @@ __device__ __forceinline__ double gadd(const GodArgs& a, double p, double q) { r
 __device__ __forceinline__ double gsub(const GodArgs& a, double p, double q) { return fma(-q, a.one, p); }
 __device__ __forceinline__ double gmul(const GodArgs& a, double p, double q) { return fma(p, q, a.mz); }
 
-// Last CTA to finish adds the 2 x ntiles tile sums in tile order (see finish_tiles).
-__device__ __forceinline__ void finish_two(const double* partials, int64_t ntiles, unsigned* counter, double* d0,
-                                           double* d1, double* red) {
+// Variant bits of k_god beside the outputs: G_DP adds (dc/dp)^T w to J^T w, G_PAR reads the
+// parameters from the device.
+constexpr unsigned G_DP = 1u << 10, G_PAR = 1u << 11;
+
+// Last CTA to finish adds each series q < COUNT of tile sums, partials[q * ntiles + tile], in
+// tile order (see finish_tiles) into dst[q] (skipped where null).
+template <int COUNT>
+__device__ __forceinline__ void finish_sums(const double* partials, int64_t ntiles, unsigned* counter,
+                                            double* const (&dst)[COUNT], double* red) {
   __shared__ int s_last;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -71,18 +82,15 @@ __device__ __forceinline__ void finish_two(const double* partials, int64_t ntile
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  double s0 = 0.0, s1 = 0.0;
-  for (int64_t i = threadIdx.x; i < ntiles; i += GT) {
-    s0 = s0 + __ldcg(partials + i);
-    s1 = s1 + __ldcg(partials + ntiles + i);
+#pragma unroll 1
+  for (int q = 0; q < COUNT; ++q) {
+    if (!dst[q]) continue;  // CTA-uniform
+    double sq = 0.0;
+    for (int64_t i = threadIdx.x; i < ntiles; i += GT) sq = sq + __ldcg(partials + q * ntiles + i);
+    sq = cta_sum<GT>(sq, red);
+    if (threadIdx.x == 0) *dst[q] = sq;
   }
-  s0 = cta_sum<GT>(s0, red);
-  s1 = cta_sum<GT>(s1, red);
-  if (threadIdx.x == 0) {
-    if (d0) *d0 = s0;
-    if (d1) *d1 = s1;
-    *counter = 0u;
-  }
+  if (threadIdx.x == 0) *counter = 0u;
 }
 
 template <unsigned OUT, bool FREE>
@@ -91,6 +99,8 @@ __global__ void __launch_bounds__(GT) k_god(const __grid_constant__ GodArgs a) {
   constexpr bool WJV = OUT & O_JV, WJTV = OUT & O_JTV, WHV = OUT & O_HV;
   constexpr bool NEEDD = WJ || WH || WJV || WJTV || WHV;   // first derivatives of f
   constexpr bool RED = FREE && (WJTV || WHV);              // tf components of the products
+  constexpr bool DP = WJTV && (OUT & G_DP);                // (dc/dp)^T w
+  constexpr bool PAR = OUT & G_PAR;
   constexpr int F1 = FREE ? 1 : 0;
   constexpr int CR = 4 + F1, CV = 8 + F1, CM = 4 + F1;     // entries per defect row of r, v, m
   constexpr int R = GT - 1;
@@ -112,6 +122,10 @@ __global__ void __launch_bounds__(GT) k_god(const __grid_constant__ GodArgs a) {
     hh = sHH;
   }
   const double mhh = -hh, mk = -a.kappa;
+  // the parameters: kernel arguments, or device memory with PAR (bT = b Tmax as on the host)
+  const double Cd = PAR ? __ldg(a.p_dev) : a.Cd, beta = PAR ? __ldg(a.p_dev + 1) : a.beta;
+  const double Tmax = PAR ? __ldg(a.p_dev + 2) : a.Tmax, bpar = PAR ? __ldg(a.p_dev + 3) : a.b;
+  const double bT = PAR ? gmul(a, bpar, Tmax) : a.bT;
   double vt = 0.0;  // tf component of the direction
   if (FREE && (WJV || WHV)) vt = __ldg(a.vn + a.tau);
 
@@ -130,17 +144,18 @@ __global__ void __launch_bounds__(GT) k_god(const __grid_constant__ GodArgs a) {
     double pa[3] = {0.0, 0.0, 0.0}, pb[3] = {0.0, 0.0, 0.0};
     double jA[3] = {0.0, 0.0, 0.0}, jB[3] = {0.0, 0.0, 0.0}, fk[3] = {0.0, 0.0, 0.0};
     double accJ = 0.0, accH = 0.0;
+    double accP[4] = {0.0, 0.0, 0.0, 0.0};
     if (act) {
       const double r = __ldg(a.x + 3 * j), v = __ldg(a.x + 3 * j + 1), m = __ldg(a.x + 3 * j + 2);
       const double u = __ldg(a.x + a.uoff + j);
-      const double E = exp(fma(-a.beta, r, a.beta));          // exp(-beta (r - 1))
+      const double E = exp(fma(-beta, r, beta));          // exp(-beta (r - 1))
       const double im = recip(a.one, m), ir = recip(a.one, r);
       const double ir2 = gmul(a, ir, ir);
-      const double q1 = gmul(a, gmul(a, a.Cd, E), im);        // Cd E / m
+      const double q1 = gmul(a, gmul(a, Cd, E), im);        // Cd E / m
       const double D = gmul(a, gmul(a, q1, v), v);
-      const double aU = gmul(a, a.Tmax, im);                  // dv'/du = Tmax / m
+      const double aU = gmul(a, Tmax, im);                  // dv'/du = Tmax / m
       const double fv = fma(u, aU, -gadd(a, D, ir2));
-      const double fm = gmul(a, -a.bT, u);
+      const double fm = gmul(a, -bT, u);
       pa[0] = fma(hh, v, r);  pb[0] = fma(mhh, v, r);
       pa[1] = fma(hh, fv, v); pb[1] = fma(mhh, fv, v);
       pa[2] = fma(hh, fm, m); pb[2] = fma(mhh, fm, m);
@@ -150,12 +165,12 @@ __global__ void __launch_bounds__(GT) k_god(const __grid_constant__ GodArgs a) {
         fk[2] = gmul(a, mk, fm);
       }
       if (NEEDD) {
-        const double ar = fma(a.beta, D, gmul(a, 2.0, gmul(a, ir2, ir)));   // beta D + 2/r^3
+        const double ar = fma(beta, D, gmul(a, 2.0, gmul(a, ir2, ir)));   // beta D + 2/r^3
         const double av = gmul(a, -2.0, gmul(a, q1, v));                     // -2 Cd v E / m
         const double am = gmul(a, gsub(a, D, gmul(a, u, aU)), im);          // (D - u Tmax/m) / m
         // Jacobian values without the identity: -hh df/dz
         const double jr = gmul(a, mhh, ar), jvv = gmul(a, mhh, av), jm = gmul(a, mhh, am);
-        const double ju = gmul(a, mhh, aU), jmu = gmul(a, hh, a.bT);
+        const double ju = gmul(a, mhh, aU), jmu = gmul(a, hh, bT);
         if (sJ) {  // left part of row t, right part of row t-1
           if (t < nrows) {
             double* rr = sm + t * CR;
@@ -225,6 +240,13 @@ __global__ void __launch_bounds__(GT) k_god(const __grid_constant__ GodArgs a) {
           a.ojtv[3 * j] = o[0]; a.ojtv[3 * j + 1] = o[1]; a.ojtv[3 * j + 2] = o[2];
           a.ojtv[a.uoff + j] = o[3];
           if (FREE) accJ = fma(wb[0], fk[0], fma(wb[1], fk[1], gmul(a, wb[2], fk[2])));
+          if (DP) {  // sum_k wbar_k (-hh df_k/dp_i)
+            const double vEm = gmul(a, gmul(a, gmul(a, E, im), v), v);        // v^2 E / m
+            accP[0] = gmul(a, wb[1], gmul(a, hh, vEm));
+            accP[1] = gmul(a, wb[1], gmul(a, mhh, gmul(a, D, gsub(a, r, a.one))));
+            accP[2] = fma(wb[1], gmul(a, mhh, gmul(a, u, im)), gmul(a, wb[2], gmul(a, hh, gmul(a, bpar, u))));
+            accP[3] = gmul(a, wb[2], gmul(a, hh, gmul(a, Tmax, u)));
+          }
         }
         if (doH && own) {
           // multiplier sums ybar_k = y_{k,j-1} + y_{k,j} (v always; r and m for the tf row)
@@ -241,10 +263,10 @@ __global__ void __launch_bounds__(GT) k_god(const __grid_constant__ GodArgs a) {
           const double y1 = gmul(a, mhh, yb[1]);
           const double ir4 = gmul(a, ir2, ir2);
           double hd[7];
-          hd[0] = gmul(a, y1, fma(-gmul(a, a.beta, a.beta), D, gmul(a, -6.0, ir4)));   // (r, r)
-          hd[1] = gmul(a, y1, gmul(a, -a.beta, av));                                 // (v, r)
+          hd[0] = gmul(a, y1, fma(-gmul(a, beta, beta), D, gmul(a, -6.0, ir4)));   // (r, r)
+          hd[1] = gmul(a, y1, gmul(a, -beta, av));                                 // (v, r)
           hd[2] = gmul(a, y1, gmul(a, -2.0, q1));                                    // (v, v)
-          hd[3] = gmul(a, y1, gmul(a, gmul(a, -a.beta, D), im));                     // (m, r)
+          hd[3] = gmul(a, y1, gmul(a, gmul(a, -beta, D), im));                     // (m, r)
           hd[4] = gmul(a, y1, gmul(a, -av, im));                                     // (m, v)
           hd[5] = gmul(a, y1, gmul(a, gmul(a, 2.0, gsub(a, gmul(a, u, aU), D)), gmul(a, im, im)));  // (m, m)
           hd[6] = gmul(a, y1, gmul(a, -aU, im));                                     // (u, m)
@@ -253,7 +275,7 @@ __global__ void __launch_bounds__(GT) k_god(const __grid_constant__ GodArgs a) {
             tr = gmul(a, mk, gmul(a, yb[1], ar));
             tv = gmul(a, mk, fma(yb[1], av, yb[0]));
             tm = gmul(a, mk, gmul(a, yb[1], am));
-            tu = gmul(a, mk, fma(yb[1], aU, gmul(a, -a.bT, yb[2])));
+            tu = gmul(a, mk, fma(yb[1], aU, gmul(a, -bT, yb[2])));
           }
           if (sH) {
 #pragma unroll
@@ -369,9 +391,21 @@ __global__ void __launch_bounds__(GT) k_god(const __grid_constant__ GodArgs a) {
       }
     }
     __syncthreads();
+    if (DP) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const double si = tile_sum<GT>(accP[i], red0, a.one);
+        if (t == 0) a.partials[(2 + i) * a.ntiles + tile] = si;
+        __syncthreads();
+      }
+    }
   }
-  if (RED) finish_two(a.partials, a.ntiles, a.counter, WJTV ? a.ojtv + a.tau : nullptr,
-                      WHV ? a.ohv + a.tau : nullptr, red0);
+  if (RED || DP) {
+    double* const dst[6] = {(RED && WJTV) ? a.ojtv + a.tau : nullptr, (RED && WHV) ? a.ohv + a.tau : nullptr,
+                            DP ? a.dpar : nullptr, DP ? a.dpar + 1 : nullptr, DP ? a.dpar + 2 : nullptr,
+                            DP ? a.dpar + 3 : nullptr};
+    finish_sums<6>(a.partials, a.ntiles, a.counter, dst, red0);
+  }
 }
 
 // ======================================================================================
@@ -397,7 +431,9 @@ static void fill_god(const ocp* h, GodArgs& a) {
   a.Cd = h->params[0];
   a.beta = h->params[1];
   a.Tmax = h->params[2];
+  a.b = h->params[3];
   a.bT = h->params[3] * h->params[2];
+  a.p_dev = h->p0_dev;
   for (int k = 0; k < 3; ++k) a.mayer[k] = h->mayer.empty() ? 0.0 : h->mayer[k];
   for (int k = 0; k < 3; ++k) a.finpos[k] = -1;
   for (size_t i = 0; i < P.fin.size(); ++i) a.finpos[P.fin[i]] = (int)i;
@@ -412,7 +448,7 @@ static cudaError_t god_launch(const GodArgs& a, cudaStream_t s) {
   constexpr int F1 = FREE ? 1 : 0;
   const size_t smem = (OUT & O_J) ? sizeof(double) * (size_t)(16 + 3 * F1) * (GT - 1) : 0;
   const int grid = (int)(a.ntiles < 0x7fffffff ? a.ntiles : 0x7fffffff);
-  k_god<OUT, FREE><<<grid, GT, smem, s>>>(a);
+  k_god<OUT, FREE><<<grid, GT, smem, s>>>(a);  // (G_DP, G_PAR bits in OUT)
   return cudaGetLastError();
 }
 
@@ -430,6 +466,10 @@ ocp_status goddard_eval(ocp* h, unsigned out, const EvalCall& c, cudaStream_t s)
   a.x = c.x; a.y = c.y; a.f = c.f; a.c = c.c; a.g = c.g; a.jv = c.jv; a.hv = c.hv;
   a.vn = c.vn; a.vm = c.vm; a.ojv = c.ojv; a.ojtv = c.ojtv; a.ohv = c.ohv;
   cudaError_t e;
+  if (a.p_dev) {  // device parameters: the constraints alone
+    if (out != O_C) return set_err(h, OCP_EMODEL, "device parameters: the constraints only");
+    return cuda_err(h, god_launch_tf<O_ALL | G_PAR>(h, a, s), "Goddard kernel launch");
+  }
   switch (out) {
     case O_STEP: e = god_launch_tf<O_STEP>(h, a, s); break;
     case O_J | O_H: e = god_launch_tf<O_J | O_H>(h, a, s); break;
@@ -442,17 +482,22 @@ ocp_status goddard_prod(ocp* h, const ProdCall& c, cudaStream_t s) {
   GodArgs a;
   fill_god(h, a);
   if (2 * a.ntiles > h->max_partials) return set_err(h, OCP_EDIM, "too many tiles for the reduction scratch");
+  if (c.kind == P_JTPROD && (c.B != 0 || (c.E >= 0 && c.E != h->N + 1)))
+    return set_err(h, OCP_EMODEL, "node ranges are not provided for the Goddard model");
   a.x = c.x;
   cudaError_t e;
+  const bool par = a.p_dev != nullptr;  // device-resident parameters
   if (c.kind == P_JPROD) {
     a.vn = c.v; a.ojv = c.out;
-    e = god_launch_tf<O_JV>(h, a, s);
+    e = par ? god_launch_tf<O_JV | G_PAR>(h, a, s) : god_launch_tf<O_JV>(h, a, s);
   } else if (c.kind == P_JTPROD) {
-    a.vm = c.v; a.ojtv = c.out;
-    e = god_launch_tf<O_JTV>(h, a, s);
+    a.vm = c.v; a.ojtv = c.out; a.dpar = c.dmu;
+    if (c.dmu && 6 * a.ntiles > h->max_partials) return set_err(h, OCP_EDIM, "too many tiles for the reduction scratch");
+    if (!c.dmu) e = par ? god_launch_tf<O_JTV | G_PAR>(h, a, s) : god_launch_tf<O_JTV>(h, a, s);
+    else e = par ? god_launch_tf<O_JTV | G_DP | G_PAR>(h, a, s) : god_launch_tf<O_JTV | G_DP>(h, a, s);
   } else {
     a.y = c.y; a.vn = c.v; a.ohv = c.out;
-    e = god_launch_tf<O_HV>(h, a, s);
+    e = par ? god_launch_tf<O_HV | G_PAR>(h, a, s) : god_launch_tf<O_HV>(h, a, s);
   }
   return cuda_err(h, e, "Goddard product launch");
 }

@@ -69,6 +69,10 @@ __device__ __forceinline__ double recip(double one, double d) {
   return fma(r, e, r);
 }
 
+// Size of a per-parameter array of model M (at least 1; M::NP = 0 has no parameters).
+template <class M>
+__host__ __device__ constexpr int npa() { return M::NP > 0 ? M::NP : 1; }
+
 #define OCP_TABLE1(NAME, TYPE, N, ...)                       \
   __host__ __device__ static constexpr TYPE NAME(int k) {    \
     constexpr TYPE t[N] = __VA_ARGS__;                       \

@@ -24,7 +24,7 @@ namespace ocpg {
 //   thdd_tw = (B_tw / l - thdd_w D') / D                B_tw = -2 mp l w (c^2 - s^2)
 //   thdd_ww = -2 mp c s / D,   thdd_tF = (s / l - thdd_F D') / D
 // Constants: c[0]=mc, c[1]=mp, c[2]=l, c[3]=g, c[4]=(mc+mp) g, c[5]=1/l, c[6]=mp l, c[7]=2 mp,
-//            c[8]=mp g, c[9]=2 mp l, c[10]=4 g, c[11]=hh/l, c[12]=-hh/l, c[13]=3 mp l.
+//            c[8]=mp g, c[9]=2 mp l, c[10]=4 g, c[11]=hh/l, c[12]=-hh/l, c[13]=3 mp l, c[14]=mc+mp.
 // The kernels carry the angular acceleration scaled by l, Bu = B / D = l thdd, and its
 // derivatives (Bu_t = (B_t - Bu D') / D, Bu_w = B_w / D, Bu_F = -c / D): the 1/l then enters
 // only through the constants hh/l (defects, Jacobian) and the multiplier of the Hessian terms.
@@ -44,19 +44,32 @@ struct CartPole {
   OCP_TABLE1(HA, int, NHD, {2, 3, 3, 4})
   OCP_TABLE1(HB, int, NHD, {2, 2, 3, 2})
   static constexpr bool HAS_DPARAM = false;
+  static constexpr int NP = 4;  // (mc, mp, l, g)
+  OCP_TABLE2(DP, bool, NX, NP, {{false, false, false, false}, {true, true, true, true},
+                                {false, false, false, false}, {true, true, true, true}})
 
-  static void host_consts(const double* p, double hh, ModelConst& mc) {
-    mc.hh = hh;
-    mc.mhh = -hh;
-    mc.one = 1.0;
-    mc.mz = -0.0;
+  // The parameter-dependent constants (the same arithmetic on the host and on the device).
+  __host__ __device__ static void param_consts(const double* p, double hh, ModelConst& mc) {
     const double m_c = p[0], m_p = p[1], l = p[2], g = p[3];
     mc.c[0] = m_c; mc.c[1] = m_p; mc.c[2] = l; mc.c[3] = g;
     mc.c[4] = (m_c + m_p) * g; mc.c[5] = 1.0 / l; mc.c[6] = m_p * l; mc.c[7] = 2.0 * m_p;
     mc.c[8] = m_p * g; mc.c[9] = 2.0 * m_p * l; mc.c[10] = 4.0 * g;
     mc.c[11] = hh * (1.0 / l); mc.c[12] = -(hh * (1.0 / l)); mc.c[13] = 3.0 * m_p * l;
+    mc.c[14] = m_c + m_p;
+  }
+  static void host_consts(const double* p, double hh, ModelConst& mc) {
+    mc.hh = hh;
+    mc.mhh = -hh;
+    mc.one = 1.0;
+    mc.mz = -0.0;
+    param_consts(p, hh, mc);
   }
   __device__ __forceinline__ static void device_param(ModelConst&, double) {}
+  // Parameters from device memory: the constants recomputed (hh, one and mz stay as launched).
+  __device__ __forceinline__ static void device_params(ModelConst& K, const double* p) {
+    const double q[4] = {__ldg(p), __ldg(p + 1), __ldg(p + 2), __ldg(p + 3)};
+    param_consts(q, K.hh, K);
+  }
 
   template <bool WC, bool WJ, bool WH>
   __device__ __forceinline__ static void eval(const ModelConst& K, const double (&z)[NZ], const double (&yb)[NX],
@@ -139,6 +152,40 @@ struct CartPole {
   }
   __device__ __forceinline__ static void dparam(const ModelConst&, const double (&)[NZ], double (&mdp)[NX]) {
     mdp[0] = mdp[1] = mdp[2] = mdp[3] = 0.0;
+  }
+  // -hh df_k/dp_i for p = (mc, mp, l, g), from pdd = A / D and thdd = Bu / l with A, B, D as in
+  // eval (D_mc = 1, D_mp = s^2; A and B are linear in each parameter):
+  //   dpdd/dmc = -pdd / D,            dpdd/dmp = s (l w^2 + g c - pdd s) / D,
+  //   dpdd/dl  = mp s w^2 / D,        dpdd/dg  = mp s c / D,
+  //   dthdd/dmc = -(g s + Bu) / (l D), dthdd/dmp = -s (l w^2 c + g + Bu s) / (l D),
+  //   dthdd/dl  = -(mp s w^2 c / D + Bu / l) / l,   dthdd/dg = -(mc + mp) s / (l D).
+  __device__ __forceinline__ static void dparams(const ModelConst& K, const double (&z)[NZ], double (&mdp)[NX][NP]) {
+    const double mp = K.c[1], l = K.c[2], g = K.c[3];
+    const double th = z[2], w = z[3], F = z[4];
+    double s, c;
+    sincos(th, &s, &c);
+    const double ms = fmul(K, mp, s);
+    const double D = fma(ms, s, K.c[0]);
+    const double iD = recip(K.one, D);
+    const double w2 = fmul(K, w, w);
+    const double lw2 = fmul(K, l, w2);
+    const double gl = fma(g, c, lw2);                 // l w^2 + g c
+    const double pdd = fmul(K, fma(ms, gl, F), iD);
+    const double B = fma(-s, fma(fmul(K, K.c[6], w2), c, K.c[4]), fmul(K, -F, c));
+    const double Bu = fmul(K, B, iD);
+    const double mhiD = fmul(K, K.mhh, iD), mhhilD = fmul(K, K.c[12], iD);
+#pragma unroll
+    for (int k = 0; k < NX; ++k)
+#pragma unroll
+      for (int i = 0; i < NP; ++i) mdp[k][i] = 0.0;
+    mdp[1][0] = fmul(K, -mhiD, pdd);
+    mdp[1][1] = fmul(K, mhiD, fmul(K, s, fma(-pdd, s, gl)));
+    mdp[1][2] = fmul(K, mhiD, fmul(K, ms, w2));
+    mdp[1][3] = fmul(K, mhiD, fmul(K, ms, c));
+    mdp[3][0] = fmul(K, mhhilD, -fma(g, s, Bu));
+    mdp[3][1] = fmul(K, mhhilD, fmul(K, -s, fma(lw2, c, fma(Bu, s, g))));
+    mdp[3][2] = fmul(K, K.c[12], -fma(fmul(K, ms, fmul(K, w2, c)), iD, fmul(K, Bu, K.c[5])));
+    mdp[3][3] = fmul(K, mhhilD, fmul(K, -K.c[14], s));
   }
   __device__ __forceinline__ static void dparam_grad(const ModelConst&, const double (&)[NZ], const double (&)[NX],
                                                      double (&out)[NZ]) {

@@ -22,6 +22,8 @@ struct Dint {
   OCP_TABLE1(HA, int, 1, {0})
   OCP_TABLE1(HB, int, 1, {0})
   static constexpr bool HAS_DPARAM = false;
+  static constexpr int NP = 0;  // no parameters
+  OCP_TABLE2(DP, bool, NX, 1, {{false}, {false}})
 
   static void host_consts(const double*, double hh, ModelConst& mc) {
     mc.hh = hh;
@@ -30,6 +32,7 @@ struct Dint {
     mc.mz = -0.0;
   }
   __device__ __forceinline__ static void device_param(ModelConst&, double) {}
+  __device__ __forceinline__ static void device_params(ModelConst&, const double*) {}
 
   template <bool WC, bool WJ, bool WH>
   __device__ __forceinline__ static void eval(const ModelConst& K, const double (&z)[NZ], const double (&)[NX],
@@ -50,6 +53,9 @@ struct Dint {
   }
   __device__ __forceinline__ static void dparam(const ModelConst&, const double (&)[NZ], double (&mdp)[NX]) {
     mdp[0] = 0.0; mdp[1] = 0.0;
+  }
+  __device__ __forceinline__ static void dparams(const ModelConst&, const double (&)[NZ], double (&mdp)[NX][1]) {
+    mdp[0][0] = 0.0; mdp[1][0] = 0.0;
   }
   __device__ __forceinline__ static void dparam_grad(const ModelConst&, const double (&)[NZ], const double (&)[NX],
                                                      double (&out)[NZ]) {

@@ -48,6 +48,8 @@ struct Quadrotor {
   OCP_TABLE1(HA, int, NHD, {6, 7, 7, 8, 8, 8, 9, 9, 9, 10, 10, 11, 11})
   OCP_TABLE1(HB, int, NHD, {6, 6, 7, 6, 7, 8, 6, 7, 8, 6, 7, 6, 7})
   static constexpr bool HAS_DPARAM = false;
+  static constexpr int NP = 1;  // g
+  OCP_TABLE2(DP, bool, NX, NP, {{false}, {false}, {false}, {false}, {false}, {true}, {false}, {false}, {false}})
 
   static void host_consts(const double* p, double hh, ModelConst& mc) {
     mc.hh = hh;
@@ -57,6 +59,7 @@ struct Quadrotor {
     mc.c[0] = p[0];
   }
   __device__ __forceinline__ static void device_param(ModelConst&, double) {}
+  __device__ __forceinline__ static void device_params(ModelConst& K, const double* p) { K.c[0] = __ldg(p); }
 
   template <bool WC, bool WJ, bool WH>
   __device__ __forceinline__ static void eval(const ModelConst& K, const double (&z)[NZ], const double (&yb)[NX],
@@ -148,6 +151,12 @@ struct Quadrotor {
   }
   __device__ __forceinline__ static void dparam(const ModelConst&, const double (&)[NZ], double (&mdp)[NX]) {
     for (int k = 0; k < NX; ++k) mdp[k] = 0.0;
+  }
+  // -hh df_k/dg: only x6' = u1 R - g depends on g
+  __device__ __forceinline__ static void dparams(const ModelConst& K, const double (&)[NZ], double (&mdp)[NX][NP]) {
+#pragma unroll
+    for (int k = 0; k < NX; ++k) mdp[k][0] = 0.0;
+    mdp[5][0] = K.hh;
   }
   __device__ __forceinline__ static void dparam_grad(const ModelConst&, const double (&)[NZ], const double (&)[NX],
                                                      double (&out)[NZ]) {

@@ -26,6 +26,8 @@ struct VdP {
   OCP_TABLE1(HA, int, NHD, {0, 1})
   OCP_TABLE1(HB, int, NHD, {0, 0})
   static constexpr bool HAS_DPARAM = true;
+  static constexpr int NP = 1;  // mu
+  OCP_TABLE2(DP, bool, NX, NP, {{false}, {true}})
 
   static void host_consts(const double* p, double hh, ModelConst& mc) {
     mc.hh = hh;
@@ -42,6 +44,7 @@ struct VdP {
     K.c[1] = K.hh * mu;
     K.c[2] = -K.c[1];
   }
+  __device__ __forceinline__ static void device_params(ModelConst& K, const double* p) { device_param(K, __ldg(p)); }
 
   template <bool WC, bool WJ, bool WH>
   __device__ __forceinline__ static void eval(const ModelConst& K, const double (&z)[NZ], const double (&yb)[NX],
@@ -81,6 +84,12 @@ struct VdP {
     const double x1 = z[0], x2 = z[1];
     mdp[0] = 0.0;
     mdp[1] = fmul(K, K.mhh, fmul(K, fma(-x1, x1, 1.0), x2));
+  }
+  __device__ __forceinline__ static void dparams(const ModelConst& K, const double (&z)[NZ], double (&mdp)[NX][NP]) {
+    double t[NX];
+    dparam(K, z, t);
+    mdp[0][0] = t[0];
+    mdp[1][0] = t[1];
   }
   // sum_k wbar_k (-hh d2 f_k / dmu dz_v) for every local v
   __device__ __forceinline__ static void dparam_grad(const ModelConst& K, const double (&z)[NZ],

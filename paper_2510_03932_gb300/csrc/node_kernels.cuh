@@ -69,12 +69,12 @@ struct NodeArgs {
   double* ohv;                    // fused step: H v   (length n)
   double* partials;
   unsigned* counter;
-  double* dmu;                    // jtprod with the parameter derivative
+  double* dmu;                    // jtprod: (dc/dp)^T w (M::NP doubles); hprod: the mixed term's dot
   const double* pdir_dev;         // jprod: parameter direction (device scalar) or null
   const double* mixw;             // hprod: multipliers of the mixed parameter term or null
   const double* mixs;             // hprod: scale of the mixed term (device scalar)
   double pdir;                    // jprod: parameter direction (host scalar)
-  const double* p0_dev;           // model parameter 0 read from the device (or null: K as given)
+  const double* p0_dev;           // model parameters read from the device (or null: K as given)
   int64_t N, nb, B, E, ntiles, uoff;  // uoff = nx (N+1): first U entry of x
   int has_final, has_ref, range;
   const double* xtrack;            // time-varying state reference, (N+1) x ntrk node-major, or null
@@ -153,11 +153,12 @@ __device__ __forceinline__ double tile_sum(double v, double* red, double one) {
   return s;
 }
 
-// Completion of a reduction over tiles: every tile t stored its fixed-order CTA sum in
-// partials[t]; the last CTA to finish (completion ticket) adds partials[0..ntiles) in a
-// fixed order (strided per thread, then a fixed tree) and writes scale * sum to *dst.
-// The result depends only on the tile size, not on the grid or the kernel variant.
-template <int TILE>
+// Completion of a reduction over tiles: every tile t stored its fixed-order CTA sum of value
+// i < count in partials[i * ntiles + t]; the last CTA to finish (completion ticket) adds each
+// partials[i * ntiles + 0..ntiles) in a fixed order (strided per thread, then a fixed tree)
+// and writes scale * sum to dst[i].  The result depends only on the tile size, not on the grid
+// or the kernel variant.
+template <int TILE, int COUNT = 1>
 __device__ __forceinline__ void finish_tiles(const double* partials, int64_t ntiles, unsigned* counter, double* dst,
                                              double scale, double* red) {
   __shared__ int s_last;
@@ -170,13 +171,15 @@ __device__ __forceinline__ void finish_tiles(const double* partials, int64_t nti
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  double s = 0.0;
-  for (int64_t i = threadIdx.x; i < ntiles; i += TILE) s = s + __ldcg(partials + i);
-  s = cta_sum<TILE>(s, red);
-  if (threadIdx.x == 0) {
-    *dst = scale * s;
-    *counter = 0u;
+#pragma unroll 1
+  for (int q = 0; q < COUNT; ++q) {
+    const double* part = partials + q * ntiles;
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < ntiles; i += TILE) s = s + __ldcg(part + i);
+    s = cta_sum<TILE>(s, red);
+    if (threadIdx.x == 0) dst[q] = scale * s;
   }
+  if (threadIdx.x == 0) *counter = 0u;
 }
 
 template <class M>
@@ -187,14 +190,15 @@ __device__ __forceinline__ void load_node(const NodeArgs<M>& a, int64_t j, doubl
   for (int i = 0; i < M::NU; ++i) z[M::NX + i] = __ldg(a.x + a.uoff + M::NU * j + i);
 }
 
-// The model constants of a launch.  With PAR (a device-resident parameter bound by
-// ocp_bind_param0) the parameter-dependent constants are recomputed from it.  PAR is a
+// The model constants of a launch.  With PAR (device-resident parameters: params[0] bound by
+// ocp_bind_param0, or the model's whole parameter vector for one call) the
+// parameter-dependent constants are recomputed from them.  PAR is a
 // template argument rather than a run-time test: a branch this short is if-converted, and
 // its predicated-off FP64 instructions would still take FP64 pipe slots in every warp.
 template <class M, bool PAR>
 __device__ __forceinline__ ModelConst launch_consts(const NodeArgs<M>& a) {
   ModelConst K = a.K;
-  if constexpr (PAR) M::device_param(K, __ldg(a.p0_dev));
+  if constexpr (PAR) M::device_params(K, a.p0_dev);
   return K;
 }
 
@@ -699,19 +703,23 @@ __global__ void __launch_bounds__(TILE) k_node_jprod(const __grid_constant__ Nod
 // ======================================================================================
 // J^T w, node-local:  (J^T w)_{X_j,a} = (w_{a,j-1} - w_{a,j}) + sum_k wbar_k mjx_k,a(z_j)
 //                     (+ w of the boundary rows at j = 0 / N);  (J^T w)_{U_j,i} likewise.
-// With DPAR, also (dc/dmu)^T w = sum_j sum_k wbar_k mdp_k(z_j) (deterministic reduction).
+// With DPAR, also (dc/dp_i)^T w = sum_j sum_k wbar_k mdp_k,i(z_j) for every dynamics
+// parameter i < M::NP (mdp = -hh df/dp; one deterministic reduction per parameter).
 // ======================================================================================
 template <class M, int TILE, bool DPAR, bool PAR>
 __global__ void __launch_bounds__(TILE) k_node_jtprod(const __grid_constant__ NodeArgs<M> a) {
   constexpr int NX = M::NX, NZ = M::NZ;
   constexpr int NHD = (M::NHD > 0) ? M::NHD : 1;
+  constexpr int NP = M::NP, NPA = (NP > 0) ? NP : 1;
   __shared__ double red[TILE];
   ModelConst K = launch_consts<M, PAR>(a);
   const int64_t nchunks = (a.E - a.B + TILE - 1) / TILE;   // the nodes [B, E) in chunks of TILE
   for (int64_t chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
     const int64_t j0 = a.B + chunk * TILE, j = j0 + threadIdx.x;
     const bool bnd = (j0 == 0) || (j0 + TILE > a.N);  // chunk may hold node 0 or node N (uniform)
-    double acc_mu = 0.0;
+    double acc[NPA];
+#pragma unroll
+    for (int i = 0; i < NPA; ++i) acc[i] = 0.0;
     if (j < a.E) {
       double z[NZ], yb[NX], cqd[NZ], pa[NX], pb[NX], mjx[NX][M::MAXRX], mju[NX][M::MAXRU], hd[NHD];
       double wb[NX], wl[NX], wr[NX];
@@ -721,21 +729,26 @@ __global__ void __launch_bounds__(TILE) k_node_jtprod(const __grid_constant__ No
       double o[NZ];
       jtv_node<M>(a, K, a.v, j, bnd, mjx, mju, wl, wr, wb, o);
       store_nz<M>(a, a.out, j, o);
-      if (DPAR) {
-        double mdp[NX];
-        M::dparam(K, z, mdp);
+      if (DPAR && NP > 0) {
+        double mdp[NX][NPA];
+        M::dparams(K, z, mdp);
 #pragma unroll
-        for (int k = 0; k < NX; ++k)
-          if (M::HAS_DPARAM) acc_mu = fma(wb[k], mdp[k], acc_mu);
+        for (int i = 0; i < NPA; ++i)
+#pragma unroll
+          for (int k = 0; k < NX; ++k)
+            if (M::DP(k, i)) acc[i] = fma(wb[k], mdp[k][i], acc[i]);
       }
     }
     if (DPAR) {
-      const double ts = tile_sum<TILE>(acc_mu, red, K.one);
-      if (threadIdx.x == 0) a.partials[chunk] = ts;
-      __syncthreads();
+#pragma unroll
+      for (int i = 0; i < NPA; ++i) {
+        const double ts = tile_sum<TILE>(acc[i], red, K.one);
+        if (threadIdx.x == 0) a.partials[i * nchunks + chunk] = ts;
+        __syncthreads();
+      }
     }
   }
-  if (DPAR) finish_tiles<TILE>(a.partials, nchunks, a.counter, a.dmu, 1.0, red);
+  if (DPAR) finish_tiles<TILE, NPA>(a.partials, nchunks, a.counter, a.dmu, 1.0, red);
 }
 
 // ======================================================================================
@@ -853,8 +866,12 @@ ocp_status launch_eval_k(ocp* h, const EvalCall& c, cudaStream_t s) {
 
 template <class M, int TILE, int NPT, unsigned OUT>
 ocp_status launch_eval_t(ocp* h, const EvalCall& c, cudaStream_t s) {
-  if constexpr (M::HAS_DPARAM) {
+  // device parameters: every output for the Van der Pol mu (the differentiation form's bound
+  // parameter); the constraints alone for the other models
+  if constexpr (M::HAS_DPARAM || (M::NP > 0 && OUT == O_C)) {
     if (h->p0_dev) return launch_eval_k<M, TILE, NPT, OUT, true>(h, c, s);
+  } else {
+    if (h->p0_dev) return set_err(h, OCP_EMODEL, "device parameters are not provided for this output set");
   }
   return launch_eval_k<M, TILE, NPT, OUT, false>(h, c, s);
 }
@@ -1059,8 +1076,11 @@ ocp_status launch_euler_k(ocp* h, NodeArgs<M>& a, cudaStream_t s) {
 
 template <class M, int TILE, unsigned OUT>
 ocp_status launch_euler_t(ocp* h, NodeArgs<M>& a, cudaStream_t s) {
-  if constexpr (M::HAS_DPARAM) {
+  // (under forward Euler the constraints alone run through the O_ALL kernel, null outputs skipped)
+  if constexpr (M::HAS_DPARAM || (M::NP > 0 && OUT == O_ALL)) {
     if (a.p0_dev) return launch_euler_k<M, TILE, OUT, true>(h, a, s);
+  } else {
+    if (a.p0_dev) return set_err(h, OCP_EMODEL, "device parameters are not provided for this output set");
   }
   return launch_euler_k<M, TILE, OUT, false>(h, a, s);
 }
@@ -1091,6 +1111,8 @@ template <class M, int TILE>
 ocp_status euler_prod_dispatch(ocp* h, const ProdCall& c, cudaStream_t s) {
   if (c.dmu || c.pdir != 0.0 || c.pdir_dev || c.mixw)
     return set_err(h, OCP_EMODEL, "parameter derivatives are provided for the trapezoidal scheme");
+  if (!M::HAS_DPARAM && h->p0_dev)
+    return set_err(h, OCP_EMODEL, "device parameters under forward Euler: the constraints only");
   NodeArgs<M> a;
   fill_euler_args<M>(h, c.sigma, a);
   a.x = c.x; a.y = c.y;
@@ -1102,6 +1124,7 @@ ocp_status euler_prod_dispatch(ocp* h, const ProdCall& c, cudaStream_t s) {
 
 template <class M, int TILE>
 ocp_status node_eval_dispatch(ocp* h, unsigned out, const EvalCall& c, cudaStream_t s) {
+  if (!M::HAS_DPARAM && h->p0_dev && out != O_C) return set_err(h, OCP_EMODEL, "device parameters: the constraints only");
   if (h->scheme == OCP_SCHEME_EULER) return euler_eval_dispatch<M, TILE>(h, out, c, s);
   switch (out) {
     case O_F: return launch_eval_t<M, TILE, 1, O_F>(h, c, s);
@@ -1121,8 +1144,11 @@ cudaError_t node_prod_launch(ocp* h, const ProdCall& c, const NodeArgs<M>& a, cu
     const int grid = occupancy_grid(h, (const void*)kern, TILE, 0, units);
     kern<<<grid, TILE, 0, s>>>(a);
   };
+  // the parameter-direction and mixed terms of the double backward exist for the Van der Pol
+  // model alone (the C-ABI rejects them for the others)
+  constexpr bool VDP = M::HAS_DPARAM;
   if (c.kind == P_JPROD) {
-    if (c.pdir != 0.0 || c.pdir_dev) go(k_node_jprod<M, TILE, true, PAR>, a.ntiles);
+    if (VDP && (c.pdir != 0.0 || c.pdir_dev)) go(k_node_jprod<M, TILE, VDP, PAR>, a.ntiles);
     else go(k_node_jprod<M, TILE, false, PAR>, a.ntiles);
   } else if (c.kind == P_JTPROD) {
     const int64_t blocks = (a.E - a.B + TILE - 1) / TILE;
@@ -1130,7 +1156,7 @@ cudaError_t node_prod_launch(ocp* h, const ProdCall& c, const NodeArgs<M>& a, cu
     else go(k_node_jtprod<M, TILE, false, PAR>, blocks);
   } else {
     const int64_t blocks = (h->N + 1 + TILE - 1) / TILE;
-    if (c.mixw && c.mixs) go(k_node_hprod<M, TILE, true, PAR>, blocks);
+    if (VDP && c.mixw && c.mixs) go(k_node_hprod<M, TILE, VDP, PAR>, blocks);
     else go(k_node_hprod<M, TILE, false, PAR>, blocks);
   }
   return cudaGetLastError();
@@ -1147,7 +1173,9 @@ ocp_status node_prod_dispatch(ocp* h, const ProdCall& c, cudaStream_t s) {
   if (c.kind == P_JTPROD) { a.B = c.B; a.E = c.E < 0 ? h->N + 1 : c.E; }
   if (c.kind == P_JPROD) a.ntiles = (h->N + 1 + (TILE - 2)) / (TILE - 1);
   cudaError_t e;
-  if constexpr (M::HAS_DPARAM) {
+  if (c.kind == P_JTPROD && c.dmu && (int64_t)npa<M>() * ((a.E - a.B + TILE - 1) / TILE) > h->max_partials)
+    return set_err(h, OCP_EDIM, "too many tiles for the reduction scratch");
+  if constexpr (M::NP > 0) {  // device-resident parameters (bound for one call or more)
     e = a.p0_dev ? node_prod_launch<M, TILE, true>(h, c, a, s) : node_prod_launch<M, TILE, false>(h, c, a, s);
   } else {
     e = node_prod_launch<M, TILE, false>(h, c, a, s);

@@ -102,7 +102,9 @@ struct ocp {
   // boundary cost sum_v [a (z_v - b)^2 + l z_v] on z = (X_0, X_N) added to the objective (2 nx)
   bool has_bol = false;
   std::vector<double> bol_a, bol_b, bol_l;
-  const double* p0_dev = nullptr;  // device scalar overriding params[0] (or null)
+  // device-resident parameters overriding params (or null): params[0] alone for the Van der Pol
+  // binding, the model's whole dynamics-parameter vector for one call otherwise
+  const double* p0_dev = nullptr;
   // time-varying state reference: xref_k + xslope_k t_j + xamp_k sin(xfreq_k t_j) for the
   // components trk_comp (ntrk of them), tabulated once per node in d_xtrack[(N+1) x ntrk]
   std::vector<double> xslope, xamp, xfreq;
@@ -187,7 +189,7 @@ struct ProdCall {
   double sigma = 1.0;
   const double* v = nullptr;
   double* out = nullptr;
-  double* dmu = nullptr;  // jtprod: (dc/dp0)^T v (device scalar), may be null
+  double* dmu = nullptr;  // jtprod: (dc/dp)^T v, one double per dynamics parameter (or null)
   // autograd extensions (Van der Pol): parameter-direction terms
   double pdir = 0.0;            // jprod: adds (dc/dp0) * pdir  (host scalar)
   const double* pdir_dev = nullptr;  // jprod: same with a device scalar

@@ -84,6 +84,11 @@ _SIGS = {
     "ocp_eval_cons_p": [_P, _P, _P, _P, _P],
     "ocp_vjp_param_p": [_P, _P, _P, _P, _P, _P, _P],
     "ocp_set_param0": [_P, _D],
+    "ocp_param_count": [_P, _P],
+    "ocp_set_params": [_P, _P, C.c_int],
+    "ocp_bind_params": [_P, _P],
+    "ocp_eval_cons_params": [_P, _P, _P, _P, _P],
+    "ocp_vjp_params": [_P, _P, _P, _P, _P, _P, _P],
     "ocp_bind_param0": [_P, _P],
     "ocp_jprod_param": [_P, _P, _P, _P, _P, _P],
     "ocp_hprod_param": [_P, _P, _P, _D, _P, _P, _P, _P, _P],
@@ -528,6 +533,47 @@ class OCP:
     def set_param0(self, value: float):
         _check(lib().ocp_set_param0(self.h, float(value)), self.h)
 
+    @property
+    def nparams(self) -> int:
+        """Number of dynamics parameters with a derivative (ocp_param_count): Van der Pol 1
+        (mu), cart-pole 4 (m_c, m_p, l, g), Goddard 4 (Cd, beta, Tmax, b), quadrotor 1 (g),
+        the double integrator and the heat model 0."""
+        if getattr(self, "_nparams", None) is None:
+            n = C.c_int()
+            _check(lib().ocp_param_count(self.h, C.byref(n)), self.h)
+            self._nparams = n.value
+        return self._nparams
+
+    def set_params(self, values):
+        """Replace the dynamics parameters (host values, ocp_set_params)."""
+        a = (C.c_double * len(values))(*[float(v) for v in values])
+        _check(lib().ocp_set_params(self.h, a, len(values)), self.h)
+
+    def _pvec(self, p, name="p"):
+        if p is None:
+            return None
+        if p.dtype != torch.float64 or not p.is_cuda or p.numel() != self.nparams or not p.is_contiguous():
+            raise TypeError("%s must be a contiguous float64 CUDA tensor of %d elements" % (name, self.nparams))
+        return p
+
+    def eval_cons_params(self, x, p=None, out=None, stream=None):
+        """c(x; p) with the dynamics parameters read from the CUDA tensor p for this call
+        (ocp_eval_cons_params; None: the handle's values)."""
+        x = self._vec(x, self.n, "x"); p = self._pvec(p)
+        out = self._out(out, self.m, "c")
+        _check(lib().ocp_eval_cons_params(self.h, _ptr(x), _ptr(p), _ptr(out), _stream(stream)), self.h)
+        return out
+
+    def vjp_params(self, x, w, p=None, Jtw=None, dp=None, stream=None):
+        """(J^T w, (dc/dp)^T w) for every dynamics parameter, p as in eval_cons_params
+        (ocp_vjp_params)."""
+        x = self._vec(x, self.n, "x"); w = self._vec(w, self.m, "w"); p = self._pvec(p)
+        Jtw = self._out(Jtw, self.n, "Jtw")
+        dp = self._out(dp, max(self.nparams, 1), "dp")
+        _check(lib().ocp_vjp_params(self.h, _ptr(x), _ptr(w), _ptr(p), _ptr(Jtw), _ptr(dp), _stream(stream)),
+               self.h)
+        return Jtw, dp
+
     def _scalar(self, t, name):
         if t is None:
             return None
@@ -556,6 +602,27 @@ class OCP:
     def param0(self, p0):
         """Context manager: calls inside it read params[0] from the CUDA scalar p0."""
         return OCP._Bound(self, p0)
+
+    def bind_params(self, p):
+        """Read every dynamics parameter from the CUDA tensor p (None unbinds; ocp_bind_params)."""
+        p = self._pvec(p)
+        _check(lib().ocp_bind_params(self.h, _ptr(p)), self.h)
+
+    class _BoundAll:
+        def __init__(self, H, p):
+            self.H, self.p = H, p
+
+        def __enter__(self):
+            self.H.bind_params(self.p)
+            return self.H
+
+        def __exit__(self, *exc):
+            self.H.bind_params(None)
+            return False
+
+    def params_bound(self, p):
+        """Context manager: calls inside it read the dynamics parameters from the CUDA tensor p."""
+        return OCP._BoundAll(self, p)
 
     def jprod_param(self, x, v, s=None, out=None, stream=None):
         x = self._vec(x, self.n, "x"); v = self._vec(v, self.n, "v"); s = self._scalar(s, "s")

@@ -46,8 +46,8 @@ def test_constraints_gradcheck_cartpole(mods):
     w, d = small("cartpole_n1e5", 6)
     H = ocp.OCP.from_workload(w)
     x = torch.from_numpy(d["x"]).cuda().requires_grad_(True)
-    mu = torch.zeros(1, dtype=torch.float64, device="cuda")
-    f = lambda x: A.constraints(H, x, mu)
+    p = torch.tensor(w["params"], dtype=torch.float64, device="cuda")   # (m_c, m_p, l, g), held fixed
+    f = lambda x: A.constraints(H, x, p)
     assert torch.autograd.gradcheck(f, (x,), eps=1e-6, atol=1e-6, rtol=1e-5)
     assert torch.autograd.gradgradcheck(f, (x,), eps=1e-6, atol=1e-5, rtol=1e-4)
 
