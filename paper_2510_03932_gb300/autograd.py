@@ -25,7 +25,7 @@ from __future__ import annotations
 
 import torch
 
-from .ocp import OCP
+from .ocp import OCP, _check, _raw_stream
 
 
 def _zero_scalar(like):
@@ -70,25 +70,48 @@ class _ConsVJP(torch.autograd.Function):
         return None, dx, None, dw
 
 
+def _cur_stream(t):
+    """Handle of the current stream of t's device (the stream the autograd engine runs on)."""
+    if _raw_stream is not None:
+        return _raw_stream(t.get_device())
+    return torch.cuda.current_stream(t.device).cuda_stream
+
+
 class _Constraints(torch.autograd.Function):
+    # The first-order path makes one C-ABI call each way with the arguments checked once in
+    # constraints(): the step is host-bound at the sizes where autograd overhead matters.
     @staticmethod
-    def forward(ctx, H: OCP, x, mu):
+    def forward(ctx, H: OCP, x, p):
         ctx.H = H
-        ctx.save_for_backward(x, mu)
-        return H.eval_cons_params(x, mu.reshape(-1) if H.nparams > 0 else None)
+        ctx.save_for_backward(x, p)
+        c = torch.empty(H.m, dtype=torch.float64, device=x.device)
+        st = H._lib.ocp_eval_cons_params(H.h, x.data_ptr(), p.data_ptr() if H.nparams else None, c.data_ptr(),
+                                         _cur_stream(x))
+        if st:
+            _check(st, H.h)
+        return c
 
     @staticmethod
     def backward(ctx, gc):
-        x, mu = ctx.saved_tensors
+        x, p = ctx.saved_tensors
         H = ctx.H
         if torch.is_grad_enabled():   # create_graph: the backward itself is differentiated
-            gx, gmu = _ConsVJP.apply(H, x, mu, gc.contiguous())
-        elif H.nparams > 0:           # one launch: J^T w and (dc/dp)^T w
-            gx, gmu = H.vjp_params(x, gc.contiguous(), mu.reshape(-1))
-            gmu = gmu.reshape(mu.shape)
+            return (None,) + _ConsVJP.apply(H, x, p, gc.contiguous())
+        if not gc.is_contiguous():
+            gc = gc.contiguous()
+        gx = torch.empty_like(x)
+        if H.nparams:   # one launch: J^T w at the parameters p and (dc/dp)^T w
+            gp = torch.empty_like(p)
+            st = H._lib.ocp_vjp_params(H.h, x.data_ptr(), gc.data_ptr(), p.data_ptr(), gx.data_ptr(), gp.data_ptr(),
+                                       _cur_stream(x))
+            if not ctx.needs_input_grad[2]:
+                gp = None
         else:
-            gx, gmu = H.jtprod(x, gc.contiguous()), torch.zeros_like(mu)
-        return None, gx, gmu
+            gp = None
+            st = H._lib.jtprod(H.h, x.data_ptr(), gc.data_ptr(), gx.data_ptr(), _cur_stream(x))
+        if st:
+            _check(st, H.h)
+        return None, gx, gp
 
 
 class _ObjGrad(torch.autograd.Function):
@@ -120,11 +143,15 @@ class _Objective(torch.autograd.Function):
 
 
 def constraints(H: OCP, x: torch.Tensor, p: torch.Tensor) -> torch.Tensor:
-    """c(x; p) with backward (J^T w, (dc/dp)^T w) and a double backward.  p holds the model's
-    H.nparams dynamics parameters (Van der Pol: mu alone); for models without parameters
-    (double integrator, heat) it is ignored and receives a zero gradient."""
-    if H.nparams > 0 and p.numel() != H.nparams:
-        raise ValueError("p must hold the %d dynamics parameters of the %s model" % (H.nparams, H.model))
+    """c(x; p) with backward (J^T w, (dc/dp)^T w) and a double backward.  x: contiguous float64
+    CUDA tensor of H.n entries; p: contiguous float64 CUDA tensor holding the model's H.nparams
+    dynamics parameters (Van der Pol: mu alone; any shape); for models without parameters
+    (double integrator, heat) p is not read and receives no gradient."""
+    H._vec(x, H.n, "x")
+    if H.nparams > 0:
+        if p.dtype != torch.float64 or not p.is_cuda or not p.is_contiguous() or p.numel() != H.nparams:
+            raise ValueError("p must be a contiguous float64 CUDA tensor of the %d dynamics parameters of the "
+                             "%s model" % (H.nparams, H.model))
     return _Constraints.apply(H, x, p)
 
 

@@ -190,6 +190,7 @@ class OCP:
                  x0=None, xf=None, xslope=None, xamp=None, xfreq=None, free_tf=False, xf_comp=None,
                  mayer=None, bounds=None, scheme="trapezoid", path=None, bineq=None, bolza=None):
         L = lib()
+        self._lib = L
         self._keep = []
 
         def arr(v):
