@@ -83,8 +83,8 @@ def _counts(w):
 # bench reports no FP64 fraction for that model until they are measured again.
 FP64_OPS_PER_NODE = {("vdp", "eval_all"): 26.6, ("vdp", "jh"): 10.0, ("vdp", "jprod"): 13.0,
                      ("vdp", "jtprod"): 12.0, ("vdp", "hprod"): 11.0, ("vdp", "step"): 50.6,
-                     ("cartpole", "eval_all"): 117.8, ("cartpole", "jh"): 95.7, ("cartpole", "jprod"): 78.6,
-                     ("cartpole", "jtprod"): 75.0, ("cartpole", "hprod"): 103.0, ("cartpole", "step"): 165.9,
+                     ("cartpole", "eval_all"): 118.8, ("cartpole", "jh"): 95.7, ("cartpole", "jprod"): 82.6,
+                     ("cartpole", "jtprod"): 79.0, ("cartpole", "hprod"): 97.0, ("cartpole", "step"): 164.9,
                      ("quadrotor", "eval_all"): 250.1, ("quadrotor", "jh"): 176.7, ("quadrotor", "jprod"): 163.4,
                      ("quadrotor", "jtprod"): 155.0, ("quadrotor", "hprod"): 198.0, ("quadrotor", "step"): 397.8,
                      ("goddard", "eval_all"): 98.2, ("goddard", "jh"): 89.2, ("goddard", "jprod"): 66.3,
@@ -108,8 +108,8 @@ KERNEL_SOURCES = {
     "heat64": _COMMON + ["heat_kernels.cu"],
 }
 # Tags of the sources the FP64_OPS_PER_NODE counts (and TRAFFIC) were measured on.
-FP64_OPS_SRC = {"vdp": "bc6e02341ed5", "vdp:euler": "bc6e02341ed5", "cartpole": "617d024fcabf",
-                "quadrotor": "1438c421633e", "goddard": "ed2db7630e54", "heat64": "894a5428b343"}
+FP64_OPS_SRC = {"vdp": "25e59eb7dcb6", "vdp:euler": "25e59eb7dcb6", "cartpole": "96eaf32d6270",
+                "quadrotor": "eddd71fe8cc1", "goddard": "266fb7d19966", "heat64": "74410ef1e8e5"}
 
 
 def kernel_source_tag(key):
@@ -158,7 +158,7 @@ def named_workload(name):
 # DRAM bytes (read + write) of one launch at a workload, from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum; writes still dirty in L2 when the kernel ends
 # are not counted), with the source tag of the kernel it was captured on (see traffic()).
-TRAFFIC = {("vdp_mu_n1e6", "step"): (227.35e6, "bc6e02341ed5")}
+TRAFFIC = {("vdp_mu_n1e6", "step"): (227.33e6, "25e59eb7dcb6")}
 # Each SM's FP64 pipe completes 2 FP64 instructions (one lane each) per clock: the recipe's
 # nominal 1.25 TFLOP/s FP64 of GB300 is 6.25e11 FMA/s = 1.99 per clock per SM at 152 SMs and
 # 2070 MHz.  bench.py measures the rate live (measure_fp64_rate) and reports it beside the peak.

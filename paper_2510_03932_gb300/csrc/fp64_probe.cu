@@ -9,6 +9,8 @@
 // pipe more independent work than its latency needs, so the launch measures its issue rate.
 #include <cuda_runtime.h>
 
+#include <cstring>
+
 #include "model_base.cuh"
 #include "ocp_internal.h"
 #include "ocp_probe.h"
@@ -48,7 +50,38 @@ __global__ void k_probe_recip(const double* d, double* out, int64_t n, double on
     out[i] = ocpg::recip(one, d[i]);
 }
 
+// The kernels' sincos (sincos_red) and the library's on the same arguments.
+__global__ void k_probe_sincos(const double* x, double* s, double* c, double* sl, double* cl, int64_t n,
+                               const __grid_constant__ ocpg::ModelConst K) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double a, b;
+    ocpg::sincos_red(K, x[i], a, b);
+    s[i] = a;
+    c[i] = b;
+    sincos(x[i], &a, &b);
+    sl[i] = a;
+    cl[i] = b;
+  }
+}
+
 }  // namespace
+
+extern "C" ocp_status ocp_probe_sincos(const double* x, double* s, double* c, double* s_lib, double* c_lib, int64_t n,
+                                       void* stream) {
+  OCP_RANGE();
+  const double* p[5] = {x, s, c, s_lib, c_lib};
+  for (const double* q : p)
+    if (!q || ((uintptr_t)q & 7u)) return ocpg::set_err(nullptr, OCP_EINVAL, "ocp_probe_sincos: bad pointer");
+  if (n < 0) return ocpg::set_err(nullptr, OCP_EINVAL, "ocp_probe_sincos: n < 0");
+  if (n == 0) return OCP_OK;
+  ocpg::ModelConst K;
+  memset(&K, 0, sizeof(K));
+  K.one = 1.0;
+  K.mz = -0.0;
+  const int grid = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+  k_probe_sincos<<<grid, 256, 0, (cudaStream_t)stream>>>(x, s, c, s_lib, c_lib, n, K);
+  return ocpg::cuda_err(nullptr, cudaGetLastError(), "ocp_probe_sincos launch");
+}
 
 extern "C" ocp_status ocp_probe_recip(const double* d, double* out, int64_t n, void* stream) {
   OCP_RANGE();

@@ -81,7 +81,7 @@ struct CartPole {
     const double hh = K.hh, mhh = K.mhh;
     const double p = z[0], pd = z[1], th = z[2], w = z[3], F = z[4];
     double s, c;
-    sincos(th, &s, &c);
+    sincos_red(K, th, s, c);
     const double ms = fmul(K, mp, s);
     const double D = fma(ms, s, mcm);
     const double iD = recip(K.one, D);
@@ -126,27 +126,25 @@ struct CartPole {
         // for the angular rows the 1/l), m1 = -hh ybar_1 / D and m3 = -hh ybar_3 / (l D), and the
         // numerators are combined directly (those of the angular rows scaled by l).
         const double m1 = fmul(K, mhiD, yb[1]), m3 = fmul(K, fmul(K, mhhil, yb[3]), iD);
-        const double pdd_w = fmul(K, A_w, iD);
         const double Dpp = fmul(K, mp2, c2s2);
         const double mDp2 = fmul(K, -2.0, Dp);
         // A_tt = -mp s (l w^2 + 4 g c)
         const double A_tt = fmul(K, -ms, fma(g4, c, lw2));
         const double n_pdd_tt = fma(-pdd, Dpp, fma(pdd_t, mDp2, A_tt));
-        const double A_tw = fmul(K, lw, c);
-        const double n_pdd_tw = fma(-pdd_w, Dp, A_tw);
-        const double n_pdd_ww = fmul(K, mpl2, s);
-        const double n_pdd_tF = fmul(K, -Dp, iD);
         // B_tt = F c + 4 mp l w^2 s c + (mc+mp) g s = -B + 3 mp l w^2 s c
         const double B_tt = fma(sc, fmul(K, K.c[13], w2), -B);
         const double n_bu_tt = fma(-Bu, Dpp, fma(Bu_t, mDp2, B_tt));
-        const double B_tw = fmul(K, -lw, c2s2);
-        const double n_bu_tw = fma(-Bu_w, Dp, B_tw);
-        const double n_bu_ww = fmul(K, -mpl2, sc);
-        const double n_bu_tF = fma(-Bu_F, Dp, s);
         hd[0] = fma(m1, n_pdd_tt, fma(m3, n_bu_tt, cqd[2]));   // (th, th)
-        hd[1] = fma(m1, n_pdd_tw, fmul(K, m3, n_bu_tw));       // (w, th)
-        hd[2] = fma(m1, n_pdd_ww, fma(m3, n_bu_ww, cqd[3]));   // (w, w)
-        hd[3] = fma(m1, n_pdd_tF, fmul(K, m3, n_bu_tF));       // (F, th)
+        // The other three entries, with t = m3 c - m1 and e = D' / D, from
+        //   pdd_ww = 2 mp l s / D,  Bu_ww = -2 mp l s c / D                  -> (w, w)  = -t 2 mp l s
+        //   pdd_tF = -e / D,        Bu_tF = (s + c e) / D                     -> (F, th) = m3 s + e t
+        //   pdd_tw = 2 mp l w (c - s e) / D,  Bu_tw = -2 mp l w (c^2 - s^2 - s c e) / D
+        //                                    -> (w, th) = 2 mp l w (m1 c - m3 (c^2 - s^2) + e s t)
+        const double t = fma(m3, c, -m1);
+        const double e = fmul(K, Dp, iD);
+        hd[1] = fmul(K, lw, fma(fmul(K, e, s), t, fma(m1, c, -fmul(K, m3, c2s2))));   // (w, th)
+        hd[2] = fma(-t, fmul(K, mpl2, s), cqd[3]);                                  // (w, w)
+        hd[3] = fma(e, t, fmul(K, m3, s));                                          // (F, th)
       }
     }
   }
@@ -163,7 +161,7 @@ struct CartPole {
     const double mp = K.c[1], l = K.c[2], g = K.c[3];
     const double th = z[2], w = z[3], F = z[4];
     double s, c;
-    sincos(th, &s, &c);
+    sincos_red(K, th, s, c);
     const double ms = fmul(K, mp, s);
     const double D = fma(ms, s, K.c[0]);
     const double iD = recip(K.one, D);
