@@ -438,9 +438,17 @@ ocp_status ocp_eval_step_range(ocp_t* h, int64_t node_begin, int64_t node_end, c
 ocp_status ocp_vjp_param_range(ocp_t* h, int64_t node_begin, int64_t node_end, const double* x,
                                const double* w, double* Jtw, double* dmu, void* stream);
 
+/* ocp_vjp_params on the nodes [node_begin, node_end) only: J^T w on those nodes' entries of Jtw
+ * and dp = their shares of (dc/dp)^T w (np doubles; the shards' shares add up to the whole
+ * product), with p as in ocp_vjp_params (device parameters, NULL: the handle's).  The node
+ * models with parameters (Van der Pol, cart-pole, quadrotor); otherwise the restrictions and
+ * errors of ocp_eval_step_range, and OCP_EMODEL for a model without parameters. */
+ocp_status ocp_vjp_params_range(ocp_t* h, int64_t node_begin, int64_t node_end, const double* x, const double* w,
+                                const double* p, double* Jtw, double* dp, void* stream);
+
 /* out = parts[0] + parts[1] + ... + parts[count-1], added in index order (device arrays; one
- * thread): the rank-ordered combination of the shards' partial sums of ocp_eval_step_range and
- * ocp_vjp_param_range, which gives every rank the same bits.  Errors: OCP_EINVAL, OCP_ECUDA
+ * thread): the rank-ordered combination of the shards' partial sums of ocp_eval_step_range,
+ * ocp_vjp_param_range and ocp_vjp_params_range, which gives every rank the same bits.  Errors: OCP_EINVAL, OCP_ECUDA
  * (ocp_last_error(NULL)). */
 ocp_status ocp_sum_ordered(const double* parts, int count, double* out, void* stream);
 

@@ -690,6 +690,23 @@ ocp_status ocp_vjp_param_p(ocp_t* h, const double* x, const double* w, const dou
   return dispatch_prod(h, c, stream);
 }
 
+ocp_status ocp_vjp_params_range(ocp_t* h, int64_t node_begin, int64_t node_end, const double* x, const double* w,
+                                const double* p, double* Jtw, double* dp, void* stream) {
+  OCP_RANGE();
+  if (!h) return OCP_EINVAL;
+  if (h->unusable) return unusable_err(h);
+  if (model_nderiv(h->model) == 0)
+    return set_err(h, OCP_EMODEL, "the model has no dynamics parameters with a derivative");
+  ocp_status st = check_range(h, node_begin, node_end, true);
+  if (st != OCP_OK) return st;
+  NEED(x); NEED(w); NEED(Jtw); NEED(dp); OPT(p);
+  ParamScope ps(h, p);
+  ProdCall c;
+  c.kind = P_JTPROD; c.x = x; c.v = w; c.out = Jtw; c.dmu = dp;
+  c.B = node_begin; c.E = node_end;
+  return dispatch_prod(h, c, stream);
+}
+
 ocp_status ocp_param_count(const ocp_t* h, int* np) {
   OCP_RANGE();
   if (!h || !np) return OCP_EINVAL;

@@ -87,6 +87,7 @@ _SIGS = {
     "ocp_param_count": [_P, _P],
     "ocp_set_params": [_P, _P, C.c_int],
     "ocp_bind_params": [_P, _P],
+    "ocp_vjp_params_range": [_P, _I64, _I64, _P, _P, _P, _P, _P, _P],
     "ocp_eval_cons_params": [_P, _P, _P, _P, _P],
     "ocp_vjp_params": [_P, _P, _P, _P, _P, _P, _P],
     "ocp_bind_param0": [_P, _P],
@@ -443,6 +444,15 @@ class OCP:
         _check(lib().ocp_vjp_param_range(self.h, int(node_begin), int(node_end), _ptr(x), _ptr(w), _ptr(Jtw),
                                          _ptr(dmu), _stream(stream)), self.h)
         return Jtw, dmu
+
+    def vjp_params_range(self, node_begin, node_end, x, w, Jtw, dp, p=None, stream=None):
+        """ocp_vjp_params_range: J^T w on the nodes [node_begin, node_end) and their shares of
+        (dc/dp)^T w for every dynamics parameter."""
+        x = self._vec(x, self.n, "x"); w = self._vec(w, self.m, "w"); p = self._pvec(p)
+        Jtw = self._vec(Jtw, self.n, "Jtw"); dp = self._vec(dp, self.nparams, "dp")
+        _check(lib().ocp_vjp_params_range(self.h, int(node_begin), int(node_end), _ptr(x), _ptr(w), _ptr(p),
+                                          _ptr(Jtw), _ptr(dp), _stream(stream)), self.h)
+        return Jtw, dp
 
     def value_layout(self):
         """ocp_value_layout: nb, values per defect row of each component, Hessian values per node

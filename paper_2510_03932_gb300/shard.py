@@ -94,21 +94,29 @@ class ShardedOCP:
         self.H.close()
 
     def combine(self, part, out=None, stream=None):
-        """Sum over the ranks of the one-element CUDA tensor `part`, in rank order, into `out`."""
+        """Sum over the ranks of the CUDA tensor `part` (k doubles), entry by entry in rank
+        order, into `out`: one all-gather of k doubles per rank."""
         import torch
         import torch.distributed as dist
 
         from . import ocp
         out = part if out is None else out
+        k = part.numel()
         if dist.get_backend(self.group) == "nccl":
-            parts = torch.empty(self.world, dtype=torch.float64, device=part.device)
-            dist.all_gather_into_tensor(parts, part.reshape(1), group=self.group)
+            parts = torch.empty(self.world * k, dtype=torch.float64, device=part.device)
+            dist.all_gather_into_tensor(parts, part.reshape(k), group=self.group)
         else:
-            host = part.detach().reshape(1).cpu()
+            host = part.detach().reshape(k).cpu()
             gathered = [torch.empty_like(host) for _ in range(self.world)]
             dist.all_gather(gathered, host, group=self.group)
             parts = torch.cat(gathered).to(part.device)
-        return ocp.sum_ordered(parts, out, stream)
+        if k == 1:
+            return ocp.sum_ordered(parts, out, stream)
+        byentry = parts.reshape(self.world, k).t().contiguous()   # entry i's shares, rank order
+        flat = out.reshape(k)
+        for i in range(k):
+            ocp.sum_ordered(byentry[i], flat[i:i + 1], stream)
+        return out
 
     def eval_step(self, x, y, sigma, vn, vm, outs, stream=None):
         """This rank's shard of the fused step into the full-size buffers `outs` = (f, c, g,
@@ -122,6 +130,13 @@ class ShardedOCP:
         self.H.vjp_param_range(self.a, self.b, x, w, Jtw, dmu, stream)
         self.combine(dmu, stream=stream)
         return Jtw, dmu
+
+    def vjp_params(self, x, w, Jtw, dp, p=None, stream=None):
+        """This rank's entries of J^T w and the whole (dc/dp)^T w for every dynamics parameter
+        (p: device parameters, or None for the handle's)."""
+        self.H.vjp_params_range(self.a, self.b, x, w, Jtw, dp, p, stream)
+        self.combine(dp, stream=stream)
+        return Jtw, dp
 
     # the product outputs share the slots of c (Jv) and g (J^T w, H v)
     _SLOTS = {"c": "c", "g": "g", "jac": "jac", "hess": "hess", "Jv": "c", "Jtv": "g", "Hv": "g"}

@@ -1,8 +1,8 @@
 """The sharded evaluator with real shards: two or three processes share the GPU, each runs its
-own node shard through ocp_eval_step_range / ocp_vjp_param_range (ShardedOCP), and the ranks
-combine their partials over gloo.  The assembled outputs must equal the unsharded fused step
-bit for bit, and the combined objective and (dc/dmu)^T w must agree with the oracle within the
-parity gate.  (The ranks never wait on each other inside a kernel: every exchange happens on
+own node shard through ocp_eval_step_range / ocp_vjp_param_range / ocp_vjp_params_range
+(ShardedOCP), and the ranks combine their partials over gloo.  The assembled outputs must equal
+the unsharded fused step bit for bit, and the combined objective, (dc/dmu)^T w and (dc/dp)^T w
+for every dynamics parameter must agree with the oracle within the parity gate.  (The ranks never wait on each other inside a kernel: every exchange happens on
 the host, between launches.)"""
 import os
 import socket
@@ -56,6 +56,16 @@ def _rank(rank, world, port, name, N, q):
             dmu = torch.zeros(1, dtype=torch.float64, device="cuda")
             S.vjp_param(x, vm, Jtw, dmu)
             vjp = (S.gather("Jtv", Jtw), float(dmu))
+        vjps = None
+        if H.nparams > 0:   # every dynamics parameter, read from a device tensor
+            p = torch.tensor(w["params"][:H.nparams], dtype=torch.float64, device="cuda")
+            Jtw = torch.full((H.n,), float("nan"), dtype=torch.float64, device="cuda")
+            dp = torch.zeros(H.nparams, dtype=torch.float64, device="cuda")
+            S.vjp_params(x, vm, Jtw, dp, p)
+            vjps = (S.gather("Jtv", Jtw), dp.cpu().numpy())
+            dps = [None] * world
+            dist.all_gather_object(dps, vjps[1].tolist())
+            assert all(v == dps[0] for v in dps), dps   # the same bits on every rank
         f = float(outs[0])
         fs = [None] * world
         dist.all_gather_object(fs, f)
@@ -73,6 +83,11 @@ def _rank(rank, world, port, name, N, q):
                 assert torch.equal(vjp[0], Jtw_ref.cpu())
                 o, m = O.dpar_vjp(P, d["x"], d["vm"], shadow=True)
                 gate("dmu", np.array([vjp[1]]), np.array([o]), np.array([m]))
+            if vjps is not None:
+                Jtw_ref, _ = H.vjp_params(x, vm)
+                assert torch.equal(vjps[0], Jtw_ref.cpu())
+                o, m = O.dpar_vjp_all(P, d["x"], d["vm"], shadow=True)
+                gate("dc/dp^T w", vjps[1], o, m)
         dist.barrier()
         S.close()
         q.put((rank, "ok"))
