@@ -16,6 +16,7 @@ in the data path); rank 0 prints the JSON line.
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import os
 import subprocess
@@ -817,6 +818,13 @@ def run_forms(args, hbm):
     flush = L2Flush("cuda")
 
     def timed(fn):
+        # the same allocator state for every form: collect garbage, then release the caching
+        # allocator's free blocks (the preamble torch.cuda.graph runs before a capture).  After a
+        # full garbage collection that frees CUDA tensors, this eager step measured 106-127 us
+        # instead of 73 us until the cache was emptied; the small problem (N = 2000) and the
+        # plain calls showed no such effect.
+        gc.collect()
+        torch.cuda.empty_cache()
         for _ in range(3):
             fn()
         ts = []
