@@ -86,8 +86,8 @@ FP64_OPS_PER_NODE = {("vdp", "eval_all"): 26.6, ("vdp", "jh"): 10.0, ("vdp", "jp
                      ("vdp", "jtprod"): 12.0, ("vdp", "hprod"): 11.0, ("vdp", "step"): 50.6,
                      ("cartpole", "eval_all"): 118.8, ("cartpole", "jh"): 95.7, ("cartpole", "jprod"): 82.6,
                      ("cartpole", "jtprod"): 79.0, ("cartpole", "hprod"): 97.0, ("cartpole", "step"): 164.9,
-                     ("quadrotor", "eval_all"): 250.1, ("quadrotor", "jh"): 176.7, ("quadrotor", "jprod"): 163.4,
-                     ("quadrotor", "jtprod"): 155.0, ("quadrotor", "hprod"): 198.0, ("quadrotor", "step"): 397.8,
+                     ("quadrotor", "eval_all"): 247.6, ("quadrotor", "jh"): 175.4, ("quadrotor", "jprod"): 163.4,
+                     ("quadrotor", "jtprod"): 155.0, ("quadrotor", "hprod"): 198.0, ("quadrotor", "step"): 394.9,
                      ("goddard", "eval_all"): 98.2, ("goddard", "jh"): 89.2, ("goddard", "jprod"): 66.3,
                      ("goddard", "jtprod"): 67.1, ("goddard", "hprod"): 93.1, ("goddard", "step"): 153.4,
                      ("vdp:euler", "eval_all"): 21.5, ("vdp:euler", "jh"): 8.0, ("vdp:euler", "jprod"): 11.0,
@@ -109,8 +109,8 @@ KERNEL_SOURCES = {
     "heat64": _COMMON + ["heat_kernels.cu"],
 }
 # Tags of the sources the FP64_OPS_PER_NODE counts (and TRAFFIC) were measured on.
-FP64_OPS_SRC = {"vdp": "25e59eb7dcb6", "vdp:euler": "25e59eb7dcb6", "cartpole": "96eaf32d6270",
-                "quadrotor": "eddd71fe8cc1", "goddard": "266fb7d19966", "heat64": "74410ef1e8e5"}
+FP64_OPS_SRC = {"vdp": "cc658d1f082c", "vdp:euler": "cc658d1f082c", "cartpole": "061236c3a755",
+                "quadrotor": "a813de1053eb", "goddard": "5c6666cb0cfe", "heat64": "b26b2a768223"}
 
 
 def kernel_source_tag(key):
@@ -159,7 +159,7 @@ def named_workload(name):
 # DRAM bytes (read + write) of one launch at a workload, from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum; writes still dirty in L2 when the kernel ends
 # are not counted), with the source tag of the kernel it was captured on (see traffic()).
-TRAFFIC = {("vdp_mu_n1e6", "step"): (227.33e6, "25e59eb7dcb6")}
+TRAFFIC = {("vdp_mu_n1e6", "step"): (227.13e6, "cc658d1f082c")}
 # Each SM's FP64 pipe completes 2 FP64 instructions (one lane each) per clock: the recipe's
 # nominal 1.25 TFLOP/s FP64 of GB300 is 6.25e11 FMA/s = 1.99 per clock per SM at 152 SMs and
 # 2070 MHz.  bench.py measures the rate live (measure_fp64_rate) and reports it beside the peak.
@@ -873,6 +873,29 @@ def run_forms(args, hbm):
         res["graphed"] = timed(graphed)
     if whole:
         res["whole_graph"] = timed(whole)
+    # the cart-pole's four parameters (m_c, m_p, l, g) as a device tensor: c(x; p) forward and
+    # (J^T w, (dc/dp)^T w) backward at N = 1e6, against the same two C-ABI calls made directly
+    wc = synth.workload("cartpole_n1e6")
+    dc = synth.draw(wc)
+    Hc = ocp.OCP.from_workload(wc)
+    xc = torch.from_numpy(dc["x"]).cuda().requires_grad_(True)
+    pc = torch.tensor(wc["params"], dtype=torch.float64, device="cuda", requires_grad=True)
+    wcv = torch.from_numpy(dc["vm"]).cuda()
+
+    def ad_step_p():
+        cc = A.constraints(Hc, xc, pc)
+        return torch.autograd.grad(cc, (xc, pc), grad_outputs=wcv)
+
+    def plain_step_p():
+        Hc.eval_cons_params(xc.detach(), pc.detach())
+        Hc.vjp_params(xc.detach(), wcv, pc.detach())
+
+    res_p = {"autograd": timed(ad_step_p), "plain": timed(plain_step_p)}
+    out["adjoint_params"] = dict(workload="cartpole_n1e6", step="c(x;p) forward + (J^T w, dc/dp^T w) backward, "
+                                 "p = (m_c, m_p, l, g) on the device", autograd_ms=res_p["autograd"],
+                                 plain_ms=res_p["plain"], overhead=res_p["autograd"] / res_p["plain"])
+    Hc.close()
+    del xc, pc, wcv
     out["adjoint"] = dict(workload="vdp_mu_n1e6", step="c(x;mu) forward + (J^T w, dc/dmu^T w) backward",
                           autograd_ms=res["autograd"], plain_ms=res["plain"],
                           overhead=res["autograd"] / res["plain"])

@@ -50,7 +50,7 @@ int64_t objective_tiles(int model, int64_t nodes) {
     case OCP_MODEL_VDP: owned = TILE_VDP - 1; break;
     case OCP_MODEL_CARTPOLE: owned = TILE_CARTPOLE - 1; break;
     case OCP_MODEL_DINT: owned = TILE_DINT - 1; break;
-    case OCP_MODEL_QUADROTOR: owned = TILE_QUAD - 1; break;
+    case OCP_MODEL_QUADROTOR: owned = TILE_QUAD_EVAL - 1; break;
     case OCP_MODEL_HEAT1D: owned = HEAT_TILE_NODES - 1; break;
     default: return -1;
   }

@@ -6,6 +6,12 @@ namespace ocpg {
 
 // Threads (= nodes) per CTA of the node-model kernels; a tile owns TILE-1 nodes.
 constexpr int TILE_VDP = 256, TILE_CARTPOLE = 128, TILE_DINT = 256, TILE_QUAD = 64;
+// The quadrotor's evaluation kernels (F, c, g, J, H and the fused step) run 128-node tiles with
+// three CTAs per SM at its register cap, its product kernels 64-node tiles (measured at N = 1e6:
+// fused step 846 -> 832 us, evaluation 533 -> 512 us; the products gain nothing from the larger
+// tile and lose up to 5% at N = 1e5).  Every output is per node but the objective, whose tile
+// sums only the evaluation kernels form.
+constexpr int TILE_QUAD_EVAL = 128;
 // Most state components with a time-varying reference (node models have at most 9 states).
 constexpr int kMaxTrack = 16;
 // Nodes per CTA of the heat-equation kernels (one per lane); a tile owns 31 nodes.

@@ -71,11 +71,19 @@ struct CartPole {
     param_consts(q, K.hh, K);
   }
 
-  template <bool WC, bool WJ, bool WH>
+  // With WP (the parameter derivative of J^T w) eval also fills mdp = -hh df/dp, p = (mc, mp, l,
+  // g), from the same intermediates (FUSED_DP: the kernels call no separate dparams):
+  //   dpdd/dmc = -pdd / D,            dpdd/dmp = s (l w^2 + g c - pdd s) / D,
+  //   dpdd/dl  = mp s w^2 / D,        dpdd/dg  = mp s c / D,
+  //   dthdd/dmc = -(g s + Bu) / (l D), dthdd/dmp = -s (l w^2 c + g + Bu s) / (l D),
+  //   dthdd/dl  = -(mp s w^2 c / D + Bu / l) / l,   dthdd/dg = -(mc + mp) s / (l D)
+  // (D_mc = 1, D_mp = s^2; A and B are linear in each parameter).
+  static constexpr bool FUSED_DP = true;
+  template <bool WC, bool WJ, bool WH, bool WP = false>
   __device__ __forceinline__ static void eval(const ModelConst& K, const double (&z)[NZ], const double (&yb)[NX],
                                               const double (&cqd)[NZ], double (&pa)[NX], double (&pb)[NX],
                                               double (&mjx)[NX][MAXRX], double (&mju)[NX][MAXRU],
-                                              double (&hd)[NHD]) {
+                                              double (&hd)[NHD], double (*mdp)[NP] = nullptr) {
     const double mcm = K.c[0], mp = K.c[1], l = K.c[2], g = K.c[3], Mg = K.c[4];
     const double mpl = K.c[6], mp2 = K.c[7], mpg = K.c[8], mpl2 = K.c[9], g4 = K.c[10];
     const double hh = K.hh, mhh = K.mhh;
@@ -87,7 +95,8 @@ struct CartPole {
     const double iD = recip(K.one, D);
     const double w2 = fmul(K, w, w);
     const double lw2 = fmul(K, l, w2);
-    const double A = fma(ms, fma(g, c, lw2), F);
+    const double gl = fma(g, c, lw2);             // l w^2 + g c
+    const double A = fma(ms, gl, F);
     const double pdd = fmul(K, A, iD);
     const double mplw2 = fmul(K, mpl, w2);
     const double B = fma(-s, fma(mplw2, c, Mg), fmul(K, -F, c));
@@ -121,6 +130,21 @@ struct CartPole {
         mjx[3][0] = fmul(K, mhhil, Bu_t); mjx[3][1] = fmul(K, mhhil, Bu_w);
         mju[3][0] = fmul(K, mhhil, Bu_F);
       }
+      if (WP) {
+#pragma unroll
+        for (int k = 0; k < NX; ++k)
+#pragma unroll
+          for (int i = 0; i < NP; ++i) mdp[k][i] = 0.0;
+        const double mhhilD = fmul(K, mhhil, iD);
+        mdp[1][0] = fmul(K, -mhiD, pdd);
+        mdp[1][1] = fmul(K, mhiD, fmul(K, s, fma(-pdd, s, gl)));
+        mdp[1][2] = fmul(K, mhiD, fmul(K, ms, w2));
+        mdp[1][3] = fmul(K, mhiD, fmul(K, ms, c));
+        mdp[3][0] = fmul(K, mhhilD, -fma(g, s, Bu));
+        mdp[3][1] = fmul(K, mhhilD, fmul(K, -s, fma(lw2, c, fma(Bu, s, g))));
+        mdp[3][2] = fmul(K, mhhil, -fma(fmul(K, ms, fmul(K, w2, c)), iD, fmul(K, Bu, K.c[5])));
+        mdp[3][3] = fmul(K, mhhilD, fmul(K, -K.c[14], s));
+      }
       if (WH) {
         // Every second derivative above is (numerator) / D: the multipliers carry the 1/D (and
         // for the angular rows the 1/l), m1 = -hh ybar_1 / D and m3 = -hh ybar_3 / (l D), and the
@@ -150,40 +174,6 @@ struct CartPole {
   }
   __device__ __forceinline__ static void dparam(const ModelConst&, const double (&)[NZ], double (&mdp)[NX]) {
     mdp[0] = mdp[1] = mdp[2] = mdp[3] = 0.0;
-  }
-  // -hh df_k/dp_i for p = (mc, mp, l, g), from pdd = A / D and thdd = Bu / l with A, B, D as in
-  // eval (D_mc = 1, D_mp = s^2; A and B are linear in each parameter):
-  //   dpdd/dmc = -pdd / D,            dpdd/dmp = s (l w^2 + g c - pdd s) / D,
-  //   dpdd/dl  = mp s w^2 / D,        dpdd/dg  = mp s c / D,
-  //   dthdd/dmc = -(g s + Bu) / (l D), dthdd/dmp = -s (l w^2 c + g + Bu s) / (l D),
-  //   dthdd/dl  = -(mp s w^2 c / D + Bu / l) / l,   dthdd/dg = -(mc + mp) s / (l D).
-  __device__ __forceinline__ static void dparams(const ModelConst& K, const double (&z)[NZ], double (&mdp)[NX][NP]) {
-    const double mp = K.c[1], l = K.c[2], g = K.c[3];
-    const double th = z[2], w = z[3], F = z[4];
-    double s, c;
-    sincos_red(K, th, s, c);
-    const double ms = fmul(K, mp, s);
-    const double D = fma(ms, s, K.c[0]);
-    const double iD = recip(K.one, D);
-    const double w2 = fmul(K, w, w);
-    const double lw2 = fmul(K, l, w2);
-    const double gl = fma(g, c, lw2);                 // l w^2 + g c
-    const double pdd = fmul(K, fma(ms, gl, F), iD);
-    const double B = fma(-s, fma(fmul(K, K.c[6], w2), c, K.c[4]), fmul(K, -F, c));
-    const double Bu = fmul(K, B, iD);
-    const double mhiD = fmul(K, K.mhh, iD), mhhilD = fmul(K, K.c[12], iD);
-#pragma unroll
-    for (int k = 0; k < NX; ++k)
-#pragma unroll
-      for (int i = 0; i < NP; ++i) mdp[k][i] = 0.0;
-    mdp[1][0] = fmul(K, -mhiD, pdd);
-    mdp[1][1] = fmul(K, mhiD, fmul(K, s, fma(-pdd, s, gl)));
-    mdp[1][2] = fmul(K, mhiD, fmul(K, ms, w2));
-    mdp[1][3] = fmul(K, mhiD, fmul(K, ms, c));
-    mdp[3][0] = fmul(K, mhhilD, -fma(g, s, Bu));
-    mdp[3][1] = fmul(K, mhhilD, fmul(K, -s, fma(lw2, c, fma(Bu, s, g))));
-    mdp[3][2] = fmul(K, K.c[12], -fma(fmul(K, ms, fmul(K, w2, c)), iD, fmul(K, Bu, K.c[5])));
-    mdp[3][3] = fmul(K, mhhilD, fmul(K, -K.c[14], s));
   }
   __device__ __forceinline__ static void dparam_grad(const ModelConst&, const double (&)[NZ], const double (&)[NX],
                                                      double (&out)[NZ]) {

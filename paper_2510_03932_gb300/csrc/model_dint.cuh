@@ -23,6 +23,7 @@ struct Dint {
   OCP_TABLE1(HB, int, 1, {0})
   static constexpr bool HAS_DPARAM = false;
   static constexpr int NP = 0;  // no parameters
+  static constexpr bool FUSED_DP = false;
   OCP_TABLE2(DP, bool, NX, 1, {{false}, {false}})
 
   static void host_consts(const double*, double hh, ModelConst& mc) {

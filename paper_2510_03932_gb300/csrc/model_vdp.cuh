@@ -27,6 +27,7 @@ struct VdP {
   OCP_TABLE1(HB, int, NHD, {0, 0})
   static constexpr bool HAS_DPARAM = true;
   static constexpr int NP = 1;  // mu
+  static constexpr bool FUSED_DP = false;  // dparams separately (cheap)
   OCP_TABLE2(DP, bool, NX, NP, {{false}, {true}})
 
   static void host_consts(const double* p, double hh, ModelConst& mc) {

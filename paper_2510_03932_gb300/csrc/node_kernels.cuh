@@ -153,6 +153,24 @@ __device__ __forceinline__ double tile_sum(double v, double* red, double one) {
   return s;
 }
 
+// tile_sum of COUNT values per thread at once (the same fixed order for each), with one barrier
+// for all of them.  `red` holds COUNT * TILE doubles; results valid in thread 0.
+template <int TILE, int COUNT>
+__device__ __forceinline__ void tile_sum_n(const double (&v)[COUNT], double* red, double one, double (&out)[COUNT]) {
+#pragma unroll
+  for (int q = 0; q < COUNT; ++q) red[q * TILE + threadIdx.x] = v[q];
+  __syncthreads();
+  if (threadIdx.x < 32) {
+#pragma unroll
+    for (int q = 0; q < COUNT; ++q) {
+      double s = red[q * TILE + threadIdx.x];
+#pragma unroll
+      for (int i = 1; i < TILE / 32; ++i) s = fma(red[q * TILE + threadIdx.x + 32 * i], one, s);
+      out[q] = warp_sum(s, one);
+    }
+  }
+}
+
 // Completion of a reduction over tiles: every tile t stored its fixed-order CTA sum of value
 // i < count in partials[i * ntiles + t]; the last CTA to finish (completion ticket) adds each
 // partials[i * ntiles + 0..ntiles) in a fixed order (strided per thread, then a fixed tree)
@@ -711,7 +729,7 @@ __global__ void __launch_bounds__(TILE) k_node_jtprod(const __grid_constant__ No
   constexpr int NX = M::NX, NZ = M::NZ;
   constexpr int NHD = (M::NHD > 0) ? M::NHD : 1;
   constexpr int NP = M::NP, NPA = (NP > 0) ? NP : 1;
-  __shared__ double red[TILE];
+  __shared__ double red[TILE * NPA];
   ModelConst K = launch_consts<M, PAR>(a);
   const int64_t nchunks = (a.E - a.B + TILE - 1) / TILE;   // the nodes [B, E) in chunks of TILE
   for (int64_t chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
@@ -725,13 +743,17 @@ __global__ void __launch_bounds__(TILE) k_node_jtprod(const __grid_constant__ No
       double wb[NX], wl[NX], wr[NX];
       load_node<M>(a, j, z);
       load_bar<M>(a, K, a.v, j, wb, wl, wr);
-      M::template eval<false, true, false>(K, z, yb, cqd, pa, pb, mjx, mju, hd);
+      double mdp[NX][NPA];
+      if constexpr (DPAR && M::FUSED_DP) {   // J and -hh df/dp from one set of intermediates
+        M::template eval<false, true, false, true>(K, z, yb, cqd, pa, pb, mjx, mju, hd, mdp);
+      } else {
+        M::template eval<false, true, false>(K, z, yb, cqd, pa, pb, mjx, mju, hd);
+        if constexpr (DPAR && NP > 0 && !M::FUSED_DP) M::dparams(K, z, mdp);
+      }
       double o[NZ];
       jtv_node<M>(a, K, a.v, j, bnd, mjx, mju, wl, wr, wb, o);
       store_nz<M>(a, a.out, j, o);
       if (DPAR && NP > 0) {
-        double mdp[NX][NPA];
-        M::dparams(K, z, mdp);
 #pragma unroll
         for (int i = 0; i < NPA; ++i)
 #pragma unroll
@@ -740,12 +762,13 @@ __global__ void __launch_bounds__(TILE) k_node_jtprod(const __grid_constant__ No
       }
     }
     if (DPAR) {
+      double ts[NPA];
+      tile_sum_n<TILE, NPA>(acc, red, K.one, ts);
+      if (threadIdx.x == 0) {
 #pragma unroll
-      for (int i = 0; i < NPA; ++i) {
-        const double ts = tile_sum<TILE>(acc[i], red, K.one);
-        if (threadIdx.x == 0) a.partials[i * nchunks + chunk] = ts;
-        __syncthreads();
+        for (int i = 0; i < NPA; ++i) a.partials[i * nchunks + chunk] = ts[i];
       }
+      __syncthreads();
     }
   }
   if (DPAR) finish_tiles<TILE, NPA>(a.partials, nchunks, a.counter, a.dmu, 1.0, red);

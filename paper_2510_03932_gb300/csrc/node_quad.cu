@@ -4,7 +4,7 @@
 
 namespace ocpg {
 ocp_status node_eval_quad(ocp* h, unsigned out, const EvalCall& c, cudaStream_t s) {
-  return node_eval_dispatch<Quadrotor, TILE_QUAD>(h, out, c, s);
+  return node_eval_dispatch<Quadrotor, TILE_QUAD_EVAL>(h, out, c, s);
 }
 ocp_status node_prod_quad(ocp* h, const ProdCall& c, cudaStream_t s) {
   return node_prod_dispatch<Quadrotor, TILE_QUAD>(h, c, s);

@@ -102,7 +102,7 @@ SMALL = [("vdp_n1e3", N) for N in (1, 2, 3, 254, 255, 256, 510, 1000, 1777)] + \
         [("cartpole_n1e5", N) for N in (1, 2, 126, 127, 128, 1000, 1303)] + \
         [("heat_n2e4", N) for N in (1, 2, 30, 31, 32, 100, 333)] + \
         [("dint", N) for N in (1, 2, 100, 997)] + \
-        [("quadrotor_n1e3", N) for N in (1, 2, 62, 63, 64, 126, 1000, 1777)] + \
+        [("quadrotor_n1e3", N) for N in (1, 2, 62, 63, 64, 126, 127, 128, 254, 1000, 1777)] + \
         [("goddard_n1e3", N) for N in (1, 2, 254, 255, 256, 510, 1000, 1777)] + \
         [("vdp_n1e3:euler", N) for N in (1, 2, 255, 256, 257, 1000)] + \
         [("cartpole_n1e5:euler", N) for N in (1, 127, 128, 129, 1303)] + \
