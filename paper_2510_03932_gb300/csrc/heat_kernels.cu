@@ -119,11 +119,15 @@ __device__ __forceinline__ void heat_jbound(const HeatArgs& a, int k, int64_t j)
 }
 
 // Hessian diagonal of cell k at node j: 6 hh ybar_k x_k + the objective's sigma w q_k
+// (yl, yr = y_{k,j-1}, y_{k,j}, zero beyond the first and last rows)
+__device__ __forceinline__ double heat_hdiag_y(const HeatArgs& a, int k, bool endp, double xk, double yl, double yr) {
+  const double ty = hmul(a, a.h6, hadd(a, yl, yr));
+  return fma(ty, xk, endp ? a.cq_end[k] : a.cq_in[k]);
+}
 __device__ __forceinline__ double heat_hdiag(const HeatArgs& a, int k, int64_t j, bool endp, double xk) {
   const double yl = (j >= 1) ? __ldg(a.y + a.nb + (int64_t)k * a.N + j - 1) : 0.0;
   const double yr = (j < a.N) ? __ldg(a.y + a.nb + (int64_t)k * a.N + j) : 0.0;
-  const double ty = hmul(a, a.h6, hadd(a, yl, yr));
-  return fma(ty, xk, endp ? a.cq_end[k] : a.cq_in[k]);
+  return heat_hdiag_y(a, k, endp, xk, yl, yr);
 }
 
 // gradient entry of cell k at node j and its objective term
@@ -258,6 +262,78 @@ __global__ void __launch_bounds__(HT_THREADS, (OUT & O_C) ? 5 : 8) k_heat_eval(c
     __syncthreads();
   }
   if (WF) finish_tiles<HT_THREADS>(a.partials, a.ntiles, a.counter, a.f, 0.5, red);
+}
+
+// ======================================================================================
+// Jacobian and Hessian values alone (no objective, defects or gradient).  Each entry depends on
+// its own cell only, so a CTA of two warps takes one tile's 32 nodes (31 owned) and 16 of its
+// cells, eight per warp: a problem splits into ceil(n/16) times as many CTAs as tiles, spread
+// evenly over the SMs (at N = 2e4 and 64 cells: 2584 CTAs, 17 per SM in one wave, where the
+// 646 CTAs of whole tiles put 4 on some SMs and 5 on others).  Every entry is computed by the
+// same expressions as in k_heat_eval, so the values are bit-identical.
+// ======================================================================================
+constexpr int HJ_CELLS = 16, HJ_WARPS = 2, HJ_THREADS = 32 * HJ_WARPS, HJ_LD = HJ_CELLS + 1;
+
+template <unsigned OUT>
+__global__ void __launch_bounds__(HJ_THREADS, 18) k_heat_jh(const __grid_constant__ HeatArgs a, int cgroups) {
+  constexpr bool CJ = OUT & O_J, CH = OUT & O_H;
+  const bool WJ = CJ && a.jv, WH = CH && a.hv;
+  // the states of the unit's cells, node-major in padded rows, overwritten in place by the
+  // Hessian diagonal; the multipliers y_{k, r0-1 .. r0+30} of its cells, cell-major
+  __shared__ double sX[HT_LANES * HJ_LD];
+  __shared__ double sY[HJ_CELLS * HT_LANES];
+  const int n = a.n;
+  const int t = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t units = a.ntiles * cgroups;
+  for (int64_t unit = blockIdx.x; unit < units; unit += gridDim.x) {
+    const int64_t tile = unit / cgroups;
+    const int c0 = (int)(unit - tile * cgroups) * HJ_CELLS;
+    const int nc = min(HJ_CELLS, n - c0);
+    const int64_t r0 = a.B + tile * (HT_LANES - 1);
+    const int64_t own_end = min(r0 + HT_LANES - 1, a.E);
+    const int64_t row_end = min(own_end, a.N);
+    const int nn = (int)(row_end + 1 - r0);
+    const int nown = (int)(own_end - r0);
+    const int nrows = (int)max(row_end - r0, (int64_t)0);
+    const int64_t j = r0 + t;
+    const bool act = t < nn;
+    const bool own = t < nown;
+    const bool endp = (j == 0) || (j == a.N);
+    for (int i = threadIdx.x; i < nn * nc; i += HJ_THREADS) {
+      const int tt = i / nc, kk = i - tt * nc;
+      sX[tt * HJ_LD + kk] = __ldg(a.x + (int64_t)n * (r0 + tt) + c0 + kk);
+    }
+    if (WH) {
+      // rows outside [0, N) stage as zero: y_{k,j-1} for j = 0 and y_{k,j} for j = N
+      for (int i = threadIdx.x; i < nc * HT_LANES; i += HJ_THREADS) {
+        const int kk = i / HT_LANES;
+        const int64_t jj = r0 - 1 + (i - kk * HT_LANES);
+        sY[i] = (jj >= 0 && jj < a.N) ? __ldg(a.y + a.nb + (int64_t)(c0 + kk) * a.N + jj) : 0.0;
+      }
+    }
+    __syncthreads();
+    // the control's Hessian entry (u, u), by the unit of the first cells
+    if (c0 == 0 && warp == 0 && own && WH && a.hu) a.hv[(int64_t)n * (a.N + 1) + j] = endp ? a.cq_end[n] : a.cq_in[n];
+    const int k1 = min(8 * warp + 8, nc);
+    for (int kk = 8 * warp; kk < k1; ++kk) {
+      const int k = c0 + kk;
+      double xk = 0.0;
+      if (act) xk = sX[t * HJ_LD + kk];
+      if (WJ) heat_jrows(a, k, k == n - 1, t, act, nrows, r0, hmul(a, xk, xk));
+      if (WJ && own) heat_jbound(a, k, j);
+      // an owned lane t <= 30 reads the multipliers of rows j-1 and j at positions t and t+1
+      if (own && WH) sX[t * HJ_LD + kk] = heat_hdiag_y(a, k, endp, xk, sY[kk * HT_LANES + t], sY[kk * HT_LANES + t + 1]);
+    }
+    __syncthreads();
+    if (WH) {
+      double* dst = a.hv + (int64_t)n * r0 + c0;
+      for (int i = threadIdx.x; i < nown * nc; i += HJ_THREADS) {
+        const int tt = i / nc, kk = i - tt * nc;
+        dst[(int64_t)n * tt + kk] = sX[tt * HJ_LD + kk];
+      }
+    }
+    __syncthreads();
+  }
 }
 
 // ======================================================================================
@@ -463,14 +539,32 @@ static ocp_status heat_eval_t(ocp* h, const EvalCall& c, cudaStream_t s) {
   return cuda_err(h, cudaGetLastError(), "k_heat_eval launch");
 }
 
+// Jacobian and / or Hessian values alone: units of one tile and 16 cells (k_heat_jh)
+template <unsigned OUT>
+static ocp_status heat_jh_t(ocp* h, const EvalCall& c, cudaStream_t s) {
+  HeatArgs a;
+  heat_fill(h, c.sigma, a);
+  a.x = c.x; a.y = c.y; a.jv = c.jv; a.hv = c.hv;
+  a.B = c.B; a.E = c.E;
+  const int64_t nodes = c.E - c.B;
+  a.ntiles = (nodes + (HT_LANES - 2)) / (HT_LANES - 1);
+  if (a.ntiles < 1) a.ntiles = 1;
+  const int cgroups = (h->nx + HJ_CELLS - 1) / HJ_CELLS;
+  auto kern = k_heat_jh<OUT>;
+  const int grid = occupancy_grid(h, (const void*)kern, HJ_THREADS, 0, a.ntiles * cgroups);
+  if (grid <= 0) return set_err(h, OCP_ECUDA, "occupancy query failed");
+  kern<<<grid, HJ_THREADS, 0, s>>>(a, cgroups);
+  return cuda_err(h, cudaGetLastError(), "k_heat_jh launch");
+}
+
 ocp_status heat_eval(ocp* h, unsigned out, const EvalCall& c, cudaStream_t s) {
   switch (out) {
     case O_F: return heat_eval_t<O_F>(h, c, s);
     case O_C: return heat_eval_t<O_C>(h, c, s);
     case O_G: return heat_eval_t<O_G>(h, c, s);
-    case O_J: return heat_eval_t<O_J>(h, c, s);
-    case O_H: return heat_eval_t<O_H>(h, c, s);
-    case O_J | O_H: return heat_eval_t<O_J | O_H>(h, c, s);
+    case O_J: return heat_jh_t<O_J>(h, c, s);
+    case O_H: return heat_jh_t<O_H>(h, c, s);
+    case O_J | O_H: return heat_jh_t<O_J | O_H>(h, c, s);
     default: return heat_eval_t<O_ALL>(h, c, s);
   }
 }

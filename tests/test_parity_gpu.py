@@ -87,6 +87,10 @@ def full_check(ocp, w, report=None, products=True):
     assert np.array_equal(host(H.eval_grad(x)), host(g))
     assert np.array_equal(host(H.jac_coo_values(x)), host(jv))
     assert np.array_equal(host(H.hess_coo_values(x, y, sigma)), host(hv))
+    # J and H values alone (the two-output launch), every slot written (NaN prefill)
+    jv2, hv2 = torch.full_like(jv, float("nan")), torch.full_like(hv, float("nan"))
+    H.eval_all(x, y, sigma, None, None, None, jv2, hv2, alloc=False)
+    assert np.array_equal(host(jv2), host(jv)) and np.array_equal(host(hv2), host(hv))
     if products:
         o, m = O.jprod(P, d["x"], d["vn"], shadow=True)
         gate("jprod", host(H.jprod(x, vn)), o, m, rep)
