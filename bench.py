@@ -110,7 +110,7 @@ KERNEL_SOURCES = {
 }
 # Tags of the sources the FP64_OPS_PER_NODE counts (and TRAFFIC) were measured on.
 FP64_OPS_SRC = {"vdp": "cc658d1f082c", "vdp:euler": "cc658d1f082c", "cartpole": "061236c3a755",
-                "quadrotor": "a813de1053eb", "goddard": "5c6666cb0cfe", "heat64": "885ea04bd247"}
+                "quadrotor": "a813de1053eb", "goddard": "5c6666cb0cfe", "heat64": "d7a6a1dbfeb5"}
 
 
 def kernel_source_tag(key):

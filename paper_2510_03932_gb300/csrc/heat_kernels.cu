@@ -7,9 +7,11 @@
 // Row template of component k (the defect of cell k): X cells {k-1, k, k+1} within 0..n-1 on
 // each side, plus the control for k = 0, so 6 entries per row except the last cell's 4.
 //
-// Work decomposition: a CTA covers 32 consecutive nodes (one per lane); its 8 warps take the
-// cells in groups of 8.  Row-coupled outputs (defects, Jacobian rows) use tiles that overlap
-// by one node (the CTA owns 31 of its 32 nodes); node-local products use disjoint tiles.
+// Work decomposition: a CTA covers 32 consecutive nodes (one per lane); in the evaluation and
+// H v its 8 warps take the cells in groups of 8, while the J + H values, Jv and J^T w run two
+// warps per CTA on units of 16 cells of a tile (four times as many CTAs, the same number on
+// every SM).  Row-coupled outputs (defects, Jacobian rows) use tiles that overlap by one node
+// (the CTA owns 31 of its 32 nodes); node-local products use disjoint tiles.
 // The states of the tile's nodes are staged in shared memory with a padded row (n+1 doubles)
 // so that lanes reading different nodes hit different banks; node-major outputs (Hessian
 // diagonal, J^T w, H v) are staged the same way and stored with consecutive threads on
@@ -337,142 +339,187 @@ __global__ void __launch_bounds__(HJ_THREADS, 18) k_heat_jh(const __grid_constan
 }
 
 // ======================================================================================
-// Jv:  p_k(j) = -hh grad f_k(z_j) . v_{z_j};  row (k,j) = (p_k(j) - v_{X_j,k}) + (p_k(j+1) + v_{X_{j+1},k})
+// H v (node-local):    out_a = (2 sigma w q_a + 6 hh ybar_a x_a) v_a,  out_u = 2 sigma w r v_u
+// (whole tiles of 32 nodes and their 64 cells: measured faster than the 16-cell units of the
+// other products, 23.3 against 24.3 us at N = 2e4, 39.4 against 41.1 at N = 5e4); at most 51
+// registers: five CTAs per SM, one wave of 626 tiles at N = 2e4 (measured faster)
 // ======================================================================================
-__global__ void __launch_bounds__(HT_THREADS) k_heat_jprod(const __grid_constant__ HeatArgs a) {
+__global__ void __launch_bounds__(HT_THREADS, 5) k_heat_hprod(const __grid_constant__ HeatArgs a) {
   extern __shared__ __align__(16) double sm[];
   const int n = a.n, ld = n + 1;
   double* sX = sm;
-  double* sV = sX + HT_LANES * ld;
+  double* sV = sX + HT_LANES * ld;  // the direction
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
-    const int64_t r0 = tile * (HT_LANES - 1);
-    const int64_t own_end = min(r0 + HT_LANES - 1, a.N + 1);
-    const int64_t row_end = min(own_end, a.N);
-    const int nn = (int)(row_end + 1 - r0);
-    const int nrows = (int)max(row_end - r0, (int64_t)0);
+    const int64_t r0 = tile * HT_LANES;
+    const int nn = (int)min((int64_t)HT_LANES, a.N + 1 - r0);
     const int t = lane;
     const int64_t j = r0 + t;
     const bool act = t < nn;
+    const bool endp = (j == 0) || (j == a.N);
     heat_stage(a, a.x, r0, nn, sX);
     heat_stage(a, a.v, r0, nn, sV);
     __syncthreads();
     const int ngroups = (n + 7) / 8;
     for (int gi = warp; gi < ngroups; gi += HT_WARPS) {
       const int k0 = gi * 8, k1 = min(k0 + 8, n);
-      for (int k = k0; k < k1; ++k) {
-        double p = 0.0, vk = 0.0;
-        if (act) {
-          const double xk = sX[t * ld + k];
-          const bool last = (k == n - 1);
-          vk = sV[t * ld + k];
-          const double vl = (k == 0) ? sV[t * ld + n] : sV[t * ld + k - 1];
-          const double dk = fma(a.h3, hmul(a, xk, xk), last ? a.d_last : a.d_in);
-          const double nsum = last ? vl : hadd(a, vl, sV[t * ld + k + 1]);
-          p = fma(a.mhidx2, nsum, hmul(a, dk, vk));
-        }
-        const double right = __shfl_down_sync(0xffffffffu, hadd(a, p, vk), 1);
-        if (t < nrows) a.out[a.nb + (int64_t)k * a.N + j] = hadd(a, hsub(a, p, vk), right);
-        if (act && j == 0) a.out[k] = vk;
-        if (act && a.has_final && j == a.N && t < (int)(own_end - r0)) a.out[n + k] = vk;
+      // elementwise: the group's multiplier rows are loaded before any arithmetic needs them
+      double yl[8], yr[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int k = k0 + q;
+        yl[q] = (act && k < k1 && j >= 1) ? __ldg(a.y + a.nb + (int64_t)k * a.N + j - 1) : 0.0;
+        yr[q] = (act && k < k1 && j < a.N) ? __ldg(a.y + a.nb + (int64_t)k * a.N + j) : 0.0;
       }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int k = k0 + q;
+        if (act && k < k1) {
+          const double xk = sX[t * ld + k];
+          const double hk = fma(hmul(a, a.h6, hadd(a, yl[q], yr[q])), xk, endp ? a.cq_end[k] : a.cq_in[k]);
+          sX[t * ld + k] = hmul(a, hk, sV[t * ld + k]);  // in place: x no longer needed for cell k
+        }
+      }
+    }
+    if (warp == 0 && act) {
+      const double cu = a.hu ? (endp ? a.cq_end[n] : a.cq_in[n]) : 0.0;
+      sX[t * ld + n] = hmul(a, cu, sV[t * ld + n]);
+    }
+    __syncthreads();
+    {
+      const int total = nn * n;
+      double* dst = a.out + (int64_t)n * r0;
+      for (int i = threadIdx.x; i < total; i += HT_THREADS) {
+        const int tt = i / n, k = i - tt * n;
+        dst[i] = sX[tt * ld + k];
+      }
+      for (int tt = threadIdx.x; tt < nn; tt += HT_THREADS) a.out[a.uoff + r0 + tt] = sX[tt * ld + n];
     }
     __syncthreads();
   }
 }
 
 // ======================================================================================
-// J^T w (node-local):  out_a = (w_{a,j-1} - w_{a,j}) + wbar_a dd_a - hh/dx^2 (wbar_{a-1} + wbar_{a+1})
-//                      out_u = -hh/dx^2 wbar_0       (dd_a = -hh df_a/dx_a)
-// H v (node-local):    out_a = (2 sigma w q_a + 6 hh ybar_a x_a) v_a,  out_u = 2 sigma w r v_u
+// Jv and J^T w on units of one tile and 16 cells (two warps of 8 cells each, as in k_heat_jh),
+// so that the work spreads evenly over the SMs (at N = 2e4: Jv 35.0 -> 31.4 us, J^T w 31.8 ->
+// 28.9 us, against whole tiles of 32 nodes and 64 cells).
+//   Jv:     p_k(j) = -hh grad f_k(z_j) . v_{z_j};
+//           row (k,j) = (p_k(j) - v_{X_j,k}) + (p_k(j+1) + v_{X_{j+1},k})
+//           on tiles overlapping by one node (its rows couple nodes j and j+1); the direction of
+//           cells c0-1 .. c0+16 is staged, the control's in place of cell -1.
+//   J^T w:  out_a = (w_{a,j-1} - w_{a,j}) + wbar_a dd_a - hh/dx^2 (wbar_{a-1} + wbar_{a+1}),
+//           out_u = -hh/dx^2 wbar_0  (dd_a = -hh df_a/dx_a), node-local on disjoint tiles; the
+//           result is staged and stored node by node in runs of the unit's cells.
 // ======================================================================================
-template <bool JT>
-// (at most 51 registers: five CTAs per SM, one wave of 626 tiles at N = 2e4; measured faster)
-__global__ void __launch_bounds__(HT_THREADS, 5) k_heat_local(const __grid_constant__ HeatArgs a) {
-  extern __shared__ __align__(16) double sm[];
-  const int n = a.n, ld = n + 1;
-  double* sX = sm;
-  double* sV = sX + HT_LANES * ld;  // H v: the direction; J^T w: the output staging
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int64_t tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x) {
-    const int64_t r0 = tile * HT_LANES;
-    const int nn = (int)min((int64_t)HT_LANES, a.N + 1 - r0);
-    const bool bnd = (tile == 0) || (r0 + HT_LANES > a.N);
-    const int t = lane;
+enum : int { HP_JPROD = 0, HP_JTPROD = 1 };
+constexpr int HP_LDV = HJ_CELLS + 3;  // padded row of the staged direction (or J^T w result)
+
+template <int KIND>
+__global__ void __launch_bounds__(HJ_THREADS, 18) k_heat_prod_unit(const __grid_constant__ HeatArgs a, int cgroups) {
+  constexpr bool JP = KIND == HP_JPROD, JT = KIND == HP_JTPROD;
+  constexpr int LDV = JP ? HP_LDV : HJ_LD;
+  __shared__ double sX[HT_LANES * HJ_LD];  // states of the unit's cells
+  __shared__ double sV[HT_LANES * LDV];    // Jv: the direction; J^T w: the result
+  const int n = a.n;
+  const int t = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t units = a.ntiles * cgroups;
+  for (int64_t unit = blockIdx.x; unit < units; unit += gridDim.x) {
+    const int64_t tile = unit / cgroups;
+    const int c0 = (int)(unit - tile * cgroups) * HJ_CELLS;
+    const int nc = min(HJ_CELLS, n - c0);
+    const int kb = 8 * warp, ke = min(8 * warp + 8, nc);  // this warp's cells c0 + [kb, ke)
+    int64_t r0;
+    int nn, nrows = 0, nown = 0;
+    bool bnd = false;
+    if (JP) {
+      r0 = tile * (HT_LANES - 1);
+      const int64_t own_end = min(r0 + HT_LANES - 1, a.N + 1);
+      const int64_t row_end = min(own_end, a.N);
+      nn = (int)(row_end + 1 - r0);
+      nrows = (int)max(row_end - r0, (int64_t)0);
+      nown = (int)(own_end - r0);
+    } else {
+      r0 = tile * HT_LANES;
+      nn = (int)min((int64_t)HT_LANES, a.N + 1 - r0);
+      bnd = (tile == 0) || (r0 + HT_LANES > a.N);
+    }
     const int64_t j = r0 + t;
     const bool act = t < nn;
-    const bool endp = (j == 0) || (j == a.N);
-    heat_stage(a, a.x, r0, nn, sX);
-    if (!JT) heat_stage(a, a.v, r0, nn, sV);
+    for (int i = threadIdx.x; i < nn * nc; i += HJ_THREADS) {
+      const int tt = i / nc, kk = i - tt * nc;
+      sX[tt * HJ_LD + kk] = __ldg(a.x + (int64_t)n * (r0 + tt) + c0 + kk);
+    }
+    if (JP) {
+      const int w = nc + 2;  // cells c0-1 .. c0+nc at positions 0 .. nc+1
+      for (int i = threadIdx.x; i < nn * w; i += HJ_THREADS) {
+        const int tt = i / w, e = i - tt * w, k = c0 - 1 + e;
+        double val = 0.0;
+        if (k < 0) val = __ldg(a.v + a.uoff + r0 + tt);
+        else if (k < n) val = __ldg(a.v + (int64_t)n * (r0 + tt) + k);
+        sV[tt * HP_LDV + e] = val;
+      }
+    }
     __syncthreads();
-    const int ngroups = (n + 7) / 8;
-    for (int gi = warp; gi < ngroups; gi += HT_WARPS) {
-      const int k0 = gi * 8, k1 = min(k0 + 8, n);
-      if (JT) {
-        // wbar of cells k0-1 .. k1 (clamped), rolling window
-        auto wbar = [&](int k, double& wl, double& wr) {
-          const double* row = a.v + a.nb + (int64_t)k * a.N;
-          wl = (j >= 1) ? __ldg(row + j - 1) : 0.0;
-          wr = (j < a.N) ? __ldg(row + j) : 0.0;
-        };
-        double wbm = 0.0, wbc = 0.0, wbp = 0.0, wlc = 0.0, wrc = 0.0;
+    if (JP) {
+      for (int kk = kb; kk < ke; ++kk) {
+        const int k = c0 + kk;
+        double p = 0.0, vk = 0.0;
         if (act) {
-          if (k0 > 0) { double l2, r2; wbar(k0 - 1, l2, r2); wbm = hadd(a, l2, r2); }
-          wbar(k0, wlc, wrc);
-          wbc = hadd(a, wlc, wrc);
-          if (k0 == 0) sV[t * ld + n] = hmul(a, a.mhidx2, wbc);  // control column: -hh/dx^2 wbar_0
+          const double xk = sX[t * HJ_LD + kk];
+          const bool last = (k == n - 1);
+          vk = sV[t * HP_LDV + kk + 1];
+          const double vl = sV[t * HP_LDV + kk];  // cell k-1, or the control for k = 0
+          const double dk = fma(a.h3, hmul(a, xk, xk), last ? a.d_last : a.d_in);
+          const double nsum = last ? vl : hadd(a, vl, sV[t * HP_LDV + kk + 2]);
+          p = fma(a.mhidx2, nsum, hmul(a, dk, vk));
         }
-        for (int k = k0; k < k1; ++k) {
-          if (act) {
-            double wlp = 0.0, wrp = 0.0;
-            if (k + 1 < n) { wbar(k + 1, wlp, wrp); wbp = hadd(a, wlp, wrp); } else wbp = 0.0;
-            const double xk = sX[t * ld + k];
-            const bool last = (k == n - 1);
-            const double dk = fma(a.h3, hmul(a, xk, xk), last ? a.d_last : a.d_in);
-            double s = fma(wbc, dk, hsub(a, wlc, wrc));
-            s = fma(a.mhidx2, hadd(a, wbm, wbp), s);
-            if (bnd) {  // only the CTAs holding node 0 or node N (uniform branch)
-              if (j == 0) s = hadd(a, s, __ldg(a.v + k));
-              if (a.has_final && j == a.N) s = hadd(a, s, __ldg(a.v + n + k));
-            }
-            sV[t * ld + k] = s;
-            wbm = wbc; wbc = wbp; wlc = wlp; wrc = wrp;
-          }
-        }
-      } else {
-        // elementwise: the group's multiplier rows are loaded before any arithmetic needs them
-        double yl[8], yr[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int k = k0 + q;
-          yl[q] = (act && k < k1 && j >= 1) ? __ldg(a.y + a.nb + (int64_t)k * a.N + j - 1) : 0.0;
-          yr[q] = (act && k < k1 && j < a.N) ? __ldg(a.y + a.nb + (int64_t)k * a.N + j) : 0.0;
-        }
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const int k = k0 + q;
-          if (act && k < k1) {
-            const double xk = sX[t * ld + k];
-            const double hk = fma(hmul(a, a.h6, hadd(a, yl[q], yr[q])), xk, endp ? a.cq_end[k] : a.cq_in[k]);
-            sX[t * ld + k] = hmul(a, hk, sV[t * ld + k]);  // in place: x no longer needed for cell k
-          }
-        }
+        const double right = __shfl_down_sync(0xffffffffu, hadd(a, p, vk), 1);
+        if (t < nrows) a.out[a.nb + (int64_t)k * a.N + j] = hadd(a, hsub(a, p, vk), right);
+        if (act && j == 0) a.out[k] = vk;
+        if (act && a.has_final && j == a.N && t < nown) a.out[n + k] = vk;
       }
     }
-    if (!JT && warp == 0 && act) {
-      const double cu = a.hu ? (endp ? a.cq_end[n] : a.cq_in[n]) : 0.0;
-      sX[t * ld + n] = hmul(a, cu, sV[t * ld + n]);
+    if (JT && kb < ke) {
+      // wbar of cells k0-1 .. k1 (clamped), rolling window
+      auto wbar = [&](int k, double& wl, double& wr) {
+        const double* row = a.v + a.nb + (int64_t)k * a.N;
+        wl = (j >= 1) ? __ldg(row + j - 1) : 0.0;
+        wr = (j < a.N) ? __ldg(row + j) : 0.0;
+      };
+      const int k0 = c0 + kb, k1 = c0 + ke;
+      double wbm = 0.0, wbc = 0.0, wbp = 0.0, wlc = 0.0, wrc = 0.0;
+      if (act) {
+        if (k0 > 0) { double l2, r2; wbar(k0 - 1, l2, r2); wbm = hadd(a, l2, r2); }
+        wbar(k0, wlc, wrc);
+        wbc = hadd(a, wlc, wrc);
+        if (k0 == 0) a.out[a.uoff + j] = hmul(a, a.mhidx2, wbc);  // control column: -hh/dx^2 wbar_0
+      }
+      for (int k = k0; k < k1; ++k) {
+        if (act) {
+          double wlp = 0.0, wrp = 0.0;
+          if (k + 1 < n) { wbar(k + 1, wlp, wrp); wbp = hadd(a, wlp, wrp); } else wbp = 0.0;
+          const double xk = sX[t * HJ_LD + (k - c0)];
+          const bool last = (k == n - 1);
+          const double dk = fma(a.h3, hmul(a, xk, xk), last ? a.d_last : a.d_in);
+          double s = fma(wbc, dk, hsub(a, wlc, wrc));
+          s = fma(a.mhidx2, hadd(a, wbm, wbp), s);
+          if (bnd) {  // only the CTAs holding node 0 or node N (uniform branch)
+            if (j == 0) s = hadd(a, s, __ldg(a.v + k));
+            if (a.has_final && j == a.N) s = hadd(a, s, __ldg(a.v + n + k));
+          }
+          sV[t * LDV + (k - c0)] = s;
+          wbm = wbc; wbc = wbp; wlc = wlp; wrc = wrp;
+        }
+      }
     }
     __syncthreads();
-    const double* res = JT ? sV : sX;
-    {
-      const int total = nn * n;
-      double* dst = a.out + (int64_t)n * r0;
-      for (int i = threadIdx.x; i < total; i += HT_THREADS) {
-        const int tt = i / n, k = i - tt * n;
-        dst[i] = res[tt * ld + k];
+    if (JT) {
+      // node-major results of the unit's cells, in runs of nc per node
+      double* dst = a.out + (int64_t)n * r0 + c0;
+      for (int i = threadIdx.x; i < nn * nc; i += HJ_THREADS) {
+        const int tt = i / nc, kk = i - tt * nc;
+        dst[(int64_t)n * tt + kk] = sV[tt * HJ_LD + kk];
       }
-      for (int tt = threadIdx.x; tt < nn; tt += HT_THREADS) a.out[a.uoff + r0 + tt] = res[tt * ld + n];
     }
     __syncthreads();
   }
@@ -573,32 +620,24 @@ ocp_status heat_prod(ocp* h, const ProdCall& c, cudaStream_t s) {
   HeatArgs a;
   heat_fill(h, c.sigma, a);
   a.x = c.x; a.y = c.y; a.v = c.v; a.out = c.out;
-  const int ld = h->nx + 1;
-  const size_t smem = sizeof(double) * (size_t)HT_LANES * ld * 2;  // states and direction/result
-  cudaError_t e;
-  if (c.kind == P_JPROD) {
-    a.ntiles = (h->N + 1 + (HT_LANES - 2)) / (HT_LANES - 1);
-    auto k = k_heat_jprod;
-    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return cuda_err(h, e, "cudaFuncSetAttribute(heat jprod)");
+  if (c.kind == P_HPROD) {
+    a.ntiles = (h->N + 1 + HT_LANES - 1) / HT_LANES;
+    const size_t smem = sizeof(double) * (size_t)HT_LANES * (h->nx + 1) * 2;  // states and direction
+    auto k = k_heat_hprod;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_err(h, e, "cudaFuncSetAttribute(heat hprod)");
     const int grid = occupancy_grid(h, (const void*)k, HT_THREADS, smem, a.ntiles);
     k<<<grid, HT_THREADS, smem, s>>>(a);
-  } else {
-    a.ntiles = (h->N + 1 + HT_LANES - 1) / HT_LANES;
-    if (c.kind == P_JTPROD) {
-      auto k = k_heat_local<true>;
-      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return cuda_err(h, e, "cudaFuncSetAttribute(heat jtprod)");
-      const int grid = occupancy_grid(h, (const void*)k, HT_THREADS, smem, a.ntiles);
-      k<<<grid, HT_THREADS, smem, s>>>(a);
-    } else {
-      auto k = k_heat_local<false>;
-      e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return cuda_err(h, e, "cudaFuncSetAttribute(heat hprod)");
-      const int grid = occupancy_grid(h, (const void*)k, HT_THREADS, smem, a.ntiles);
-      k<<<grid, HT_THREADS, smem, s>>>(a);
-    }
+    return cuda_err(h, cudaGetLastError(), "heat product launch");
   }
+  const int cgroups = (h->nx + HJ_CELLS - 1) / HJ_CELLS;
+  if (c.kind == P_JPROD) a.ntiles = (h->N + 1 + (HT_LANES - 2)) / (HT_LANES - 1);
+  else a.ntiles = (h->N + 1 + HT_LANES - 1) / HT_LANES;
+  const void* k = (c.kind == P_JPROD) ? (const void*)k_heat_prod_unit<HP_JPROD> : (const void*)k_heat_prod_unit<HP_JTPROD>;
+  const int grid = occupancy_grid(h, k, HJ_THREADS, 0, a.ntiles * cgroups);
+  if (grid <= 0) return set_err(h, OCP_ECUDA, "occupancy query failed");
+  if (c.kind == P_JPROD) k_heat_prod_unit<HP_JPROD><<<grid, HJ_THREADS, 0, s>>>(a, cgroups);
+  else k_heat_prod_unit<HP_JTPROD><<<grid, HJ_THREADS, 0, s>>>(a, cgroups);
   return cuda_err(h, cudaGetLastError(), "heat product launch");
 }
 
