@@ -467,7 +467,7 @@ ocp_status ocp_value_layout(const ocp_t* h, int64_t* nb, int32_t* row_count, int
  * asynchronous on `stream`.  The reduction scratch is a file-scope device array of 65536
  * tiles (about 512 KB on every device that loads the library, held until the process exits);
  * a horizon needing more tiles (N+1 above 65536 x 255 nodes for Van der Pol and the double
- * integrator, x 127 for the cart-pole, x 63 for the quadrotor, x 31 for the heat model; the
+ * integrator, x 127 for the cart-pole and the quadrotor, x 31 for the heat model; the
  * constant reference only) returns OCP_EDIM without
  * launching.  The first call on a device looks up the array's device address with that device
  * current (and caches it for the life of the process); make that first call before any stream
