@@ -84,10 +84,10 @@ def _counts(w):
 # bench reports no FP64 fraction for that model until they are measured again.
 FP64_OPS_PER_NODE = {("vdp", "eval_all"): 26.6, ("vdp", "jh"): 10.0, ("vdp", "jprod"): 13.0,
                      ("vdp", "jtprod"): 12.0, ("vdp", "hprod"): 11.0, ("vdp", "step"): 50.6,
-                     ("cartpole", "eval_all"): 118.8, ("cartpole", "jh"): 95.7, ("cartpole", "jprod"): 82.6,
-                     ("cartpole", "jtprod"): 79.0, ("cartpole", "hprod"): 97.0, ("cartpole", "step"): 164.9,
-                     ("quadrotor", "eval_all"): 247.6, ("quadrotor", "jh"): 175.4, ("quadrotor", "jprod"): 163.4,
-                     ("quadrotor", "jtprod"): 155.0, ("quadrotor", "hprod"): 198.0, ("quadrotor", "step"): 394.9,
+                     ("cartpole", "eval_all"): 110.8, ("cartpole", "jh"): 87.7, ("cartpole", "jprod"): 74.6,
+                     ("cartpole", "jtprod"): 71.0, ("cartpole", "hprod"): 89.0, ("cartpole", "step"): 156.9,
+                     ("quadrotor", "eval_all"): 235.5, ("quadrotor", "jh"): 163.3, ("quadrotor", "jprod"): 151.2,
+                     ("quadrotor", "jtprod"): 143.0, ("quadrotor", "hprod"): 186.0, ("quadrotor", "step"): 382.8,
                      ("goddard", "eval_all"): 98.2, ("goddard", "jh"): 89.2, ("goddard", "jprod"): 66.3,
                      ("goddard", "jtprod"): 67.1, ("goddard", "hprod"): 93.1, ("goddard", "step"): 153.4,
                      ("vdp:euler", "eval_all"): 21.5, ("vdp:euler", "jh"): 8.0, ("vdp:euler", "jprod"): 11.0,
@@ -103,14 +103,14 @@ _COMMON = ["node_kernels.cuh", "model_base.cuh", "kernel_config.h"]
 KERNEL_SOURCES = {
     "vdp": _COMMON + ["model_vdp.cuh", "node_vdp.cu"],
     "vdp:euler": _COMMON + ["model_vdp.cuh", "node_vdp.cu"],
-    "cartpole": _COMMON + ["model_cartpole.cuh", "node_cartpole.cu"],
-    "quadrotor": _COMMON + ["model_quad.cuh", "node_quad.cu"],
+    "cartpole": _COMMON + ["model_cartpole.cuh", "node_cartpole.cu", "sincos_table.cuh", "sincos_table_data.h"],
+    "quadrotor": _COMMON + ["model_quad.cuh", "node_quad.cu", "sincos_table.cuh", "sincos_table_data.h"],
     "goddard": _COMMON + ["goddard_kernels.cu"],
     "heat64": _COMMON + ["heat_kernels.cu"],
 }
 # Tags of the sources the FP64_OPS_PER_NODE counts (and TRAFFIC) were measured on.
-FP64_OPS_SRC = {"vdp": "cc658d1f082c", "vdp:euler": "cc658d1f082c", "cartpole": "061236c3a755",
-                "quadrotor": "a813de1053eb", "goddard": "5c6666cb0cfe", "heat64": "d7a6a1dbfeb5"}
+FP64_OPS_SRC = {"vdp": "cc658d1f082c", "vdp:euler": "cc658d1f082c", "cartpole": "fc0d1c1f54b5",
+                "quadrotor": "8626a7941187", "goddard": "5c6666cb0cfe", "heat64": "d7a6a1dbfeb5"}
 
 
 def kernel_source_tag(key):

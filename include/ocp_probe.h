@@ -43,6 +43,14 @@ ocp_status ocp_probe_recip(const double* d, double* out, int64_t n, void* stream
 ocp_status ocp_probe_sincos(const double* x, double* s, double* c, double* s_lib, double* c_lib, int64_t n,
                             void* stream);
 
+/* The same for the table-driven sin and cos of the cart-pole and quadrotor kernels (|x| = k pi/512
+ * + r, sin and cos of k pi/512 from a table of the doubles nearest the exact values, short
+ * polynomials in r, the library routine for warps holding an argument beyond 1e5 or not
+ * finite): s[i], c[i], and CUDA's sincos in s_lib[i], c_lib[i] (device arrays; asynchronous on
+ * `stream`).  Errors: OCP_EINVAL, OCP_ECUDA (ocp_last_error(NULL)). */
+ocp_status ocp_probe_sincos_table(const double* x, double* s, double* c, double* s_lib, double* c_lib, int64_t n,
+                                  void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -14,6 +14,7 @@
 #include "model_base.cuh"
 #include "ocp_internal.h"
 #include "ocp_probe.h"
+#include "sincos_table.cuh"
 
 namespace {
 
@@ -64,7 +65,38 @@ __global__ void k_probe_sincos(const double* x, double* s, double* c, double* sl
   }
 }
 
+// The table-driven sincos (sincos_tab) and the library's on the same arguments.
+__global__ void k_probe_sincos_tab(const double* x, double* s, double* c, double* sl, double* cl, int64_t n,
+                                   const __grid_constant__ ocpg::ModelConst K) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double a, b;
+    ocpg::sincos_tab(K, x[i], a, b);
+    s[i] = a;
+    c[i] = b;
+    sincos(x[i], &a, &b);
+    sl[i] = a;
+    cl[i] = b;
+  }
+}
+
 }  // namespace
+
+extern "C" ocp_status ocp_probe_sincos_table(const double* x, double* s, double* c, double* s_lib, double* c_lib,
+                                             int64_t n, void* stream) {
+  OCP_RANGE();
+  const double* p[5] = {x, s, c, s_lib, c_lib};
+  for (const double* q : p)
+    if (!q || ((uintptr_t)q & 7u)) return ocpg::set_err(nullptr, OCP_EINVAL, "ocp_probe_sincos_table: bad pointer");
+  if (n < 0) return ocpg::set_err(nullptr, OCP_EINVAL, "ocp_probe_sincos_table: n < 0");
+  if (n == 0) return OCP_OK;
+  ocpg::ModelConst K;
+  memset(&K, 0, sizeof(K));
+  K.one = 1.0;
+  K.mz = -0.0;
+  const int grid = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+  k_probe_sincos_tab<<<grid, 256, 0, (cudaStream_t)stream>>>(x, s, c, s_lib, c_lib, n, K);
+  return ocpg::cuda_err(nullptr, cudaGetLastError(), "ocp_probe_sincos_table launch");
+}
 
 extern "C" ocp_status ocp_probe_sincos(const double* x, double* s, double* c, double* s_lib, double* c_lib, int64_t n,
                                        void* stream) {

@@ -2,6 +2,7 @@
 // model_base.cuh).
 #pragma once
 #include "model_base.cuh"
+#include "sincos_table.cuh"
 
 namespace ocpg {
 
@@ -89,7 +90,7 @@ struct CartPole {
     const double hh = K.hh, mhh = K.mhh;
     const double p = z[0], pd = z[1], th = z[2], w = z[3], F = z[4];
     double s, c;
-    sincos_red(K, th, s, c);
+    sincos_tab(K, th, s, c);
     const double ms = fmul(K, mp, s);
     const double D = fma(ms, s, mcm);
     const double iD = recip(K.one, D);

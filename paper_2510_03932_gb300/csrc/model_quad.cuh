@@ -2,6 +2,7 @@
 // model_base.cuh).
 #pragma once
 #include "model_base.cuh"
+#include "sincos_table.cuh"
 
 namespace ocpg {
 
@@ -72,12 +73,10 @@ struct Quadrotor {
                                               double (&hd)[NHD]) {
     const double hh = K.hh, mhh = K.mhh;
     const double u1 = z[9], u2 = z[10], u3 = z[11];
-    // the library routine: the reduced-argument sincos of model_base.cuh measured slower in the
-    // quadrotor's register-capped fused kernels (step 846 -> 868 us at N = 1e6)
     double s7, c7, s8, c8, s9, c9;
-    sincos(z[6], &s7, &c7);
-    sincos(z[7], &s8, &c8);
-    sincos(z[8], &s9, &c9);
+    sincos_tab(K, z[6], s7, c7);
+    sincos_tab(K, z[7], s8, c8);
+    sincos_tab(K, z[8], s9, c9);
     const double e = recip(K.one, c8);
     const double t = fmul(K, s8, e);
     const double c7s8 = fmul(K, c7, s8), s7s8 = fmul(K, s7, s8);

@@ -99,6 +99,7 @@ _SIGS = {
     "ocp_probe_fp64": [C.c_int, C.c_int, C.c_int, C.c_int, _P, _P],
     "ocp_probe_recip": [_P, _P, _I64, _P],
     "ocp_probe_sincos": [_P, _P, _P, _P, _P, _I64, _P],
+    "ocp_probe_sincos_table": [_P, _P, _P, _P, _P, _I64, _P],
     "ocp_set_fault": [C.c_char_p],
     "ocp_last_error": [_P],
 }
@@ -153,13 +154,14 @@ def probe_recip(d, out=None, stream=None):
     return out
 
 
-def probe_sincos(x, stream=None):
-    """ocp_probe_sincos: (sin, cos) of the kernels and (sin, cos) of CUDA's sincos for every entry
-    of the CUDA float64 tensor x."""
+def probe_sincos(x, stream=None, table=False):
+    """ocp_probe_sincos (or, with table=True, ocp_probe_sincos_table): (sin, cos) of the kernels'
+    routine and (sin, cos) of CUDA's sincos for every entry of the CUDA float64 tensor x."""
     if x.dtype != torch.float64 or not x.is_cuda or not x.is_contiguous():
         raise TypeError("x must be a contiguous float64 CUDA tensor")
     outs = [torch.empty_like(x) for _ in range(4)]
-    _check(lib().ocp_probe_sincos(*[C.c_void_p(t.data_ptr()) for t in [x] + outs], int(x.numel()), _stream(stream)))
+    fn = lib().ocp_probe_sincos_table if table else lib().ocp_probe_sincos
+    _check(fn(*[C.c_void_p(t.data_ptr()) for t in [x] + outs], int(x.numel()), _stream(stream)))
     return tuple(outs)
 
 

@@ -1,8 +1,11 @@
-"""The evaluation kernels' sin and cos (three-constant Cody-Waite reduction to |r| <= pi/4,
-Taylor polynomials of sin r through r^17 and cos r through r^16, the library routine for warps
-holding an argument beyond 1e5 or not finite; used by the cart-pole model) against numpy
-within two ulps and CUDA's sincos within three, on uniform, log-uniform and
-near-multiple-of-pi/2 samples; exact zeros and signs where the result is exact; the library's own values on the fallback path."""
+"""The evaluation kernels' two sin and cos routines against numpy within two ulps and CUDA's
+sincos within three, on uniform, log-uniform, near-multiple-of-pi/2 and table-edge samples;
+exact zeros and signs where the result is exact; the library's own values on the fallback
+path.  The routines: a three-constant Cody-Waite reduction to |r| <= pi/4 with Taylor
+polynomials of sin r through r^17 and cos r through r^16 (ocp_probe_sincos), and the
+table-driven one of the cart-pole and quadrotor models, |x| = k pi/512 + r with sin, cos of
+k pi/512 from a table and short polynomials in r (ocp_probe_sincos_table); both take the
+library routine for warps holding an argument beyond 1e5 or not finite."""
 import numpy as np
 import pytest
 import torch
@@ -10,12 +13,12 @@ import torch
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module")
-def probe():
+@pytest.fixture(scope="module", params=[False, True], ids=["reduced", "table"])
+def probe(request):
     if not torch.cuda.is_available():
         pytest.skip("needs a GPU")
     from paper_2510_03932_gb300 import ocp
-    return ocp.probe_sincos
+    return lambda x: ocp.probe_sincos(x, table=request.param)
 
 
 def ulps(got, ref):
@@ -34,7 +37,9 @@ def test_within_two_ulps(probe):
     x = np.concatenate([rng.uniform(-1.0, 1.0, 200000), rng.uniform(-7.0, 7.0, 200000),
                         rng.uniform(-1e5, 1e5, 100000), 10.0 ** rng.uniform(-300.0, 5.0, 100000),
                         k * (np.pi / 2) + rng.uniform(-1e-6, 1e-6, k.size),   # near multiples of pi/2
-                        np.arange(-64, 65) * (np.pi / 4)])
+                        np.arange(-64, 65) * (np.pi / 4),
+                        (np.arange(-4096, 4096) + 0.5) * (np.pi / 512),          # table edges
+                        (np.arange(-4096, 4096) + rng.uniform(-0.5, 0.5, 8192)) * (np.pi / 512)])
     x = x[np.abs(x) <= 1e5]
     s, c, sl, cl = run(probe, x)
     # against numpy (glibc: correctly rounded or within an ulp) and against CUDA's sincos
