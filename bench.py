@@ -84,7 +84,7 @@ def _counts(w):
 # bench reports no FP64 fraction for that model until they are measured again.
 FP64_OPS_PER_NODE = {("vdp", "eval_all"): 26.6, ("vdp", "jh"): 10.0, ("vdp", "jprod"): 13.0,
                      ("vdp", "jtprod"): 12.0, ("vdp", "hprod"): 11.0, ("vdp", "step"): 50.6,
-                     ("cartpole", "eval_all"): 110.8, ("cartpole", "jh"): 87.7, ("cartpole", "jprod"): 74.6,
+                     ("cartpole", "eval_all"): 109.7, ("cartpole", "jh"): 87.7, ("cartpole", "jprod"): 74.6,
                      ("cartpole", "jtprod"): 71.0, ("cartpole", "hprod"): 89.0, ("cartpole", "step"): 156.9,
                      ("quadrotor", "eval_all"): 235.5, ("quadrotor", "jh"): 163.3, ("quadrotor", "jprod"): 151.2,
                      ("quadrotor", "jtprod"): 143.0, ("quadrotor", "hprod"): 186.0, ("quadrotor", "step"): 382.8,
@@ -109,8 +109,8 @@ KERNEL_SOURCES = {
     "heat64": _COMMON + ["heat_kernels.cu"],
 }
 # Tags of the sources the FP64_OPS_PER_NODE counts (and TRAFFIC) were measured on.
-FP64_OPS_SRC = {"vdp": "cc658d1f082c", "vdp:euler": "cc658d1f082c", "cartpole": "fc0d1c1f54b5",
-                "quadrotor": "8626a7941187", "goddard": "5c6666cb0cfe", "heat64": "d7a6a1dbfeb5"}
+FP64_OPS_SRC = {"vdp": "76d84f0080b4", "vdp:euler": "76d84f0080b4", "cartpole": "810d82f3b0b7",
+                "quadrotor": "d9efc5bf84c0", "goddard": "fcf26598a4e3", "heat64": "cb98df7b64c7"}
 
 
 def kernel_source_tag(key):
@@ -159,7 +159,7 @@ def named_workload(name):
 # DRAM bytes (read + write) of one launch at a workload, from an ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum; writes still dirty in L2 when the kernel ends
 # are not counted), with the source tag of the kernel it was captured on (see traffic()).
-TRAFFIC = {("vdp_mu_n1e6", "step"): (227.13e6, "cc658d1f082c")}
+TRAFFIC = {("vdp_mu_n1e6", "step"): (227.69e6, "76d84f0080b4")}
 # Each SM's FP64 pipe completes 2 FP64 instructions (one lane each) per clock: the recipe's
 # nominal 1.25 TFLOP/s FP64 of GB300 is 6.25e11 FMA/s = 1.99 per clock per SM at 152 SMs and
 # 2070 MHz.  bench.py measures the rate live (measure_fp64_rate) and reports it beside the peak.

@@ -451,17 +451,43 @@ __device__ __forceinline__ void node_eval_tile(const NodeArgs<M>& a, const Model
         jv_node<M, false>(K, mjx, mju, mdp, 0.0, vz, jA[q], jB[q]);
       }
     }
-    if (own) {
-      if (WHV) {
-        double o[NZ];
-        hv_node<M>(a, K, hd, cqd, vz, o);
-        store_nz<M>(a, a.ohv, j, o);
+    // ---- Jacobian rows staged in shared memory: left part of row lt, right part of row lt-1
+    if (WJ && act) {
+#pragma unroll
+      for (int k = 0; k < NX; ++k) {
+        const int cnt = row_count<M>(k);
+        double* sj = sm + jrow_off<M>(k) * R;
+        if (lt < nrows) {
+          double* rp = sj + lt * cnt;
+#pragma unroll
+          for (int e = 0; e < M::MAXRX; ++e)
+            if (e < M::RX(k)) rp[e] = (M::XV(k, e) == k) ? (M::JZ(k, e) ? -1.0 : fma(mjx[k][e], K.one, -1.0)) : mjx[k][e];
+#pragma unroll
+          for (int e = 0; e < M::MAXRU; ++e)
+            if (e < M::RU(k)) rp[2 * M::RX(k) + e] = mju[k][e];
+        }
+        if (lt >= 1 && lt - 1 < nrows) {
+          double* rp = sj + (lt - 1) * cnt;
+#pragma unroll
+          for (int e = 0; e < M::MAXRX; ++e)
+            if (e < M::RX(k)) rp[M::RX(k) + e] = (M::XV(k, e) == k) ? (M::JZ(k, e) ? 1.0 : fma(mjx[k][e], K.one, 1.0)) : mjx[k][e];
+#pragma unroll
+          for (int e = 0; e < M::MAXRU; ++e)
+            if (e < M::RU(k)) rp[2 * M::RX(k) + M::RU(k) + e] = mju[k][e];
+        }
       }
+    }
+    if (own) {
       if (WJTV) {
         double wb[NX], wl[NX], wr[NX], o[NZ];
         load_bar<M>(a, K, a.wv, j, wb, wl, wr);
         jtv_node<M>(a, K, a.wv, j, bnd, mjx, mju, wl, wr, wb, o);
         store_nz<M>(a, a.ojtv, j, o);
+      }
+      if (WHV) {
+        double o[NZ];
+        hv_node<M>(a, K, hd, cqd, vz, o);
+        store_nz<M>(a, a.ohv, j, o);
       }
       if (WJV && bnd) {
         if (j == 0) {
@@ -507,32 +533,6 @@ __device__ __forceinline__ void node_eval_tile(const NodeArgs<M>& a, const Model
         for (int k = 0; k < NX; ++k) {
           if (sC) a.c[NX + k] = z[k];
           if (sJ) a.jv[NX + k] = 1.0;
-        }
-      }
-    }
-    // ---- Jacobian rows staged in shared memory: left part of row lt, right part of row lt-1
-    if (WJ && act) {
-#pragma unroll
-      for (int k = 0; k < NX; ++k) {
-        const int cnt = row_count<M>(k);
-        double* sj = sm + jrow_off<M>(k) * R;
-        if (lt < nrows) {
-          double* rp = sj + lt * cnt;
-#pragma unroll
-          for (int e = 0; e < M::MAXRX; ++e)
-            if (e < M::RX(k)) rp[e] = (M::XV(k, e) == k) ? (M::JZ(k, e) ? -1.0 : fma(mjx[k][e], K.one, -1.0)) : mjx[k][e];
-#pragma unroll
-          for (int e = 0; e < M::MAXRU; ++e)
-            if (e < M::RU(k)) rp[2 * M::RX(k) + e] = mju[k][e];
-        }
-        if (lt >= 1 && lt - 1 < nrows) {
-          double* rp = sj + (lt - 1) * cnt;
-#pragma unroll
-          for (int e = 0; e < M::MAXRX; ++e)
-            if (e < M::RX(k)) rp[M::RX(k) + e] = (M::XV(k, e) == k) ? (M::JZ(k, e) ? 1.0 : fma(mjx[k][e], K.one, 1.0)) : mjx[k][e];
-#pragma unroll
-          for (int e = 0; e < M::MAXRU; ++e)
-            if (e < M::RU(k)) rp[2 * M::RX(k) + M::RU(k) + e] = mju[k][e];
         }
       }
     }
