@@ -51,6 +51,13 @@ ocp_status ocp_probe_sincos(const double* x, double* s, double* c, double* s_lib
 ocp_status ocp_probe_sincos_table(const double* x, double* s, double* c, double* s_lib, double* c_lib, int64_t n,
                                   void* stream);
 
+/* The Goddard kernels' table-driven exponential (x = (32 m + j) ln 2/32 + r, 2^(j/32) from a table
+ * of the doubles nearest the exact values, a degree-6 polynomial in r, 2^m on the exponent
+ * bits; the library routine for warps holding an argument beyond 700 in magnitude or not
+ * finite) and CUDA's exp on the same n arguments: e[i] and e_lib[i] (device arrays;
+ * asynchronous on `stream`).  Errors: OCP_EINVAL, OCP_ECUDA (ocp_last_error(NULL)). */
+ocp_status ocp_probe_exp_table(const double* x, double* e, double* e_lib, int64_t n, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -14,6 +14,7 @@
 #include "model_base.cuh"
 #include "ocp_internal.h"
 #include "ocp_probe.h"
+#include "exp_table.cuh"
 #include "sincos_table.cuh"
 
 namespace {
@@ -79,7 +80,27 @@ __global__ void k_probe_sincos_tab(const double* x, double* s, double* c, double
   }
 }
 
+// The table-driven exponential (exp_tab) and the library's on the same arguments.
+__global__ void k_probe_exp(const double* x, double* e, double* el, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    e[i] = ocpg::exp_tab(x[i], 1.0, -0.0);
+    el[i] = exp(x[i]);
+  }
+}
+
 }  // namespace
+
+extern "C" ocp_status ocp_probe_exp_table(const double* x, double* e, double* e_lib, int64_t n, void* stream) {
+  OCP_RANGE();
+  const double* p[3] = {x, e, e_lib};
+  for (const double* q : p)
+    if (!q || ((uintptr_t)q & 7u)) return ocpg::set_err(nullptr, OCP_EINVAL, "ocp_probe_exp_table: bad pointer");
+  if (n < 0) return ocpg::set_err(nullptr, OCP_EINVAL, "ocp_probe_exp_table: n < 0");
+  if (n == 0) return OCP_OK;
+  const int grid = (int)((n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096);
+  k_probe_exp<<<grid, 256, 0, (cudaStream_t)stream>>>(x, e, e_lib, n);
+  return ocpg::cuda_err(nullptr, cudaGetLastError(), "ocp_probe_exp_table launch");
+}
 
 extern "C" ocp_status ocp_probe_sincos_table(const double* x, double* s, double* c, double* s_lib, double* c_lib,
                                              int64_t n, void* stream) {

@@ -28,6 +28,7 @@
 // lane+1 by shuffle (or the next warp's lane 0 through shared memory).  No atomics on values.
 #include <cstring>
 
+#include "exp_table.cuh"
 #include "node_kernels.cuh"
 #include "ocp_internal.h"
 
@@ -148,7 +149,7 @@ __global__ void __launch_bounds__(GT) k_god(const __grid_constant__ GodArgs a) {
     if (act) {
       const double r = __ldg(a.x + 3 * j), v = __ldg(a.x + 3 * j + 1), m = __ldg(a.x + 3 * j + 2);
       const double u = __ldg(a.x + a.uoff + j);
-      const double E = exp(fma(-beta, r, beta));          // exp(-beta (r - 1))
+      const double E = exp_tab(fma(-beta, r, beta), a.one, a.mz);  // exp(-beta (r - 1))
       const double im = recip(a.one, m), ir = recip(a.one, r);
       const double ir2 = gmul(a, ir, ir);
       const double q1 = gmul(a, gmul(a, Cd, E), im);        // Cd E / m

@@ -100,6 +100,7 @@ _SIGS = {
     "ocp_probe_recip": [_P, _P, _I64, _P],
     "ocp_probe_sincos": [_P, _P, _P, _P, _P, _I64, _P],
     "ocp_probe_sincos_table": [_P, _P, _P, _P, _P, _I64, _P],
+    "ocp_probe_exp_table": [_P, _P, _P, _I64, _P],
     "ocp_set_fault": [C.c_char_p],
     "ocp_last_error": [_P],
 }
@@ -162,6 +163,17 @@ def probe_sincos(x, stream=None, table=False):
     outs = [torch.empty_like(x) for _ in range(4)]
     fn = lib().ocp_probe_sincos_table if table else lib().ocp_probe_sincos
     _check(fn(*[C.c_void_p(t.data_ptr()) for t in [x] + outs], int(x.numel()), _stream(stream)))
+    return tuple(outs)
+
+
+def probe_exp(x, stream=None):
+    """ocp_probe_exp_table: exp of the kernels' table-driven routine and CUDA's exp for every entry
+    of the CUDA float64 tensor x."""
+    if x.dtype != torch.float64 or not x.is_cuda or not x.is_contiguous():
+        raise TypeError("x must be a contiguous float64 CUDA tensor")
+    outs = [torch.empty_like(x) for _ in range(2)]
+    _check(lib().ocp_probe_exp_table(*[C.c_void_p(t.data_ptr()) for t in [x] + outs], int(x.numel()),
+                                     _stream(stream)))
     return tuple(outs)
 
 
