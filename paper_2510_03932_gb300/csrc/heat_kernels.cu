@@ -34,7 +34,9 @@ struct HeatArgs {
   const double* __restrict__ x;
   const double* __restrict__ y;
   const double* __restrict__ v;
+  const double* __restrict__ v2;  // Jv and J^T w in one launch: the direction of J^T w
   double *f, *c, *g, *jv, *hv, *out;
+  double* out2;                   // ... and J^T w
   double* partials;
   unsigned* counter;
   int64_t N, nb, B, E, ntiles, uoff;
@@ -410,16 +412,23 @@ __global__ void __launch_bounds__(HT_THREADS, 5) k_heat_hprod(const __grid_const
 //   J^T w:  out_a = (w_{a,j-1} - w_{a,j}) + wbar_a dd_a - hh/dx^2 (wbar_{a-1} + wbar_{a+1}),
 //           out_u = -hh/dx^2 wbar_0  (dd_a = -hh df_a/dx_a), node-local on disjoint tiles; the
 //           result is staged and stored node by node in runs of the unit's cells.
+//   Both (the heat model's fused step): the two products of the same unit in one launch, on the
+//           tiles of Jv; J^T w for the owned nodes, its result written over the staged states
+//           once Jv has read them.  Each entry by the same expressions as the separate launches.
 // ======================================================================================
-enum : int { HP_JPROD = 0, HP_JTPROD = 1 };
+enum : int { HP_JPROD = 0, HP_JTPROD = 1, HP_BOTH = 2 };
 constexpr int HP_LDV = HJ_CELLS + 3;  // padded row of the staged direction (or J^T w result)
 
 template <int KIND>
 __global__ void __launch_bounds__(HJ_THREADS, 18) k_heat_prod_unit(const __grid_constant__ HeatArgs a, int cgroups) {
-  constexpr bool JP = KIND == HP_JPROD, JT = KIND == HP_JTPROD;
+  constexpr bool BOTH = KIND == HP_BOTH;
+  constexpr bool JP = KIND == HP_JPROD || BOTH, JT = KIND == HP_JTPROD || BOTH;
   constexpr int LDV = JP ? HP_LDV : HJ_LD;
-  __shared__ double sX[HT_LANES * HJ_LD];  // states of the unit's cells
-  __shared__ double sV[HT_LANES * LDV];    // Jv: the direction; J^T w: the result
+  __shared__ double sX[HT_LANES * HJ_LD];  // states of the unit's cells (both: then the J^T w result)
+  __shared__ double sV[HT_LANES * LDV];    // Jv: the direction; J^T w alone: the result
+  double* const sO = BOTH ? sX : sV;       // the J^T w result (row length HJ_LD either way)
+  const double* const wv = BOTH ? a.v2 : a.v;
+  double* const wout = BOTH ? a.out2 : a.out;
   const int n = a.n;
   const int t = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t units = a.ntiles * cgroups;
@@ -443,8 +452,10 @@ __global__ void __launch_bounds__(HJ_THREADS, 18) k_heat_prod_unit(const __grid_
       nn = (int)min((int64_t)HT_LANES, a.N + 1 - r0);
       bnd = (tile == 0) || (r0 + HT_LANES > a.N);
     }
+    if (BOTH) bnd = (r0 == 0) || (r0 + nown == a.N + 1);  // the tile holds node 0 or node N
     const int64_t j = r0 + t;
     const bool act = t < nn;
+    const bool jown = BOTH ? (t < nown) : act;  // J^T w: the owned nodes
     for (int i = threadIdx.x; i < nn * nc; i += HJ_THREADS) {
       const int tt = i / nc, kk = i - tt * nc;
       sX[tt * HJ_LD + kk] = __ldg(a.x + (int64_t)n * (r0 + tt) + c0 + kk);
@@ -482,20 +493,20 @@ __global__ void __launch_bounds__(HJ_THREADS, 18) k_heat_prod_unit(const __grid_
     if (JT && kb < ke) {
       // wbar of cells k0-1 .. k1 (clamped), rolling window
       auto wbar = [&](int k, double& wl, double& wr) {
-        const double* row = a.v + a.nb + (int64_t)k * a.N;
+        const double* row = wv + a.nb + (int64_t)k * a.N;
         wl = (j >= 1) ? __ldg(row + j - 1) : 0.0;
         wr = (j < a.N) ? __ldg(row + j) : 0.0;
       };
       const int k0 = c0 + kb, k1 = c0 + ke;
       double wbm = 0.0, wbc = 0.0, wbp = 0.0, wlc = 0.0, wrc = 0.0;
-      if (act) {
+      if (jown) {
         if (k0 > 0) { double l2, r2; wbar(k0 - 1, l2, r2); wbm = hadd(a, l2, r2); }
         wbar(k0, wlc, wrc);
         wbc = hadd(a, wlc, wrc);
-        if (k0 == 0) a.out[a.uoff + j] = hmul(a, a.mhidx2, wbc);  // control column: -hh/dx^2 wbar_0
+        if (k0 == 0) wout[a.uoff + j] = hmul(a, a.mhidx2, wbc);  // control column: -hh/dx^2 wbar_0
       }
       for (int k = k0; k < k1; ++k) {
-        if (act) {
+        if (jown) {
           double wlp = 0.0, wrp = 0.0;
           if (k + 1 < n) { wbar(k + 1, wlp, wrp); wbp = hadd(a, wlp, wrp); } else wbp = 0.0;
           const double xk = sX[t * HJ_LD + (k - c0)];
@@ -504,10 +515,10 @@ __global__ void __launch_bounds__(HJ_THREADS, 18) k_heat_prod_unit(const __grid_
           double s = fma(wbc, dk, hsub(a, wlc, wrc));
           s = fma(a.mhidx2, hadd(a, wbm, wbp), s);
           if (bnd) {  // only the CTAs holding node 0 or node N (uniform branch)
-            if (j == 0) s = hadd(a, s, __ldg(a.v + k));
-            if (a.has_final && j == a.N) s = hadd(a, s, __ldg(a.v + n + k));
+            if (j == 0) s = hadd(a, s, __ldg(wv + k));
+            if (a.has_final && j == a.N) s = hadd(a, s, __ldg(wv + n + k));
           }
-          sV[t * LDV + (k - c0)] = s;
+          sO[t * HJ_LD + (k - c0)] = s;
           wbm = wbc; wbc = wbp; wlc = wlp; wrc = wrp;
         }
       }
@@ -515,10 +526,11 @@ __global__ void __launch_bounds__(HJ_THREADS, 18) k_heat_prod_unit(const __grid_
     __syncthreads();
     if (JT) {
       // node-major results of the unit's cells, in runs of nc per node
-      double* dst = a.out + (int64_t)n * r0 + c0;
-      for (int i = threadIdx.x; i < nn * nc; i += HJ_THREADS) {
+      double* dst = wout + (int64_t)n * r0 + c0;
+      const int nst = BOTH ? nown : nn;
+      for (int i = threadIdx.x; i < nst * nc; i += HJ_THREADS) {
         const int tt = i / nc, kk = i - tt * nc;
-        dst[(int64_t)n * tt + kk] = sV[tt * HJ_LD + kk];
+        dst[(int64_t)n * tt + kk] = sO[tt * HJ_LD + kk];
       }
     }
     __syncthreads();
@@ -614,6 +626,19 @@ ocp_status heat_eval(ocp* h, unsigned out, const EvalCall& c, cudaStream_t s) {
     case O_J | O_H: return heat_jh_t<O_J | O_H>(h, c, s);
     default: return heat_eval_t<O_ALL>(h, c, s);
   }
+}
+
+// Jv (jp.v -> jp.out) and J^T w (jt.v -> jt.out) of the heat model in one launch (the fused step)
+ocp_status heat_prod2(ocp* h, const ProdCall& jp, const ProdCall& jt, cudaStream_t s) {
+  HeatArgs a;
+  heat_fill(h, 1.0, a);
+  a.x = jp.x; a.v = jp.v; a.out = jp.out; a.v2 = jt.v; a.out2 = jt.out;
+  const int cgroups = (h->nx + HJ_CELLS - 1) / HJ_CELLS;
+  a.ntiles = (h->N + 1 + (HT_LANES - 2)) / (HT_LANES - 1);
+  const int grid = occupancy_grid(h, (const void*)k_heat_prod_unit<HP_BOTH>, HJ_THREADS, 0, a.ntiles * cgroups);
+  if (grid <= 0) return set_err(h, OCP_ECUDA, "occupancy query failed");
+  k_heat_prod_unit<HP_BOTH><<<grid, HJ_THREADS, 0, s>>>(a, cgroups);
+  return cuda_err(h, cudaGetLastError(), "heat product launch");
 }
 
 ocp_status heat_prod(ocp* h, const ProdCall& c, cudaStream_t s) {
