@@ -555,21 +555,21 @@ ocp_status ocp_eval_step(ocp_t* h, const double* x, const double* y, double sigm
   NEED(x); NEED(y); NEED(vn); NEED(vm); NEED(f); NEED(cv); NEED(g); NEED(jvals); NEED(hvals);
   NEED(Jv); NEED(Jtv); NEED(Hv);
   if (h->model == OCP_MODEL_HEAT1D) {
-    // the heat model runs three kernels in sequence: the evaluation, Jv and J^T w in one launch,
-    // H v; then each product's path, boundary-inequality and boundary-cost terms as in the
+    // the heat model runs two kernels in sequence: the evaluation, and Jv, J^T w and H v in one
+    // launch; then each product's path, boundary-inequality and boundary-cost terms as in the
     // separate calls (each array's own operations in the same order: the same bits)
     ocp_status st = ocp_eval_all(h, x, y, sigma, f, cv, g, jvals, hvals, stream);
-    ProdCall a, b;
+    ProdCall a, b, c;
     a.kind = P_JPROD; a.x = x; a.v = vn; a.out = Jv;
     b.kind = P_JTPROD; b.x = x; b.v = vm; b.out = Jtv;
+    c.kind = P_HPROD; c.x = x; c.y = y; c.sigma = sigma; c.v = vn; c.out = Hv;
     cudaStream_t s = (cudaStream_t)stream;
-    if (st == OCP_OK) st = heat_prod2(h, a, b, s);
-    for (const ProdCall* pc : {&a, &b}) {
+    if (st == OCP_OK) st = heat_prod2(h, a, b, &c, s);
+    for (const ProdCall* pc : {&a, &b, &c}) {
       if (st == OCP_OK && h->pat.npath > 0) st = path_prod(h, *pc, s);
       if (st == OCP_OK && h->pat.nbin > 0) st = bin_prod(h, *pc, s);
       if (st == OCP_OK && h->has_bol) st = bol_prod(h, *pc, s);
     }
-    if (st == OCP_OK) st = hprod(h, x, y, sigma, vn, Hv, stream);
     return st;
   }
   EvalCall c = full_call(h);

@@ -37,6 +37,7 @@ struct HeatArgs {
   const double* __restrict__ v2;  // Jv and J^T w in one launch: the direction of J^T w
   double *f, *c, *g, *jv, *hv, *out;
   double* out2;                   // ... and J^T w
+  double* out3;                   // Jv, J^T w and H v in one launch: H v (direction v, multipliers y)
   double* partials;
   unsigned* counter;
   int64_t N, nb, B, E, ntiles, uoff;
@@ -414,14 +415,16 @@ __global__ void __launch_bounds__(HT_THREADS, 5) k_heat_hprod(const __grid_const
 //           result is staged and stored node by node in runs of the unit's cells.
 //   Both (the heat model's fused step): the two products of the same unit in one launch, on the
 //           tiles of Jv; J^T w for the owned nodes, its result written over the staged states
-//           once Jv has read them.  Each entry by the same expressions as the separate launches.
+//           once Jv has read them.  All three: H v of the owned nodes as well, each entry formed
+//           in Jv's cell loop from the same state and direction values and stored by its lane.
+//           Each entry by the same expressions as the separate launches.
 // ======================================================================================
-enum : int { HP_JPROD = 0, HP_JTPROD = 1, HP_BOTH = 2 };
+enum : int { HP_JPROD = 0, HP_JTPROD = 1, HP_BOTH = 2, HP_ALL3 = 3 };
 constexpr int HP_LDV = HJ_CELLS + 3;  // padded row of the staged direction (or J^T w result)
 
 template <int KIND>
 __global__ void __launch_bounds__(HJ_THREADS, 18) k_heat_prod_unit(const __grid_constant__ HeatArgs a, int cgroups) {
-  constexpr bool BOTH = KIND == HP_BOTH;
+  constexpr bool ALL3 = KIND == HP_ALL3, BOTH = KIND == HP_BOTH || ALL3;
   constexpr bool JP = KIND == HP_JPROD || BOTH, JT = KIND == HP_JTPROD || BOTH;
   constexpr int LDV = JP ? HP_LDV : HJ_LD;
   __shared__ double sX[HT_LANES * HJ_LD];  // states of the unit's cells (both: then the J^T w result)
@@ -472,12 +475,24 @@ __global__ void __launch_bounds__(HJ_THREADS, 18) k_heat_prod_unit(const __grid_
     }
     __syncthreads();
     if (JP) {
+      const bool endp = (j == 0) || (j == a.N);
+      if (ALL3 && c0 == 0 && warp == 0 && jown) {  // H v, the control: 2 sigma w r v_u
+        const double cu = a.hu ? (endp ? a.cq_end[n] : a.cq_in[n]) : 0.0;
+        a.out3[a.uoff + j] = hmul(a, cu, sV[t * HP_LDV]);
+      }
       for (int kk = kb; kk < ke; ++kk) {
         const int k = c0 + kk;
         double p = 0.0, vk = 0.0;
         if (act) {
           const double xk = sX[t * HJ_LD + kk];
           const bool last = (k == n - 1);
+          if (ALL3 && jown) {  // H v: (2 sigma w q_k + 6 hh ybar_k x_k) v_k
+            const double* yrow = a.y + a.nb + (int64_t)k * a.N;
+            const double yl = (j >= 1) ? __ldg(yrow + j - 1) : 0.0;
+            const double yr = (j < a.N) ? __ldg(yrow + j) : 0.0;
+            const double hk = fma(hmul(a, a.h6, hadd(a, yl, yr)), xk, endp ? a.cq_end[k] : a.cq_in[k]);
+            a.out3[(int64_t)n * j + k] = hmul(a, hk, sV[t * HP_LDV + kk + 1]);
+          }
           vk = sV[t * HP_LDV + kk + 1];
           const double vl = sV[t * HP_LDV + kk];  // cell k-1, or the control for k = 0
           const double dk = fma(a.h3, hmul(a, xk, xk), last ? a.d_last : a.d_in);
@@ -628,16 +643,20 @@ ocp_status heat_eval(ocp* h, unsigned out, const EvalCall& c, cudaStream_t s) {
   }
 }
 
-// Jv (jp.v -> jp.out) and J^T w (jt.v -> jt.out) of the heat model in one launch (the fused step)
-ocp_status heat_prod2(ocp* h, const ProdCall& jp, const ProdCall& jt, cudaStream_t s) {
+// Jv (jp.v -> jp.out), J^T w (jt.v -> jt.out) and, with hp, H v (hp.y, hp.sigma, the direction
+// jp.v -> hp.out) of the heat model in one launch (the fused step)
+ocp_status heat_prod2(ocp* h, const ProdCall& jp, const ProdCall& jt, const ProdCall* hp, cudaStream_t s) {
   HeatArgs a;
-  heat_fill(h, 1.0, a);
+  heat_fill(h, hp ? hp->sigma : 1.0, a);
   a.x = jp.x; a.v = jp.v; a.out = jp.out; a.v2 = jt.v; a.out2 = jt.out;
+  if (hp) { a.y = hp->y; a.out3 = hp->out; }
   const int cgroups = (h->nx + HJ_CELLS - 1) / HJ_CELLS;
   a.ntiles = (h->N + 1 + (HT_LANES - 2)) / (HT_LANES - 1);
-  const int grid = occupancy_grid(h, (const void*)k_heat_prod_unit<HP_BOTH>, HJ_THREADS, 0, a.ntiles * cgroups);
+  const void* k = hp ? (const void*)k_heat_prod_unit<HP_ALL3> : (const void*)k_heat_prod_unit<HP_BOTH>;
+  const int grid = occupancy_grid(h, k, HJ_THREADS, 0, a.ntiles * cgroups);
   if (grid <= 0) return set_err(h, OCP_ECUDA, "occupancy query failed");
-  k_heat_prod_unit<HP_BOTH><<<grid, HJ_THREADS, 0, s>>>(a, cgroups);
+  if (hp) k_heat_prod_unit<HP_ALL3><<<grid, HJ_THREADS, 0, s>>>(a, cgroups);
+  else k_heat_prod_unit<HP_BOTH><<<grid, HJ_THREADS, 0, s>>>(a, cgroups);
   return cuda_err(h, cudaGetLastError(), "heat product launch");
 }
 

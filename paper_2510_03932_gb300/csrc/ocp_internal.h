@@ -215,8 +215,8 @@ ocp_status goddard_eval(ocp* h, unsigned out, const EvalCall& c, cudaStream_t s)
 ocp_status goddard_prod(ocp* h, const ProdCall& c, cudaStream_t s);
 ocp_status heat_eval(ocp* h, unsigned out, const EvalCall& c, cudaStream_t s);
 ocp_status heat_prod(ocp* h, const ProdCall& c, cudaStream_t s);
-// The heat model's Jv (jp) and J^T w (jt) in one launch.
-ocp_status heat_prod2(ocp* h, const ProdCall& jp, const ProdCall& jt, cudaStream_t s);
+// The heat model's Jv (jp), J^T w (jt) and, unless hp is null, H v (hp) in one launch.
+ocp_status heat_prod2(ocp* h, const ProdCall& jp, const ProdCall& jt, const ProdCall* hp, cudaStream_t s);
 
 struct EvalCall;
 ocp_status dispatch_eval(ocp* h, unsigned out, const EvalCall& c, void* stream);
