@@ -281,7 +281,8 @@ ocp_status ocp_eval_all(ocp_t* h, const double* x, const double* y, double sigma
 /* The whole per-iteration evaluation in one pass over the nodes: everything of ocp_eval_all
  * plus the products Jv = J vn, Jtv = J^T vm and Hv = H(y, sigma) vn at the same x, sharing the
  * per-node derivative work and the loads of x and y (one launch for the node models; the heat
- * model runs its four kernels in sequence).  vn has length n, vm length m.  All arguments are
+ * model runs two: its evaluation, then its three products in one).  vn has length n, vm length
+ * m.  All arguments are
  * required.  Values are bit-identical to the separate calls. */
 ocp_status ocp_eval_step(ocp_t* h, const double* x, const double* y, double sigma, const double* vn,
                          const double* vm, double* f, double* c, double* g, double* jvals,
