@@ -98,3 +98,95 @@ def test_exp_reduction_constants():
                    (4, r"fma\(r, q, (\S+)\);\s+// 1/4!"), (3, r"fma\(r, q, (\S+)\);\s+// 1/3!")):
         c = float.fromhex(re.search(pat, src).group(1))
         assert c == float(1 / mpmath.factorial(n)), n
+
+
+def _fma(a, b, c):
+    """a * b + c with one rounding (exact rational arithmetic, then the nearest double)."""
+    from fractions import Fraction
+    return float(Fraction(a) * Fraction(b) + Fraction(c))
+
+
+def _hexes(pattern, src, count):
+    found = [float.fromhex(m) for m in re.findall(pattern, src)]
+    assert len(found) == count, (pattern, found)
+    return found
+
+
+def test_sincos_method_within_two_ulps_on_the_cpu():
+    """The table-driven sin and cos, replayed step by step on the CPU with the constants and table
+    of the committed sources (each FMA rounded once), stay within two ulps of the exact values
+    (mpmath) on a sample that covers small, large, near-multiple-of-pi/2 and table-edge arguments."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 40
+    src = open(os.path.join(CSRC, "sincos_table.cuh")).read()
+    inv = _hexes(r"fma\(ax, (\S+), 0x1\.8p52\);\s+// 512/pi", src, 1)[0]
+    p1, p2, p3 = _hexes(r"r = fma\(-k, (\S+), (?:ax|r)\);\s+// P\d", src, 3)
+    HEX = r"(-?0x[0-9a-f.]+p[-+]\d+)"
+    m = re.search(r"fma\(z, " + HEX + ", " + HEX + r"\), r\);\s+// 1/5!, -1/3!", src)
+    c5, c3 = float.fromhex(m.group(1)), float.fromhex(m.group(2))
+    c4 = float.fromhex(re.search(r"fma\(z, " + HEX + r", -0\.5\)\);\s+// 1/4!, -1/2!", src).group(1))
+    assert (c5, c3, c4) == (1 / 120, -1 / 6, 1 / 24)
+    tab = table()
+    C52 = 1.5 * 2.0 ** 52
+
+    def sincos(x):
+        ax = abs(x)
+        t = _fma(ax, inv, C52)
+        k = _fma(-C52, 1.0, t)
+        r = _fma(-k, p1, ax); r = _fma(-k, p2, r); r = _fma(-k, p3, r)
+        ki = int(k)
+        sa, ca = tab[ki & 255]
+        z = _fma(r, r, -0.0)
+        sr = _fma(_fma(r, z, -0.0), _fma(z, c5, c3), r)
+        cm1 = _fma(z, _fma(z, c4, -0.5), -0.0)
+        sy = _fma(ca, sr, _fma(sa, cm1, sa))
+        cy = _fma(-sa, sr, _fma(ca, cm1, ca))
+        q = (ki >> 8) & 3
+        s, c = [(sy, cy), (cy, -sy), (-sy, -cy), (-cy, sy)][q]
+        return (s if x >= 0 else -s), c
+
+    rng = np.random.default_rng(29)
+    k = rng.integers(-60000, 60000, 300)
+    xs = np.concatenate([rng.uniform(-1, 1, 400), rng.uniform(-1e5, 1e5, 300), 10.0 ** rng.uniform(-300, 5, 200),
+                         k * (np.pi / 2) + rng.uniform(-1e-6, 1e-6, k.size),
+                         (rng.integers(-4000, 4000, 400) + 0.5) * (np.pi / 512)])
+    xs = xs[np.abs(xs) <= 1e5]
+    for x in xs:
+        s, c = sincos(float(x))
+        es, ec = mpmath.sin(float(x)), mpmath.cos(float(x))
+        for got, exact in ((s, es), (c, ec)):
+            ref = float(exact)
+            assert abs(mpmath.mpf(got) - exact) <= 2 * np.spacing(max(abs(ref), 2.0 ** -1022)), (x, got, ref)
+
+
+def test_exp_method_within_one_ulp_on_the_cpu():
+    """The table-driven exponential, replayed step by step on the CPU with the constants and table
+    of the committed sources, stays within one ulp of the exact value (mpmath)."""
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 40
+    src = open(os.path.join(CSRC, "exp_table.cuh")).read()
+    inv = float.fromhex(re.search(r"fma\(x, (\S+), 0x1\.8p52\);\s+// 32 / ln 2", src).group(1))
+    l1, l2 = _hexes(r"r = fma\(-k, (\S+), (?:x|r)\);\s+// L\d", src, 2)
+    c6 = float.fromhex(re.search(r"fma\(r, (\S+), \S+\);\s+// 1/6!", src).group(1))
+    c5 = float.fromhex(re.search(r"fma\(r, \S+, (\S+)\);\s+// 1/6!, 1/5!", src).group(1))
+    c4 = float.fromhex(re.search(r"fma\(r, q, (\S+)\);\s+// 1/4!", src).group(1))
+    c3 = float.fromhex(re.search(r"fma\(r, q, (\S+)\);\s+// 1/3!", src).group(1))
+    tab = exp_table()
+    C52 = 1.5 * 2.0 ** 52
+
+    def ex(x):
+        t = _fma(x, inv, C52)
+        k = _fma(-C52, 1.0, t)
+        r = _fma(-k, l1, x); r = _fma(-k, l2, r)
+        ki = int(k)
+        q = _fma(r, c6, c5); q = _fma(r, q, c4); q = _fma(r, q, c3); q = _fma(r, q, 0.5)
+        p = _fma(_fma(r, r, -0.0), q, r)
+        tj = tab[ki & 31]
+        return _fma(tj, p, tj) * 2.0 ** (ki >> 5)
+
+    rng = np.random.default_rng(31)
+    xs = np.concatenate([rng.uniform(-1, 1, 400), rng.uniform(-20, 0, 400), rng.uniform(-700, 700, 300),
+                         (rng.integers(-20000, 20000, 300) + 0.5) * (np.log(2) / 32)])
+    for x in xs:
+        got, exact = ex(float(x)), mpmath.exp(float(x))
+        assert abs(mpmath.mpf(got) - exact) <= np.spacing(float(exact)), (x, got)
