@@ -35,10 +35,11 @@ ocp_status ocp_probe_fp64(int op, int blocks, int threads, int iters, double* ou
  * OCP_ECUDA (ocp_last_error(NULL)). */
 ocp_status ocp_probe_recip(const double* d, double* out, int64_t n, void* stream);
 
-/* The evaluation kernels' sin and cos (a three-constant Cody-Waite reduction to |r| <= pi/4 and
- * Taylor polynomials, with the library routine for warps holding an argument beyond 1e5 or not
- * finite) and CUDA's sincos on the same n arguments: s[i], c[i] and s_lib[i], c_lib[i] (device
- * arrays; asynchronous on `stream`), so that a test can bound the difference.  Errors:
+/* The library's reduced-argument sin and cos (a three-constant Cody-Waite reduction to
+ * |r| <= pi/4 and Taylor polynomials, with CUDA's routine for warps holding an argument beyond
+ * 1e5 or not finite; the evaluation kernels used it before the table-driven routine below
+ * replaced it) and CUDA's sincos on the same n arguments: s[i], c[i] and s_lib[i], c_lib[i]
+ * (device arrays; asynchronous on `stream`), so that a test can bound the difference.  Errors:
  * OCP_EINVAL, OCP_ECUDA (ocp_last_error(NULL)). */
 ocp_status ocp_probe_sincos(const double* x, double* s, double* c, double* s_lib, double* c_lib, int64_t n,
                             void* stream);

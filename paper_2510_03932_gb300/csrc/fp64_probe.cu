@@ -52,7 +52,7 @@ __global__ void k_probe_recip(const double* d, double* out, int64_t n, double on
     out[i] = ocpg::recip(one, d[i]);
 }
 
-// The kernels' sincos (sincos_red) and the library's on the same arguments.
+// The reduced-argument sincos (sincos_red) and the library's on the same arguments.
 __global__ void k_probe_sincos(const double* x, double* s, double* c, double* sl, double* cl, int64_t n,
                                const __grid_constant__ ocpg::ModelConst K) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
